@@ -1,0 +1,216 @@
+"""Pins for the oracle's whole step (closed forms, invariants, brute force)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import OracleEnv
+from oracle import distance as ds
+from oracle.broadphase import candidates, canonical
+from oracle.ccd import accd_batch, accd_toi, exact_toi
+
+
+def _run(sc, params=None, steps=None):
+    env = OracleEnv(sc.scene, params or sc.params)
+    x, v, y, yd = env.rest_state()
+    if sc.v0 is not None:
+        v = sc.v0.copy()
+    if sc.ydot0 is not None:
+        yd = sc.ydot0.copy()
+    out = [(x, v, y, yd, None)]
+    for s in range(steps if steps is not None else sc.n_steps):
+        sy = env.targets_from_delta(sc.delta(s))
+        x, v, y, yd, st = env.step(x, v, y, yd, sy)
+        out.append((x, v, y, yd, st))
+    return env, out
+
+
+def test_free_fall_closed_form():
+    sc = scenes.free_fall_scene()
+    prm = sc.params.parity()
+    env, out = _run(sc, prm)
+    x0, v0, y0, yd0, _ = out[0]
+    h, g = prm.dt, np.asarray(prm.gravity)
+    for n, (x, v, y, yd, st) in enumerate(out[1:], start=1):
+        assert st.status == 0
+        xe = x0 + n * h * v0 + 0.5 * n * (n + 1) * h * h * g
+        assert np.abs(x - xe).max() < 1e-12
+        pe = y0[0, :3] + n * h * yd0[0, :3] + 0.5 * n * (n + 1) * h * h * g
+        assert np.abs(y[0, :3] - pe).max() < 1e-12
+        assert np.abs(y[0, 3:] - y0[0, 3:]).max() < 1e-12
+        assert st.newton_iters <= 2
+
+
+def test_momentum_conserved_through_contact():
+    sc = scenes.small_contact_scene(body="cube", driven=False)
+    sc.scene.pinned[:] = False
+    prm = sc.params.parity()
+    prm.gravity = (0.0, 0.0, 0.0)
+    env = OracleEnv(sc.scene, prm)
+    x, v, y, yd = env.rest_state()
+    yd[0, 2] = -0.08                       # cube moves down onto the gel
+    m = env.gel.mass
+    mb = env.bodies[0].mass
+    P0 = (m[:, None] * v).sum(0) + mb * yd[0, :3]
+    touched = False
+    for s in range(8):
+        x, v, y, yd, st = env.step(x, v, y, yd, y.copy())
+        assert st.status == 0
+        P = (m[:, None] * v).sum(0) + mb * yd[0, :3]
+        assert np.abs(P - P0).max() < 1e-5 * np.abs(P0).max()
+        touched |= st.min_dist < prm.dhat
+    assert touched, "the cube never came within dhat of the gel"
+
+
+def test_rigid_spin_stays_rotation():
+    sc = scenes.spin_scene(omega=(0.0, 0.0, 20.0))
+    prm = sc.params.parity()
+    env, out = _run(sc, prm)
+    h = prm.dt
+    for n, (x, v, y, yd, st) in enumerate(out[1:], start=1):
+        A = np.stack([y[0, 3:6], y[0, 6:9], y[0, 9:12]], axis=1)
+        assert abs(np.linalg.det(A) - 1.0) < 1e-7
+        assert np.abs(A.T @ A - np.eye(3)).max() < 1e-7
+        ang = np.arctan2(A[1, 0], A[0, 0])
+        assert 0.9 * n * 20.0 * h <= ang <= n * 20.0 * h * (1 + 1e-9)
+
+
+def test_config0_invariants_and_monotone_energy():
+    sc = scenes.config0()
+    env, out = _run(sc)
+    for x, v, y, yd, st in out[1:]:
+        assert st.status == 0
+        assert st.min_dist > 0.0
+        assert st.min_J > 0.0
+        for E0, E1 in st.energies:
+            assert E1 <= E0
+    # by the end the cube has pressed the gel: contact pairs within dhat exist
+    assert out[-1][4].min_dist < sc.params.dhat
+
+
+def test_converged_step_is_stationary():
+    sc = scenes.small_contact_scene(body="sphere", driven=True, depth=2e-4, n_steps=3)
+    prm = sc.params.parity()
+    env = OracleEnv(sc.scene, prm)
+    x, v, y, yd = env.rest_state()
+    for s in range(3):
+        x, v, y, yd, st = env.step(x, v, y, yd, env.targets_from_delta(sc.delta(s)))
+        assert st.status == 0
+    assert st.min_dist < prm.dhat
+    pairs = env.pair_arrays(*env.static_pairs(x, y))
+    g, _ = env.grad_hess(x, y, st.ctx, pairs)
+    # compare with the gravity force scale of a gel vertex
+    scale = prm.dt ** 2 * 9.81 * env.gel.mass.max()
+    assert np.abs(g[env.free]).max() < 1e-3 * scale
+
+
+def test_objective_gradient_matches_energy():
+    sc = scenes.small_contact_scene(body="sphere", driven=True, depth=2e-4, n_steps=3)
+    prm = sc.params.parity()
+    env = OracleEnv(sc.scene, prm)
+    x, v, y, yd = env.rest_state()
+    x, v, y, yd, st = env.step(x, v, y, yd, env.targets_from_delta(sc.delta(0)))
+    x, v, y, yd, st = env.step(x, v, y, yd, env.targets_from_delta(sc.delta(1)))
+    ctx = env.make_ctx(x, v, y, yd, env.targets_from_delta(sc.delta(2)))
+    rng = np.random.default_rng(3)
+    ctx["lam_y"] = rng.normal(size=ctx["lam_y"].shape) * 1e-6
+    pairs = env.pair_arrays(*env.static_pairs(x, y))
+    assert len(pairs[0]) > 0
+    g, H = env.grad_hess(x, y, ctx, pairs, project=False)
+    q = env.join(x, y)
+    for _ in range(4):
+        u = rng.normal(size=q.shape) * env.free
+        u *= 1e-9 / np.abs(u).max()
+        f = lambda t: env.energy(*env.split(q + t * u), ctx, pairs)
+        fd = (f(1.0) - f(-1.0)) / 2.0
+        assert fd == pytest.approx(g @ u, rel=1e-5, abs=1e-9 * np.abs(g).max() * 1e-9)
+        # Hessian by FD of the gradient along a shorter u (the barrier is
+        # strongly nonlinear at micrometre gaps)
+        w = u * 1e-2
+        gp, _ = env.grad_hess(*env.split(q + w), ctx, pairs, project=False)
+        gm, _ = env.grad_hess(*env.split(q - w), ctx, pairs, project=False)
+        Hw = H @ w
+        assert np.abs((gp - gm) / 2.0 - Hw).max() < 1e-6 * np.abs(Hw).max()
+
+
+# ---------------------------------------------------------------- broad phase
+def test_candidates_match_naive_loops_and_cover_dhat():
+    sc = scenes.small_contact_scene(body="sphere", level=1, gap=3e-5, n_steps=2)
+    env = OracleEnv(sc.scene, sc.params)
+    x, v, y, yd = env.rest_state()
+    rng = np.random.default_rng(5)
+    y = y.copy()
+    y[0, :3] += rng.normal(scale=2e-5, size=3) + np.array([0, 0, -1e-5])
+    Xc = env.contact_positions(x, y)
+    sd, dhat = env.sd, sc.params.dhat
+    pt, ee = candidates(sd, Xc, dhat, env.excluded)
+
+    def box(ids):
+        P = Xc[list(ids)]
+        return P.min(0), P.max(0)
+
+    def ov(a, b):
+        return all(a[0][k] <= b[1][k] + dhat and b[0][k] <= a[1][k] + dhat for k in range(3))
+    npt = set()
+    for pi, p in enumerate(sd.points):
+        for ti, t in enumerate(sd.tris):
+            if sd.point_obj[pi] != sd.tri_obj[ti] and ov(box([p]), box(t)):
+                npt.add((int(p), ti))
+    nee = set()
+    for i, j in itertools.combinations(range(len(sd.edges)), 2):
+        oi, oj = sd.edge_obj[i], sd.edge_obj[j]
+        if oi == oj:
+            continue
+        a, b = (i, j) if oi < oj else (j, i)
+        if ov(box(sd.edges[a]), box(sd.edges[b])):
+            nee.add((a, b))
+    npt = {pr for pr in npt if not (sd.fixed[pr[0]] and all(sd.fixed[sd.tris[pr[1]]]))}
+    assert set(map(tuple, pt.tolist())) == npt
+    assert set(map(tuple, ee.tolist())) == nee
+    # every pair of different objects closer than dhat is a candidate
+    allpt = np.array([(p, t) for (p, t) in itertools.product(range(len(sd.points)), range(len(sd.tris)))
+                      if sd.point_obj[p] != sd.tri_obj[t]])
+    X12 = np.concatenate([Xc[sd.points[allpt[:, 0]]][:, None], Xc[sd.tris[allpt[:, 1]]]], axis=1)
+    d = ds.pair_distance(X12, np.zeros(len(allpt), bool))
+    close = {(int(sd.points[p]), int(t)) for (p, t), dd in zip(allpt, d) if dd < dhat}
+    assert close and close <= npt
+    a, b = canonical(sd, pt, ee)
+    assert a.shape == (len(pt), 4) and b.shape == (len(ee), 4)
+
+
+# ---------------------------------------------------------------- CCD
+@pytest.mark.parametrize("seed", range(20))
+def test_accd_conservative_vs_exact_roots(seed):
+    rng = np.random.default_rng(900 + seed)
+    is_ee = bool(seed % 2)
+    x0 = rng.normal(size=(4, 3))
+    p = rng.normal(size=(4, 3)) * 2.0
+    d0 = ds.pair_distance(x0[None], np.array([is_ee]))[0]
+    t = accd_toi(x0, p, is_ee)
+    tb = accd_batch(x0[None], p[None], np.array([is_ee]))[0]
+    assert t == tb
+    te = exact_toi(x0, p, is_ee)
+    assert 0.0 < t <= 1.0
+    assert t <= te + 1e-12
+    # the pair stays apart on [0, t]
+    for s in np.linspace(0.0, t, 50):
+        assert ds.pair_distance((x0 + s * p)[None], np.array([is_ee]))[0] > 0.0
+    if te < 1.0:
+        # ACCD stops short of contact but keeps a fraction of the gap
+        dt = ds.pair_distance((x0 + t * p)[None], np.array([is_ee]))[0]
+        assert dt >= 0.1 * d0 * (1 - 1e-9) or t == 1.0
+
+
+def test_accd_head_on_point_triangle():
+    # point falling straight onto a triangle interior from height 1 by 2:
+    # exact contact at t = 0.5, ACCD returns t < 0.5 with gap >= 0.1
+    x0 = np.array([[0.2, 0.2, 1.0], [0, 0, 0], [1, 0, 0], [0, 1, 0]], float)
+    p = np.zeros((4, 3))
+    p[0, 2] = -2.0
+    assert exact_toi(x0, p, False) == pytest.approx(0.5, abs=1e-9)
+    t = accd_toi(x0, p, False)
+    assert t < 0.5
+    assert 1.0 - 2.0 * t >= 0.1 - 1e-12
+    # no approach: full step
+    assert accd_toi(x0, np.ones((4, 3)), False) == 1.0
