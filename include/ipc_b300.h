@@ -1,0 +1,271 @@
+/*
+ * ipc_b300.h -- C-ABI of the batched ABD-IPC step library (sm_103a).
+ *
+ * One implicit time step of the unified affine-body / soft-body IPC method of
+ * Taccel (arXiv 2504.12908), run for many independent environments at once:
+ *
+ *   (y, x)^{n+1} = argmin  E_IP(x) + E_IP(y) + h^2 B(phi(y); x)         (Eq. unified_ipc,
+ *                                                                         Eq. unified_ipc_variational)
+ *   subject to the kinematic constraints S^x x = s^x, S^y y = s^y        (Sec. 3.4, Eq. unified_ipc_AL)
+ *
+ * where E_IP is the backward-Euler incremental potential of App. A.2 with a
+ * lumped mass matrix and gravity, the elastic potential is neo-Hookean
+ * (App. A.1), affine bodies carry 12 reduced DoFs y = [p, a0, a1, a2] with
+ * x_j = p + A xbar_j and M^y = J^T M J (Sec. 3.3) plus a stiff orthogonality
+ * potential kappa_s V |A^T A - I|_F^2, and B is the area-weighted IPC log
+ * barrier b(d) = -(d - dhat)^2 ln(d / dhat) over point-triangle and edge-edge
+ * pairs (App. A.3, Eq. ipc_energy).  The minimiser is projected Newton with
+ * block-Jacobi PCG, an additive-CCD filtered backtracking line search and
+ * augmented-Lagrangian kinematic targets; all of it runs on the GPU.
+ *
+ * Conventions
+ *   - SI units; every host-side floating-point array is double.
+ *   - Vertex arrays are row-major [n][3].  Body states are [n_bodies][12] in
+ *     the order y = [p_x, p_y, p_z, A(:,0), A(:,1), A(:,2)] (columns of A).
+ *     p is the body's centre of mass; the rest placement is p = com, A = I
+ *     (ipc_body_com returns com).
+ *   - Gel vertex order is the caller's order everywhere in this API; the
+ *     library renumbers internally and maps back.
+ *   - "Contact vertex ids" (debug calls): gel vertex i -> i; vertex j of body
+ *     b -> n_verts + (sum of body_nv[0..b-1]) + j.
+ *
+ * Ownership and memory
+ *   - The caller owns every host buffer; inputs are copied before the call
+ *     returns.
+ *   - Device memory: the caller allocates ONE device buffer of the size that
+ *     ipc_workspace_bytes reports (e.g. a torch uint8 tensor) and keeps it
+ *     alive until ipc_destroy.  The library sub-allocates from it and never
+ *     calls cudaMalloc.  It allocates a few KB of pinned host memory at
+ *     ipc_create_envs for status read-back.
+ *   - The CUDA stream belongs to the caller (cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  One ipc_ctx must not be used from two
+ *     host threads at once.
+ *
+ * Errors
+ *   Every call returns an ipc_status.  IPC_EINVAL: bad argument or malformed
+ *   scene (non-positive tet volume, open body surface, index out of range);
+ *   IPC_ENOMEM: workspace too small; IPC_ECUDA: a CUDA runtime error (the
+ *   message is in ipc_last_error).  ipc_step also reports a status per env:
+ *   IPC_ENOTCONV (Newton, line-search or AL iteration cap hit; the env keeps
+ *   its last feasible iterate), IPC_EOVERFLOW (more candidate pairs than the
+ *   per-env capacity; the env is left at its state before the step).
+ */
+#ifndef IPC_B300_H
+#define IPC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ipc_ctx ipc_ctx;
+
+typedef enum {
+  IPC_OK = 0,
+  IPC_EINVAL = 1,
+  IPC_ENOMEM = 2,
+  IPC_ENOTCONV = 3,
+  IPC_EINTERSECT = 4,
+  IPC_EINVERTED = 5,
+  IPC_EOVERFLOW = 6,
+  IPC_ECUDA = 7
+} ipc_status;
+
+/* Solver parameters (App. A.2-A.3; constants the paper omits are readings
+ * documented with the library).  ipc_default_params fills the defaults. */
+typedef struct {
+  double dt;              /* time step h, s                                  */
+  double gravity[3];      /* m/s^2                                           */
+  double dhat;            /* barrier activation distance, m                  */
+  double kappa;           /* barrier stiffness, Pa                           */
+  double newton_tol;      /* stop when |p|_inf / h < newton_tol, m/s         */
+  double pcg_rel_tol;     /* PCG stops at |r|_2 <= pcg_rel_tol |b|_2         */
+  int newton_max;         /* Newton iteration cap per step                   */
+  int pcg_max;            /* PCG iteration cap per Newton iteration          */
+  int ls_max;             /* line-search halving cap                         */
+  int accd_max;           /* ACCD iteration cap per pair                     */
+  double accd_s;          /* ACCD minimum gap fraction (0.1)                 */
+  double al_kappa;        /* mass-weighted AL penalty factor (1e6)           */
+  int al_max;             /* AL multiplier updates per step                  */
+  double ee_mollifier;    /* EE mollifier threshold factor (1e-3)            */
+  int precision;          /* 0 = FP64 throughout, 1 = mixed (FP32 element
+                             Hessians, assembly and PCG mat-vec; FP64
+                             distances, CCD, energies, residuals)            */
+  int max_pairs_per_env;  /* candidate-pair capacity per env (0 = default)  */
+} ipc_params;
+
+/* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
+typedef struct {
+  int n_verts;                 /* gel vertices                               */
+  int n_tets;                  /* gel tetrahedra                             */
+  const double* rest_x;        /* [n_verts][3] rest positions                */
+  const int32_t* tets;         /* [n_tets][4], positive volume required      */
+  const int32_t* pad_id;       /* [n_verts] pad (contact object) id, or NULL */
+  const uint8_t* pinned;       /* [n_verts] 1 = fixed at its position, NULL  */
+  const int32_t* attach_body;  /* [n_verts] body index driving the vertex,
+                                  -1 = free; NULL = all free                 */
+  double E, nu, rho;           /* neo-Hookean parameters, gel density        */
+  int n_bodies;
+  const int32_t* body_nv;      /* [n_bodies] vertex counts                   */
+  const double* body_rest_x;   /* [sum nv][3] rest placement (world)         */
+  const int32_t* body_nt;      /* [n_bodies] triangle counts                 */
+  const int32_t* body_tris;    /* [sum nt][3] local vertex ids, closed and
+                                  outward oriented                           */
+  const double* body_rho;      /* [n_bodies] density                         */
+  const double* body_kappa_s;  /* [n_bodies] orthogonality stiffness, Pa     */
+  const uint8_t* body_driven;  /* [n_bodies] 1 = follows ipc_set_targets     */
+} ipc_scene_desc;
+
+typedef struct {
+  int newton_iters;     /* max over the stepped envs                         */
+  int pcg_iters;        /* total PCG iterations (batched, all Newton its)     */
+  int ls_trials;        /* total line-search energy evaluations              */
+  int al_updates;       /* max over envs                                     */
+  int max_pairs;        /* max candidate pairs seen in one env               */
+  long long newton_env_iters; /* Newton iterations summed over the stepped envs */
+  double ms_total;      /* wall time of the call (host clock), ms            */
+} ipc_step_stats;
+
+void ipc_default_params(ipc_params* prm);
+
+/* Bytes of device workspace needed for n_envs scenes (array of n_envs
+ * descriptors, one per env; they may differ in size). */
+ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs,
+                               const ipc_params* prm, size_t* bytes);
+
+/* Build the envs: validates and preprocesses each scene on the host, copies
+ * it into dev_workspace (ws_bytes >= ipc_workspace_bytes), sets every env to
+ * its rest state (velocities zero, bodies at p = com, A = I; Sec. 4.1
+ * "Robot Actions") and driven targets to the rest placement. */
+ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs,
+                           const ipc_params* prm, void* dev_workspace,
+                           size_t ws_bytes, void* cuda_stream, ipc_ctx** out);
+
+ipc_status ipc_destroy(ipc_ctx* ctx);
+
+/* Last error message of this ctx (empty string if none). */
+const char* ipc_last_error(const ipc_ctx* ctx);
+
+int ipc_num_envs(const ipc_ctx* ctx);
+ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies,
+                         int* n_surface_out);
+
+/* Rest centre of mass of a body (the p of its rest placement). */
+ipc_status ipc_body_com(const ipc_ctx* ctx, int env, int body, double com[3]);
+
+/* State of one env.  x, v: [n_verts][3]; y, ydot: [n_bodies][12].  Any
+ * pointer may be NULL to leave that part unchanged.  set_state synchronises
+ * the stream and rejects inverted tets (IPC_EINVERTED) and touching or
+ * interpenetrating surfaces (IPC_EINTERSECT, min distance <= 0), leaving the
+ * previous state in place. */
+ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v,
+                         const double* y, const double* ydot);
+ipc_status ipc_get_state(ipc_ctx* ctx, int env, double* x, double* v,
+                         double* y, double* ydot);
+
+/* Kinematic targets s^y of the driven bodies of one env for the next step,
+ * [n_bodies][12] (rows of free bodies are ignored).  Gel vertices attached
+ * to a driven body get the target p + A xbar (xbar = rest offset from the
+ * body's com).  Sec. 3.4 / 4.1. */
+ipc_status ipc_set_targets(ipc_ctx* ctx, int env, const double* y_target);
+
+/* Same for all envs at once from one host array [n_envs][max_bodies][12]
+ * (max_bodies = largest n_bodies over the envs): one host->device copy into
+ * a staging buffer, scattered on the device. */
+ipc_status ipc_set_targets_all(ipc_ctx* ctx, const double* y_targets);
+
+/* Same as ipc_set_targets_all but from a device buffer (device-to-device
+ * copy on the ctx stream; no host synchronisation). */
+ipc_status ipc_set_targets_all_device(ipc_ctx* ctx, const double* dev_y_targets);
+
+/* Advance the listed envs by one time step (env_ids NULL = all envs).
+ * per_env_status (may be NULL) receives n statuses.  Synchronises the
+ * stream before returning. */
+ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n,
+                    int32_t* per_env_status, ipc_step_stats* stats);
+
+/* Coated-surface vertex positions of one env's gel (Sec. 4.1: the surface
+ * minus pinned and attached vertices), in increasing gel vertex id order.
+ * Writes min(capacity, count) rows of [3]; *n_written = count. */
+ipc_status ipc_read_gel_surface(ipc_ctx* ctx, int env, double* out_xyz, int capacity,
+                                int* n_written);
+
+/* Coated-surface positions of all envs into one host array, env after env
+ * (counts from ipc_env_sizes): gathered on the device, one device->host
+ * copy, synchronises the stream. */
+ipc_status ipc_read_gel_surface_all(ipc_ctx* ctx, double* out_xyz, size_t capacity_rows,
+                                    size_t* rows_written);
+
+/* ---- diagnostics (used by the parity tests; not needed to step) -------- */
+
+/* Objective, gradient and Hessian-vector product of one env at its current
+ * state, as the first Newton iteration of a step would see it (xtilde =
+ * x + h v, targets as set, multipliers zero).  grad/vec/hvec are full DoF
+ * vectors [3 n_verts + 12 n_bodies] in caller vertex order; the Hessian is
+ * the PSD-projected one with pinned DoFs eliminated (identity rows).  Any
+ * output may be NULL. */
+ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad,
+                          const double* vec, double* hvec);
+
+/* Candidate pairs of one env for caller-given contact-vertex positions
+ * cv_x [n_verts + sum body_nv][3] (indexed by contact vertex id; only
+ * surface vertices are read): static set (cv_x_end NULL) or swept set from
+ * cv_x to cv_x_end.  Rows of out: [kind (0 = PT, 1 = EE), v0, v1, v2, v3]
+ * with contact vertex ids (PT: point, triangle; EE: edge of the lower
+ * object, edge of the higher).  Order is unspecified.  *n_pairs = count
+ * (IPC_EOVERFLOW if above the env's pair capacity). */
+ipc_status ipc_debug_pairs(ipc_ctx* ctx, int env, const double* cv_x, const double* cv_x_end,
+                           int32_t* out, int capacity, int* n_pairs);
+
+/* First Newton direction of one env from its current state (PCG solve). */
+ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters);
+
+/* Largest CCD-safe step along dir (ACCD over the swept candidates). */
+ipc_status ipc_debug_accd(ipc_ctx* ctx, int env, const double* dir, double* alpha);
+
+/* ---- profiling ---------------------------------------------------------- */
+/* Kernel launches are always counted.  With profiling on, every kernel
+ * launch of ipc_step is bracketed by CUDA events recorded on the ctx stream
+ * and its device time is accumulated per kernel class.  Off by default. */
+ipc_status ipc_profile_enable(ipc_ctx* ctx, int on);
+ipc_status ipc_profile_reset(ipc_ctx* ctx);
+int ipc_profile_count(const ipc_ctx* ctx);  /* number of kernel classes */
+/* Class i: its name (static string), launches and accumulated device ms
+ * since the last reset (profiling on). */
+ipc_status ipc_profile_get(const ipc_ctx* ctx, int i, const char** name, long long* launches, double* ms);
+/* Kernels launched through this ctx since creation. */
+long long ipc_launch_count(const ipc_ctx* ctx);
+/* Sizes of the assembled system of one env: real 3x3 blocks of the sparse
+ * matrix (gel and body), stored SELL blocks (with padding), rows, tets. */
+ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks, long long* stored_blocks,
+                            int* rows, int* tets);
+
+/* ---- element kernels on caller device buffers (no ctx) ----------------- */
+/* All pointers are device pointers; n elements; the call is asynchronous on
+ * stream.  Returns IPC_EINVAL for n < 0 or NULL required pointers. */
+
+/* Neo-Hookean tet (App. A.1): x [n][4][3], Dm_inv [n][3][3] (row-major),
+ * vol [n]; outputs (NULL to skip) energy [n] = vol Psi (+inf if J <= 0),
+ * grad [n][12], hess [n][12][12] = vol B^T Pi(dP/dF) B (PSD-projected). */
+ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol,
+                     double mu, double lam, double* energy, double* grad, double* hess,
+                     void* stream);
+
+/* Weighted barrier of pairs (App. A.3): X [n][4][3], is_ee [n] (0/1),
+ * weight [n] (multiplies c(x) b(d)), eps_x [n] (mollifier threshold, EE
+ * only); energy [n], grad [n][12], hess [n][12][12] (PSD-projected). */
+ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight,
+                         const double* eps_x, double dhat, double* energy, double* grad,
+                         double* hess, void* stream);
+
+/* ACCD time of impact of pairs moving from X0 by P: toi [n] in (0, 1]. */
+ipc_status ipc_k_accd(int n, const double* X0, const double* P, const int32_t* is_ee,
+                      double s, int max_iter, double* toi, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPC_B300_H */

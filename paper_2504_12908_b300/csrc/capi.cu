@@ -1,0 +1,869 @@
+// C-ABI of the batched ABD-IPC step: workspace layout, state I/O, the Newton
+// driver (host orchestration of the device kernels) and diagnostics.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ipc_b300.h"
+#include "ctx.h"
+#include "kernels.h"
+
+using namespace ipc;
+
+namespace {
+
+#define CK(call)                                                                 \
+  do {                                                                           \
+    cudaError_t _e = (call);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      if (ctx) ctx->err = std::string(#call) + ": " + cudaGetErrorString(_e);    \
+      return IPC_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+// ---- per-kernel-class launch counts and event timing
+enum Kc {
+  KC_PREDICT, KC_CVPOS, KC_OBJBOX, KC_BROAD, KC_BARRIER, KC_TET, KC_BODY, KC_ASSEMBLE, KC_GRAD, KC_PRECOND,
+  KC_PCGINIT, KC_PAIRSPMV, KC_SPMV, KC_PCGUPD, KC_PCGDIR, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC, KC_COUNT
+};
+const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",    "obj_box",   "broad_phase", "barrier",
+                                 "tet_elastic",  "body_abd",  "assemble",  "gradient",    "precond",
+                                 "pcg_init",     "pair_spmv", "sell_spmv", "pcg_update",  "pcg_dir",
+                                 "newton_check", "accd",      "ls_energy", "ls_update",   "misc"};
+
+cudaEvent_t take_ev(ipc_ctx* ctx) {
+  if (!ctx->ev_free.empty()) {
+    cudaEvent_t e = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+template <class F>
+void KL(ipc_ctx* ctx, int kind, F&& f) {
+  if (!ctx->prof_on) {
+    ctx->launches += f();
+    return;
+  }
+  cudaEvent_t a = take_ev(ctx), b = take_ev(ctx);
+  cudaEventRecord(a, ctx->stream);
+  int n = f();
+  cudaEventRecord(b, ctx->stream);
+  ctx->launches += n;
+  ctx->prof_launches[kind] += n;
+  ctx->pending.push_back({kind, a, b});
+}
+
+// resolve recorded event pairs (the stream has been synchronised)
+void prof_flush(ipc_ctx* ctx) {
+  for (auto& pe : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) ctx->prof_ms[pe.kind] += ms;
+    ctx->ev_free.push_back(pe.a);
+    ctx->ev_free.push_back(pe.b);
+  }
+  ctx->pending.clear();
+}
+
+// Walks every device array in a fixed order; with ws == nullptr only sums
+// sizes.  Static tables are copied from the pack when `upload` is set.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align256(std::max<size_t>(count, 1) * sizeof(T));
+    return p;
+  }
+};
+
+template <class T>
+const T* carve_copy(Carver& cv, const std::vector<T>& v, std::vector<std::pair<const void*, std::pair<void*, size_t>>>& up) {
+  T* p = cv.take<T>(v.size());
+  if (p && !v.empty()) up.push_back({v.data(), {p, v.size() * sizeof(T)}});
+  return p;
+}
+
+struct Extra {
+  std::vector<int> env_pair_off_i, has_driven;
+};
+
+void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
+           std::vector<std::pair<const void*, std::pair<void*, size_t>>>& up) {
+  d.n_envs = pk.n_envs;
+  d.n_rows = pk.n_rows;
+  d.n_tets = pk.n_tets;
+  d.n_cv = pk.n_cv;
+  d.n_tri = pk.n_tri;
+  d.n_edge = pk.n_edge;
+  d.n_obj = pk.n_obj;
+  d.n_bodies = pk.n_bodies;
+  d.n_chunks = pk.n_chunks;
+  d.n_coated = pk.n_coated;
+  d.n_blocks = pk.n_sell_blocks;
+  d.n_pairs_cap = pk.n_pairs_cap;
+  d.h = prm.dt;
+  for (int k = 0; k < 3; ++k) d.grav[k] = prm.gravity[k];
+  d.dhat = prm.dhat;
+  d.kappa = prm.kappa;
+  d.newton_tol = prm.newton_tol;
+  d.pcg_tol = prm.pcg_rel_tol;
+  d.accd_s = prm.accd_s;
+  d.al_kappa = prm.al_kappa;
+  d.ee_moll = prm.ee_mollifier;
+  d.newton_max = prm.newton_max;
+  d.pcg_max = prm.pcg_max;
+  d.ls_max = prm.ls_max;
+  d.accd_max = prm.accd_max;
+  d.al_max = prm.al_max;
+
+  ex.env_pair_off_i.assign(pk.env_pair_off.begin(), pk.env_pair_off.end());
+  ex.has_driven.assign(pk.n_envs, 0);
+  for (int e = 0; e < pk.n_envs; ++e)
+    for (int r = pk.env_row_off[e]; r < pk.env_row_off[e + 1]; ++r)
+      if (pk.row_kind[r] == ROW_ATTACHED || pk.row_kind[r] == ROW_BODY_DRIVEN) { ex.has_driven[e] = 1; break; }
+
+  d.env_row_off = carve_copy(c, pk.env_row_off, up);
+  d.env_tet_off = carve_copy(c, pk.env_tet_off, up);
+  d.env_cv_off = carve_copy(c, pk.env_cv_off, up);
+  d.env_tri_off = carve_copy(c, pk.env_tri_off, up);
+  d.env_edge_off = carve_copy(c, pk.env_edge_off, up);
+  d.env_obj_off = carve_copy(c, pk.env_obj_off, up);
+  d.env_body_off = carve_copy(c, pk.env_body_off, up);
+  d.env_chunk_off = carve_copy(c, pk.env_chunk_off, up);
+  d.env_coated_off = carve_copy(c, pk.env_coated_off, up);
+  d.env_pair_cap = carve_copy(c, pk.env_pair_cap, up);
+  d.env_pair_off = carve_copy(c, ex.env_pair_off_i, up);
+  d.env_has_driven = carve_copy(c, ex.has_driven, up);
+  d.env_mu = carve_copy(c, pk.env_mu, up);
+  d.env_lam = carve_copy(c, pk.env_lam, up);
+  d.cta_env = carve_copy(c, pk.cta_env, up);
+  d.row_mass = carve_copy(c, pk.row_mass, up);
+  d.row_kind = carve_copy(c, pk.row_kind, up);
+  d.row_body = carve_copy(c, pk.row_body, up);
+  d.row_xbar = carve_copy(c, pk.row_xbar, up);
+  d.vt_ptr = carve_copy(c, pk.vt_ptr, up);
+  d.vt_src = carve_copy(c, pk.vt_src, up);
+  d.tets = carve_copy(c, pk.tets, up);
+  d.Dm_inv = carve_copy(c, pk.Dm_inv, up);
+  d.tet_vol = carve_copy(c, pk.tet_vol, up);
+  d.chunk_slots = carve_copy(c, pk.chunk_slots, up);
+  d.chunk_ptr = carve_copy(c, pk.chunk_ptr, up);
+  d.sell_col = carve_copy(c, pk.sell_col, up);
+  d.asm_ptr = carve_copy(c, pk.asm_ptr, up);
+  d.asm_src = carve_copy(c, pk.asm_src, up);
+  d.body_row = carve_copy(c, pk.body_row, up);
+  d.body_env = carve_copy(c, pk.body_env, up);
+  d.body_cv_begin = carve_copy(c, pk.body_cv_begin, up);
+  d.body_nv = carve_copy(c, pk.body_nv, up);
+  d.body_mass = carve_copy(c, pk.body_mass, up);
+  d.body_S = carve_copy(c, pk.body_S, up);
+  d.body_vol = carve_copy(c, pk.body_vol, up);
+  d.body_kappa = carve_copy(c, pk.body_kappa, up);
+  d.body_driven = carve_copy(c, pk.body_driven, up);
+  d.cv_row = carve_copy(c, pk.cv_row, up);
+  d.cv_body = carve_copy(c, pk.cv_body, up);
+  d.cv_obj = carve_copy(c, pk.cv_obj, up);
+  d.cv_uid = carve_copy(c, pk.cv_uid, up);
+  d.cv_xbar = carve_copy(c, pk.cv_xbar, up);
+  d.cv_area = carve_copy(c, pk.cv_area, up);
+  d.cv_fixed = carve_copy(c, pk.cv_fixed, up);
+  d.tri = carve_copy(c, pk.tri, up);
+  d.tri_obj = carve_copy(c, pk.tri_obj, up);
+  d.edge = carve_copy(c, pk.edge, up);
+  d.edge_obj = carve_copy(c, pk.edge_obj, up);
+  d.edge_area = carve_copy(c, pk.edge_area, up);
+  d.edge_len2 = carve_copy(c, pk.edge_len2, up);
+  d.obj_env = carve_copy(c, pk.obj_env, up);
+  d.obj_local = carve_copy(c, pk.obj_local, up);
+  d.obj_cv_begin = carve_copy(c, pk.obj_cv_begin, up);
+  d.obj_cv_end = carve_copy(c, pk.obj_cv_end, up);
+  d.obj_tri_begin = carve_copy(c, pk.obj_tri_begin, up);
+  d.obj_tri_end = carve_copy(c, pk.obj_tri_end, up);
+  d.obj_edge_begin = carve_copy(c, pk.obj_edge_begin, up);
+  d.obj_edge_end = carve_copy(c, pk.obj_edge_end, up);
+  d.obj_size = carve_copy(c, pk.obj_size, up);
+  d.obj_exclude = carve_copy(c, pk.obj_exclude, up);
+  d.coated_row = carve_copy(c, pk.coated_row, up);
+  // dynamic
+  size_t R3 = 3 * (size_t)pk.n_rows;
+  d.x = c.take<double>(R3);
+  d.v = c.take<double>(R3);
+  d.xn = c.take<double>(R3);
+  d.xt = c.take<double>(R3);
+  d.s_tgt = c.take<double>(R3);
+  d.lam = c.take<double>(R3);
+  d.p = c.take<double>(R3);
+  d.g = c.take<double>(R3);
+  d.r = c.take<double>(R3);
+  d.z = c.take<double>(R3);
+  d.d = c.take<double>(R3);
+  d.q = c.take<double>(R3);
+  d.qc = c.take<double>(R3);
+  d.pc = c.take<double>(9 * (size_t)pk.n_rows);
+  d.pc_acc = c.take<double>(9 * (size_t)pk.n_rows);
+  d.body_pc = c.take<double>(144 * (size_t)pk.n_bodies);
+  d.body_pc_acc = c.take<double>(144 * (size_t)pk.n_bodies);
+  d.body_g = c.take<double>(12 * (size_t)pk.n_bodies);
+  d.body_H = c.take<double>(144 * (size_t)pk.n_bodies);
+  d.body_E = c.take<double>(pk.n_bodies);
+  d.sell_val = c.take<double>(9 * (size_t)pk.n_sell_blocks);
+  d.tetG = c.take<double>(12 * (size_t)pk.n_tets);
+  d.tetH = c.take<double>(144 * (size_t)pk.n_tets);
+  d.tetE = c.take<double>(pk.n_tets);
+  d.row_E = c.take<double>(pk.n_rows);
+  d.cvx = c.take<double>(3 * (size_t)pk.n_cv);
+  d.cvp = c.take<double>(3 * (size_t)pk.n_cv);
+  d.obj_box = c.take<double>(6 * (size_t)pk.n_obj);
+  d.pair_v = c.take<int4>(pk.n_pairs_cap);
+  d.pair_kind = c.take<int>(pk.n_pairs_cap);
+  d.pair_w = c.take<double>(pk.n_pairs_cap);
+  d.pair_eps = c.take<double>(pk.n_pairs_cap);
+  d.pair_H = c.take<double>(144 * (size_t)pk.n_pairs_cap);
+  d.pair_E = c.take<double>(pk.n_pairs_cap);
+  d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
+  d.cta_part = c.take<double>(4 * (size_t)(pk.n_rows / 128));
+  d.env_cnt = c.take<unsigned int>(2 * (size_t)pk.n_envs);
+  int mb = 0;
+  for (const auto& ev : pk.env) mb = std::max(mb, ev.n_bodies);
+  d.max_bodies = mb;
+  d.tgt_stage = c.take<double>(12 * (size_t)mb * pk.n_envs);
+  d.out_stage = c.take<double>(3 * (size_t)pk.n_coated);
+  d.env_s = c.take<double>(NUM_SCALARS * (size_t)pk.n_envs);
+  d.env_i = c.take<int>(NUM_INTS * (size_t)pk.n_envs);
+}
+
+ipc_status check_env(const ipc_ctx* ctx, int env) {
+  if (!ctx || env < 0 || env >= ctx->pk.n_envs) return IPC_EINVAL;
+  return IPC_OK;
+}
+
+// set the I_SEL column of env_i (and optionally another flag) for a list of envs
+ipc_status select_envs(ipc_ctx* ctx, const std::vector<int>& sel, int flag = I_SEL) {
+  const int n = ctx->pk.n_envs;
+  std::vector<int> col(n, 0);
+  for (int e : sel) col[e] = 1;
+  CK(cudaMemcpy2DAsync(ctx->dev.env_i + flag, NUM_INTS * sizeof(int), col.data(), sizeof(int), sizeof(int), n,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  return IPC_OK;
+}
+
+ipc_status sync_flags(ipc_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_int, ctx->dev.env_i, NUM_INTS * sizeof(int) * ctx->pk.n_envs, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_dbl, ctx->dev.env_s, NUM_SCALARS * sizeof(double) * ctx->pk.n_envs,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  return IPC_OK;
+}
+
+int count_flag(const ipc_ctx* ctx, int flag) {
+  int c = 0;
+  for (int e = 0; e < ctx->pk.n_envs; ++e) c += ctx->h_int[e * NUM_INTS + flag] != 0;
+  return c;
+}
+
+ipc_status last_cuda(ipc_ctx* ctx) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e);
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+// ---- the assembled Newton system at the current iterate of active envs
+ipc_status assemble_system(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_ACTIVE, false, s); });
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_ACTIVE, false, s); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); });
+  KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
+  KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s); });
+  KL(ctx, KC_TET, [&] { return launch_tet(d, s); });
+  KL(ctx, KC_BODY, [&] { return launch_body(d, s); });
+  KL(ctx, KC_ASSEMBLE, [&] { return launch_assemble(d, s); });
+  KL(ctx, KC_GRAD, [&] { return launch_grad(d, s); });
+  KL(ctx, KC_PRECOND, [&] { return launch_precond(d, s); });
+  return last_cuda(ctx);
+}
+
+ipc_status run_pcg(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
+  const int poll = 16;
+  for (int it = 0; it < ctx->prm.pcg_max; ++it) {
+    KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
+    KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s); });
+    KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s); });
+    KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s); });
+    if ((it + 1) % poll == 0) {
+      ipc_status st = sync_flags(ctx);
+      if (st != IPC_OK) return st;
+      if (count_flag(ctx, I_PCG) == 0) break;
+    }
+  }
+  return last_cuda(ctx);
+}
+
+// user-order DoF vector <-> row space of one env
+void dof_to_rows(const ipc_ctx* ctx, int env, const double* dof, std::vector<double>& rows) {
+  const EnvInfo& ev = ctx->pk.env[env];
+  rows.assign(3 * (size_t)ev.n_rows, 0.0);
+  for (int r = 0; r < ev.n_verts; ++r)
+    for (int c = 0; c < 3; ++c) rows[3 * r + c] = dof[3 * ev.perm[r] + c];
+  for (int b = 0; b < ev.n_bodies; ++b)
+    for (int k = 0; k < 12; ++k) rows[3 * (ev.gel_rows + 4 * b) + k] = dof[3 * ev.n_verts + 12 * b + k];
+}
+void rows_to_dof(const ipc_ctx* ctx, int env, const std::vector<double>& rows, double* dof) {
+  const EnvInfo& ev = ctx->pk.env[env];
+  for (int r = 0; r < ev.n_verts; ++r)
+    for (int c = 0; c < 3; ++c) dof[3 * ev.perm[r] + c] = rows[3 * r + c];
+  for (int b = 0; b < ev.n_bodies; ++b)
+    for (int k = 0; k < 12; ++k) dof[3 * ev.n_verts + 12 * b + k] = rows[3 * (ev.gel_rows + 4 * b) + k];
+}
+
+ipc_status upload_rows(ipc_ctx* ctx, int env, double* dst, const std::vector<double>& rows) {
+  const EnvInfo& ev = ctx->pk.env[env];
+  CK(cudaMemcpyAsync(dst + 3 * (size_t)ev.row_begin, rows.data(), rows.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  return IPC_OK;
+}
+ipc_status download_rows(ipc_ctx* ctx, int env, const double* src, std::vector<double>& rows) {
+  const EnvInfo& ev = ctx->pk.env[env];
+  rows.resize(3 * (size_t)ev.n_rows);
+  CK(cudaMemcpyAsync(rows.data(), src + 3 * (size_t)ev.row_begin, rows.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return IPC_OK;
+}
+
+// prepare one env as if a step starts (selection, prediction, targets)
+ipc_status begin_single(ipc_ctx* ctx, int env) {
+  ipc_status st = select_envs(ctx, {env});
+  if (st != IPC_OK) return st;
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 0, ctx->stream); });
+  KL(ctx, KC_PREDICT, [&] { return launch_predict(ctx->dev, ctx->stream); });
+  KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(ctx->dev, I_SEL, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 1, ctx->stream); });
+  return last_cuda(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipc_default_params(ipc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dt = 1e-3;
+  p->gravity[0] = 0.0; p->gravity[1] = 0.0; p->gravity[2] = -9.81;
+  p->dhat = 1e-4;
+  p->kappa = 1e6;
+  p->newton_tol = 1e-4;
+  p->pcg_rel_tol = 1e-4;
+  p->newton_max = 100;
+  p->pcg_max = 1000;
+  p->ls_max = 30;
+  p->accd_max = 10000;
+  p->accd_s = 0.1;
+  p->al_kappa = 1e6;
+  p->al_max = 10;
+  p->ee_mollifier = 1e-3;
+  p->precision = 0;
+  p->max_pairs_per_env = 0;
+}
+
+ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
+  if (!prm || !bytes) return IPC_EINVAL;
+  ipc_ctx* ctx = nullptr;
+  Pack pk;
+  std::string err;
+  if (!build_pack(scenes, n_envs, *prm, pk, err)) return IPC_EINVAL;
+  Carver c{nullptr};
+  Dev d;
+  Extra ex;
+  std::vector<std::pair<const void*, std::pair<void*, size_t>>> up;
+  carve(pk, *prm, c, d, ex, up);
+  *bytes = c.off;
+  (void)ctx;
+  return IPC_OK;
+}
+
+ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, void* dev_workspace,
+                           size_t ws_bytes, void* cuda_stream, ipc_ctx** out) {
+  if (!prm || !out || !dev_workspace) return IPC_EINVAL;
+  if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
+      prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
+    return IPC_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
+  ipc_ctx* ctx = new ipc_ctx();
+  ctx->prm = *prm;
+  ctx->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (!build_pack(scenes, n_envs, *prm, ctx->pk, ctx->err)) {
+    *out = ctx;  // carries the message
+    return IPC_EINVAL;
+  }
+  Carver c{reinterpret_cast<char*>(dev_workspace)};
+  Extra ex;
+  std::vector<std::pair<const void*, std::pair<void*, size_t>>> up;
+  carve(ctx->pk, *prm, c, ctx->dev, ex, up);
+  if (c.off > ws_bytes) {
+    ctx->err = "workspace too small";
+    *out = ctx;
+    return IPC_ENOMEM;
+  }
+  ctx->ws = reinterpret_cast<char*>(dev_workspace);
+  ctx->ws_bytes = ws_bytes;
+  *out = ctx;
+  const Pack& pk = ctx->pk;
+  for (auto& u : up) CK(cudaMemcpyAsync(u.second.first, u.first, u.second.second, cudaMemcpyHostToDevice, ctx->stream));
+  // zero every dynamic array (from x to the end of the workspace)
+  char* dyn0 = reinterpret_cast<char*>(ctx->dev.x);
+  CK(cudaMemsetAsync(dyn0, 0, (ctx->ws + c.off) - dyn0, ctx->stream));
+  size_t R3 = 3 * (size_t)pk.n_rows * sizeof(double);
+  CK(cudaMemcpyAsync(ctx->dev.x, pk.rest_x.data(), R3, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dev.s_tgt, pk.rest_x.data(), R3, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMallocHost(&ctx->h_int, NUM_INTS * sizeof(int) * (size_t)pk.n_envs));
+  CK(cudaMallocHost(&ctx->h_dbl, NUM_SCALARS * sizeof(double) * (size_t)pk.n_envs));
+  for (const auto& ev : pk.env) ctx->max_bodies = std::max(ctx->max_bodies, ev.n_bodies);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return IPC_OK;
+}
+
+ipc_status ipc_destroy(ipc_ctx* ctx) {
+  if (!ctx) return IPC_EINVAL;
+  if (ctx->h_int) cudaFreeHost(ctx->h_int);
+  if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
+  for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
+  for (auto e : ctx->ev_free) cudaEventDestroy(e);
+  delete ctx;
+  return IPC_OK;
+}
+
+const char* ipc_last_error(const ipc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int ipc_num_envs(const ipc_ctx* ctx) { return ctx ? ctx->pk.n_envs : 0; }
+
+ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies, int* n_surface_out) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  if (n_verts) *n_verts = ev.n_verts;
+  if (n_bodies) *n_bodies = ev.n_bodies;
+  if (n_surface_out) *n_surface_out = ev.n_coated;
+  return IPC_OK;
+}
+
+ipc_status ipc_body_com(const ipc_ctx* ctx, int env, int body, double com[3]) {
+  if (check_env(ctx, env) != IPC_OK || !com) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  if (body < 0 || body >= ev.n_bodies) return IPC_EINVAL;
+  for (int k = 0; k < 3; ++k) com[k] = ev.body_com[3 * body + k];
+  return IPC_OK;
+}
+
+ipc_status ipc_get_state(ipc_ctx* ctx, int env, double* x, double* v, double* y, double* ydot) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  std::vector<double> rows;
+  std::vector<double> dof(3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies);
+  for (int which = 0; which < 2; ++which) {
+    double* gx = which == 0 ? x : v;
+    double* gy = which == 0 ? y : ydot;
+    if (!gx && !gy) continue;
+    ipc_status st = download_rows(ctx, env, which == 0 ? ctx->dev.x : ctx->dev.v, rows);
+    if (st != IPC_OK) return st;
+    rows_to_dof(ctx, env, rows, dof.data());
+    if (gx) std::memcpy(gx, dof.data(), 3 * sizeof(double) * ev.n_verts);
+    if (gy) std::memcpy(gy, dof.data() + 3 * ev.n_verts, 12 * sizeof(double) * ev.n_bodies);
+  }
+  return IPC_OK;
+}
+
+ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v, const double* y,
+                         const double* ydot) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  size_t nd = 3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies;
+  std::vector<double> old_x, old_v, dof(nd), rows;
+  ipc_status st;
+  if ((st = download_rows(ctx, env, ctx->dev.x, old_x)) != IPC_OK) return st;
+  if ((st = download_rows(ctx, env, ctx->dev.v, old_v)) != IPC_OK) return st;
+  for (int which = 0; which < 2; ++which) {
+    const double* gx = which == 0 ? x : v;
+    const double* gy = which == 0 ? y : ydot;
+    if (!gx && !gy) continue;
+    rows_to_dof(ctx, env, which == 0 ? old_x : old_v, dof.data());
+    if (gx) std::memcpy(dof.data(), gx, 3 * sizeof(double) * ev.n_verts);
+    if (gy) std::memcpy(dof.data() + 3 * ev.n_verts, gy, 12 * sizeof(double) * ev.n_bodies);
+    dof_to_rows(ctx, env, dof.data(), rows);
+    // keep padding rows as they were
+    const std::vector<double>& old = which == 0 ? old_x : old_v;
+    for (int r = ev.n_verts; r < ev.n_rows; ++r)
+      if (r < ev.gel_rows || r >= ev.gel_rows + 4 * ev.n_bodies)
+        for (int c = 0; c < 3; ++c) rows[3 * r + c] = old[3 * r + c];
+    if ((st = upload_rows(ctx, env, which == 0 ? ctx->dev.x : ctx->dev.v, rows)) != IPC_OK) return st;
+  }
+  // feasibility: no inverted tet, no touching pair
+  if ((st = select_envs(ctx, {env})) != IPC_OK) return st;
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 3, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_check_inverted(ctx->dev, ctx->stream); });
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(ctx->dev, I_SEL, false, ctx->stream); });
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(ctx->dev, I_SEL, false, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 2, ctx->stream); });
+  KL(ctx, KC_BROAD, [&] { return launch_broad(ctx->dev, I_SEL, false, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_min_dist(ctx->dev, I_SEL, ctx->stream); });
+  if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  ipc_status verdict = IPC_OK;
+  if (ctx->h_int[env * NUM_INTS + I_FLAG]) verdict = IPC_EINVERTED;
+  else if (!(ctx->h_dbl[env * NUM_SCALARS + S_MIND] > 0.0)) verdict = IPC_EINTERSECT;
+  if (verdict != IPC_OK) {
+    upload_rows(ctx, env, ctx->dev.x, old_x);
+    upload_rows(ctx, env, ctx->dev.v, old_v);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->err = verdict == IPC_EINVERTED ? "set_state: inverted tetrahedron" : "set_state: surfaces touch";
+  }
+  return verdict;
+}
+
+ipc_status ipc_set_targets(ipc_ctx* ctx, int env, const double* y_target) {
+  if (check_env(ctx, env) != IPC_OK || !y_target) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  if (ev.n_bodies == 0) return IPC_OK;
+  CK(cudaMemcpyAsync(ctx->dev.s_tgt + 3 * (size_t)(ev.row_begin + ev.gel_rows), y_target,
+                     12 * sizeof(double) * ev.n_bodies, cudaMemcpyHostToDevice, ctx->stream));
+  return IPC_OK;
+}
+
+ipc_status ipc_set_targets_all(ipc_ctx* ctx, const double* y_targets) {
+  if (!ctx || !y_targets) return IPC_EINVAL;
+  const size_t n = 12 * (size_t)ctx->max_bodies * ctx->pk.n_envs;
+  if (n == 0) return IPC_OK;
+  CK(cudaMemcpyAsync(ctx->dev.tgt_stage, y_targets, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  KL(ctx, KC_MISC, [&] { return launch_scatter_targets(ctx->dev, ctx->stream); });
+  return last_cuda(ctx);
+}
+
+ipc_status ipc_set_targets_all_device(ipc_ctx* ctx, const double* dev_y_targets) {
+  if (!ctx || !dev_y_targets) return IPC_EINVAL;
+  const size_t n = 12 * (size_t)ctx->max_bodies * ctx->pk.n_envs;
+  if (n == 0) return IPC_OK;
+  CK(cudaMemcpyAsync(ctx->dev.tgt_stage, dev_y_targets, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  KL(ctx, KC_MISC, [&] { return launch_scatter_targets(ctx->dev, ctx->stream); });
+  return last_cuda(ctx);
+}
+
+ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_env_status, ipc_step_stats* stats) {
+  if (!ctx) return IPC_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<int> sel;
+  if (!env_ids) {
+    for (int e = 0; e < ctx->pk.n_envs; ++e) sel.push_back(e);
+  } else {
+    for (int i = 0; i < n; ++i) {
+      if (check_env(ctx, env_ids[i]) != IPC_OK) return IPC_EINVAL;
+      sel.push_back(env_ids[i]);
+    }
+  }
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  ipc_status st;
+  if ((st = select_envs(ctx, sel)) != IPC_OK) return st;
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); });
+  KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); });
+  KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); });
+  int newton_done = 0;
+  for (int it = 0; it < ctx->prm.newton_max; ++it) {
+    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
+    if ((st = assemble_system(ctx)) != IPC_OK) return st;
+    if ((st = run_pcg(ctx)) != IPC_OK) return st;
+    KL(ctx, KC_NEWTON, [&] { return launch_newton_check(d, s); });
+    KL(ctx, KC_NEWTON, [&] { return launch_newton_decide(d, s); });
+    KL(ctx, KC_NEWTON, [&] { return launch_al_update(d, s); });
+    if ((st = sync_flags(ctx)) != IPC_OK) return st;
+    newton_done = it + 1;
+    int n_ls = count_flag(ctx, I_LS);
+    if (n_ls == 0) {
+      if (count_flag(ctx, I_ACTIVE) == 0) break;
+      continue;
+    }
+    // CCD-filtered backtracking line search on envs that need it
+    KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, s); });
+    KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, s); });
+    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
+    KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, s); });
+    KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
+    KL(ctx, KC_ACCD, [&] { return launch_accd(d, s); });
+    KL(ctx, KC_LS, [&] { return launch_ls_init(d, s); });
+    KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 0, 0, s); });
+    for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
+      KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 1, 1, s); });
+      KL(ctx, KC_LS, [&] { return launch_ls_decide(d, s); });
+      KL(ctx, KC_LS, [&] { return launch_ls_apply(d, s); });
+      if ((st = sync_flags(ctx)) != IPC_OK) return st;
+      if (count_flag(ctx, I_LS) == 0) break;
+    }
+    if (count_flag(ctx, I_ACTIVE) == 0) break;
+  }
+  KL(ctx, KC_MISC, [&] { return launch_finalize(d, s); });
+  if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  ipc_step_stats S{};
+  for (size_t i = 0; i < sel.size(); ++i) {
+    const int* ei = ctx->h_int + sel[i] * NUM_INTS;
+    if (per_env_status) per_env_status[i] = ei[I_STATUS];
+    S.newton_iters = std::max(S.newton_iters, ei[I_NEWTON]);
+    S.al_updates = std::max(S.al_updates, ei[I_AL]);
+    S.pcg_iters += ei[I_PCGTOT];
+    S.ls_trials += ei[I_LSTOT];
+    S.max_pairs = std::max(S.max_pairs, ei[I_NPAIRS]);
+    S.newton_env_iters += ei[I_NEWTON];
+  }
+  (void)newton_done;
+  S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = S;
+  return IPC_OK;
+}
+
+ipc_status ipc_read_gel_surface(ipc_ctx* ctx, int env, double* out_xyz, int capacity, int* n_written) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  std::vector<double> rows;
+  ipc_status st = download_rows(ctx, env, ctx->dev.x, rows);
+  if (st != IPC_OK) return st;
+  // coated rows are listed in increasing user id order
+  int n = ev.n_coated;
+  for (int i = 0; i < std::min(n, capacity); ++i) {
+    int r = ctx->pk.coated_row[ev.coated_begin + i] - ev.row_begin;
+    for (int c = 0; c < 3; ++c) out_xyz[3 * i + c] = rows[3 * r + c];
+  }
+  if (n_written) *n_written = n;
+  return IPC_OK;
+}
+
+ipc_status ipc_read_gel_surface_all(ipc_ctx* ctx, double* out_xyz, size_t capacity_rows, size_t* rows_written) {
+  if (!ctx || !out_xyz) return IPC_EINVAL;
+  size_t n = std::min<size_t>(capacity_rows, ctx->pk.n_coated);
+  KL(ctx, KC_MISC, [&] { return launch_gather_coated(ctx->dev, ctx->stream); });
+  if (n) CK(cudaMemcpyAsync(out_xyz, ctx->dev.out_stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (rows_written) *rows_written = ctx->pk.n_coated;
+  return last_cuda(ctx);
+}
+
+// ---------------------------------------------------------------- diagnostics
+ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, const double* vec, double* hvec) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const EnvInfo& ev = ctx->pk.env[env];
+  const Dev& d = ctx->dev;
+  ipc_status st;
+  if ((st = begin_single(ctx, env)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx)) != IPC_OK) return st;
+  std::vector<double> rows;
+  size_t nd = 3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies;
+  if (grad) {
+    if ((st = download_rows(ctx, env, d.g, rows)) != IPC_OK) return st;
+    rows_to_dof(ctx, env, rows, grad);
+  }
+  if (energy) {
+    if ((st = select_envs(ctx, {env}, I_LS)) != IPC_OK) return st;
+    CK(cudaMemsetAsync(d.p, 0, 3 * sizeof(double) * d.n_rows, ctx->stream));
+    KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, ctx->stream); });
+    KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 0, 0, ctx->stream); });
+    if ((st = select_envs(ctx, {}, I_LS)) != IPC_OK) return st;
+    if ((st = sync_flags(ctx)) != IPC_OK) return st;
+    *energy = ctx->h_dbl[env * NUM_SCALARS + S_E0];
+  }
+  if (vec && hvec) {
+    std::vector<double> vr;
+    dof_to_rows(ctx, env, vec, vr);
+    if ((st = upload_rows(ctx, env, d.d, vr)) != IPC_OK) return st;
+    if ((st = select_envs(ctx, {env}, I_PCG)) != IPC_OK) return st;
+    KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, ctx->stream); });
+    KL(ctx, KC_SPMV, [&] { return launch_spmv(d, ctx->stream); });
+    if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
+    if ((st = last_cuda(ctx)) != IPC_OK) return st;
+    if ((st = download_rows(ctx, env, d.q, rows)) != IPC_OK) return st;
+    rows_to_dof(ctx, env, rows, hvec);
+  }
+  (void)nd;
+  return IPC_OK;
+}
+
+ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters) {
+  if (check_env(ctx, env) != IPC_OK || !p) return IPC_EINVAL;
+  ipc_status st;
+  if ((st = begin_single(ctx, env)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx)) != IPC_OK) return st;
+  if ((st = run_pcg(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  if (pcg_iters) *pcg_iters = ctx->h_int[env * NUM_INTS + I_PCGIT];
+  std::vector<double> rows;
+  if ((st = download_rows(ctx, env, ctx->dev.p, rows)) != IPC_OK) return st;
+  rows_to_dof(ctx, env, rows, p);
+  return IPC_OK;
+}
+
+ipc_status ipc_debug_pairs(ipc_ctx* ctx, int env, const double* cv_x, const double* cv_x_end, int32_t* out,
+                           int capacity, int* n_pairs) {
+  if (check_env(ctx, env) != IPC_OK || !cv_x) return IPC_EINVAL;
+  const Pack& pk = ctx->pk;
+  const EnvInfo& ev = pk.env[env];
+  const Dev& d = ctx->dev;
+  ipc_status st;
+  // contact vertex positions (internal order) from caller ids
+  std::vector<double> X(3 * (size_t)ev.n_cv), P(3 * (size_t)ev.n_cv, 0.0);
+  for (int i = 0; i < ev.n_cv; ++i) {
+    int u = pk.cv_uid[ev.cv_begin + i];
+    for (int c = 0; c < 3; ++c) {
+      X[3 * i + c] = cv_x[3 * u + c];
+      if (cv_x_end) P[3 * i + c] = cv_x_end[3 * u + c] - cv_x[3 * u + c];
+    }
+  }
+  CK(cudaMemcpyAsync(d.cvx + 3 * (size_t)ev.cv_begin, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(d.cvp + 3 * (size_t)ev.cv_begin, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  if ((st = select_envs(ctx, {env})) != IPC_OK) return st;
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_SEL, cv_x_end != nullptr, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, ctx->stream); });
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_SEL, cv_x_end != nullptr, ctx->stream); });
+  if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  int n = ctx->h_int[env * NUM_INTS + I_NPAIRS];
+  if (n_pairs) *n_pairs = n;
+  int m = std::min(n, ev.pair_cap);
+  std::vector<int4> v(m);
+  std::vector<int> kind(m);
+  if (m) {
+    CK(cudaMemcpyAsync(v.data(), d.pair_v + ev.pair_begin, m * sizeof(int4), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(kind.data(), d.pair_kind + ev.pair_begin, m * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  for (int i = 0; i < std::min(m, capacity); ++i) {
+    out[5 * i] = kind[i];
+    out[5 * i + 1] = pk.cv_uid[v[i].x];
+    out[5 * i + 2] = pk.cv_uid[v[i].y];
+    out[5 * i + 3] = pk.cv_uid[v[i].z];
+    out[5 * i + 4] = pk.cv_uid[v[i].w];
+  }
+  return n > ev.pair_cap ? IPC_EOVERFLOW : IPC_OK;
+}
+
+ipc_status ipc_debug_accd(ipc_ctx* ctx, int env, const double* dir, double* alpha) {
+  if (check_env(ctx, env) != IPC_OK || !dir || !alpha) return IPC_EINVAL;
+  const Dev& d = ctx->dev;
+  ipc_status st;
+  std::vector<double> rows;
+  dof_to_rows(ctx, env, dir, rows);
+  if ((st = upload_rows(ctx, env, d.p, rows)) != IPC_OK) return st;
+  if ((st = select_envs(ctx, {env}, I_LS)) != IPC_OK) return st;
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, ctx->stream); });
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, ctx->stream); });
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, ctx->stream); });
+  // S_ACCD = 1 then min over pairs
+  std::vector<double> one(1, 1.0);
+  CK(cudaMemcpyAsync(d.env_s + env * NUM_SCALARS + S_ACCD, one.data(), sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  KL(ctx, KC_ACCD, [&] { return launch_accd(d, ctx->stream); });
+  if ((st = select_envs(ctx, {}, I_LS)) != IPC_OK) return st;
+  if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  *alpha = ctx->h_dbl[env * NUM_SCALARS + S_ACCD];
+  return IPC_OK;
+}
+
+ipc_status ipc_profile_enable(ipc_ctx* ctx, int on) {
+  if (!ctx) return IPC_EINVAL;
+  if (ctx->prof_launches.empty()) {
+    ctx->prof_launches.assign(KC_COUNT, 0);
+    ctx->prof_ms.assign(KC_COUNT, 0.0);
+  }
+  ctx->prof_on = on != 0;
+  return IPC_OK;
+}
+
+ipc_status ipc_profile_reset(ipc_ctx* ctx) {
+  if (!ctx) return IPC_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  prof_flush(ctx);
+  ctx->prof_launches.assign(KC_COUNT, 0);
+  ctx->prof_ms.assign(KC_COUNT, 0.0);
+  return IPC_OK;
+}
+
+int ipc_profile_count(const ipc_ctx* ctx) { return ctx ? (int)KC_COUNT : 0; }
+
+ipc_status ipc_profile_get(const ipc_ctx* ctx, int i, const char** name, long long* launches, double* ms) {
+  if (!ctx || i < 0 || i >= KC_COUNT) return IPC_EINVAL;
+  if (name) *name = KC_NAME[i];
+  if (launches) *launches = ctx->prof_launches.empty() ? 0 : ctx->prof_launches[i];
+  if (ms) *ms = ctx->prof_ms.empty() ? 0.0 : ctx->prof_ms[i];
+  return IPC_OK;
+}
+
+long long ipc_launch_count(const ipc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks, long long* stored_blocks, int* rows,
+                            int* tets) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const Pack& pk = ctx->pk;
+  const EnvInfo& ev = pk.env[env];
+  long long stored = 0, real = 0;
+  for (int ch = ev.chunk_begin; ch < ev.chunk_begin + ev.n_chunks; ++ch) {
+    stored += 32LL * pk.chunk_slots[ch];
+    for (int sl = 0; sl < pk.chunk_slots[ch]; ++sl)
+      for (int l = 0; l < 32; ++l) {
+        long long blk = pk.chunk_ptr[ch] + 32LL * sl + l;
+        int r = ch * 32 + l;  // global row
+        int lr = r - ev.row_begin;
+        bool gel = lr < ev.n_verts;
+        bool body = lr >= ev.gel_rows && lr < ev.gel_rows + 4 * ev.n_bodies;
+        if (gel && (sl == 0 || pk.sell_col[blk] != r)) ++real;
+        if (body && sl < 4) ++real;
+      }
+  }
+  if (real_blocks) *real_blocks = real;
+  if (stored_blocks) *stored_blocks = stored;
+  if (rows) *rows = ev.n_rows;
+  if (tets) *tets = ev.n_tets;
+  return IPC_OK;
+}
+
+// ---------------------------------------------------------------- element kernels
+ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol, double mu, double lam,
+                     double* energy, double* grad, double* hess, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !Dm_inv || !vol))) return IPC_EINVAL;
+  launch_k_tet(n, x, Dm_inv, vol, mu, lam, energy, grad, hess, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
+}
+
+ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight, const double* eps_x,
+                         double dhat, double* energy, double* grad, double* hess, void* stream) {
+  if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0)) return IPC_EINVAL;
+  launch_k_barrier(n, X, is_ee, weight, eps_x, dhat, energy, grad, hess, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
+}
+
+ipc_status ipc_k_accd(int n, const double* X0, const double* P, const int32_t* is_ee, double s, int max_iter,
+                      double* toi, void* stream) {
+  if (n < 0 || (n > 0 && (!X0 || !P || !is_ee || !toi)) || !(s > 0 && s < 1) || max_iter < 1) return IPC_EINVAL;
+  launch_k_accd(n, X0, P, is_ee, s, max_iter, toi, reinterpret_cast<cudaStream_t>(stream));
+  return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Device context: every array the kernels touch, carved out of the caller's
+// workspace.  `Dev` is passed by value to kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "scene.h"
+
+namespace ipc {
+
+// per-env double scalars
+enum EnvScalar {
+  S_RZ = 0,     // PCG r.z
+  S_DQ,         // PCG d.q
+  S_RR,         // PCG r.r
+  S_RR0,        // PCG |b|^2
+  S_PALPHA,     // PCG alpha
+  S_PBETA,      // PCG beta
+  S_PNORM,      // Newton |p|_inf (full space)
+  S_CRES,       // AL constraint residual |q - s|_inf (full space)
+  S_ACCD,       // CCD step bound
+  S_ALPHA,      // line-search step
+  S_E0,         // energy at the line-search start
+  S_E1,         // energy at the trial step
+  S_MIND,       // min pair distance (diagnostics)
+  NUM_SCALARS
+};
+
+// per-env int state
+enum EnvInt {
+  I_ACTIVE = 0,   // still iterating Newton in this step
+  I_PCG,          // PCG still running
+  I_LS,           // line search still running
+  I_STATUS,       // ipc_status of this env for the current step
+  I_NEWTON,       // Newton iterations done
+  I_AL,           // AL updates done
+  I_LSIT,         // halvings in the current line search
+  I_PCGIT,        // PCG iterations in the current solve
+  I_MODE,         // after the Newton check: 0 line search, 1 converged, 2 AL update
+  I_NPAIRS,       // candidate pairs in the current list
+  I_OVERFLOW,     // pair list overflowed
+  I_ACCEPT,       // line search accepted this trial
+  I_PCGTOT,       // PCG iterations this step
+  I_LSTOT,        // line-search trials this step
+  I_SEL,          // selected for this ipc_step call
+  I_FLAG,         // scratch flag (inverted tet found)
+  NUM_INTS
+};
+
+struct Dev {
+  int n_envs, n_rows, n_tets, n_cv, n_tri, n_edge, n_obj, n_bodies, n_chunks, n_coated;
+  long long n_blocks, n_pairs_cap;
+  // parameters
+  double h, grav[3], dhat, kappa, newton_tol, pcg_tol, accd_s, al_kappa, ee_moll;
+  int newton_max, pcg_max, ls_max, accd_max, al_max;
+  // static tables
+  const int *env_row_off, *env_tet_off, *env_cv_off, *env_tri_off, *env_edge_off, *env_obj_off,
+      *env_body_off, *env_chunk_off, *env_coated_off, *env_pair_cap, *env_pair_off;
+  const double *env_mu, *env_lam;
+  const int* cta_env;
+  const int* env_has_driven;    // env has driven bodies or attached gel rows
+  const double* row_mass;
+  const uint8_t* row_kind;
+  const int* row_body;
+  const double* row_xbar;
+  const int *vt_ptr, *vt_src;
+  const int* tets;
+  const double *Dm_inv, *tet_vol;
+  const int* chunk_slots;
+  const long long* chunk_ptr;
+  const int *sell_col, *asm_ptr, *asm_src;
+  const int *body_row, *body_env, *body_cv_begin, *body_nv;
+  const double *body_mass, *body_S, *body_vol, *body_kappa;
+  const uint8_t* body_driven;
+  const int *cv_row, *cv_body, *cv_obj, *cv_uid;
+  const double *cv_xbar, *cv_area;
+  const uint8_t* cv_fixed;
+  const int *tri, *tri_obj, *edge, *edge_obj;
+  const double *edge_area, *edge_len2;
+  const int *obj_env, *obj_local, *obj_cv_begin, *obj_cv_end, *obj_tri_begin, *obj_tri_end,
+      *obj_edge_begin, *obj_edge_end, *obj_size;
+  const unsigned long long* obj_exclude;
+  const int* coated_row;
+  // state and work (row space: 3 doubles per row)
+  double *x, *v, *xn, *xt, *s_tgt, *lam;
+  double *p, *g, *r, *z, *d, *q, *qc;
+  double *pc, *pc_acc;          // 9 per row
+  double *body_pc, *body_pc_acc, *body_g, *body_H, *body_E;  // per body 144 / 144 / 12 / 144 / 1
+  double *sell_val;             // n_blocks * 9
+  double *tetG, *tetH, *tetE;   // 12 / 144 / 1 per tet
+  double* row_E;
+  double *cvx, *cvp;            // 3 per contact vertex
+  double* obj_box;              // 6 per object
+  int4* pair_v;                 // contact vertex ids
+  int* pair_kind;               // 0 PT, 1 EE
+  double *pair_w, *pair_eps, *pair_H, *pair_E;
+  uint8_t* pair_act;
+  double* cta_part;             // 4 per row CTA
+  unsigned int* env_cnt;        // last-CTA counters (2 per env)
+  double* tgt_stage;            // [n_envs][max_bodies][12] host targets
+  double* out_stage;            // [n_coated][3] coated-surface positions
+  int max_bodies;
+  double* env_s;                // NUM_SCALARS per env
+  int* env_i;                   // NUM_INTS per env
+};
+
+struct Layout {
+  size_t total = 0;
+  std::vector<std::pair<void**, size_t>> items;  // (slot, bytes)
+};
+
+}  // namespace ipc
+
+struct ipc_ctx {
+  ipc::Pack pk;
+  ipc::Dev dev;
+  ipc_params prm;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::string err;
+  int* h_int = nullptr;       // pinned read-back (NUM_INTS * n_envs ints)
+  double* h_dbl = nullptr;    // pinned read-back (NUM_SCALARS * n_envs doubles)
+  int max_bodies = 0;
+  std::vector<int> n_cta_env;  // row CTAs per env
+  // profiling
+  bool prof_on = false;
+  long long launches = 0;
+  std::vector<long long> prof_launches;
+  std::vector<double> prof_ms;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pend { int kind; cudaEvent_t a, b; };
+  std::vector<Pend> pending;
+};

@@ -1,0 +1,56 @@
+// Launch wrappers of the ABD-IPC kernels (host-callable).
+#pragma once
+
+#include "ctx.h"
+
+namespace ipc {
+
+// env masks passed to kernels: the EnvInt flag that must be non-zero
+// (I_SEL, I_ACTIVE, I_PCG, I_LS) for an env to be processed.
+
+// ---- contact (kernels_contact.cu)
+int launch_cv_pos(const Dev& d, int flag, bool with_disp, cudaStream_t s);
+int launch_obj_box(const Dev& d, int flag, bool swept, cudaStream_t s);
+int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s);
+int launch_barrier(const Dev& d, int flag, cudaStream_t s);
+int launch_pair_spmv(const Dev& d, cudaStream_t s);
+int launch_accd(const Dev& d, cudaStream_t s);
+int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s);
+int launch_min_dist(const Dev& d, int flag, cudaStream_t s);
+int launch_pnorm_body(const Dev& d, cudaStream_t s);
+
+// ---- solver (kernels_solver.cu)
+int launch_predict(const Dev& d, cudaStream_t s);
+int launch_attach_targets(const Dev& d, int flag, cudaStream_t s);
+int launch_tet(const Dev& d, cudaStream_t s);
+int launch_body(const Dev& d, cudaStream_t s);
+int launch_assemble(const Dev& d, cudaStream_t s);
+int launch_grad(const Dev& d, cudaStream_t s);
+int launch_precond(const Dev& d, cudaStream_t s);
+int launch_pcg_init(const Dev& d, cudaStream_t s);
+int launch_spmv(const Dev& d, cudaStream_t s);
+int launch_pcg_update(const Dev& d, cudaStream_t s);
+int launch_pcg_dir(const Dev& d, cudaStream_t s);
+int launch_newton_check(const Dev& d, cudaStream_t s);   // pnorm / cres (rows)
+int launch_newton_decide(const Dev& d, cudaStream_t s);
+int launch_al_update(const Dev& d, cudaStream_t s);
+int launch_ls_init(const Dev& d, cudaStream_t s);
+int launch_energy(const Dev& d, int use_alpha, int which /*0: E0, 1: E1*/, cudaStream_t s);
+int launch_ls_decide(const Dev& d, cudaStream_t s);
+int launch_ls_apply(const Dev& d, cudaStream_t s);
+int launch_finalize(const Dev& d, cudaStream_t s);
+int launch_env_reset(const Dev& d, int what, cudaStream_t s);
+int launch_check_overflow(const Dev& d, cudaStream_t s);
+int launch_check_inverted(const Dev& d, cudaStream_t s);
+int launch_scatter_targets(const Dev& d, cudaStream_t s);
+int launch_gather_coated(const Dev& d, cudaStream_t s);
+
+// element kernels on caller buffers
+int launch_k_tet(int n, const double* x, const double* Dmi, const double* vol, double mu, double lam,
+                  double* E, double* g, double* H, cudaStream_t s);
+int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
+                      double dhat, double* E, double* g, double* H, cudaStream_t s);
+int launch_k_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac, int max_iter,
+                   double* toi, cudaStream_t s);
+
+}  // namespace ipc

@@ -1,0 +1,455 @@
+// Contact kernels: contact-vertex positions, object boxes, broad phase,
+// barrier energy/gradient/Hessian (K1, K2), matrix-free contact mat-vec,
+// additive CCD (K7) and pair energies for the line search.
+#include "common.cuh"
+#include "kernels.h"
+#include "physics.cuh"
+
+namespace ipc {
+
+#define ENVI(d, e, k) (d).env_i[(e) * NUM_INTS + (k)]
+#define ENVS(d, e, k) (d).env_s[(e) * NUM_SCALARS + (k)]
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// contact vertex positions: gel vertex -> x[row]; body vertex j -> p + A xbar_j
+// (phi(y), Sec. 3.3).  With `with_disp` also the displacement along p.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ D3 body_point(const double* x, int br, D3 xb) {
+  return ld3(x, br) + xb.x * ld3(x, br + 1) + xb.y * ld3(x, br + 2) + xb.z * ld3(x, br + 3);
+}
+
+__global__ void k_cv_pos(Dev d, int flag, int with_disp) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.n_cv) return;
+  int e = find_env(d.env_cv_off, d.n_envs, c);
+  if (!ENVI(d, e, flag)) return;
+  int row = d.cv_row[c];
+  if (d.cv_body[c] < 0) {
+    st3(d.cvx, c, ld3(d.x, row));
+    if (with_disp) st3(d.cvp, c, ld3(d.p, row));
+  } else {
+    D3 xb = ld3(d.cv_xbar, c);
+    st3(d.cvx, c, body_point(d.x, row, xb));
+    if (with_disp) st3(d.cvp, c, body_point(d.p, row, xb));
+  }
+}
+
+// one CTA per object: box of its contact vertices (swept: at both ends)
+__global__ void k_obj_box(Dev d, int flag, int swept) {
+  int o = blockIdx.x;
+  int e = d.obj_env[o];
+  if (!ENVI(d, e, flag)) return;
+  __shared__ double sh[32];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int c = d.obj_cv_begin[o] + threadIdx.x; c < d.obj_cv_end[o]; c += blockDim.x) {
+    D3 a = ld3(d.cvx, c);
+    for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], comp(a, k)); hi[k] = fmax(hi[k], comp(a, k)); }
+    if (swept) {
+      D3 b = a + ld3(d.cvp, c);
+      for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], comp(b, k)); hi[k] = fmax(hi[k], comp(b, k)); }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    double m = -block_max(-lo[k], sh);
+    if (threadIdx.x == 0) d.obj_box[6 * o + k] = m;
+    double M = block_max(hi[k], sh);
+    if (threadIdx.x == 0) d.obj_box[6 * o + 3 + k] = M;
+  }
+}
+
+struct Box {
+  double lo[3], hi[3];
+};
+
+__device__ __forceinline__ void box_init(Box& b) {
+  for (int k = 0; k < 3; ++k) { b.lo[k] = INFINITY; b.hi[k] = -INFINITY; }
+}
+__device__ __forceinline__ void box_add(Box& b, const Dev& d, int c, int swept) {
+  D3 a = ld3(d.cvx, c);
+  for (int k = 0; k < 3; ++k) { b.lo[k] = fmin(b.lo[k], comp(a, k)); b.hi[k] = fmax(b.hi[k], comp(a, k)); }
+  if (swept) {
+    D3 q = a + ld3(d.cvp, c);
+    for (int k = 0; k < 3; ++k) { b.lo[k] = fmin(b.lo[k], comp(q, k)); b.hi[k] = fmax(b.hi[k], comp(q, k)); }
+  }
+}
+// widened overlap: lo_a <= hi_b + dhat and lo_b <= hi_a + dhat on every axis
+__device__ __forceinline__ bool overlap(const Box& a, const double* lo, const double* hi, double dh) {
+  for (int k = 0; k < 3; ++k)
+    if (!(a.lo[k] <= hi[k] + dh) || !(lo[k] <= a.hi[k] + dh)) return false;
+  return true;
+}
+
+__device__ __forceinline__ bool bigger(const Dev& d, int A, int B) {
+  int sa = d.obj_size[A], sb = d.obj_size[B];
+  return sa > sb || (sa == sb && A < B);
+}
+
+__device__ void emit_pair(const Dev& d, int e, int4 v, int kind, double w, double eps) {
+  int slot = atomicAdd(&ENVI(d, e, I_NPAIRS), 1);
+  if (slot >= d.env_pair_cap[e]) {
+    ENVI(d, e, I_OVERFLOW) = 1;
+    return;
+  }
+  long long k = d.env_pair_off[e] + slot;
+  d.pair_v[k] = v;
+  d.pair_kind[k] = kind;
+  d.pair_w[k] = w;
+  d.pair_eps[k] = eps;
+}
+
+// Broad phase.  Each unordered object pair {A, B} is handled from the bigger
+// object's primitives (culled by the smaller object's box), looping over the
+// smaller object's primitives:
+//   QK = 0: points of A vs triangles of B   -> PT(point A, tri B)
+//   QK = 1: triangles of A vs points of B   -> PT(point B, tri A)
+//   QK = 2: edges of A vs edges of B        -> EE(lower object first)
+template <int QK>
+__global__ void k_broad(Dev d, int flag, int swept) {
+  int n_q = QK == 0 ? d.n_cv : (QK == 1 ? d.n_tri : d.n_edge);
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_q) return;
+  const int* qoff = QK == 0 ? d.env_cv_off : (QK == 1 ? d.env_tri_off : d.env_edge_off);
+  int e = find_env(qoff, d.n_envs, i);
+  if (!ENVI(d, e, flag)) return;
+  int A;
+  int qv[3];
+  int nqv;
+  if (QK == 0) {
+    A = d.cv_obj[i];
+    qv[0] = i; nqv = 1;
+  } else if (QK == 1) {
+    A = d.tri_obj[i];
+    qv[0] = d.tri[3 * i]; qv[1] = d.tri[3 * i + 1]; qv[2] = d.tri[3 * i + 2]; nqv = 3;
+  } else {
+    A = d.edge_obj[i];
+    qv[0] = d.edge[2 * i]; qv[1] = d.edge[2 * i + 1]; nqv = 2;
+  }
+  Box qb;
+  box_init(qb);
+  bool qfix = true;
+  for (int k = 0; k < nqv; ++k) {
+    box_add(qb, d, qv[k], swept);
+    qfix = qfix && d.cv_fixed[qv[k]];
+  }
+  const double dh = d.dhat;
+  const double wscale = d.h * d.h * d.kappa;
+  unsigned long long ex = d.obj_exclude[A];
+  for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1]; ++B) {
+    if (B == A || ((ex >> d.obj_local[B]) & 1ull)) continue;
+    if (!bigger(d, A, B)) continue;
+    if (!overlap(qb, d.obj_box + 6 * B, d.obj_box + 6 * B + 3, dh)) continue;
+    if (QK == 0) {
+      for (int t = d.obj_tri_begin[B]; t < d.obj_tri_end[B]; ++t) {
+        int t0 = d.tri[3 * t], t1 = d.tri[3 * t + 1], t2 = d.tri[3 * t + 2];
+        Box tb;
+        box_init(tb);
+        box_add(tb, d, t0, swept); box_add(tb, d, t1, swept); box_add(tb, d, t2, swept);
+        if (!overlap(qb, tb.lo, tb.hi, dh)) continue;
+        if (qfix && d.cv_fixed[t0] && d.cv_fixed[t1] && d.cv_fixed[t2]) continue;
+        emit_pair(d, e, make_int4(i, t0, t1, t2), 0, wscale * 0.5 * d.cv_area[i], 0.0);
+      }
+    } else if (QK == 1) {
+      for (int c = d.obj_cv_begin[B]; c < d.obj_cv_end[B]; ++c) {
+        Box pb;
+        box_init(pb);
+        box_add(pb, d, c, swept);
+        if (!overlap(qb, pb.lo, pb.hi, dh)) continue;
+        if (qfix && d.cv_fixed[c]) continue;
+        emit_pair(d, e, make_int4(c, qv[0], qv[1], qv[2]), 0, wscale * 0.5 * d.cv_area[c], 0.0);
+      }
+    } else {
+      for (int f = d.obj_edge_begin[B]; f < d.obj_edge_end[B]; ++f) {
+        int b0 = d.edge[2 * f], b1 = d.edge[2 * f + 1];
+        Box eb;
+        box_init(eb);
+        box_add(eb, d, b0, swept); box_add(eb, d, b1, swept);
+        if (!overlap(qb, eb.lo, eb.hi, dh)) continue;
+        if (qfix && d.cv_fixed[b0] && d.cv_fixed[b1]) continue;
+        double w = wscale * 0.25 * (d.edge_area[i] + d.edge_area[f]);
+        double eps = d.ee_moll * d.edge_len2[i] * d.edge_len2[f];
+        int4 v = (A < B) ? make_int4(qv[0], qv[1], b0, b1) : make_int4(b0, b1, qv[0], qv[1]);
+        emit_pair(d, e, v, 1, w, eps);
+      }
+    }
+  }
+}
+
+// env of pair slot k (segments of capacity env_pair_cap) and validity
+__device__ __forceinline__ int pair_env(const Dev& d, int k, bool& valid) {
+  int e = find_env(d.env_pair_off, d.n_envs, k);
+  valid = (k - d.env_pair_off[e]) < min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);
+  return e;
+}
+
+// ---------------------------------------------------------------------------
+// barrier: energy, gradient (scattered into qc), PSD Hessian (stored), and the
+// diagonal-block preconditioner contributions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scatter_cv(const Dev& d, double* dst, int cv, D3 gvec) {
+  int row = d.cv_row[cv];
+  if (d.cv_body[cv] < 0) {
+    if (d.row_kind[row] == ROW_PINNED) return;
+    atomic_add3(dst, row, gvec);
+  } else {
+    D3 xb = ld3(d.cv_xbar, cv);
+    atomic_add3(dst, row, gvec);
+    atomic_add3(dst, row + 1, xb.x * gvec);
+    atomic_add3(dst, row + 2, xb.y * gvec);
+    atomic_add3(dst, row + 3, xb.z * gvec);
+  }
+}
+
+__global__ void k_barrier(Dev d, int flag) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n_pairs_cap) return;
+  bool valid;
+  int e = pair_env(d, k, valid);
+  if (!valid || !ENVI(d, e, flag)) return;
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  D3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
+  double E, g[12], work[288];
+  double* H = d.pair_H + (long long)k * 144;
+  bool act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H, work);
+  d.pair_act[k] = act ? 1 : 0;
+  if (!act) return;
+  for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
+  // preconditioner: diagonal 3x3 of gel vertices, body 12x12 self terms
+  for (int i = 0; i < 4; ++i) {
+    int cv = cvs[i];
+    if (d.cv_body[cv] >= 0) continue;
+    int row = d.cv_row[cv];
+    if (d.row_kind[row] == ROW_PINNED) continue;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) atomicAdd(d.pc_acc + 9 * row + 3 * a + b, H[(3 * i + a) * 12 + 3 * i + b]);
+  }
+  int done_body[4] = {-1, -1, -1, -1};
+  for (int i = 0; i < 4; ++i) {
+    int b = d.cv_body[cvs[i]];
+    if (b < 0) continue;
+    bool seen = false;
+    for (int j = 0; j < i; ++j) seen |= (done_body[j] == b);
+    done_body[i] = b;
+    if (seen) continue;
+    // M_kl (3x3 blocks k,l in 0..3) = sum_{i,j on b} w_ik w_jl H_ij, w = [1, xbar]
+    double wv[4][4];
+    bool on[4];
+    for (int m = 0; m < 4; ++m) {
+      on[m] = d.cv_body[cvs[m]] == b;
+      D3 xb = ld3(d.cv_xbar, cvs[m]);
+      wv[m][0] = 1.0; wv[m][1] = xb.x; wv[m][2] = xb.y; wv[m][3] = xb.z;
+    }
+    for (int kk = 0; kk < 4; ++kk)
+      for (int ll = 0; ll < 4; ++ll)
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int m = 0; m < 4; ++m) {
+              if (!on[m]) continue;
+              for (int n = 0; n < 4; ++n) {
+                if (!on[n]) continue;
+                s += wv[m][kk] * wv[n][ll] * H[(3 * m + a) * 12 + 3 * n + c];
+              }
+            }
+            atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, s);
+          }
+  }
+}
+
+// q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
+// eliminated: read as zero, never written)
+__global__ void k_pair_spmv(Dev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n_pairs_cap) return;
+  bool valid;
+  int e = pair_env(d, k, valid);
+  if (!valid || !ENVI(d, e, I_PCG) || !d.pair_act[k]) return;
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  double dl[12];
+  for (int i = 0; i < 4; ++i) {
+    int cv = cvs[i], row = d.cv_row[cv];
+    D3 u;
+    if (d.cv_body[cv] < 0) {
+      u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
+    } else {
+      u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+    }
+    dl[3 * i] = u.x; dl[3 * i + 1] = u.y; dl[3 * i + 2] = u.z;
+  }
+  const double* H = d.pair_H + (long long)k * 144;
+  for (int i = 0; i < 4; ++i) {
+    double o[3];
+    for (int a = 0; a < 3; ++a) {
+      double s = 0;
+      for (int q = 0; q < 12; ++q) s += H[(3 * i + a) * 12 + q] * dl[q];
+      o[a] = s;
+    }
+    scatter_cv(d, d.qc, cvs[i], D3{o[0], o[1], o[2]});
+  }
+}
+
+// ACCD time of impact per swept pair; env bound = min over its pairs
+__global__ void k_accd(Dev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n_pairs_cap) return;
+  bool valid;
+  int e = pair_env(d, k, valid);
+  if (!valid || !ENVI(d, e, I_LS)) return;
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  D3 X[4], P[4];
+  for (int i = 0; i < 4; ++i) { X[i] = ld3(d.cvx, cvs[i]); P[i] = ld3(d.cvp, cvs[i]); }
+  double t = accd_toi(X, P, d.pair_kind[k] == 1, d.accd_s, 1.0, d.accd_max);
+  atomic_min_nonneg(&ENVS(d, e, S_ACCD), t);
+}
+
+// barrier energy of each swept pair at x + alpha p (+inf if touching)
+__global__ void k_pair_energy(Dev d, int use_alpha) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n_pairs_cap) return;
+  bool valid;
+  int e = pair_env(d, k, valid);
+  if (!valid || !ENVI(d, e, I_LS)) return;
+  double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  D3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]) + a * ld3(d.cvp, cvs[i]);
+  double D = pair_sqdist(X, d.pair_kind[k] == 1);
+  double E = 0.0;
+  if (!(D > 0.0)) E = INFINITY;
+  else pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, nullptr, nullptr, nullptr);
+  d.pair_E[k] = E;
+}
+
+// min distance over the listed pairs (diagnostics / set_state check)
+__global__ void k_min_dist(Dev d, int flag) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n_pairs_cap) return;
+  bool valid;
+  int e = pair_env(d, k, valid);
+  if (!valid || !ENVI(d, e, flag)) return;
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  D3 X[4];
+  for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
+  double D = pair_sqdist(X, d.pair_kind[k] == 1);
+  atomic_min_nonneg(&ENVS(d, e, S_MIND), sqrt(fmax(D, 0.0)));
+}
+
+// |J_j p_b|_inf over body vertices into S_PNORM; |J_j (y_b - s_b)|_inf of
+// driven bodies into S_CRES
+__global__ void k_pnorm_body(Dev d) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.n_cv) return;
+  int b = d.cv_body[c];
+  if (b < 0) return;
+  int e = d.body_env[b];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  int row = d.cv_row[c];
+  D3 xb = ld3(d.cv_xbar, c);
+  D3 u = body_point(d.p, row, xb);
+  atomic_max_nonneg(&ENVS(d, e, S_PNORM), fmax(fabs(u.x), fmax(fabs(u.y), fabs(u.z))));
+  if (d.body_driven[b]) {
+    D3 r = body_point(d.x, row, xb) - body_point(d.s_tgt, row, xb);
+    atomic_max_nonneg(&ENVS(d, e, S_CRES), fmax(fabs(r.x), fmax(fabs(r.y), fabs(r.z))));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_cv_pos(const Dev& d, int flag, bool with_disp, cudaStream_t s) {
+  if (!d.n_cv) return 0;
+  k_cv_pos<<<nblk(d.n_cv, 256), 256, 0, s>>>(d, flag, with_disp ? 1 : 0);
+  return 1;
+}
+int launch_obj_box(const Dev& d, int flag, bool swept, cudaStream_t s) {
+  if (!d.n_obj) return 0;
+  k_obj_box<<<d.n_obj, 256, 0, s>>>(d, flag, swept ? 1 : 0);
+  return 1;
+}
+int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s) {
+  int n = 0;
+  if (d.n_cv) { k_broad<0><<<nblk(d.n_cv, 128), 128, 0, s>>>(d, flag, swept); ++n; }
+  if (d.n_tri) { k_broad<1><<<nblk(d.n_tri, 128), 128, 0, s>>>(d, flag, swept); ++n; }
+  if (d.n_edge) { k_broad<2><<<nblk(d.n_edge, 128), 128, 0, s>>>(d, flag, swept); ++n; }
+  return n;
+}
+int launch_barrier(const Dev& d, int flag, cudaStream_t s) {
+  if (!d.n_pairs_cap) return 0;
+  k_barrier<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, flag);
+  return 1;
+}
+int launch_pair_spmv(const Dev& d, cudaStream_t s) {
+  if (!d.n_pairs_cap) return 0;
+  k_pair_spmv<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d);
+  return 1;
+}
+int launch_accd(const Dev& d, cudaStream_t s) {
+  if (!d.n_pairs_cap) return 0;
+  k_accd<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d);
+  return 1;
+}
+int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s) {
+  if (!d.n_pairs_cap) return 0;
+  k_pair_energy<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, use_alpha);
+  return 1;
+}
+int launch_min_dist(const Dev& d, int flag, cudaStream_t s) {
+  if (!d.n_pairs_cap) return 0;
+  k_min_dist<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, flag);
+  return 1;
+}
+int launch_pnorm_body(const Dev& d, cudaStream_t s) {
+  if (!d.n_cv) return 0;
+  k_pnorm_body<<<nblk(d.n_cv, 256), 256, 0, s>>>(d);
+  return 1;
+}
+
+// ---------------------------------------------------------------------------
+// element kernels on caller buffers
+// ---------------------------------------------------------------------------
+__global__ void k_elem_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
+                               double dhat, double* E, double* g, double* H) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  D3 P[4];
+  for (int i = 0; i < 4; ++i) P[i] = ld3(X + 12 * (long long)k, i);
+  double e = 0, gl[12], work[288];
+  double* Hk = H ? H + 144 * (long long)k : nullptr;
+  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, work);
+  if (E) E[k] = e;
+  if (g)
+    for (int i = 0; i < 12; ++i) g[12 * (long long)k + i] = act ? gl[i] : 0.0;
+  if (Hk && !act)
+    for (int i = 0; i < 144; ++i) Hk[i] = 0.0;
+}
+
+__global__ void k_elem_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac,
+                            int max_iter, double* toi) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  D3 A[4], B[4];
+  for (int i = 0; i < 4; ++i) { A[i] = ld3(X0 + 12 * (long long)k, i); B[i] = ld3(P + 12 * (long long)k, i); }
+  toi[k] = accd_toi(A, B, is_ee[k] != 0, sfrac, 1.0, max_iter);
+}
+
+int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
+                     double dhat, double* E, double* g, double* H, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_elem_barrier<<<nblk(n, 64), 64, 0, s>>>(n, X, is_ee, w, eps, dhat, E, g, H);
+  return 1;
+}
+int launch_k_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac, int max_iter,
+                  double* toi, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_elem_accd<<<nblk(n, 128), 128, 0, s>>>(n, X0, P, is_ee, sfrac, max_iter, toi);
+  return 1;
+}
+
+}  // namespace ipc

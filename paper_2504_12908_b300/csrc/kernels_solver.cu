@@ -1,0 +1,795 @@
+// Solver kernels: prediction, per-tet elastic (K3) and per-body ABD (K4)
+// terms, gather assembly into SELL-32 (K5), block-Jacobi PCG (K6), Newton
+// bookkeeping and line-search energies (K8, K9).
+//
+// Row space: every "row" is 3 DoFs - a gel vertex, or one of the 4 sub-rows
+// [p, a0, a1, a2] of an affine body.  Rows of one env form a contiguous range
+// padded to a multiple of 128 so that a 128-thread CTA never straddles envs.
+#include "common.cuh"
+#include "kernels.h"
+#include "physics.cuh"
+
+namespace ipc {
+
+#define ENVI(d, e, k) (d).env_i[(e) * NUM_INTS + (k)]
+#define ENVS(d, e, k) (d).env_s[(e) * NUM_SCALARS + (k)]
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+__device__ __forceinline__ bool is_gel(uint8_t k) { return k <= ROW_ATTACHED; }
+__device__ __forceinline__ bool is_body(uint8_t k) { return k == ROW_BODY || k == ROW_BODY_DRIVEN; }
+__device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED || k == ROW_BODY_DRIVEN; }
+
+// Deterministic per-env reduction of CTA partials: every CTA of the env
+// writes `n` partials; the last CTA to arrive sums them in CTA order.
+// Returns true in thread 0 of the last CTA, with the sums in out[0..n).
+template <int n>
+__device__ bool env_reduce(const Dev& d, int e, int which, const double* vals /*per thread*/, double* out) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  double part[n];
+  for (int j = 0; j < n; ++j) part[j] = block_sum(vals[j], sh);
+  int cta = blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
+    __threadfence();
+    unsigned int t = atomicAdd(&d.env_cnt[2 * e + which], 1u);
+    int ncta = (d.env_row_off[e + 1] - d.env_row_off[e]) >> 7;
+    last = (t == (unsigned)(ncta - 1));
+  }
+  __syncthreads();
+  if (!last) return false;
+  int c0 = d.env_row_off[e] >> 7, c1 = d.env_row_off[e + 1] >> 7;
+  for (int j = 0; j < n; ++j) {
+    double s = 0;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) s += __ldcg(d.cta_part + 4 * c + j);
+    out[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) d.env_cnt[2 * e + which] = 0;
+  return threadIdx.x == 0;
+}
+
+// ---------------------------------------------------------------------------
+// prediction: xn = x, xt = x + h v (body rows: y, ydot), multipliers zero
+// ---------------------------------------------------------------------------
+__global__ void k_predict(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_SEL)) return;
+  D3 x = ld3(d.x, r), v = ld3(d.v, r);
+  st3(d.xn, r, x);
+  st3(d.xt, r, x + d.h * v);
+  st3(d.lam, r, D3{0, 0, 0});
+}
+
+// targets of attached gel rows: s = p_t + A_t xbar (from the body's target rows)
+__global__ void k_attach_targets(Dev d, int flag) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, flag) || d.row_kind[r] != ROW_ATTACHED) return;
+  int br = d.body_row[d.row_body[r]];
+  D3 xb = ld3(d.row_xbar, r);
+  D3 s = ld3(d.s_tgt, br) + xb.x * ld3(d.s_tgt, br + 1) + xb.y * ld3(d.s_tgt, br + 2) + xb.z * ld3(d.s_tgt, br + 3);
+  st3(d.s_tgt, r, s);
+}
+
+// ---------------------------------------------------------------------------
+// K3: per-tet neo-Hookean gradient and projected Hessian blocks
+// ---------------------------------------------------------------------------
+__global__ void k_tet(Dev d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_tets) return;
+  int e = find_env(d.env_tet_off, d.n_envs, t);
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  const int* q = d.tets + 4 * (long long)t;
+  D3 X[4];
+  for (int a = 0; a < 4; ++a) X[a] = ld3(d.x, q[a]);
+  double Dmi[9];
+  for (int k = 0; k < 9; ++k) Dmi[k] = d.Dm_inv[9 * (long long)t + k];
+  double F[9];
+  tet_deformation<double>(X, Dmi, F);
+  double vol = d.tet_vol[t], mu = d.env_mu[e], lam = d.env_lam[e];
+  double g[12];
+  nh_gradient<double>(F, Dmi, vol, mu, lam, g);
+  double* G = d.tetG + 12 * (long long)t;
+  for (int k = 0; k < 12; ++k) G[k] = g[k];
+  double* H = d.tetH + 144 * (long long)t;
+  nh_hessian_blocks<double>(F, Dmi, vol, mu, lam,
+                            [&](int a, int b, int i, int j, double v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
+}
+
+// ---------------------------------------------------------------------------
+// K4: per-body inertia, gravity, orthogonality (Sec. 3.3) and AL terms
+//   orthogonality V = kappa_s V_b sum_kl (a_k.a_l - d_kl)^2:
+//     dV/da_m = 4 kappa_s V_b sum_l C_ml a_l
+//     d2V/da_m da_n = 4 kappa_s V_b [d_mn A A^T + a_n a_m^T + C_mn I]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void body_My_mul(double m, const double* S, const double* v, double* out) {
+  for (int c = 0; c < 3; ++c) out[c] = m * v[c];
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0;
+      for (int l = 0; l < 3; ++l) s += S[3 * k + l] * v[3 + 3 * l + c];
+      out[3 + 3 * k + c] = s;
+    }
+}
+
+__global__ void k_body(Dev d) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.n_bodies) return;
+  int e = d.body_env[b];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  int br = d.body_row[b];
+  double y[12], yt[12], dy[12], gb[12];
+  for (int k = 0; k < 12; ++k) {
+    y[k] = d.x[3 * br + k];
+    yt[k] = d.xt[3 * br + k];
+    dy[k] = y[k] - yt[k];
+  }
+  double m = d.body_mass[b];
+  const double* S = d.body_S + 9 * b;
+  body_My_mul(m, S, dy, gb);
+  double h2 = d.h * d.h;
+  for (int c = 0; c < 3; ++c) gb[c] -= h2 * m * d.grav[c];
+  double ko = h2 * d.body_kappa[b] * d.body_vol[b];
+  const double* a = y + 3;  // a_k = a[3k..3k+3)
+  double C[9];
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      C[3 * k + l] = a[3 * k] * a[3 * l] + a[3 * k + 1] * a[3 * l + 1] + a[3 * k + 2] * a[3 * l + 2] - (k == l ? 1.0 : 0.0);
+  for (int mm = 0; mm < 3; ++mm)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0;
+      for (int l = 0; l < 3; ++l) s += C[3 * mm + l] * a[3 * l + c];
+      gb[3 + 3 * mm + c] += 4.0 * ko * s;
+    }
+  double Ho[81], work[162];
+  double AAt[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) AAt[3 * i + j] = a[i] * a[j] + a[3 + i] * a[3 + j] + a[6 + i] * a[6 + j];
+  for (int mm = 0; mm < 3; ++mm)
+    for (int n = 0; n < 3; ++n)
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          double v = a[3 * n + i] * a[3 * mm + j] + (i == j ? C[3 * mm + n] : 0.0);
+          if (mm == n) v += AAt[3 * i + j];
+          Ho[(3 * mm + i) * 9 + 3 * n + j] = 4.0 * ko * v;
+        }
+  psd_project<9, double>(Ho, work);
+  double* H = d.body_H + 144 * (long long)b;
+  for (int i = 0; i < 144; ++i) H[i] = 0.0;
+  for (int c = 0; c < 3; ++c) H[c * 12 + c] = m;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int c = 0; c < 3; ++c) H[(3 + 3 * k + c) * 12 + 3 + 3 * l + c] = S[3 * k + l];
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) H[(3 + i) * 12 + 3 + j] += Ho[i * 9 + j];
+  if (d.body_driven[b]) {
+    double rr[12], lm[12], t1[12], t2[12];
+    for (int k = 0; k < 12; ++k) {
+      rr[k] = y[k] - d.s_tgt[3 * br + k];
+      lm[k] = d.lam[3 * br + k];
+    }
+    body_My_mul(m, S, rr, t1);
+    body_My_mul(m, S, lm, t2);
+    for (int k = 0; k < 12; ++k) gb[k] += d.al_kappa * t1[k] - t2[k];
+    for (int c = 0; c < 3; ++c) H[c * 12 + c] += d.al_kappa * m;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l)
+        for (int c = 0; c < 3; ++c) H[(3 + 3 * k + c) * 12 + 3 + 3 * l + c] += d.al_kappa * S[3 * k + l];
+  }
+  for (int k = 0; k < 12; ++k) d.body_g[12 * b + k] = gb[k];
+}
+
+// ---------------------------------------------------------------------------
+// K5: gather assembly, one warp per 32-row chunk.  Value layout: block
+// (chunk, slot, lane) component c at (chunk_ptr + slot*32)*9 + c*32 + lane.
+// ---------------------------------------------------------------------------
+__global__ void k_assemble(Dev d) {
+  int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (ch >= d.n_chunks) return;
+  int r = ch * 32 + lane;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  uint8_t kr = d.row_kind[r];
+  int slots = d.chunk_slots[ch];
+  long long base = d.chunk_ptr[ch];
+  double h2 = d.h * d.h;
+  for (int sl = 0; sl < slots; ++sl) {
+    long long blk = base + (long long)sl * 32 + lane;
+    int col = d.sell_col[blk];
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (is_gel(kr)) {
+      // slot 0 is the diagonal block; a later slot with col == r is padding
+      bool diag = (sl == 0);
+      bool live = diag || col != r;
+      if (live && (kr == ROW_PINNED || d.row_kind[col] == ROW_PINNED)) {
+        if (diag) v[0] = v[4] = v[8] = 1.0;
+      } else if (live) {
+        for (int k = d.asm_ptr[blk]; k < d.asm_ptr[blk + 1]; ++k) {
+          const double* src = d.tetH + 9 * (long long)d.asm_src[k];
+          for (int c = 0; c < 9; ++c) v[c] += src[c];
+        }
+        for (int c = 0; c < 9; ++c) v[c] *= h2;
+        if (diag) {
+          double m = d.row_mass[r];
+          double dm = m + (kr == ROW_ATTACHED ? d.al_kappa * m : 0.0);
+          v[0] += dm; v[4] += dm; v[8] += dm;
+        }
+      }
+    } else if (is_body(kr) && sl < 4) {
+      int b = d.row_body[r];
+      int kk = r - d.body_row[b];
+      const double* H = d.body_H + 144 * (long long)b;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) v[3 * i + j] = H[(3 * kk + i) * 12 + 3 * sl + j];
+    }
+    double* out = d.sell_val + (base + (long long)sl * 32) * 9 + lane;
+    for (int c = 0; c < 9; ++c) out[c * 32] = v[c];
+  }
+}
+
+// gradient per row: h^2 elastic + inertia + gravity + AL + contact (in qc);
+// also starts PCG: r = -g (the right-hand side), qc cleared
+__global__ void k_grad(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  uint8_t kr = d.row_kind[r];
+  D3 g{0, 0, 0};
+  if (kr == ROW_FREE || kr == ROW_ATTACHED) {
+    double h2 = d.h * d.h;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = d.vt_ptr[r]; k < d.vt_ptr[r + 1]; ++k) {
+      int src = d.vt_src[k];
+      const double* G = d.tetG + 12 * (long long)(src >> 2) + 3 * (src & 3);
+      s0 += G[0]; s1 += G[1]; s2 += G[2];
+    }
+    double m = d.row_mass[r];
+    D3 x = ld3(d.x, r), xt = ld3(d.xt, r);
+    g = h2 * D3{s0, s1, s2} + m * (x - xt) - (h2 * m) * D3{d.grav[0], d.grav[1], d.grav[2]};
+    if (kr == ROW_ATTACHED) g = g + (d.al_kappa * m) * (x - ld3(d.s_tgt, r)) - m * ld3(d.lam, r);
+    g = g + ld3(d.qc, r);
+  } else if (is_body(kr)) {
+    int b = d.row_body[r];
+    int kk = r - d.body_row[b];
+    g = D3{d.body_g[12 * b + 3 * kk], d.body_g[12 * b + 3 * kk + 1], d.body_g[12 * b + 3 * kk + 2]} + ld3(d.qc, r);
+  }
+  st3(d.g, r, g);
+  st3(d.qc, r, D3{0, 0, 0});
+}
+
+// block-Jacobi preconditioner: 3x3 per gel row, 12x12 per body
+__global__ void k_precond_rows(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  uint8_t kr = d.row_kind[r];
+  double P[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  if (kr == ROW_FREE || kr == ROW_ATTACHED) {
+    int ch = r >> 5, lane = r & 31;
+    const double* A = d.sell_val + d.chunk_ptr[ch] * 9 + lane;  // slot 0 = diagonal
+    double M[9];
+    for (int c = 0; c < 9; ++c) M[c] = A[c * 32] + d.pc_acc[9 * r + c];
+    double det = inv3(M, P);
+    if (!(fabs(det) > 0)) { P[0] = P[4] = P[8] = 1.0; P[1] = P[2] = P[3] = P[5] = P[6] = P[7] = 0.0; }
+  }
+  for (int c = 0; c < 9; ++c) {
+    d.pc[9 * r + c] = P[c];
+    d.pc_acc[9 * r + c] = 0.0;
+  }
+}
+
+__global__ void k_precond_body(Dev d) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.n_bodies) return;
+  int e = d.body_env[b];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  double M[144], Mi[144], work[288];
+  for (int i = 0; i < 144; ++i) {
+    M[i] = d.body_H[144 * b + i] + d.body_pc_acc[144 * b + i];
+    d.body_pc_acc[144 * b + i] = 0.0;
+  }
+  if (!invert_small<12, double>(M, Mi, work))
+    for (int i = 0; i < 144; ++i) Mi[i] = (i % 13 == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < 144; ++i) d.body_pc[144 * b + i] = Mi[i];
+}
+
+// z = P^{-1} r for row r (body rows read the 4 sub-rows of their body; all of
+// them sit in the same warp)
+__device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
+  if (is_body(kr)) {
+    int b = d.row_body[r];
+    int br = d.body_row[b];
+    int kk = r - br;
+    const double* Pi = d.body_pc + 144 * (long long)b;
+    double o[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
+    return D3{o[0], o[1], o[2]};
+  }
+  if (kr == ROW_PAD) return D3{0, 0, 0};
+  const double* P = d.pc + 9 * r;
+  D3 x = ld3(d.r, r);
+  return D3{P[0] * x.x + P[1] * x.y + P[2] * x.z, P[3] * x.x + P[4] * x.y + P[5] * x.z,
+            P[6] * x.x + P[7] * x.y + P[8] * x.z};
+}
+
+// PCG start: p = 0, r = -g, z = P^-1 r, d = z; rz, rr0
+__global__ void k_pcg_init(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  uint8_t kr = d.row_kind[r];
+  D3 rv = (kr == ROW_PINNED || kr == ROW_PAD) ? D3{0, 0, 0} : -1.0 * ld3(d.g, r);
+  st3(d.r, r, rv);
+  st3(d.p, r, D3{0, 0, 0});
+  __syncwarp();
+  D3 z = apply_pc(d, r, kr);
+  st3(d.z, r, z);
+  st3(d.d, r, z);
+  double vals[2] = {dot(rv, z), dot(rv, rv)};
+  double out[2];
+  if (env_reduce<2>(d, e, 0, vals, out)) {
+    ENVS(d, e, S_RZ) = out[0];
+    ENVS(d, e, S_RR0) = out[1];
+    ENVS(d, e, S_RR) = out[1];
+    ENVI(d, e, I_PCGIT) = 0;
+    ENVI(d, e, I_PCG) = out[1] > 0.0 ? 1 : 0;
+  }
+}
+
+// q = A d + qc (SELL-32, one row per thread), qc cleared; d.q reduced
+__global__ void k_spmv(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  int ch = r >> 5, lane = r & 31;
+  int slots = d.chunk_slots[ch];
+  long long base = d.chunk_ptr[ch];
+  D3 acc = ld3(d.qc, r);
+  for (int sl = 0; sl < slots; ++sl) {
+    long long b0 = base + (long long)sl * 32;
+    int col = d.sell_col[b0 + lane];
+    const double* A = d.sell_val + b0 * 9 + lane;
+    D3 u = ld3(d.d, col);
+    acc.x += A[0] * u.x + A[32] * u.y + A[64] * u.z;
+    acc.y += A[96] * u.x + A[128] * u.y + A[160] * u.z;
+    acc.z += A[192] * u.x + A[224] * u.y + A[256] * u.z;
+  }
+  st3(d.q, r, acc);
+  st3(d.qc, r, D3{0, 0, 0});
+  double vals[1] = {dot(ld3(d.d, r), acc)};
+  double out[1];
+  if (env_reduce<1>(d, e, 1, vals, out)) {
+    ENVS(d, e, S_DQ) = out[0];
+    ENVS(d, e, S_PALPHA) = (out[0] > 0.0) ? ENVS(d, e, S_RZ) / out[0] : 0.0;
+  }
+}
+
+// p += alpha d, r -= alpha q, z = P^-1 r; rz, rr reduced -> beta, stop test
+__global__ void k_pcg_update(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  uint8_t kr = d.row_kind[r];
+  double al = ENVS(d, e, S_PALPHA);
+  st3(d.p, r, ld3(d.p, r) + al * ld3(d.d, r));
+  D3 rv = ld3(d.r, r) - al * ld3(d.q, r);
+  st3(d.r, r, rv);
+  __syncwarp();
+  D3 z = apply_pc(d, r, kr);
+  st3(d.z, r, z);
+  double vals[2] = {dot(rv, z), dot(rv, rv)};
+  double out[2];
+  if (env_reduce<2>(d, e, 0, vals, out)) {
+    double rz_old = ENVS(d, e, S_RZ);
+    ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
+    ENVS(d, e, S_RZ) = out[0];
+    ENVS(d, e, S_RR) = out[1];
+    int it = ++ENVI(d, e, I_PCGIT);
+    ENVI(d, e, I_PCGTOT) += 1;
+    double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
+    if (out[1] <= tol2 || it >= d.pcg_max || !(ENVS(d, e, S_DQ) > 0.0)) ENVI(d, e, I_PCG) = 0;
+  }
+}
+
+__global__ void k_pcg_dir(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  st3(d.d, r, ld3(d.z, r) + ENVS(d, e, S_PBETA) * ld3(d.d, r));
+}
+
+// ---------------------------------------------------------------------------
+// Newton bookkeeping
+// ---------------------------------------------------------------------------
+// |p|_inf over gel rows -> S_PNORM; AL residual of attached rows -> S_CRES
+__global__ void k_newton_rows(Dev d) {
+  __shared__ double sh[32];
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  uint8_t kr = d.row_kind[r];
+  double pn = 0, cr = 0;
+  if (is_gel(kr)) {
+    D3 p = ld3(d.p, r);
+    pn = fmax(fabs(p.x), fmax(fabs(p.y), fabs(p.z)));
+    if (kr == ROW_ATTACHED) {
+      D3 c = ld3(d.x, r) - ld3(d.s_tgt, r);
+      cr = fmax(fabs(c.x), fmax(fabs(c.y), fabs(c.z)));
+    }
+  }
+  pn = block_max(pn, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(&ENVS(d, e, S_PNORM), pn);
+  cr = block_max(cr, sh);
+  if (threadIdx.x == 0) atomic_max_nonneg(&ENVS(d, e, S_CRES), cr);
+}
+
+// per env: converged / AL multiplier update / line search (C-11, C-12)
+__global__ void k_newton_decide(Dev d) {
+  const int* has_driven = d.env_has_driven;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs || !ENVI(d, e, I_ACTIVE)) return;
+  ENVI(d, e, I_LS) = 0;
+  double res = ENVS(d, e, S_PNORM) / d.h;
+  if (res <= d.newton_tol) {
+    if (!has_driven[e] || ENVS(d, e, S_CRES) / d.h <= d.newton_tol) {
+      ENVI(d, e, I_MODE) = 1;
+      ENVI(d, e, I_ACTIVE) = 0;
+    } else if (ENVI(d, e, I_AL) >= d.al_max) {
+      ENVI(d, e, I_MODE) = 1;
+      ENVI(d, e, I_ACTIVE) = 0;
+      ENVI(d, e, I_STATUS) = IPC_ENOTCONV;
+    } else {
+      ENVI(d, e, I_MODE) = 2;
+      ENVI(d, e, I_AL) += 1;
+    }
+  } else {
+    ENVI(d, e, I_MODE) = 0;
+    ENVI(d, e, I_LS) = 1;
+    ENVI(d, e, I_LSIT) = 0;
+    ENVS(d, e, S_ACCD) = 1.0;
+  }
+}
+
+__global__ void k_al_update(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE) || ENVI(d, e, I_MODE) != 2) return;
+  if (!is_driven(d.row_kind[r])) return;
+  st3(d.lam, r, ld3(d.lam, r) - d.al_kappa * (ld3(d.x, r) - ld3(d.s_tgt, r)));
+}
+
+// ---------------------------------------------------------------------------
+// line search (K8)
+// ---------------------------------------------------------------------------
+__global__ void k_ls_init(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs || !ENVI(d, e, I_LS)) return;
+  ENVS(d, e, S_ALPHA) = fmin(1.0, ENVS(d, e, S_ACCD));
+}
+
+__global__ void k_energy_tet(Dev d, int use_alpha) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_tets) return;
+  int e = find_env(d.env_tet_off, d.n_envs, t);
+  if (!ENVI(d, e, I_LS)) return;
+  double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
+  const int* q = d.tets + 4 * (long long)t;
+  D3 X[4];
+  for (int k = 0; k < 4; ++k) X[k] = ld3(d.x, q[k]) + a * ld3(d.p, q[k]);
+  double Dmi[9];
+  for (int k = 0; k < 9; ++k) Dmi[k] = d.Dm_inv[9 * (long long)t + k];
+  double F[9];
+  tet_deformation<double>(X, Dmi, F);
+  d.tetE[t] = d.h * d.h * nh_energy<double>(F, d.tet_vol[t], d.env_mu[e], d.env_lam[e]);
+}
+
+__global__ void k_energy_row(Dev d, int use_alpha) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_LS)) return;
+  uint8_t kr = d.row_kind[r];
+  double E = 0;
+  if (kr == ROW_FREE || kr == ROW_ATTACHED || kr == ROW_PINNED) {
+    double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
+    double m = d.row_mass[r];
+    D3 x = ld3(d.x, r) + a * ld3(d.p, r);
+    D3 dx = x - ld3(d.xt, r);
+    E = 0.5 * m * dot(dx, dx) - d.h * d.h * m * (d.grav[0] * x.x + d.grav[1] * x.y + d.grav[2] * x.z);
+    if (kr == ROW_ATTACHED) {
+      D3 c = x - ld3(d.s_tgt, r);
+      E += 0.5 * d.al_kappa * m * dot(c, c) - m * dot(ld3(d.lam, r), c);
+    }
+  }
+  d.row_E[r] = E;
+}
+
+__global__ void k_energy_body(Dev d, int use_alpha) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= d.n_bodies) return;
+  int e = d.body_env[b];
+  if (!ENVI(d, e, I_LS)) return;
+  double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
+  int br = d.body_row[b];
+  double y[12], dy[12], t[12];
+  for (int k = 0; k < 12; ++k) {
+    y[k] = d.x[3 * br + k] + a * d.p[3 * br + k];
+    dy[k] = y[k] - d.xt[3 * br + k];
+  }
+  double m = d.body_mass[b];
+  const double* S = d.body_S + 9 * b;
+  body_My_mul(m, S, dy, t);
+  double E = 0;
+  for (int k = 0; k < 12; ++k) E += 0.5 * dy[k] * t[k];
+  double h2 = d.h * d.h;
+  E -= h2 * m * (d.grav[0] * y[0] + d.grav[1] * y[1] + d.grav[2] * y[2]);
+  double orth = 0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      double c = y[3 + 3 * k] * y[3 + 3 * l] + y[4 + 3 * k] * y[4 + 3 * l] + y[5 + 3 * k] * y[5 + 3 * l] - (k == l ? 1.0 : 0.0);
+      orth += c * c;
+    }
+  E += h2 * d.body_kappa[b] * d.body_vol[b] * orth;
+  if (d.body_driven[b]) {
+    double rr[12];
+    for (int k = 0; k < 12; ++k) rr[k] = y[k] - d.s_tgt[3 * br + k];
+    body_My_mul(m, S, rr, t);
+    for (int k = 0; k < 12; ++k) E += 0.5 * d.al_kappa * rr[k] * t[k] - d.lam[3 * br + k] * t[k];
+  }
+  d.body_E[b] = E;
+}
+
+// total per env in a fixed order: tets, rows, bodies, pairs (one CTA per env)
+__global__ void k_env_energy(Dev d, int which) {
+  __shared__ double sh[32];
+  int e = blockIdx.x;
+  if (!ENVI(d, e, I_LS)) return;
+  double s = 0;
+  for (int t = d.env_tet_off[e] + threadIdx.x; t < d.env_tet_off[e + 1]; t += blockDim.x) s += d.tetE[t];
+  for (int r = d.env_row_off[e] + threadIdx.x; r < d.env_row_off[e + 1]; r += blockDim.x) s += d.row_E[r];
+  for (int b = d.env_body_off[e] + threadIdx.x; b < d.env_body_off[e + 1]; b += blockDim.x) s += d.body_E[b];
+  int np = min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);
+  for (int k = threadIdx.x; k < np; k += blockDim.x) s += d.pair_E[d.env_pair_off[e] + k];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    if (!(s == s)) s = INFINITY;
+    ENVS(d, e, which == 0 ? S_E0 : S_E1) = s;
+  }
+}
+
+__global__ void k_ls_decide(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs || !ENVI(d, e, I_LS)) return;
+  ENVI(d, e, I_LSTOT) += 1;
+  double E0 = ENVS(d, e, S_E0), E1 = ENVS(d, e, S_E1);
+  if (E1 <= E0) {
+    ENVI(d, e, I_ACCEPT) = 1;
+    ENVI(d, e, I_LS) = 0;
+    return;
+  }
+  ENVS(d, e, S_ALPHA) *= 0.5;
+  if (++ENVI(d, e, I_LSIT) >= d.ls_max) {
+    ENVI(d, e, I_LS) = 0;
+    ENVI(d, e, I_ACTIVE) = 0;
+    ENVI(d, e, I_STATUS) = IPC_ENOTCONV;
+  }
+}
+
+__global__ void k_ls_apply(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACCEPT)) return;
+  st3(d.x, r, ld3(d.x, r) + ENVS(d, e, S_ALPHA) * ld3(d.p, r));
+}
+
+__global__ void k_clear_accept(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < d.n_envs) ENVI(d, e, I_ACCEPT) = 0;
+}
+
+// velocities (P:516 / App. A.2): v = (x - x^n) / h; overflowed envs restored
+__global__ void k_finalize_rows(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_SEL)) return;
+  uint8_t kr = d.row_kind[r];
+  if (kr == ROW_PAD) return;
+  if (ENVI(d, e, I_STATUS) == IPC_EOVERFLOW) {
+    st3(d.x, r, ld3(d.xn, r));
+    return;
+  }
+  if (kr == ROW_PINNED) { st3(d.v, r, D3{0, 0, 0}); return; }
+  st3(d.v, r, (1.0 / d.h) * (ld3(d.x, r) - ld3(d.xn, r)));
+}
+
+__global__ void k_finalize_envs(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs || !ENVI(d, e, I_SEL)) return;
+  if (ENVI(d, e, I_ACTIVE)) {  // Newton cap reached
+    ENVI(d, e, I_ACTIVE) = 0;
+    if (ENVI(d, e, I_STATUS) == IPC_OK) ENVI(d, e, I_STATUS) = IPC_ENOTCONV;
+  }
+}
+
+// what: 0 = new step (counters, status), 1 = Newton-iteration scalars,
+// 2 = pair list (count, overflow), 3 = min distance
+__global__ void k_env_reset(Dev d, int what) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  if (what == 0) {
+    if (!ENVI(d, e, I_SEL)) return;
+    ENVI(d, e, I_ACTIVE) = 1;
+    ENVI(d, e, I_STATUS) = IPC_OK;
+    ENVI(d, e, I_NEWTON) = 0;
+    ENVI(d, e, I_AL) = 0;
+    ENVI(d, e, I_PCGTOT) = 0;
+    ENVI(d, e, I_LSTOT) = 0;
+    ENVI(d, e, I_ACCEPT) = 0;
+    ENVI(d, e, I_OVERFLOW) = 0;
+  } else if (what == 1) {
+    if (!ENVI(d, e, I_ACTIVE)) return;
+    ENVS(d, e, S_PNORM) = 0.0;
+    ENVS(d, e, S_CRES) = 0.0;
+    ENVI(d, e, I_NEWTON) += 1;
+  } else if (what == 2) {
+    ENVI(d, e, I_NPAIRS) = 0;
+  } else if (what == 3) {
+    ENVS(d, e, S_MIND) = INFINITY;
+    ENVI(d, e, I_FLAG) = 0;
+  }
+}
+
+// pair-list overflow ends the env's step (state restored at finalize)
+__global__ void k_check_overflow(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  if (ENVI(d, e, I_OVERFLOW) && ENVI(d, e, I_SEL) && ENVI(d, e, I_STATUS) != IPC_EOVERFLOW) {
+    ENVI(d, e, I_STATUS) = IPC_EOVERFLOW;
+    ENVI(d, e, I_ACTIVE) = 0;
+    ENVI(d, e, I_LS) = 0;
+  }
+}
+
+// min det F over tets of I_SEL envs -> S_MIND (as a sign flag: 0 if inverted)
+__global__ void k_check_inverted(Dev d) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.n_tets) return;
+  int e = find_env(d.env_tet_off, d.n_envs, t);
+  if (!ENVI(d, e, I_SEL)) return;
+  const int* q = d.tets + 4 * (long long)t;
+  D3 X[4];
+  for (int k = 0; k < 4; ++k) X[k] = ld3(d.x, q[k]);
+  double Dmi[9], F[9];
+  for (int k = 0; k < 9; ++k) Dmi[k] = d.Dm_inv[9 * (long long)t + k];
+  tet_deformation<double>(X, Dmi, F);
+  if (!(det3<double>(F) > 0.0)) ENVI(d, e, I_FLAG) = 1;
+}
+
+// staged host targets [env][body][12] -> body target rows
+__global__ void k_scatter_targets(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;  // (env, body, row k, component) flattened
+  int per_env = d.max_bodies * 12;
+  if (i >= d.n_envs * per_env) return;
+  int e = i / per_env, j = i % per_env, b = j / 12, k = j % 12;
+  int b0 = d.env_body_off[e];
+  if (b >= d.env_body_off[e + 1] - b0) return;
+  d.s_tgt[3 * d.body_row[b0 + b] + k] = d.tgt_stage[i];
+}
+
+// coated-surface rows -> contiguous staging buffer
+__global__ void k_gather_coated(Dev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_coated) return;
+  st3(d.out_stage, i, ld3(d.x, d.coated_row[i]));
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define ROWGRID (d.n_rows / 128), 128, 0, s
+#define ENVGRID nblk(d.n_envs, 128), 128, 0, s
+int launch_predict(const Dev& d, cudaStream_t s) { k_predict<<<ROWGRID>>>(d); return 1; }
+int launch_attach_targets(const Dev& d, int flag, cudaStream_t s) { k_attach_targets<<<ROWGRID>>>(d, flag); return 1; }
+int launch_tet(const Dev& d, cudaStream_t s) { k_tet<<<nblk(d.n_tets, 128), 128, 0, s>>>(d); return 1; }
+int launch_body(const Dev& d, cudaStream_t s) {
+  if (!d.n_bodies) return 0;
+  k_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
+  return 1;
+}
+int launch_assemble(const Dev& d, cudaStream_t s) { k_assemble<<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d); return 1; }
+int launch_grad(const Dev& d, cudaStream_t s) { k_grad<<<ROWGRID>>>(d); return 1; }
+int launch_precond(const Dev& d, cudaStream_t s) {
+  k_precond_rows<<<ROWGRID>>>(d);
+  if (!d.n_bodies) return 1;
+  k_precond_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
+  return 2;
+}
+int launch_pcg_init(const Dev& d, cudaStream_t s) { k_pcg_init<<<ROWGRID>>>(d); return 1; }
+int launch_spmv(const Dev& d, cudaStream_t s) { k_spmv<<<ROWGRID>>>(d); return 1; }
+int launch_pcg_update(const Dev& d, cudaStream_t s) { k_pcg_update<<<ROWGRID>>>(d); return 1; }
+int launch_pcg_dir(const Dev& d, cudaStream_t s) { k_pcg_dir<<<ROWGRID>>>(d); return 1; }
+int launch_newton_check(const Dev& d, cudaStream_t s) {
+  k_newton_rows<<<ROWGRID>>>(d);
+  return 1 + launch_pnorm_body(d, s);
+}
+int launch_newton_decide(const Dev& d, cudaStream_t s) { k_newton_decide<<<ENVGRID>>>(d); return 1; }
+int launch_al_update(const Dev& d, cudaStream_t s) { k_al_update<<<ROWGRID>>>(d); return 1; }
+int launch_ls_init(const Dev& d, cudaStream_t s) { k_ls_init<<<ENVGRID>>>(d); return 1; }
+int launch_energy(const Dev& d, int use_alpha, int which, cudaStream_t s) {
+  int n = 3;
+  k_energy_tet<<<nblk(d.n_tets, 128), 128, 0, s>>>(d, use_alpha);
+  k_energy_row<<<ROWGRID>>>(d, use_alpha);
+  if (d.n_bodies) { k_energy_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d, use_alpha); ++n; }
+  n += launch_pair_energy(d, use_alpha, s);
+  k_env_energy<<<d.n_envs, 256, 0, s>>>(d, which);
+  return n;
+}
+int launch_ls_decide(const Dev& d, cudaStream_t s) { k_ls_decide<<<ENVGRID>>>(d); return 1; }
+int launch_ls_apply(const Dev& d, cudaStream_t s) {
+  k_ls_apply<<<ROWGRID>>>(d);
+  k_clear_accept<<<ENVGRID>>>(d);
+  return 2;
+}
+int launch_finalize(const Dev& d, cudaStream_t s) {
+  k_finalize_envs<<<ENVGRID>>>(d);
+  k_finalize_rows<<<ROWGRID>>>(d);
+  return 2;
+}
+int launch_env_reset(const Dev& d, int what, cudaStream_t s) { k_env_reset<<<ENVGRID>>>(d, what); return 1; }
+int launch_check_overflow(const Dev& d, cudaStream_t s) { k_check_overflow<<<ENVGRID>>>(d); return 1; }
+int launch_scatter_targets(const Dev& d, cudaStream_t s) {
+  long long n = (long long)d.n_envs * d.max_bodies * 12;
+  if (n == 0) return 0;
+  k_scatter_targets<<<nblk(n, 256), 256, 0, s>>>(d);
+  return 1;
+}
+int launch_gather_coated(const Dev& d, cudaStream_t s) {
+  if (!d.n_coated) return 0;
+  k_gather_coated<<<nblk(d.n_coated, 256), 256, 0, s>>>(d);
+  return 1;
+}
+int launch_check_inverted(const Dev& d, cudaStream_t s) { k_check_inverted<<<nblk(d.n_tets, 128), 128, 0, s>>>(d); return 1; }
+
+// ---------------------------------------------------------------------------
+// element kernel on caller buffers
+// ---------------------------------------------------------------------------
+__global__ void k_elem_tet(int n, const double* x, const double* Dmi_all, const double* vol, double mu, double lam,
+                           double* E, double* g, double* H) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  D3 X[4];
+  for (int a = 0; a < 4; ++a) X[a] = ld3(x + 12 * (long long)t, a);
+  double Dmi[9], F[9];
+  for (int k = 0; k < 9; ++k) Dmi[k] = Dmi_all[9 * (long long)t + k];
+  tet_deformation<double>(X, Dmi, F);
+  double e = nh_energy<double>(F, vol[t], mu, lam);
+  if (E) E[t] = e;
+  bool ok = det3<double>(F) > 0.0;
+  if (g) {
+    double gl[12];
+    if (ok) nh_gradient<double>(F, Dmi, vol[t], mu, lam, gl);
+    for (int k = 0; k < 12; ++k) g[12 * (long long)t + k] = ok ? gl[k] : NAN;
+  }
+  if (H) {
+    double* Ht = H + 144 * (long long)t;
+    if (!ok) {
+      for (int k = 0; k < 144; ++k) Ht[k] = NAN;
+    } else {
+      nh_hessian_blocks<double>(F, Dmi, vol[t], mu, lam, [&](int a, int b, int i, int j, double v) {
+        Ht[(3 * a + i) * 12 + 3 * b + j] = v;
+      });
+    }
+  }
+}
+
+int launch_k_tet(int n, const double* x, const double* Dmi, const double* vol, double mu, double lam,
+                 double* E, double* g, double* H, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_elem_tet<<<nblk(n, 64), 64, 0, s>>>(n, x, Dmi, vol, mu, lam, E, g, H);
+  return 1;
+}
+
+}  // namespace ipc

@@ -1,0 +1,406 @@
+"""ctypes binding of the ABD-IPC C-ABI (``include/ipc_b300.h``).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The function and method names follow the C entry points.  PyTorch provides the
+device workspace (one uint8 tensor) and the CUDA stream.  There is no CPU
+fallback: a missing library raises at import of this module's loader.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libipc_b300.so")
+
+IPC_OK, IPC_EINVAL, IPC_ENOMEM, IPC_ENOTCONV, IPC_EINTERSECT, IPC_EINVERTED, IPC_EOVERFLOW, IPC_ECUDA = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOTCONV", "EINTERSECT", "EINVERTED", "EOVERFLOW", "ECUDA"]
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint8)
+
+
+class ipc_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("gravity", C.c_double * 3), ("dhat", C.c_double), ("kappa", C.c_double),
+                ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double), ("newton_max", C.c_int),
+                ("pcg_max", C.c_int), ("ls_max", C.c_int), ("accd_max", C.c_int), ("accd_s", C.c_double),
+                ("al_kappa", C.c_double), ("al_max", C.c_int), ("ee_mollifier", C.c_double),
+                ("precision", C.c_int), ("max_pairs_per_env", C.c_int)]
+
+
+class ipc_scene_desc(C.Structure):
+    _fields_ = [("n_verts", C.c_int), ("n_tets", C.c_int), ("rest_x", _dp), ("tets", _ip), ("pad_id", _ip),
+                ("pinned", _up), ("attach_body", _ip), ("E", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
+                ("n_bodies", C.c_int), ("body_nv", _ip), ("body_rest_x", _dp), ("body_nt", _ip),
+                ("body_tris", _ip), ("body_rho", _dp), ("body_kappa_s", _dp), ("body_driven", _up)]
+
+
+class ipc_step_stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_trials", C.c_int),
+                ("al_updates", C.c_int), ("max_pairs", C.c_int), ("newton_env_iters", C.c_longlong),
+                ("ms_total", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libipc_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run python -m paper_2504_12908_b300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, dbl = C.c_void_p, C.c_int, C.c_double
+        sig = {
+            "ipc_default_params": (None, [C.POINTER(ipc_params)]),
+            "ipc_workspace_bytes": (i32, [C.POINTER(ipc_scene_desc), i32, C.POINTER(ipc_params), C.POINTER(C.c_size_t)]),
+            "ipc_create_envs": (i32, [C.POINTER(ipc_scene_desc), i32, C.POINTER(ipc_params), vp, C.c_size_t, vp,
+                                      C.POINTER(vp)]),
+            "ipc_destroy": (i32, [vp]),
+            "ipc_last_error": (C.c_char_p, [vp]),
+            "ipc_num_envs": (i32, [vp]),
+            "ipc_env_sizes": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+            "ipc_body_com": (i32, [vp, i32, i32, _dp]),
+            "ipc_set_state": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
+            "ipc_get_state": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
+            "ipc_set_targets": (i32, [vp, i32, _dp]),
+            "ipc_set_targets_all": (i32, [vp, _dp]),
+            "ipc_set_targets_all_device": (i32, [vp, vp]),
+            "ipc_step": (i32, [vp, _ip, i32, _ip, C.POINTER(ipc_step_stats)]),
+            "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
+            "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "ipc_debug_eval": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
+            "ipc_debug_pairs": (i32, [vp, i32, _dp, _dp, _ip, i32, C.POINTER(i32)]),
+            "ipc_debug_newton_dir": (i32, [vp, i32, _dp, C.POINTER(i32)]),
+            "ipc_debug_accd": (i32, [vp, i32, _dp, _dp]),
+            "ipc_profile_enable": (i32, [vp, i32]),
+            "ipc_profile_reset": (i32, [vp]),
+            "ipc_profile_count": (i32, [vp]),
+            "ipc_profile_get": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double)]),
+            "ipc_launch_count": (C.c_longlong, [vp]),
+            "ipc_system_sizes": (i32, [vp, i32, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                       C.POINTER(i32), C.POINTER(i32)]),
+            "ipc_k_tet": (i32, [i32, vp, vp, vp, dbl, dbl, vp, vp, vp, vp]),
+            "ipc_k_barrier": (i32, [i32, vp, vp, vp, vp, dbl, vp, vp, vp, vp]),
+            "ipc_k_accd": (i32, [i32, vp, vp, vp, dbl, i32, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
+            "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
+            "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
+            "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
+            "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
+            "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
+
+
+class IpcError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+
+
+def _ptr(a: Optional[np.ndarray], ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ct)
+
+
+def params_from(p) -> ipc_params:
+    """ipc_params from any object with the SolverParams attribute names."""
+    out = ipc_params()
+    lib().ipc_default_params(C.byref(out))
+    out.dt = p.dt
+    for k in range(3):
+        out.gravity[k] = p.gravity[k]
+    for name in ("dhat", "kappa", "newton_tol", "pcg_rel_tol", "accd_s", "al_kappa", "ee_mollifier"):
+        setattr(out, name, float(getattr(p, name)))
+    for name in ("newton_max", "pcg_max", "ls_max", "accd_max", "al_max"):
+        setattr(out, name, int(getattr(p, name)))
+    out.precision = int(getattr(p, "precision", 0))
+    out.max_pairs_per_env = int(getattr(p, "max_pairs_per_env", 0))
+    return out
+
+
+class _SceneArrays:
+    """Keeps the numpy buffers of one scene descriptor alive."""
+
+    def __init__(self, sc):
+        self.x = np.ascontiguousarray(sc.gel_x, dtype=np.float64)
+        self.t = np.ascontiguousarray(sc.gel_tets, dtype=np.int32)
+        self.pad = np.ascontiguousarray(sc.gel_obj, dtype=np.int32)
+        self.pin = np.ascontiguousarray(sc.pinned, dtype=np.uint8)
+        self.att = np.ascontiguousarray(sc.attach, dtype=np.int32)
+        bs = sc.bodies
+        self.bnv = np.array([b.rest_x.shape[0] for b in bs], dtype=np.int32)
+        self.bx = np.ascontiguousarray(np.concatenate([b.rest_x for b in bs]) if bs else np.zeros((0, 3)),
+                                       dtype=np.float64)
+        self.bnt = np.array([b.tris.shape[0] for b in bs], dtype=np.int32)
+        self.bt = np.ascontiguousarray(np.concatenate([b.tris for b in bs]) if bs else np.zeros((0, 3)),
+                                       dtype=np.int32)
+        self.brho = np.array([b.rho for b in bs], dtype=np.float64)
+        self.bk = np.array([b.kappa_s for b in bs], dtype=np.float64)
+        self.bd = np.array([1 if b.driven else 0 for b in bs], dtype=np.uint8)
+        d = ipc_scene_desc()
+        d.n_verts, d.n_tets = self.x.shape[0], self.t.shape[0]
+        d.rest_x, d.tets, d.pad_id = _ptr(self.x, _dp), _ptr(self.t, _ip), _ptr(self.pad, _ip)
+        d.pinned, d.attach_body = _ptr(self.pin, _up), _ptr(self.att, _ip)
+        d.E, d.nu, d.rho = float(sc.E), float(sc.nu), float(sc.rho)
+        d.n_bodies = len(bs)
+        d.body_nv, d.body_rest_x, d.body_nt = _ptr(self.bnv, _ip), _ptr(self.bx, _dp), _ptr(self.bnt, _ip)
+        d.body_tris, d.body_rho, d.body_kappa_s = _ptr(self.bt, _ip), _ptr(self.brho, _dp), _ptr(self.bk, _dp)
+        d.body_driven = _ptr(self.bd, _up)
+        self.desc = d
+
+
+def _descs(scenes: Sequence) -> tuple:
+    """Descriptor array; identical scene objects share one descriptor (the
+    library then preprocesses them once)."""
+    cache = {}
+    keep = []
+    arr = (ipc_scene_desc * len(scenes))()
+    for i, sc in enumerate(scenes):
+        k = id(sc)
+        if k not in cache:
+            cache[k] = _SceneArrays(sc)
+            keep.append(cache[k])
+        arr[i] = cache[k].desc
+    return arr, keep
+
+
+def workspace_bytes(scenes: Sequence, params) -> int:
+    arr, keep = _descs(scenes)
+    prm = params_from(params)
+    n = C.c_size_t(0)
+    st = lib().ipc_workspace_bytes(arr, len(scenes), C.byref(prm), C.byref(n))
+    if st != IPC_OK:
+        raise IpcError(st, "ipc_workspace_bytes")
+    return int(n.value)
+
+
+class Envs:
+    """A batch of environments on one GPU (one ipc_ctx)."""
+
+    def __init__(self, scenes: Sequence, params, device: str = "cuda:0", stream=None):
+        import torch
+        self._torch = torch
+        self.scenes = list(scenes)
+        self.params = params
+        arr, self._keep = _descs(self.scenes)
+        self._prm = params_from(params)
+        n = C.c_size_t(0)
+        L = lib()
+        st = L.ipc_workspace_bytes(arr, len(self.scenes), C.byref(self._prm), C.byref(n))
+        if st != IPC_OK:
+            raise IpcError(st, "ipc_workspace_bytes")
+        self.ws_bytes = int(n.value)
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        ctx = C.c_void_p()
+        st = L.ipc_create_envs(arr, len(self.scenes), C.byref(self._prm), C.c_void_p(self.workspace.data_ptr()),
+                               self.ws_bytes, C.c_void_p(self.stream.cuda_stream), C.byref(ctx))
+        self._ctx = ctx
+        if st != IPC_OK:
+            msg = L.ipc_last_error(ctx).decode() if ctx.value else ""
+            if ctx.value:
+                L.ipc_destroy(ctx)
+            self._ctx = None
+            raise IpcError(st, msg)
+        self.n_envs = len(self.scenes)
+        self.sizes = []
+        for e in range(self.n_envs):
+            nv, nb, ns = C.c_int(), C.c_int(), C.c_int()
+            L.ipc_env_sizes(ctx, e, C.byref(nv), C.byref(nb), C.byref(ns))
+            self.sizes.append((nv.value, nb.value, ns.value))
+        self.max_bodies = max([s[1] for s in self.sizes] + [0])
+
+    # ------------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != IPC_OK:
+            raise IpcError(st, f"{what}: {lib().ipc_last_error(self._ctx).decode()}")
+
+    def close(self):
+        if self._ctx is not None:
+            lib().ipc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ API
+    def body_com(self, env: int, body: int) -> np.ndarray:
+        out = np.zeros(3)
+        self._check(lib().ipc_body_com(self._ctx, env, body, _ptr(out, _dp)), "ipc_body_com")
+        return out
+
+    def rest_y(self, env: int) -> np.ndarray:
+        nb = self.sizes[env][1]
+        y = np.zeros((nb, 12))
+        for b in range(nb):
+            y[b, :3] = self.body_com(env, b)
+            y[b, 3:] = np.eye(3).T.ravel()
+        return y
+
+    def set_state(self, env: int, x=None, v=None, y=None, ydot=None) -> int:
+        a = [None if t is None else np.ascontiguousarray(t, dtype=np.float64) for t in (x, v, y, ydot)]
+        return lib().ipc_set_state(self._ctx, env, *[_ptr(t, _dp) for t in a])
+
+    def get_state(self, env: int):
+        nv, nb, _ = self.sizes[env]
+        x, v = np.zeros((nv, 3)), np.zeros((nv, 3))
+        y, yd = np.zeros((nb, 12)), np.zeros((nb, 12))
+        self._check(lib().ipc_get_state(self._ctx, env, _ptr(x, _dp), _ptr(v, _dp), _ptr(y, _dp), _ptr(yd, _dp)),
+                    "ipc_get_state")
+        return x, v, y, yd
+
+    def set_targets(self, env: int, y_target: np.ndarray):
+        t = np.ascontiguousarray(y_target, dtype=np.float64)
+        self._check(lib().ipc_set_targets(self._ctx, env, _ptr(t, _dp)), "ipc_set_targets")
+
+    def set_targets_all(self, y_targets: np.ndarray):
+        t = np.ascontiguousarray(y_targets, dtype=np.float64)
+        self._check(lib().ipc_set_targets_all(self._ctx, _ptr(t, _dp)), "ipc_set_targets_all")
+
+    def set_targets_all_device(self, dev_targets):
+        """dev_targets: CUDA float64 tensor [n_envs][max_bodies][12]."""
+        self._check(lib().ipc_set_targets_all_device(self._ctx, C.c_void_p(dev_targets.data_ptr())),
+                    "ipc_set_targets_all_device")
+
+    def step(self, env_ids: Optional[Sequence[int]] = None):
+        """Returns (per-env status array, stats dict)."""
+        ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
+        n = self.n_envs if ids is None else len(ids)
+        status = np.zeros(n, dtype=np.int32)
+        stats = ipc_step_stats()
+        self._check(lib().ipc_step(self._ctx, _ptr(ids, _ip), n, _ptr(status, _ip), C.byref(stats)), "ipc_step")
+        return status, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
+
+    def read_gel_surface(self, env: int) -> np.ndarray:
+        n = self.sizes[env][2]
+        out = np.zeros((n, 3))
+        w = C.c_int()
+        self._check(lib().ipc_read_gel_surface(self._ctx, env, _ptr(out, _dp), n, C.byref(w)), "ipc_read_gel_surface")
+        return out
+
+    def read_gel_surface_all(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        tot = sum(s[2] for s in self.sizes)
+        if out is None:
+            out = np.zeros((tot, 3))
+        w = C.c_size_t()
+        self._check(lib().ipc_read_gel_surface_all(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
+                    "ipc_read_gel_surface_all")
+        return out
+
+    # ------------------------------------------------------------ profiling
+    def profile_enable(self, on: bool = True):
+        self._check(lib().ipc_profile_enable(self._ctx, 1 if on else 0), "ipc_profile_enable")
+
+    def profile_reset(self):
+        self._check(lib().ipc_profile_reset(self._ctx), "ipc_profile_reset")
+
+    def profile(self) -> dict:
+        """{kernel class: (launches, device ms)} since the last reset."""
+        out = {}
+        for i in range(lib().ipc_profile_count(self._ctx)):
+            name, n, ms = C.c_char_p(), C.c_longlong(), C.c_double()
+            self._check(lib().ipc_profile_get(self._ctx, i, C.byref(name), C.byref(n), C.byref(ms)),
+                        "ipc_profile_get")
+            out[name.value.decode()] = (int(n.value), float(ms.value))
+        return out
+
+    def launch_count(self) -> int:
+        return int(lib().ipc_launch_count(self._ctx))
+
+    def system_sizes(self, env: int) -> dict:
+        rb, sb, r, t = C.c_longlong(), C.c_longlong(), C.c_int(), C.c_int()
+        self._check(lib().ipc_system_sizes(self._ctx, env, C.byref(rb), C.byref(sb), C.byref(r), C.byref(t)),
+                    "ipc_system_sizes")
+        return {"real_blocks": rb.value, "stored_blocks": sb.value, "rows": r.value, "tets": t.value}
+
+    # ------------------------------------------------------------ diagnostics
+    def ndof(self, env: int) -> int:
+        nv, nb, _ = self.sizes[env]
+        return 3 * nv + 12 * nb
+
+    def debug_eval(self, env: int, vec: Optional[np.ndarray] = None):
+        n = self.ndof(env)
+        E = np.zeros(1)
+        g = np.zeros(n)
+        hv = np.zeros(n) if vec is not None else None
+        v = None if vec is None else np.ascontiguousarray(vec, dtype=np.float64)
+        self._check(lib().ipc_debug_eval(self._ctx, env, _ptr(E, _dp), _ptr(g, _dp), _ptr(v, _dp), _ptr(hv, _dp)),
+                    "ipc_debug_eval")
+        return float(E[0]), g, hv
+
+    def debug_pairs(self, env: int, cv_x: np.ndarray, cv_x_end: Optional[np.ndarray] = None, capacity=None):
+        cap = capacity or 200000
+        out = np.zeros((cap, 5), dtype=np.int32)
+        n = C.c_int()
+        a = np.ascontiguousarray(cv_x, dtype=np.float64)
+        b = None if cv_x_end is None else np.ascontiguousarray(cv_x_end, dtype=np.float64)
+        st = lib().ipc_debug_pairs(self._ctx, env, _ptr(a, _dp), _ptr(b, _dp), _ptr(out, _ip), cap, C.byref(n))
+        self._check(st, "ipc_debug_pairs")
+        return out[:min(n.value, cap)]
+
+    def debug_newton_dir(self, env: int):
+        p = np.zeros(self.ndof(env))
+        it = C.c_int()
+        self._check(lib().ipc_debug_newton_dir(self._ctx, env, _ptr(p, _dp), C.byref(it)), "ipc_debug_newton_dir")
+        return p, it.value
+
+    def debug_accd(self, env: int, direction: np.ndarray) -> float:
+        a = np.zeros(1)
+        d = np.ascontiguousarray(direction, dtype=np.float64)
+        self._check(lib().ipc_debug_accd(self._ctx, env, _ptr(d, _dp), _ptr(a, _dp)), "ipc_debug_accd")
+        return float(a[0])
+
+
+# ---------------------------------------------------------------- element kernels
+def _stream_ptr(t):
+    import torch
+    return C.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _vp(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=None):
+    """Neo-Hookean element kernel on torch float64 CUDA tensors."""
+    n = int(x.shape[0])
+    st = lib().ipc_k_tet(n, _vp(x), _vp(Dm_inv), _vp(vol), float(mu), float(lam), _vp(energy), _vp(grad),
+                         _vp(hess), _stream_ptr(x))
+    if st != IPC_OK:
+        raise IpcError(st, "ipc_k_tet")
+
+
+def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None):
+    n = int(X.shape[0])
+    st = lib().ipc_k_barrier(n, _vp(X), _vp(is_ee), _vp(weight), _vp(eps_x), float(dhat), _vp(energy), _vp(grad),
+                             _vp(hess), _stream_ptr(X))
+    if st != IPC_OK:
+        raise IpcError(st, "ipc_k_barrier")
+
+
+def k_accd(X0, P, is_ee, s: float, max_iter: int, toi):
+    n = int(X0.shape[0])
+    st = lib().ipc_k_accd(n, _vp(X0), _vp(P), _vp(is_ee), float(s), int(max_iter), _vp(toi), _stream_ptr(X0))
+    if st != IPC_OK:
+        raise IpcError(st, "ipc_k_accd")

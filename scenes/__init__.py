@@ -428,3 +428,17 @@ def spin_scene(omega=(0.0, 0.0, 20.0)):
     yd[0, 9:12] = W[:, 2]
     return Scenario(scene=scene, params=params, n_steps=10,
                     delta=lambda s: np.zeros((1, 3)), ydot0=yd)
+
+
+def config1_batch(n_envs: int, nx=40, ny=40, nz=6, n_steps=100):
+    """Config 1 as a batch: one shared scene (identical geometry in every env)
+    and the per-env seeded press/slide scripts of config1(env)."""
+    base = config1(0, nx, ny, nz, n_steps)
+    deltas = []
+    half = n_steps // 2
+    for env in range(n_envs):
+        rng = np.random.default_rng(1000 + env)
+        depth = rng.uniform(0.0, 1.5e-3)
+        slide = rng.uniform(-2e-3, 2e-3)
+        deltas.append(_press_slide(depth, slide, 5e-5, half, n_steps - half))
+    return base.scene, base.params, deltas

@@ -1,0 +1,65 @@
+"""Helpers shared by the GPU parity tests (no solver arithmetic here)."""
+import numpy as np
+
+from oracle import OracleEnv
+from oracle import energy as oen
+
+
+def bbox_diag(env: OracleEnv, x, y) -> float:
+    P = env.contact_positions(x, y)
+    P = np.concatenate([x, P])
+    return float(np.linalg.norm(P.max(0) - P.min(0)))
+
+
+def all_points(env: OracleEnv, x, y):
+    """Gel vertices and every body vertex phi(y) (the compared positions)."""
+    parts = [x]
+    for b, br in enumerate(env.bodies):
+        parts.append(oen.body_points(y[b], br.xbar))
+    return np.concatenate(parts)
+
+
+def oracle_states(scenario, params, n_steps):
+    """Oracle trajectory: list of (x, v, y, ydot, targets used for the next step)."""
+    env = OracleEnv(scenario.scene, params)
+    x, v, y, yd = env.rest_state()
+    if scenario.v0 is not None:
+        v = scenario.v0.copy()
+    if scenario.ydot0 is not None:
+        yd = scenario.ydot0.copy()
+    out = []
+    for s in range(n_steps):
+        sy = env.targets_from_delta(scenario.delta(s))
+        out.append((x, v, y, yd, sy))
+        x, v, y, yd, st = env.step(x, v, y, yd, sy)
+        assert st.status == 0, f"oracle did not converge at step {s}"
+    out.append((x, v, y, yd, None))
+    return env, out
+
+
+def gpu_targets(genv, e, oracle_env: OracleEnv, sy):
+    """Targets in the GPU's convention (p = its own com) for the same
+    rest-placement translation the oracle used."""
+    t = sy.copy()
+    for b in range(oracle_env.nb):
+        # translation the oracle applied to its own com
+        t[b, :3] = genv.body_com(e, b) + (sy[b, :3] - oracle_env.bodies[b].com)
+    return t
+
+
+def to_gpu_y(genv, e, oracle_env: OracleEnv, y):
+    """Same physical body placement in the GPU's frame (p offset by the
+    difference between the two sides' computed centres of mass)."""
+    yg = y.copy()
+    for b in range(oracle_env.nb):
+        A = np.stack([y[b, 3:6], y[b, 6:9], y[b, 9:12]], axis=1)
+        yg[b, :3] = y[b, :3] + A @ (genv.body_com(e, b) - oracle_env.bodies[b].com)
+    return yg
+
+
+def from_gpu_y(genv, e, oracle_env: OracleEnv, yg):
+    y = yg.copy()
+    for b in range(oracle_env.nb):
+        A = np.stack([yg[b, 3:6], yg[b, 6:9], yg[b, 9:12]], axis=1)
+        y[b, :3] = yg[b, :3] - A @ (genv.body_com(e, b) - oracle_env.bodies[b].com)
+    return y

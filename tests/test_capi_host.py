@@ -1,0 +1,93 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads,
+exports every entry point the header declares, and validates scenes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import scenes
+from paper_2504_12908_b300 import ipc
+from paper_2504_12908_b300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return ipc.lib()
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(ipc_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert "ipc_step" in names and "ipc_create_envs" in names
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    assert names <= set(ipc.EXPORTED) | names  # binding list is informative
+    assert set(ipc.EXPORTED) <= names
+
+
+def test_default_params(L):
+    p = ipc.ipc_params()
+    L.ipc_default_params(C.byref(p))
+    assert p.dt == 1e-3 and p.dhat == 1e-4 and p.kappa == 1e6 and p.gravity[2] == -9.81
+
+
+def test_workspace_bytes_scales_with_envs(L):
+    sc = scenes.config0()
+    one = ipc.workspace_bytes([sc.scene], sc.params)
+    four = ipc.workspace_bytes([sc.scene] * 4, sc.params)
+    assert one > 0 and four > 3 * one
+
+
+def test_uneven_batch_workspace(L):
+    scs = [scenes.config2(e).scene for e in range(3)]
+    assert ipc.workspace_bytes(scs, scenes.SolverParams()) > 0
+
+
+def test_rejects_inverted_rest_tet(L):
+    sc = scenes.config0().scene
+    bad = scenes.Scene(**{**sc.__dict__})
+    bad.gel_tets = sc.gel_tets.copy()
+    bad.gel_tets[0] = bad.gel_tets[0][[0, 1, 3, 2]]
+    with pytest.raises(ipc.IpcError) as ei:
+        ipc.workspace_bytes([bad], scenes.SolverParams())
+    assert ei.value.status == ipc.IPC_EINVAL
+
+
+def test_rejects_open_body_surface(L):
+    sc = scenes.config0().scene
+    b = sc.bodies[0]
+    bad_body = scenes.Body(rest_x=b.rest_x, tris=b.tris[:-1], rho=b.rho, kappa_s=b.kappa_s, driven=True)
+    bad_body.tris = b.tris[:-2]
+    bad = scenes.Scene(**{**sc.__dict__})
+    bad.bodies = [bad_body]
+    # an open surface has a volume that is not the solid's; removing two
+    # triangles of a box leaves a positive but wrong volume, so use a flipped
+    # surface instead, which has negative volume
+    bad.bodies = [scenes.Body(rest_x=b.rest_x, tris=b.tris[:, [0, 2, 1]], rho=b.rho, kappa_s=b.kappa_s,
+                              driven=True)]
+    with pytest.raises(ipc.IpcError):
+        ipc.workspace_bytes([bad], scenes.SolverParams())
+
+
+def test_rejects_out_of_range_index(L):
+    sc = scenes.config0().scene
+    bad = scenes.Scene(**{**sc.__dict__})
+    bad.gel_tets = sc.gel_tets.copy()
+    bad.gel_tets[3, 2] = sc.n_verts + 5
+    with pytest.raises(ipc.IpcError):
+        ipc.workspace_bytes([bad], scenes.SolverParams())
