@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s"
-WORKLOAD = "uniform batch: 256 envs x (gel 40x40x6 + ABD icosphere L2, press/slide), FP64"
+WORKLOAD = "uniform batch: 256 envs x (gel 40x40x6 + ABD icosphere L2, press/slide)"
 
 
 def parse():
@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--envs", type=int, default=256)
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=1,
+                    help="1: time FP64 then mixed (headline); 0: FP64 only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -125,31 +126,44 @@ def targets_for(envs, deltas, step, com):
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample_seconds(scene, params, delta, step_index=0):
-    """Wall time of the FP64 oracle advancing one env by one step, BLAS at 1 thread."""
-    from threadpoolctl import threadpool_limits
+_ORACLE_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import scenes
+from oracle import OracleEnv
+from oracle import distance as ods
+for k in ("PP", "PE", "PT", "EE", "X"):
+    ods._sym(k)          # symbolic set-up outside the timed sample
+scene, params, deltas = scenes.config1_batch({env} + 1)
+env = OracleEnv(scene, params)
+x, v, y, yd = env.rest_state()
+t0 = time.perf_counter()
+x, v, y, yd, st = env.step(x, v, y, yd, env.targets_from_delta(deltas[{env}]({step})))
+dt = time.perf_counter() - t0
+print(json.dumps({{"seconds": dt, "status": st.status, "newton": st.newton_iters}}))
+"""
 
-    from oracle import OracleEnv
-    from oracle import distance as ods
-    for k in ("PP", "PE", "PT", "EE", "X"):
-        ods._sym(k)   # symbolic set-up outside the timed sample
-    with threadpool_limits(1):
-        env = OracleEnv(scene, params)
-        x, v, y, yd = env.rest_state()
-        t0 = time.perf_counter()
-        x, v, y, yd, st = env.step(x, v, y, yd, env.targets_from_delta(delta(step_index)))
-        dt = time.perf_counter() - t0
-    return dt, st
+
+def oracle_sample_seconds(env_index=0, step_index=0):
+    """Wall time of the FP64 oracle advancing one env of the workload by one
+    step, in a child process with every BLAS/OpenMP pool at one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    code = _ORACLE_SAMPLE.format(root=ROOT, env=env_index, step=step_index)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["seconds"], d
 
 
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    scene, params, deltas = build_workload(args.envs, 0)
     times = []
     for k in range(args.warmup + args.steps):
-        dt, st = oracle_sample_seconds(scene, params, deltas[k % len(deltas)], 0)
+        dt, st = oracle_sample_seconds(k % args.envs, 0)
         if k >= args.warmup:
             times.append(dt)
     ms = 1e3 * float(np.mean(times))
@@ -166,46 +180,41 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ ours
 def kernel_bytes(genv, stats_tot, prof):
-    """Algorithmic bytes of the main kernel classes over the timed region."""
+    """Algorithmic bytes of the main kernel classes over the timed region
+    (what each kernel must move at minimum for the work it did)."""
     sz = genv.system_sizes(0)
     nv, nb, _ = genv.sizes[0]
     rows_real = nv + 4 * nb
-    n_envs = genv.n_envs
     T = sz["tets"]
+    hs = 4 if getattr(genv.params, "precision", 0) else 8   # Hessian / matrix value bytes
     out = {}
-    # SELL SpMV: 72 B values + 4 B column per real block; per row d, qc read,
-    # q, qc written (24 B each)
-    spmv_env_iter = sz["real_blocks"] * 76 + rows_real * 96
+    # SELL SpMV per env-iteration: 9 values + 4 B column per real block;
+    # per row d and qc read, q and qc written (FP64, 24 B each)
+    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * 96
     out["sell_spmv"] = stats_tot["pcg_iters"] * spmv_env_iter
-    # PCG update: reads p, d, r, q, P^-1 (72), writes p, r, z
+    # PCG update: reads p, d, r, q, P^-1 (9 doubles), writes p, r, z
     out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (4 * 24 + 72 + 3 * 24)
     out["pcg_dir"] = stats_tot["pcg_iters"] * rows_real * 72
-    # elastic element kernel: x of 4 vertices, Dm^-1, vol, indices; writes
-    # 12 gradient + 144 Hessian doubles
-    out["tet_elastic"] = stats_tot["newton_env_iters"] * T * (16 + 96 + 72 + 8 + 96 + 1152)
-    # assembly: reads the 16 element blocks of every tet once, writes every
-    # real block once (72 B) and reads its column (4 B)
-    out["assemble"] = stats_tot["newton_env_iters"] * (T * 16 * 72 + sz["real_blocks"] * 76)
+    # elastic element kernel: 4 indices + 4 positions + Dm^-1 + vol read,
+    # 12 FP64 gradient and 144 Hessian values written
+    out["tet_elastic"] = stats_tot["newton_env_iters"] * T * (16 + 96 + 72 + 8 + 96 + 144 * hs)
+    # assembly: every element block read once, every real block written once
+    out["assemble"] = stats_tot["newton_env_iters"] * (T * 144 * hs + sz["real_blocks"] * (9 * hs + 4))
     return out, spmv_env_iter
 
 
-def run_ours(args):
+def time_precision(args, scene, params, deltas, precision, local, world, profile=True):
+    """Warm-up + timed region for one precision mode; returns a result dict
+    and leaves the Envs open (caller closes)."""
     import torch
 
     from paper_2504_12908_b300 import ipc
-    from paper_2504_12908_b300.build import build
-
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    build()
-    scene, params, deltas = build_workload(args.envs, args.precision)
-    genv = ipc.Envs([scene] * args.envs, params, device=f"cuda:{local}")
+    prm = type(params)(**params.__dict__)
+    prm.precision = precision
+    genv = ipc.Envs([scene] * args.envs, prm, device=f"cuda:{local}")
     com = genv.body_com(0, 0)
-    n_steps_total = args.warmup + args.steps
-    dev_tg = torch.as_tensor(np.stack([targets_for(None, deltas, k, com) for k in range(n_steps_total + args.steps)]),
+    n_total = args.warmup + args.steps
+    dev_tg = torch.as_tensor(np.stack([targets_for(None, deltas, k, com) for k in range(n_total + args.steps)]),
                              dtype=torch.float64, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
 
@@ -213,14 +222,14 @@ def run_ours(args):
         genv.set_targets_all_device(dev_tg[k])
         return genv.step()
 
-    # warm-up
     for k in range(args.warmup):
-        st, _ = one_step(k)
+        one_step(k)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    genv.profile_enable(True)
-    genv.profile_reset()
+    if profile:
+        genv.profile_enable(True)
+        genv.profile_reset()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = genv.launch_count()
@@ -250,47 +259,87 @@ def run_ours(args):
         t = torch.tensor([ms_total], device=f"cuda:{local}")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_total = float(t.item())
-    prof = genv.profile()
+    prof = genv.profile() if profile else {}
     genv.profile_enable(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ok = all(np.all(s == 0) for s in statuses)
-    value = args.envs * args.steps * world / (ms_total / 1e3)
+    step_ms = [a_.elapsed_time(b_) for a_, b_ in ev]
+    n_bad = int(sum(int(np.sum(s_ != 0)) for s_ in statuses))
+    return {"genv": genv, "value": args.envs * args.steps * world / (ms_total / 1e3), "ms_total": ms_total,
+            "step_ms": step_ms, "tot": tot, "prof": prof, "clocks": clk, "launches": launches, "n_bad": n_bad,
+            "statuses": statuses, "deltas": deltas, "com": com, "n_total": n_total}
 
-    # roofline of the dominant kernel class
-    kb, spmv_env_iter = kernel_bytes(genv, tot, prof)
-    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+
+def roofline_of(genv, res):
+    kb, _ = kernel_bytes(genv, res["tot"], res["prof"])
+    prof = res["prof"]
     peak, peak_kind = measured_peaks()
+    tot_ms = max(sum(v[1] for v in prof.values()), 1e-9)
     kernels = {}
     for name, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
         if n == 0:
             continue
-        row = {"launches": n, "ms": round(ms, 3), "share": round(ms / max(sum(v[1] for v in prof.values()), 1e-9), 4)}
+        row = {"launches": n, "ms": round(ms, 3), "share": round(ms / tot_ms, 4)}
         if name in kb and ms > 0:
             row["GB/s"] = round(kb[name] / (ms / 1e3) / 1e9, 1)
         kernels[name] = row
-    if dom in kb:
-        n, ms = prof[dom]
-        achieved = kb[dom] / (ms / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
-                "bytes_per_launch": kb[dom] / max(n, 1)}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    # the roofline is reported for the dominant kernel with an HBM bound
+    hbm = [k for k in kernels if k in kb]
+    rk = dom if dom in kb else (hbm[0] if hbm else None)
+    roof = {"kernel": rk, "dominant_kernel": dom}
+    if rk is not None:
+        n, ms = prof[rk]
+        achieved = kb[rk] / (ms / 1e3) / 1e9
+        roof.update({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                     "bytes_per_launch": kb[rk] / max(n, 1), "share_of_step": kernels[rk]["share"]})
+    return roof, kernels
 
-    # e2e: host targets in pinned memory, one H2D + step + one D2H per step
+
+def run_ours(args):
+    import torch
+
+    from paper_2504_12908_b300.build import build
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build()
+    scene, params, deltas = build_workload(args.envs, 0)
+
+    # plain FP64 path (the comparison), then the mixed-precision path (headline)
+    precisions = [0] if args.precision == 0 else [0, 1]
+    results = {}
+    surf = {}
+    for prec in precisions:
+        res = time_precision(args, scene, params, deltas, prec, local, world)
+        surf[prec] = res["genv"].read_gel_surface_all()
+        results[prec] = res
+        if prec != precisions[-1]:
+            res["genv"].close()
+            torch.cuda.empty_cache()
+    head = results[precisions[-1]]
+    genv = head["genv"]
+    roof, kernels = roofline_of(genv, head)
+    rel_err = None
+    if len(precisions) == 2:
+        diag = float(np.linalg.norm(np.array([0.02, 0.02, 0.004])))
+        rel_err = float(np.abs(surf[1] - surf[0]).max() / diag)
+
+    # e2e on the headline path: pinned host targets in, coated surfaces out
     e2e = None
     if not args.no_e2e:
         mb = genv.max_bodies
         host_tg = torch.empty((args.envs, mb, 12), dtype=torch.float64, pin_memory=True)
-        n_out = sum(s[2] for s in genv.sizes)
+        n_out = sum(s_[2] for s_ in genv.sizes)
         host_out = torch.empty((n_out, 3), dtype=torch.float64, pin_memory=True)
         tg_np, out_np = host_tg.numpy(), host_out.numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.steps):
-            k = n_steps_total + i
-            tg_np[:] = targets_for(None, deltas, k, com)
+            k = head["n_total"] + i
+            tg_np[:] = targets_for(None, deltas, k, head["com"])
             genv.set_targets_all(tg_np)
             genv.step()
             genv.read_gel_surface_all(out_np)
@@ -298,30 +347,39 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         e2e = {"value": args.envs * args.steps * world / dt, "unit": METRIC,
                "h2d_bytes_per_step": int(tg_np.nbytes), "d2h_bytes_per_step": int(out_np.nbytes)}
+    genv.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, st = oracle_sample_seconds(scene, params, deltas[0], 0)
+        dt, st = oracle_sample_seconds(0, 0)
         cpu = {"value": 1.0 / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"1 env x 1 step (step 0) of the same workload, FP64 oracle, {dt:.1f} s, BLAS threads = 1"}
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f32+f64",
+        hp = precisions[-1]
+        fp = results[0]
+        out = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": head["ms_total"] / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if hp == 0 else "f32+f64",
                "data": "synthetic",
                "config": {"workload": WORKLOAD, "envs": args.envs * world, "envs_per_gpu": args.envs,
-                          "gel_vertices": 9600, "tets": 38025, "precision": "fp64" if args.precision == 0 else "mixed",
+                          "gel_vertices": 9600, "tets": 38025,
+                          "precision": "fp64" if hp == 0 else
+                          "mixed: FP32 element/contact Hessians + mat-vec; FP64 gradient, distances, CCD, energies, PCG residual",
                           "cache": "inputs larger than L2 (~24 GB working set per GPU)", "parallelism": f"envs x{world}"},
-               "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-               "all_status_ok": bool(ok),
-               "iterations": {"newton_env_iters": tot["newton_env_iters"], "pcg_env_iters": tot["pcg_iters"],
-                              "newton_max": tot["newton_max"], "ls_trials": tot["ls_trials"],
-                              "max_pairs": tot["max_pairs"]},
-               "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": int(launches),
+               "latency_ms": {"p50": float(np.percentile(head["step_ms"], 50)),
+                              "p99": float(np.percentile(head["step_ms"], 99))},
+               "fp64": {"value": fp["value"], "ms_per_step": fp["ms_total"] / args.steps,
+                        "latency_ms": {"p50": float(np.percentile(fp["step_ms"], 50)),
+                                       "p99": float(np.percentile(fp["step_ms"], 99))},
+                        "iterations": fp["tot"], "status_not_ok": fp["n_bad"]},
+               "speedup_vs_fp64": head["value"] / fp["value"],
+               "rel_err_vs_fp64": rel_err,
+               "status_not_ok": head["n_bad"],
+               "iterations": head["tot"],
+               "roofline": roof, "kernels": kernels, "clocks": head["clocks"], "gpu_launches": int(head["launches"]),
                "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
-    genv.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

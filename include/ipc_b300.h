@@ -248,17 +248,19 @@ ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks,
 
 /* Neo-Hookean tet (App. A.1): x [n][4][3], Dm_inv [n][3][3] (row-major),
  * vol [n]; outputs (NULL to skip) energy [n] = vol Psi (+inf if J <= 0),
- * grad [n][12], hess [n][12][12] = vol B^T Pi(dP/dF) B (PSD-projected). */
+ * grad [n][12], hess [n][12][12] = vol B^T Pi(dP/dF) B, PSD-projected when
+ * project != 0 (Pi = eigen-clamp of d2Psi/dF2), the exact Hessian when 0. */
 ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol,
                      double mu, double lam, double* energy, double* grad, double* hess,
-                     void* stream);
+                     int project, void* stream);
 
 /* Weighted barrier of pairs (App. A.3): X [n][4][3], is_ee [n] (0/1),
  * weight [n] (multiplies c(x) b(d)), eps_x [n] (mollifier threshold, EE
- * only); energy [n], grad [n][12], hess [n][12][12] (PSD-projected). */
+ * only); energy [n], grad [n][12], hess [n][12][12] (PSD-projected when
+ * project != 0, the exact Hessian when 0). */
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight,
                          const double* eps_x, double dhat, double* energy, double* grad,
-                         double* hess, void* stream);
+                         double* hess, int project, void* stream);
 
 /* ACCD time of impact of pairs moving from X0 by P: toi [n] in (0, 1]. */
 ipc_status ipc_k_accd(int n, const double* X0, const double* P, const int32_t* is_ee,

@@ -124,6 +124,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.ls_max = prm.ls_max;
   d.accd_max = prm.accd_max;
   d.al_max = prm.al_max;
+  d.prec = prm.precision ? 1 : 0;
 
   ex.env_pair_off_i.assign(pk.env_pair_off.begin(), pk.env_pair_off.end());
   ex.has_driven.assign(pk.n_envs, 0);
@@ -215,21 +216,38 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.body_g = c.take<double>(12 * (size_t)pk.n_bodies);
   d.body_H = c.take<double>(144 * (size_t)pk.n_bodies);
   d.body_E = c.take<double>(pk.n_bodies);
-  d.sell_val = c.take<double>(9 * (size_t)pk.n_sell_blocks);
+  const size_t hs = d.prec ? sizeof(float) : sizeof(double);
+  d.sell_val = c.take<char>(hs * 9 * (size_t)pk.n_sell_blocks);
   d.tetG = c.take<double>(12 * (size_t)pk.n_tets);
-  d.tetH = c.take<double>(144 * (size_t)pk.n_tets);
+  d.tetH = c.take<char>(hs * 144 * (size_t)pk.n_tets);
   d.tetE = c.take<double>(pk.n_tets);
   d.row_E = c.take<double>(pk.n_rows);
   d.cvx = c.take<double>(3 * (size_t)pk.n_cv);
   d.cvp = c.take<double>(3 * (size_t)pk.n_cv);
   d.obj_box = c.take<double>(6 * (size_t)pk.n_obj);
+  d.cv_box = c.take<double>(6 * (size_t)pk.n_cv);
+  d.tri_box = c.take<double>(6 * (size_t)pk.n_tri);
+  d.edge_box = c.take<double>(6 * (size_t)pk.n_edge);
+  {
+    // worklist capacity: every query primitive against every smaller object
+    long long cap = 0;
+    for (const auto& ev : pk.env)
+      cap += (long long)(ev.n_cv + ev.n_tri + ev.n_edge) * std::max(1, ev.n_obj - 1);
+    d.bp_cap = (int)std::min<long long>(cap, 1LL << 30);
+  }
+  d.bp_items = c.take<int4>(d.bp_cap);
+  d.bp_count = c.take<int>(1);
+  d.bp_overflow = c.take<int>(1);
   d.pair_v = c.take<int4>(pk.n_pairs_cap);
   d.pair_kind = c.take<int>(pk.n_pairs_cap);
   d.pair_w = c.take<double>(pk.n_pairs_cap);
   d.pair_eps = c.take<double>(pk.n_pairs_cap);
-  d.pair_H = c.take<double>(144 * (size_t)pk.n_pairs_cap);
+  d.pair_H = c.take<char>(hs * 144 * (size_t)pk.n_pairs_cap);
   d.pair_E = c.take<double>(pk.n_pairs_cap);
   d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
+  d.pair_scan = c.take<int>(pk.n_envs + 1);
+  d.act_list = c.take<int>(pk.n_pairs_cap);
+  d.act_count = c.take<int>(1);
   d.cta_part = c.take<double>(4 * (size_t)(pk.n_rows / 128));
   d.env_cnt = c.take<unsigned int>(2 * (size_t)pk.n_envs);
   int mb = 0;
@@ -846,16 +864,17 @@ ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks,
 
 // ---------------------------------------------------------------- element kernels
 ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol, double mu, double lam,
-                     double* energy, double* grad, double* hess, void* stream) {
+                     double* energy, double* grad, double* hess, int project, void* stream) {
   if (n < 0 || (n > 0 && (!x || !Dm_inv || !vol))) return IPC_EINVAL;
-  launch_k_tet(n, x, Dm_inv, vol, mu, lam, energy, grad, hess, reinterpret_cast<cudaStream_t>(stream));
+  launch_k_tet(n, x, Dm_inv, vol, mu, lam, energy, grad, hess, project, reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
 }
 
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight, const double* eps_x,
-                         double dhat, double* energy, double* grad, double* hess, void* stream) {
+                         double dhat, double* energy, double* grad, double* hess, int project, void* stream) {
   if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0)) return IPC_EINVAL;
-  launch_k_barrier(n, X, is_ee, weight, eps_x, dhat, energy, grad, hess, reinterpret_cast<cudaStream_t>(stream));
+  launch_k_barrier(n, X, is_ee, weight, eps_x, dhat, energy, grad, hess, project,
+                   reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
 }
 

@@ -6,7 +6,8 @@
 #include <math.h>
 
 #define IPC_HD __host__ __device__ __forceinline__
-#define IPC_D __device__ __forceinline__
+#define IPC_D __host__ __device__ __forceinline__
+#define IPC_DEV __device__ __forceinline__
 
 namespace ipc {
 
@@ -34,7 +35,7 @@ using D3 = V3<double>;
 
 IPC_D D3 ld3(const double* p, int i) { return D3{p[3 * i], p[3 * i + 1], p[3 * i + 2]}; }
 IPC_D void st3(double* p, int i, D3 v) { p[3 * i] = v.x; p[3 * i + 1] = v.y; p[3 * i + 2] = v.z; }
-IPC_D void atomic_add3(double* p, int i, D3 v) {
+IPC_DEV void atomic_add3(double* p, int i, D3 v) {
   atomicAdd(p + 3 * i, v.x);
   atomicAdd(p + 3 * i + 1, v.y);
   atomicAdd(p + 3 * i + 2, v.z);
@@ -43,27 +44,27 @@ IPC_D double comp(D3 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
 
 // ---------------------------------------------------------------- atomics
 // min / max of non-negative doubles through their (monotone) bit patterns
-IPC_D void atomic_max_nonneg(double* addr, double v) {
+IPC_DEV void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
-IPC_D void atomic_min_nonneg(double* addr, double v) {
+IPC_DEV void atomic_min_nonneg(double* addr, double v) {
   atomicMin(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
 // ---------------------------------------------------------------- reductions
-template <class T> IPC_D T warp_sum(T v) {
+template <class T> IPC_DEV T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-template <class T> IPC_D T warp_max(T v) {
+template <class T> IPC_DEV T warp_max(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
 // Block sum in a fixed order (deterministic); blockDim.x multiple of 32, <= 1024.
-template <class T> IPC_D T block_sum(T v, T* sh /* >= 32 */) {
+template <class T> IPC_DEV T block_sum(T v, T* sh /* >= 32 */) {
   v = warp_sum(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -74,7 +75,7 @@ template <class T> IPC_D T block_sum(T v, T* sh /* >= 32 */) {
   if (w == 0) r = warp_sum(r);
   return r;  // valid in thread 0
 }
-template <class T> IPC_D T block_max(T v, T* sh) {
+template <class T> IPC_DEV T block_max(T v, T* sh) {
   v = warp_max(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
@@ -87,7 +88,7 @@ template <class T> IPC_D T block_max(T v, T* sh) {
 }
 
 // env index of item i given prefix offsets off[0..n_envs] (off[e] <= i < off[e+1])
-IPC_D int find_env(const int* off, int n_envs, int i) {
+IPC_DEV int find_env(const int* off, int n_envs, int i) {
   int lo = 0, hi = n_envs;  // invariant off[lo] <= i < off[hi]
   while (hi - lo > 1) {
     int mid = (lo + hi) >> 1;

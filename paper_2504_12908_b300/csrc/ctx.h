@@ -57,6 +57,7 @@ struct Dev {
   // parameters
   double h, grav[3], dhat, kappa, newton_tol, pcg_tol, accd_s, al_kappa, ee_moll;
   int newton_max, pcg_max, ls_max, accd_max, al_max;
+  int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
   // static tables
   const int *env_row_off, *env_tet_off, *env_cv_off, *env_tri_off, *env_edge_off, *env_obj_off,
       *env_body_off, *env_chunk_off, *env_coated_off, *env_pair_cap, *env_pair_off;
@@ -90,15 +91,25 @@ struct Dev {
   double *p, *g, *r, *z, *d, *q, *qc;
   double *pc, *pc_acc;          // 9 per row
   double *body_pc, *body_pc_acc, *body_g, *body_H, *body_E;  // per body 144 / 144 / 12 / 144 / 1
-  double *sell_val;             // n_blocks * 9
-  double *tetG, *tetH, *tetE;   // 12 / 144 / 1 per tet
+  void* sell_val;               // n_blocks * 9 (double, or float in mixed mode)
+  double *tetG, *tetE;          // 12 / 1 per tet
+  void* tetH;                   // 144 per tet (double, or float in mixed mode)
   double* row_E;
   double *cvx, *cvp;            // 3 per contact vertex
   double* obj_box;              // 6 per object
+  double *cv_box, *tri_box, *edge_box;  // 6 per primitive
+  int4* bp_items;               // broad-phase worklist (kind, query, object, env)
+  int* bp_count;
+  int* bp_overflow;
+  int bp_cap;
   int4* pair_v;                 // contact vertex ids
   int* pair_kind;               // 0 PT, 1 EE
-  double *pair_w, *pair_eps, *pair_H, *pair_E;
+  double *pair_w, *pair_eps, *pair_E;
+  void* pair_H;                 // 144 per pair (double, or float in mixed mode)
   uint8_t* pair_act;
+  int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
+  int* act_list;                 // slots of active (d < dhat) pairs
+  int* act_count;
   double* cta_part;             // 4 per row CTA
   unsigned int* env_cnt;        // last-CTA counters (2 per env)
   double* tgt_stage;            // [n_envs][max_bodies][12] host targets

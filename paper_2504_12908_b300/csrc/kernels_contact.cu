@@ -36,20 +36,46 @@ __global__ void k_cv_pos(Dev d, int flag, int with_disp) {
   }
 }
 
-// one CTA per object: box of its contact vertices (swept: at both ends)
-__global__ void k_obj_box(Dev d, int flag, int swept) {
+// Boxes of every contact primitive (swept: over both ends of the step).
+// idx in [0, n_cv + n_tri + n_edge): points, then triangles, then edges.
+__device__ __forceinline__ void grow(double* bx, D3 a) {
+  bx[0] = fmin(bx[0], a.x); bx[1] = fmin(bx[1], a.y); bx[2] = fmin(bx[2], a.z);
+  bx[3] = fmax(bx[3], a.x); bx[4] = fmax(bx[4], a.y); bx[5] = fmax(bx[5], a.z);
+}
+
+__global__ void k_prim_boxes(Dev d, int flag, int swept) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int n = d.n_cv + d.n_tri + d.n_edge;
+  if (i >= n) return;
+  int kind, j, e;
+  if (i < d.n_cv) { kind = 0; j = i; e = find_env(d.env_cv_off, d.n_envs, j); }
+  else if (i < d.n_cv + d.n_tri) { kind = 1; j = i - d.n_cv; e = find_env(d.env_tri_off, d.n_envs, j); }
+  else { kind = 2; j = i - d.n_cv - d.n_tri; e = find_env(d.env_edge_off, d.n_envs, j); }
+  if (!ENVI(d, e, flag)) return;
+  int v[3], nv;
+  if (kind == 0) { v[0] = j; nv = 1; }
+  else if (kind == 1) { v[0] = d.tri[3 * j]; v[1] = d.tri[3 * j + 1]; v[2] = d.tri[3 * j + 2]; nv = 3; }
+  else { v[0] = d.edge[2 * j]; v[1] = d.edge[2 * j + 1]; nv = 2; }
+  double bx[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int k = 0; k < nv; ++k) {
+    D3 a = ld3(d.cvx, v[k]);
+    grow(bx, a);
+    if (swept) grow(bx, a + ld3(d.cvp, v[k]));
+  }
+  double* out = (kind == 0 ? d.cv_box : (kind == 1 ? d.tri_box : d.edge_box)) + 6 * (long long)j;
+  for (int k = 0; k < 6; ++k) out[k] = bx[k];
+}
+
+// one CTA per object: box of its contact-vertex boxes
+__global__ void k_obj_box(Dev d, int flag) {
   int o = blockIdx.x;
   int e = d.obj_env[o];
   if (!ENVI(d, e, flag)) return;
   __shared__ double sh[32];
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int c = d.obj_cv_begin[o] + threadIdx.x; c < d.obj_cv_end[o]; c += blockDim.x) {
-    D3 a = ld3(d.cvx, c);
-    for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], comp(a, k)); hi[k] = fmax(hi[k], comp(a, k)); }
-    if (swept) {
-      D3 b = a + ld3(d.cvp, c);
-      for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], comp(b, k)); hi[k] = fmax(hi[k], comp(b, k)); }
-    }
+    const double* b = d.cv_box + 6 * (long long)c;
+    for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], b[k]); hi[k] = fmax(hi[k], b[3 + k]); }
   }
   for (int k = 0; k < 3; ++k) {
     double m = -block_max(-lo[k], sh);
@@ -59,25 +85,10 @@ __global__ void k_obj_box(Dev d, int flag, int swept) {
   }
 }
 
-struct Box {
-  double lo[3], hi[3];
-};
-
-__device__ __forceinline__ void box_init(Box& b) {
-  for (int k = 0; k < 3; ++k) { b.lo[k] = INFINITY; b.hi[k] = -INFINITY; }
-}
-__device__ __forceinline__ void box_add(Box& b, const Dev& d, int c, int swept) {
-  D3 a = ld3(d.cvx, c);
-  for (int k = 0; k < 3; ++k) { b.lo[k] = fmin(b.lo[k], comp(a, k)); b.hi[k] = fmax(b.hi[k], comp(a, k)); }
-  if (swept) {
-    D3 q = a + ld3(d.cvp, c);
-    for (int k = 0; k < 3; ++k) { b.lo[k] = fmin(b.lo[k], comp(q, k)); b.hi[k] = fmax(b.hi[k], comp(q, k)); }
-  }
-}
 // widened overlap: lo_a <= hi_b + dhat and lo_b <= hi_a + dhat on every axis
-__device__ __forceinline__ bool overlap(const Box& a, const double* lo, const double* hi, double dh) {
+__device__ __forceinline__ bool overlap6(const double* a, const double* b, double dh) {
   for (int k = 0; k < 3; ++k)
-    if (!(a.lo[k] <= hi[k] + dh) || !(lo[k] <= a.hi[k] + dh)) return false;
+    if (!(a[k] <= b[3 + k] + dh) || !(b[k] <= a[3 + k] + dh)) return false;
   return true;
 }
 
@@ -99,82 +110,160 @@ __device__ void emit_pair(const Dev& d, int e, int4 v, int kind, double w, doubl
   d.pair_eps[k] = eps;
 }
 
-// Broad phase.  Each unordered object pair {A, B} is handled from the bigger
-// object's primitives (culled by the smaller object's box), looping over the
-// smaller object's primitives:
+// Broad phase, stage 1: worklist of (query primitive, other object) items.
+// Each unordered object pair {A, B} is handled from the bigger object's
+// primitives, kept only when the primitive's box meets B's widened box:
 //   QK = 0: points of A vs triangles of B   -> PT(point A, tri B)
 //   QK = 1: triangles of A vs points of B   -> PT(point B, tri A)
 //   QK = 2: edges of A vs edges of B        -> EE(lower object first)
+// Items of one warp are written contiguously (one atomic per warp).
 template <int QK>
-__global__ void k_broad(Dev d, int flag, int swept) {
+__global__ void k_worklist(Dev d, int flag) {
   int n_q = QK == 0 ? d.n_cv : (QK == 1 ? d.n_tri : d.n_edge);
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_q) return;
-  const int* qoff = QK == 0 ? d.env_cv_off : (QK == 1 ? d.env_tri_off : d.env_edge_off);
-  int e = find_env(qoff, d.n_envs, i);
-  if (!ENVI(d, e, flag)) return;
-  int A;
-  int qv[3];
-  int nqv;
-  if (QK == 0) {
-    A = d.cv_obj[i];
-    qv[0] = i; nqv = 1;
-  } else if (QK == 1) {
-    A = d.tri_obj[i];
-    qv[0] = d.tri[3 * i]; qv[1] = d.tri[3 * i + 1]; qv[2] = d.tri[3 * i + 2]; nqv = 3;
-  } else {
-    A = d.edge_obj[i];
-    qv[0] = d.edge[2 * i]; qv[1] = d.edge[2 * i + 1]; nqv = 2;
+  int lane = threadIdx.x & 31;
+  int cnt = 0, e = 0, A = 0;
+  bool live = false;
+  const double* qb = nullptr;
+  unsigned long long ex = 0;
+  if (i < n_q) {
+    const int* qoff = QK == 0 ? d.env_cv_off : (QK == 1 ? d.env_tri_off : d.env_edge_off);
+    e = find_env(qoff, d.n_envs, i);
+    live = ENVI(d, e, flag) != 0;
+    if (live) {
+      A = QK == 0 ? d.cv_obj[i] : (QK == 1 ? d.tri_obj[i] : d.edge_obj[i]);
+      qb = (QK == 0 ? d.cv_box : (QK == 1 ? d.tri_box : d.edge_box)) + 6 * (long long)i;
+      ex = d.obj_exclude[A];
+    }
   }
-  Box qb;
-  box_init(qb);
-  bool qfix = true;
-  for (int k = 0; k < nqv; ++k) {
-    box_add(qb, d, qv[k], swept);
-    qfix = qfix && d.cv_fixed[qv[k]];
+  // pass 1: count the objects this query meets; pass 2 (after the warp scan)
+  // writes them, re-evaluating the same test
+  auto keep = [&](int B) {
+    return !(B == A || ((ex >> d.obj_local[B]) & 1ull) || !bigger(d, A, B)) &&
+           overlap6(qb, d.obj_box + 6 * B, d.dhat);
+  };
+  if (live)
+    for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1]; ++B) cnt += keep(B) ? 1 : 0;
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
+  int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(d.bp_count, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  int pos = base + incl - cnt;
+  if (live && cnt)
+    for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1]; ++B) {
+      if (!keep(B)) continue;
+      if (pos < d.bp_cap) d.bp_items[pos] = make_int4(QK, i, B, e);
+      else *d.bp_overflow = 1;
+      ++pos;
+    }
+}
+
+// Broad phase, stage 2: every item tests its query box against the boxes of
+// the other object's primitives of the complementary kind.
+__global__ void k_pairs(Dev d) {
+  const int n = min(*d.bp_count, d.bp_cap);
   const double dh = d.dhat;
   const double wscale = d.h * d.h * d.kappa;
-  unsigned long long ex = d.obj_exclude[A];
-  for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1]; ++B) {
-    if (B == A || ((ex >> d.obj_local[B]) & 1ull)) continue;
-    if (!bigger(d, A, B)) continue;
-    if (!overlap(qb, d.obj_box + 6 * B, d.obj_box + 6 * B + 3, dh)) continue;
-    if (QK == 0) {
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    int4 item = d.bp_items[it];
+    int qk = item.x, i = item.y, B = item.z, e = item.w;
+    if (qk == 0) {
+      const double* qb = d.cv_box + 6 * (long long)i;
+      bool qfix = d.cv_fixed[i];
       for (int t = d.obj_tri_begin[B]; t < d.obj_tri_end[B]; ++t) {
+        if (!overlap6(qb, d.tri_box + 6 * (long long)t, dh)) continue;
         int t0 = d.tri[3 * t], t1 = d.tri[3 * t + 1], t2 = d.tri[3 * t + 2];
-        Box tb;
-        box_init(tb);
-        box_add(tb, d, t0, swept); box_add(tb, d, t1, swept); box_add(tb, d, t2, swept);
-        if (!overlap(qb, tb.lo, tb.hi, dh)) continue;
         if (qfix && d.cv_fixed[t0] && d.cv_fixed[t1] && d.cv_fixed[t2]) continue;
         emit_pair(d, e, make_int4(i, t0, t1, t2), 0, wscale * 0.5 * d.cv_area[i], 0.0);
       }
-    } else if (QK == 1) {
+    } else if (qk == 1) {
+      const double* qb = d.tri_box + 6 * (long long)i;
+      int q0 = d.tri[3 * i], q1 = d.tri[3 * i + 1], q2 = d.tri[3 * i + 2];
+      bool qfix = d.cv_fixed[q0] && d.cv_fixed[q1] && d.cv_fixed[q2];
       for (int c = d.obj_cv_begin[B]; c < d.obj_cv_end[B]; ++c) {
-        Box pb;
-        box_init(pb);
-        box_add(pb, d, c, swept);
-        if (!overlap(qb, pb.lo, pb.hi, dh)) continue;
+        if (!overlap6(qb, d.cv_box + 6 * (long long)c, dh)) continue;
         if (qfix && d.cv_fixed[c]) continue;
-        emit_pair(d, e, make_int4(c, qv[0], qv[1], qv[2]), 0, wscale * 0.5 * d.cv_area[c], 0.0);
+        emit_pair(d, e, make_int4(c, q0, q1, q2), 0, wscale * 0.5 * d.cv_area[c], 0.0);
       }
     } else {
+      const double* qb = d.edge_box + 6 * (long long)i;
+      int q0 = d.edge[2 * i], q1 = d.edge[2 * i + 1];
+      bool qfix = d.cv_fixed[q0] && d.cv_fixed[q1];
+      int A = d.edge_obj[i];
       for (int f = d.obj_edge_begin[B]; f < d.obj_edge_end[B]; ++f) {
+        if (!overlap6(qb, d.edge_box + 6 * (long long)f, dh)) continue;
         int b0 = d.edge[2 * f], b1 = d.edge[2 * f + 1];
-        Box eb;
-        box_init(eb);
-        box_add(eb, d, b0, swept); box_add(eb, d, b1, swept);
-        if (!overlap(qb, eb.lo, eb.hi, dh)) continue;
         if (qfix && d.cv_fixed[b0] && d.cv_fixed[b1]) continue;
         double w = wscale * 0.25 * (d.edge_area[i] + d.edge_area[f]);
         double eps = d.ee_moll * d.edge_len2[i] * d.edge_len2[f];
-        int4 v = (A < B) ? make_int4(qv[0], qv[1], b0, b1) : make_int4(b0, b1, qv[0], qv[1]);
+        int4 v = (A < B) ? make_int4(q0, q1, b0, b1) : make_int4(b0, b1, q0, q1);
         emit_pair(d, e, v, 1, w, eps);
       }
     }
   }
 }
+
+__global__ void k_bp_reset(Dev d) {
+  *d.bp_count = 0;
+  *d.bp_overflow = 0;
+}
+
+// a worklist overflow marks every selected env as overflowed (conservative)
+__global__ void k_bp_check(Dev d, int flag) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < d.n_envs && *d.bp_overflow && ENVI(d, e, flag)) ENVI(d, e, I_OVERFLOW) = 1;
+}
+
+// Exclusive scan of the per-env pair counts (one CTA): pair kernels then
+// walk a flat index space of real pairs only.  Also clears the active list.
+__global__ void k_pair_scan(Dev d) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) { carry = 0; *d.act_count = 0; }
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < d.n_envs; base += blockDim.x) {
+    int e = base + threadIdx.x;
+    int c = (e < d.n_envs) ? min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]) : 0;
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : 0;
+      int vi = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, vi, o);
+        if (lane >= o) vi += t;
+      }
+      warp_tot[lane] = vi - v;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int excl = carry + warp_tot[wid] + incl - c;
+    if (e < d.n_envs) d.pair_scan[e] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + c;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d.pair_scan[d.n_envs] = carry;
+}
+
+// flat index f over real pairs -> (env, slot k in capacity space)
+__device__ __forceinline__ int pair_at(const Dev& d, int f, int& e) {
+  e = find_env(d.pair_scan, d.n_envs, f);
+  return d.env_pair_off[e] + (f - d.pair_scan[e]);
+}
+
+#define FOR_PAIRS(d, f) for (int f = blockIdx.x * blockDim.x + threadIdx.x, _n = (d).pair_scan[(d).n_envs]; f < _n; \
+                             f += gridDim.x * blockDim.x)
 
 // env of pair slot k (segments of capacity env_pair_cap) and validity
 __device__ __forceinline__ int pair_env(const Dev& d, int k, bool& valid) {
@@ -201,21 +290,25 @@ __device__ __forceinline__ void scatter_cv(const Dev& d, double* dst, int cv, D3
   }
 }
 
+// HT: storage type of the pair Hessian (double: FP64 mode; float: mixed
+// mode).  Distances, barrier derivatives and the projection are FP64 either way.
+template <class HT>
 __global__ void k_barrier(Dev d, int flag) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n_pairs_cap) return;
-  bool valid;
-  int e = pair_env(d, k, valid);
-  if (!valid || !ENVI(d, e, flag)) return;
+  FOR_PAIRS(d, f) {
+  int e;
+  int k = pair_at(d, f, e);
+  if (!ENVI(d, e, flag)) continue;
   int4 v = d.pair_v[k];
   int cvs[4] = {v.x, v.y, v.z, v.w};
   D3 X[4];
   for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
-  double E, g[12], work[288];
-  double* H = d.pair_H + (long long)k * 144;
-  bool act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H, work);
+  double E, g[12], H[144];
+  bool act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
   d.pair_act[k] = act ? 1 : 0;
-  if (!act) return;
+  if (!act) continue;
+  d.act_list[atomicAdd(d.act_count, 1)] = k;
+  HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)k * 144;
+  for (int i = 0; i < 144; ++i) Hs[i] = (HT)H[i];
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
   // preconditioner: diagonal 3x3 of gel vertices, body 12x12 self terms
   for (int i = 0; i < 4; ++i) {
@@ -257,16 +350,19 @@ __global__ void k_barrier(Dev d, int flag) {
             atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, s);
           }
   }
+  }
 }
 
 // q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
 // eliminated: read as zero, never written)
+template <class HT>
 __global__ void k_pair_spmv(Dev d) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n_pairs_cap) return;
+  const int n_act = *d.act_count;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_act; i += gridDim.x * blockDim.x) {
+  int k = d.act_list[i];
   bool valid;
   int e = pair_env(d, k, valid);
-  if (!valid || !ENVI(d, e, I_PCG) || !d.pair_act[k]) return;
+  if (!ENVI(d, e, I_PCG)) continue;
   int4 v = d.pair_v[k];
   int cvs[4] = {v.x, v.y, v.z, v.w};
   double dl[12];
@@ -280,40 +376,42 @@ __global__ void k_pair_spmv(Dev d) {
     }
     dl[3 * i] = u.x; dl[3 * i + 1] = u.y; dl[3 * i + 2] = u.z;
   }
-  const double* H = d.pair_H + (long long)k * 144;
+  const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)k * 144;
+  HT dh[12];
+  for (int q = 0; q < 12; ++q) dh[q] = (HT)dl[q];
   for (int i = 0; i < 4; ++i) {
     double o[3];
     for (int a = 0; a < 3; ++a) {
-      double s = 0;
-      for (int q = 0; q < 12; ++q) s += H[(3 * i + a) * 12 + q] * dl[q];
-      o[a] = s;
+      HT s = 0;
+      for (int q = 0; q < 12; ++q) s += H[(3 * i + a) * 12 + q] * dh[q];
+      o[a] = (double)s;
     }
     scatter_cv(d, d.qc, cvs[i], D3{o[0], o[1], o[2]});
+  }
   }
 }
 
 // ACCD time of impact per swept pair; env bound = min over its pairs
 __global__ void k_accd(Dev d) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n_pairs_cap) return;
-  bool valid;
-  int e = pair_env(d, k, valid);
-  if (!valid || !ENVI(d, e, I_LS)) return;
+  FOR_PAIRS(d, f) {
+  int e;
+  int k = pair_at(d, f, e);
+  if (!ENVI(d, e, I_LS)) continue;
   int4 v = d.pair_v[k];
   int cvs[4] = {v.x, v.y, v.z, v.w};
   D3 X[4], P[4];
   for (int i = 0; i < 4; ++i) { X[i] = ld3(d.cvx, cvs[i]); P[i] = ld3(d.cvp, cvs[i]); }
   double t = accd_toi(X, P, d.pair_kind[k] == 1, d.accd_s, 1.0, d.accd_max);
   atomic_min_nonneg(&ENVS(d, e, S_ACCD), t);
+  }
 }
 
 // barrier energy of each swept pair at x + alpha p (+inf if touching)
 __global__ void k_pair_energy(Dev d, int use_alpha) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n_pairs_cap) return;
-  bool valid;
-  int e = pair_env(d, k, valid);
-  if (!valid || !ENVI(d, e, I_LS)) return;
+  FOR_PAIRS(d, f) {
+  int e;
+  int k = pair_at(d, f, e);
+  if (!ENVI(d, e, I_LS)) continue;
   double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
   int4 v = d.pair_v[k];
   int cvs[4] = {v.x, v.y, v.z, v.w};
@@ -322,23 +420,24 @@ __global__ void k_pair_energy(Dev d, int use_alpha) {
   double D = pair_sqdist(X, d.pair_kind[k] == 1);
   double E = 0.0;
   if (!(D > 0.0)) E = INFINITY;
-  else pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, nullptr, nullptr, nullptr);
+  else pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, nullptr, nullptr);
   d.pair_E[k] = E;
+  }
 }
 
 // min distance over the listed pairs (diagnostics / set_state check)
 __global__ void k_min_dist(Dev d, int flag) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n_pairs_cap) return;
-  bool valid;
-  int e = pair_env(d, k, valid);
-  if (!valid || !ENVI(d, e, flag)) return;
+  FOR_PAIRS(d, f) {
+  int e;
+  int k = pair_at(d, f, e);
+  if (!ENVI(d, e, flag)) continue;
   int4 v = d.pair_v[k];
   int cvs[4] = {v.x, v.y, v.z, v.w};
   D3 X[4];
   for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
   double D = pair_sqdist(X, d.pair_kind[k] == 1);
   atomic_min_nonneg(&ENVS(d, e, S_MIND), sqrt(fmax(D, 0.0)));
+  }
 }
 
 // |J_j p_b|_inf over body vertices into S_PNORM; |J_j (y_b - s_b)|_inf of
@@ -368,41 +467,53 @@ int launch_cv_pos(const Dev& d, int flag, bool with_disp, cudaStream_t s) {
   k_cv_pos<<<nblk(d.n_cv, 256), 256, 0, s>>>(d, flag, with_disp ? 1 : 0);
   return 1;
 }
+// primitive boxes + object boxes (the object boxes feed the worklist)
 int launch_obj_box(const Dev& d, int flag, bool swept, cudaStream_t s) {
-  if (!d.n_obj) return 0;
-  k_obj_box<<<d.n_obj, 256, 0, s>>>(d, flag, swept ? 1 : 0);
-  return 1;
+  long long n = (long long)d.n_cv + d.n_tri + d.n_edge;
+  if (!n) return 0;
+  k_prim_boxes<<<nblk(n, 256), 256, 0, s>>>(d, flag, swept ? 1 : 0);
+  k_obj_box<<<d.n_obj, 256, 0, s>>>(d, flag);
+  return 2;
 }
 int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s) {
-  int n = 0;
-  if (d.n_cv) { k_broad<0><<<nblk(d.n_cv, 128), 128, 0, s>>>(d, flag, swept); ++n; }
-  if (d.n_tri) { k_broad<1><<<nblk(d.n_tri, 128), 128, 0, s>>>(d, flag, swept); ++n; }
-  if (d.n_edge) { k_broad<2><<<nblk(d.n_edge, 128), 128, 0, s>>>(d, flag, swept); ++n; }
-  return n;
+  (void)swept;  // boxes already include the sweep
+  k_bp_reset<<<1, 1, 0, s>>>(d);
+  int n = 1;
+  if (d.n_cv) { k_worklist<0><<<nblk(d.n_cv, 128), 128, 0, s>>>(d, flag); ++n; }
+  if (d.n_tri) { k_worklist<1><<<nblk(d.n_tri, 128), 128, 0, s>>>(d, flag); ++n; }
+  if (d.n_edge) { k_worklist<2><<<nblk(d.n_edge, 128), 128, 0, s>>>(d, flag); ++n; }
+  k_pairs<<<148 * 8, 128, 0, s>>>(d);
+  k_bp_check<<<nblk(d.n_envs, 128), 128, 0, s>>>(d, flag);
+  k_pair_scan<<<1, 1024, 0, s>>>(d);
+  return n + 3;
 }
+// pair kernels grid-stride over the real pairs (count on the device)
+#define PAIR_GRID 148 * 8, 128, 0, s
 int launch_barrier(const Dev& d, int flag, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
-  k_barrier<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, flag);
+  if (d.prec) k_barrier<float><<<PAIR_GRID>>>(d, flag);
+  else k_barrier<double><<<PAIR_GRID>>>(d, flag);
   return 1;
 }
 int launch_pair_spmv(const Dev& d, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
-  k_pair_spmv<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d);
+  if (d.prec) k_pair_spmv<float><<<PAIR_GRID>>>(d);
+  else k_pair_spmv<double><<<PAIR_GRID>>>(d);
   return 1;
 }
 int launch_accd(const Dev& d, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
-  k_accd<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d);
+  k_accd<<<PAIR_GRID>>>(d);
   return 1;
 }
 int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
-  k_pair_energy<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, use_alpha);
+  k_pair_energy<<<PAIR_GRID>>>(d, use_alpha);
   return 1;
 }
 int launch_min_dist(const Dev& d, int flag, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
-  k_min_dist<<<nblk(d.n_pairs_cap, 128), 128, 0, s>>>(d, flag);
+  k_min_dist<<<PAIR_GRID>>>(d, flag);
   return 1;
 }
 int launch_pnorm_body(const Dev& d, cudaStream_t s) {
@@ -415,14 +526,14 @@ int launch_pnorm_body(const Dev& d, cudaStream_t s) {
 // element kernels on caller buffers
 // ---------------------------------------------------------------------------
 __global__ void k_elem_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
-                               double dhat, double* E, double* g, double* H) {
+                               double dhat, double* E, double* g, double* H, int project) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   D3 P[4];
   for (int i = 0; i < 4; ++i) P[i] = ld3(X + 12 * (long long)k, i);
-  double e = 0, gl[12], work[288];
+  double e = 0, gl[12];
   double* Hk = H ? H + 144 * (long long)k : nullptr;
-  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, work);
+  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, project != 0);
   if (E) E[k] = e;
   if (g)
     for (int i = 0; i < 12; ++i) g[12 * (long long)k + i] = act ? gl[i] : 0.0;
@@ -440,9 +551,9 @@ __global__ void k_elem_accd(int n, const double* X0, const double* P, const int*
 }
 
 int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
-                     double dhat, double* E, double* g, double* H, cudaStream_t s) {
+                     double dhat, double* E, double* g, double* H, int project, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_elem_barrier<<<nblk(n, 64), 64, 0, s>>>(n, X, is_ee, w, eps, dhat, E, g, H);
+  k_elem_barrier<<<nblk(n, 64), 64, 0, s>>>(n, X, is_ee, w, eps, dhat, E, g, H, project);
   return 1;
 }
 int launch_k_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac, int max_iter,

@@ -76,6 +76,10 @@ __global__ void k_attach_targets(Dev d, int flag) {
 // ---------------------------------------------------------------------------
 // K3: per-tet neo-Hookean gradient and projected Hessian blocks
 // ---------------------------------------------------------------------------
+// HT: precision of the Hessian (computed and stored).  The gradient is FP64
+// in both modes: it fixes the converged state.  Positions are differenced in
+// FP64 before F is rounded to HT.
+template <class HT>
 __global__ void k_tet(Dev d) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= d.n_tets) return;
@@ -93,9 +97,11 @@ __global__ void k_tet(Dev d) {
   nh_gradient<double>(F, Dmi, vol, mu, lam, g);
   double* G = d.tetG + 12 * (long long)t;
   for (int k = 0; k < 12; ++k) G[k] = g[k];
-  double* H = d.tetH + 144 * (long long)t;
-  nh_hessian_blocks<double>(F, Dmi, vol, mu, lam,
-                            [&](int a, int b, int i, int j, double v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
+  HT Fh[9], Dh[9];
+  for (int k = 0; k < 9; ++k) { Fh[k] = (HT)F[k]; Dh[k] = (HT)Dmi[k]; }
+  HT* H = reinterpret_cast<HT*>(d.tetH) + 144 * (long long)t;
+  nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
+                        [&](int a, int b, int i, int j, HT v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -185,6 +191,7 @@ __global__ void k_body(Dev d) {
 // K5: gather assembly, one warp per 32-row chunk.  Value layout: block
 // (chunk, slot, lane) component c at (chunk_ptr + slot*32)*9 + c*32 + lane.
 // ---------------------------------------------------------------------------
+template <class HT>
 __global__ void k_assemble(Dev d) {
   int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -199,7 +206,7 @@ __global__ void k_assemble(Dev d) {
   for (int sl = 0; sl < slots; ++sl) {
     long long blk = base + (long long)sl * 32 + lane;
     int col = d.sell_col[blk];
-    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    HT v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (is_gel(kr)) {
       // slot 0 is the diagonal block; a later slot with col == r is padding
       bool diag = (sl == 0);
@@ -207,14 +214,15 @@ __global__ void k_assemble(Dev d) {
       if (live && (kr == ROW_PINNED || d.row_kind[col] == ROW_PINNED)) {
         if (diag) v[0] = v[4] = v[8] = 1.0;
       } else if (live) {
+        const HT* tH = reinterpret_cast<const HT*>(d.tetH);
         for (int k = d.asm_ptr[blk]; k < d.asm_ptr[blk + 1]; ++k) {
-          const double* src = d.tetH + 9 * (long long)d.asm_src[k];
+          const HT* src = tH + 9 * (long long)d.asm_src[k];
           for (int c = 0; c < 9; ++c) v[c] += src[c];
         }
-        for (int c = 0; c < 9; ++c) v[c] *= h2;
+        for (int c = 0; c < 9; ++c) v[c] *= (HT)h2;
         if (diag) {
           double m = d.row_mass[r];
-          double dm = m + (kr == ROW_ATTACHED ? d.al_kappa * m : 0.0);
+          HT dm = (HT)(m + (kr == ROW_ATTACHED ? d.al_kappa * m : 0.0));
           v[0] += dm; v[4] += dm; v[8] += dm;
         }
       }
@@ -223,9 +231,9 @@ __global__ void k_assemble(Dev d) {
       int kk = r - d.body_row[b];
       const double* H = d.body_H + 144 * (long long)b;
       for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) v[3 * i + j] = H[(3 * kk + i) * 12 + 3 * sl + j];
+        for (int j = 0; j < 3; ++j) v[3 * i + j] = (HT)H[(3 * kk + i) * 12 + 3 * sl + j];
     }
-    double* out = d.sell_val + (base + (long long)sl * 32) * 9 + lane;
+    HT* out = reinterpret_cast<HT*>(d.sell_val) + (base + (long long)sl * 32) * 9 + lane;
     for (int c = 0; c < 9; ++c) out[c * 32] = v[c];
   }
 }
@@ -261,6 +269,7 @@ __global__ void k_grad(Dev d) {
 }
 
 // block-Jacobi preconditioner: 3x3 per gel row, 12x12 per body
+template <class HT>
 __global__ void k_precond_rows(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
@@ -269,9 +278,9 @@ __global__ void k_precond_rows(Dev d) {
   double P[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   if (kr == ROW_FREE || kr == ROW_ATTACHED) {
     int ch = r >> 5, lane = r & 31;
-    const double* A = d.sell_val + d.chunk_ptr[ch] * 9 + lane;  // slot 0 = diagonal
+    const HT* A = reinterpret_cast<const HT*>(d.sell_val) + d.chunk_ptr[ch] * 9 + lane;  // slot 0 = diagonal
     double M[9];
-    for (int c = 0; c < 9; ++c) M[c] = A[c * 32] + d.pc_acc[9 * r + c];
+    for (int c = 0; c < 9; ++c) M[c] = (double)A[c * 32] + d.pc_acc[9 * r + c];
     double det = inv3(M, P);
     if (!(fabs(det) > 0)) { P[0] = P[4] = P[8] = 1.0; P[1] = P[2] = P[3] = P[5] = P[6] = P[7] = 0.0; }
   }
@@ -341,6 +350,9 @@ __global__ void k_pcg_init(Dev d) {
 }
 
 // q = A d + qc (SELL-32, one row per thread), qc cleared; d.q reduced
+// HT: matrix precision; the products are accumulated in HT, q and the
+// contact part qc stay FP64.
+template <class HT>
 __global__ void k_spmv(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
@@ -348,16 +360,19 @@ __global__ void k_spmv(Dev d) {
   int ch = r >> 5, lane = r & 31;
   int slots = d.chunk_slots[ch];
   long long base = d.chunk_ptr[ch];
-  D3 acc = ld3(d.qc, r);
+  HT ax = 0, ay = 0, az = 0;
+  const HT* val = reinterpret_cast<const HT*>(d.sell_val);
   for (int sl = 0; sl < slots; ++sl) {
     long long b0 = base + (long long)sl * 32;
     int col = d.sell_col[b0 + lane];
-    const double* A = d.sell_val + b0 * 9 + lane;
+    const HT* A = val + b0 * 9 + lane;
     D3 u = ld3(d.d, col);
-    acc.x += A[0] * u.x + A[32] * u.y + A[64] * u.z;
-    acc.y += A[96] * u.x + A[128] * u.y + A[160] * u.z;
-    acc.z += A[192] * u.x + A[224] * u.y + A[256] * u.z;
+    HT ux = (HT)u.x, uy = (HT)u.y, uz = (HT)u.z;
+    ax += A[0] * ux + A[32] * uy + A[64] * uz;
+    ay += A[96] * ux + A[128] * uy + A[160] * uz;
+    az += A[192] * ux + A[224] * uy + A[256] * uz;
   }
+  D3 acc = ld3(d.qc, r) + D3{(double)ax, (double)ay, (double)az};
   st3(d.q, r, acc);
   st3(d.qc, r, D3{0, 0, 0});
   double vals[1] = {dot(ld3(d.d, r), acc)};
@@ -693,22 +708,35 @@ __global__ void k_gather_coated(Dev d) {
 #define ENVGRID nblk(d.n_envs, 128), 128, 0, s
 int launch_predict(const Dev& d, cudaStream_t s) { k_predict<<<ROWGRID>>>(d); return 1; }
 int launch_attach_targets(const Dev& d, int flag, cudaStream_t s) { k_attach_targets<<<ROWGRID>>>(d, flag); return 1; }
-int launch_tet(const Dev& d, cudaStream_t s) { k_tet<<<nblk(d.n_tets, 128), 128, 0, s>>>(d); return 1; }
+int launch_tet(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_tet<float><<<nblk(d.n_tets, 128), 128, 0, s>>>(d);
+  else k_tet<double><<<nblk(d.n_tets, 128), 128, 0, s>>>(d);
+  return 1;
+}
 int launch_body(const Dev& d, cudaStream_t s) {
   if (!d.n_bodies) return 0;
   k_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
   return 1;
 }
-int launch_assemble(const Dev& d, cudaStream_t s) { k_assemble<<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d); return 1; }
+int launch_assemble(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_assemble<float><<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d);
+  else k_assemble<double><<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d);
+  return 1;
+}
 int launch_grad(const Dev& d, cudaStream_t s) { k_grad<<<ROWGRID>>>(d); return 1; }
 int launch_precond(const Dev& d, cudaStream_t s) {
-  k_precond_rows<<<ROWGRID>>>(d);
+  if (d.prec) k_precond_rows<float><<<ROWGRID>>>(d);
+  else k_precond_rows<double><<<ROWGRID>>>(d);
   if (!d.n_bodies) return 1;
   k_precond_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
   return 2;
 }
 int launch_pcg_init(const Dev& d, cudaStream_t s) { k_pcg_init<<<ROWGRID>>>(d); return 1; }
-int launch_spmv(const Dev& d, cudaStream_t s) { k_spmv<<<ROWGRID>>>(d); return 1; }
+int launch_spmv(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_spmv<float><<<ROWGRID>>>(d);
+  else k_spmv<double><<<ROWGRID>>>(d);
+  return 1;
+}
 int launch_pcg_update(const Dev& d, cudaStream_t s) { k_pcg_update<<<ROWGRID>>>(d); return 1; }
 int launch_pcg_dir(const Dev& d, cudaStream_t s) { k_pcg_dir<<<ROWGRID>>>(d); return 1; }
 int launch_newton_check(const Dev& d, cudaStream_t s) {
@@ -757,7 +785,7 @@ int launch_check_inverted(const Dev& d, cudaStream_t s) { k_check_inverted<<<nbl
 // element kernel on caller buffers
 // ---------------------------------------------------------------------------
 __global__ void k_elem_tet(int n, const double* x, const double* Dmi_all, const double* vol, double mu, double lam,
-                           double* E, double* g, double* H) {
+                           double* E, double* g, double* H, int project) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   D3 X[4];
@@ -778,17 +806,17 @@ __global__ void k_elem_tet(int n, const double* x, const double* Dmi_all, const 
     if (!ok) {
       for (int k = 0; k < 144; ++k) Ht[k] = NAN;
     } else {
-      nh_hessian_blocks<double>(F, Dmi, vol[t], mu, lam, [&](int a, int b, int i, int j, double v) {
-        Ht[(3 * a + i) * 12 + 3 * b + j] = v;
-      });
+      nh_hessian_blocks<double>(
+          F, Dmi, vol[t], mu, lam, [&](int a, int b, int i, int j, double v) { Ht[(3 * a + i) * 12 + 3 * b + j] = v; },
+          project != 0);
     }
   }
 }
 
 int launch_k_tet(int n, const double* x, const double* Dmi, const double* vol, double mu, double lam,
-                 double* E, double* g, double* H, cudaStream_t s) {
+                 double* E, double* g, double* H, int project, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_elem_tet<<<nblk(n, 64), 64, 0, s>>>(n, x, Dmi, vol, mu, lam, E, g, H);
+  k_elem_tet<<<nblk(n, 64), 64, 0, s>>>(n, x, Dmi, vol, mu, lam, E, g, H, project);
   return 1;
 }
 

@@ -132,14 +132,14 @@ IPC_HD void svd3(const T* F, T* U, T* s, T* V) {
 // Projected 9x9 d2Psi/dF2 (index 3i+j <-> F_ij), upper triangle packed into
 // Pi[45] row by row.
 template <class T>
-IPC_HD void nh_projected_dPdF(const T* F, T mu, T lam, T* Pi) {
+IPC_HD void nh_projected_dPdF(const T* F, T mu, T lam, T* Pi, bool project = true) {
   T U[9], V[9], s[3];
   svd3(F, U, s, V);
   T lnJ = log(s[0] * s[1] * s[2]);
   T c = mu - lam * lnJ;
   for (int k = 0; k < 45; ++k) Pi[k] = 0;
   auto add_mode = [&](T lmb, const T* Q) {
-    if (!(lmb > T(0))) return;
+    if (project && !(lmb > T(0))) return;
     int idx = 0;
     for (int a = 0; a < 9; ++a)
       for (int b = a; b < 9; ++b) Pi[idx++] += lmb * Q[a] * Q[b];
@@ -185,9 +185,9 @@ IPC_HD int sym9(int a, int b) {  // packed index of (a, b), a, b in [0, 9)
 // Projected element Hessian, all 16 3x3 blocks: H[(a*4+b)*9 + i*3 + j]
 // = vol * sum_{n,n'} D_a[n] Pi[(i,n),(j,n')] D_b[n'].
 template <class T, class Out>
-IPC_HD void nh_hessian_blocks(const T* F, const T* Dmi, T vol, T mu, T lam, Out&& out) {
+IPC_HD void nh_hessian_blocks(const T* F, const T* Dmi, T vol, T mu, T lam, Out&& out, bool project = true) {
   T Pi[45];
-  nh_projected_dPdF(F, mu, lam, Pi);
+  nh_projected_dPdF(F, mu, lam, Pi, project);
   T D[4][3];
   for (int n = 0; n < 3; ++n) {
     D[1][n] = Dmi[n];
@@ -457,11 +457,104 @@ IPC_D double ee_cross2(const D3* X, double* gx, double* Hx) {
   return x;
 }
 
+// Exact PSD projection of a symmetric 12x12 H whose range lies in the span of
+// the closest-feature basis {w (x) e_c (c = 0..2), c_m (x) r (m < k)}: this
+// holds for the unmollified barrier, H = bD2 gD gD^T + bD1 hess D, because
+// gD = 2 w (x) r and hess D = 2 (w w^T (x) I3) - F Mi F^T with
+// F_m = 2 (c_m (x) r + w (x) R_m).  With Q an orthonormal basis of that span
+// (dimension <= 5), H = Q (Q^T H Q) Q^T and the clamp acts on the small matrix.
+static __host__ __device__ __noinline__ void gs_push(double (*Q)[12], int& nq, double* u) {
+  double n0 = 0;
+  for (int p = 0; p < 12; ++p) n0 += u[p] * u[p];
+  if (!(n0 > 0.0)) return;
+  for (int round = 0; round < 2; ++round)  // two rounds of Gram-Schmidt
+    for (int j = 0; j < nq; ++j) {
+      double dd = 0;
+      for (int p = 0; p < 12; ++p) dd += Q[j][p] * u[p];
+      for (int p = 0; p < 12; ++p) u[p] -= dd * Q[j][p];
+    }
+  double n1 = 0;
+  for (int p = 0; p < 12; ++p) n1 += u[p] * u[p];
+  if (!(n1 > 1e-24 * n0)) return;
+  double inv = 1.0 / sqrt(n1);
+  for (int p = 0; p < 12; ++p) Q[nq][p] = u[p] * inv;
+  ++nq;
+}
+
+static __host__ __device__ __noinline__ void psd_project_closest(const Closest& cl, double* H) {
+  double Q[5][12];
+  int nq = 0;
+  double u[12];
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < 4; ++i)
+      for (int a = 0; a < 3; ++a) u[3 * i + a] = (a == c) ? cl.w[i] : 0.0;
+    gs_push(Q, nq, u);
+  }
+  for (int m = 0; m < cl.k; ++m) {
+    for (int i = 0; i < 4; ++i) {
+      u[3 * i] = cl.c[i][m] * cl.r.x;
+      u[3 * i + 1] = cl.c[i][m] * cl.r.y;
+      u[3 * i + 2] = cl.c[i][m] * cl.r.z;
+    }
+    gs_push(Q, nq, u);
+  }
+  // M = Q^T H Q (padded to 5x5)
+  double HQ[12][5];
+  for (int p = 0; p < 12; ++p)
+    for (int j = 0; j < 5; ++j) {
+      double acc = 0;
+      if (j < nq)
+        for (int q = 0; q < 12; ++q) acc += H[p * 12 + q] * Q[j][q];
+      HQ[p][j] = acc;
+    }
+  double M[25], V[25];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      double acc = 0;
+      if (i < nq && j < nq)
+        for (int p = 0; p < 12; ++p) acc += Q[i][p] * HQ[p][j];
+      M[5 * i + j] = acc;
+    }
+  for (int i = 0; i < 5; ++i)
+    for (int j = i + 1; j < 5; ++j) {
+      double sm = 0.5 * (M[5 * i + j] + M[5 * j + i]);
+      M[5 * i + j] = M[5 * j + i] = sm;
+    }
+  jacobi_eigen<5, double>(M, V, 20);
+  bool neg = false;
+  for (int k = 0; k < 5; ++k) neg |= M[6 * k] < 0.0;
+  if (!neg) return;
+  // H = sum_k max(l_k, 0) (Q^T v_k)(Q^T v_k)^T
+  double Y[5][12];
+  for (int k = 0; k < 5; ++k)
+    for (int p = 0; p < 12; ++p) {
+      double acc = 0;
+      for (int i = 0; i < nq; ++i) acc += Q[i][p] * V[5 * i + k];
+      Y[k][p] = acc;
+    }
+  for (int p = 0; p < 12; ++p)
+    for (int q = p; q < 12; ++q) {
+      double acc = 0;
+      for (int k = 0; k < 5; ++k) {
+        double l = M[6 * k];
+        if (l > 0.0) acc += l * Y[k][p] * Y[k][q];
+      }
+      H[p * 12 + q] = acc;
+      H[q * 12 + p] = acc;
+    }
+}
+
+// full 12x12 eigen-clamp with its own scratch
+static __host__ __device__ __noinline__ void psd_project12(double* H) {
+  double scratch[288];
+  psd_project<12, double>(H, scratch);
+}
+
 // Weighted barrier of one pair: E = w c(x) b(d).  Returns false when the
 // pair is inactive (d >= dhat): E = 0 and g/H untouched.  g (12) and H
 // (144, PSD-projected) are written when non-null.  `work` holds 288 doubles.
 IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double dhat,
-                        double* E, double* g, double* H, double* work) {
+                        double* E, double* g, double* H, bool project = true) {
   Closest cl;
   classify(X, is_ee, cl);
   double D = cl.D;
@@ -485,10 +578,7 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
   }
   *E = w * c * b;
   if (!g && !H) return true;
-  double gD[12];
-  double* HD = work;            // 144
-  double* Hx = work + 144;      // 144 (mollifier only)
-  double gx[12];
+  double gD[12], HD[144], gx[12], Hx[144];
   sqdist_derivs(cl, gD, HD);
   if (moll) ee_cross2(X, gx, Hx);
   if (g) {
@@ -510,14 +600,16 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
         }
         H[p * 12 + q] = w * v;
       }
-    // symmetrise then project (work reused)
+    // symmetrise then project: low-rank exact projection unless mollified
     for (int p = 0; p < 12; ++p)
       for (int q = p + 1; q < 12; ++q) {
         double s = 0.5 * (H[p * 12 + q] + H[q * 12 + p]);
         H[p * 12 + q] = s;
         H[q * 12 + p] = s;
       }
-    psd_project<12, double>(H, work);
+    if (!project) return true;
+    if (moll) psd_project12(H);
+    else psd_project_closest(cl, H);
   }
   return true;
 }

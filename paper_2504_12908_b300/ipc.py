@@ -86,8 +86,8 @@ def lib():
             "ipc_launch_count": (C.c_longlong, [vp]),
             "ipc_system_sizes": (i32, [vp, i32, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                        C.POINTER(i32), C.POINTER(i32)]),
-            "ipc_k_tet": (i32, [i32, vp, vp, vp, dbl, dbl, vp, vp, vp, vp]),
-            "ipc_k_barrier": (i32, [i32, vp, vp, vp, vp, dbl, vp, vp, vp, vp]),
+            "ipc_k_tet": (i32, [i32, vp, vp, vp, dbl, dbl, vp, vp, vp, i32, vp]),
+            "ipc_k_barrier": (i32, [i32, vp, vp, vp, vp, dbl, vp, vp, vp, i32, vp]),
             "ipc_k_accd": (i32, [i32, vp, vp, vp, dbl, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -382,19 +382,19 @@ def _vp(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
-def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=None):
+def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=None, project=True):
     """Neo-Hookean element kernel on torch float64 CUDA tensors."""
     n = int(x.shape[0])
     st = lib().ipc_k_tet(n, _vp(x), _vp(Dm_inv), _vp(vol), float(mu), float(lam), _vp(energy), _vp(grad),
-                         _vp(hess), _stream_ptr(x))
+                         _vp(hess), 1 if project else 0, _stream_ptr(x))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_tet")
 
 
-def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None):
+def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None, project=True):
     n = int(X.shape[0])
     st = lib().ipc_k_barrier(n, _vp(X), _vp(is_ee), _vp(weight), _vp(eps_x), float(dhat), _vp(energy), _vp(grad),
-                             _vp(hess), _stream_ptr(X))
+                             _vp(hess), 1 if project else 0, _stream_ptr(X))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_barrier")
 

@@ -90,6 +90,8 @@ class SolverParams:
     al_kappa: float = 1e6           # mass-weighted AL penalty factor
     al_max: int = 10
     ee_mollifier: float = 1e-3
+    precision: int = 0              # 0 FP64, 1 mixed (FP32 Hessians / mat-vec)
+    max_pairs_per_env: int = 0      # candidate-pair capacity per env (0 = default)
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""
