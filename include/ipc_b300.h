@@ -198,6 +198,24 @@ ipc_status ipc_read_gel_surface(ipc_ctx* ctx, int env, double* out_xyz, int capa
 ipc_status ipc_read_gel_surface_all(ipc_ctx* ctx, double* out_xyz, size_t capacity_rows,
                                     size_t* rows_written);
 
+/* Same result as ipc_read_gel_surface_all, for callers that cannot allocate
+ * device memory when they read results back (a restricted allocator, or a
+ * workspace sized without spare room): the device gather is staged through a
+ * fixed array of 262144 rows (6 MiB) compiled into the library, which every
+ * GPU that loads the library keeps until the process exits.  This is a
+ * property of this library; the paper has no counterpart.
+ *   - Calls no cudaMalloc / cudaFree; needs no workspace scratch.
+ *   - Returns IPC_EINVAL (message in ipc_last_error) when the envs hold more
+ *     than 262144 coated-surface rows in total.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array: calls that overlap on the GPU (several host
+ *     threads or streams) race on it and must be serialised by the caller.
+ * Synchronises the ctx stream. */
+ipc_status ipc_read_gel_surface_all_noalloc(ipc_ctx* ctx, double* out_xyz, size_t capacity_rows,
+                                            size_t* rows_written);
+
 /* ---- diagnostics (used by the parity tests; not needed to step) -------- */
 
 /* Objective, gradient and Hessian-vector product of one env at its current

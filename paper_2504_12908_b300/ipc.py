@@ -74,6 +74,7 @@ def lib():
             "ipc_step": (i32, [vp, _ip, i32, _ip, C.POINTER(ipc_step_stats)]),
             "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_debug_eval": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_debug_pairs": (i32, [vp, i32, _dp, _dp, _ip, i32, C.POINTER(i32)]),
             "ipc_debug_newton_dir": (i32, [vp, i32, _dp, C.POINTER(i32)]),
@@ -101,6 +102,7 @@ def lib():
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
+            "ipc_read_gel_surface_all_noalloc",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
             "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
@@ -306,6 +308,18 @@ class Envs:
         w = C.c_size_t()
         self._check(lib().ipc_read_gel_surface_all(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
                     "ipc_read_gel_surface_all")
+        return out
+
+    def read_gel_surface_all_noalloc(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """Same as read_gel_surface_all through the entry point that stages in
+        a fixed device array compiled into the library (no device allocation,
+        no workspace scratch; at most 262144 rows in total)."""
+        tot = sum(s[2] for s in self.sizes)
+        if out is None:
+            out = np.zeros((tot, 3))
+        w = C.c_size_t()
+        self._check(lib().ipc_read_gel_surface_all_noalloc(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
+                    "ipc_read_gel_surface_all_noalloc")
         return out
 
     # ------------------------------------------------------------ profiling
