@@ -125,6 +125,9 @@ typedef struct {
   int al_updates;       /* max over envs                                     */
   int max_pairs;        /* max candidate pairs seen in one env               */
   long long newton_env_iters; /* Newton iterations summed over the stepped envs */
+  long long al_env_updates;   /* AL multiplier updates summed over the envs    */
+  long long ccd_limited;      /* line searches that started below alpha = 1    */
+  double alpha_sum;           /* accepted line-search steps, summed            */
   double ms_total;      /* wall time of the call (host clock), ms            */
 } ipc_step_stats;
 
@@ -280,9 +283,10 @@ ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const dou
                          const double* eps_x, double dhat, double* energy, double* grad,
                          double* hess, int project, void* stream);
 
-/* ACCD time of impact of pairs moving from X0 by P: toi [n] in (0, 1]. */
+/* ACCD time of impact of pairs moving from X0 by P: toi [n] in (0, 1];
+ * iters [n] (may be NULL) receives the advancement iterations of each pair. */
 ipc_status ipc_k_accd(int n, const double* X0, const double* P, const int32_t* is_ee,
-                      double s, int max_iter, double* toi, void* stream);
+                      double s, int max_iter, double* toi, int32_t* iters, void* stream);
 
 #ifdef __cplusplus
 }

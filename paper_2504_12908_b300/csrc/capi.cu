@@ -242,7 +242,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_kind = c.take<int>(pk.n_pairs_cap);
   d.pair_w = c.take<double>(pk.n_pairs_cap);
   d.pair_eps = c.take<double>(pk.n_pairs_cap);
-  d.pair_H = c.take<char>(hs * 144 * (size_t)pk.n_pairs_cap);
+  d.pair_H = c.take<char>(hs * 78 * (size_t)pk.n_pairs_cap);
   d.pair_E = c.take<double>(pk.n_pairs_cap);
   d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
   d.pair_scan = c.take<int>(pk.n_envs + 1);
@@ -649,6 +649,9 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     S.ls_trials += ei[I_LSTOT];
     S.max_pairs = std::max(S.max_pairs, ei[I_NPAIRS]);
     S.newton_env_iters += ei[I_NEWTON];
+    S.al_env_updates += ei[I_AL];
+    S.ccd_limited += ei[I_CCDCUT];
+    S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
   }
   (void)newton_done;
   S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -879,9 +882,9 @@ ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const dou
 }
 
 ipc_status ipc_k_accd(int n, const double* X0, const double* P, const int32_t* is_ee, double s, int max_iter,
-                      double* toi, void* stream) {
+                      double* toi, int32_t* iters, void* stream) {
   if (n < 0 || (n > 0 && (!X0 || !P || !is_ee || !toi)) || !(s > 0 && s < 1) || max_iter < 1) return IPC_EINVAL;
-  launch_k_accd(n, X0, P, is_ee, s, max_iter, toi, reinterpret_cast<cudaStream_t>(stream));
+  launch_k_accd(n, X0, P, is_ee, s, max_iter, toi, iters, reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
 }
 

@@ -27,6 +27,7 @@ enum EnvScalar {
   S_E0,         // energy at the line-search start
   S_E1,         // energy at the trial step
   S_MIND,       // min pair distance (diagnostics)
+  S_ASUM,       // accepted line-search steps this step, summed
   NUM_SCALARS
 };
 
@@ -48,6 +49,7 @@ enum EnvInt {
   I_LSTOT,        // line-search trials this step
   I_SEL,          // selected for this ipc_step call
   I_FLAG,         // scratch flag (inverted tet found)
+  I_CCDCUT,       // line searches starting below alpha = 1 this step
   NUM_INTS
 };
 
@@ -105,7 +107,7 @@ struct Dev {
   int4* pair_v;                 // contact vertex ids
   int* pair_kind;               // 0 PT, 1 EE
   double *pair_w, *pair_eps, *pair_E;
-  void* pair_H;                 // 144 per pair (double, or float in mixed mode)
+  void* pair_H;                 // 78 per pair: packed upper triangle (double, or float in mixed mode)
   uint8_t* pair_act;
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
   int* act_list;                 // slots of active (d < dhat) pairs

@@ -51,6 +51,6 @@ int launch_k_tet(int n, const double* x, const double* Dmi, const double* vol, d
 int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
                      double dhat, double* E, double* g, double* H, int project, cudaStream_t s);
 int launch_k_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac, int max_iter,
-                   double* toi, cudaStream_t s);
+                  double* toi, int* iters, cudaStream_t s);
 
 }  // namespace ipc

@@ -307,8 +307,9 @@ __global__ void k_barrier(Dev d, int flag) {
   d.pair_act[k] = act ? 1 : 0;
   if (!act) continue;
   d.act_list[atomicAdd(d.act_count, 1)] = k;
-  HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)k * 144;
-  for (int i = 0; i < 144; ++i) Hs[i] = (HT)H[i];
+  HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)k * 78;
+  for (int p = 0, o = 0; p < 12; ++p)
+    for (int q = p; q < 12; ++q) Hs[o++] = (HT)H[p * 12 + q];
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
   // preconditioner: diagonal 3x3 of gel vertices, body 12x12 self terms
   for (int i = 0; i < 4; ++i) {
@@ -355,39 +356,96 @@ __global__ void k_barrier(Dev d, int flag) {
 
 // q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
 // eliminated: read as zero, never written)
+// index of (p, q), p <= q, in the packed upper triangle of a 12x12 matrix
+__device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) / 2 + (q - p); }
+
+// q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
+// eliminated: read as zero, never written).  H_k is stored as its packed
+// upper triangle.  The body part J^T (H_k d) of a warp whose lanes all touch
+// the same single body is summed across the warp before the atomics (every
+// contact of an env hits the same 12 body DoFs).
 template <class HT>
 __global__ void k_pair_spmv(Dev d) {
   const int n_act = *d.act_count;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_act; i += gridDim.x * blockDim.x) {
-  int k = d.act_list[i];
-  bool valid;
-  int e = pair_env(d, k, valid);
-  if (!ENVI(d, e, I_PCG)) continue;
-  int4 v = d.pair_v[k];
-  int cvs[4] = {v.x, v.y, v.z, v.w};
-  double dl[12];
-  for (int i = 0; i < 4; ++i) {
-    int cv = cvs[i], row = d.cv_row[cv];
-    D3 u;
-    if (d.cv_body[cv] < 0) {
-      u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
-    } else {
-      u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_act; base += stride) {
+    const int i = base + lane;
+    int k = -1, e = 0;
+    bool live = false;
+    if (i < n_act) {
+      k = d.act_list[i];
+      bool valid;
+      e = pair_env(d, k, valid);
+      live = ENVI(d, e, I_PCG) != 0;
     }
-    dl[3 * i] = u.x; dl[3 * i + 1] = u.y; dl[3 * i + 2] = u.z;
-  }
-  const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)k * 144;
-  HT dh[12];
-  for (int q = 0; q < 12; ++q) dh[q] = (HT)dl[q];
-  for (int i = 0; i < 4; ++i) {
-    double o[3];
-    for (int a = 0; a < 3; ++a) {
-      HT s = 0;
-      for (int q = 0; q < 12; ++q) s += H[(3 * i + a) * 12 + q] * dh[q];
-      o[a] = (double)s;
+    int cvs[4] = {0, 0, 0, 0};
+    double o[12];
+    for (int q = 0; q < 12; ++q) o[q] = 0.0;
+    int body = -2;  // -2: none yet, -1: several bodies, >= 0: the single body
+    if (live) {
+      int4 v = d.pair_v[k];
+      cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
+      HT dh[12];
+      for (int m = 0; m < 4; ++m) {
+        int cv = cvs[m], row = d.cv_row[cv];
+        D3 u;
+        int b = d.cv_body[cv];
+        if (b < 0) {
+          u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
+        } else {
+          u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+          body = (body == -2 || body == b) ? b : -1;
+        }
+        dh[3 * m] = (HT)u.x; dh[3 * m + 1] = (HT)u.y; dh[3 * m + 2] = (HT)u.z;
+      }
+      const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)k * 78;
+      HT acc[12];
+      for (int q = 0; q < 12; ++q) acc[q] = 0;
+      for (int p = 0; p < 12; ++p) {
+        acc[p] += H[ut12(p, p)] * dh[p];
+        for (int q = p + 1; q < 12; ++q) {
+          HT h = H[ut12(p, q)];
+          acc[p] += h * dh[q];
+          acc[q] += h * dh[p];
+        }
+      }
+      for (int q = 0; q < 12; ++q) o[q] = (double)acc[q];
     }
-    scatter_cv(d, d.qc, cvs[i], D3{o[0], o[1], o[2]});
-  }
+    // gel points: direct atomics
+    for (int m = 0; m < 4; ++m)
+      if (live && d.cv_body[cvs[m]] < 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
+    // body points: J^T o, i.e. 12 values on the body's 4 sub-rows
+    double jb[12];
+    for (int q = 0; q < 12; ++q) jb[q] = 0.0;
+    if (live && body >= 0)
+      for (int m = 0; m < 4; ++m) {
+        if (d.cv_body[cvs[m]] != body) continue;
+        D3 xb = ld3(d.cv_xbar, cvs[m]);
+        const double w4[4] = {1.0, xb.x, xb.y, xb.z};
+        for (int s4 = 0; s4 < 4; ++s4)
+          for (int c = 0; c < 3; ++c) jb[3 * s4 + c] += w4[s4] * o[3 * m + c];
+      }
+    int key = (live && body >= 0) ? body : -1;
+    unsigned peers = __match_any_sync(0xffffffffu, key);
+    bool uniform = (peers == 0xffffffffu) && key >= 0;
+    if (uniform) {
+      for (int q = 0; q < 12; ++q) {
+        double t = jb[q];
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        jb[q] = t;
+      }
+      if (lane == 0) {
+        int br = d.body_row[key];
+        for (int q = 0; q < 12; ++q) atomicAdd(d.qc + 3 * br + q, jb[q]);
+      }
+    } else if (key >= 0) {
+      int br = d.body_row[key];
+      for (int q = 0; q < 12; ++q) atomicAdd(d.qc + 3 * br + q, jb[q]);
+    } else if (live && body == -1) {  // points of several bodies: per point
+      for (int m = 0; m < 4; ++m)
+        if (d.cv_body[cvs[m]] >= 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
+    }
   }
 }
 
@@ -542,12 +600,14 @@ __global__ void k_elem_barrier(int n, const double* X, const int* is_ee, const d
 }
 
 __global__ void k_elem_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac,
-                            int max_iter, double* toi) {
+                            int max_iter, double* toi, int* iters) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   D3 A[4], B[4];
   for (int i = 0; i < 4; ++i) { A[i] = ld3(X0 + 12 * (long long)k, i); B[i] = ld3(P + 12 * (long long)k, i); }
-  toi[k] = accd_toi(A, B, is_ee[k] != 0, sfrac, 1.0, max_iter);
+  int it = 0;
+  toi[k] = accd_toi(A, B, is_ee[k] != 0, sfrac, 1.0, max_iter, &it);
+  if (iters) iters[k] = it;
 }
 
 int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, const double* eps,
@@ -557,9 +617,9 @@ int launch_k_barrier(int n, const double* X, const int* is_ee, const double* w, 
   return 1;
 }
 int launch_k_accd(int n, const double* X0, const double* P, const int* is_ee, double sfrac, int max_iter,
-                  double* toi, cudaStream_t s) {
+                  double* toi, int* iters, cudaStream_t s) {
   if (n <= 0) return 0;
-  k_elem_accd<<<nblk(n, 128), 128, 0, s>>>(n, X0, P, is_ee, sfrac, max_iter, toi);
+  k_elem_accd<<<nblk(n, 128), 128, 0, s>>>(n, X0, P, is_ee, sfrac, max_iter, toi, iters);
   return 1;
 }
 

@@ -484,6 +484,7 @@ __global__ void k_ls_init(Dev d) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.n_envs || !ENVI(d, e, I_LS)) return;
   ENVS(d, e, S_ALPHA) = fmin(1.0, ENVS(d, e, S_ACCD));
+  if (ENVS(d, e, S_ACCD) < 1.0) ENVI(d, e, I_CCDCUT) += 1;
 }
 
 __global__ void k_energy_tet(Dev d, int use_alpha) {
@@ -583,6 +584,7 @@ __global__ void k_ls_decide(Dev d) {
   if (E1 <= E0) {
     ENVI(d, e, I_ACCEPT) = 1;
     ENVI(d, e, I_LS) = 0;
+    ENVS(d, e, S_ASUM) += ENVS(d, e, S_ALPHA);
     return;
   }
   ENVS(d, e, S_ALPHA) *= 0.5;
@@ -644,6 +646,8 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_LSTOT) = 0;
     ENVI(d, e, I_ACCEPT) = 0;
     ENVI(d, e, I_OVERFLOW) = 0;
+    ENVI(d, e, I_CCDCUT) = 0;
+    ENVS(d, e, S_ASUM) = 0.0;
   } else if (what == 1) {
     if (!ENVI(d, e, I_ACTIVE)) return;
     ENVS(d, e, S_PNORM) = 0.0;

@@ -617,12 +617,14 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
 // =====================================================================
 // additive CCD
 // =====================================================================
-IPC_D double accd_toi(const D3* X0, const D3* P, bool is_ee, double s, double t_max, int max_iter) {
+IPC_D double accd_toi(const D3* X0, const D3* P, bool is_ee, double s, double t_max, int max_iter,
+                      int* iters = nullptr) {
   D3 pm = 0.25 * (P[0] + P[1] + P[2] + P[3]);
   double nq[4];
   for (int i = 0; i < 4; ++i) nq[i] = sqrt(norm2(P[i] - pm));
   double lp = is_ee ? fmax(nq[0], nq[1]) + fmax(nq[2], nq[3])
                     : nq[0] + fmax(nq[1], fmax(nq[2], nq[3]));
+  if (iters) *iters = 0;
   if (lp == 0.0) return t_max;
   double d0 = sqrt(pair_sqdist(X0, is_ee));
   double gap = s * d0;
@@ -630,6 +632,7 @@ IPC_D double accd_toi(const D3* X0, const D3* P, bool is_ee, double s, double t_
   double tl = (1.0 - s) * d0 / lp;
   D3 X[4];
   for (int it = 0; it < max_iter; ++it) {
+    if (iters) *iters = it + 1;
     double tt = t + tl;
     for (int i = 0; i < 4; ++i) X[i] = X0[i] + tt * P[i];
     double d = sqrt(pair_sqdist(X, is_ee));

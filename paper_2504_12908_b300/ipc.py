@@ -42,6 +42,7 @@ class ipc_scene_desc(C.Structure):
 class ipc_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_trials", C.c_int),
                 ("al_updates", C.c_int), ("max_pairs", C.c_int), ("newton_env_iters", C.c_longlong),
+                ("al_env_updates", C.c_longlong), ("ccd_limited", C.c_longlong), ("alpha_sum", C.c_double),
                 ("ms_total", C.c_double)]
 
 
@@ -89,7 +90,7 @@ def lib():
                                        C.POINTER(i32), C.POINTER(i32)]),
             "ipc_k_tet": (i32, [i32, vp, vp, vp, dbl, dbl, vp, vp, vp, i32, vp]),
             "ipc_k_barrier": (i32, [i32, vp, vp, vp, vp, dbl, vp, vp, vp, i32, vp]),
-            "ipc_k_accd": (i32, [i32, vp, vp, vp, dbl, i32, vp, vp]),
+            "ipc_k_accd": (i32, [i32, vp, vp, vp, dbl, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -413,8 +414,9 @@ def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess
         raise IpcError(st, "ipc_k_barrier")
 
 
-def k_accd(X0, P, is_ee, s: float, max_iter: int, toi):
+def k_accd(X0, P, is_ee, s: float, max_iter: int, toi, iters=None):
     n = int(X0.shape[0])
-    st = lib().ipc_k_accd(n, _vp(X0), _vp(P), _vp(is_ee), float(s), int(max_iter), _vp(toi), _stream_ptr(X0))
+    st = lib().ipc_k_accd(n, _vp(X0), _vp(P), _vp(is_ee), float(s), int(max_iter), _vp(toi), _vp(iters),
+                          _stream_ptr(X0))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_accd")

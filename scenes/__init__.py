@@ -306,16 +306,20 @@ def config2(env: int, n_steps=100) -> Scenario:
                     precision=1)
 
 
-def config3(env: int, n=32, nz=6, n_steps=200, level=4) -> Scenario:
+def config3(env: int, n=32, nz=6, n_steps=200, level=4, gap=None) -> Scenario:
     """Two gel pads on ABD fingers closing at 10 mm/s on a free icosphere.
 
     Pads are 20x20x4 mm with their contact faces normal to x; each pad's back
     face is attached to a 22x22x4 mm finger box behind it.  The object is a
-    free icosphere (r = 10 mm, rho = 800) under gravity.
+    free icosphere (r = 10 mm, rho = 800) under gravity.  The initial gap
+    between each pad and the sphere is 1 mm + U(0, 0.2) mm, or `gap` when
+    given (small scenes that reach contact within a few steps).
     """
     rng = np.random.default_rng(3000 + env)
     r = 10e-3
     gap0 = 1e-3 + rng.uniform(0.0, 2e-4)
+    if gap is not None:
+        gap0 = float(gap)
     thick = 4e-3
     xs, ys, zs = [], [], []
     parts_x, parts_t, obj, pinned, attach = [], [], [], [], []
@@ -328,12 +332,9 @@ def config3(env: int, n=32, nz=6, n_steps=200, level=4) -> Scenario:
         # contact face (w = 0) at x = sgn * (r + gap0), back face farther out.
         w = x[:, 2]
         X = np.stack([sgn * (r + gap0 - w), x[:, 0], x[:, 1]], axis=1)
-        t = tets.copy()
-        if sgn > 0:
-            # the map (u,v,w)->(-w,u,v) keeps orientation for sgn=+1?  Re-orient.
-            pass
+        # the map to world coordinates mirrors one pad: re-orient every tet
         tt = []
-        for q in t:
+        for q in tets:
             tt.append(_orient(X, list(q)))
         tt = np.asarray(tt, np.int32)
         parts_x.append(X)
