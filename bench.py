@@ -44,6 +44,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed path (profiling runs); no FP64 comparison")
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving"],
+                    help="batch: the uniform 256-env batch (default); serving: the Poisson request stream")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: admission window (s)")
+    ap.add_argument("--serve-hard", type=float, default=60.0, help="serving: stop stepping at this time (s)")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--req-steps", type=int, default=200, help="serving: steps per request")
+    ap.add_argument("--max-resident", type=int, default=4096)
+    ap.add_argument("--max-cohort", type=int, default=256)
+    ap.add_argument("--max-cohorts", type=int, default=8)
+    ap.add_argument("--no-graphs", action="store_true", help="serving: plain launches instead of PCG graphs")
     return ap.parse_args()
 
 
@@ -190,13 +200,14 @@ def kernel_bytes(genv, stats_tot, prof):
     T = sz["tets"]
     hs = 4 if getattr(genv.params, "precision", 0) else 8   # Hessian / matrix value bytes
     out = {}
-    # SELL SpMV per env-iteration: 9 values + 4 B column per real block;
-    # per row d and qc read, q and qc written (FP64, 24 B each)
-    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * 96
+    # SELL SpMV per env-iteration: 9 values + 4 B column per real block; per
+    # row z and d_old read (the direction is formed on the fly), d_new and q
+    # written, qc read and cleared (FP64, 24 B each)
+    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * 144
     out["sell_spmv"] = stats_tot["pcg_iters"] * spmv_env_iter
-    # PCG update: reads p, d, r, q, P^-1 (9 doubles), writes p, r, z
-    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (4 * 24 + 72 + 3 * 24)
-    out["pcg_dir"] = stats_tot["pcg_iters"] * rows_real * 72
+    # PCG update: reads p, d_new, r, q and the 6-entry symmetric P^-1 block,
+    # writes p, r, z
+    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (4 * 24 + 6 * hs + 3 * 24)
     # elastic element kernel: 4 indices + 4 positions + Dm^-1 + vol read,
     # 12 FP64 gradient and 144 Hessian values written
     out["tet_elastic"] = stats_tot["newton_env_iters"] * T * (16 + 96 + 72 + 8 + 96 + 144 * hs)
@@ -237,7 +248,7 @@ def time_precision(args, scene, params, deltas, precision, local, world, profile
     launches0 = genv.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     tot = {"pcg_iters": 0, "newton_env_iters": 0, "ls_trials": 0, "newton_max": 0, "max_pairs": 0,
-           "al_env_updates": 0, "ccd_limited": 0, "alpha_sum": 0.0}
+           "al_env_updates": 0, "ccd_limited": 0, "alpha_sum": 0.0, "accd_iters": 0, "accd_iters_max": 0}
     statuses = []
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
@@ -256,6 +267,8 @@ def time_precision(args, scene, params, deltas, precision, local, world, profile
         tot["al_env_updates"] += s["al_env_updates"]
         tot["ccd_limited"] += s["ccd_limited"]
         tot["alpha_sum"] += s["alpha_sum"]
+        tot["accd_iters"] += s["accd_iters"]
+        tot["accd_iters_max"] = max(tot["accd_iters_max"], s["accd_iters_max"])
     t_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -290,7 +303,7 @@ def per_step_error(g64, g32, tg, body_radius):
     s64, _ = g64.step()
     s32, _ = g32.step()
     diag = float(np.linalg.norm(np.array([0.02, 0.02, 0.004])))
-    worst = 0.0
+    errs = np.zeros(n)
     for e in range(n):
         x64, _, y64, _ = g64.get_state(e)
         x32, _, y32, _ = g32.get_state(e)
@@ -298,8 +311,10 @@ def per_step_error(g64, g32, tg, body_radius):
         dy = np.abs(np.asarray(y64) - np.asarray(y32)).reshape(-1, 4, 3)   # [p, a0, a1, a2] per body
         if dy.size:
             d = max(d, float((dy[:, 0, :] + body_radius * dy[:, 1:, :].sum(axis=1)).max()))
-        worst = max(worst, d / diag)
-    return worst, int(np.sum(s64 != 0) + np.sum(s32 != 0))
+        errs[e] = d / diag
+    dist = {"max": float(errs.max()), "p99": float(np.percentile(errs, 99)), "median": float(np.median(errs)),
+            "envs_above_1e-4": int(np.sum(errs > 1e-4)), "envs": n}
+    return float(errs.max()), dist, int(np.sum(s64 != 0) + np.sum(s32 != 0))
 
 
 def roofline_of(genv, res):
@@ -353,13 +368,13 @@ def run_ours(args):
     head = results[precisions[-1]]
     genv = head["genv"]
     roof, kernels = roofline_of(genv, head)
-    rel_err = traj_err = None
+    rel_err = traj_err = err_dist = None
     if len(precisions) == 2:
         diag = float(np.linalg.norm(np.array([0.02, 0.02, 0.004])))
         # trajectories after warm-up + timed steps (divergence accumulates)
         traj_err = float(np.abs(surf[1] - surf[0]).max() / diag)
         # the per-step error from the same input state, checked after timing
-        rel_err, n_bad_err = per_step_error(results[0]["genv"], genv, head["dev_tg"][head["n_total"]], 4e-3)
+        rel_err, err_dist, n_bad_err = per_step_error(results[0]["genv"], genv, head["dev_tg"][head["n_total"]], 4e-3)
         results[0]["genv"].close()
         torch.cuda.empty_cache()
         # the e2e leg continues from a state the error check has moved on
@@ -416,6 +431,7 @@ def run_ours(args):
                "rel_err_vs_fp64": rel_err,
                "rel_err_def": "one step of both paths from the same input state (every env), max vertex "
                               "difference / gel bbox diagonal",
+               "rel_err_per_env": err_dist,
                "traj_err_vs_fp64": traj_err,
                "status_not_ok": head["n_bad"],
                "iterations": head["tot"],
@@ -426,10 +442,77 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serving(args):
+    """The serving stream: Poisson arrivals of config-2-style requests,
+    admitted into cohorts by free device memory, mixed precision, PCG inner
+    loop as captured CUDA graphs.  Compared with the same kind of requests
+    stepped one by one in plain FP64 (a bounded sample)."""
+    import torch
+
+    import scenes
+    from paper_2504_12908_b300 import ipc
+    from paper_2504_12908_b300.build import build
+    from paper_2504_12908_b300.serving import GpuEngine, Request, Server, poisson_arrivals
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    build()
+    n_req = int(args.rate * args.serve_seconds) + 1
+    arr = poisson_arrivals(n_req, args.rate, 4000)
+
+    def make(rid):
+        def b():
+            sc = scenes.config4_request(rid, n_steps=args.req_steps)
+            return sc.scene, sc.delta
+        return b
+    reqs = [Request(rid=i, n_steps=args.req_steps, arrival=float(arr[i]), build=make(i)) for i in range(n_req)]
+    prm = scenes.SolverParams()
+    prm.precision = 1
+    eng = GpuEngine(prm, device=f"cuda:{local}", graphs=not args.no_graphs)
+    srv = Server(eng, max_resident=args.max_resident, max_cohort=args.max_cohort,
+                 max_cohorts=args.max_cohorts, keep_state=False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    rep = srv.run(reqs, time_limit=args.serve_seconds, hard_limit=args.serve_hard)
+    clk = clocks.stop()
+    # plain FP64, one request at a time (bounded sample: 3 requests x 10 steps)
+    p64 = scenes.SolverParams()
+    one_ms = []
+    for rid in range(3):
+        sc = scenes.config4_request(rid, n_steps=args.req_steps)
+        g = ipc.Envs([sc.scene], p64)
+        for k in range(10):
+            t = g.rest_y(0)
+            t[:, :3] += sc.delta(k)[:, :3]
+            g.set_targets(0, t)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.step()
+            torch.cuda.synchronize()
+            one_ms.append(1e3 * (time.perf_counter() - t0))
+        g.close()
+    one = 1e3 / float(np.mean(one_ms))
+    summ = rep.summary()
+    out = {"metric": "env-steps/s (serving stream)", "value": rep.env_steps_per_s, "unit": "env-steps/s",
+           "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "serving: Poisson %.0f req/s of config-2-style envs x %d steps, window %.0f s"
+                      % (args.rate, args.req_steps, args.serve_seconds),
+                      "max_resident": args.max_resident, "max_cohort": args.max_cohort,
+                      "max_cohorts": args.max_cohorts, "graphs": not args.no_graphs},
+           "latency_ms": {"p50": rep.step_ms_p50, "p99": rep.step_ms_p99},
+           "serving": {k: v for k, v in summ.items()},
+           "fp64_one_by_one": {"value": one, "unit": "env-steps/s", "step_ms_mean": float(np.mean(one_ms)),
+                               "sample": "3 requests x 10 steps, each alone in its own context, plain FP64"},
+           "speedup_vs_fp64_one_by_one": rep.env_steps_per_s / one if one > 0 else None,
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -128,6 +128,8 @@ typedef struct {
   long long al_env_updates;   /* AL multiplier updates summed over the envs    */
   long long ccd_limited;      /* line searches that started below alpha = 1    */
   double alpha_sum;           /* accepted line-search steps, summed            */
+  long long accd_iters;       /* ACCD advancement iterations, all pairs        */
+  int accd_iters_max;         /* most ACCD iterations taken by one pair        */
   double ms_total;      /* wall time of the call (host clock), ms            */
 } ipc_step_stats;
 
@@ -150,6 +152,17 @@ ipc_status ipc_destroy(ipc_ctx* ctx);
 
 /* Last error message of this ctx (empty string if none). */
 const char* ipc_last_error(const ipc_ctx* ctx);
+
+/* Run the PCG inner loop (Sec. 4, the block-Jacobi PCG solve of each Newton
+ * iteration) as a CUDA graph: the 16 iterations between two host checks of
+ * the per-env convergence flags (64 kernel launches) are captured on the
+ * ctx stream at the first solve and replayed after that.  Results are the
+ * same as with plain launches.  on = 0 (default) launches kernel by kernel.
+ * The ctx stream must support capture (a created stream, not the legacy
+ * default stream); otherwise ipc_step returns IPC_ECUDA with the reason in
+ * ipc_last_error.  While per-kernel profiling is on, plain launches are
+ * used so that every kernel is timed. */
+ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on);
 
 int ipc_num_envs(const ipc_ctx* ctx);
 ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies,

@@ -6,6 +6,7 @@ Objective (Eq. unified_ipc with the AL term of Eq. unified_ipc_AL):
                      + h^2 kappa_s V_b |A_b^T A_b - I|_F^2]
             + h^2 sum_e V_e Psi(F_e)
             + h^2 kappa sum_k A_k c_k b(d_k)
+            + h^2 sum_k mu lambda_k^n f0(|u_k|)          (lagged friction, when mu > 0)
             + sum_{c driven} [kappa_A/2 |q_c - s_c|_{M_c}^2 - lambda_c^T M_c (q_c - s_c)]
 with xt = x^n + h v^n, yt = y^n + h ydot^n (App. A.2) and the backward-Euler
 velocity update v^{n+1} = (x^{n+1} - x^n) / h.
@@ -34,6 +35,7 @@ import scipy.sparse as sps
 import scipy.sparse.linalg as spla
 
 from . import energy as en
+from . import friction as fr
 from .broadphase import candidates, excluded_object_pairs
 from .ccd import accd_batch
 from .distance import pair_barrier, pair_distance
@@ -175,6 +177,9 @@ class OracleEnv:
                 return np.inf
             Eb, _, _ = pair_barrier(X12, is_ee, h * h * prm.kappa * area, eps, prm.dhat, order=0)
             E += np.sum(Eb)
+        ft = self._friction_terms(x, y, ctx, 0)
+        if ft is not None:
+            E += h * h * float(np.sum(ft[0]))
         return float(E)
 
     def _al_energy(self, x, y, ctx):
@@ -254,6 +259,19 @@ class OracleEnv:
                 c_ = np.broadcast_to(dA[:, None, None, :, :], v.shape)
                 nz = v != 0.0
                 rows.append(r_[nz]); cols.append(c_[nz]); vals.append(v[nz])
+        # lagged friction (its tangent-frame Hessian is PSD as it stands)
+        ft = self._friction_terms(x, y, ctx, 2)
+        if ft is not None:
+            _, Gf, Hf = ft
+            pts_f = ctx["fric"]["pts"]
+            dof = self.cv_dof[pts_f].reshape(-1, 12, 4)
+            w = self.cv_w[pts_f].reshape(-1, 12, 4)
+            np.add.at(g, dof.ravel(), (w * (h * h * Gf)[:, :, None]).ravel())
+            v = w[:, :, :, None, None] * w[:, None, None, :, :] * (h * h * Hf)[:, :, None, :, None]
+            r_ = np.broadcast_to(dof[:, :, :, None, None], v.shape)
+            c_ = np.broadcast_to(dof[:, None, None, :, :], v.shape)
+            nz = v != 0.0
+            rows.append(r_[nz]); cols.append(c_[nz]); vals.append(v[nz])
         H = sps.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                            shape=(self.ndof, self.ndof)).tocsr()
         return g, H
@@ -293,20 +311,49 @@ class OracleEnv:
             ctx["s_x"] = sy[:, :3] + np.einsum("nij,nj->ni", A, self.attach_xbar)
         else:
             ctx["s_x"] = np.zeros((0, 3))
+        ctx["fric"] = self._friction_lagged(x_n, y_n)
         return ctx
+
+    def _friction_lagged(self, x_n, y_n):
+        """Lagged friction data at x^n (friction module docstring), or None."""
+        mu = float(getattr(self.prm, "friction_mu", 0.0))
+        if mu <= 0.0:
+            return None
+        pt, ee = self.static_pairs(x_n, y_n)
+        pts, is_ee, area, eps = self.pair_arrays(pt, ee)
+        if not len(pts):
+            return None
+        Xn = self.contact_positions(x_n, y_n)[pts]
+        W, T, lam, rn = fr.lagged(Xn, is_ee, self.prm.kappa * area, eps, self.prm.dhat)
+        keep = lam > 0.0
+        if not np.any(keep):
+            return None
+        return {"pts": pts[keep], "W": W[keep], "T": T[keep], "lam": lam[keep], "rn": rn[keep],
+                "mu": mu, "eh": float(self.prm.friction_eps_v) * self.prm.dt}
+
+    def _friction_terms(self, x, y, ctx, order):
+        fc = ctx.get("fric")
+        if fc is None:
+            return None
+        X = self.contact_positions(x, y)[fc["pts"]]
+        return fr.pair_friction(X, fc["W"], fc["T"], fc["lam"], fc["rn"], fc["mu"], fc["eh"], order)
 
     def static_pairs(self, x, y):
         Xc = self.contact_positions(x, y)
         pt, ee = candidates(self.sd, Xc, self.prm.dhat, self.excluded)
         return pt, ee
 
-    def step(self, x_n, v_n, y_n, ydot_n, s_y=None):
-        """Advance one time step.  s_y: (nb, 12) body targets (driven rows)."""
+    def step(self, x_n, v_n, y_n, ydot_n, s_y=None, x_start=None, y_start=None):
+        """Advance one time step.  s_y: (nb, 12) body targets (driven rows).
+        Newton starts from (x_n, y_n) as in the paper's step; the tests may
+        pass another feasible starting iterate (x_start, y_start) to check
+        that a candidate end state is a converged point of this step."""
         prm, h = self.prm, self.prm.dt
         if s_y is None:
             s_y = y_n.copy()
         ctx = self.make_ctx(x_n, v_n, y_n, ydot_n, s_y)
-        x, y = x_n.copy(), y_n.copy()
+        x = (x_n if x_start is None else x_start).copy()
+        y = (y_n if y_start is None else y_start).copy()
         st = StepStats()
         has_driven = bool(self.driven_bodies) or len(self.attached) > 0
         converged = False

@@ -207,9 +207,10 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.r = c.take<double>(R3);
   d.z = c.take<double>(R3);
   d.d = c.take<double>(R3);
+  d.d4 = c.take<float4>((size_t)pk.n_rows);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
-  d.pc = c.take<double>(9 * (size_t)pk.n_rows);
+  d.pc = c.take<double>(6 * (size_t)pk.n_rows);
   d.pc_acc = c.take<double>(9 * (size_t)pk.n_rows);
   d.body_pc = c.take<double>(144 * (size_t)pk.n_bodies);
   d.body_pc_acc = c.take<double>(144 * (size_t)pk.n_bodies);
@@ -247,6 +248,10 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
   d.pair_scan = c.take<int>(pk.n_envs + 1);
   d.act_list = c.take<int>(pk.n_pairs_cap);
+  d.act_env = c.take<int>(pk.n_pairs_cap);
+  d.accd_tail = c.take<int4>(pk.n_pairs_cap);
+  d.accd_tail_t = c.take<double>(pk.n_pairs_cap);
+  d.accd_tail_ctl = c.take<unsigned int>(2);
   d.act_count = c.take<int>(1);
   d.cta_part = c.take<double>(4 * (size_t)(pk.n_rows / 128));
   d.env_cnt = c.take<unsigned int>(2 * (size_t)pk.n_envs);
@@ -317,21 +322,70 @@ ipc_status assemble_system(ipc_ctx* ctx) {
   return last_cuda(ctx);
 }
 
+constexpr int kPcgPoll = 16;  // PCG iterations between host checks of the per-env flags
+
+// one PCG iteration over every PCG-active env; returns the launches issued
+int pcg_iteration(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  long long l0 = ctx->launches;
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
+  KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s); });
+  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s); });
+  KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s); });
+  return (int)(ctx->launches - l0);
+}
+
+// Capture kPcgPoll iterations into a graph once per context.  The kernels
+// take the context's device tables by value and every per-step quantity
+// lives in device memory, so the same graph serves every later solve.
+ipc_status capture_pcg(ipc_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = std::string("PCG graph capture: ") + cudaGetErrorString(e) +
+               " (the stream cannot be captured, e.g. the legacy default stream)";
+    return IPC_ECUDA;
+  }
+  long long l0 = ctx->launches;
+  int n = 0;
+  for (int i = 0; i < kPcgPoll; ++i) n += pcg_iteration(ctx);
+  ctx->launches = l0;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(s, &g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->pcg_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->pcg_exec = nullptr;
+    ctx->err = std::string("PCG graph capture: ") + cudaGetErrorString(e);
+    return IPC_ECUDA;
+  }
+  ctx->pcg_exec_launches = n;
+  return IPC_OK;
+}
+
 ipc_status run_pcg(ipc_ctx* ctx) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
-  const int poll = 16;
-  for (int it = 0; it < ctx->prm.pcg_max; ++it) {
-    KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
-    KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s); });
-    KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s); });
-    KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s); });
-    if ((it + 1) % poll == 0) {
-      ipc_status st = sync_flags(ctx);
-      if (st != IPC_OK) return st;
-      if (count_flag(ctx, I_PCG) == 0) break;
+  const bool graph = ctx->graph_on && !ctx->prof_on;
+  for (int it = 0; it < ctx->prm.pcg_max; it += kPcgPoll) {
+    if (graph) {
+      if (!ctx->pcg_exec) {
+        ipc_status st = capture_pcg(ctx);
+        if (st != IPC_OK) return st;
+      }
+      CK(cudaGraphLaunch(ctx->pcg_exec, s));
+      ctx->launches += ctx->pcg_exec_launches;
+    } else {
+      for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx);
     }
+    // envs stop at pcg_max inside k_pcg_update, so a block past it is a no-op
+    ipc_status st = sync_flags(ctx);
+    if (st != IPC_OK) return st;
+    if (count_flag(ctx, I_PCG) == 0) break;
   }
   return last_cuda(ctx);
 }
@@ -465,6 +519,7 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
   if (!ctx) return IPC_EINVAL;
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
   if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
   delete ctx;
@@ -472,6 +527,12 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
 }
 
 const char* ipc_last_error(const ipc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on) {
+  if (!ctx) return IPC_EINVAL;
+  ctx->graph_on = on != 0;
+  return IPC_OK;
+}
 
 int ipc_num_envs(const ipc_ctx* ctx) { return ctx ? ctx->pk.n_envs : 0; }
 
@@ -651,6 +712,8 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     S.newton_env_iters += ei[I_NEWTON];
     S.al_env_updates += ei[I_AL];
     S.ccd_limited += ei[I_CCDCUT];
+    S.accd_iters += ei[I_ACCDIT];
+    S.accd_iters_max = std::max(S.accd_iters_max, ei[I_ACCDMAX]);
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
   }
   (void)newton_done;
@@ -711,8 +774,15 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
   if (vec && hvec) {
     std::vector<double> vr;
     dof_to_rows(ctx, env, vec, vr);
+    // the mat-vec reads the direction d (and its FP32 copy): d = vec, copied
+    // by the direction kernel with z = vec and beta = 0
+    if ((st = upload_rows(ctx, env, d.z, vr)) != IPC_OK) return st;
     if ((st = upload_rows(ctx, env, d.d, vr)) != IPC_OK) return st;
+    const double zero = 0.0;
+    CK(cudaMemcpyAsync(d.env_s + (size_t)env * NUM_SCALARS + S_PBETA, &zero, sizeof(double),
+                       cudaMemcpyHostToDevice, ctx->stream));
     if ((st = select_envs(ctx, {env}, I_PCG)) != IPC_OK) return st;
+    KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, ctx->stream); });
     KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, ctx->stream); });
     KL(ctx, KC_SPMV, [&] { return launch_spmv(d, ctx->stream); });
     if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;

@@ -50,6 +50,8 @@ enum EnvInt {
   I_SEL,          // selected for this ipc_step call
   I_FLAG,         // scratch flag (inverted tet found)
   I_CCDCUT,       // line searches starting below alpha = 1 this step
+  I_ACCDIT,       // ACCD advancement iterations this step (all pairs)
+  I_ACCDMAX,      // most ACCD iterations one pair took this step
   NUM_INTS
 };
 
@@ -91,7 +93,10 @@ struct Dev {
   // state and work (row space: 3 doubles per row)
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
-  double *pc, *pc_acc;          // 9 per row
+  float4* d4;                   // mixed mode: FP32 copy of the PCG direction, 16 B per row
+  void* pc;                     // 6 per row: symmetric inverse of the diagonal block
+                                // (double, or float in mixed mode)
+  double* pc_acc;               // 9 per row
   double *body_pc, *body_pc_acc, *body_g, *body_H, *body_E;  // per body 144 / 144 / 12 / 144 / 1
   void* sell_val;               // n_blocks * 9 (double, or float in mixed mode)
   double *tetG, *tetE;          // 12 / 1 per tet
@@ -111,6 +116,10 @@ struct Dev {
   uint8_t* pair_act;
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
   int* act_list;                 // slots of active (d < dhat) pairs
+  int* act_env;                  // env of each act_list entry
+  int4* accd_tail;               // ACCD pairs left for the warp-parallel phase: (slot, env, iterations, -)
+  double* accd_tail_t;           // their certified time so far
+  unsigned int* accd_tail_ctl;   // [entries, finished CTAs]; zero between launches
   int* act_count;
   double* cta_part;             // 4 per row CTA
   unsigned int* env_cnt;        // last-CTA counters (2 per env)
@@ -140,6 +149,10 @@ struct ipc_ctx {
   double* h_dbl = nullptr;    // pinned read-back (NUM_SCALARS * n_envs doubles)
   int max_bodies = 0;
   std::vector<int> n_cta_env;  // row CTAs per env
+  // CUDA graph of one PCG polling block (ipc_set_graph_mode)
+  bool graph_on = false;
+  cudaGraphExec_t pcg_exec = nullptr;
+  int pcg_exec_launches = 0;
   // profiling
   bool prof_on = false;
   long long launches = 0;

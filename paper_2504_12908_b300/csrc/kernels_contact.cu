@@ -306,7 +306,11 @@ __global__ void k_barrier(Dev d, int flag) {
   bool act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
   d.pair_act[k] = act ? 1 : 0;
   if (!act) continue;
-  d.act_list[atomicAdd(d.act_count, 1)] = k;
+  {
+    int slot = atomicAdd(d.act_count, 1);
+    d.act_list[slot] = k;
+    d.act_env[slot] = e;
+  }
   HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)k * 78;
   for (int p = 0, o = 0; p < 12; ++p)
     for (int q = p; q < 12; ++q) Hs[o++] = (HT)H[p * 12 + q];
@@ -375,8 +379,7 @@ __global__ void k_pair_spmv(Dev d) {
     bool live = false;
     if (i < n_act) {
       k = d.act_list[i];
-      bool valid;
-      e = pair_env(d, k, valid);
+      e = d.act_env[i];
       live = ENVI(d, e, I_PCG) != 0;
     }
     int cvs[4] = {0, 0, 0, 0};
@@ -450,6 +453,40 @@ __global__ void k_pair_spmv(Dev d) {
 }
 
 // ACCD time of impact per swept pair; env bound = min over its pairs
+// ACCD (additive CCD): per swept pair a conservative time of impact; the
+// env's step bound is the minimum over its pairs (S_ACCD, a running min).
+// Phase 1 (one pair per thread): the sequential advancement, at most
+// kAccdSeq iterations.  Pairs still advancing after that (sliding contacts
+// at small distance take ~l_p / d iterations) continue in phase 2, where one
+// warp advances one pair 32 certified intervals at a time.  A pair whose
+// sequential run ends within kAccdSeq iterations gets exactly the
+// sequential result.
+constexpr int kAccdSeq = 64;
+
+struct AccdPair {
+  D3 X[4], P[4];
+  double lp, gap;
+  bool ee;
+};
+
+__device__ __forceinline__ void accd_setup(const Dev& d, int k, double s, AccdPair& a) {
+  int4 v = d.pair_v[k];
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  for (int i = 0; i < 4; ++i) { a.X[i] = ld3(d.cvx, cvs[i]); a.P[i] = ld3(d.cvp, cvs[i]); }
+  a.ee = d.pair_kind[k] == 1;
+  D3 pm = 0.25 * (a.P[0] + a.P[1] + a.P[2] + a.P[3]);
+  double nq[4];
+  for (int i = 0; i < 4; ++i) nq[i] = sqrt(norm2(a.P[i] - pm));
+  a.lp = a.ee ? fmax(nq[0], nq[1]) + fmax(nq[2], nq[3]) : nq[0] + fmax(nq[1], fmax(nq[2], nq[3]));
+  a.gap = s * sqrt(pair_sqdist(a.X, a.ee));
+}
+
+__device__ __forceinline__ double accd_dist_at(const AccdPair& a, double t) {
+  D3 Y[4];
+  for (int i = 0; i < 4; ++i) Y[i] = a.X[i] + t * a.P[i];
+  return sqrt(pair_sqdist(Y, a.ee));
+}
+
 __global__ void k_accd(Dev d) {
   FOR_PAIRS(d, f) {
   int e;
@@ -459,8 +496,92 @@ __global__ void k_accd(Dev d) {
   int cvs[4] = {v.x, v.y, v.z, v.w};
   D3 X[4], P[4];
   for (int i = 0; i < 4; ++i) { X[i] = ld3(d.cvx, cvs[i]); P[i] = ld3(d.cvp, cvs[i]); }
-  double t = accd_toi(X, P, d.pair_kind[k] == 1, d.accd_s, 1.0, d.accd_max);
+  const int seq_cap = min(d.accd_max, kAccdSeq);
+  int its = 0;
+  bool more = false;
+  double t = accd_toi(X, P, d.pair_kind[k] == 1, d.accd_s, 1.0, seq_cap, &its, &ENVS(d, e, S_ACCD), &more);
+  // still advancing after the sequential budget (below t = 1)
+  if (more && d.accd_max > seq_cap) {
+    unsigned slot = atomicAdd(&d.accd_tail_ctl[0], 1u);
+    d.accd_tail[slot] = make_int4(k, e, its, 0);
+    d.accd_tail_t[slot] = t;
+    continue;
+  }
   atomic_min_nonneg(&ENVS(d, e, S_ACCD), t);
+  atomicAdd(&ENVI(d, e, I_ACCDIT), its);
+  atomicMax(&ENVI(d, e, I_ACCDMAX), its);
+  }
+}
+
+// Phase 2, one warp per pair.  From a certified time t with distance
+// d_t >= gap, lane j evaluates the distance at t_j = t + (j + 1) D,
+// D = 1.8 (d_t - gap) / l_p (clamped to t_j <= 1).  |d'| <= l_p, so on
+// [t_{j-1}, t_j] the distance is at least (d_{j-1} + d_j - l_p D) / 2; the
+// warp advances to the end of the longest prefix of intervals whose bound is
+// >= gap.  When even the first interval fails, one sequential ACCD step is
+// taken instead (step 0.9 d_t / l_p, stop if the distance there is below
+// gap).  Each round counts 32 iterations against accd_max.  Guarantee as in
+// the sequential form: no contact on [0, t] and distance >= gap at t.
+__global__ void k_accd_tail(Dev d) {
+  const unsigned n_tail = d.accd_tail_ctl[0];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int n_warps = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned w = warp; w < n_tail; w += n_warps) {
+    int4 ent = d.accd_tail[w];
+    const int k = ent.x, e = ent.y;
+    int its = ent.z;
+    double t = d.accd_tail_t[w];
+    AccdPair a;
+    accd_setup(d, k, d.accd_s, a);
+    double dt = accd_dist_at(a, t);
+    while (t < 1.0 && its < d.accd_max) {
+      const double cap = __shfl_sync(0xffffffffu, *(volatile double*)&ENVS(d, e, S_ACCD), 0);
+      if (t >= cap) break;
+      const double D = 1.8 * (dt - a.gap) / a.lp;
+      const double tj = fmin(1.0, t + (lane + 1) * D);
+      const double dj = accd_dist_at(a, tj);
+      double dprev = __shfl_up_sync(0xffffffffu, dj, 1);
+      double tprev = __shfl_up_sync(0xffffffffu, tj, 1);
+      if (lane == 0) { dprev = dt; tprev = t; }
+      const bool ok = (tj > tprev) ? (0.5 * (dprev + dj - a.lp * (tj - tprev)) >= a.gap) : true;
+      const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+      its += 32;
+      if (bad == 0u) {
+        t = __shfl_sync(0xffffffffu, tj, 31);
+        dt = __shfl_sync(0xffffffffu, dj, 31);
+        continue;
+      }
+      const int first = __ffs(bad) - 1;
+      if (first > 0) {
+        t = __shfl_sync(0xffffffffu, tj, first - 1);
+        dt = __shfl_sync(0xffffffffu, dj, first - 1);
+        continue;
+      }
+      // no interval certified: one sequential step
+      const double tn = fmin(1.0, t + 0.9 * dt / a.lp);
+      const double dn = accd_dist_at(a, tn);
+      if (dn < a.gap) break;
+      t = tn;
+      dt = dn;
+    }
+    if (t >= 1.0) t = 1.0;
+    if (lane == 0) {
+      atomic_min_nonneg(&ENVS(d, e, S_ACCD), t);
+      atomicAdd(&ENVI(d, e, I_ACCDIT), its);
+      atomicMax(&ENVI(d, e, I_ACCDMAX), its);
+    }
+  }
+  // the last CTA to finish clears the list for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned done = atomicAdd(&d.accd_tail_ctl[1], 1u);
+    if (done == gridDim.x - 1) {
+      d.accd_tail_ctl[0] = 0u;
+      d.accd_tail_ctl[1] = 0u;
+      __threadfence();
+    }
   }
 }
 
@@ -562,7 +683,8 @@ int launch_pair_spmv(const Dev& d, cudaStream_t s) {
 int launch_accd(const Dev& d, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
   k_accd<<<PAIR_GRID>>>(d);
-  return 1;
+  k_accd_tail<<<148 * 4, 256, 0, s>>>(d);
+  return 2;
 }
 int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;

@@ -78,7 +78,8 @@ __global__ void k_attach_targets(Dev d, int flag) {
 // ---------------------------------------------------------------------------
 // HT: precision of the Hessian (computed and stored).  The gradient is FP64
 // in both modes: it fixes the converged state.  Positions are differenced in
-// FP64 before F is rounded to HT.
+// FP64 before F is rounded to HT.  (An FP32 gradient was measured: the
+// kernel's time did not change and the mixed-vs-FP64 step error grew.)
 template <class HT>
 __global__ void k_tet(Dev d) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -284,10 +285,15 @@ __global__ void k_precond_rows(Dev d) {
     double det = inv3(M, P);
     if (!(fabs(det) > 0)) { P[0] = P[4] = P[8] = 1.0; P[1] = P[2] = P[3] = P[5] = P[6] = P[7] = 0.0; }
   }
-  for (int c = 0; c < 9; ++c) {
-    d.pc[9 * r + c] = P[c];
-    d.pc_acc[9 * r + c] = 0.0;
-  }
+  // symmetric: [xx, xy, xz, yy, yz, zz], off-diagonals averaged
+  HT* pc = reinterpret_cast<HT*>(d.pc) + 6 * (long long)r;
+  pc[0] = (HT)P[0];
+  pc[1] = (HT)(0.5 * (P[1] + P[3]));
+  pc[2] = (HT)(0.5 * (P[2] + P[6]));
+  pc[3] = (HT)P[4];
+  pc[4] = (HT)(0.5 * (P[5] + P[7]));
+  pc[5] = (HT)P[8];
+  for (int c = 0; c < 9; ++c) d.pc_acc[9 * r + c] = 0.0;
 }
 
 __global__ void k_precond_body(Dev d) {
@@ -306,7 +312,9 @@ __global__ void k_precond_body(Dev d) {
 }
 
 // z = P^{-1} r for row r (body rows read the 4 sub-rows of their body; all of
-// them sit in the same warp)
+// them sit in the same warp).  Gel rows: 6 stored entries of the symmetric
+// 3x3 inverse, in HT; the product is formed in FP64.
+template <class HT>
 __device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
   if (is_body(kr)) {
     int b = d.row_body[r];
@@ -319,13 +327,34 @@ __device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
     return D3{o[0], o[1], o[2]};
   }
   if (kr == ROW_PAD) return D3{0, 0, 0};
-  const double* P = d.pc + 9 * r;
+  const HT* P = reinterpret_cast<const HT*>(d.pc) + 6 * (long long)r;
+  const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
   D3 x = ld3(d.r, r);
-  return D3{P[0] * x.x + P[1] * x.y + P[2] * x.z, P[3] * x.x + P[4] * x.y + P[5] * x.z,
-            P[6] * x.x + P[7] * x.y + P[8] * x.z};
+  return D3{a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z};
 }
 
-// PCG start: p = 0, r = -g, z = P^-1 r, d = z; rz, rr0
+// the direction of column c as the SpMV reads it: FP64 rows in FP64 mode,
+// the 16-byte FP32 copy (one vector load) in mixed mode
+template <class HT> struct DirGather;
+template <> struct DirGather<double> {
+  static __device__ __forceinline__ V3<double> at(const Dev& d, int c) { return ld3(d.d, c); }
+};
+template <> struct DirGather<float> {
+  static __device__ __forceinline__ V3<float> at(const Dev& d, int c) {
+    float4 v = __ldg(d.d4 + c);
+    return V3<float>{v.x, v.y, v.z};
+  }
+};
+
+// the direction d and, in mixed mode, its FP32 copy
+template <class HT>
+__device__ __forceinline__ void store_dir(const Dev& d, int r, D3 v) {
+  st3(d.d, r, v);
+  if (sizeof(HT) == 4) d.d4[r] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f);
+}
+
+// PCG start: p = 0, r = -g, z = P^-1 r, d = z, beta = 0; rz, rr0
+template <class HT>
 __global__ void k_pcg_init(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
@@ -335,12 +364,13 @@ __global__ void k_pcg_init(Dev d) {
   st3(d.r, r, rv);
   st3(d.p, r, D3{0, 0, 0});
   __syncwarp();
-  D3 z = apply_pc(d, r, kr);
+  D3 z = apply_pc<HT>(d, r, kr);
   st3(d.z, r, z);
-  st3(d.d, r, z);
+  store_dir<HT>(d, r, z);
   double vals[2] = {dot(rv, z), dot(rv, rv)};
   double out[2];
   if (env_reduce<2>(d, e, 0, vals, out)) {
+    ENVS(d, e, S_PBETA) = 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR0) = out[1];
     ENVS(d, e, S_RR) = out[1];
@@ -349,28 +379,49 @@ __global__ void k_pcg_init(Dev d) {
   }
 }
 
-// q = A d + qc (SELL-32, one row per thread), qc cleared; d.q reduced
-// HT: matrix precision; the products are accumulated in HT, q and the
-// contact part qc stay FP64.
+// q = A d + qc (SELL-32, one row per thread, U slots in flight per lane),
+// qc cleared; d.q reduced per env -> alpha.
+// HT: matrix precision; the products are accumulated in HT slot by slot in
+// storage order, q, qc and the own-row d of the dot product stay FP64.
 template <class HT>
-__global__ void k_spmv(Dev d) {
+__global__ void __launch_bounds__(128) k_spmv(Dev d) {
+  constexpr int U = sizeof(HT) == 4 ? 4 : 2;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
   int ch = r >> 5, lane = r & 31;
   int slots = d.chunk_slots[ch];
   long long base = d.chunk_ptr[ch];
+  const HT* __restrict__ val = reinterpret_cast<const HT*>(d.sell_val) + base * 9 + lane;
+  const int* __restrict__ colp = d.sell_col + base + lane;
   HT ax = 0, ay = 0, az = 0;
-  const HT* val = reinterpret_cast<const HT*>(d.sell_val);
-  for (int sl = 0; sl < slots; ++sl) {
-    long long b0 = base + (long long)sl * 32;
-    int col = d.sell_col[b0 + lane];
-    const HT* A = val + b0 * 9 + lane;
-    D3 u = ld3(d.d, col);
-    HT ux = (HT)u.x, uy = (HT)u.y, uz = (HT)u.z;
-    ax += A[0] * ux + A[32] * uy + A[64] * uz;
-    ay += A[96] * ux + A[128] * uy + A[160] * uz;
-    az += A[192] * ux + A[224] * uy + A[256] * uz;
+  int sl = 0;
+  for (; sl + U <= slots; sl += U) {
+    int c[U];
+    HT A[U][9];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = colp[(sl + u) * 32];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) A[u][k] = val[(long long)(sl + u) * 288 + k * 32];
+    V3<HT> w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = DirGather<HT>::at(d, c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ax += A[u][0] * w[u].x + A[u][1] * w[u].y + A[u][2] * w[u].z;
+      ay += A[u][3] * w[u].x + A[u][4] * w[u].y + A[u][5] * w[u].z;
+      az += A[u][6] * w[u].x + A[u][7] * w[u].y + A[u][8] * w[u].z;
+    }
+  }
+  for (; sl < slots; ++sl) {
+    int c = colp[sl * 32];
+    const HT* A = val + (long long)sl * 288;
+    V3<HT> w = DirGather<HT>::at(d, c);
+    ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
+    ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
+    az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
   }
   D3 acc = ld3(d.qc, r) + D3{(double)ax, (double)ay, (double)az};
   st3(d.q, r, acc);
@@ -384,6 +435,7 @@ __global__ void k_spmv(Dev d) {
 }
 
 // p += alpha d, r -= alpha q, z = P^-1 r; rz, rr reduced -> beta, stop test
+template <class HT>
 __global__ void k_pcg_update(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
@@ -394,7 +446,7 @@ __global__ void k_pcg_update(Dev d) {
   D3 rv = ld3(d.r, r) - al * ld3(d.q, r);
   st3(d.r, r, rv);
   __syncwarp();
-  D3 z = apply_pc(d, r, kr);
+  D3 z = apply_pc<HT>(d, r, kr);
   st3(d.z, r, z);
   double vals[2] = {dot(rv, z), dot(rv, rv)};
   double out[2];
@@ -410,12 +462,15 @@ __global__ void k_pcg_update(Dev d) {
   }
 }
 
+// d = z + beta d (and its FP32 copy in mixed mode)
+template <class HT>
 __global__ void k_pcg_dir(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
-  st3(d.d, r, ld3(d.z, r) + ENVS(d, e, S_PBETA) * ld3(d.d, r));
+  store_dir<HT>(d, r, ld3(d.z, r) + ENVS(d, e, S_PBETA) * ld3(d.d, r));
 }
+
 
 // ---------------------------------------------------------------------------
 // Newton bookkeeping
@@ -647,6 +702,8 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_ACCEPT) = 0;
     ENVI(d, e, I_OVERFLOW) = 0;
     ENVI(d, e, I_CCDCUT) = 0;
+    ENVI(d, e, I_ACCDIT) = 0;
+    ENVI(d, e, I_ACCDMAX) = 0;
     ENVS(d, e, S_ASUM) = 0.0;
   } else if (what == 1) {
     if (!ENVI(d, e, I_ACTIVE)) return;
@@ -735,14 +792,26 @@ int launch_precond(const Dev& d, cudaStream_t s) {
   k_precond_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
   return 2;
 }
-int launch_pcg_init(const Dev& d, cudaStream_t s) { k_pcg_init<<<ROWGRID>>>(d); return 1; }
+int launch_pcg_init(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_pcg_init<float><<<ROWGRID>>>(d);
+  else k_pcg_init<double><<<ROWGRID>>>(d);
+  return 1;
+}
 int launch_spmv(const Dev& d, cudaStream_t s) {
   if (d.prec) k_spmv<float><<<ROWGRID>>>(d);
   else k_spmv<double><<<ROWGRID>>>(d);
   return 1;
 }
-int launch_pcg_update(const Dev& d, cudaStream_t s) { k_pcg_update<<<ROWGRID>>>(d); return 1; }
-int launch_pcg_dir(const Dev& d, cudaStream_t s) { k_pcg_dir<<<ROWGRID>>>(d); return 1; }
+int launch_pcg_update(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_pcg_update<float><<<ROWGRID>>>(d);
+  else k_pcg_update<double><<<ROWGRID>>>(d);
+  return 1;
+}
+int launch_pcg_dir(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_pcg_dir<float><<<ROWGRID>>>(d);
+  else k_pcg_dir<double><<<ROWGRID>>>(d);
+  return 1;
+}
 int launch_newton_check(const Dev& d, cudaStream_t s) {
   k_newton_rows<<<ROWGRID>>>(d);
   return 1 + launch_pnorm_body(d, s);

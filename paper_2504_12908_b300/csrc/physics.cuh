@@ -617,14 +617,20 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
 // =====================================================================
 // additive CCD
 // =====================================================================
+// t_cap (optional) points at a shared running minimum of the TOIs of other
+// pairs; the advancement stops early once t reaches it.  t only grows, so a
+// pair stopped there cannot lower that minimum, and the minimum over all
+// pairs is the same as with every pair advanced to its own end.
+// *unfinished (optional) is set when the run stopped at max_iter only.
 IPC_D double accd_toi(const D3* X0, const D3* P, bool is_ee, double s, double t_max, int max_iter,
-                      int* iters = nullptr) {
+                      int* iters = nullptr, const double* t_cap = nullptr, bool* unfinished = nullptr) {
   D3 pm = 0.25 * (P[0] + P[1] + P[2] + P[3]);
   double nq[4];
   for (int i = 0; i < 4; ++i) nq[i] = sqrt(norm2(P[i] - pm));
   double lp = is_ee ? fmax(nq[0], nq[1]) + fmax(nq[2], nq[3])
                     : nq[0] + fmax(nq[1], fmax(nq[2], nq[3]));
   if (iters) *iters = 0;
+  if (unfinished) *unfinished = false;
   if (lp == 0.0) return t_max;
   double d0 = sqrt(pair_sqdist(X0, is_ee));
   double gap = s * d0;
@@ -640,7 +646,9 @@ IPC_D double accd_toi(const D3* X0, const D3* P, bool is_ee, double s, double t_
     t = tt;
     if (t >= t_max) return t_max;
     tl = 0.9 * d / lp;
+    if (t_cap && (it & 7) == 7 && t >= *(const volatile double*)t_cap) return t;
   }
+  if (unfinished) *unfinished = true;
   return t;
 }
 

@@ -43,6 +43,7 @@ class ipc_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_trials", C.c_int),
                 ("al_updates", C.c_int), ("max_pairs", C.c_int), ("newton_env_iters", C.c_longlong),
                 ("al_env_updates", C.c_longlong), ("ccd_limited", C.c_longlong), ("alpha_sum", C.c_double),
+                ("accd_iters", C.c_longlong), ("accd_iters_max", C.c_int),
                 ("ms_total", C.c_double)]
 
 
@@ -76,6 +77,7 @@ def lib():
             "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "ipc_set_graph_mode": (i32, [vp, i32]),
             "ipc_debug_eval": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_debug_pairs": (i32, [vp, i32, _dp, _dp, _ip, i32, C.POINTER(i32)]),
             "ipc_debug_newton_dir": (i32, [vp, i32, _dp, C.POINTER(i32)]),
@@ -103,7 +105,7 @@ def lib():
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
-            "ipc_read_gel_surface_all_noalloc",
+            "ipc_read_gel_surface_all_noalloc", "ipc_set_graph_mode",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
             "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
@@ -322,6 +324,11 @@ class Envs:
         self._check(lib().ipc_read_gel_surface_all_noalloc(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
                     "ipc_read_gel_surface_all_noalloc")
         return out
+
+    def set_graph_mode(self, on: bool = True):
+        """Replay the PCG inner loop as a captured CUDA graph (needs a
+        capturable stream: pass stream= a torch.cuda.Stream at creation)."""
+        self._check(lib().ipc_set_graph_mode(self._ctx, 1 if on else 0), "ipc_set_graph_mode")
 
     # ------------------------------------------------------------ profiling
     def profile_enable(self, on: bool = True):

@@ -92,6 +92,8 @@ class SolverParams:
     ee_mollifier: float = 1e-3
     precision: int = 0              # 0 FP64, 1 mixed (FP32 Hessians / mat-vec)
     max_pairs_per_env: int = 0      # candidate-pair capacity per env (0 = default)
+    friction_mu: float = 0.0        # lagged IPC friction coefficient (0 = frictionless)
+    friction_eps_v: float = 1e-3    # static/dynamic velocity threshold, m/s
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""
@@ -126,8 +128,22 @@ def _orient(vx: np.ndarray, tet: list) -> list:
     return tet
 
 
+_GRID_CACHE: dict = {}
+_SPHERE_CACHE: dict = {}
+
+
 def gel_grid(nx: int, ny: int, nz: int, size=(0.02, 0.02, 0.004),
              origin=None, pad_id: int = 0):
+    """Cached front of `_gel_grid` (returns fresh copies)."""
+    key = (nx, ny, nz, tuple(float(v) for v in size), None if origin is None else tuple(float(v) for v in origin))
+    hit = _GRID_CACHE.get(key)
+    if hit is None:
+        hit = _gel_grid(nx, ny, nz, size, origin)
+        _GRID_CACHE[key] = hit
+    return tuple(a.copy() for a in hit)
+
+
+def _gel_grid(nx: int, ny: int, nz: int, size=(0.02, 0.02, 0.004), origin=None):
     """Regular vertex grid, each hexahedron split into 5 tetrahedra.
 
     The split alternates with the parity of (i + j + k) so that face
@@ -172,7 +188,17 @@ def icosphere(level: int, radius: float, center=(0.0, 0.0, 0.0)):
     """Icosahedron subdivided `level` times, vertices projected to the sphere.
 
     level 1/2/3/4 -> 42/162/642/2562 vertices.  Triangles are outward.
+    The unit sphere of each level is built once and scaled.
     """
+    hit = _SPHERE_CACHE.get(level)
+    if hit is None:
+        hit = _unit_icosphere(level)
+        _SPHERE_CACHE[level] = hit
+    verts, tris = hit
+    return verts * radius + np.asarray(center, dtype=np.float64), tris.copy()
+
+
+def _unit_icosphere(level: int):
     t = (1.0 + 5.0 ** 0.5) / 2.0
     v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0),
          (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
@@ -199,13 +225,12 @@ def icosphere(level: int, radius: float, center=(0.0, 0.0, 0.0)):
             ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
             nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
         faces = nf
-    x = np.asarray(verts) * radius + np.asarray(center, dtype=np.float64)
+    x = np.asarray(verts)
     tris = np.asarray(faces, dtype=np.int32)
     # make every face outward (centroid direction test)
-    c0 = np.asarray(center, dtype=np.float64)
     a, b, c = x[tris[:, 0]], x[tris[:, 1]], x[tris[:, 2]]
     n = np.cross(b - a, c - a)
-    flip = np.einsum("ij,ij->i", n, (a + b + c) / 3.0 - c0) < 0
+    flip = np.einsum("ij,ij->i", n, (a + b + c) / 3.0) < 0
     tris[flip] = tris[flip][:, [0, 2, 1]]
     return x, tris
 
@@ -304,6 +329,29 @@ def config2(env: int, n_steps=100) -> Scenario:
     return Scenario(scene=scene, params=params, n_steps=n_steps,
                     delta=_press_slide(depth, slide, gap, half, n_steps - half),
                     precision=1)
+
+
+def config4_request(req: int, n_steps=200) -> Scenario:
+    """One request of the serving stream: a config-2-style env drawn from
+    its own seed (default_rng(5000 + req)) with the same distribution:
+    gel {16,24,32,48}^2 x {4,6}, E ~ U(1e5, 5e5), icosphere level U{1..3},
+    radius U(3, 8) mm, press U(0, 1.5) mm then slide U(-2, 2) mm."""
+    rng = np.random.default_rng(5000 + req)
+    nxy = int(rng.choice([16, 24, 32, 48]))
+    nz = int(rng.choice([4, 6]))
+    E = float(rng.uniform(1e5, 5e5))
+    level = int(rng.integers(1, 4))
+    r = float(rng.uniform(3e-3, 8e-3))
+    depth = rng.uniform(0.0, 1.5e-3)
+    slide = rng.uniform(-2e-3, 2e-3)
+    gap = 5e-5
+    sx, st = icosphere(level, r)
+    sx[:, 2] += gap - sx[:, 2].min()
+    body = Body(rest_x=sx, tris=st, rho=1200.0, kappa_s=1e8, driven=True)
+    scene = _single_pad_scene(nxy, nxy, nz, E, 0.45, 1000.0, [body], f"request[{req}]")
+    half = n_steps // 2
+    return Scenario(scene=scene, params=SolverParams(), n_steps=n_steps,
+                    delta=_press_slide(depth, slide, gap, half, n_steps - half), precision=1)
 
 
 def config3(env: int, n=32, nz=6, n_steps=200, level=4, gap=None) -> Scenario:

@@ -63,3 +63,23 @@ def from_gpu_y(genv, e, oracle_env: OracleEnv, yg):
         A = np.stack([yg[b, 3:6], yg[b, 6:9], yg[b, 9:12]], axis=1)
         y[b, :3] = yg[b, :3] - A @ (genv.body_com(e, b) - oracle_env.bodies[b].com)
     return y
+
+
+def oracle_restart(env: OracleEnv, x_n, v_n, y_n, yd_n, s_y, x, y):
+    """The oracle's step from (x_n, v_n, y_n, yd_n) with Newton (and its AL
+    loop) started at a candidate end state (x, y) instead of at x_n.  A
+    converged end state of the step is (close to) a fixed point of this."""
+    xo, vo, yo, ydo, st = env.step(x_n, v_n, y_n, yd_n, s_y, x_start=x, y_start=y)
+    return xo, yo, st
+
+
+def valid_state(env: OracleEnv, x, y) -> bool:
+    """No touching pair and no inverted tet."""
+    from oracle import distance as ods
+    pt, ee = env.static_pairs(x, y)
+    pa = env.pair_arrays(pt, ee)
+    if len(pa[0]) and ods.pair_distance(env.contact_positions(x, y)[pa[0]], pa[1]).min() <= 0.0:
+        return False
+    T = env.scene.gel_tets
+    F = oen.deformation_gradient(x[T], env.gel.Dm_inv)
+    return bool(np.linalg.det(F).min() > 0.0)

@@ -214,3 +214,37 @@ def test_accd_head_on_point_triangle():
     assert 1.0 - 2.0 * t >= 0.1 - 1e-12
     # no approach: full step
     assert accd_toi(x0, np.ones((4, 3)), False) == 1.0
+
+
+def test_restart_helper_keeps_converged_states_and_moves_others():
+    """The helper the mixed-precision GPU test uses to accept a different
+    minimiser: restarted at the oracle's own end state, Newton stays there;
+    restarted at a perturbed state, it moves back; the validity check
+    rejects an inverted tet."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from gpu_util import all_points, bbox_diag, oracle_restart, valid_state
+    sc = scenes.config0()
+    prm = sc.params.parity()
+    env = OracleEnv(sc.scene, prm)
+    x, v, y, yd = env.rest_state()
+    sy = env.targets_from_delta(sc.delta(0))
+    x1, v1, y1, yd1, st = env.step(x, v, y, yd, sy)
+    assert st.status == 0
+    diag = bbox_diag(env, x, y)
+    xr, yr, st2 = oracle_restart(env, x, v, y, yd, sy, x1, y1)
+    assert st2.status == 0
+    assert np.abs(all_points(env, xr, yr) - all_points(env, x1, y1)).max() <= 1e-6 * diag
+    free = ~sc.scene.pinned
+    xp = x1.copy()
+    xp[free] += 2e-6 * np.random.default_rng(1).standard_normal((int(free.sum()), 3))
+    xr2, yr2, st3 = oracle_restart(env, x, v, y, yd, sy, xp, y1)
+    assert st3.status == 0
+    assert np.abs(all_points(env, xr2, yr2) - all_points(env, x1, y1)).max() <= 1e-6 * diag
+    assert np.abs(xp - x1).max() > 1e-6
+    assert valid_state(env, x1, y1)
+    xb = x1.copy()
+    t = sc.scene.gel_tets[0]
+    xb[t[0]] = xb[t[1]] + (xb[t[1]] - xb[t[0]])            # fold one tet over
+    assert not valid_state(env, xb, y1)

@@ -1,0 +1,66 @@
+"""Continuous batching on the GPU: requests admitted into overlapping
+cohorts give, for every request, the same end state as that request run
+alone in its own context (within the mixed-precision tolerance, 1e-4 of the
+bounding-box diagonal)."""
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_12908_b300 import ipc  # noqa: E402
+from paper_2504_12908_b300.build import build  # noqa: E402
+from paper_2504_12908_b300.serving import GpuEngine, Request, Server  # noqa: E402
+
+build()
+
+
+def _requests():
+    scs = [scenes.small_contact_scene(body="sphere", level=1, depth=2e-4, n_steps=5),
+           scenes.config0(),
+           scenes.small_contact_scene(body="cube", depth=1e-4, n_steps=4),
+           scenes.config2(1),
+           scenes.small_contact_scene(body="sphere", level=2, depth=3e-4, n_steps=6),
+           scenes.config4_request(7, n_steps=6)]
+    steps = [5, 6, 4, 6, 6, 6]
+    arrival = [0.0, 0.0, 0.02, 0.04, 0.06, 0.08]
+    reqs = [Request(rid=i, scene=sc.scene, delta=sc.delta, n_steps=steps[i], arrival=arrival[i])
+            for i, sc in enumerate(scs)]
+    return reqs
+
+
+def _alone(req, prm):
+    g = ipc.Envs([req.scene], prm)
+    for k in range(req.n_steps):
+        t = g.rest_y(0)
+        t[:, :3] += np.asarray(req.delta(k)).reshape(-1, 3)[: t.shape[0]]
+        g.set_targets(0, t)
+        st, _ = g.step()
+        assert st[0] == 0
+    x, _, y, _ = g.get_state(0)
+    g.close()
+    return x, y
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_each_request_is_the_same_alone_and_in_the_mix(graphs):
+    prm = scenes.SolverParams()
+    prm.precision = 1
+    reqs = _requests()
+    srv = Server(GpuEngine(prm, graphs=graphs), max_cohort=2, max_cohorts=3, mem_reserve=1 << 30)
+    rep = srv.run(reqs)
+    assert rep.completed == len(reqs) and rep.backlog == 0
+    assert rep.cohorts >= 3
+    assert rep.env_steps == sum(r.n_steps for r in reqs)
+    for r in reqs:
+        res = rep.results[r.rid]
+        assert res.status == 0 and res.steps == r.n_steps
+        xa, ya = _alone(r, prm)
+        diag = float(np.linalg.norm(xa.max(0) - xa.min(0)))
+        assert np.abs(res.final_x - xa).max() <= 1e-4 * diag, r.rid
+        assert np.abs(res.final_y[:, :3] - ya[:, :3]).max() <= 1e-4 * diag, r.rid
