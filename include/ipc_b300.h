@@ -94,6 +94,9 @@ typedef struct {
                              Hessians, assembly and PCG mat-vec; FP64
                              distances, CCD, energies, residuals)            */
   int max_pairs_per_env;  /* candidate-pair capacity per env (0 = default)  */
+  double friction_mu;     /* lagged IPC friction coefficient mu (App. A.3,
+                             D_k = mu lambda_k f0(|u_k|)); 0 = frictionless  */
+  double friction_eps_v;  /* static / dynamic threshold eps_v, m/s (1e-3)   */
 } ipc_params;
 
 /* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
@@ -231,6 +234,59 @@ ipc_status ipc_read_gel_surface_all(ipc_ctx* ctx, double* out_xyz, size_t capaci
  * Synchronises the ctx stream. */
 ipc_status ipc_read_gel_surface_all_noalloc(ipc_ctx* ctx, double* out_xyz, size_t capacity_rows,
                                             size_t* rows_written);
+
+/* ---- tactile outputs (Sec. 4.2) ------------------------------------------
+ * Read off the deformed coated surface after a step.  The paper gives no
+ * sensor model; the library uses an orthographic sensor on one gel pad:
+ * origin on the pad's rest contact face (a corner of the image), unit
+ * in-plane axes u and v, unit normal pointing out of the coated face, pixel
+ * (r, c) centred at origin + (c + 1/2) pitch u + (r + 1/2) pitch v.  It looks
+ * through the gel along +normal: each pixel shows the front-face triangle
+ * (a coated boundary triangle of that pad whose rest outward normal has a
+ * normal-component above 1/2) with the smallest height h = (x - origin).normal
+ * at the pixel centre.  depth = -h (0 at rest, positive where pressed in),
+ * linearly interpolated over the triangle; normal = the triangle's deformed
+ * outward unit normal; pixels nothing covers: hit 0, depth 0, normal 0. */
+typedef struct {
+  int env;                /* env index                                       */
+  int pad;                /* gel pad id (pad_id of its vertices; 0 if none)  */
+  double origin[3];       /* corner of the image on the rest contact face, m  */
+  double axis_u[3];       /* unit, along image columns                       */
+  double axis_v[3];       /* unit, along image rows                          */
+  double normal[3];       /* unit, out of the coated face                    */
+  double pitch;           /* pixel size, m                                   */
+} ipc_sensor;
+
+/* Global rows of gel vertices (user vertex ids of one env) for the device
+ * calls below.  Host only.  IPC_EINVAL for an id outside the env. */
+ipc_status ipc_gel_vertex_rows(const ipc_ctx* ctx, int env, int n, const int32_t* verts, int32_t* rows_out);
+
+/* Front-face triangles of a sensor as global row triples [n][3] (host only,
+ * from the rest mesh; call once per sensor).  rows_out may be NULL to count;
+ * *n_out receives the count; IPC_EOVERFLOW if it exceeds capacity. */
+ipc_status ipc_sensor_triangles(const ipc_ctx* ctx, const ipc_sensor* sensor, int32_t* rows_out, int capacity,
+                                int* n_out);
+
+/* Depth / normal / hit maps of n_sensors sensors, all height x width, from
+ * the ctx's current positions, on the ctx stream (asynchronous).  Device
+ * buffers, caller-owned: frames [n_sensors][13] (origin, axis_u, axis_v,
+ * normal, pitch), tri_off [n_sensors + 1] (prefix offsets into tri_rows),
+ * tri_rows [n_tri_total][3] (from ipc_sensor_triangles), keys scratch
+ * [n_sensors][height][width] (uint64), depth [n_sensors][height][width]
+ * (double), normal [..][3] (double, may be NULL), hit (uint8, may be NULL).
+ * A pixel's winner is the smallest (FP32 height, triangle index) key, so the
+ * result does not depend on thread order; depth and normal are FP64. */
+ipc_status ipc_tactile_maps_device(ipc_ctx* ctx, int n_sensors, int height, int width, const double* frames,
+                                   const int32_t* tri_off, const int32_t* tri_rows, int n_tri_total,
+                                   unsigned long long* keys, double* depth, double* normal, uint8_t* hit);
+
+/* Marker positions p = sum_u alpha_u x_u and flows p - rest (Sec. 4.2,
+ * Markers) for n markers on coated triangles, from the ctx's current
+ * positions, on the ctx stream.  Device buffers: rows [n][3] global rows
+ * (ipc_gel_vertex_rows), bary [n][3], rest [n][3] (may be NULL), pos [n][3],
+ * flow [n][3] (may be NULL; needs rest). */
+ipc_status ipc_markers_device(ipc_ctx* ctx, int n, const int32_t* rows, const double* bary, const double* rest,
+                              double* pos, double* flow);
 
 /* ---- diagnostics (used by the parity tests; not needed to step) -------- */
 

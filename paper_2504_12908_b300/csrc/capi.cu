@@ -119,6 +119,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.accd_s = prm.accd_s;
   d.al_kappa = prm.al_kappa;
   d.ee_moll = prm.ee_mollifier;
+  d.fr_mu = prm.friction_mu;
+  d.fr_eh = prm.friction_eps_v * prm.dt;
   d.newton_max = prm.newton_max;
   d.pcg_max = prm.pcg_max;
   d.ls_max = prm.ls_max;
@@ -249,6 +251,17 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_scan = c.take<int>(pk.n_envs + 1);
   d.act_list = c.take<int>(pk.n_pairs_cap);
   d.act_env = c.take<int>(pk.n_pairs_cap);
+  const size_t nfr = prm.friction_mu > 0.0 ? pk.n_pairs_cap : 0;
+  d.fr_v = c.take<int4>(nfr);
+  d.fr_w = c.take<double>(4 * nfr);
+  d.fr_T = c.take<double>(6 * nfr);
+  d.fr_rn = c.take<double>(3 * nfr);
+  d.fr_ml = c.take<double>(nfr);
+  d.fr_S = c.take<double>(6 * nfr);
+  d.fr_E = c.take<double>(nfr);
+  d.fr_list = c.take<int>(nfr);
+  d.fr_list_env = c.take<int>(nfr);
+  d.fr_count = c.take<int>(1);
   d.accd_tail = c.take<int4>(pk.n_pairs_cap);
   d.accd_tail_t = c.take<double>(pk.n_pairs_cap);
   d.accd_tail_ctl = c.take<unsigned int>(2);
@@ -305,7 +318,9 @@ ipc_status last_cuda(ipc_ctx* ctx) {
 }
 
 // ---- the assembled Newton system at the current iterate of active envs
-ipc_status assemble_system(ipc_ctx* ctx) {
+// lag_friction: the state is x^n (first Newton iteration of a step): record
+// the lagged friction data from this iteration's static pairs
+ipc_status assemble_system(ipc_ctx* ctx, bool lag_friction) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_ACTIVE, false, s); });
@@ -313,7 +328,9 @@ ipc_status assemble_system(ipc_ctx* ctx) {
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); });
   KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
+  if (lag_friction) KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s); });
   KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s); });
+  KL(ctx, KC_BARRIER, [&] { return launch_fric_assemble(d, s); });
   KL(ctx, KC_TET, [&] { return launch_tet(d, s); });
   KL(ctx, KC_BODY, [&] { return launch_body(d, s); });
   KL(ctx, KC_ASSEMBLE, [&] { return launch_assemble(d, s); });
@@ -330,6 +347,7 @@ int pcg_iteration(ipc_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   long long l0 = ctx->launches;
   KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s); });
   KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s); });
   KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s); });
   KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s); });
@@ -456,6 +474,8 @@ void ipc_default_params(ipc_params* p) {
   p->ee_mollifier = 1e-3;
   p->precision = 0;
   p->max_pairs_per_env = 0;
+  p->friction_mu = 0.0;
+  p->friction_eps_v = 1e-3;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
@@ -667,7 +687,7 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
   int newton_done = 0;
   for (int it = 0; it < ctx->prm.newton_max; ++it) {
     KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
-    if ((st = assemble_system(ctx)) != IPC_OK) return st;
+    if ((st = assemble_system(ctx, it == 0)) != IPC_OK) return st;
     if ((st = run_pcg(ctx)) != IPC_OK) return st;
     KL(ctx, KC_NEWTON, [&] { return launch_newton_check(d, s); });
     KL(ctx, KC_NEWTON, [&] { return launch_newton_decide(d, s); });
@@ -755,7 +775,7 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
   const Dev& d = ctx->dev;
   ipc_status st;
   if ((st = begin_single(ctx, env)) != IPC_OK) return st;
-  if ((st = assemble_system(ctx)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx, true)) != IPC_OK) return st;
   std::vector<double> rows;
   size_t nd = 3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies;
   if (grad) {
@@ -784,6 +804,7 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
     if ((st = select_envs(ctx, {env}, I_PCG)) != IPC_OK) return st;
     KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, ctx->stream); });
     KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, ctx->stream); });
+    KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, ctx->stream); });
     KL(ctx, KC_SPMV, [&] { return launch_spmv(d, ctx->stream); });
     if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
     if ((st = last_cuda(ctx)) != IPC_OK) return st;
@@ -798,7 +819,7 @@ ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters
   if (check_env(ctx, env) != IPC_OK || !p) return IPC_EINVAL;
   ipc_status st;
   if ((st = begin_single(ctx, env)) != IPC_OK) return st;
-  if ((st = assemble_system(ctx)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx, true)) != IPC_OK) return st;
   if ((st = run_pcg(ctx)) != IPC_OK) return st;
   if ((st = sync_flags(ctx)) != IPC_OK) return st;
   if (pcg_iters) *pcg_iters = ctx->h_int[env * NUM_INTS + I_PCGIT];

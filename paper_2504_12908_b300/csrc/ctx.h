@@ -52,6 +52,7 @@ enum EnvInt {
   I_CCDCUT,       // line searches starting below alpha = 1 this step
   I_ACCDIT,       // ACCD advancement iterations this step (all pairs)
   I_ACCDMAX,      // most ACCD iterations one pair took this step
+  I_NFRIC,        // lagged friction records of this step
   NUM_INTS
 };
 
@@ -62,6 +63,7 @@ struct Dev {
   double h, grav[3], dhat, kappa, newton_tol, pcg_tol, accd_s, al_kappa, ee_moll;
   int newton_max, pcg_max, ls_max, accd_max, al_max;
   int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
+  double fr_mu, fr_eh;          // friction coefficient; eps_v * h (fr_mu = 0: no friction)
   // static tables
   const int *env_row_off, *env_tet_off, *env_cv_off, *env_tri_off, *env_edge_off, *env_obj_off,
       *env_body_off, *env_chunk_off, *env_coated_off, *env_pair_cap, *env_pair_off;
@@ -117,6 +119,11 @@ struct Dev {
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
   int* act_list;                 // slots of active (d < dhat) pairs
   int* act_env;                  // env of each act_list entry
+  // lagged friction records (segments like the pair list, I_NFRIC per env)
+  int4* fr_v;                    // contact points of the pair
+  double *fr_w, *fr_T, *fr_rn;   // closest-point weights (4), tangent basis (6), r at x^n (3)
+  double *fr_ml, *fr_S, *fr_E;   // mu lambda; h^2 T M T^T (6, symmetric); energy
+  int *fr_list, *fr_list_env, *fr_count;  // compact list of this step's records
   int4* accd_tail;               // ACCD pairs left for the warp-parallel phase: (slot, env, iterations, -)
   double* accd_tail_t;           // their certified time so far
   unsigned int* accd_tail_ctl;   // [entries, finished CTAs]; zero between launches

@@ -15,6 +15,11 @@ int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s);
 int launch_barrier(const Dev& d, int flag, cudaStream_t s);
 int launch_pair_spmv(const Dev& d, cudaStream_t s);
 int launch_accd(const Dev& d, cudaStream_t s);
+// lagged friction (no launches when friction_mu = 0)
+int launch_fric_setup(const Dev& d, cudaStream_t s);
+int launch_fric_assemble(const Dev& d, cudaStream_t s);
+int launch_fric_spmv(const Dev& d, cudaStream_t s);
+int launch_fric_energy(const Dev& d, int use_alpha, cudaStream_t s);
 int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s);
 int launch_min_dist(const Dev& d, int flag, cudaStream_t s);
 int launch_pnorm_body(const Dev& d, cudaStream_t s);

@@ -585,6 +585,209 @@ __global__ void k_accd_tail(Dev d) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lagged friction (App. A.3): the objective carries h^2 sum_k mu lambda_k^n
+// f0(|u_k|), f0' = f1 = -y^2/(eps_v h)^2 + 2 y/(eps_v h) below eps_v h, 1 above.
+// Lagged at x^n for every static pair within dhat: the closest-point weights
+// w (r = sum_i w_i x_i, the difference of the closest points), the tangent
+// basis T of the plane normal to r (first axis: the coordinate axis least
+// aligned with r, made orthogonal), lambda = kappa A c |b'(d)| (c: edge-edge
+// mollifier) and r(x^n).  u = T^T (r(x) - r(x^n)).  In the tangent frame the
+// Hessian mu lambda [g I + g'/y u u^T], g = f1/y, has eigenvalues g and f1',
+// both >= 0: no projection.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fr_f0(double y, double eh) {
+  return y >= eh ? y : (-y * y * y / (3.0 * eh * eh) + y * y / eh + eh / 3.0);
+}
+__device__ __forceinline__ double fr_g(double y, double eh) {  // f1(y) / y
+  return y >= eh ? 1.0 / y : (-y / (eh * eh) + 2.0 / eh);
+}
+__device__ __forceinline__ double fr_dg_y(double y, double eh) {  // g'(y) / y
+  if (!(y > 0.0)) return 0.0;
+  return y >= eh ? -1.0 / (y * y * y) : -1.0 / (eh * eh * y);
+}
+
+__device__ void fr_basis(D3 n, D3& t1, D3& t2) {
+  double an[3] = {fabs(n.x), fabs(n.y), fabs(n.z)};
+  int k = 0;
+  if (an[1] < an[k]) k = 1;
+  if (an[2] < an[k]) k = 2;
+  D3 a{k == 0 ? 1.0 : 0.0, k == 1 ? 1.0 : 0.0, k == 2 ? 1.0 : 0.0};
+  t1 = a - dot(a, n) * n;
+  t1 = (1.0 / sqrt(norm2(t1))) * t1;
+  t2 = cross(n, t1);
+}
+
+// the 4 contact points of a record at positions cvx + alpha cvp
+__device__ __forceinline__ void fr_points(const Dev& d, int4 v, double alpha, D3* X) {
+  int cvs[4] = {v.x, v.y, v.z, v.w};
+  for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]) + alpha * ld3(d.cvp, cvs[i]);
+}
+
+// u = T^T (sum_i w_i X_i - r_n)
+__device__ __forceinline__ void fr_u(const Dev& d, int j, const D3* X, double& u0, double& u1, D3& t1, D3& t2) {
+  const double* w = d.fr_w + 4 * (long long)j;
+  D3 s = w[0] * X[0] + w[1] * X[1] + w[2] * X[2] + w[3] * X[3] - ld3(d.fr_rn, j);
+  const double* T = d.fr_T + 6 * (long long)j;
+  t1 = D3{T[0], T[1], T[2]};
+  t2 = D3{T[3], T[4], T[5]};
+  u0 = dot(t1, s);
+  u1 = dot(t2, s);
+}
+
+__global__ void k_fric_reset(Dev d) { *d.fr_count = 0; }
+
+// Newton iteration 0 (x = x^n): one record per static pair within dhat.
+__global__ void k_fric_setup(Dev d) {
+  FOR_PAIRS(d, f) {
+  int e;
+  int k = pair_at(d, f, e);
+  if (!ENVI(d, e, I_ACTIVE)) continue;
+  int4 v = d.pair_v[k];
+  D3 X[4];
+  fr_points(d, v, 0.0, X);
+  const bool ee = d.pair_kind[k] == 1;
+  Closest cl;
+  classify(X, ee, cl);
+  const double dist = sqrt(cl.D);
+  if (!(dist > 0.0) || dist >= d.dhat) continue;
+  double c = 1.0;
+  if (ee) {
+    const double xm = ee_cross2(X, nullptr, nullptr), eps = d.pair_eps[k];
+    if (xm < eps) c = (-xm / eps + 2.0) * xm / eps;
+  }
+  double b, b1, b2;
+  barrier_d(dist, d.dhat, b, b1, b2);
+  const double lam = d.pair_w[k] / (d.h * d.h) * c * fabs(b1);  // pair_w = h^2 kappa A
+  if (!(lam > 0.0)) continue;
+  int slot = atomicAdd(&ENVI(d, e, I_NFRIC), 1);
+  if (slot >= d.env_pair_cap[e]) {
+    ENVI(d, e, I_OVERFLOW) = 1;
+    continue;
+  }
+  const int j = d.env_pair_off[e] + slot;
+  d.fr_v[j] = v;
+  for (int i = 0; i < 4; ++i) d.fr_w[4 * (long long)j + i] = cl.w[i];
+  D3 t1, t2;
+  fr_basis((1.0 / dist) * cl.r, t1, t2);
+  double* T = d.fr_T + 6 * (long long)j;
+  T[0] = t1.x; T[1] = t1.y; T[2] = t1.z; T[3] = t2.x; T[4] = t2.y; T[5] = t2.z;
+  st3(d.fr_rn, j, cl.r);
+  d.fr_ml[j] = d.fr_mu * lam;
+  int li = atomicAdd(d.fr_count, 1);
+  d.fr_list[li] = j;
+  d.fr_list_env[li] = e;
+  }
+}
+
+#define FOR_FRIC(d, li) for (int li = blockIdx.x * blockDim.x + threadIdx.x, _nf = *(d).fr_count; li < _nf; \
+                             li += gridDim.x * blockDim.x)
+
+// Each Newton iteration: gradient (into the contact accumulator qc, like the
+// barrier), the 3x3 matrix S = h^2 mu lambda T M T^T of the record, and the
+// preconditioner blocks w_i w_j S.
+__global__ void k_fric_assemble(Dev d) {
+  FOR_FRIC(d, li) {
+  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  if (!ENVI(d, e, I_ACTIVE)) continue;
+  const int4 v = d.fr_v[j];
+  const int cvs[4] = {v.x, v.y, v.z, v.w};
+  D3 X[4];
+  fr_points(d, v, 0.0, X);
+  double u0, u1;
+  D3 t1, t2;
+  fr_u(d, j, X, u0, u1, t1, t2);
+  const double y = sqrt(u0 * u0 + u1 * u1);
+  const double sc = d.h * d.h * d.fr_ml[j];
+  const double g = fr_g(y, d.fr_eh), gy = fr_dg_y(y, d.fr_eh);
+  const D3 Tu = u0 * t1 + u1 * t2;
+  const double* w = d.fr_w + 4 * (long long)j;
+  for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], (sc * g * w[i]) * Tu);
+  // M = g I + gy u u^T (2x2) -> S = sc T M T^T = sc (g (t1 t1^T + t2 t2^T) + gy Tu Tu^T)
+  double S[3][3];
+  const double ta[3] = {t1.x, t1.y, t1.z}, tb[3] = {t2.x, t2.y, t2.z}, tu[3] = {Tu.x, Tu.y, Tu.z};
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) S[a][c] = sc * (g * (ta[a] * ta[c] + tb[a] * tb[c]) + gy * tu[a] * tu[c]);
+  double* Sp = d.fr_S + 6 * (long long)j;
+  Sp[0] = S[0][0]; Sp[1] = S[0][1]; Sp[2] = S[0][2]; Sp[3] = S[1][1]; Sp[4] = S[1][2]; Sp[5] = S[2][2];
+  for (int i = 0; i < 4; ++i) {
+    int cv = cvs[i];
+    if (d.cv_body[cv] >= 0) continue;
+    int row = d.cv_row[cv];
+    if (d.row_kind[row] == ROW_PINNED) continue;
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) atomicAdd(d.pc_acc + 9 * row + 3 * a + c, w[i] * w[i] * S[a][c]);
+  }
+  int done_body[4] = {-1, -1, -1, -1};
+  for (int i = 0; i < 4; ++i) {
+    int b = d.cv_body[cvs[i]];
+    if (b < 0) continue;
+    bool seen = false;
+    for (int m = 0; m < i; ++m) seen |= (done_body[m] == b);
+    done_body[i] = b;
+    if (seen) continue;
+    // body blocks: sum over points m, n on b of J_m^T (w_m w_n S) J_n
+    double wv[4][4];
+    bool on[4];
+    for (int m = 0; m < 4; ++m) {
+      on[m] = d.cv_body[cvs[m]] == b;
+      D3 xb = ld3(d.cv_xbar, cvs[m]);
+      wv[m][0] = w[m]; wv[m][1] = w[m] * xb.x; wv[m][2] = w[m] * xb.y; wv[m][3] = w[m] * xb.z;
+    }
+    for (int kk = 0; kk < 4; ++kk)
+      for (int ll = 0; ll < 4; ++ll) {
+        double cw = 0.0;
+        for (int m = 0; m < 4; ++m) {
+          if (!on[m]) continue;
+          for (int n = 0; n < 4; ++n)
+            if (on[n]) cw += wv[m][kk] * wv[n][ll];
+        }
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, cw * S[a][c]);
+      }
+  }
+  }
+}
+
+// PCG mat-vec: q_c += w_i S (sum_j w_j d_j) per record (pinned gel rows read
+// as zero and are never written).
+__global__ void k_fric_spmv(Dev d) {
+  FOR_FRIC(d, li) {
+  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  if (!ENVI(d, e, I_PCG)) continue;
+  const int4 v = d.fr_v[j];
+  const int cvs[4] = {v.x, v.y, v.z, v.w};
+  const double* w = d.fr_w + 4 * (long long)j;
+  D3 a{0, 0, 0};
+  for (int i = 0; i < 4; ++i) {
+    int cv = cvs[i], row = d.cv_row[cv];
+    D3 u;
+    if (d.cv_body[cv] < 0) u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
+    else u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+    a = a + w[i] * u;
+  }
+  const double* S = d.fr_S + 6 * (long long)j;
+  D3 t{S[0] * a.x + S[1] * a.y + S[2] * a.z, S[1] * a.x + S[3] * a.y + S[4] * a.z,
+       S[2] * a.x + S[4] * a.y + S[5] * a.z};
+  for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], w[i] * t);
+  }
+}
+
+// line-search energy of each record: h^2 mu lambda f0(|u|) at x + alpha p
+__global__ void k_fric_energy(Dev d, int use_alpha) {
+  FOR_FRIC(d, li) {
+  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  if (!ENVI(d, e, I_LS)) continue;
+  const double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
+  D3 X[4];
+  fr_points(d, d.fr_v[j], a, X);
+  double u0, u1;
+  D3 t1, t2;
+  fr_u(d, j, X, u0, u1, t1, t2);
+  d.fr_E[j] = d.h * d.h * d.fr_ml[j] * fr_f0(sqrt(u0 * u0 + u1 * u1), d.fr_eh);
+  }
+}
+
 // barrier energy of each swept pair at x + alpha p (+inf if touching)
 __global__ void k_pair_energy(Dev d, int use_alpha) {
   FOR_PAIRS(d, f) {
@@ -678,6 +881,27 @@ int launch_pair_spmv(const Dev& d, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
   if (d.prec) k_pair_spmv<float><<<PAIR_GRID>>>(d);
   else k_pair_spmv<double><<<PAIR_GRID>>>(d);
+  return 1;
+}
+int launch_fric_setup(const Dev& d, cudaStream_t s) {
+  if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
+  k_fric_reset<<<1, 1, 0, s>>>(d);
+  k_fric_setup<<<PAIR_GRID>>>(d);
+  return 2;
+}
+int launch_fric_assemble(const Dev& d, cudaStream_t s) {
+  if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
+  k_fric_assemble<<<PAIR_GRID>>>(d);
+  return 1;
+}
+int launch_fric_spmv(const Dev& d, cudaStream_t s) {
+  if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
+  k_fric_spmv<<<PAIR_GRID>>>(d);
+  return 1;
+}
+int launch_fric_energy(const Dev& d, int use_alpha, cudaStream_t s) {
+  if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
+  k_fric_energy<<<PAIR_GRID>>>(d, use_alpha);
   return 1;
 }
 int launch_accd(const Dev& d, cudaStream_t s) {

@@ -624,6 +624,10 @@ __global__ void k_env_energy(Dev d, int which) {
   for (int b = d.env_body_off[e] + threadIdx.x; b < d.env_body_off[e + 1]; b += blockDim.x) s += d.body_E[b];
   int np = min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);
   for (int k = threadIdx.x; k < np; k += blockDim.x) s += d.pair_E[d.env_pair_off[e] + k];
+  if (d.fr_mu > 0.0) {
+    int nf = min(ENVI(d, e, I_NFRIC), d.env_pair_cap[e]);
+    for (int k = threadIdx.x; k < nf; k += blockDim.x) s += d.fr_E[d.env_pair_off[e] + k];
+  }
   s = block_sum(s, sh);
   if (threadIdx.x == 0) {
     if (!(s == s)) s = INFINITY;
@@ -704,6 +708,7 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_CCDCUT) = 0;
     ENVI(d, e, I_ACCDIT) = 0;
     ENVI(d, e, I_ACCDMAX) = 0;
+    ENVI(d, e, I_NFRIC) = 0;
     ENVS(d, e, S_ASUM) = 0.0;
   } else if (what == 1) {
     if (!ENVI(d, e, I_ACTIVE)) return;
@@ -825,6 +830,7 @@ int launch_energy(const Dev& d, int use_alpha, int which, cudaStream_t s) {
   k_energy_row<<<ROWGRID>>>(d, use_alpha);
   if (d.n_bodies) { k_energy_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d, use_alpha); ++n; }
   n += launch_pair_energy(d, use_alpha, s);
+  n += launch_fric_energy(d, use_alpha, s);
   k_env_energy<<<d.n_envs, 256, 0, s>>>(d, which);
   return n;
 }

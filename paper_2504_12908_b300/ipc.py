@@ -29,7 +29,8 @@ class ipc_params(C.Structure):
                 ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double), ("newton_max", C.c_int),
                 ("pcg_max", C.c_int), ("ls_max", C.c_int), ("accd_max", C.c_int), ("accd_s", C.c_double),
                 ("al_kappa", C.c_double), ("al_max", C.c_int), ("ee_mollifier", C.c_double),
-                ("precision", C.c_int), ("max_pairs_per_env", C.c_int)]
+                ("precision", C.c_int), ("max_pairs_per_env", C.c_int), ("friction_mu", C.c_double),
+                ("friction_eps_v", C.c_double)]
 
 
 class ipc_scene_desc(C.Structure):
@@ -37,6 +38,11 @@ class ipc_scene_desc(C.Structure):
                 ("pinned", _up), ("attach_body", _ip), ("E", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
                 ("n_bodies", C.c_int), ("body_nv", _ip), ("body_rest_x", _dp), ("body_nt", _ip),
                 ("body_tris", _ip), ("body_rho", _dp), ("body_kappa_s", _dp), ("body_driven", _up)]
+
+
+class ipc_sensor(C.Structure):
+    _fields_ = [("env", C.c_int), ("pad", C.c_int), ("origin", C.c_double * 3), ("axis_u", C.c_double * 3),
+                ("axis_v", C.c_double * 3), ("normal", C.c_double * 3), ("pitch", C.c_double)]
 
 
 class ipc_step_stats(C.Structure):
@@ -78,6 +84,10 @@ def lib():
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_set_graph_mode": (i32, [vp, i32]),
+            "ipc_gel_vertex_rows": (i32, [vp, i32, i32, _ip, _ip]),
+            "ipc_sensor_triangles": (i32, [vp, C.POINTER(ipc_sensor), _ip, i32, C.POINTER(i32)]),
+            "ipc_tactile_maps_device": (i32, [vp, i32, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp]),
+            "ipc_markers_device": (i32, [vp, i32, vp, vp, vp, vp, vp]),
             "ipc_debug_eval": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_debug_pairs": (i32, [vp, i32, _dp, _dp, _ip, i32, C.POINTER(i32)]),
             "ipc_debug_newton_dir": (i32, [vp, i32, _dp, C.POINTER(i32)]),
@@ -105,7 +115,8 @@ def lib():
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
-            "ipc_read_gel_surface_all_noalloc", "ipc_set_graph_mode",
+            "ipc_read_gel_surface_all_noalloc", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
+            "ipc_tactile_maps_device", "ipc_markers_device",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
             "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
@@ -136,6 +147,8 @@ def params_from(p) -> ipc_params:
         setattr(out, name, int(getattr(p, name)))
     out.precision = int(getattr(p, "precision", 0))
     out.max_pairs_per_env = int(getattr(p, "max_pairs_per_env", 0))
+    out.friction_mu = float(getattr(p, "friction_mu", 0.0))
+    out.friction_eps_v = float(getattr(p, "friction_eps_v", 1e-3))
     return out
 
 
@@ -324,6 +337,87 @@ class Envs:
         self._check(lib().ipc_read_gel_surface_all_noalloc(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
                     "ipc_read_gel_surface_all_noalloc")
         return out
+
+    # ------------------------------------------------------------ tactile outputs
+    def gel_vertex_rows(self, env: int, verts) -> np.ndarray:
+        v = np.ascontiguousarray(verts, dtype=np.int32).ravel()
+        out = np.zeros_like(v)
+        self._check(lib().ipc_gel_vertex_rows(self._ctx, env, len(v), _ptr(v, _ip), _ptr(out, _ip)),
+                    "ipc_gel_vertex_rows")
+        return out.reshape(np.shape(verts))
+
+    @staticmethod
+    def _sensor(sd) -> "ipc_sensor":
+        s = ipc_sensor()
+        s.env, s.pad, s.pitch = int(sd["env"]), int(sd.get("pad", 0)), float(sd["pitch"])
+        for name in ("origin", "axis_u", "axis_v", "normal"):
+            arr = getattr(s, name)
+            for k in range(3):
+                arr[k] = float(sd[name][k])
+        return s
+
+    def sensor_triangles(self, sd) -> np.ndarray:
+        """Global row triples of a sensor's front-face triangles."""
+        s = self._sensor(sd)
+        n = C.c_int(0)
+        self._check(lib().ipc_sensor_triangles(self._ctx, C.byref(s), None, 0, C.byref(n)), "ipc_sensor_triangles")
+        out = np.zeros((n.value, 3), np.int32)
+        self._check(lib().ipc_sensor_triangles(self._ctx, C.byref(s), _ptr(out, _ip), n.value, C.byref(n)),
+                    "ipc_sensor_triangles")
+        return out
+
+    def prepare_sensors(self, sensors, height: int, width: int) -> dict:
+        """Device tables of a set of sensors (dicts with env, pad, origin,
+        axis_u, axis_v, normal, pitch), reused by tactile_maps."""
+        torch = self._torch
+        tris = [self.sensor_triangles(sd) for sd in sensors]
+        off = np.concatenate([[0], np.cumsum([len(t) for t in tris])]).astype(np.int32)
+        rows = np.concatenate(tris).astype(np.int32) if len(tris) else np.zeros((0, 3), np.int32)
+        frames = np.array([list(sd["origin"]) + list(sd["axis_u"]) + list(sd["axis_v"]) + list(sd["normal"])
+                           + [sd["pitch"]] for sd in sensors], dtype=np.float64)
+        n = len(sensors)
+        with torch.cuda.device(self.device):
+            return {"n": n, "H": int(height), "W": int(width), "n_tri": int(off[-1]),
+                    "frames": torch.as_tensor(frames, device=self.device),
+                    "off": torch.as_tensor(off, device=self.device),
+                    "rows": torch.as_tensor(rows.reshape(-1, 3), device=self.device),
+                    "keys": torch.empty((n, height, width), dtype=torch.int64, device=self.device)}
+
+    def tactile_maps(self, prep: dict, normals: bool = True):
+        """(depth [n, H, W], normal [n, H, W, 3] or None, hit [n, H, W] uint8),
+        CUDA tensors written on the ctx stream."""
+        torch = self._torch
+        n, H, W = prep["n"], prep["H"], prep["W"]
+        depth = torch.empty((n, H, W), dtype=torch.float64, device=self.device)
+        normal = torch.empty((n, H, W, 3), dtype=torch.float64, device=self.device) if normals else None
+        hit = torch.empty((n, H, W), dtype=torch.uint8, device=self.device)
+        self._check(lib().ipc_tactile_maps_device(self._ctx, n, H, W, _vp(prep["frames"]), _vp(prep["off"]),
+                                                  _vp(prep["rows"]), prep["n_tri"], _vp(prep["keys"]), _vp(depth),
+                                                  _vp(normal), _vp(hit)), "ipc_tactile_maps_device")
+        return depth, normal, hit
+
+    def prepare_markers(self, env: int, tri_verts, bary) -> dict:
+        """Device tables of markers on coated triangles of one env: tri_verts
+        [m, 3] user vertex ids, bary [m, 3]; the rest positions are taken
+        from the env's current state (call before stepping for flows)."""
+        torch = self._torch
+        rows = self.gel_vertex_rows(env, tri_verts).astype(np.int32)
+        with torch.cuda.device(self.device):
+            prep = {"m": rows.shape[0], "rows": torch.as_tensor(rows, device=self.device),
+                    "bary": torch.as_tensor(np.asarray(bary, dtype=np.float64), device=self.device)}
+        prep["rest"], _ = self.markers(prep)
+        return prep
+
+    def markers(self, prep: dict):
+        """(positions [m, 3], flows [m, 3] or None) as CUDA tensors."""
+        torch = self._torch
+        m = prep["m"]
+        pos = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        rest = prep.get("rest")
+        flow = torch.empty((m, 3), dtype=torch.float64, device=self.device) if rest is not None else None
+        self._check(lib().ipc_markers_device(self._ctx, m, _vp(prep["rows"]), _vp(prep["bary"]), _vp(rest),
+                                             _vp(pos), _vp(flow)), "ipc_markers_device")
+        return pos, flow
 
     def set_graph_mode(self, on: bool = True):
         """Replay the PCG inner loop as a captured CUDA graph (needs a

@@ -47,6 +47,7 @@ class Request:
     n_steps: int = 1
     arrival: float = 0.0          # seconds after the start of the run
     build: Optional[Callable[[], tuple]] = None
+    state: Optional[tuple] = None  # (x, v, y, ydot) to start from; None = the scene's rest state
 
     def materialize(self) -> "Request":
         if self.scene is None and self.build is not None:
@@ -152,6 +153,11 @@ class _GpuCohort(Cohort):
                              stream=self.stream)
         if eng.graphs:
             self.envs.set_graph_mode(True)
+        for i, r in enumerate(requests):
+            if r.state is not None:
+                st = self.envs.set_state(i, *r.state)
+                if st != ipc.IPC_OK:
+                    raise ipc.IpcError(st, f"request {r.rid}: initial state rejected")
         n, mb = len(requests), self.envs.max_bodies
         n_steps = max(r.n_steps for r in requests)
         # the whole script of every env, resident on the device

@@ -1,7 +1,11 @@
 """Continuous batching on the GPU: requests admitted into overlapping
-cohorts give, for every request, the same end state as that request run
-alone in its own context (within the mixed-precision tolerance, 1e-4 of the
-bounding-box diagonal)."""
+cohorts give, for every request, the same result as that request run alone
+in its own context: whole multi-step requests at the FP64 parity tolerances
+(1e-6 of the bounding-box diagonal), and single mixed-precision steps from
+in-contact states at the mixed bar (1e-4), the per-step form in which the
+tolerances are stated.  (At the mixed benchmark tolerances whole trajectories
+of the same request can take different Newton paths through contact onset;
+one 6-step config-2 request ended 5e-4 of the diagonal apart.)"""
 import numpy as np
 import pytest
 
@@ -36,6 +40,8 @@ def _requests():
 
 def _alone(req, prm):
     g = ipc.Envs([req.scene], prm)
+    if req.state is not None:
+        assert g.set_state(0, *req.state) == ipc.IPC_OK
     for k in range(req.n_steps):
         t = g.rest_y(0)
         t[:, :3] += np.asarray(req.delta(k)).reshape(-1, 3)[: t.shape[0]]
@@ -47,20 +53,55 @@ def _alone(req, prm):
     return x, y
 
 
+def _compare(rep, reqs, prm, bound):
+    for r in reqs:
+        res = rep.results[r.rid]
+        assert res.status == 0 and res.steps == r.n_steps
+        xa, ya = _alone(r, prm)
+        diag = float(np.linalg.norm(xa.max(0) - xa.min(0)))
+        assert np.abs(res.final_x - xa).max() <= bound * diag, r.rid
+        assert np.abs(res.final_y[:, :3] - ya[:, :3]).max() <= bound * diag, r.rid
+
+
 @pytest.mark.parametrize("graphs", [True, False])
 def test_each_request_is_the_same_alone_and_in_the_mix(graphs):
-    prm = scenes.SolverParams()
-    prm.precision = 1
+    """Multi-step requests at the FP64 parity tolerances (where one step's
+    result is unique to ~1e-10 m): every request ends where it ends alone,
+    within the FP64 bar of 1e-6 of the bbox diagonal."""
+    prm = scenes.SolverParams().parity()
     reqs = _requests()
     srv = Server(GpuEngine(prm, graphs=graphs), max_cohort=2, max_cohorts=3, mem_reserve=1 << 30)
     rep = srv.run(reqs)
     assert rep.completed == len(reqs) and rep.backlog == 0
     assert rep.cohorts >= 3
     assert rep.env_steps == sum(r.n_steps for r in reqs)
+    _compare(rep, reqs, prm, 1e-6)
+
+
+def test_mixed_precision_steps_are_the_same_alone_and_in_the_mix():
+    """Mixed precision at the benchmark tolerances, one step per request from
+    an in-contact state (the per-step form of the mixed bar, 1e-4 of the
+    bbox diagonal): each step in the mix matches the same step alone."""
+    prm = scenes.SolverParams()
+    prm.precision = 1
+    reqs = _requests()
+    # advance each scene alone to an in-contact state, then ask for one step
+    one = []
     for r in reqs:
-        res = rep.results[r.rid]
-        assert res.status == 0 and res.steps == r.n_steps
-        xa, ya = _alone(r, prm)
-        diag = float(np.linalg.norm(xa.max(0) - xa.min(0)))
-        assert np.abs(res.final_x - xa).max() <= 1e-4 * diag, r.rid
-        assert np.abs(res.final_y[:, :3] - ya[:, :3]).max() <= 1e-4 * diag, r.rid
+        g = ipc.Envs([r.scene], prm)
+        for k in range(r.n_steps):
+            t = g.rest_y(0)
+            t[:, :3] += np.asarray(r.delta(k)).reshape(-1, 3)[: t.shape[0]]
+            g.set_targets(0, t)
+            assert g.step()[0][0] == 0
+        state = g.get_state(0)
+        g.close()
+        k0 = r.n_steps
+
+        def delta(k, d=r.delta, k0=k0):
+            return d(k0 + k)
+        one.append(Request(rid=r.rid, scene=r.scene, delta=delta, n_steps=1, arrival=r.arrival, state=state))
+    srv = Server(GpuEngine(prm, graphs=True), max_cohort=2, max_cohorts=3, mem_reserve=1 << 30)
+    rep = srv.run(one)
+    assert rep.completed == len(one) and rep.cohorts >= 3
+    _compare(rep, one, prm, 1e-4)
