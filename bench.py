@@ -201,13 +201,16 @@ def kernel_bytes(genv, stats_tot, prof):
     hs = 4 if getattr(genv.params, "precision", 0) else 8   # Hessian / matrix value bytes
     out = {}
     # SELL SpMV per env-iteration: 9 values + 4 B column per real block; per
-    # row z and d_old read (the direction is formed on the fly), d_new and q
-    # written, qc read and cleared (FP64, 24 B each)
-    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * 144
+    # row the own direction read, q written (16 B FP32 rows in mixed mode,
+    # 24 B FP64 rows otherwise), the FP64 contact part qc read and cleared
+    vb = 16 if hs == 4 else 24
+    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * (2 * vb + 48)
     out["sell_spmv"] = stats_tot["pcg_iters"] * spmv_env_iter
-    # PCG update: reads p, d_new, r, q and the 6-entry symmetric P^-1 block,
-    # writes p, r, z
-    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (4 * 24 + 6 * hs + 3 * 24)
+    # PCG update: p (FP64) read + written, d and q read, r (FP64) read +
+    # written, the 6-entry symmetric P^-1 block, z written
+    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (48 + 2 * vb + 48 + 6 * hs + vb)
+    # PCG direction: z and d read, d written
+    out["pcg_dir"] = stats_tot["pcg_iters"] * rows_real * 3 * vb
     # elastic element kernel: 4 indices + 4 positions + Dm^-1 + vol read,
     # 12 FP64 gradient and 144 Hessian values written
     out["tet_elastic"] = stats_tot["newton_env_iters"] * T * (16 + 96 + 72 + 8 + 96 + 144 * hs)
@@ -317,6 +320,33 @@ def per_step_error(g64, g32, tg, body_radius):
     return float(errs.max()), dist, int(np.sum(s64 != 0) + np.sum(s32 != 0))
 
 
+# DRAM traffic of one SpMV launch with every env of the 256-env workload
+# active: dram__bytes_read.sum + dram__bytes_write.sum of the first k_spmv
+# launch of `bench.py --only-mixed --steps 1 --warmup 1` under ncu
+# (profiles/k_spmv_traffic_mixed_256env_gel40x40x6.md).  Reported only while
+# the kernel's source is the one that was measured (hash of its text).
+SPMV_TRAFFIC = {"envs": 256, "bytes": None, "source_sha256": None}
+
+
+def _spmv_source_hash() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2504_12908_b300", "csrc")
+    src = open(os.path.join(csrc, "kernels_solver.cu")).read()
+    c = src.index("__global__ void __launch_bounds__(128) k_spmv(Dev d) {")
+    d = src.index("\n}\n", c)
+    vec = open(os.path.join(csrc, "pcgvec.cuh")).read()
+    return hashlib.sha256((vec + src[c:d]).encode()).hexdigest()
+
+
+def spmv_traffic_per_launch(stats_tot, launches):
+    """Measured DRAM bytes scaled to the average launch of the timed region
+    (envs active per launch = env-iterations / launches), or None."""
+    if SPMV_TRAFFIC["bytes"] is None or _spmv_source_hash() != SPMV_TRAFFIC["source_sha256"]:
+        return None
+    active = stats_tot["pcg_iters"] / max(launches, 1)
+    return SPMV_TRAFFIC["bytes"] / SPMV_TRAFFIC["envs"] * active
+
+
 def roofline_of(genv, res):
     kb, _ = kernel_bytes(genv, res["tot"], res["prof"])
     prof = res["prof"]
@@ -338,8 +368,9 @@ def roofline_of(genv, res):
     if rk is not None:
         n, ms = prof[rk]
         achieved = kb[rk] / (ms / 1e3) / 1e9
+        traffic = spmv_traffic_per_launch(res["tot"], n) if rk == "sell_spmv" else None
         roof.update({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                      "bytes_per_launch": kb[rk] / max(n, 1), "share_of_step": kernels[rk]["share"]})
     return roof, kernels
 

@@ -209,7 +209,10 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.r = c.take<double>(R3);
   d.z = c.take<double>(R3);
   d.d = c.take<double>(R3);
+  d.z4 = c.take<float4>((size_t)pk.n_rows);
   d.d4 = c.take<float4>((size_t)pk.n_rows);
+  d.q4 = c.take<float4>((size_t)pk.n_rows);
+  d.cta_list = c.take<int>((size_t)pk.n_rows / 128);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
   d.pc = c.take<double>(6 * (size_t)pk.n_rows);
@@ -245,7 +248,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_kind = c.take<int>(pk.n_pairs_cap);
   d.pair_w = c.take<double>(pk.n_pairs_cap);
   d.pair_eps = c.take<double>(pk.n_pairs_cap);
-  d.pair_H = c.take<char>(hs * 78 * (size_t)pk.n_pairs_cap);
+  d.pair_H = c.take<char>(hs * 78 * ((size_t)pk.n_pairs_cap + 32));
   d.pair_E = c.take<double>(pk.n_pairs_cap);
   d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
   d.pair_scan = c.take<int>(pk.n_envs + 1);
@@ -341,17 +344,36 @@ ipc_status assemble_system(ipc_ctx* ctx, bool lag_friction) {
 
 constexpr int kPcgPoll = 16;  // PCG iterations between host checks of the per-env flags
 
-// one PCG iteration over every PCG-active env; returns the launches issued
-int pcg_iteration(ipc_ctx* ctx) {
+// one PCG iteration over every PCG-active env; returns the launches issued.
+// n_cta >= 0: the row kernels run only the CTAs listed in Dev::cta_list.
+int pcg_iteration(ipc_ctx* ctx, int n_cta = -1) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   long long l0 = ctx->launches;
   KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
   KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s); });
-  KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s); });
-  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s); });
-  KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s); });
+  KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s, n_cta); });
+  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, n_cta); });
+  KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s, n_cta); });
   return (int)(ctx->launches - l0);
+}
+
+// Row CTAs of the envs whose flag is set (from the last flag read-back),
+// uploaded to Dev::cta_list; returns their number.  The row kernels check
+// the flag themselves, so a list that is a superset is still correct.
+ipc_status upload_cta_list(ipc_ctx* ctx, int flag, int* n_out) {
+  const Pack& pk = ctx->pk;
+  int n = 0;
+  for (int e = 0; e < pk.n_envs; ++e) {
+    if (!ctx->h_int[e * NUM_INTS + flag]) continue;
+    const EnvInfo& ev = pk.env[e];
+    for (int c = ev.row_begin / 128; c < (ev.row_begin + ev.n_rows) / 128; ++c) ctx->h_cta_list[n++] = c;
+  }
+  if (n > 0)
+    CK(cudaMemcpyAsync(ctx->dev.cta_list, ctx->h_cta_list, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  *n_out = n;
+  return IPC_OK;
 }
 
 // Capture kPcgPoll iterations into a graph once per context.  The kernels
@@ -389,6 +411,7 @@ ipc_status run_pcg(ipc_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
   const bool graph = ctx->graph_on && !ctx->prof_on;
+  int n_cta = -1;  // first block: every row CTA (the PCG set is read back after it)
   for (int it = 0; it < ctx->prm.pcg_max; it += kPcgPoll) {
     if (graph) {
       if (!ctx->pcg_exec) {
@@ -398,12 +421,14 @@ ipc_status run_pcg(ipc_ctx* ctx) {
       CK(cudaGraphLaunch(ctx->pcg_exec, s));
       ctx->launches += ctx->pcg_exec_launches;
     } else {
-      for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx);
+      for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx, n_cta);
     }
     // envs stop at pcg_max inside k_pcg_update, so a block past it is a no-op
     ipc_status st = sync_flags(ctx);
     if (st != IPC_OK) return st;
     if (count_flag(ctx, I_PCG) == 0) break;
+    // later blocks launch only the CTAs of envs still iterating
+    if (!graph && (st = upload_cta_list(ctx, I_PCG, &n_cta)) != IPC_OK) return st;
   }
   return last_cuda(ctx);
 }
@@ -530,6 +555,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaMemcpyAsync(ctx->dev.s_tgt, pk.rest_x.data(), R3, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMallocHost(&ctx->h_int, NUM_INTS * sizeof(int) * (size_t)pk.n_envs));
   CK(cudaMallocHost(&ctx->h_dbl, NUM_SCALARS * sizeof(double) * (size_t)pk.n_envs));
+  CK(cudaMallocHost(&ctx->h_cta_list, sizeof(int) * (size_t)(pk.n_rows / 128)));
   for (const auto& ev : pk.env) ctx->max_bodies = std::max(ctx->max_bodies, ev.n_bodies);
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
@@ -539,6 +565,7 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
   if (!ctx) return IPC_EINVAL;
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
   if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
+  if (ctx->h_cta_list) cudaFreeHost(ctx->h_cta_list);
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
@@ -794,18 +821,15 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
   if (vec && hvec) {
     std::vector<double> vr;
     dof_to_rows(ctx, env, vec, vr);
-    // the mat-vec reads the direction d (and its FP32 copy): d = vec, copied
-    // by the direction kernel with z = vec and beta = 0
+    // the mat-vec reads the PCG direction (FP32 rows in mixed mode): loaded
+    // from FP64 rows staged in d.z
     if ((st = upload_rows(ctx, env, d.z, vr)) != IPC_OK) return st;
-    if ((st = upload_rows(ctx, env, d.d, vr)) != IPC_OK) return st;
-    const double zero = 0.0;
-    CK(cudaMemcpyAsync(d.env_s + (size_t)env * NUM_SCALARS + S_PBETA, &zero, sizeof(double),
-                       cudaMemcpyHostToDevice, ctx->stream));
     if ((st = select_envs(ctx, {env}, I_PCG)) != IPC_OK) return st;
-    KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, ctx->stream); });
+    KL(ctx, KC_PCGDIR, [&] { return launch_debug_dir_from_rows(d, ctx->stream); });
     KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, ctx->stream); });
     KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, ctx->stream); });
     KL(ctx, KC_SPMV, [&] { return launch_spmv(d, ctx->stream); });
+    KL(ctx, KC_PCGDIR, [&] { return launch_debug_q_to_rows(d, ctx->stream); });
     if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
     if ((st = last_cuda(ctx)) != IPC_OK) return st;
     if ((st = download_rows(ctx, env, d.q, rows)) != IPC_OK) return st;

@@ -95,7 +95,8 @@ struct Dev {
   // state and work (row space: 3 doubles per row)
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
-  float4* d4;                   // mixed mode: FP32 copy of the PCG direction, 16 B per row
+  float4 *z4, *d4, *q4;         // mixed mode: the PCG vectors z, d, q as FP32 rows (16 B)
+  int* cta_list;                // row CTAs (128 rows each) of the envs still in PCG
   void* pc;                     // 6 per row: symmetric inverse of the diagonal block
                                 // (double, or float in mixed mode)
   double* pc_acc;               // 9 per row
@@ -114,7 +115,8 @@ struct Dev {
   int4* pair_v;                 // contact vertex ids
   int* pair_kind;               // 0 PT, 1 EE
   double *pair_w, *pair_eps, *pair_E;
-  void* pair_H;                 // 78 per pair: packed upper triangle (double, or float in mixed mode)
+  void* pair_H;                 // 78 per active pair, by act_list slot s: entry j of the packed upper
+                                // triangle at ((s / 32) * 78 + j) * 32 + s % 32 (double, or float in mixed mode)
   uint8_t* pair_act;
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
   int* act_list;                 // slots of active (d < dhat) pairs
@@ -153,6 +155,7 @@ struct ipc_ctx {
   size_t ws_bytes = 0;
   std::string err;
   int* h_int = nullptr;       // pinned read-back (NUM_INTS * n_envs ints)
+  int* h_cta_list = nullptr;  // pinned staging of Dev::cta_list
   double* h_dbl = nullptr;    // pinned read-back (NUM_SCALARS * n_envs doubles)
   int max_bodies = 0;
   std::vector<int> n_cta_env;  // row CTAs per env

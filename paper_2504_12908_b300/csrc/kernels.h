@@ -33,9 +33,14 @@ int launch_assemble(const Dev& d, cudaStream_t s);
 int launch_grad(const Dev& d, cudaStream_t s);
 int launch_precond(const Dev& d, cudaStream_t s);
 int launch_pcg_init(const Dev& d, cudaStream_t s);
-int launch_spmv(const Dev& d, cudaStream_t s);
-int launch_pcg_update(const Dev& d, cudaStream_t s);
-int launch_pcg_dir(const Dev& d, cudaStream_t s);
+// PCG row kernels: n_cta < 0 launches every row CTA; otherwise only the
+// first n_cta CTAs listed in Dev::cta_list (the envs still in PCG)
+int launch_spmv(const Dev& d, cudaStream_t s, int n_cta = -1);
+int launch_pcg_update(const Dev& d, cudaStream_t s, int n_cta = -1);
+int launch_pcg_dir(const Dev& d, cudaStream_t s, int n_cta = -1);
+// diagnostics: PCG direction from the FP64 rows in Dev::z; q back to Dev::q
+int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s);
+int launch_debug_q_to_rows(const Dev& d, cudaStream_t s);
 int launch_newton_check(const Dev& d, cudaStream_t s);   // pnorm / cres (rows)
 int launch_newton_decide(const Dev& d, cudaStream_t s);
 int launch_al_update(const Dev& d, cudaStream_t s);

@@ -3,6 +3,7 @@
 // additive CCD (K7) and pair energies for the line search.
 #include "common.cuh"
 #include "kernels.h"
+#include "pcgvec.cuh"
 #include "physics.cuh"
 
 namespace ipc {
@@ -297,23 +298,33 @@ __global__ void k_barrier(Dev d, int flag) {
   FOR_PAIRS(d, f) {
   int e;
   int k = pair_at(d, f, e);
-  if (!ENVI(d, e, flag)) continue;
-  int4 v = d.pair_v[k];
-  int cvs[4] = {v.x, v.y, v.z, v.w};
-  D3 X[4];
-  for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
+  int cvs[4] = {0, 0, 0, 0};
   double E, g[12], H[144];
-  bool act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
-  d.pair_act[k] = act ? 1 : 0;
-  if (!act) continue;
-  {
-    int slot = atomicAdd(d.act_count, 1);
-    d.act_list[slot] = k;
-    d.act_env[slot] = e;
+  bool act = false;
+  if (ENVI(d, e, flag)) {
+    int4 v = d.pair_v[k];
+    cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
+    D3 X[4];
+    for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
+    act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
+    d.pair_act[k] = act ? 1 : 0;
   }
-  HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)k * 78;
+  // the warp's active pairs (consecutive pairs, mostly of one env) take
+  // consecutive slots: one atomic per warp
+  const unsigned wm = __activemask();
+  const unsigned am = __ballot_sync(wm, act);
+  if (!act) continue;
+  const int lane = threadIdx.x & 31, leader = __ffs(am) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(d.act_count, __popc(am));
+  base = __shfl_sync(am, base, leader);
+  const int slot = base + __popc(am & ((1u << lane) - 1u));
+  d.act_list[slot] = k;
+  d.act_env[slot] = e;
+  // interleaved by warp of slots so that the mat-vec's loads coalesce
+  HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)(slot >> 5) * 78 * 32 + (slot & 31);
   for (int p = 0, o = 0; p < 12; ++p)
-    for (int q = p; q < 12; ++q) Hs[o++] = (HT)H[p * 12 + q];
+    for (int q = p; q < 12; ++q, ++o) Hs[o * 32] = (HT)H[p * 12 + q];
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
   // preconditioner: diagonal 3x3 of gel vertices, body 12x12 self terms
   for (int i = 0; i < 4; ++i) {
@@ -390,62 +401,77 @@ __global__ void k_pair_spmv(Dev d) {
       int4 v = d.pair_v[k];
       cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
       HT dh[12];
+#pragma unroll
       for (int m = 0; m < 4; ++m) {
         int cv = cvs[m], row = d.cv_row[cv];
         D3 u;
         int b = d.cv_body[cv];
         if (b < 0) {
-          u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
+          u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : PV<HT>::dir(d, row);
         } else {
-          u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+          D3 xb = ld3(d.cv_xbar, cv);
+          u = PV<HT>::dir(d, row) + xb.x * PV<HT>::dir(d, row + 1) + xb.y * PV<HT>::dir(d, row + 2) +
+              xb.z * PV<HT>::dir(d, row + 3);
           body = (body == -2 || body == b) ? b : -1;
         }
         dh[3 * m] = (HT)u.x; dh[3 * m + 1] = (HT)u.y; dh[3 * m + 2] = (HT)u.z;
       }
-      const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)k * 78;
+      const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)(i >> 5) * 78 * 32 + (i & 31);
       HT acc[12];
+#pragma unroll
       for (int q = 0; q < 12; ++q) acc[q] = 0;
+#pragma unroll
       for (int p = 0; p < 12; ++p) {
-        acc[p] += H[ut12(p, p)] * dh[p];
+        acc[p] += H[ut12(p, p) * 32] * dh[p];
+#pragma unroll
         for (int q = p + 1; q < 12; ++q) {
-          HT h = H[ut12(p, q)];
+          HT h = H[ut12(p, q) * 32];
           acc[p] += h * dh[q];
           acc[q] += h * dh[p];
         }
       }
+#pragma unroll
       for (int q = 0; q < 12; ++q) o[q] = (double)acc[q];
     }
     // gel points: direct atomics
+#pragma unroll
     for (int m = 0; m < 4; ++m)
       if (live && d.cv_body[cvs[m]] < 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
     // body points: J^T o, i.e. 12 values on the body's 4 sub-rows
     double jb[12];
+#pragma unroll
     for (int q = 0; q < 12; ++q) jb[q] = 0.0;
-    if (live && body >= 0)
+    if (live && body >= 0) {
+#pragma unroll
       for (int m = 0; m < 4; ++m) {
         if (d.cv_body[cvs[m]] != body) continue;
         D3 xb = ld3(d.cv_xbar, cvs[m]);
         const double w4[4] = {1.0, xb.x, xb.y, xb.z};
+#pragma unroll
         for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
           for (int c = 0; c < 3; ++c) jb[3 * s4 + c] += w4[s4] * o[3 * m + c];
       }
-    int key = (live && body >= 0) ? body : -1;
-    unsigned peers = __match_any_sync(0xffffffffu, key);
-    bool uniform = (peers == 0xffffffffu) && key >= 0;
-    if (uniform) {
+    }
+    // one reduction and 12 atomics per distinct body in the warp (lanes are
+    // consecutive active pairs, mostly of one env and so of one body)
+    const int key = (live && body >= 0) ? body : -1;
+    unsigned todo = __ballot_sync(0xffffffffu, key >= 0);
+    while (todo) {
+      const int leader = __ffs(todo) - 1;
+      const int k0 = __shfl_sync(0xffffffffu, key, leader);
+      const bool mine = key == k0;
+      const int br = d.body_row[k0];
+#pragma unroll
       for (int q = 0; q < 12; ++q) {
-        double t = jb[q];
+        double t = mine ? jb[q] : 0.0;
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        jb[q] = t;
+        if (lane == leader) atomicAdd(d.qc + 3 * br + q, t);
       }
-      if (lane == 0) {
-        int br = d.body_row[key];
-        for (int q = 0; q < 12; ++q) atomicAdd(d.qc + 3 * br + q, jb[q]);
-      }
-    } else if (key >= 0) {
-      int br = d.body_row[key];
-      for (int q = 0; q < 12; ++q) atomicAdd(d.qc + 3 * br + q, jb[q]);
-    } else if (live && body == -1) {  // points of several bodies: per point
+      todo &= ~__ballot_sync(0xffffffffu, mine);
+    }
+    if (live && body == -1) {  // points of several bodies: per point
+#pragma unroll
       for (int m = 0; m < 4; ++m)
         if (d.cv_body[cvs[m]] >= 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
     }
@@ -762,8 +788,8 @@ __global__ void k_fric_spmv(Dev d) {
   for (int i = 0; i < 4; ++i) {
     int cv = cvs[i], row = d.cv_row[cv];
     D3 u;
-    if (d.cv_body[cv] < 0) u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : ld3(d.d, row);
-    else u = body_point(d.d, row, ld3(d.cv_xbar, cv));
+    if (d.cv_body[cv] < 0) u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : dir_row(d, row);
+    else u = dir_body_point(d, row, ld3(d.cv_xbar, cv));
     a = a + w[i] * u;
   }
   const double* S = d.fr_S + 6 * (long long)j;

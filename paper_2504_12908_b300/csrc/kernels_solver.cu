@@ -7,6 +7,7 @@
 // padded to a multiple of 128 so that a 128-thread CTA never straddles envs.
 #include "common.cuh"
 #include "kernels.h"
+#include "pcgvec.cuh"
 #include "physics.cuh"
 
 namespace ipc {
@@ -22,14 +23,16 @@ __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED 
 
 // Deterministic per-env reduction of CTA partials: every CTA of the env
 // writes `n` partials; the last CTA to arrive sums them in CTA order.
-// Returns true in thread 0 of the last CTA, with the sums in out[0..n).
+// cta: the row CTA (row / 128), which is not blockIdx.x when the launch runs
+// a list of CTAs.  Returns true in thread 0 of the last CTA, with the sums
+// in out[0..n).
 template <int n>
-__device__ bool env_reduce(const Dev& d, int e, int which, const double* vals /*per thread*/, double* out) {
+__device__ bool env_reduce(const Dev& d, int e, int which, int cta, const double* vals /*per thread*/,
+                           double* out) {
   __shared__ double sh[32];
   __shared__ bool last;
   double part[n];
   for (int j = 0; j < n; ++j) part[j] = block_sum(vals[j], sh);
-  int cta = blockIdx.x;
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
     __threadfence();
@@ -81,28 +84,53 @@ __global__ void k_attach_targets(Dev d, int flag) {
 // FP64 before F is rounded to HT.  (An FP32 gradient was measured: the
 // kernel's time did not change and the mixed-vs-FP64 step error grew.)
 template <class HT>
-__global__ void k_tet(Dev d) {
+__global__ void __launch_bounds__(64) k_tet(Dev d) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d.n_tets) return;
-  int e = find_env(d.env_tet_off, d.n_envs, t);
-  if (!ENVI(d, e, I_ACTIVE)) return;
-  const int* q = d.tets + 4 * (long long)t;
-  D3 X[4];
-  for (int a = 0; a < 4; ++a) X[a] = ld3(d.x, q[a]);
-  double Dmi[9];
-  for (int k = 0; k < 9; ++k) Dmi[k] = d.Dm_inv[9 * (long long)t + k];
-  double F[9];
-  tet_deformation<double>(X, Dmi, F);
-  double vol = d.tet_vol[t], mu = d.env_mu[e], lam = d.env_lam[e];
-  double g[12];
-  nh_gradient<double>(F, Dmi, vol, mu, lam, g);
-  double* G = d.tetG + 12 * (long long)t;
-  for (int k = 0; k < 12; ++k) G[k] = g[k];
-  HT Fh[9], Dh[9];
-  for (int k = 0; k < 9; ++k) { Fh[k] = (HT)F[k]; Dh[k] = (HT)Dmi[k]; }
-  HT* H = reinterpret_cast<HT*>(d.tetH) + 144 * (long long)t;
-  nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
-                        [&](int a, int b, int i, int j, HT v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
+  bool ok = t < d.n_tets;
+  int e = ok ? find_env(d.env_tet_off, d.n_envs, t) : 0;
+  ok = ok && ENVI(d, e, I_ACTIVE);
+  // mixed mode: each warp stages its 32 tets' 144 Hessian values in shared
+  // memory (rows padded to 145 words: conflict-free) and writes the 32 x 144
+  // block out contiguously; FP64 mode stores directly
+  constexpr bool kStage = sizeof(HT) == 4;
+  __shared__ float sH[kStage ? 2 * 32 * 145 : 1];
+  const int lane = threadIdx.x & 31;
+  float* mine = sH + (kStage ? ((threadIdx.x >> 5) * 32 + lane) * 145 : 0);
+  if (ok) {
+    const int* q = d.tets + 4 * (long long)t;
+    D3 X[4];
+    for (int a = 0; a < 4; ++a) X[a] = ld3(d.x, q[a]);
+    double Dmi[9];
+    for (int k = 0; k < 9; ++k) Dmi[k] = d.Dm_inv[9 * (long long)t + k];
+    double F[9];
+    tet_deformation<double>(X, Dmi, F);
+    double vol = d.tet_vol[t], mu = d.env_mu[e], lam = d.env_lam[e];
+    double g[12];
+    nh_gradient<double>(F, Dmi, vol, mu, lam, g);
+    double* G = d.tetG + 12 * (long long)t;
+    for (int k = 0; k < 12; ++k) G[k] = g[k];
+    HT Fh[9], Dh[9];
+    for (int k = 0; k < 9; ++k) { Fh[k] = (HT)F[k]; Dh[k] = (HT)Dmi[k]; }
+    if (kStage) {
+      nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
+                            [&](int a, int b, int i, int j, HT v) { mine[(a * 4 + b) * 9 + i * 3 + j] = (float)v; });
+    } else {
+      HT* H = reinterpret_cast<HT*>(d.tetH) + 144 * (long long)t;
+      nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
+                            [&](int a, int b, int i, int j, HT v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
+    }
+  }
+  if (kStage) {
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    __syncwarp();
+    const int t0 = t - lane;
+    const float* wsh = sH + (threadIdx.x >> 5) * 32 * 145;
+    float* H = reinterpret_cast<float*>(d.tetH) + 144 * (long long)t0;
+    for (int i = lane; i < 32 * 144; i += 32) {
+      const int tt = i / 144;
+      if ((okm >> tt) & 1u) H[i] = wsh[tt * 145 + (i - tt * 144)];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -313,7 +341,8 @@ __global__ void k_precond_body(Dev d) {
 
 // z = P^{-1} r for row r (body rows read the 4 sub-rows of their body; all of
 // them sit in the same warp).  Gel rows: 6 stored entries of the symmetric
-// 3x3 inverse, in HT; the product is formed in FP64.
+// 3x3 inverse, applied in HT (FP32 in mixed mode); body rows: the body's
+// 12x12 inverse in FP64.
 template <class HT>
 __device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
   if (is_body(kr)) {
@@ -328,29 +357,17 @@ __device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
   }
   if (kr == ROW_PAD) return D3{0, 0, 0};
   const HT* P = reinterpret_cast<const HT*>(d.pc) + 6 * (long long)r;
-  const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
+  const HT a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
   D3 x = ld3(d.r, r);
-  return D3{a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z};
+  const HT X = (HT)x.x, Y = (HT)x.y, Z = (HT)x.z;
+  return D3{(double)(a * X + b * Y + c * Z), (double)(b * X + e * Y + f * Z), (double)(c * X + f * Y + g * Z)};
 }
 
-// the direction of column c as the SpMV reads it: FP64 rows in FP64 mode,
-// the 16-byte FP32 copy (one vector load) in mixed mode
-template <class HT> struct DirGather;
-template <> struct DirGather<double> {
-  static __device__ __forceinline__ V3<double> at(const Dev& d, int c) { return ld3(d.d, c); }
-};
-template <> struct DirGather<float> {
-  static __device__ __forceinline__ V3<float> at(const Dev& d, int c) {
-    float4 v = __ldg(d.d4 + c);
-    return V3<float>{v.x, v.y, v.z};
-  }
-};
-
-// the direction d and, in mixed mode, its FP32 copy
+// r.z of a row in HT (z is an HT quantity); r.r, which decides convergence,
+// is always FP64
 template <class HT>
-__device__ __forceinline__ void store_dir(const Dev& d, int r, D3 v) {
-  st3(d.d, r, v);
-  if (sizeof(HT) == 4) d.d4[r] = make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f);
+__device__ __forceinline__ double dot_rz(D3 rv, D3 z) {
+  return (double)((HT)rv.x * (HT)z.x + (HT)rv.y * (HT)z.y + (HT)rv.z * (HT)z.z);
 }
 
 // PCG start: p = 0, r = -g, z = P^-1 r, d = z, beta = 0; rz, rr0
@@ -365,11 +382,11 @@ __global__ void k_pcg_init(Dev d) {
   st3(d.p, r, D3{0, 0, 0});
   __syncwarp();
   D3 z = apply_pc<HT>(d, r, kr);
-  st3(d.z, r, z);
-  store_dir<HT>(d, r, z);
-  double vals[2] = {dot(rv, z), dot(rv, rv)};
+  PV<HT>::set_z(d, r, z);
+  PV<HT>::set_dir(d, r, z);
+  double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
   double out[2];
-  if (env_reduce<2>(d, e, 0, vals, out)) {
+  if (env_reduce<2>(d, e, 0, r >> 7, vals, out)) {
     ENVS(d, e, S_PBETA) = 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR0) = out[1];
@@ -382,11 +399,11 @@ __global__ void k_pcg_init(Dev d) {
 // q = A d + qc (SELL-32, one row per thread, U slots in flight per lane),
 // qc cleared; d.q reduced per env -> alpha.
 // HT: matrix precision; the products are accumulated in HT slot by slot in
-// storage order, q, qc and the own-row d of the dot product stay FP64.
+// storage order; the contact part qc and the dot product are FP64.
 template <class HT>
-__global__ void __launch_bounds__(128) k_spmv(Dev d) {
+__global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta_list) {
   constexpr int U = sizeof(HT) == 4 ? 4 : 2;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
   int ch = r >> 5, lane = r & 31;
@@ -407,7 +424,7 @@ __global__ void __launch_bounds__(128) k_spmv(Dev d) {
       for (int k = 0; k < 9; ++k) A[u][k] = val[(long long)(sl + u) * 288 + k * 32];
     V3<HT> w[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = DirGather<HT>::at(d, c[u]);
+    for (int u = 0; u < U; ++u) w[u] = PV<HT>::gather(d, c[u]);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ax += A[u][0] * w[u].x + A[u][1] * w[u].y + A[u][2] * w[u].z;
@@ -418,17 +435,17 @@ __global__ void __launch_bounds__(128) k_spmv(Dev d) {
   for (; sl < slots; ++sl) {
     int c = colp[sl * 32];
     const HT* A = val + (long long)sl * 288;
-    V3<HT> w = DirGather<HT>::at(d, c);
+    V3<HT> w = PV<HT>::gather(d, c);
     ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
     ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
     az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
   }
   D3 acc = ld3(d.qc, r) + D3{(double)ax, (double)ay, (double)az};
-  st3(d.q, r, acc);
+  PV<HT>::set_q(d, r, acc);
   st3(d.qc, r, D3{0, 0, 0});
-  double vals[1] = {dot(ld3(d.d, r), acc)};
+  double vals[1] = {dot(PV<HT>::dir(d, r), acc)};
   double out[1];
-  if (env_reduce<1>(d, e, 1, vals, out)) {
+  if (env_reduce<1>(d, e, 1, r >> 7, vals, out)) {
     ENVS(d, e, S_DQ) = out[0];
     ENVS(d, e, S_PALPHA) = (out[0] > 0.0) ? ENVS(d, e, S_RZ) / out[0] : 0.0;
   }
@@ -436,21 +453,21 @@ __global__ void __launch_bounds__(128) k_spmv(Dev d) {
 
 // p += alpha d, r -= alpha q, z = P^-1 r; rz, rr reduced -> beta, stop test
 template <class HT>
-__global__ void k_pcg_update(Dev d) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
+  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
   uint8_t kr = d.row_kind[r];
   double al = ENVS(d, e, S_PALPHA);
-  st3(d.p, r, ld3(d.p, r) + al * ld3(d.d, r));
-  D3 rv = ld3(d.r, r) - al * ld3(d.q, r);
+  st3(d.p, r, ld3(d.p, r) + al * PV<HT>::dir(d, r));
+  D3 rv = ld3(d.r, r) - al * PV<HT>::q(d, r);
   st3(d.r, r, rv);
   __syncwarp();
   D3 z = apply_pc<HT>(d, r, kr);
-  st3(d.z, r, z);
-  double vals[2] = {dot(rv, z), dot(rv, rv)};
+  PV<HT>::set_z(d, r, z);
+  double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
   double out[2];
-  if (env_reduce<2>(d, e, 0, vals, out)) {
+  if (env_reduce<2>(d, e, 0, r >> 7, vals, out)) {
     double rz_old = ENVS(d, e, S_RZ);
     ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
     ENVS(d, e, S_RZ) = out[0];
@@ -462,15 +479,36 @@ __global__ void k_pcg_update(Dev d) {
   }
 }
 
-// d = z + beta d (and its FP32 copy in mixed mode)
+// d = z + beta d (in HT)
 template <class HT>
-__global__ void k_pcg_dir(Dev d) {
+__global__ void k_pcg_dir(Dev d, const int* __restrict__ cta_list) {
+  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  if (sizeof(HT) == 4) {
+    const float be = (float)ENVS(d, e, S_PBETA);
+    const float4 z = d.z4[r], dd = d.d4[r];
+    d.d4[r] = make_float4(z.x + be * dd.x, z.y + be * dd.y, z.z + be * dd.z, 0.0f);
+  } else {
+    PV<HT>::set_dir(d, r, PV<HT>::z(d, r) + ENVS(d, e, S_PBETA) * PV<HT>::dir(d, r));
+  }
+}
+
+// diagnostics: the direction from FP64 rows held in d.z; q back to FP64 rows
+template <class HT>
+__global__ void k_debug_dir_from_rows(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
-  store_dir<HT>(d, r, ld3(d.z, r) + ENVS(d, e, S_PBETA) * ld3(d.d, r));
+  PV<HT>::set_dir(d, r, ld3(d.z, r));
 }
-
+template <class HT>
+__global__ void k_debug_q_to_rows(Dev d) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  st3(d.q, r, PV<HT>::q(d, r));
+}
 
 // ---------------------------------------------------------------------------
 // Newton bookkeeping
@@ -775,8 +813,8 @@ __global__ void k_gather_coated(Dev d) {
 int launch_predict(const Dev& d, cudaStream_t s) { k_predict<<<ROWGRID>>>(d); return 1; }
 int launch_attach_targets(const Dev& d, int flag, cudaStream_t s) { k_attach_targets<<<ROWGRID>>>(d, flag); return 1; }
 int launch_tet(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_tet<float><<<nblk(d.n_tets, 128), 128, 0, s>>>(d);
-  else k_tet<double><<<nblk(d.n_tets, 128), 128, 0, s>>>(d);
+  if (d.prec) k_tet<float><<<nblk(d.n_tets, 64), 64, 0, s>>>(d);
+  else k_tet<double><<<nblk(d.n_tets, 64), 64, 0, s>>>(d);
   return 1;
 }
 int launch_body(const Dev& d, cudaStream_t s) {
@@ -802,19 +840,32 @@ int launch_pcg_init(const Dev& d, cudaStream_t s) {
   else k_pcg_init<double><<<ROWGRID>>>(d);
   return 1;
 }
-int launch_spmv(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_spmv<float><<<ROWGRID>>>(d);
-  else k_spmv<double><<<ROWGRID>>>(d);
+// n_cta < 0: every row CTA; else the first n_cta entries of Dev::cta_list
+#define LISTGRID (n_cta < 0 ? d.n_rows / 128 : n_cta), 128, 0, s
+#define LISTARG (n_cta < 0 ? nullptr : d.cta_list)
+int launch_spmv(const Dev& d, cudaStream_t s, int n_cta) {
+  if (d.prec) k_spmv<float><<<LISTGRID>>>(d, LISTARG);
+  else k_spmv<double><<<LISTGRID>>>(d, LISTARG);
   return 1;
 }
-int launch_pcg_update(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_pcg_update<float><<<ROWGRID>>>(d);
-  else k_pcg_update<double><<<ROWGRID>>>(d);
+int launch_pcg_update(const Dev& d, cudaStream_t s, int n_cta) {
+  if (d.prec) k_pcg_update<float><<<LISTGRID>>>(d, LISTARG);
+  else k_pcg_update<double><<<LISTGRID>>>(d, LISTARG);
   return 1;
 }
-int launch_pcg_dir(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_pcg_dir<float><<<ROWGRID>>>(d);
-  else k_pcg_dir<double><<<ROWGRID>>>(d);
+int launch_pcg_dir(const Dev& d, cudaStream_t s, int n_cta) {
+  if (d.prec) k_pcg_dir<float><<<LISTGRID>>>(d, LISTARG);
+  else k_pcg_dir<double><<<LISTGRID>>>(d, LISTARG);
+  return 1;
+}
+int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_debug_dir_from_rows<float><<<ROWGRID>>>(d);
+  else k_debug_dir_from_rows<double><<<ROWGRID>>>(d);
+  return 1;
+}
+int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_debug_q_to_rows<float><<<ROWGRID>>>(d);
+  else k_debug_q_to_rows<double><<<ROWGRID>>>(d);
   return 1;
 }
 int launch_newton_check(const Dev& d, cudaStream_t s) {
