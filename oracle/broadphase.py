@@ -1,7 +1,7 @@
 """Brute-force candidate pairs (oracle side).
 
 Pairs (App. A.3): point-triangle and edge-edge pairs between surface
-primitives.  Reading C-10: only primitives of different objects pair up
+primitives.  Reading: only primitives of different objects pair up
 (gel pads and affine bodies are objects; gel self-contact is not modelled),
 pairs whose four vertices are all fixed are dropped, and a gel pad never
 pairs with the body it is attached to.

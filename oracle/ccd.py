@@ -1,7 +1,7 @@
 """Continuous collision detection (oracle side).
 
 The paper guarantees intersection-free trajectories (Sec. 1, Sec. 2) but does
-not name its CCD.  Reading (C-8): additive CCD (ACCD, from the codimensional
+not name its CCD.  Reading: additive CCD (ACCD, from the codimensional
 IPC follow-up work), restated here from its definition:
 
   * subtract the mean displacement of the pair's four points (a common

@@ -16,7 +16,7 @@ definitions with no hand algebra:
     EE: ((a0 - b0) . n)^2 / |n|^2,       n = (a1 - a0) x (b1 - b0)
 Edge-edge pairs are multiplied by the IPC mollifier of |(a1-a0) x (b1-b0)|^2
 with threshold eps_x = c |a0bar a1bar|^2 |b0bar b1bar|^2 (rest lengths), which
-keeps the energy smooth for near-parallel edges (reading C-9: the paper is
+keeps the energy smooth for near-parallel edges (reading: the paper is
 silent; the constant c = 1e-3 follows the cited IPC work).
 """
 from __future__ import annotations

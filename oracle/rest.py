@@ -134,7 +134,9 @@ def _edges_of(tris: np.ndarray):
 
 
 def surface_data(scene, bodies: list) -> SurfaceData:
-    """Gel boundary + body surfaces, areas (reading C-3) and fixed flags."""
+    """Gel boundary + body surfaces, areas and fixed flags (reading: the
+    contact area weights come from one third of the incident rest triangle
+    areas)."""
     N = scene.n_verts
     nb = len(scene.bodies)
     off = np.zeros(nb + 1, np.int64)

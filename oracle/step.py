@@ -12,19 +12,19 @@ with xt = x^n + h v^n, yt = y^n + h ydot^n (App. A.2) and the backward-Euler
 velocity update v^{n+1} = (x^{n+1} - x^n) / h.
 
 Readings (the paper is silent or garbled on these):
-  * C-4: h^2 multiplies every potential, the barrier included.
-  * C-11: pinned gel vertices (targets equal to their current position) are
+  * h^2 multiplies every potential, the barrier included.
+  * pinned gel vertices (targets equal to their current position) are
     eliminated; driven DoFs (scripted bodies, gel vertices attached to a
     body) use the augmented Lagrangian the paper names, in its standard
     mass-weighted form (the printed squared scalar is not an AL), with the
     multiplier update lambda <- lambda - kappa_A (q - s) once the inner
     Newton loop has converged and the constraint residual is still above
     tolerance.
-  * C-7: line search starts at min(1, alpha_CCD) and halves until the energy
+  * line search starts at min(1, alpha_CCD) and halves until the energy
     does not increase and no tet is inverted (cap ls_max halvings).
-  * C-12: Newton stops when |p|_inf / h < tol, p measured as full-space
+  * Newton stops when |p|_inf / h < tol, p measured as full-space
     vertex displacements (gel p and J_j p_y on body vertices).
-  * C-13: the linear solve is a sparse direct solve here (the GPU uses PCG).
+  * the linear solve is a sparse direct solve here (the GPU uses PCG).
 """
 from __future__ import annotations
 

@@ -535,7 +535,7 @@ __global__ void k_newton_rows(Dev d) {
   if (threadIdx.x == 0) atomic_max_nonneg(&ENVS(d, e, S_CRES), cr);
 }
 
-// per env: converged / AL multiplier update / line search (C-11, C-12)
+// per env: converged / AL multiplier update / line search
 __global__ void k_newton_decide(Dev d) {
   const int* has_driven = d.env_has_driven;
   int e = blockIdx.x * blockDim.x + threadIdx.x;

@@ -4,7 +4,7 @@ Tolerances (FP64 mode): element energies/gradients 1e-10 relative, projected
 Hessians 1e-8 of their largest entry (the PSD clamp is Lipschitz, and the
 two sides reach it through different eigen-solvers), Newton directions 1e-6
 (PCG at relative residual 1e-10 vs a direct solve), per-step positions
-1e-6 of the scene's bounding-box diagonal (the spec FP64 bar) with
+1e-6 of the scene's bounding-box diagonal (the FP64 bar) with
 both sides at the parity Newton tolerance 1e-7 m/s.  Candidate sets: exact.
 """
 import numpy as np
