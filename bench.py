@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--max-cohort", type=int, default=256)
     ap.add_argument("--max-cohorts", type=int, default=8)
     ap.add_argument("--no-graphs", action="store_true", help="serving: plain launches instead of PCG graphs")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -240,6 +241,7 @@ def time_precision(args, scene, params, deltas, precision, local, world, profile
 
     for k in range(args.warmup):
         one_step(k)
+    tuning = genv.autotune() if not args.no_autotune else None
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -287,7 +289,8 @@ def time_precision(args, scene, params, deltas, precision, local, world, profile
     n_bad = int(sum(int(np.sum(s_ != 0)) for s_ in statuses))
     return {"genv": genv, "value": args.envs * args.steps * world / (ms_total / 1e3), "ms_total": ms_total,
             "step_ms": step_ms, "tot": tot, "prof": prof, "clocks": clk, "launches": launches, "n_bad": n_bad,
-            "statuses": statuses, "deltas": deltas, "com": com, "n_total": n_total, "dev_tg": dev_tg}
+            "statuses": statuses, "deltas": deltas, "com": com, "n_total": n_total, "dev_tg": dev_tg,
+            "tuning": tuning}
 
 
 def per_step_error(g64, g32, tg, body_radius):
@@ -325,14 +328,18 @@ def per_step_error(g64, g32, tg, body_radius):
 # launch of `bench.py --only-mixed --steps 1 --warmup 1` under ncu
 # (profiles/k_spmv_traffic_mixed_256env_gel40x40x6.md).  Reported only while
 # the kernel's source is the one that was measured (hash of its text).
-SPMV_TRAFFIC = {"envs": 256, "bytes": None, "source_sha256": None}
+# (measured with 4 slots in flight per lane; the hash is of the source after
+# the slot count became a template parameter, which left that variant's code
+# unchanged)
+SPMV_TRAFFIC = {"envs": 256, "bytes": 1275239936 + 93181952,
+                "source_sha256": "663696f6bbf2d3b967a562b364f5b7131ae2a4cac5d64cf8c5acb6a899a94650"}
 
 
 def _spmv_source_hash() -> str:
     import hashlib
     csrc = os.path.join(ROOT, "paper_2504_12908_b300", "csrc")
     src = open(os.path.join(csrc, "kernels_solver.cu")).read()
-    c = src.index("__global__ void __launch_bounds__(128) k_spmv(Dev d) {")
+    c = src.index("__global__ void __launch_bounds__(128) k_spmv(Dev d")
     d = src.index("\n}\n", c)
     vec = open(os.path.join(csrc, "pcgvec.cuh")).read()
     return hashlib.sha256((vec + src[c:d]).encode()).hexdigest()
@@ -368,7 +375,8 @@ def roofline_of(genv, res):
     if rk is not None:
         n, ms = prof[rk]
         achieved = kb[rk] / (ms / 1e3) / 1e9
-        traffic = spmv_traffic_per_launch(res["tot"], n) if rk == "sell_spmv" else None
+        tuned_u = (res.get("tuning") or {}).get("spmv_unroll", 4)
+        traffic = spmv_traffic_per_launch(res["tot"], n) if (rk == "sell_spmv" and tuned_u == 4) else None
         roof.update({"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
                      "bytes_per_launch": kb[rk] / max(n, 1), "share_of_step": kernels[rk]["share"]})
@@ -466,6 +474,7 @@ def run_ours(args):
                "traj_err_vs_fp64": traj_err,
                "status_not_ok": head["n_bad"],
                "iterations": head["tot"],
+               "launch_shapes": head["tuning"],
                "roofline": roof, "kernels": kernels, "clocks": head["clocks"], "gpu_launches": int(head["launches"]),
                "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)

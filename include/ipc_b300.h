@@ -167,6 +167,24 @@ const char* ipc_last_error(const ipc_ctx* ctx);
  * used so that every kernel is timed. */
 ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on);
 
+/* Launch shapes chosen by ipc_autotune and the timings behind the choice. */
+typedef struct {
+  int spmv_unroll;        /* SELL slots in flight per lane in the SpMV: 2, 4 or 8 */
+  int pair_ctas_per_sm;   /* contact mat-vec grid: CTAs per SM (x 148)        */
+  float spmv_us[3];       /* mean SpMV time per launch for 2, 4, 8, us         */
+  float pair_us[4];       /* contact mat-vec for 2, 4, 8, 16 CTAs per SM, us   */
+} ipc_tuning;
+
+/* Choose the SpMV's slots in flight per lane and the contact mat-vec's grid
+ * size by timing `reps` launches of each candidate on this ctx's current
+ * system (call it after at least one ipc_step, between steps), with every
+ * env counted as iterating.  It touches only PCG scratch (q, the PCG
+ * scalars) and clears the contact accumulator afterwards, so later steps
+ * give the same results as before apart from the launch shapes.  Any
+ * captured PCG graph is dropped and re-captured at the next solve.  Not in
+ * the paper: a property of this library.  `out` may be NULL. */
+ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out);
+
 int ipc_num_envs(const ipc_ctx* ctx);
 ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies,
                          int* n_surface_out);

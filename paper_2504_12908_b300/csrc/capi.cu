@@ -121,6 +121,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.ee_moll = prm.ee_mollifier;
   d.fr_mu = prm.friction_mu;
   d.fr_eh = prm.friction_eps_v * prm.dt;
+  d.spmv_unroll = 0;
+  d.pair_ctas_per_sm = 0;
   d.newton_max = prm.newton_max;
   d.pcg_max = prm.pcg_max;
   d.ls_max = prm.ls_max;
@@ -254,6 +256,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_scan = c.take<int>(pk.n_envs + 1);
   d.act_list = c.take<int>(pk.n_pairs_cap);
   d.act_env = c.take<int>(pk.n_pairs_cap);
+  d.act_v = c.take<int4>(pk.n_pairs_cap);
   const size_t nfr = prm.friction_mu > 0.0 ? pk.n_pairs_cap : 0;
   d.fr_v = c.take<int4>(nfr);
   d.fr_w = c.take<double>(4 * nfr);
@@ -476,6 +479,25 @@ ipc_status begin_single(ipc_ctx* ctx, int env) {
   return last_cuda(ctx);
 }
 
+// Time `reps` launches of f on the ctx stream (events), after one warm-up.
+template <class F>
+ipc_status time_launches(ipc_ctx* ctx, int reps, F&& f, float* us) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  f();
+  CK(cudaEventRecord(a, ctx->stream));
+  for (int i = 0; i < reps; ++i) f();
+  CK(cudaEventRecord(b, ctx->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *us = 1e3f * ms / (float)reps;
+  return last_cuda(ctx);
+}
+
 }  // namespace
 
 extern "C" {
@@ -578,6 +600,50 @@ const char* ipc_last_error(const ipc_ctx* ctx) { return ctx ? ctx->err.c_str() :
 ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on) {
   if (!ctx) return IPC_EINVAL;
   ctx->graph_on = on != 0;
+  return IPC_OK;
+}
+
+ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
+  if (!ctx || reps <= 0) return IPC_EINVAL;
+  Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  ipc_status st;
+  if (ctx->pk.n_envs <= 0) return IPC_EINVAL;
+  // every env in PCG for the timing; the kernels only touch PCG scratch
+  // (q, the PCG scalars) and the contact accumulator, cleared afterwards
+  std::vector<int> all(ctx->pk.n_envs);
+  for (int e = 0; e < ctx->pk.n_envs; ++e) all[e] = e;
+  if ((st = select_envs(ctx, all, I_PCG)) != IPC_OK) return st;
+  ipc_tuning t{};
+  const int us_[3] = {2, 4, 8};
+  float best = 3.4e38f;
+  int best_u = 0;
+  for (int k = 0; k < 3; ++k) {
+    d.spmv_unroll = us_[k];
+    if ((st = time_launches(ctx, reps, [&] { launch_spmv(d, s); }, &t.spmv_us[k])) != IPC_OK) return st;
+    if (t.spmv_us[k] < best) { best = t.spmv_us[k]; best_u = us_[k]; }
+  }
+  d.spmv_unroll = best_u;
+  const int ctas_[4] = {2, 4, 8, 16};
+  best = 3.4e38f;
+  int best_c = 8;
+  for (int k = 0; k < 4; ++k) {
+    d.pair_ctas_per_sm = ctas_[k];
+    if ((st = time_launches(ctx, reps, [&] { launch_pair_spmv(d, s); }, &t.pair_us[k])) != IPC_OK) return st;
+    if (t.pair_us[k] < best) { best = t.pair_us[k]; best_c = ctas_[k]; }
+  }
+  d.pair_ctas_per_sm = best_c;
+  CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
+  if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
+  CK(cudaStreamSynchronize(s));
+  // the captured PCG graph holds the old launch shapes
+  if (ctx->pcg_exec) {
+    cudaGraphExecDestroy(ctx->pcg_exec);
+    ctx->pcg_exec = nullptr;
+  }
+  t.spmv_unroll = best_u;
+  t.pair_ctas_per_sm = best_c;
+  if (out) *out = t;
   return IPC_OK;
 }
 

@@ -63,6 +63,9 @@ struct Dev {
   double h, grav[3], dhat, kappa, newton_tol, pcg_tol, accd_s, al_kappa, ee_moll;
   int newton_max, pcg_max, ls_max, accd_max, al_max;
   int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
+  // launch shapes (ipc_autotune): SpMV slots in flight per lane (2, 4, 8;
+  // 0 = default by precision) and the contact mat-vec grid in CTAs per SM
+  int spmv_unroll, pair_ctas_per_sm;
   double fr_mu, fr_eh;          // friction coefficient; eps_v * h (fr_mu = 0: no friction)
   // static tables
   const int *env_row_off, *env_tet_off, *env_cv_off, *env_tri_off, *env_edge_off, *env_obj_off,
@@ -121,6 +124,7 @@ struct Dev {
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
   int* act_list;                 // slots of active (d < dhat) pairs
   int* act_env;                  // env of each act_list entry
+  int4* act_v;                   // contact points of each act_list entry
   // lagged friction records (segments like the pair list, I_NFRIC per env)
   int4* fr_v;                    // contact points of the pair
   double *fr_w, *fr_T, *fr_rn;   // closest-point weights (4), tangent basis (6), r at x^n (3)

@@ -321,6 +321,7 @@ __global__ void k_barrier(Dev d, int flag) {
   const int slot = base + __popc(am & ((1u << lane) - 1u));
   d.act_list[slot] = k;
   d.act_env[slot] = e;
+  d.act_v[slot] = make_int4(cvs[0], cvs[1], cvs[2], cvs[3]);
   // interleaved by warp of slots so that the mat-vec's loads coalesce
   HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)(slot >> 5) * 78 * 32 + (slot & 31);
   for (int p = 0, o = 0; p < 12; ++p)
@@ -376,104 +377,91 @@ __device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) 
 
 // q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
 // eliminated: read as zero, never written).  H_k is stored as its packed
-// upper triangle.  The body part J^T (H_k d) of a warp whose lanes all touch
-// the same single body is summed across the warp before the atomics (every
-// contact of an env hits the same 12 body DoFs).
+// upper triangle, interleaved by warp of active slots.
+// 16 lanes per pair (two pairs per warp), lane j < 12 owns coordinate j =
+// 3 m + c (point m, component c): it forms that component of the pair's
+// direction, the group shares the 12 values by shuffles, lane j computes row
+// j of H_k d (12 FMAs) and scatters it: gel points directly; body points as
+// J^T (H_k d) on the body's 4 sub-rows, merged with the other pair of the
+// warp when both touch the same single body.
 template <class HT>
 __global__ void k_pair_spmv(Dev d) {
   const int n_act = *d.act_count;
-  const int lane = threadIdx.x & 31;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_act; base += stride) {
-    const int i = base + lane;
-    int k = -1, e = 0;
-    bool live = false;
-    if (i < n_act) {
-      k = d.act_list[i];
+  const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+  const int m = j / 3, c = j - 3 * m;
+  const int n_groups = (gridDim.x * blockDim.x) >> 4;
+  for (int g0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 4; g0 < n_act; g0 += n_groups) {
+    const int i = g0 + half;                       // this half-warp's active slot
+    bool live = i < n_act;
+    int e = 0;
+    if (live) {
       e = d.act_env[i];
       live = ENVI(d, e, I_PCG) != 0;
     }
-    int cvs[4] = {0, 0, 0, 0};
-    double o[12];
-    for (int q = 0; q < 12; ++q) o[q] = 0.0;
-    int body = -2;  // -2: none yet, -1: several bodies, >= 0: the single body
-    if (live) {
-      int4 v = d.pair_v[k];
-      cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
-      HT dh[12];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        int cv = cvs[m], row = d.cv_row[cv];
-        D3 u;
-        int b = d.cv_body[cv];
-        if (b < 0) {
-          u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : PV<HT>::dir(d, row);
-        } else {
-          D3 xb = ld3(d.cv_xbar, cv);
-          u = PV<HT>::dir(d, row) + xb.x * PV<HT>::dir(d, row + 1) + xb.y * PV<HT>::dir(d, row + 2) +
-              xb.z * PV<HT>::dir(d, row + 3);
-          body = (body == -2 || body == b) ? b : -1;
-        }
-        dh[3 * m] = (HT)u.x; dh[3 * m + 1] = (HT)u.y; dh[3 * m + 2] = (HT)u.z;
-      }
-      const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)(i >> 5) * 78 * 32 + (i & 31);
-      HT acc[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) acc[q] = 0;
-#pragma unroll
-      for (int p = 0; p < 12; ++p) {
-        acc[p] += H[ut12(p, p) * 32] * dh[p];
-#pragma unroll
-        for (int q = p + 1; q < 12; ++q) {
-          HT h = H[ut12(p, q) * 32];
-          acc[p] += h * dh[q];
-          acc[q] += h * dh[p];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 12; ++q) o[q] = (double)acc[q];
-    }
-    // gel points: direct atomics
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-      if (live && d.cv_body[cvs[m]] < 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
-    // body points: J^T o, i.e. 12 values on the body's 4 sub-rows
-    double jb[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) jb[q] = 0.0;
-    if (live && body >= 0) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (d.cv_body[cvs[m]] != body) continue;
-        D3 xb = ld3(d.cv_xbar, cvs[m]);
-        const double w4[4] = {1.0, xb.x, xb.y, xb.z};
-#pragma unroll
-        for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) jb[3 * s4 + c] += w4[s4] * o[3 * m + c];
+    int4 v = live ? d.act_v[i] : make_int4(0, 0, 0, 0);
+    const int cv = m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+    // body of each point of the pair (-1: gel) and the pair's single body
+    int b_pt = -1, row = 0;
+    double xb[3] = {0, 0, 0};
+    HT dj = 0;
+    if (live && j < 12) {
+      row = d.cv_row[cv];
+      b_pt = d.cv_body[cv];
+      if (b_pt < 0) {
+        dj = (d.row_kind[row] == ROW_PINNED) ? (HT)0 : (HT)comp(PV<HT>::dir(d, row), c);
+      } else {
+        D3 x3 = ld3(d.cv_xbar, cv);
+        xb[0] = x3.x; xb[1] = x3.y; xb[2] = x3.z;
+        dj = (HT)(comp(PV<HT>::dir(d, row), c) + xb[0] * comp(PV<HT>::dir(d, row + 1), c) +
+                  xb[1] * comp(PV<HT>::dir(d, row + 2), c) + xb[2] * comp(PV<HT>::dir(d, row + 3), c));
       }
     }
-    // one reduction and 12 atomics per distinct body in the warp (lanes are
-    // consecutive active pairs, mostly of one env and so of one body)
-    const int key = (live && body >= 0) ? body : -1;
-    unsigned todo = __ballot_sync(0xffffffffu, key >= 0);
-    while (todo) {
-      const int leader = __ffs(todo) - 1;
-      const int k0 = __shfl_sync(0xffffffffu, key, leader);
-      const bool mine = key == k0;
-      const int br = d.body_row[k0];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        double t = mine ? jb[q] : 0.0;
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-        if (lane == leader) atomicAdd(d.qc + 3 * br + q, t);
+    // row j of H d
+    HT oj = 0;
+    const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)(i >> 5) * 78 * 32 + (i & 31);
+    for (int q = 0; q < 12; ++q) {
+      const HT dq = __shfl_sync(0xffffffffu, dj, (lane & 16) + q);
+      if (live && j < 12) {
+        const int lo = min(j, q), hi = max(j, q);
+        oj += H[ut12(lo, hi) * 32] * dq;
       }
-      todo &= ~__ballot_sync(0xffffffffu, mine);
     }
-    if (live && body == -1) {  // points of several bodies: per point
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (d.cv_body[cvs[m]] >= 0) scatter_cv(d, d.qc, cvs[m], D3{o[3 * m], o[3 * m + 1], o[3 * m + 2]});
+    const double o = (double)oj;
+    // gel points: one atomic per coordinate
+    if (live && j < 12 && b_pt < 0 && d.row_kind[row] != ROW_PINNED) atomicAdd(d.qc + 3 * row + c, o);
+    // body points: the pair's single body (or several: per point)
+    int bm[4];
+    for (int mm = 0; mm < 4; ++mm) bm[mm] = __shfl_sync(0xffffffffu, b_pt, (lane & 16) + 3 * mm);
+    int body = -2;
+    for (int mm = 0; mm < 4; ++mm)
+      if (bm[mm] >= 0) body = (body == -2 || body == bm[mm]) ? bm[mm] : -1;
+    if (!live) body = -2;
+    // lane j = 3 s + c of the group: sub-row s of J^T o, component c
+    const int s4 = j / 3;
+    double jb = 0.0;
+    for (int mm = 0; mm < 4; ++mm) {
+      const int src = (lane & 16) + 3 * mm;          // holds point mm's xbar
+      const double om = __shfl_sync(0xffffffffu, o, src + c);
+      const double x0 = __shfl_sync(0xffffffffu, xb[0], src);
+      const double x1 = __shfl_sync(0xffffffffu, xb[1], src);
+      const double x2 = __shfl_sync(0xffffffffu, xb[2], src);
+      const double xs = s4 == 0 ? 1.0 : (s4 == 1 ? x0 : (s4 == 2 ? x1 : x2));
+      if (body >= 0 && bm[mm] == body) jb += xs * om;
+    }
+    // the two pairs of the warp on the same body: one atomic for both
+    const int other = __shfl_xor_sync(0xffffffffu, body, 16);
+    const double jb_other = __shfl_xor_sync(0xffffffffu, jb, 16);
+    if (body >= 0 && j < 12) {
+      if (other == body) {
+        if (half == 0) atomicAdd(d.qc + 3 * d.body_row[body] + j, jb + jb_other);
+      } else {
+        atomicAdd(d.qc + 3 * d.body_row[body] + j, jb);
+      }
+    }
+    if (body == -1 && j < 12 && b_pt >= 0) {  // points of several bodies: per point
+      const int br = d.body_row[b_pt];
+      atomicAdd(d.qc + 3 * br + c, o);
+      for (int s = 0; s < 3; ++s) atomicAdd(d.qc + 3 * (br + 1 + s) + c, xb[s] * o);
     }
   }
 }
@@ -904,9 +892,10 @@ int launch_barrier(const Dev& d, int flag, cudaStream_t s) {
   return 1;
 }
 int launch_pair_spmv(const Dev& d, cudaStream_t s) {
+  const int ctas = 148 * (d.pair_ctas_per_sm > 0 ? d.pair_ctas_per_sm : 8);
   if (!d.n_pairs_cap) return 0;
-  if (d.prec) k_pair_spmv<float><<<PAIR_GRID>>>(d);
-  else k_pair_spmv<double><<<PAIR_GRID>>>(d);
+  if (d.prec) k_pair_spmv<float><<<ctas, 128, 0, s>>>(d);
+  else k_pair_spmv<double><<<ctas, 128, 0, s>>>(d);
   return 1;
 }
 int launch_fric_setup(const Dev& d, cudaStream_t s) {

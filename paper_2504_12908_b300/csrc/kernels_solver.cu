@@ -400,9 +400,8 @@ __global__ void k_pcg_init(Dev d) {
 // qc cleared; d.q reduced per env -> alpha.
 // HT: matrix precision; the products are accumulated in HT slot by slot in
 // storage order; the contact part qc and the dot product are FP64.
-template <class HT>
+template <class HT, int U>
 __global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta_list) {
-  constexpr int U = sizeof(HT) == 4 ? 4 : 2;
   int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
@@ -844,8 +843,16 @@ int launch_pcg_init(const Dev& d, cudaStream_t s) {
 #define LISTGRID (n_cta < 0 ? d.n_rows / 128 : n_cta), 128, 0, s
 #define LISTARG (n_cta < 0 ? nullptr : d.cta_list)
 int launch_spmv(const Dev& d, cudaStream_t s, int n_cta) {
-  if (d.prec) k_spmv<float><<<LISTGRID>>>(d, LISTARG);
-  else k_spmv<double><<<LISTGRID>>>(d, LISTARG);
+  const int u = d.spmv_unroll ? d.spmv_unroll : (d.prec ? 4 : 2);
+  if (d.prec) {
+    if (u == 2) k_spmv<float, 2><<<LISTGRID>>>(d, LISTARG);
+    else if (u == 8) k_spmv<float, 8><<<LISTGRID>>>(d, LISTARG);
+    else k_spmv<float, 4><<<LISTGRID>>>(d, LISTARG);
+  } else {
+    if (u == 4) k_spmv<double, 4><<<LISTGRID>>>(d, LISTARG);
+    else if (u == 8) k_spmv<double, 8><<<LISTGRID>>>(d, LISTARG);
+    else k_spmv<double, 2><<<LISTGRID>>>(d, LISTARG);
+  }
   return 1;
 }
 int launch_pcg_update(const Dev& d, cudaStream_t s, int n_cta) {

@@ -45,6 +45,11 @@ class ipc_sensor(C.Structure):
                 ("axis_v", C.c_double * 3), ("normal", C.c_double * 3), ("pitch", C.c_double)]
 
 
+class ipc_tuning(C.Structure):
+    _fields_ = [("spmv_unroll", C.c_int), ("pair_ctas_per_sm", C.c_int), ("spmv_us", C.c_float * 3),
+                ("pair_us", C.c_float * 4)]
+
+
 class ipc_step_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("pcg_iters", C.c_int), ("ls_trials", C.c_int),
                 ("al_updates", C.c_int), ("max_pairs", C.c_int), ("newton_env_iters", C.c_longlong),
@@ -84,6 +89,7 @@ def lib():
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_set_graph_mode": (i32, [vp, i32]),
+            "ipc_autotune": (i32, [vp, i32, C.POINTER(ipc_tuning)]),
             "ipc_gel_vertex_rows": (i32, [vp, i32, i32, _ip, _ip]),
             "ipc_sensor_triangles": (i32, [vp, C.POINTER(ipc_sensor), _ip, i32, C.POINTER(i32)]),
             "ipc_tactile_maps_device": (i32, [vp, i32, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp]),
@@ -116,7 +122,7 @@ EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
             "ipc_read_gel_surface_all_noalloc", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
-            "ipc_tactile_maps_device", "ipc_markers_device",
+            "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
             "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
@@ -418,6 +424,15 @@ class Envs:
         self._check(lib().ipc_markers_device(self._ctx, m, _vp(prep["rows"]), _vp(prep["bary"]), _vp(rest),
                                              _vp(pos), _vp(flow)), "ipc_markers_device")
         return pos, flow
+
+    def autotune(self, reps: int = 10) -> dict:
+        """Pick the SpMV unroll and the contact mat-vec grid by timing them
+        on this batch's current system (call between steps)."""
+        t = ipc_tuning()
+        self._check(lib().ipc_autotune(self._ctx, int(reps), C.byref(t)), "ipc_autotune")
+        return {"spmv_unroll": t.spmv_unroll, "pair_ctas_per_sm": t.pair_ctas_per_sm,
+                "spmv_us": {u: round(float(t.spmv_us[k]), 2) for k, u in enumerate((2, 4, 8))},
+                "pair_us": {c: round(float(t.pair_us[k]), 2) for k, c in enumerate((2, 4, 8, 16))}}
 
     def set_graph_mode(self, on: bool = True):
         """Replay the PCG inner loop as a captured CUDA graph (needs a

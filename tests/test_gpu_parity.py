@@ -512,6 +512,38 @@ def test_graph_mode_matches_plain_launches(precision):
     graph.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_picks_valid_shapes_and_keeps_results(precision):
+    """ipc_autotune times the SpMV unrolls and contact mat-vec grids on the
+    ctx's own system between steps; later steps match a ctx that was not
+    tuned (to rounding: atomics order)."""
+    scs = [scenes.config2(e) for e in range(3)]
+    prm = scenes.SolverParams().parity() if precision == 0 else scenes.SolverParams()
+    prm.precision = precision
+    a = ipc.Envs([s.scene for s in scs], prm)
+    b = ipc.Envs([s.scene for s in scs], prm)
+    bound = 1e-8 if precision == 0 else 1e-5
+    for step in range(3):
+        for e, s in enumerate(scs):
+            t = a.rest_y(e)
+            t[:, :3] += s.delta(step)[:, :3]
+            a.set_targets(e, t)
+            b.set_targets(e, t)
+        sa, _ = a.step()
+        sb, _ = b.step()
+        assert np.all(sa == 0) and np.all(sb == 0)
+        if step == 0:
+            tun = a.autotune(reps=3)
+            assert tun["spmv_unroll"] in (2, 4, 8) and tun["pair_ctas_per_sm"] in (2, 4, 8, 16)
+            assert all(v > 0 for v in tun["spmv_us"].values())
+        for e in range(3):
+            xa, xb = a.get_state(e)[0], b.get_state(e)[0]
+            diag = np.linalg.norm(xa.max(0) - xa.min(0))
+            assert np.abs(xa - xb).max() <= bound * diag
+    a.close()
+    b.close()
+
+
 # ------------------------------------------------------------------ mixed precision
 def _mixed(prm):
     prm = scenes.SolverParams(**prm.__dict__)
