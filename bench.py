@@ -58,6 +58,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The timed region of the slowest rank (every rank gets it)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(envs_per_rank: int, steps: int, world: int, ms: float) -> float:
+    """env-steps/s of the whole job: every rank advanced its own envs (weak
+    scaling over independent envs), divided by the slowest rank's time."""
+    return envs_per_rank * steps * world / (ms / 1e3)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -278,16 +294,12 @@ def time_precision(args, scene, params, deltas, precision, local, world, profile
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = genv.launch_count() - launches0
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), world, f"cuda:{local}")
     prof = genv.profile() if profile else {}
     genv.profile_enable(False)
     step_ms = [a_.elapsed_time(b_) for a_, b_ in ev]
     n_bad = int(sum(int(np.sum(s_ != 0)) for s_ in statuses))
-    return {"genv": genv, "value": args.envs * args.steps * world / (ms_total / 1e3), "ms_total": ms_total,
+    return {"genv": genv, "value": whole_job_rate(args.envs, args.steps, world, ms_total), "ms_total": ms_total,
             "step_ms": step_ms, "tot": tot, "prof": prof, "clocks": clk, "launches": launches, "n_bad": n_bad,
             "statuses": statuses, "deltas": deltas, "com": com, "n_total": n_total, "dev_tg": dev_tg,
             "tuning": tuning}

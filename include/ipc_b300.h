@@ -178,7 +178,8 @@ typedef struct {
 /* Choose the SpMV's slots in flight per lane and the contact mat-vec's grid
  * size by timing `reps` launches of each candidate on this ctx's current
  * system (call it after at least one ipc_step, between steps), with every
- * env counted as iterating.  It touches only PCG scratch (q, the PCG
+ * env counted as iterating.  A candidate replaces the default shape only
+ * when it is more than 5% faster.  It touches only PCG scratch (q, the PCG
  * scalars) and clears the contact accumulator afterwards, so later steps
  * give the same results as before apart from the launch shapes.  Any
  * captured PCG graph is dropped and re-captured at the next solve.  Not in

@@ -164,6 +164,25 @@ IPC_HD void psd_project(T* H, T* work) {
     }
 }
 
+// True when the symmetric n x n matrix is positive definite (Cholesky runs
+// to the end with positive pivots).  work: n * n.
+template <int n, class T>
+IPC_HD bool is_pos_def(const T* A, T* work) {
+  T* L = work;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      T s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (!(s > T(0))) return false;
+        L[i * n + i] = sqrt(s);
+      } else {
+        L[i * n + j] = s / L[j * n + j];
+      }
+    }
+  return true;
+}
+
 // Inverse of a symmetric positive definite n x n matrix by Gauss-Jordan with
 // partial pivoting (small n).  Returns false if singular.
 template <int n, class T>

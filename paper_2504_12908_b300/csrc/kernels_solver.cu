@@ -190,7 +190,9 @@ __global__ void k_body(Dev d) {
           if (mm == n) v += AAt[3 * i + j];
           Ho[(3 * mm + i) * 9 + 3 * n + j] = 4.0 * ko * v;
         }
-  psd_project<9, double>(Ho, work);
+  // a positive definite Hessian is its own projection (the common case near
+  // rigid states); the eigen-decomposition only runs otherwise
+  if (!is_pos_def<9, double>(Ho, work)) psd_project<9, double>(Ho, work);
   double* H = d.body_H + 144 * (long long)b;
   for (int i = 0; i < 144; ++i) H[i] = 0.0;
   for (int c = 0; c < 3; ++c) H[c * 12 + c] = m;

@@ -439,6 +439,31 @@ def test_state_round_trip_and_rejections():
     genv.close()
 
 
+def test_subset_and_empty_steps_touch_only_the_selected_envs():
+    # a ragged batch: a gel-only env (no bodies) next to envs with one body
+    scs = [scenes.config0(), scenes.free_fall_scene(with_body=False), scenes.small_contact_scene(body="cube")]
+    genv = ipc.Envs([s.scene for s in scs], scenes.SolverParams())
+    assert genv.sizes[1][1] == 0 and genv.max_bodies == 1
+    before = [genv.get_state(e) for e in range(3)]
+    st, stats = genv.step([])                              # empty selection: a no-op
+    assert len(st) == 0 and stats["newton_iters"] == 0
+    for e in range(3):
+        assert all(np.array_equal(a, b) for a, b in zip(genv.get_state(e), before[e]))
+    st, _ = genv.step([1])                                 # only the gel-only env moves
+    assert st[0] == ipc.IPC_OK
+    after = [genv.get_state(e) for e in range(3)]
+    for e in (0, 2):
+        assert all(np.array_equal(a, b) for a, b in zip(after[e], before[e]))
+    assert not np.array_equal(after[1][0], before[1][0])  # it falls under gravity
+    with pytest.raises(ipc.IpcError):
+        genv.step([3])                                     # out of range
+    with pytest.raises(ipc.IpcError):
+        genv.step([-1])
+    st, _ = genv.step()                                    # the whole ragged batch
+    assert np.all(st == ipc.IPC_OK)
+    genv.close()
+
+
 def test_pair_overflow_reported_and_state_kept():
     sc = scenes.config0()
     prm = sc.params
