@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed path (profiling runs); no FP64 comparison")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving"],
-                    help="batch: the uniform 256-env batch (default); serving: the Poisson request stream")
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "uneven"],
+                    help="batch: the uniform 256-env batch (default); serving: the Poisson request stream; "
+                         "uneven: 512 config-2 envs of different sizes in one launch")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: admission window (s)")
     ap.add_argument("--serve-hard", type=float, default=60.0, help="serving: stop stepping at this time (s)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
@@ -559,12 +560,71 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+def run_uneven(args):
+    """512 config-2 envs of different sizes stepped together: mixed vs plain
+    FP64 on the same batch (press phase steps after the warm-up)."""
+    import torch
+
+    import scenes
+    from paper_2504_12908_b300 import ipc
+    from paper_2504_12908_b300.build import build
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    build()
+    n = 512
+    scs = [scenes.config2(e) for e in range(n)]
+    out = {}
+    for prec in (0, 1):
+        prm = scenes.SolverParams()
+        prm.precision = prec
+        g = ipc.Envs([sc.scene for sc in scs], prm, device=f"cuda:{local}")
+        rest = [g.rest_y(e) for e in range(n)]
+        mb = g.max_bodies
+
+        def targets(k):
+            t = np.zeros((n, mb, 12))
+            for e, sc in enumerate(scs):
+                r = rest[e].copy()
+                r[:, :3] += sc.delta(k)[:, :3]
+                t[e, :r.shape[0]] = r
+            return t
+        tg = [targets(k) for k in range(args.warmup + args.steps)]
+        for k in range(args.warmup):
+            g.set_targets_all(tg[k])
+            g.step()
+        if prec == 1 and not args.no_autotune:
+            g.autotune()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        bad = 0
+        ev0.record()
+        for k in range(args.warmup, args.warmup + args.steps):
+            g.set_targets_all(tg[k])
+            st, _ = g.step()
+            bad += int(np.sum(st != 0))
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        out[prec] = {"value": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps, "status_not_ok": bad}
+        g.close()
+        torch.cuda.empty_cache()
+    line = {"metric": "env-steps/s (uneven batch)", "value": out[1]["value"], "unit": "env-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": out[1]["ms_per_step"],
+            "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "uneven batch: 512 config-2 envs (gel {16,24,32,48}^2 x {4,6}, icosphere L1-3)",
+                       "cache": "inputs larger than L2"},
+            "fp64": out[0], "mixed": out[1], "speedup_vs_fp64": out[1]["value"] / out[0]["value"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "uneven":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -26,13 +26,17 @@ __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED 
 // cta: the row CTA (row / 128), which is not blockIdx.x when the launch runs
 // a list of CTAs.  Returns true in thread 0 of the last CTA, with the sums
 // in out[0..n).
-template <int n>
+// T0: type in which the first value is summed within the CTA (FP32 for the
+// FP32 product r.z of mixed mode; the CTA partials are summed in FP64).
+template <int n, class T0 = double>
 __device__ bool env_reduce(const Dev& d, int e, int which, int cta, const double* vals /*per thread*/,
                            double* out) {
   __shared__ double sh[32];
+  __shared__ T0 sh0[32];
   __shared__ bool last;
   double part[n];
-  for (int j = 0; j < n; ++j) part[j] = block_sum(vals[j], sh);
+  part[0] = (double)block_sum((T0)vals[0], sh0);
+  for (int j = 1; j < n; ++j) part[j] = block_sum(vals[j], sh);
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
     __threadfence();
@@ -388,7 +392,7 @@ __global__ void k_pcg_init(Dev d) {
   PV<HT>::set_dir(d, r, z);
   double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
   double out[2];
-  if (env_reduce<2>(d, e, 0, r >> 7, vals, out)) {
+  if (env_reduce<2, HT>(d, e, 0, r >> 7, vals, out)) {
     ENVS(d, e, S_PBETA) = 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR0) = out[1];
@@ -468,7 +472,7 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
   PV<HT>::set_z(d, r, z);
   double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
   double out[2];
-  if (env_reduce<2>(d, e, 0, r >> 7, vals, out)) {
+  if (env_reduce<2, HT>(d, e, 0, r >> 7, vals, out)) {
     double rz_old = ENVS(d, e, S_RZ);
     ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
     ENVS(d, e, S_RZ) = out[0];
