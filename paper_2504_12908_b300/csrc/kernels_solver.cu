@@ -6,6 +6,7 @@
 // [p, a0, a1, a2] of an affine body.  Rows of one env form a contiguous range
 // padded to a multiple of 128 so that a 128-thread CTA never straddles envs.
 #include "common.cuh"
+#include "fpconv.cuh"
 #include "kernels.h"
 #include "pcgvec.cuh"
 #include "physics.cuh"
@@ -26,17 +27,18 @@ __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED 
 // cta: the row CTA (row / 128), which is not blockIdx.x when the launch runs
 // a list of CTAs.  Returns true in thread 0 of the last CTA, with the sums
 // in out[0..n).
-// T0: type in which the first value is summed within the CTA (FP32 for the
-// FP32 product r.z of mixed mode; the CTA partials are summed in FP64).
+// T0: type in which the first value (v0) is summed within the CTA (FP32 for
+// the FP32 products r.z and d.q of mixed mode); the other n - 1 values are
+// FP64, and the CTA partials are summed in FP64.
 template <int n, class T0 = double>
-__device__ bool env_reduce(const Dev& d, int e, int which, int cta, const double* vals /*per thread*/,
+__device__ bool env_reduce(const Dev& d, int e, int which, int cta, T0 v0, const double* rest /* n - 1 */,
                            double* out) {
   __shared__ double sh[32];
   __shared__ T0 sh0[32];
   __shared__ bool last;
   double part[n];
-  part[0] = (double)block_sum((T0)vals[0], sh0);
-  for (int j = 1; j < n; ++j) part[j] = block_sum(vals[j], sh);
+  part[0] = (double)block_sum(v0, sh0);
+  for (int j = 1; j < n; ++j) part[j] = block_sum(rest[j - 1], sh);
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
     __threadfence();
@@ -345,36 +347,48 @@ __global__ void k_precond_body(Dev d) {
   for (int i = 0; i < 144; ++i) d.body_pc[144 * b + i] = Mi[i];
 }
 
-// z = P^{-1} r for row r (body rows read the 4 sub-rows of their body; all of
-// them sit in the same warp).  Gel rows: 6 stored entries of the symmetric
-// 3x3 inverse, applied in HT (FP32 in mixed mode); body rows: the body's
-// 12x12 inverse in FP64.
-template <class HT>
-__device__ __forceinline__ D3 apply_pc(const Dev& d, int r, uint8_t kr) {
-  if (is_body(kr)) {
-    int b = d.row_body[r];
-    int br = d.body_row[b];
-    int kk = r - br;
-    const double* Pi = d.body_pc + 144 * (long long)b;
-    double o[3] = {0, 0, 0};
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
-    return D3{o[0], o[1], o[2]};
-  }
-  if (kr == ROW_PAD) return D3{0, 0, 0};
-  const HT* P = reinterpret_cast<const HT*>(d.pc) + 6 * (long long)r;
-  const HT a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
-  D3 x = ld3(d.r, r);
-  const HT X = (HT)x.x, Y = (HT)x.y, Z = (HT)x.z;
-  return D3{(double)(a * X + b * Y + c * Z), (double)(b * X + e * Y + f * Z), (double)(c * X + f * Y + g * Z)};
+// z = P^{-1} r for row r.  Body rows read the 4 sub-rows of their body (all
+// of them sit in the same warp) and apply the body's 12x12 inverse in FP64.
+__device__ __forceinline__ D3 apply_pc_body(const Dev& d, int r) {
+  int b = d.row_body[r];
+  int br = d.body_row[b];
+  int kk = r - br;
+  const double* Pi = d.body_pc + 144 * (long long)b;
+  double o[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
+  return D3{o[0], o[1], o[2]};
 }
 
-// r.z of a row in HT (z is an HT quantity); r.r, which decides convergence,
-// is always FP64
-template <class HT>
-__device__ __forceinline__ double dot_rz(D3 rv, D3 z) {
-  return (double)((HT)rv.x * (HT)z.x + (HT)rv.y * (HT)z.y + (HT)rv.z * (HT)z.z);
+// FP64 mode: gel rows apply the 6 stored entries of the symmetric 3x3 inverse
+__device__ __forceinline__ D3 apply_pc64(const Dev& d, int r, uint8_t kr, D3 x) {
+  if (is_body(kr)) return apply_pc_body(d, r);
+  if (kr == ROW_PAD) return D3{0, 0, 0};
+  const double* P = reinterpret_cast<const double*>(d.pc) + 6 * (long long)r;
+  const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
+  return D3{a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z};
 }
+
+// mixed mode: FP32 inverse applied to the FP32-rounded residual rf of the row
+__device__ __forceinline__ float4 apply_pc32(const Dev& d, int r, uint8_t kr, float3 x) {
+  if (is_body(kr)) {
+    const D3 z = apply_pc_body(d, r);
+    return make_float4(d2f_bits(z.x), d2f_bits(z.y), d2f_bits(z.z), 0.0f);
+  }
+  if (kr == ROW_PAD) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float* P = reinterpret_cast<const float*>(d.pc) + 6 * (long long)r;
+  const float a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
+  return make_float4(a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z, 0.0f);
+}
+
+__device__ __forceinline__ float3 round_row(D3 v) { return make_float3(d2f_bits(v.x), d2f_bits(v.y), d2f_bits(v.z)); }
+__device__ __forceinline__ D3 widen_row(float4 v) { return D3{f2d_bits(v.x), f2d_bits(v.y), f2d_bits(v.z)}; }
+
+// Mixed mode keeps FP64 for r, p and r.r only.  B300 issues FP64
+// instructions (conversions included) at a small fraction of its FP32 rate,
+// so the FP32 rows z, d, q are widened and r rounded on the integer pipe
+// (fpconv.cuh), and r.z and d.q are FP32 products summed in FP32 within a
+// CTA, in FP64 across CTAs.
 
 // PCG start: p = 0, r = -g, z = P^-1 r, d = z, beta = 0; rz, rr0
 template <class HT>
@@ -387,12 +401,22 @@ __global__ void k_pcg_init(Dev d) {
   st3(d.r, r, rv);
   st3(d.p, r, D3{0, 0, 0});
   __syncwarp();
-  D3 z = apply_pc<HT>(d, r, kr);
-  PV<HT>::set_z(d, r, z);
-  PV<HT>::set_dir(d, r, z);
-  double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
+  const double rr = dot(rv, rv);
   double out[2];
-  if (env_reduce<2, HT>(d, e, 0, r >> 7, vals, out)) {
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    const float3 rf = round_row(rv);
+    const float4 z = apply_pc32(d, r, kr, rf);
+    d.z4[r] = z;
+    d.d4[r] = z;
+    last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
+  } else {
+    const D3 z = apply_pc64(d, r, kr, rv);
+    PV<double>::set_z(d, r, z);
+    PV<double>::set_dir(d, r, z);
+    last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
+  }
+  if (last) {
     ENVS(d, e, S_PBETA) = 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR0) = out[1];
@@ -405,7 +429,8 @@ __global__ void k_pcg_init(Dev d) {
 // q = A d + qc (SELL-32, one row per thread, U slots in flight per lane),
 // qc cleared; d.q reduced per env -> alpha.
 // HT: matrix precision; the products are accumulated in HT slot by slot in
-// storage order; the contact part qc and the dot product are FP64.
+// storage order.  FP64 mode: the contact part qc is added and d.q formed in
+// FP64; mixed: qc is rounded into the FP32 row q and d.q is an FP32 product.
 template <class HT, int U>
 __global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta_list) {
   int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
@@ -445,12 +470,22 @@ __global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta
     ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
     az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
   }
-  D3 acc = ld3(d.qc, r) + D3{(double)ax, (double)ay, (double)az};
-  PV<HT>::set_q(d, r, acc);
+  const D3 qc = ld3(d.qc, r);
   st3(d.qc, r, D3{0, 0, 0});
-  double vals[1] = {dot(PV<HT>::dir(d, r), acc)};
   double out[1];
-  if (env_reduce<1>(d, e, 1, r >> 7, vals, out)) {
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    const float3 c3 = round_row(qc);
+    const float4 q = make_float4(ax + c3.x, ay + c3.y, az + c3.z, 0.0f);
+    d.q4[r] = q;
+    const float4 w = d.d4[r];
+    last = env_reduce<1, float>(d, e, 1, r >> 7, w.x * q.x + w.y * q.y + w.z * q.z, nullptr, out);
+  } else {
+    const D3 acc = qc + D3{(double)ax, (double)ay, (double)az};
+    PV<double>::set_q(d, r, acc);
+    last = env_reduce<1>(d, e, 1, r >> 7, dot(PV<double>::dir(d, r), acc), nullptr, out);
+  }
+  if (last) {
     ENVS(d, e, S_DQ) = out[0];
     ENVS(d, e, S_PALPHA) = (out[0] > 0.0) ? ENVS(d, e, S_RZ) / out[0] : 0.0;
   }
@@ -464,15 +499,30 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
   if (!ENVI(d, e, I_PCG)) return;
   uint8_t kr = d.row_kind[r];
   double al = ENVS(d, e, S_PALPHA);
-  st3(d.p, r, ld3(d.p, r) + al * PV<HT>::dir(d, r));
-  D3 rv = ld3(d.r, r) - al * PV<HT>::q(d, r);
-  st3(d.r, r, rv);
-  __syncwarp();
-  D3 z = apply_pc<HT>(d, r, kr);
-  PV<HT>::set_z(d, r, z);
-  double vals[2] = {dot_rz<HT>(rv, z), dot(rv, rv)};
   double out[2];
-  if (env_reduce<2, HT>(d, e, 0, r >> 7, vals, out)) {
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    const float4 dd = d.d4[r], qq = d.q4[r];
+    st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
+    const D3 rv = ld3(d.r, r) - al * widen_row(qq);
+    st3(d.r, r, rv);
+    __syncwarp();
+    const double rr = dot(rv, rv);
+    const float3 rf = round_row(rv);
+    const float4 z = apply_pc32(d, r, kr, rf);
+    d.z4[r] = z;
+    last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
+  } else {
+    st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r));
+    const D3 rv = ld3(d.r, r) - al * PV<double>::q(d, r);
+    st3(d.r, r, rv);
+    __syncwarp();
+    const double rr = dot(rv, rv);
+    const D3 z = apply_pc64(d, r, kr, rv);
+    PV<double>::set_z(d, r, z);
+    last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
+  }
+  if (last) {
     double rz_old = ENVS(d, e, S_RZ);
     ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
     ENVS(d, e, S_RZ) = out[0];
@@ -490,12 +540,12 @@ __global__ void k_pcg_dir(Dev d, const int* __restrict__ cta_list) {
   int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
-  if (sizeof(HT) == 4) {
-    const float be = (float)ENVS(d, e, S_PBETA);
+  if constexpr (sizeof(HT) == 4) {
+    const float be = d2f_bits(ENVS(d, e, S_PBETA));
     const float4 z = d.z4[r], dd = d.d4[r];
     d.d4[r] = make_float4(z.x + be * dd.x, z.y + be * dd.y, z.z + be * dd.z, 0.0f);
   } else {
-    PV<HT>::set_dir(d, r, PV<HT>::z(d, r) + ENVS(d, e, S_PBETA) * PV<HT>::dir(d, r));
+    PV<double>::set_dir(d, r, PV<double>::z(d, r) + ENVS(d, e, S_PBETA) * PV<double>::dir(d, r));
   }
 }
 
