@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed path (profiling runs); no FP64 comparison")
-    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "uneven"],
+    ap.add_argument("--workload", default="batch", choices=["batch", "serving", "uneven", "self_contact"],
                     help="batch: the uniform 256-env batch (default); serving: the Poisson request stream; "
-                         "uneven: 512 config-2 envs of different sizes in one launch")
+                         "uneven: 512 config-2 envs of different sizes in one launch; "
+                         "self_contact: 1024 two-block pads pressed together (gel self-contact)")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="serving: admission window (s)")
     ap.add_argument("--serve-hard", type=float, default=60.0, help="serving: stop stepping at this time (s)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
@@ -341,11 +342,9 @@ def per_step_error(g64, g32, tg, body_radius):
 # launch of `bench.py --only-mixed --steps 1 --warmup 1` under ncu
 # (profiles/k_spmv_traffic_mixed_256env_gel40x40x6.md).  Reported only while
 # the kernel's source is the one that was measured (hash of its text).
-# (measured with 4 slots in flight per lane; the hash is of the source after
-# the slot count became a template parameter, which left that variant's code
-# unchanged)
-SPMV_TRAFFIC = {"envs": 256, "bytes": 1275239936 + 93181952,
-                "source_sha256": "663696f6bbf2d3b967a562b364f5b7131ae2a4cac5d64cf8c5acb6a899a94650"}
+# (measured with 4 slots in flight per lane)
+SPMV_TRAFFIC = {"envs": 256, "bytes": 1275934208 + 90306816,
+                "source_sha256": "830203d985315711f5332876ced428e43c65ae8bc3a3b875c54921744617e589"}
 
 
 def _spmv_source_hash() -> str:
@@ -560,19 +559,18 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
-def run_uneven(args):
-    """512 config-2 envs of different sizes stepped together: mixed vs plain
-    FP64 on the same batch (press phase steps after the warm-up)."""
+def _mixed_vs_fp64(args, scs):
+    """Step one batch of scenarios in mixed precision and in plain FP64 (the
+    same scripted targets; K timed steps after W warm-up steps)."""
     import torch
 
-    import scenes
     from paper_2504_12908_b300 import ipc
     from paper_2504_12908_b300.build import build
+    import scenes
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
     build()
-    n = 512
-    scs = [scenes.config2(e) for e in range(n)]
+    n = len(scs)
     out = {}
     for prec in (0, 1):
         prm = scenes.SolverParams()
@@ -608,12 +606,39 @@ def run_uneven(args):
         out[prec] = {"value": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps, "status_not_ok": bad}
         g.close()
         torch.cuda.empty_cache()
-    line = {"metric": "env-steps/s (uneven batch)", "value": out[1]["value"], "unit": "env-steps/s", "n_gpus": 1,
+    return out
+
+
+def _batch_line(args, out, metric, workload):
+    return {"metric": metric, "value": out[1]["value"], "unit": "env-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": out[1]["ms_per_step"],
             "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "uneven batch: 512 config-2 envs (gel {16,24,32,48}^2 x {4,6}, icosphere L1-3)",
-                       "cache": "inputs larger than L2"},
+            "config": {"workload": workload, "cache": "inputs larger than L2"},
             "fp64": out[0], "mixed": out[1], "speedup_vs_fp64": out[1]["value"] / out[0]["value"]}
+
+
+def run_uneven(args):
+    """512 config-2 envs of different sizes stepped together: mixed vs plain
+    FP64 on the same batch (press phase steps after the warm-up)."""
+    import scenes
+    out = _mixed_vs_fp64(args, [scenes.config2(e) for e in range(512)])
+    print(json.dumps(_batch_line(args, out, "env-steps/s (uneven batch)",
+                                 "uneven batch: 512 config-2 envs (gel {16,24,32,48}^2 x {4,6}, icosphere L1-3)")),
+          flush=True)
+
+
+def run_self_contact(args):
+    """Gel self-contact batch: 1024 envs of one pad made of two blocks that a
+    driven cube presses together (seeded press depth per env), mixed vs
+    plain FP64."""
+    import scenes
+    scs = [scenes.self_contact_scene(depth=float(np.random.default_rng(6000 + e).uniform(5e-5, 1.5e-4)))
+           for e in range(1024)]
+    out = _mixed_vs_fp64(args, scs)
+    line = _batch_line(args, out, "env-steps/s (self-contact batch)",
+                       "self-contact batch: 1024 envs x (two-block pad, 82 gel vertices, 125 tets, "
+                       "self-contact on) + driven 3 mm cube")
+    line["config"]["cache"] = "working set within L2 (small envs)"
     print(json.dumps(line), flush=True)
 
 
@@ -625,6 +650,8 @@ def main():
         run_serving(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "self_contact":
+        run_self_contact(args)
     else:
         run_ours(args)
 

@@ -119,6 +119,14 @@ typedef struct {
   const double* body_rho;      /* [n_bodies] density                         */
   const double* body_kappa_s;  /* [n_bodies] orthogonality stiffness, Pa     */
   const uint8_t* body_driven;  /* [n_bodies] 1 = follows ipc_set_targets     */
+  const uint8_t* pad_self_contact; /* [n_pads] (n_pads = 1 + max pad_id): 1 =
+                                  the pad's own primitives that share no
+                                  vertex pair up too (gel self-contact, the
+                                  soft-soft contact of the soft-block
+                                  pressing comparison, Fig. sim-compare b);
+                                  NULL = no pad self-contacts.  Candidate
+                                  search within such a pad is quadratic in
+                                  its surface size.                          */
 } ipc_scene_desc;
 
 typedef struct {

@@ -1,16 +1,22 @@
 """Brute-force candidate pairs (oracle side).
 
 Pairs (App. A.3): point-triangle and edge-edge pairs between surface
-primitives.  Reading: only primitives of different objects pair up
-(gel pads and affine bodies are objects; gel self-contact is not modelled),
-pairs whose four vertices are all fixed are dropped, and a gel pad never
-pairs with the body it is attached to.
+primitives.  Readings: primitives of different objects pair up (gel pads and
+affine bodies are objects); a pad flagged for self-contact also pairs its own
+primitives that share no vertex (a point against a triangle not incident to
+it, two edges without a common end point), which is the soft-soft contact of
+a gel with itself; an affine body never pairs with itself (it is rigid up to
+its affine modes).  Pairs whose four vertices are all fixed are dropped, and
+a gel pad never pairs with the body it is attached to.
 
 Candidate test: axis-aligned boxes of the two primitives, each taken over the
 primitive's vertices (and, for the swept set, over their positions at both
 ends of the step), overlap after widening by dhat:
     lo_a <= hi_b + dhat  and  lo_b <= hi_a + dhat   on every axis
 (closed intervals; a pair closer than dhat always passes).
+
+Object pairs that never pair are one set of ordered (a, b) object ids; an
+object that does not self-contact appears there as (a, a).
 """
 from __future__ import annotations
 
@@ -42,7 +48,8 @@ def _overlap(loA, hiA, loB, hiB, dhat, chunk=2048):
 
 
 def excluded_object_pairs(scene) -> set:
-    """(pad, body-object) pairs excluded because the pad is attached to it."""
+    """Object pairs that never pair: (pad, body) when the pad is attached to
+    the body, and (o, o) for every object that does not self-contact."""
     n_pads = int(scene.gel_obj.max()) + 1 if scene.n_verts else 0
     ex = set()
     m = scene.attach >= 0
@@ -50,15 +57,21 @@ def excluded_object_pairs(scene) -> set:
         o = n_pads + int(b)
         ex.add((int(pad), o))
         ex.add((o, int(pad)))
+    selfc = np.zeros(n_pads, bool) if scene.self_contact is None else np.asarray(scene.self_contact, bool)
+    for o in range(n_pads + len(scene.bodies)):
+        if o >= n_pads or not selfc[o]:
+            ex.add((o, o))
     return ex
 
 
 def candidates(sd, Xc: np.ndarray, dhat: float, excluded: set, Xc_end=None):
     """Returns (pt (n,2) [point cv id, tri index], ee (m,2) [edge, edge]).
 
-    PT pairs: every point against every triangle of another object.
-    EE pairs: edge a of object oa against edge b of object ob with oa < ob.
-    Rows are sorted lexicographically.
+    PT pairs: every point against every triangle of another object, and of
+    its own object when that object self-contacts and the triangle does not
+    contain the point.  EE pairs: edge a of object oa against edge b of
+    object ob with oa < ob, or, within a self-contacting object, edges a < b
+    with no common vertex.  Rows are sorted lexicographically.
     """
     plo, phi = _boxes(Xc, sd.points[:, None], Xc_end)
     tlo, thi = _boxes(Xc, sd.tris, Xc_end)
@@ -69,17 +82,26 @@ def candidates(sd, Xc: np.ndarray, dhat: float, excluded: set, Xc_end=None):
         pa = np.nonzero(sd.point_obj == oa)[0]
         ea = np.nonzero(sd.edge_obj == oa)[0]
         for ob in objs:
-            if oa == ob or (oa, ob) in excluded:
+            if (oa, ob) in excluded:
                 continue
             tb = np.nonzero(sd.tri_obj == ob)[0]
             if len(pa) and len(tb):
                 i, j = _overlap(plo[pa], phi[pa], tlo[tb], thi[tb], dhat)
-                pts.append(np.stack([sd.points[pa[i]], tb[j]], axis=1))
-            if oa < ob:
+                p, t = sd.points[pa[i]], tb[j]
+                if oa == ob:  # the point must not be a vertex of the triangle
+                    keep = np.all(sd.tris[t] != p[:, None], axis=1)
+                    p, t = p[keep], t[keep]
+                pts.append(np.stack([p, t], axis=1))
+            if oa <= ob:
                 eb = np.nonzero(sd.edge_obj == ob)[0]
                 if len(ea) and len(eb):
                     i, j = _overlap(elo[ea], ehi[ea], elo[eb], ehi[eb], dhat)
-                    ees.append(np.stack([ea[i], eb[j]], axis=1))
+                    a, b = ea[i], eb[j]
+                    if oa == ob:  # each unordered pair once, no common vertex
+                        A, B = sd.edges[a], sd.edges[b]
+                        keep = (a < b) & np.all(A[:, :, None] != B[:, None, :], axis=(1, 2))
+                        a, b = a[keep], b[keep]
+                    ees.append(np.stack([a, b], axis=1))
     pt = np.concatenate(pts) if pts else np.zeros((0, 2), np.int64)
     ee = np.concatenate(ees) if ees else np.zeros((0, 2), np.int64)
     # drop pairs whose four vertices are all fixed
@@ -96,10 +118,16 @@ def candidates(sd, Xc: np.ndarray, dhat: float, excluded: set, Xc_end=None):
 
 def canonical(sd, pt: np.ndarray, ee: np.ndarray):
     """Vertex-id form used to compare candidate sets across implementations:
-    PT -> (p, sorted triangle vertices), EE -> (sorted edge a, sorted edge b)
-    with the edge of the lower object first."""
+    PT -> (p, sorted triangle vertices), EE -> the two sorted edges, the
+    lexicographically smaller first (an EE pair is unordered)."""
     a = np.concatenate([pt[:, :1], np.sort(sd.tris[pt[:, 1]], axis=1)], axis=1) if len(pt) else np.zeros((0, 4), np.int64)
-    b = np.concatenate([np.sort(sd.edges[ee[:, 0]], axis=1), np.sort(sd.edges[ee[:, 1]], axis=1)], axis=1) if len(ee) else np.zeros((0, 4), np.int64)
+    if len(ee):
+        e0, e1 = np.sort(sd.edges[ee[:, 0]], axis=1), np.sort(sd.edges[ee[:, 1]], axis=1)
+        swap = (e0[:, 0] > e1[:, 0]) | ((e0[:, 0] == e1[:, 0]) & (e0[:, 1] > e1[:, 1]))
+        e0[swap], e1[swap] = e1[swap].copy(), e0[swap].copy()
+        b = np.concatenate([e0, e1], axis=1)
+    else:
+        b = np.zeros((0, 4), np.int64)
     a = a[np.lexsort(a.T[::-1])] if len(a) else a
     b = b[np.lexsort(b.T[::-1])] if len(b) else b
     return a, b

@@ -117,6 +117,9 @@ __device__ void emit_pair(const Dev& d, int e, int4 v, int kind, double w, doubl
 //   QK = 0: points of A vs triangles of B   -> PT(point A, tri B)
 //   QK = 1: triangles of A vs points of B   -> PT(point B, tri A)
 //   QK = 2: edges of A vs edges of B        -> EE(lower object first)
+// A self-contacting pad (its own exclusion bit clear) also gets the item
+// (q, A) for its points and edges: QK = 0 covers its own PT pairs and
+// QK = 2 its own EE pairs; QK = 1 would repeat the PT pairs.
 // Items of one warp are written contiguously (one atomic per warp).
 template <int QK>
 __global__ void k_worklist(Dev d, int flag) {
@@ -140,8 +143,9 @@ __global__ void k_worklist(Dev d, int flag) {
   // pass 1: count the objects this query meets; pass 2 (after the warp scan)
   // writes them, re-evaluating the same test
   auto keep = [&](int B) {
-    return !(B == A || ((ex >> d.obj_local[B]) & 1ull) || !bigger(d, A, B)) &&
-           overlap6(qb, d.obj_box + 6 * B, d.dhat);
+    if ((ex >> d.obj_local[B]) & 1ull) return false;
+    if (B == A ? QK == 1 : !bigger(d, A, B)) return false;
+    return overlap6(qb, d.obj_box + 6 * B, d.dhat);
   };
   if (live)
     for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1]; ++B) cnt += keep(B) ? 1 : 0;
@@ -165,7 +169,10 @@ __global__ void k_worklist(Dev d, int flag) {
 }
 
 // Broad phase, stage 2: every item tests its query box against the boxes of
-// the other object's primitives of the complementary kind.
+// the other object's primitives of the complementary kind.  Within one
+// (self-contacting) object: a point never pairs with a triangle it is a
+// vertex of, and an edge pairs only with edges of higher index that share
+// no vertex with it.
 __global__ void k_pairs(Dev d) {
   const int n = min(*d.bp_count, d.bp_cap);
   const double dh = d.dhat;
@@ -176,9 +183,11 @@ __global__ void k_pairs(Dev d) {
     if (qk == 0) {
       const double* qb = d.cv_box + 6 * (long long)i;
       bool qfix = d.cv_fixed[i];
+      const bool self = d.cv_obj[i] == B;
       for (int t = d.obj_tri_begin[B]; t < d.obj_tri_end[B]; ++t) {
         if (!overlap6(qb, d.tri_box + 6 * (long long)t, dh)) continue;
         int t0 = d.tri[3 * t], t1 = d.tri[3 * t + 1], t2 = d.tri[3 * t + 2];
+        if (self && (i == t0 || i == t1 || i == t2)) continue;
         if (qfix && d.cv_fixed[t0] && d.cv_fixed[t1] && d.cv_fixed[t2]) continue;
         emit_pair(d, e, make_int4(i, t0, t1, t2), 0, wscale * 0.5 * d.cv_area[i], 0.0);
       }
@@ -196,13 +205,15 @@ __global__ void k_pairs(Dev d) {
       int q0 = d.edge[2 * i], q1 = d.edge[2 * i + 1];
       bool qfix = d.cv_fixed[q0] && d.cv_fixed[q1];
       int A = d.edge_obj[i];
-      for (int f = d.obj_edge_begin[B]; f < d.obj_edge_end[B]; ++f) {
+      const bool self = A == B;
+      for (int f = self ? i + 1 : d.obj_edge_begin[B]; f < d.obj_edge_end[B]; ++f) {
         if (!overlap6(qb, d.edge_box + 6 * (long long)f, dh)) continue;
         int b0 = d.edge[2 * f], b1 = d.edge[2 * f + 1];
+        if (self && (b0 == q0 || b0 == q1 || b1 == q0 || b1 == q1)) continue;
         if (qfix && d.cv_fixed[b0] && d.cv_fixed[b1]) continue;
         double w = wscale * 0.25 * (d.edge_area[i] + d.edge_area[f]);
         double eps = d.ee_moll * d.edge_len2[i] * d.edge_len2[f];
-        int4 v = (A < B) ? make_int4(q0, q1, b0, b1) : make_int4(b0, b1, q0, q1);
+        int4 v = (A <= B) ? make_int4(q0, q1, b0, b1) : make_int4(b0, b1, q0, q1);
         emit_pair(d, e, v, 1, w, eps);
       }
     }

@@ -441,7 +441,10 @@ bool build_local(const ipc_scene_desc& s, int e, const ipc_params& prm, EnvLocal
     L.obj_te.push_back(ntri);
     L.obj_eb.push_back(eb);
     L.obj_ee.push_back(nedge);
-    L.obj_ex.push_back(1ull << o);
+    // an object never pairs with itself, except a pad flagged for
+    // self-contact (its own primitives that share no vertex pair up)
+    const bool self = o < n_pads && s.pad_self_contact && s.pad_self_contact[o];
+    L.obj_ex.push_back(self ? 0ull : 1ull << o);
   }
   for (int u = 0; u < N; ++u)
     if (attach[u] >= 0) {

@@ -93,7 +93,8 @@ struct Pack {
   // objects
   std::vector<int> obj_env, obj_local, obj_cv_begin, obj_cv_end, obj_tri_begin, obj_tri_end,
       obj_edge_begin, obj_edge_end, obj_size;
-  std::vector<unsigned long long> obj_exclude;  // bit j: never pair with env-local object j
+  std::vector<unsigned long long> obj_exclude;  // bit j: never pair with env-local object j;
+                                                // own bit clear: self-contact
   // coated surface rows (read_gel_surface)
   std::vector<int> coated_row;
 };

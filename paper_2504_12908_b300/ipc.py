@@ -37,7 +37,8 @@ class ipc_scene_desc(C.Structure):
     _fields_ = [("n_verts", C.c_int), ("n_tets", C.c_int), ("rest_x", _dp), ("tets", _ip), ("pad_id", _ip),
                 ("pinned", _up), ("attach_body", _ip), ("E", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
                 ("n_bodies", C.c_int), ("body_nv", _ip), ("body_rest_x", _dp), ("body_nt", _ip),
-                ("body_tris", _ip), ("body_rho", _dp), ("body_kappa_s", _dp), ("body_driven", _up)]
+                ("body_tris", _ip), ("body_rho", _dp), ("body_kappa_s", _dp), ("body_driven", _up),
+                ("pad_self_contact", _up)]
 
 
 class ipc_sensor(C.Structure):
@@ -177,6 +178,8 @@ class _SceneArrays:
         self.brho = np.array([b.rho for b in bs], dtype=np.float64)
         self.bk = np.array([b.kappa_s for b in bs], dtype=np.float64)
         self.bd = np.array([1 if b.driven else 0 for b in bs], dtype=np.uint8)
+        selfc = getattr(sc, "self_contact", None)
+        self.selfc = None if selfc is None else np.ascontiguousarray(np.asarray(selfc, dtype=bool), dtype=np.uint8)
         d = ipc_scene_desc()
         d.n_verts, d.n_tets = self.x.shape[0], self.t.shape[0]
         d.rest_x, d.tets, d.pad_id = _ptr(self.x, _dp), _ptr(self.t, _ip), _ptr(self.pad, _ip)
@@ -186,6 +189,11 @@ class _SceneArrays:
         d.body_nv, d.body_rest_x, d.body_nt = _ptr(self.bnv, _ip), _ptr(self.bx, _dp), _ptr(self.bnt, _ip)
         d.body_tris, d.body_rho, d.body_kappa_s = _ptr(self.bt, _ip), _ptr(self.brho, _dp), _ptr(self.bk, _dp)
         d.body_driven = _ptr(self.bd, _up)
+        if self.selfc is not None:
+            n_pads = int(self.pad.max()) + 1 if self.pad.size else 1
+            if self.selfc.shape != (n_pads,):
+                raise ValueError(f"self_contact needs one flag per pad ({n_pads})")
+            d.pad_self_contact = _ptr(self.selfc, _up)
         self.desc = d
 
 

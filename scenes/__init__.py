@@ -15,7 +15,9 @@ Scene layout (all SI units, float64 coordinates):
   held fixed (the bottom face of a pad resting on a table), ``attach`` gives,
   per vertex, the index of the affine body that drives it (``-1`` = free),
   which models the sensor-attached region of a gel pad (Sec. 4.1, "Tactile
-  Sensors Modeling").
+  Sensors Modeling").  ``self_contact`` (optional, one flag per pad) lets
+  the primitives of a pad that share no vertex touch one another: gel
+  self-contact (soft-soft contact within one pad).
 * Each affine body is a closed, outward-oriented triangle surface given at its
   rest placement in world coordinates.  Its reduced state is
   ``y = [p, a0, a1, a2]`` where ``p`` is the world position of its centre of
@@ -36,7 +38,7 @@ __all__ = [
     "Body", "Scene", "Scenario", "SolverParams",
     "gel_grid", "icosphere", "box_surface",
     "config0", "config1", "config2", "config3", "small_contact_scene",
-    "free_fall_scene", "spin_scene",
+    "free_fall_scene", "spin_scene", "self_contact_scene",
 ]
 
 
@@ -64,6 +66,7 @@ class Scene:
     rho: float                  # gel density, kg/m^3
     bodies: List[Body] = field(default_factory=list)
     name: str = ""
+    self_contact: Optional[np.ndarray] = None   # (n_pads,) bool, None = no pad self-contacts
 
     @property
     def n_verts(self) -> int:
@@ -435,6 +438,35 @@ def small_contact_scene(nx=5, ny=5, nz=3, body="cube", level=1, radius=2e-3,
 
     def delta(step):
         return np.array([[0.0, 0.0, -(gap + depth) * min(step + 1, n_steps) / n_steps]])
+    return Scenario(scene=scene, params=params, n_steps=n_steps, delta=delta)
+
+
+def self_contact_scene(nx=5, ny=5, nz=2, nu_xy=4, gap=5e-5, depth=1e-4, n_steps=4,
+                       self_contact=True, with_body=True) -> Scenario:
+    """Gel self-contact: one pad made of two blocks, a pinned 10x10x2 mm base
+    and a free 6x6x2 mm block resting `gap` above it (slightly offset so that
+    no vertices line up), pressed onto the base by a driven 3 mm cube.  Both
+    blocks are the same pad, so the contact between them exists only as
+    self-contact of the pad."""
+    xl, tl, bl, _ = gel_grid(nx, ny, nz, size=(0.01, 0.01, 0.002))
+    xu, tu, _, _ = gel_grid(nu_xy, nu_xy, nz, size=(0.006, 0.006, 0.002),
+                            origin=(-0.003 + 3e-4, -0.003 + 1e-4, gap))
+    x = np.concatenate([xl, xu])
+    tets = np.concatenate([tl, tu + xl.shape[0]]).astype(np.int32)
+    n = x.shape[0]
+    pinned = np.concatenate([bl, np.zeros(xu.shape[0], bool)])
+    bodies = []
+    if with_body:
+        s3, z0 = 3e-3, gap + 0.002 + gap
+        bx, bt = box_surface((-s3 / 2 + 2e-4, -s3 / 2 + 3e-4, z0), (s3 / 2 + 2e-4, s3 / 2 + 3e-4, z0 + s3))
+        bodies.append(Body(rest_x=bx, tris=bt, rho=1200.0, kappa_s=1e8, driven=True))
+    scene = Scene(gel_x=x, gel_tets=tets, gel_obj=np.zeros(n, np.int32), pinned=pinned,
+                  attach=-np.ones(n, np.int32), E=3e5, nu=0.45, rho=1000.0, bodies=bodies,
+                  name="self_contact", self_contact=np.array([bool(self_contact)]))
+    params = SolverParams()
+
+    def delta(step):
+        return np.array([[0.0, 0.0, -(2 * gap + depth) * min(step + 1, n_steps) / n_steps]])[:len(bodies)]
     return Scenario(scene=scene, params=params, n_steps=n_steps, delta=delta)
 
 

@@ -239,19 +239,24 @@ def _gpu_canon(rows):
     a = rows[rows[:, 0] == 0][:, 1:].astype(np.int64)
     b = rows[rows[:, 0] == 1][:, 1:].astype(np.int64)
     a = np.concatenate([a[:, :1], np.sort(a[:, 1:], axis=1)], axis=1)
-    b = np.concatenate([np.sort(b[:, :2], axis=1), np.sort(b[:, 2:], axis=1)], axis=1)
+    e0, e1 = np.sort(b[:, :2], axis=1), np.sort(b[:, 2:], axis=1)
+    swap = (e0[:, 0] > e1[:, 0]) | ((e0[:, 0] == e1[:, 0]) & (e0[:, 1] > e1[:, 1]))   # unordered EE pair
+    e0[swap], e1[swap] = e1[swap].copy(), e0[swap].copy()
+    b = np.concatenate([e0, e1], axis=1)
     a = a[np.lexsort(a.T[::-1])] if len(a) else a.reshape(0, 4)
     b = b[np.lexsort(b.T[::-1])] if len(b) else b.reshape(0, 4)
     return a, b
 
 
-@pytest.mark.parametrize("which", ["config0", "small_sphere", "config1"])
+@pytest.mark.parametrize("which", ["config0", "small_sphere", "config1", "self_contact"])
 def test_candidate_sets_bit_exact(which):
-    rng = np.random.default_rng({"config0": 1, "small_sphere": 2, "config1": 3}[which])
+    rng = np.random.default_rng({"config0": 1, "small_sphere": 2, "config1": 3, "self_contact": 4}[which])
     if which == "config0":
         sc = scenes.config0()
     elif which == "config1":
         sc = scenes.config1(0)
+    elif which == "self_contact":
+        sc = scenes.self_contact_scene()
     else:
         sc = scenes.small_contact_scene(body="sphere", level=2)
     oenv = OracleEnv(sc.scene, sc.params)
@@ -348,7 +353,7 @@ def _step_parity(sc, prm, n_steps, tol=1e-6):
         assert err <= tol, (s, err)
         assert np.abs(vg - vo).max() <= tol * bbox_diag(oenv, x, y) / prm.dt
     genv.close()
-    return worst
+    return worst, oenv, traj
 
 
 def test_step_free_fall_closed_form():
@@ -385,6 +390,23 @@ def test_step_parity_two_finger_grasp():
     # and body-body pairs); the pads start 20 um from the sphere
     sc = scenes.config3(0, n=5, nz=3, level=1, gap=2e-5)
     _step_parity(sc, sc.params.parity(), 6)
+
+
+def test_step_parity_self_contact():
+    # gel self-contact: the two blocks of one pad are pressed together by a
+    # driven cube; the pairs that hold them apart are pairs within the pad
+    sc = scenes.self_contact_scene()
+    prm = sc.params.parity()
+    prm.newton_max = 400        # the last step takes ~100 iterations at the parity tolerance
+    _, oenv, traj = _step_parity(sc, prm, sc.n_steps)
+    x, _, y, _, _ = traj[-1]
+    pt, ee = oenv.static_pairs(x, y)
+    pa = oenv.pair_arrays(pt, ee)
+    own = np.all(pa[0] < oenv.N, axis=1)             # all four points are gel vertices
+    assert own.any()
+    d = ods.pair_distance(oenv.contact_positions(x, y)[pa[0][own]], pa[1][own])
+    assert d.min() < prm.dhat                          # active barrier pairs within the pad
+    assert valid_state(oenv, x, y)
 
 
 def test_step_parity_spin():
@@ -576,7 +598,7 @@ def _mixed(prm):
     return prm
 
 
-@pytest.mark.parametrize("which", ["config0", "small_sphere", "two_finger"])
+@pytest.mark.parametrize("which", ["config0", "small_sphere", "two_finger", "self_contact"])
 def test_mixed_precision_step_within_1e4_of_oracle(which):
     """Mixed mode (FP32 element/contact Hessians and mat-vec; FP64 gradient,
     distances, CCD, energies, residuals) at the benchmark tolerances: each
@@ -594,6 +616,8 @@ def test_mixed_precision_step_within_1e4_of_oracle(which):
         sc, n = scenes.config0(), 20
     elif which == "two_finger":
         sc, n = scenes.config3(0, n=5, nz=3, level=1, gap=2e-5), 6
+    elif which == "self_contact":
+        sc, n = scenes.self_contact_scene(), 4
     else:
         sc, n = scenes.small_contact_scene(body="sphere", level=2, depth=3e-4, n_steps=6), 6
     oenv, traj = oracle_states(sc, sc.params.parity(), n)

@@ -179,6 +179,93 @@ def test_candidates_match_naive_loops_and_cover_dhat():
     assert a.shape == (len(pt), 4) and b.shape == (len(ee), 4)
 
 
+def test_self_contact_candidates_match_naive_loops_and_cover_dhat():
+    """Gel self-contact: within a flagged pad a point pairs with every
+    triangle not incident to it and an edge with every edge it shares no
+    vertex with (each unordered pair once); across objects as before."""
+    sc = scenes.self_contact_scene()
+    env = OracleEnv(sc.scene, sc.params)
+    x, v, y, yd = env.rest_state()
+    rng = np.random.default_rng(6)
+    x = x + rng.normal(scale=1e-5, size=x.shape)
+    Xc = env.contact_positions(x, y)
+    sd, dhat = env.sd, sc.params.dhat
+    pt, ee = candidates(sd, Xc, dhat, env.excluded)
+
+    def box(ids):
+        P = Xc[list(ids)]
+        return P.min(0), P.max(0)
+
+    def ov(a, b):
+        return all(a[0][k] <= b[1][k] + dhat and b[0][k] <= a[1][k] + dhat for k in range(3))
+
+    def may_pair(oa, ob):
+        return oa != ob or oa == 0          # object 0 is the pad (self-contact on); bodies never self-pair
+    npt = set()
+    for pi, p in enumerate(sd.points):
+        for ti, t in enumerate(sd.tris):
+            if may_pair(sd.point_obj[pi], sd.tri_obj[ti]) and p not in t and ov(box([p]), box(t)):
+                npt.add((int(p), ti))
+    nee = set()
+    for i, j in itertools.combinations(range(len(sd.edges)), 2):
+        oi, oj = sd.edge_obj[i], sd.edge_obj[j]
+        if not may_pair(oi, oj) or set(sd.edges[i]) & set(sd.edges[j]):
+            continue
+        a, b = (i, j) if oi <= oj else (j, i)
+        if ov(box(sd.edges[a]), box(sd.edges[b])):
+            nee.add((a, b))
+    npt = {pr for pr in npt if not (sd.fixed[pr[0]] and all(sd.fixed[sd.tris[pr[1]]]))}
+    nee = {pr for pr in nee if not (all(sd.fixed[sd.edges[pr[0]]]) and all(sd.fixed[sd.edges[pr[1]]]))}
+    assert set(map(tuple, pt.tolist())) == npt
+    assert set(map(tuple, ee.tolist())) == nee
+    own_pt = [(p, t) for (p, t) in npt if sd.point_obj[p] == 0 and sd.tri_obj[t] == 0]
+    assert own_pt                                     # the blocks start 50 um apart: pairs within the pad
+    # every non-incident point-triangle pair of the pad closer than dhat is a candidate
+    allpt = np.array([(p, t) for (p, t) in itertools.product(range(len(sd.points)), range(len(sd.tris)))
+                      if sd.point_obj[p] == 0 and sd.tri_obj[t] == 0 and sd.points[p] not in sd.tris[t]])
+    X12 = np.concatenate([Xc[sd.points[allpt[:, 0]]][:, None], Xc[sd.tris[allpt[:, 1]]]], axis=1)
+    d = ds.pair_distance(X12, np.zeros(len(allpt), bool))
+    close = {(int(sd.points[p]), int(t)) for (p, t), dd in zip(allpt, d) if dd < dhat}
+    assert close and close <= npt
+
+
+def _heights_above_base(sc, x):
+    """Height of every bottom vertex of the upper block above the deformed
+    top face of the base, at the same (x, y) (barycentric on the base's
+    top-face triangles)."""
+    g = sc.scene.gel_x
+    n_low = int(np.sum(g[:, 2] <= 0.0))
+    top = np.nonzero(np.isclose(g[:n_low, 2], 0.0))[0]
+    bottom_up = n_low + np.nonzero(np.isclose(g[n_low:, 2], g[n_low:, 2].min()))[0]
+    from scipy.spatial import Delaunay
+    tri = Delaunay(g[top, :2])                          # the rest top face, as triangles in (x, y)
+    out = []
+    for u in bottom_up:
+        s = int(tri.find_simplex(x[u, :2]))
+        assert s >= 0
+        T = top[tri.simplices[s]]
+        A = np.c_[x[T, :2], np.ones(3)].T
+        lam = np.linalg.solve(A, np.r_[x[u, :2], 1.0])
+        out.append(x[u, 2] - lam @ x[T, 2])
+    return np.array(out)
+
+
+def test_self_contact_holds_the_blocks_of_one_pad_apart():
+    """The same scene with and without the pad's self-contact flag: with it
+    the pressed upper block rests on the base (positive heights, active
+    pairs within the pad), without it the block sinks into the base."""
+    heights = {}
+    for flag in (True, False):
+        sc = scenes.self_contact_scene(self_contact=flag)
+        env, out = _run(sc)
+        assert all(st.status == 0 for *_, st in out[1:])
+        x, _, y, _, _ = out[-1]
+        heights[flag] = _heights_above_base(sc, x)
+    assert heights[True].min() > 0.0
+    assert heights[True].max() < 1e-4                  # pressed down onto the base
+    assert heights[False].min() < -1e-4                # no self-contact: interpenetration
+
+
 # ---------------------------------------------------------------- CCD
 @pytest.mark.parametrize("seed", range(20))
 def test_accd_conservative_vs_exact_roots(seed):
