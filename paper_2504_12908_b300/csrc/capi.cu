@@ -46,19 +46,36 @@ cudaEvent_t take_ev(ipc_ctx* ctx) {
   return e;
 }
 
+// launches on stream `st` (the ctx stream unless a side stream is named),
+// timed per class when profiling is on
 template <class F>
-void KL(ipc_ctx* ctx, int kind, F&& f) {
+void KL(ipc_ctx* ctx, int kind, F&& f, cudaStream_t st = nullptr) {
   if (!ctx->prof_on) {
     ctx->launches += f();
     return;
   }
+  if (!st) st = ctx->stream;
   cudaEvent_t a = take_ev(ctx), b = take_ev(ctx);
-  cudaEventRecord(a, ctx->stream);
+  cudaEventRecord(a, st);
   int n = f();
-  cudaEventRecord(b, ctx->stream);
+  cudaEventRecord(b, st);
   ctx->launches += n;
   ctx->prof_launches[kind] += n;
   ctx->pending.push_back({kind, a, b});
+}
+
+// the first n side streams start after everything issued so far on the
+// ctx stream ...
+void fork_side(ipc_ctx* ctx, int n = 2) {
+  cudaEventRecord(ctx->ev_fork, ctx->stream);
+  for (int i = 0; i < n; ++i) cudaStreamWaitEvent(ctx->side[i], ctx->ev_fork, 0);
+}
+// ... and the ctx stream continues only after them
+void join_side(ipc_ctx* ctx, int n = 2) {
+  for (int i = 0; i < n; ++i) {
+    cudaEventRecord(ctx->ev_join[i], ctx->side[i]);
+    cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0);
+  }
 }
 
 // resolve recorded event pairs (the stream has been synchronised)
@@ -214,6 +231,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.z4 = c.take<float4>((size_t)pk.n_rows);
   d.d4 = c.take<float4>((size_t)pk.n_rows);
   d.q4 = c.take<float4>((size_t)pk.n_rows);
+  d.qc4 = c.take<float4>((size_t)pk.n_rows);
   d.cta_list = c.take<int>((size_t)pk.n_rows / 128);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
@@ -334,11 +352,17 @@ ipc_status assemble_system(ipc_ctx* ctx, bool lag_friction) {
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); });
   KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
-  if (lag_friction) KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s); });
-  KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s); });
-  KL(ctx, KC_BARRIER, [&] { return launch_fric_assemble(d, s); });
+  // barrier terms (side stream 0) and ABD terms (side stream 1) are few,
+  // latency-bound threads; they are issued first, at high priority, and run
+  // beside the per-tet kernel, which fills the rest of the GPU
+  fork_side(ctx);
+  cudaStream_t s0 = ctx->side[0], s1 = ctx->side[1];
+  if (lag_friction) KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s0); }, s0);
+  KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s0); }, s0);
+  KL(ctx, KC_BARRIER, [&] { return launch_fric_assemble(d, s0); }, s0);
+  KL(ctx, KC_BODY, [&] { return launch_body(d, s1); }, s1);
   KL(ctx, KC_TET, [&] { return launch_tet(d, s); });
-  KL(ctx, KC_BODY, [&] { return launch_body(d, s); });
+  join_side(ctx);
   KL(ctx, KC_ASSEMBLE, [&] { return launch_assemble(d, s); });
   KL(ctx, KC_GRAD, [&] { return launch_grad(d, s); });
   KL(ctx, KC_PRECOND, [&] { return launch_precond(d, s); });
@@ -353,9 +377,14 @@ int pcg_iteration(ipc_ctx* ctx, int n_cta = -1) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   long long l0 = ctx->launches;
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s); });
+  // the contact mat-vecs (few, latency-bound pairs) run on a side stream
+  // beside the bandwidth-bound SELL SpMV; the update adds the two parts
+  fork_side(ctx, 1);
+  cudaStream_t s0 = ctx->side[0];
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s0); }, s0);
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s0); }, s0);
   KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s, n_cta); });
+  join_side(ctx, 1);
   KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, n_cta); });
   KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s, n_cta); });
   return (int)(ctx->launches - l0);
@@ -579,6 +608,13 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaMallocHost(&ctx->h_dbl, NUM_SCALARS * sizeof(double) * (size_t)pk.n_envs));
   CK(cudaMallocHost(&ctx->h_cta_list, sizeof(int) * (size_t)(pk.n_rows / 128)));
   for (const auto& ev : pk.env) ctx->max_bodies = std::max(ctx->max_bodies, ev.n_bodies);
+  int prio_least = 0, prio_greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaStreamCreateWithPriority(&ctx->side[i], cudaStreamNonBlocking, prio_greatest));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
 }
@@ -591,6 +627,11 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   delete ctx;
   return IPC_OK;
 }
@@ -641,6 +682,7 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
     if (t.pair_us[k] < best && t.pair_us[k] < 0.95f * def_pair) { best = t.pair_us[k]; best_c = ctas_[k]; }
   d.pair_ctas_per_sm = best_c;
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
+  CK(cudaMemsetAsync(d.qc4, 0, sizeof(float4) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
   CK(cudaStreamSynchronize(s));
   // the captured PCG graph holds the old launch shapes
@@ -809,9 +851,14 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
     KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, s); });
     KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
-    KL(ctx, KC_ACCD, [&] { return launch_accd(d, s); });
-    KL(ctx, KC_LS, [&] { return launch_ls_init(d, s); });
+    // ACCD (side stream) beside the energy at alpha = 0, which needs only
+    // the swept pair list; the step length starts from ACCD's bound after
+    // the join
+    fork_side(ctx, 1);
+    KL(ctx, KC_ACCD, [&] { return launch_accd(d, ctx->side[0]); }, ctx->side[0]);
     KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 0, 0, s); });
+    join_side(ctx, 1);
+    KL(ctx, KC_LS, [&] { return launch_ls_init(d, s); });
     for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
       KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 1, 1, s); });
       KL(ctx, KC_LS, [&] { return launch_ls_decide(d, s); });

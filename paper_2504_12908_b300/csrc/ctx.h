@@ -18,7 +18,6 @@ enum EnvScalar {
   S_DQ,         // PCG d.q
   S_RR,         // PCG r.r
   S_RR0,        // PCG |b|^2
-  S_PALPHA,     // PCG alpha
   S_PBETA,      // PCG beta
   S_PNORM,      // Newton |p|_inf (full space)
   S_CRES,       // AL constraint residual |q - s|_inf (full space)
@@ -28,6 +27,7 @@ enum EnvScalar {
   S_E1,         // energy at the trial step
   S_MIND,       // min pair distance (diagnostics)
   S_ASUM,       // accepted line-search steps this step, summed
+  S_DQC,        // PCG d.q, contact part (pair and friction mat-vecs)
   NUM_SCALARS
 };
 
@@ -99,6 +99,7 @@ struct Dev {
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
   float4 *z4, *d4, *q4;         // mixed mode: the PCG vectors z, d, q as FP32 rows (16 B)
+  float4* qc4;                  // mixed mode: contact part of q (FP32 rows, atomics)
   int* cta_list;                // row CTAs (128 rows each) of the envs still in PCG
   void* pc;                     // 6 per row: symmetric inverse of the diagonal block
                                 // (double, or float in mixed mode)
@@ -163,6 +164,14 @@ struct ipc_ctx {
   double* h_dbl = nullptr;    // pinned read-back (NUM_SCALARS * n_envs doubles)
   int max_bodies = 0;
   std::vector<int> n_cta_env;  // row CTAs per env
+  // Two high-priority side streams for the small, latency-bound launches
+  // that are independent of the element kernels (per-pair barrier terms and
+  // per-body ABD terms beside the per-tet elastic kernel; ACCD beside the
+  // line search's first energy).  Forked from and joined back into `stream`
+  // with events, so the caller still sees one stream.
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[2] = {nullptr, nullptr};
   // CUDA graph of one PCG polling block (ipc_set_graph_mode)
   bool graph_on = false;
   cudaGraphExec_t pcg_exec = nullptr;
