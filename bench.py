@@ -220,15 +220,14 @@ def kernel_bytes(genv, stats_tot, prof):
     hs = 4 if getattr(genv.params, "precision", 0) else 8   # Hessian / matrix value bytes
     out = {}
     # SELL SpMV per env-iteration: 9 values + 4 B column per real block; per
-    # row the own direction read and q written (16 B FP32 rows in mixed
-    # mode, 24 B FP64 rows otherwise)
+    # row the own direction read, q written (16 B FP32 rows in mixed mode,
+    # 24 B FP64 rows otherwise), the FP64 contact part qc read and cleared
     vb = 16 if hs == 4 else 24
-    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * (2 * vb)
+    spmv_env_iter = sz["real_blocks"] * (9 * hs + 4) + rows_real * (2 * vb + 48)
     out["sell_spmv"] = stats_tot["pcg_iters"] * spmv_env_iter
-    # PCG update: p (FP64) read + written, d and q read, the contact part of
-    # q read and cleared, r (FP64) read + written, the 6-entry symmetric
-    # P^-1 block, z written
-    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (48 + 2 * vb + 2 * vb + 48 + 6 * hs + vb)
+    # PCG update: p (FP64) read + written, d and q read, r (FP64) read +
+    # written, the 6-entry symmetric P^-1 block, z written
+    out["pcg_update"] = stats_tot["pcg_iters"] * rows_real * (48 + 2 * vb + 48 + 6 * hs + vb)
     # PCG direction: z and d read, d written
     out["pcg_dir"] = stats_tot["pcg_iters"] * rows_real * 3 * vb
     # elastic element kernel: 4 indices + 4 positions + Dm^-1 + vol read,
@@ -344,8 +343,8 @@ def per_step_error(g64, g32, tg, body_radius):
 # (profiles/k_spmv_traffic_mixed_256env_gel40x40x6.md).  Reported only while
 # the kernel's source is the one that was measured (hash of its text).
 # (measured with 4 slots in flight per lane)
-SPMV_TRAFFIC = {"envs": 256, "bytes": 1214072064 + 36781824,
-                "source_sha256": "ac8a83dab1c5e247a6df451f1777f74eb0e5cae4f3fb4162177b988995b7e40b"}
+SPMV_TRAFFIC = {"envs": 256, "bytes": 1275934208 + 90306816,
+                "source_sha256": "830203d985315711f5332876ced428e43c65ae8bc3a3b875c54921744617e589"}
 
 
 def _spmv_source_hash() -> str:

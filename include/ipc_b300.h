@@ -166,8 +166,9 @@ const char* ipc_last_error(const ipc_ctx* ctx);
 
 /* Run the PCG inner loop (Sec. 4, the block-Jacobi PCG solve of each Newton
  * iteration) as a CUDA graph: the 16 iterations between two host checks of
- * the per-env convergence flags (64 kernel launches) are captured on the
- * ctx stream at the first solve and replayed after that.  Results are the
+ * the per-env convergence flags (4 kernel launches each, 5 with friction)
+ * are captured on the ctx stream at the first solve and replayed after
+ * that.  Results are the
  * same as with plain launches.  on = 0 (default) launches kernel by kernel.
  * The ctx stream must support capture (a created stream, not the legacy
  * default stream); otherwise ipc_step returns IPC_ECUDA with the reason in

@@ -231,7 +231,6 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.z4 = c.take<float4>((size_t)pk.n_rows);
   d.d4 = c.take<float4>((size_t)pk.n_rows);
   d.q4 = c.take<float4>((size_t)pk.n_rows);
-  d.qc4 = c.take<float4>((size_t)pk.n_rows);
   d.cta_list = c.take<int>((size_t)pk.n_rows / 128);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
@@ -377,14 +376,9 @@ int pcg_iteration(ipc_ctx* ctx, int n_cta = -1) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   long long l0 = ctx->launches;
-  // the contact mat-vecs (few, latency-bound pairs) run on a side stream
-  // beside the bandwidth-bound SELL SpMV; the update adds the two parts
-  fork_side(ctx, 1);
-  cudaStream_t s0 = ctx->side[0];
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s0); }, s0);
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s0); }, s0);
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s); });
   KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s, n_cta); });
-  join_side(ctx, 1);
   KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, n_cta); });
   KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s, n_cta); });
   return (int)(ctx->launches - l0);
@@ -682,7 +676,6 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
     if (t.pair_us[k] < best && t.pair_us[k] < 0.95f * def_pair) { best = t.pair_us[k]; best_c = ctas_[k]; }
   d.pair_ctas_per_sm = best_c;
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
-  CK(cudaMemsetAsync(d.qc4, 0, sizeof(float4) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
   CK(cudaStreamSynchronize(s));
   // the captured PCG graph holds the old launch shapes

@@ -75,6 +75,21 @@ template <class T> IPC_DEV T block_sum(T v, T* sh /* >= 32 */) {
   if (w == 0) r = warp_sum(r);
   return r;  // valid in thread 0
 }
+// FP64 sum over a 128-thread CTA with few FP64 instructions (B300 issues
+// FP64 at a small fraction of its FP32 rate): two halving steps through
+// shared memory (3 warp-wide adds) before one warp's shuffle tree, instead
+// of a shuffle tree in every warp (25 warp-wide adds).  Fixed order
+// (deterministic).  Valid in thread 0.
+IPC_DEV double block_sum128(double v, double* sh /* >= 128 */) {
+  __syncthreads();  // a previous use of sh may still be read
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 64) sh[threadIdx.x] = v + sh[threadIdx.x + 64];
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) r = warp_sum(sh[threadIdx.x] + sh[threadIdx.x + 32]);
+  return r;
+}
 template <class T> IPC_DEV T block_max(T v, T* sh) {
   v = warp_max(v);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;

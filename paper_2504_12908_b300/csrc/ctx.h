@@ -18,6 +18,7 @@ enum EnvScalar {
   S_DQ,         // PCG d.q
   S_RR,         // PCG r.r
   S_RR0,        // PCG |b|^2
+  S_PALPHA,     // PCG alpha
   S_PBETA,      // PCG beta
   S_PNORM,      // Newton |p|_inf (full space)
   S_CRES,       // AL constraint residual |q - s|_inf (full space)
@@ -27,7 +28,6 @@ enum EnvScalar {
   S_E1,         // energy at the trial step
   S_MIND,       // min pair distance (diagnostics)
   S_ASUM,       // accepted line-search steps this step, summed
-  S_DQC,        // PCG d.q, contact part (pair and friction mat-vecs)
   NUM_SCALARS
 };
 
@@ -99,7 +99,6 @@ struct Dev {
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
   float4 *z4, *d4, *q4;         // mixed mode: the PCG vectors z, d, q as FP32 rows (16 B)
-  float4* qc4;                  // mixed mode: contact part of q (FP32 rows, atomics)
   int* cta_list;                // row CTAs (128 rows each) of the envs still in PCG
   void* pc;                     // 6 per row: symmetric inverse of the diagonal block
                                 // (double, or float in mixed mode)

@@ -302,21 +302,6 @@ __device__ __forceinline__ void scatter_cv(const Dev& d, double* dst, int cv, D3
   }
 }
 
-// PCG contact part of q: FP64 rows (Dev::qc) in FP64 mode, FP32 rows
-// (Dev::qc4) in mixed mode, where the mat-vec is FP32.
-template <class HT> __device__ __forceinline__ void qc_add(const Dev& d, int row, int c, double v);
-template <> __device__ __forceinline__ void qc_add<double>(const Dev& d, int row, int c, double v) {
-  atomicAdd(d.qc + 3 * row + c, v);
-}
-template <> __device__ __forceinline__ void qc_add<float>(const Dev& d, int row, int c, double v) {
-  atomicAdd(reinterpret_cast<float*>(d.qc4) + 4 * row + c, (float)v);
-}
-template <class HT> __device__ __forceinline__ void qc_add3(const Dev& d, int row, D3 v) {
-  qc_add<HT>(d, row, 0, v.x);
-  qc_add<HT>(d, row, 1, v.y);
-  qc_add<HT>(d, row, 2, v.z);
-}
-
 // HT: storage type of the pair Hessian (double: FP64 mode; float: mixed
 // mode).  Distances, barrier derivatives and the projection are FP64 either way.
 template <class HT>
@@ -403,9 +388,7 @@ __device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) 
 
 // q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
 // eliminated: read as zero, never written).  H_k is stored as its packed
-// upper triangle, interleaved by warp of active slots.  Each pair also adds
-// its part d_k . (H_k d_k) of d.q to the env's S_DQC (the SELL SpMV, which
-// runs at the same time, sums the rest).
+// upper triangle, interleaved by warp of active slots.
 // 16 lanes per pair (two pairs per warp), lane j < 12 owns coordinate j =
 // 3 m + c (point m, component c): it forms that component of the pair's
 // direction, the group shares the 12 values by shuffles, lane j computes row
@@ -455,21 +438,8 @@ __global__ void k_pair_spmv(Dev d) {
       }
     }
     const double o = (double)oj;
-    // the pair's d.(H d) (lanes j >= 12 and dead groups hold zeros); the two
-    // pairs of a warp share one atomic when they belong to the same env
-    HT dhd = (live && j < 12) ? dj * oj : (HT)0;
-    for (int w = 8; w > 0; w >>= 1) dhd += __shfl_xor_sync(0xffffffffu, dhd, w);
-    const int e_other = __shfl_xor_sync(0xffffffffu, live ? e : -1, 16);
-    const HT dhd_other = __shfl_xor_sync(0xffffffffu, dhd, 16);
-    if (live && j == 0) {
-      if (e_other == e) {
-        if (half == 0) atomicAdd(&ENVS(d, e, S_DQC), (double)dhd + (double)dhd_other);
-      } else {
-        atomicAdd(&ENVS(d, e, S_DQC), (double)dhd);
-      }
-    }
     // gel points: one atomic per coordinate
-    if (live && j < 12 && b_pt < 0 && d.row_kind[row] != ROW_PINNED) qc_add<HT>(d, row, c, o);
+    if (live && j < 12 && b_pt < 0 && d.row_kind[row] != ROW_PINNED) atomicAdd(d.qc + 3 * row + c, o);
     // body points: the pair's single body (or several: per point)
     int bm[4];
     for (int mm = 0; mm < 4; ++mm) bm[mm] = __shfl_sync(0xffffffffu, b_pt, (lane & 16) + 3 * mm);
@@ -493,17 +463,16 @@ __global__ void k_pair_spmv(Dev d) {
     const int other = __shfl_xor_sync(0xffffffffu, body, 16);
     const double jb_other = __shfl_xor_sync(0xffffffffu, jb, 16);
     if (body >= 0 && j < 12) {
-      const int br = d.body_row[body];
       if (other == body) {
-        if (half == 0) qc_add<HT>(d, br + j / 3, j % 3, jb + jb_other);
+        if (half == 0) atomicAdd(d.qc + 3 * d.body_row[body] + j, jb + jb_other);
       } else {
-        qc_add<HT>(d, br + j / 3, j % 3, jb);
+        atomicAdd(d.qc + 3 * d.body_row[body] + j, jb);
       }
     }
     if (body == -1 && j < 12 && b_pt >= 0) {  // points of several bodies: per point
       const int br = d.body_row[b_pt];
-      qc_add<HT>(d, br, c, o);
-      for (int s = 0; s < 3; ++s) qc_add<HT>(d, br + 1 + s, c, xb[s] * o);
+      atomicAdd(d.qc + 3 * br + c, o);
+      for (int s = 0; s < 3; ++s) atomicAdd(d.qc + 3 * (br + 1 + s) + c, xb[s] * o);
     }
   }
 }
@@ -806,23 +775,7 @@ __global__ void k_fric_assemble(Dev d) {
 }
 
 // PCG mat-vec: q_c += w_i S (sum_j w_j d_j) per record (pinned gel rows read
-// as zero and are never written); the record's part of d.q, a . (S a) with
-// a = sum_j w_j d_j, goes to the env's S_DQC.
-template <class HT>
-__device__ __forceinline__ void scatter_cv_qc(const Dev& d, int cv, D3 v) {
-  int row = d.cv_row[cv];
-  if (d.cv_body[cv] < 0) {
-    if (d.row_kind[row] == ROW_PINNED) return;
-    qc_add3<HT>(d, row, v);
-  } else {
-    D3 xb = ld3(d.cv_xbar, cv);
-    qc_add3<HT>(d, row, v);
-    qc_add3<HT>(d, row + 1, xb.x * v);
-    qc_add3<HT>(d, row + 2, xb.y * v);
-    qc_add3<HT>(d, row + 3, xb.z * v);
-  }
-}
-template <class HT>
+// as zero and are never written).
 __global__ void k_fric_spmv(Dev d) {
   FOR_FRIC(d, li) {
   const int j = d.fr_list[li], e = d.fr_list_env[li];
@@ -841,8 +794,7 @@ __global__ void k_fric_spmv(Dev d) {
   const double* S = d.fr_S + 6 * (long long)j;
   D3 t{S[0] * a.x + S[1] * a.y + S[2] * a.z, S[1] * a.x + S[3] * a.y + S[4] * a.z,
        S[2] * a.x + S[4] * a.y + S[5] * a.z};
-  for (int i = 0; i < 4; ++i) scatter_cv_qc<HT>(d, cvs[i], w[i] * t);
-  atomicAdd(&ENVS(d, e, S_DQC), dot(a, t));
+  for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], w[i] * t);
   }
 }
 
@@ -970,8 +922,7 @@ int launch_fric_assemble(const Dev& d, cudaStream_t s) {
 }
 int launch_fric_spmv(const Dev& d, cudaStream_t s) {
   if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
-  if (d.prec) k_fric_spmv<float><<<PAIR_GRID>>>(d);
-  else k_fric_spmv<double><<<PAIR_GRID>>>(d);
+  k_fric_spmv<<<PAIR_GRID>>>(d);
   return 1;
 }
 int launch_fric_energy(const Dev& d, int use_alpha, cudaStream_t s) {

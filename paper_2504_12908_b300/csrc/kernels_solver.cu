@@ -30,15 +30,18 @@ __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED 
 // T0: type in which the first value (v0) is summed within the CTA (FP32 for
 // the FP32 products r.z and d.q of mixed mode); the other n - 1 values are
 // FP64, and the CTA partials are summed in FP64.
+// The row kernels that call it run 128-thread CTAs; FP64 values are summed
+// with block_sum128.
 template <int n, class T0 = double>
 __device__ bool env_reduce(const Dev& d, int e, int which, int cta, T0 v0, const double* rest /* n - 1 */,
                            double* out) {
-  __shared__ double sh[32];
-  __shared__ T0 sh0[32];
+  __shared__ double sh[128];
+  __shared__ float shf[32];
   __shared__ bool last;
   double part[n];
-  part[0] = (double)block_sum(v0, sh0);
-  for (int j = 1; j < n; ++j) part[j] = block_sum(rest[j - 1], sh);
+  if constexpr (sizeof(T0) == 4) part[0] = (double)block_sum(v0, shf);
+  else part[0] = block_sum128(v0, sh);
+  for (int j = 1; j < n; ++j) part[j] = block_sum128(rest[j - 1], sh);
   if (threadIdx.x == 0) {
     for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
     __threadfence();
@@ -418,7 +421,6 @@ __global__ void k_pcg_init(Dev d) {
   }
   if (last) {
     ENVS(d, e, S_PBETA) = 0.0;
-    ENVS(d, e, S_DQC) = 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR0) = out[1];
     ENVS(d, e, S_RR) = out[1];
@@ -427,13 +429,11 @@ __global__ void k_pcg_init(Dev d) {
   }
 }
 
-// q = A d over the SELL-32 matrix (one row per thread, U slots in flight per
-// lane); d.q of this part reduced per env -> S_DQ.  The contact part of q
-// and of d.q come from the contact mat-vecs, which run at the same time on
-// another stream; the update adds both parts.
+// q = A d + qc (SELL-32, one row per thread, U slots in flight per lane),
+// qc cleared; d.q reduced per env -> alpha.
 // HT: matrix precision; the products are accumulated in HT slot by slot in
-// storage order.  FP64 mode: d.q in FP64; mixed: an FP32 product, summed in
-// FP32 within the CTA.
+// storage order.  FP64 mode: the contact part qc is added and d.q formed in
+// FP64; mixed: qc is rounded into the FP32 row q and d.q is an FP32 product.
 template <class HT, int U>
 __global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta_list) {
   int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
@@ -473,31 +473,25 @@ __global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta
     ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
     az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
   }
+  const D3 qc = ld3(d.qc, r);
+  st3(d.qc, r, D3{0, 0, 0});
   double out[1];
   bool last;
   if constexpr (sizeof(HT) == 4) {
-    const float4 q = make_float4(ax, ay, az, 0.0f);
+    const float3 c3 = round_row(qc);
+    const float4 q = make_float4(ax + c3.x, ay + c3.y, az + c3.z, 0.0f);
     d.q4[r] = q;
     const float4 w = d.d4[r];
     last = env_reduce<1, float>(d, e, 1, r >> 7, w.x * q.x + w.y * q.y + w.z * q.z, nullptr, out);
   } else {
-    const D3 acc{(double)ax, (double)ay, (double)az};
+    const D3 acc = qc + D3{(double)ax, (double)ay, (double)az};
     PV<double>::set_q(d, r, acc);
     last = env_reduce<1>(d, e, 1, r >> 7, dot(PV<double>::dir(d, r), acc), nullptr, out);
   }
-  if (last) ENVS(d, e, S_DQ) = out[0];
-}
-
-// alpha = r.z / d.q of the row's env, d.q = SELL part + contact part; one
-// FP64 division per CTA (all rows of a CTA belong to one env)
-__device__ __forceinline__ double pcg_alpha(const Dev& d, int e) {
-  __shared__ double al;
-  if (threadIdx.x == 0) {
-    const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
-    al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;
+  if (last) {
+    ENVS(d, e, S_DQ) = out[0];
+    ENVS(d, e, S_PALPHA) = (out[0] > 0.0) ? ENVS(d, e, S_RZ) / out[0] : 0.0;
   }
-  __syncthreads();
-  return al;
 }
 
 // p += alpha d, r -= alpha q, z = P^-1 r; rz, rr reduced -> beta, stop test
@@ -507,13 +501,11 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
   uint8_t kr = d.row_kind[r];
-  const double al = pcg_alpha(d, e);
+  double al = ENVS(d, e, S_PALPHA);
   double out[2];
   bool last;
   if constexpr (sizeof(HT) == 4) {
-    const float4 dd = d.d4[r], qs = d.q4[r], qc = d.qc4[r];
-    d.qc4[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    const float4 qq = make_float4(qs.x + qc.x, qs.y + qc.y, qs.z + qc.z, 0.0f);
+    const float4 dd = d.d4[r], qq = d.q4[r];
     st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
     const D3 rv = ld3(d.r, r) - al * widen_row(qq);
     st3(d.r, r, rv);
@@ -524,10 +516,8 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
     d.z4[r] = z;
     last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
   } else {
-    const D3 qc = ld3(d.qc, r);
-    st3(d.qc, r, D3{0, 0, 0});
     st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r));
-    const D3 rv = ld3(d.r, r) - al * (PV<double>::q(d, r) + qc);
+    const D3 rv = ld3(d.r, r) - al * PV<double>::q(d, r);
     st3(d.r, r, rv);
     __syncwarp();
     const double rr = dot(rv, rv);
@@ -536,10 +526,6 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
     last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
   }
   if (last) {
-    // every CTA of the env has read S_DQ and S_DQC (in pcg_alpha) before it
-    // counted itself in, so the last one may clear the contact part
-    const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
-    ENVS(d, e, S_DQC) = 0.0;
     double rz_old = ENVS(d, e, S_RZ);
     ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
     ENVS(d, e, S_RZ) = out[0];
@@ -547,7 +533,7 @@ __global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
     int it = ++ENVI(d, e, I_PCGIT);
     ENVI(d, e, I_PCGTOT) += 1;
     double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
-    if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) ENVI(d, e, I_PCG) = 0;
+    if (out[1] <= tol2 || it >= d.pcg_max || !(ENVS(d, e, S_DQ) > 0.0)) ENVI(d, e, I_PCG) = 0;
   }
 }
 
@@ -579,16 +565,7 @@ __global__ void k_debug_q_to_rows(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
   if (!ENVI(d, e, I_PCG)) return;
-  D3 qc;
-  if constexpr (sizeof(HT) == 4) {
-    const float4 c4 = d.qc4[r];
-    qc = D3{c4.x, c4.y, c4.z};
-    d.qc4[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  } else {
-    qc = ld3(d.qc, r);
-    st3(d.qc, r, D3{0, 0, 0});
-  }
-  st3(d.q, r, PV<HT>::q(d, r) + qc);
+  st3(d.q, r, PV<HT>::q(d, r));
 }
 
 // ---------------------------------------------------------------------------
