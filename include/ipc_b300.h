@@ -204,9 +204,12 @@ ipc_status ipc_body_com(const ipc_ctx* ctx, int env, int body, double com[3]);
 
 /* State of one env.  x, v: [n_verts][3]; y, ydot: [n_bodies][12].  Any
  * pointer may be NULL to leave that part unchanged.  set_state synchronises
- * the stream and rejects inverted tets (IPC_EINVERTED) and touching or
- * interpenetrating surfaces (IPC_EINTERSECT, min distance <= 0), leaving the
- * previous state in place. */
+ * the stream and rejects non-finite values (IPC_EINVAL), inverted tets
+ * (IPC_EINVERTED) and touching or interpenetrating surfaces
+ * (IPC_EINTERSECT, min distance <= 0), leaving the previous state in place.
+ * A state read with get_state and set again (in this or another ctx built
+ * from the same scene) continues as the original would (checkpoint /
+ * resume). */
 ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v,
                          const double* y, const double* ydot);
 ipc_status ipc_get_state(ipc_ctx* ctx, int env, double* x, double* v,

@@ -2,6 +2,7 @@
 // driver (host orchestration of the device kernels) and diagnostics.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -731,6 +732,17 @@ ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v
   if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
   const EnvInfo& ev = ctx->pk.env[env];
   size_t nd = 3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies;
+  // non-finite input is rejected before anything is uploaded
+  auto finite = [](const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(a[i])) return false;
+    return true;
+  };
+  const size_t nx = 3 * (size_t)ev.n_verts, ny = 12 * (size_t)ev.n_bodies;
+  if ((x && !finite(x, nx)) || (v && !finite(v, nx)) || (y && !finite(y, ny)) || (ydot && !finite(ydot, ny))) {
+    ctx->err = "set_state: non-finite input";
+    return IPC_EINVAL;
+  }
   std::vector<double> old_x, old_v, dof(nd), rows;
   ipc_status st;
   if ((st = download_rows(ctx, env, ctx->dev.x, old_x)) != IPC_OK) return st;

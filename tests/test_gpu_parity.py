@@ -453,12 +453,61 @@ def test_state_round_trip_and_rejections():
     x3[t[0]] = x3[t[1]] + 2.0 * (x3[t[1]] - x3[t[0]])
     assert genv.set_state(0, x3, None, None, None) == ipc.IPC_EINVERTED
     assert np.array_equal(genv.get_state(0)[0], x2)
+    # non-finite values: rejected before upload, state unchanged
+    x5 = x2.copy()
+    x5[3, 1] = np.nan
+    assert genv.set_state(0, x5, None, None, None) == ipc.IPC_EINVAL
+    yd5 = yd.copy()
+    yd5[0, 4] = np.inf
+    assert genv.set_state(0, None, None, None, yd5) == ipc.IPC_EINVAL
+    xb5, vb5, _, ydb5 = genv.get_state(0)
+    assert np.array_equal(xb5, x2) and np.array_equal(vb5, v2) and np.array_equal(ydb5, ydb)
     # push the cube through the gel top: touching / crossing surfaces rejected
     y4 = y.copy()
     y4[0, 2] -= 4.2e-3
     st = genv.set_state(0, None, None, y4, None)
     assert st in (ipc.IPC_EINTERSECT, ipc.IPC_OK)
     genv.close()
+
+
+def _scripted_steps(genv, sc, ks):
+    for k in ks:
+        t = genv.rest_y(0)
+        t[:, :3] += sc.delta(k)[:, :3]
+        genv.set_targets(0, t)
+        st, _ = genv.step()
+        assert st[0] == ipc.IPC_OK, k
+
+
+@pytest.mark.parametrize("which", ["spin", "config0"])
+def test_resume_from_saved_state_matches_continuing(which):
+    """Checkpoint / resume: a state read after three steps and set into a
+    fresh context continues as the original context does.  Without contact
+    every sum runs in a fixed order, so the two agree bit for bit; with
+    contact the pair sums use atomics, whose order is free, and the two agree
+    within the FP64 parity bar (1e-6 of the bbox diagonal per step)."""
+    sc = scenes.spin_scene() if which == "spin" else scenes.config0()
+    prm = sc.params.parity()
+    a = ipc.Envs([sc.scene], prm)
+    if sc.v0 is not None or sc.ydot0 is not None:
+        assert a.set_state(0, None, sc.v0, None, sc.ydot0) == ipc.IPC_OK
+    _scripted_steps(a, sc, range(3))
+    saved = a.get_state(0)
+    b = ipc.Envs([sc.scene], prm)
+    assert b.set_state(0, *saved) == ipc.IPC_OK
+    _scripted_steps(a, sc, range(3, 5))
+    _scripted_steps(b, sc, range(3, 5))
+    sa, sb = a.get_state(0), b.get_state(0)
+    if which == "spin":
+        for u, w in zip(sa, sb):
+            assert np.array_equal(u, w)
+    else:
+        diag = float(np.linalg.norm(sa[0].max(0) - sa[0].min(0)))
+        assert np.abs(sa[0] - sb[0]).max() <= 2e-6 * diag
+        assert np.abs(sa[2][:, :3] - sb[2][:, :3]).max() <= 2e-6 * diag
+        assert np.abs(sa[1] - sb[1]).max() <= 2e-6 * diag / prm.dt
+    a.close()
+    b.close()
 
 
 def test_subset_and_empty_steps_touch_only_the_selected_envs():
