@@ -551,7 +551,6 @@ void ipc_default_params(ipc_params* p) {
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
   if (!prm || !bytes) return IPC_EINVAL;
-  ipc_ctx* ctx = nullptr;
   Pack pk;
   std::string err;
   if (!build_pack(scenes, n_envs, *prm, pk, err)) return IPC_EINVAL;
@@ -561,7 +560,6 @@ ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const i
   std::vector<std::pair<const void*, std::pair<void*, size_t>>> up;
   carve(pk, *prm, c, d, ex, up);
   *bytes = c.off;
-  (void)ctx;
   return IPC_OK;
 }
 
@@ -835,7 +833,6 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); });
   KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); });
   KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); });
-  int newton_done = 0;
   for (int it = 0; it < ctx->prm.newton_max; ++it) {
     KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
     if ((st = assemble_system(ctx, it == 0)) != IPC_OK) return st;
@@ -844,7 +841,6 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     KL(ctx, KC_NEWTON, [&] { return launch_newton_decide(d, s); });
     KL(ctx, KC_NEWTON, [&] { return launch_al_update(d, s); });
     if ((st = sync_flags(ctx)) != IPC_OK) return st;
-    newton_done = it + 1;
     int n_ls = count_flag(ctx, I_LS);
     if (n_ls == 0) {
       if (count_flag(ctx, I_ACTIVE) == 0) break;
@@ -892,7 +888,6 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     S.accd_iters_max = std::max(S.accd_iters_max, ei[I_ACCDMAX]);
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
   }
-  (void)newton_done;
   S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = S;
   return IPC_OK;
@@ -933,7 +928,6 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
   if ((st = begin_single(ctx, env)) != IPC_OK) return st;
   if ((st = assemble_system(ctx, true)) != IPC_OK) return st;
   std::vector<double> rows;
-  size_t nd = 3 * (size_t)ev.n_verts + 12 * (size_t)ev.n_bodies;
   if (grad) {
     if ((st = download_rows(ctx, env, d.g, rows)) != IPC_OK) return st;
     rows_to_dof(ctx, env, rows, grad);
@@ -964,7 +958,6 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
     if ((st = download_rows(ctx, env, d.q, rows)) != IPC_OK) return st;
     rows_to_dof(ctx, env, rows, hvec);
   }
-  (void)nd;
   return IPC_OK;
 }
 
