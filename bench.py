@@ -339,8 +339,7 @@ def per_step_error(g64, g32, tg, body_radius):
 
 # DRAM traffic of one SpMV launch with every env of the 256-env workload
 # active: dram__bytes_read.sum + dram__bytes_write.sum of the first k_spmv
-# launch of `bench.py --only-mixed --steps 1 --warmup 1` under ncu
-# (profiles/k_spmv_traffic_mixed_256env_gel40x40x6.md).  Reported only while
+# launch of `bench.py --only-mixed --steps 1 --warmup 1` under ncu.  Reported only while
 # the kernel's source is the one that was measured (hash of its text).
 # (measured with 4 slots in flight per lane)
 SPMV_TRAFFIC = {"envs": 256, "bytes": 1275934208 + 90306816,

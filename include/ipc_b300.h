@@ -164,35 +164,40 @@ ipc_status ipc_destroy(ipc_ctx* ctx);
 /* Last error message of this ctx (empty string if none). */
 const char* ipc_last_error(const ipc_ctx* ctx);
 
-/* Run the PCG inner loop (Sec. 4, the block-Jacobi PCG solve of each Newton
- * iteration) as a CUDA graph: the 16 iterations between two host checks of
- * the per-env convergence flags (4 kernel launches each, 5 with friction)
- * are captured on the ctx stream at the first solve and replayed after
- * that.  Results are the
- * same as with plain launches.  on = 0 (default) launches kernel by kernel.
- * The ctx stream must support capture (a created stream, not the legacy
- * default stream); otherwise ipc_step returns IPC_ECUDA with the reason in
- * ipc_last_error.  While per-kernel profiling is on, plain launches are
- * used so that every kernel is timed. */
+/* Run each PCG solve (the block-Jacobi PCG of every Newton iteration,
+ * named as the method's main cost in the paper's Limitations) as one CUDA
+ * graph: a work-list kernel, then a WHILE node over one iteration (the
+ * mat-vec, the friction mat-vec when friction is on, the update) whose
+ * condition the update kernel sets on the device, so the solve runs
+ * without host round trips.  Captured on the ctx stream at the first solve
+ * and replayed after that.  Results are the same as with plain launches,
+ * which poll an on-device count of iterating envs every 16 iterations.
+ * on = 0 (default) launches kernel by kernel.  The ctx stream must support
+ * capture (a created stream, not the legacy default stream); otherwise
+ * ipc_step returns IPC_ECUDA with the reason in ipc_last_error.  While
+ * per-kernel profiling is on, plain launches are used so that every kernel
+ * is timed. */
 ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on);
 
 /* Launch shapes chosen by ipc_autotune and the timings behind the choice. */
 typedef struct {
-  int spmv_unroll;        /* SELL slots in flight per lane in the SpMV: 2, 4 or 8 */
-  int pair_ctas_per_sm;   /* contact mat-vec grid: CTAs per SM (x 148)        */
-  float spmv_us[3];       /* mean SpMV time per launch for 2, 4, 8, us         */
-  float pair_us[4];       /* contact mat-vec for 2, 4, 8, 16 CTAs per SM, us   */
+  int spmv_unroll;        /* SELL slots in flight per lane in the PCG mat-vec: 2, 4 or 8 */
+  int pcg_ctas_per_sm;    /* persistent PCG grid: CTAs per SM (x SM count)            */
+  float spmv_us[3];       /* mean mat-vec time per launch for 2, 4, 8 slots, us        */
+  int grid_ctas_per_sm[3];/* grid candidates: half, all and twice the resident CTAs   */
+  float grid_us[3];       /* mean mat-vec time per launch for those grids, us          */
 } ipc_tuning;
 
-/* Choose the SpMV's slots in flight per lane and the contact mat-vec's grid
- * size by timing `reps` launches of each candidate on this ctx's current
+/* Choose the PCG mat-vec's SELL slots in flight per lane and the persistent
+ * PCG grid by timing `reps` launches of each candidate on this ctx's current
  * system (call it after at least one ipc_step, between steps), with every
  * env counted as iterating.  A candidate replaces the default shape only
- * when it is more than 5% faster.  It touches only PCG scratch (q, the PCG
- * scalars) and clears the contact accumulator afterwards, so later steps
- * give the same results as before apart from the launch shapes.  Any
- * captured PCG graph is dropped and re-captured at the next solve.  Not in
- * the paper: a property of this library.  `out` may be NULL. */
+ * when it is more than 5% faster.  It touches only PCG scratch (q, the new
+ * direction buffer, the d.q sums) and clears the contact accumulator
+ * afterwards, so later steps give the same results as before apart from the
+ * launch shapes.  Any captured PCG graph is dropped and re-captured at the
+ * next solve.  Not in the paper: a property of this library.  `out` may be
+ * NULL. */
 ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out);
 
 int ipc_num_envs(const ipc_ctx* ctx);
@@ -236,6 +241,17 @@ ipc_status ipc_set_targets_all_device(ipc_ctx* ctx, const double* dev_y_targets)
 ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n,
                     int32_t* per_env_status, ipc_step_stats* stats);
 
+/* Per-env counters of the last ipc_step that included `env` (host only; the
+ * values were read back at the end of that step).  out[IPC_ENV_STATS]:
+ *   0 status, 1 Newton iterations, 2 AL multiplier updates, 3 PCG
+ *   iterations (all Newton iterations), 4 line-search energy trials,
+ *   5 line searches that started below alpha = 1 (CCD-limited), 6 most ACCD
+ *   iterations one pair took, 7 candidate pairs in the last list,
+ *   8 ACCD iterations over all pairs.
+ * Diagnostics of this library (the paper reports no iteration counts). */
+#define IPC_ENV_STATS 9
+ipc_status ipc_env_stats(const ipc_ctx* ctx, int env, int32_t* out);
+
 /* Coated-surface vertex positions of one env's gel (Sec. 4.1: the surface
  * minus pinned and attached vertices), in increasing gel vertex id order.
  * Writes min(capacity, count) rows of [3]; *n_written = count. */
@@ -257,9 +273,10 @@ ipc_status ipc_read_gel_surface_all(ipc_ctx* ctx, double* out_xyz, size_t capaci
  *   - Calls no cudaMalloc / cudaFree; needs no workspace scratch.
  *   - Returns IPC_EINVAL (message in ipc_last_error) when the envs hold more
  *     than 262144 coated-surface rows in total.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - The context's device must be the current device (IPC_EINVAL
+ *     otherwise); devices 0..63 are supported.  The first call on a device
+ *     looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture.
  *   - Every call shares the array: calls that overlap on the GPU (several host
  *     threads or streams) race on it and must be serialised by the caller.
  * Synchronises the ctx stream. */

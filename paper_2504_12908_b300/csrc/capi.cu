@@ -29,12 +29,12 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // ---- per-kernel-class launch counts and event timing
 enum Kc {
   KC_PREDICT, KC_CVPOS, KC_OBJBOX, KC_BROAD, KC_BARRIER, KC_TET, KC_BODY, KC_ASSEMBLE, KC_GRAD, KC_PRECOND,
-  KC_PCGINIT, KC_PAIRSPMV, KC_SPMV, KC_PCGUPD, KC_PCGDIR, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC, KC_COUNT
+  KC_PCGINIT, KC_FRICSPMV, KC_SPMV, KC_PCGUPD, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC, KC_COUNT
 };
-const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",    "obj_box",   "broad_phase", "barrier",
-                                 "tet_elastic",  "body_abd",  "assemble",  "gradient",    "precond",
-                                 "pcg_init",     "pair_spmv", "sell_spmv", "pcg_update",  "pcg_dir",
-                                 "newton_check", "accd",      "ls_energy", "ls_update",   "misc"};
+const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",      "obj_box",    "broad_phase", "barrier",
+                                 "tet_elastic",  "body_abd",    "assemble",   "gradient",    "precond",
+                                 "pcg_init",     "fric_matvec", "pcg_matvec", "pcg_update",
+                                 "newton_check", "accd",        "ls_energy",  "ls_update",   "misc"};
 
 cudaEvent_t take_ev(ipc_ctx* ctx) {
   if (!ctx->ev_free.empty()) {
@@ -140,7 +140,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.fr_mu = prm.friction_mu;
   d.fr_eh = prm.friction_eps_v * prm.dt;
   d.spmv_unroll = 0;
-  d.pair_ctas_per_sm = 0;
+  d.pcg_grid = 148;
   d.newton_max = prm.newton_max;
   d.pcg_max = prm.pcg_max;
   d.ls_max = prm.ls_max;
@@ -229,10 +229,16 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.r = c.take<double>(R3);
   d.z = c.take<double>(R3);
   d.d = c.take<double>(R3);
+  d.db = c.take<double>(R3);
   d.z4 = c.take<float4>((size_t)pk.n_rows);
   d.d4 = c.take<float4>((size_t)pk.n_rows);
+  d.d4b = c.take<float4>((size_t)pk.n_rows);
   d.q4 = c.take<float4>((size_t)pk.n_rows);
-  d.cta_list = c.take<int>((size_t)pk.n_rows / 128);
+  d.row_touch = c.take<uint8_t>((size_t)pk.n_rows);
+  d.pcg_list = c.take<int>((size_t)pk.n_envs);
+  d.pcg_item_off = c.take<int>((size_t)pk.n_envs + 1);
+  d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
+  d.pcg_ctl = c.take<unsigned int>(8);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
   d.pc = c.take<double>(6 * (size_t)pk.n_rows);
@@ -272,8 +278,6 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pair_E = c.take<double>(pk.n_pairs_cap);
   d.pair_act = c.take<uint8_t>(pk.n_pairs_cap);
   d.pair_scan = c.take<int>(pk.n_envs + 1);
-  d.act_list = c.take<int>(pk.n_pairs_cap);
-  d.act_env = c.take<int>(pk.n_pairs_cap);
   d.act_v = c.take<int4>(pk.n_pairs_cap);
   const size_t nfr = prm.friction_mu > 0.0 ? pk.n_pairs_cap : 0;
   d.fr_v = c.take<int4>(nfr);
@@ -289,7 +293,6 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.accd_tail = c.take<int4>(pk.n_pairs_cap);
   d.accd_tail_t = c.take<double>(pk.n_pairs_cap);
   d.accd_tail_ctl = c.take<unsigned int>(2);
-  d.act_count = c.take<int>(1);
   d.cta_part = c.take<double>(4 * (size_t)(pk.n_rows / 128));
   d.env_cnt = c.take<unsigned int>(2 * (size_t)pk.n_envs);
   int mb = 0;
@@ -321,7 +324,14 @@ ipc_status sync_flags(ipc_ctx* ctx) {
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_dbl, ctx->dev.env_s, NUM_SCALARS * sizeof(double) * ctx->pk.n_envs,
                      cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->pcg_graph_pending)
+    CK(cudaMemcpyAsync(ctx->h_ctl, ctx->dev.pcg_ctl, 8 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->pcg_graph_pending) {
+    // the graph ran the WHILE body h_ctl[1] times
+    ctx->launches += (long long)ctx->h_ctl[1] * ctx->pcg_iter_launches;
+    ctx->pcg_graph_pending = false;
+  }
   prof_flush(ctx);
   return IPC_OK;
 }
@@ -369,45 +379,62 @@ ipc_status assemble_system(ipc_ctx* ctx, bool lag_friction) {
   return last_cuda(ctx);
 }
 
-constexpr int kPcgPoll = 16;  // PCG iterations between host checks of the per-env flags
+constexpr int kPcgPoll = 16;  // host-driven path: PCG iterations between reads of the live-env count
 
-// one PCG iteration over every PCG-active env; returns the launches issued.
-// n_cta >= 0: the row kernels run only the CTAs listed in Dev::cta_list.
-int pcg_iteration(ipc_ctx* ctx, int n_cta = -1) {
+// one PCG iteration on stream s over the device-side work list; returns the
+// launches issued.  use_cond: the update kernel sets the graph condition h.
+int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
   const Dev& d = ctx->dev;
-  cudaStream_t s = ctx->stream;
   long long l0 = ctx->launches;
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, s); });
-  KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, s); });
-  KL(ctx, KC_SPMV, [&] { return launch_spmv(d, s, n_cta); });
-  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, n_cta); });
-  KL(ctx, KC_PCGDIR, [&] { return launch_pcg_dir(d, s, n_cta); });
+  KL(ctx, KC_SPMV, [&] { return launch_pcg_matvec(d, s); }, s);
+  KL(ctx, KC_FRICSPMV, [&] { return launch_fric_spmv(d, s); }, s);
+  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, h, use_cond); }, s);
   return (int)(ctx->launches - l0);
 }
 
-// Row CTAs of the envs whose flag is set (from the last flag read-back),
-// uploaded to Dev::cta_list; returns their number.  The row kernels check
-// the flag themselves, so a list that is a superset is still correct.
-ipc_status upload_cta_list(ipc_ctx* ctx, int flag, int* n_out) {
-  const Pack& pk = ctx->pk;
-  int n = 0;
-  for (int e = 0; e < pk.n_envs; ++e) {
-    if (!ctx->h_int[e * NUM_INTS + flag]) continue;
-    const EnvInfo& ev = pk.env[e];
-    for (int c = ev.row_begin / 128; c < (ev.row_begin + ev.n_rows) / 128; ++c) ctx->h_cta_list[n++] = c;
-  }
-  if (n > 0)
-    CK(cudaMemcpyAsync(ctx->dev.cta_list, ctx->h_cta_list, sizeof(int) * (size_t)n, cudaMemcpyHostToDevice,
-                       ctx->stream));
-  *n_out = n;
-  return IPC_OK;
+// Adds a conditional node of `type` on handle h after everything captured so
+// far on the capturing stream s, and continues the capture after it;
+// *body receives the node's body graph (to be filled by capture-to-graph).
+cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  // zero-filled storage: the parameter union has no usable default constructor
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& prm = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, edges, nd, &prm);
+  if (e != cudaSuccess) return e;
+  *body = prm.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
-// Capture kPcgPoll iterations into a graph once per context.  The kernels
-// take the context's device tables by value and every per-step quantity
-// lives in device memory, so the same graph serves every later solve.
+// graph of the capturing stream s
+cudaError_t capturing_graph(cudaStream_t s, cudaGraph_t* g) {
+  cudaStreamCaptureStatus cs;
+  return cudaStreamGetCaptureInfo(s, &cs, nullptr, g, nullptr, nullptr, nullptr);
+}
+
+// The whole PCG solve as one graph: the work-list kernel sets the condition
+// of a WHILE node whose body is one iteration; the update kernel's last CTA
+// sets it again after every iteration (1 while an env iterates, 0 once
+// every env has stopped, at the latest after pcg_max + 2 iterations).  The
+// kernels take the context's device tables by value and every per-solve
+// quantity lives in device memory, so the graph is captured once per
+// context (and again after ipc_autotune changes a launch shape).
 ipc_status capture_pcg(ipc_ctx* ctx) {
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = ctx->stream, s_body = ctx->cap[0];
   cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -415,21 +442,41 @@ ipc_status capture_pcg(ipc_ctx* ctx) {
                " (the stream cannot be captured, e.g. the legacy default stream)";
     return IPC_ECUDA;
   }
-  long long l0 = ctx->launches;
-  int n = 0;
-  for (int i = 0; i < kPcgPoll; ++i) n += pcg_iteration(ctx);
+  const long long l0 = ctx->launches;
+  cudaGraph_t g = nullptr, body = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  e = capturing_graph(s, &g);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e == cudaSuccess) {
+    launch_pcg_begin(ctx->dev, s, h, 1);
+    e = add_conditional(s, h, cudaGraphCondTypeWhile, &body);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    ctx->pcg_iter_launches = pcg_iteration(ctx, s_body, h, 1);
+    cudaGraph_t b2 = nullptr;
+    e = cudaStreamEndCapture(s_body, &b2);
+  }
+  cudaGraph_t gg = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &gg);
+  if (e == cudaSuccess) e = e2;
   ctx->launches = l0;
-  cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(s, &g);
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->pcg_exec, g, 0);
-  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->pcg_exec, gg, 0);
+  if (gg) cudaGraphDestroy(gg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->pcg_exec = nullptr;
     ctx->err = std::string("PCG graph capture: ") + cudaGetErrorString(e);
     return IPC_ECUDA;
   }
-  ctx->pcg_exec_launches = n;
+  return IPC_OK;
+}
+
+// read Dev::pcg_ctl into pinned memory (synchronises the stream)
+ipc_status read_pcg_ctl(ipc_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_ctl, ctx->dev.pcg_ctl, 8 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
   return IPC_OK;
 }
 
@@ -438,24 +485,25 @@ ipc_status run_pcg(ipc_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
   const bool graph = ctx->graph_on && !ctx->prof_on;
-  int n_cta = -1;  // first block: every row CTA (the PCG set is read back after it)
-  for (int it = 0; it < ctx->prm.pcg_max; it += kPcgPoll) {
-    if (graph) {
-      if (!ctx->pcg_exec) {
-        ipc_status st = capture_pcg(ctx);
-        if (st != IPC_OK) return st;
-      }
-      CK(cudaGraphLaunch(ctx->pcg_exec, s));
-      ctx->launches += ctx->pcg_exec_launches;
-    } else {
-      for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx, n_cta);
+  if (graph) {
+    if (!ctx->pcg_exec) {
+      ipc_status st = capture_pcg(ctx);
+      if (st != IPC_OK) return st;
     }
-    // envs stop at pcg_max inside k_pcg_update, so a block past it is a no-op
-    ipc_status st = sync_flags(ctx);
+    CK(cudaGraphLaunch(ctx->pcg_exec, s));
+    // launches: the work-list kernel now, the iterations' when the
+    // iteration count is read back (sync_flags)
+    ctx->launches += 1;
+    ctx->pcg_graph_pending = true;
+    return last_cuda(ctx);
+  }
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, s, 0, 0); });
+  // every env stops by itself after at most pcg_max iterations
+  for (int it = 0; it < ctx->prm.pcg_max + 1; it += kPcgPoll) {
+    for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx, s);
+    ipc_status st = read_pcg_ctl(ctx);
     if (st != IPC_OK) return st;
-    if (count_flag(ctx, I_PCG) == 0) break;
-    // later blocks launch only the CTAs of envs still iterating
-    if (!graph && (st = upload_cta_list(ctx, I_PCG, &n_cta)) != IPC_OK) return st;
+    if (ctx->h_ctl[4] == 0) break;  // no env still iterating
   }
   return last_cuda(ctx);
 }
@@ -589,6 +637,9 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   ctx->ws = reinterpret_cast<char*>(dev_workspace);
   ctx->ws_bytes = ws_bytes;
   *out = ctx;
+  // the device the context's stream (and workspace) belong to
+  if (ctx->stream) CK(cudaStreamGetDevice(ctx->stream, &ctx->device));
+  else CK(cudaGetDevice(&ctx->device));
   const Pack& pk = ctx->pk;
   for (auto& u : up) CK(cudaMemcpyAsync(u.second.first, u.first, u.second.second, cudaMemcpyHostToDevice, ctx->stream));
   // zero every dynamic array (from x to the end of the workspace)
@@ -599,7 +650,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaMemcpyAsync(ctx->dev.s_tgt, pk.rest_x.data(), R3, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMallocHost(&ctx->h_int, NUM_INTS * sizeof(int) * (size_t)pk.n_envs));
   CK(cudaMallocHost(&ctx->h_dbl, NUM_SCALARS * sizeof(double) * (size_t)pk.n_envs));
-  CK(cudaMallocHost(&ctx->h_cta_list, sizeof(int) * (size_t)(pk.n_rows / 128)));
+  CK(cudaMallocHost(&ctx->h_ctl, 8 * sizeof(unsigned int)));
   for (const auto& ev : pk.env) ctx->max_bodies = std::max(ctx->max_bodies, ev.n_bodies);
   int prio_least = 0, prio_greatest = 0;
   CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
@@ -608,6 +659,10 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
     CK(cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming));
   }
   CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&ctx->cap[i], cudaStreamNonBlocking));
+  // persistent PCG grid: every resident CTA of the two PCG kernels
+  CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
+  ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
 }
@@ -616,7 +671,9 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
   if (!ctx) return IPC_EINVAL;
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
   if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
-  if (ctx->h_cta_list) cudaFreeHost(ctx->h_cta_list);
+  if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->cap[i]) cudaStreamDestroy(ctx->cap[i]);
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
@@ -643,11 +700,13 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   cudaStream_t s = ctx->stream;
   ipc_status st;
   if (ctx->pk.n_envs <= 0) return IPC_EINVAL;
-  // every env in PCG for the timing; the kernels only touch PCG scratch
-  // (q, the PCG scalars) and the contact accumulator, cleared afterwards
+  // every env in PCG for the timing; the mat-vec only writes PCG scratch
+  // (q, the new direction buffer, the d.q sums) and the contact
+  // accumulator, which is cleared afterwards
   std::vector<int> all(ctx->pk.n_envs);
   for (int e = 0; e < ctx->pk.n_envs; ++e) all[e] = e;
   if ((st = select_envs(ctx, all, I_PCG)) != IPC_OK) return st;
+  launch_pcg_begin(d, s, 0, 0);
   ipc_tuning t{};
   // a candidate replaces the default shape only when it is more than 5%
   // faster (ties and noise keep the default)
@@ -655,7 +714,8 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   const int def_u = d.prec ? 4 : 2;
   for (int k = 0; k < 3; ++k) {
     d.spmv_unroll = us_[k];
-    if ((st = time_launches(ctx, reps, [&] { launch_spmv(d, s); }, &t.spmv_us[k])) != IPC_OK) return st;
+    d.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(d.prec, us_[k]);
+    if ((st = time_launches(ctx, reps, [&] { launch_pcg_matvec(d, s); }, &t.spmv_us[k])) != IPC_OK) return st;
   }
   const float def_spmv = t.spmv_us[def_u == 2 ? 0 : 1];
   int best_u = def_u;
@@ -663,17 +723,18 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   for (int k = 0; k < 3; ++k)
     if (t.spmv_us[k] < best && t.spmv_us[k] < 0.95f * def_spmv) { best = t.spmv_us[k]; best_u = us_[k]; }
   d.spmv_unroll = best_u;
-  const int ctas_[4] = {2, 4, 8, 16};
-  for (int k = 0; k < 4; ++k) {
-    d.pair_ctas_per_sm = ctas_[k];
-    if ((st = time_launches(ctx, reps, [&] { launch_pair_spmv(d, s); }, &t.pair_us[k])) != IPC_OK) return st;
+  // persistent grid: half, all or twice the resident CTAs per SM
+  const int occ = pcg_ctas_per_sm(d.prec, best_u);
+  const int cand[3] = {occ > 1 ? occ / 2 : 1, occ, 2 * occ};
+  for (int k = 0; k < 3; ++k) {
+    d.pcg_grid = ctx->n_sm * cand[k];
+    if ((st = time_launches(ctx, reps, [&] { launch_pcg_matvec(d, s); }, &t.grid_us[k])) != IPC_OK) return st;
   }
-  const float def_pair = t.pair_us[2];
-  int best_c = 8;
-  best = def_pair;
-  for (int k = 0; k < 4; ++k)
-    if (t.pair_us[k] < best && t.pair_us[k] < 0.95f * def_pair) { best = t.pair_us[k]; best_c = ctas_[k]; }
-  d.pair_ctas_per_sm = best_c;
+  int best_c = occ;
+  best = t.grid_us[1];
+  for (int k = 0; k < 3; ++k)
+    if (t.grid_us[k] < best && t.grid_us[k] < 0.95f * t.grid_us[1]) { best = t.grid_us[k]; best_c = cand[k]; }
+  d.pcg_grid = ctx->n_sm * best_c;
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
   CK(cudaStreamSynchronize(s));
@@ -683,7 +744,8 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
     ctx->pcg_exec = nullptr;
   }
   t.spmv_unroll = best_u;
-  t.pair_ctas_per_sm = best_c;
+  t.pcg_ctas_per_sm = best_c;
+  for (int k = 0; k < 3; ++k) t.grid_ctas_per_sm[k] = cand[k];
   if (out) *out = t;
   return IPC_OK;
 }
@@ -893,6 +955,14 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
   return IPC_OK;
 }
 
+ipc_status ipc_env_stats(const ipc_ctx* ctx, int env, int32_t* out) {
+  if (check_env(ctx, env) != IPC_OK || !out) return IPC_EINVAL;
+  const int* ei = ctx->h_int + env * NUM_INTS;
+  const int k[IPC_ENV_STATS] = {I_STATUS, I_NEWTON, I_AL, I_PCGTOT, I_LSTOT, I_CCDCUT, I_ACCDMAX, I_NPAIRS, I_ACCDIT};
+  for (int i = 0; i < IPC_ENV_STATS; ++i) out[i] = ei[k[i]];
+  return IPC_OK;
+}
+
 ipc_status ipc_read_gel_surface(ipc_ctx* ctx, int env, double* out_xyz, int capacity, int* n_written) {
   if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
   const EnvInfo& ev = ctx->pk.env[env];
@@ -948,11 +1018,12 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
     // from FP64 rows staged in d.z
     if ((st = upload_rows(ctx, env, d.z, vr)) != IPC_OK) return st;
     if ((st = select_envs(ctx, {env}, I_PCG)) != IPC_OK) return st;
-    KL(ctx, KC_PCGDIR, [&] { return launch_debug_dir_from_rows(d, ctx->stream); });
-    KL(ctx, KC_PAIRSPMV, [&] { return launch_pair_spmv(d, ctx->stream); });
-    KL(ctx, KC_PAIRSPMV, [&] { return launch_fric_spmv(d, ctx->stream); });
-    KL(ctx, KC_SPMV, [&] { return launch_spmv(d, ctx->stream); });
-    KL(ctx, KC_PCGDIR, [&] { return launch_debug_q_to_rows(d, ctx->stream); });
+    // one mat-vec with z = v, beta = 0 and d_{-1} = 0 (so d_0 = v)
+    KL(ctx, KC_MISC, [&] { return launch_debug_dir_from_rows(d, ctx->stream); });
+    KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, ctx->stream, 0, 0); });
+    KL(ctx, KC_SPMV, [&] { return launch_pcg_matvec(d, ctx->stream); });
+    KL(ctx, KC_FRICSPMV, [&] { return launch_fric_spmv(d, ctx->stream); });
+    KL(ctx, KC_MISC, [&] { return launch_debug_q_to_rows(d, ctx->stream); });
     if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
     if ((st = last_cuda(ctx)) != IPC_OK) return st;
     if ((st = download_rows(ctx, env, d.q, rows)) != IPC_OK) return st;

@@ -28,6 +28,7 @@ enum EnvScalar {
   S_E1,         // energy at the trial step
   S_MIND,       // min pair distance (diagnostics)
   S_ASUM,       // accepted line-search steps this step, summed
+  S_DQC,        // PCG d.q, contact part (pair and friction terms, summed by atomics)
   NUM_SCALARS
 };
 
@@ -53,6 +54,8 @@ enum EnvInt {
   I_ACCDIT,       // ACCD advancement iterations this step (all pairs)
   I_ACCDMAX,      // most ACCD iterations one pair took this step
   I_NFRIC,        // lagged friction records of this step
+  I_NACT,         // active contact pairs (d < dhat) of this Newton iteration
+  I_GEN,          // Newton iterations ever run (tags the rows contact terms touch)
   NUM_INTS
 };
 
@@ -64,8 +67,8 @@ struct Dev {
   int newton_max, pcg_max, ls_max, accd_max, al_max;
   int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
   // launch shapes (ipc_autotune): SpMV slots in flight per lane (2, 4, 8;
-  // 0 = default by precision) and the contact mat-vec grid in CTAs per SM
-  int spmv_unroll, pair_ctas_per_sm;
+  // 0 = default by precision)
+  int spmv_unroll;
   double fr_mu, fr_eh;          // friction coefficient; eps_v * h (fr_mu = 0: no friction)
   // static tables
   const int *env_row_off, *env_tet_off, *env_cv_off, *env_tri_off, *env_edge_off, *env_obj_off,
@@ -99,7 +102,21 @@ struct Dev {
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
   float4 *z4, *d4, *q4;         // mixed mode: the PCG vectors z, d, q as FP32 rows (16 B)
-  int* cta_list;                // row CTAs (128 rows each) of the envs still in PCG
+  // The PCG direction is double-buffered: iteration k reads d_{k-1} from one
+  // buffer and writes d_k = z_k + beta d_{k-1} into the other (d / d4 when
+  // k is even, db / d4b when odd).
+  double* db;
+  float4* d4b;
+  uint8_t* row_touch;           // per row: 1 + (I_GEN % 255) of the Newton iteration whose
+                                // contact terms write the row's contact accumulator qc
+  // device-side PCG work list (rebuilt on the device when an env stops):
+  int* pcg_list;                // [n_envs] envs still in PCG
+  int* pcg_item_off;            // [n_envs + 1] prefix of their mat-vec work items
+                                // (128-row CTAs, then groups of 8 active pairs)
+  int* pcg_row_off;             // [n_envs + 1] prefix of their 128-row CTAs
+  unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
+                                // [2] envs in the list, [3] the list is stale
+  int pcg_grid;                 // CTAs of the persistent PCG kernels
   void* pc;                     // 6 per row: symmetric inverse of the diagonal block
                                 // (double, or float in mixed mode)
   double* pc_acc;               // 9 per row
@@ -118,13 +135,12 @@ struct Dev {
   int4* pair_v;                 // contact vertex ids
   int* pair_kind;               // 0 PT, 1 EE
   double *pair_w, *pair_eps, *pair_E;
-  void* pair_H;                 // 78 per active pair, by act_list slot s: entry j of the packed upper
+  void* pair_H;                 // 78 per active pair, by its slot s: entry j of the packed upper
                                 // triangle at ((s / 32) * 78 + j) * 32 + s % 32 (double, or float in mixed mode)
   uint8_t* pair_act;
   int* pair_scan;                // n_envs + 1: exclusive scan of pair counts
-  int* act_list;                 // slots of active (d < dhat) pairs
-  int* act_env;                  // env of each act_list entry
-  int4* act_v;                   // contact points of each act_list entry
+  int4* act_v;                   // contact points of each active (d < dhat) pair, by slot: the
+                                 // env's active pairs fill slots env_pair_off[e] + [0, I_NACT)
   // lagged friction records (segments like the pair list, I_NFRIC per env)
   int4* fr_v;                    // contact points of the pair
   double *fr_w, *fr_T, *fr_rn;   // closest-point weights (4), tangent basis (6), r at x^n (3)
@@ -133,7 +149,6 @@ struct Dev {
   int4* accd_tail;               // ACCD pairs left for the warp-parallel phase: (slot, env, iterations, -)
   double* accd_tail_t;           // their certified time so far
   unsigned int* accd_tail_ctl;   // [entries, finished CTAs]; zero between launches
-  int* act_count;
   double* cta_part;             // 4 per row CTA
   unsigned int* env_cnt;        // last-CTA counters (2 per env)
   double* tgt_stage;            // [n_envs][max_bodies][12] host targets
@@ -155,11 +170,12 @@ struct ipc_ctx {
   ipc::Dev dev;
   ipc_params prm;
   cudaStream_t stream = nullptr;
+  int device = -1;            // CUDA device of the stream / workspace (set at create)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   std::string err;
   int* h_int = nullptr;       // pinned read-back (NUM_INTS * n_envs ints)
-  int* h_cta_list = nullptr;  // pinned staging of Dev::cta_list
+  unsigned int* h_ctl = nullptr;  // pinned read-back of Dev::pcg_ctl (8)
   double* h_dbl = nullptr;    // pinned read-back (NUM_SCALARS * n_envs doubles)
   int max_bodies = 0;
   std::vector<int> n_cta_env;  // row CTAs per env
@@ -171,10 +187,14 @@ struct ipc_ctx {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[2] = {nullptr, nullptr};
-  // CUDA graph of one PCG polling block (ipc_set_graph_mode)
+  // CUDA graph of the whole PCG solve, a WHILE node over one iteration
+  // (ipc_set_graph_mode); streams used to capture conditional bodies
   bool graph_on = false;
   cudaGraphExec_t pcg_exec = nullptr;
-  int pcg_exec_launches = 0;
+  int pcg_iter_launches = 0;      // kernel launches per PCG iteration
+  bool pcg_graph_pending = false; // a graph solve ran; its iteration count is not yet read
+  cudaStream_t cap[2] = {nullptr, nullptr};
+  int n_sm = 148;
   // profiling
   bool prof_on = false;
   long long launches = 0;

@@ -13,7 +13,6 @@ int launch_cv_pos(const Dev& d, int flag, bool with_disp, cudaStream_t s);
 int launch_obj_box(const Dev& d, int flag, bool swept, cudaStream_t s);
 int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s);
 int launch_barrier(const Dev& d, int flag, cudaStream_t s);
-int launch_pair_spmv(const Dev& d, cudaStream_t s);
 int launch_accd(const Dev& d, cudaStream_t s);
 // lagged friction (no launches when friction_mu = 0)
 int launch_fric_setup(const Dev& d, cudaStream_t s);
@@ -32,12 +31,17 @@ int launch_body(const Dev& d, cudaStream_t s);
 int launch_assemble(const Dev& d, cudaStream_t s);
 int launch_grad(const Dev& d, cudaStream_t s);
 int launch_precond(const Dev& d, cudaStream_t s);
+// ---- PCG (kernels_pcg.cu)
 int launch_pcg_init(const Dev& d, cudaStream_t s);
-// PCG row kernels: n_cta < 0 launches every row CTA; otherwise only the
-// first n_cta CTAs listed in Dev::cta_list (the envs still in PCG)
-int launch_spmv(const Dev& d, cudaStream_t s, int n_cta = -1);
-int launch_pcg_update(const Dev& d, cudaStream_t s, int n_cta = -1);
-int launch_pcg_dir(const Dev& d, cudaStream_t s, int n_cta = -1);
+// work list of the envs whose I_PCG flag is set; with use_cond the kernel
+// sets the graph condition `h` (1 while an env iterates)
+int launch_pcg_begin(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond);
+// one PCG iteration = mat-vec (+ friction mat-vec) + update; the update's
+// last CTA advances the iteration counter and, with use_cond, sets `h`
+int launch_pcg_matvec(const Dev& d, cudaStream_t s);
+int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond);
+// resident 128-thread CTAs per SM of the PCG kernels (grid = 148 x this)
+int pcg_ctas_per_sm(int prec, int unroll);
 // diagnostics: PCG direction from the FP64 rows in Dev::z; q back to Dev::q
 int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s);
 int launch_debug_q_to_rows(const Dev& d, cudaStream_t s);

@@ -232,11 +232,11 @@ __global__ void k_bp_check(Dev d, int flag) {
 }
 
 // Exclusive scan of the per-env pair counts (one CTA): pair kernels then
-// walk a flat index space of real pairs only.  Also clears the active list.
+// walk a flat index space of real pairs only.
 __global__ void k_pair_scan(Dev d) {
   __shared__ int warp_tot[32];
   __shared__ int carry;
-  if (threadIdx.x == 0) { carry = 0; *d.act_count = 0; }
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int base = 0; base < d.n_envs; base += blockDim.x) {
@@ -302,6 +302,17 @@ __device__ __forceinline__ void scatter_cv(const Dev& d, double* dst, int cv, D3
   }
 }
 
+// tag the rows scatter_cv writes for contact vertex cv (the PCG update reads
+// the contact accumulator only on tagged rows)
+__device__ __forceinline__ void touch_cv(const Dev& d, int cv, uint8_t tag) {
+  const int row = d.cv_row[cv];
+  if (d.cv_body[cv] < 0) {
+    if (d.row_kind[row] != ROW_PINNED) d.row_touch[row] = tag;
+  } else {
+    for (int k = 0; k < 4; ++k) d.row_touch[row + k] = tag;
+  }
+}
+
 // HT: storage type of the pair Hessian (double: FP64 mode; float: mixed
 // mode).  Distances, barrier derivatives and the projection are FP64 either way.
 template <class HT>
@@ -320,23 +331,26 @@ __global__ void k_barrier(Dev d, int flag) {
     act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
     d.pair_act[k] = act ? 1 : 0;
   }
-  // the warp's active pairs (consecutive pairs, mostly of one env) take
-  // consecutive slots: one atomic per warp
+  // the active pairs of an env fill its slots env_pair_off[e] + [0, I_NACT)
+  // in any order; the warp's lanes of one env take consecutive slots (one
+  // atomic per env present in the warp)
   const unsigned wm = __activemask();
   const unsigned am = __ballot_sync(wm, act);
   if (!act) continue;
-  const int lane = threadIdx.x & 31, leader = __ffs(am) - 1;
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(am, e);
+  const int leader = __ffs(grp) - 1;
   int base = 0;
-  if (lane == leader) base = atomicAdd(d.act_count, __popc(am));
-  base = __shfl_sync(am, base, leader);
-  const int slot = base + __popc(am & ((1u << lane) - 1u));
-  d.act_list[slot] = k;
-  d.act_env[slot] = e;
+  if (lane == leader) base = atomicAdd(&ENVI(d, e, I_NACT), __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  const int slot = d.env_pair_off[e] + base + __popc(grp & ((1u << lane) - 1u));
   d.act_v[slot] = make_int4(cvs[0], cvs[1], cvs[2], cvs[3]);
   // interleaved by warp of slots so that the mat-vec's loads coalesce
   HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)(slot >> 5) * 78 * 32 + (slot & 31);
   for (int p = 0, o = 0; p < 12; ++p)
     for (int q = p; q < 12; ++q, ++o) Hs[o * 32] = (HT)H[p * 12 + q];
+  const uint8_t tag = touch_tag(d, e);
+  for (int i = 0; i < 4; ++i) touch_cv(d, cvs[i], tag);
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
   // preconditioner: diagonal 3x3 of gel vertices, body 12x12 self terms
   for (int i = 0; i < 4; ++i) {
@@ -378,102 +392,6 @@ __global__ void k_barrier(Dev d, int flag) {
             atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, s);
           }
   }
-  }
-}
-
-// q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
-// eliminated: read as zero, never written)
-// index of (p, q), p <= q, in the packed upper triangle of a 12x12 matrix
-__device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) / 2 + (q - p); }
-
-// q_c += H_k d for every active pair of PCG-active envs (pinned gel rows are
-// eliminated: read as zero, never written).  H_k is stored as its packed
-// upper triangle, interleaved by warp of active slots.
-// 16 lanes per pair (two pairs per warp), lane j < 12 owns coordinate j =
-// 3 m + c (point m, component c): it forms that component of the pair's
-// direction, the group shares the 12 values by shuffles, lane j computes row
-// j of H_k d (12 FMAs) and scatters it: gel points directly; body points as
-// J^T (H_k d) on the body's 4 sub-rows, merged with the other pair of the
-// warp when both touch the same single body.
-template <class HT>
-__global__ void k_pair_spmv(Dev d) {
-  const int n_act = *d.act_count;
-  const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
-  const int m = j / 3, c = j - 3 * m;
-  const int n_groups = (gridDim.x * blockDim.x) >> 4;
-  for (int g0 = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 4; g0 < n_act; g0 += n_groups) {
-    const int i = g0 + half;                       // this half-warp's active slot
-    bool live = i < n_act;
-    int e = 0;
-    if (live) {
-      e = d.act_env[i];
-      live = ENVI(d, e, I_PCG) != 0;
-    }
-    int4 v = live ? d.act_v[i] : make_int4(0, 0, 0, 0);
-    const int cv = m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
-    // body of each point of the pair (-1: gel) and the pair's single body
-    int b_pt = -1, row = 0;
-    double xb[3] = {0, 0, 0};
-    HT dj = 0;
-    if (live && j < 12) {
-      row = d.cv_row[cv];
-      b_pt = d.cv_body[cv];
-      if (b_pt < 0) {
-        dj = (d.row_kind[row] == ROW_PINNED) ? (HT)0 : (HT)comp(PV<HT>::dir(d, row), c);
-      } else {
-        D3 x3 = ld3(d.cv_xbar, cv);
-        xb[0] = x3.x; xb[1] = x3.y; xb[2] = x3.z;
-        dj = (HT)(comp(PV<HT>::dir(d, row), c) + xb[0] * comp(PV<HT>::dir(d, row + 1), c) +
-                  xb[1] * comp(PV<HT>::dir(d, row + 2), c) + xb[2] * comp(PV<HT>::dir(d, row + 3), c));
-      }
-    }
-    // row j of H d
-    HT oj = 0;
-    const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)(i >> 5) * 78 * 32 + (i & 31);
-    for (int q = 0; q < 12; ++q) {
-      const HT dq = __shfl_sync(0xffffffffu, dj, (lane & 16) + q);
-      if (live && j < 12) {
-        const int lo = min(j, q), hi = max(j, q);
-        oj += H[ut12(lo, hi) * 32] * dq;
-      }
-    }
-    const double o = (double)oj;
-    // gel points: one atomic per coordinate
-    if (live && j < 12 && b_pt < 0 && d.row_kind[row] != ROW_PINNED) atomicAdd(d.qc + 3 * row + c, o);
-    // body points: the pair's single body (or several: per point)
-    int bm[4];
-    for (int mm = 0; mm < 4; ++mm) bm[mm] = __shfl_sync(0xffffffffu, b_pt, (lane & 16) + 3 * mm);
-    int body = -2;
-    for (int mm = 0; mm < 4; ++mm)
-      if (bm[mm] >= 0) body = (body == -2 || body == bm[mm]) ? bm[mm] : -1;
-    if (!live) body = -2;
-    // lane j = 3 s + c of the group: sub-row s of J^T o, component c
-    const int s4 = j / 3;
-    double jb = 0.0;
-    for (int mm = 0; mm < 4; ++mm) {
-      const int src = (lane & 16) + 3 * mm;          // holds point mm's xbar
-      const double om = __shfl_sync(0xffffffffu, o, src + c);
-      const double x0 = __shfl_sync(0xffffffffu, xb[0], src);
-      const double x1 = __shfl_sync(0xffffffffu, xb[1], src);
-      const double x2 = __shfl_sync(0xffffffffu, xb[2], src);
-      const double xs = s4 == 0 ? 1.0 : (s4 == 1 ? x0 : (s4 == 2 ? x1 : x2));
-      if (body >= 0 && bm[mm] == body) jb += xs * om;
-    }
-    // the two pairs of the warp on the same body: one atomic for both
-    const int other = __shfl_xor_sync(0xffffffffu, body, 16);
-    const double jb_other = __shfl_xor_sync(0xffffffffu, jb, 16);
-    if (body >= 0 && j < 12) {
-      if (other == body) {
-        if (half == 0) atomicAdd(d.qc + 3 * d.body_row[body] + j, jb + jb_other);
-      } else {
-        atomicAdd(d.qc + 3 * d.body_row[body] + j, jb);
-      }
-    }
-    if (body == -1 && j < 12 && b_pt >= 0) {  // points of several bodies: per point
-      const int br = d.body_row[b_pt];
-      atomicAdd(d.qc + 3 * br + c, o);
-      for (int s = 0; s < 3; ++s) atomicAdd(d.qc + 3 * (br + 1 + s) + c, xb[s] * o);
-    }
   }
 }
 
@@ -728,6 +646,8 @@ __global__ void k_fric_assemble(Dev d) {
   const D3 Tu = u0 * t1 + u1 * t2;
   const double* w = d.fr_w + 4 * (long long)j;
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], (sc * g * w[i]) * Tu);
+  const uint8_t tag = touch_tag(d, e);
+  for (int i = 0; i < 4; ++i) touch_cv(d, cvs[i], tag);
   // M = g I + gy u u^T (2x2) -> S = sc T M T^T = sc (g (t1 t1^T + t2 t2^T) + gy Tu Tu^T)
   double S[3][3];
   const double ta[3] = {t1.x, t1.y, t1.z}, tb[3] = {t2.x, t2.y, t2.z}, tu[3] = {Tu.x, Tu.y, Tu.z};
@@ -774,9 +694,12 @@ __global__ void k_fric_assemble(Dev d) {
   }
 }
 
-// PCG mat-vec: q_c += w_i S (sum_j w_j d_j) per record (pinned gel rows read
-// as zero and are never written).
+// PCG mat-vec, after the SELL / pair mat-vec of the same iteration (which
+// wrote this iteration's direction): q_c += w_i S (sum_j w_j d_j) per record
+// (pinned gel rows read as zero and are never written), and the record's
+// a^T S a (a = sum_j w_j d_j) into the env's contact part of d.q.
 __global__ void k_fric_spmv(Dev d) {
+  const int nb = pcg_new_buf(d);
   FOR_FRIC(d, li) {
   const int j = d.fr_list[li], e = d.fr_list_env[li];
   if (!ENVI(d, e, I_PCG)) continue;
@@ -787,14 +710,15 @@ __global__ void k_fric_spmv(Dev d) {
   for (int i = 0; i < 4; ++i) {
     int cv = cvs[i], row = d.cv_row[cv];
     D3 u;
-    if (d.cv_body[cv] < 0) u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : dir_row(d, row);
-    else u = dir_body_point(d, row, ld3(d.cv_xbar, cv));
+    if (d.cv_body[cv] < 0) u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : dir_row(d, row, nb);
+    else u = dir_body_point(d, row, ld3(d.cv_xbar, cv), nb);
     a = a + w[i] * u;
   }
   const double* S = d.fr_S + 6 * (long long)j;
   D3 t{S[0] * a.x + S[1] * a.y + S[2] * a.z, S[1] * a.x + S[3] * a.y + S[4] * a.z,
        S[2] * a.x + S[4] * a.y + S[5] * a.z};
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], w[i] * t);
+  atomicAdd(&ENVS(d, e, S_DQC), dot(a, t));
   }
 }
 
@@ -900,13 +824,6 @@ int launch_barrier(const Dev& d, int flag, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
   if (d.prec) k_barrier<float><<<PAIR_GRID>>>(d, flag);
   else k_barrier<double><<<PAIR_GRID>>>(d, flag);
-  return 1;
-}
-int launch_pair_spmv(const Dev& d, cudaStream_t s) {
-  const int ctas = 148 * (d.pair_ctas_per_sm > 0 ? d.pair_ctas_per_sm : 8);
-  if (!d.n_pairs_cap) return 0;
-  if (d.prec) k_pair_spmv<float><<<ctas, 128, 0, s>>>(d);
-  else k_pair_spmv<double><<<ctas, 128, 0, s>>>(d);
   return 1;
 }
 int launch_fric_setup(const Dev& d, cudaStream_t s) {

@@ -1,0 +1,556 @@
+// Block-Jacobi preconditioned conjugate gradients on H p = -g (K6), the
+// step the paper names as its main cost (Limitations).
+//
+// One PCG iteration is two persistent kernels over a device-side work list
+// of the envs still iterating:
+//   k_pcg_matvec: d_k = z_k + beta_k d_{k-1} (formed on the fly, written to
+//     the other direction buffer), q = A d_k over the SELL-32 matrix, and the
+//     contact terms H_c d_k of the env's active pairs (matrix-free, added to
+//     the accumulator qc); d_k . q summed per env (SELL part by CTA partials,
+//     contact part by atomics).
+//   k_pcg_update: alpha = r.z / d.q, p += alpha d, r -= alpha q, z = P^-1 r,
+//     r.z and r.r per env -> beta and the stop test.  The last CTA of the
+//     grid rebuilds the work list when stopped envs hold a quarter of its
+//     items, and (inside a CUDA graph) sets the loop's condition, so the
+//     whole solve runs without the host.
+// A work item is 128 consecutive rows of one env (one row per thread) or a
+// group of 8 active pairs of one env (16 lanes per pair).
+#include "common.cuh"
+#include "fpconv.cuh"
+#include "kernels.h"
+#include "pcgvec.cuh"
+
+namespace ipc {
+
+#define ENVI(d, e, k) (d).env_i[(e) * NUM_INTS + (k)]
+#define ENVS(d, e, k) (d).env_s[(e) * NUM_SCALARS + (k)]
+
+namespace {
+
+enum PcgCtl { C_ARRIVED = 0, C_ITER, C_LEN, C_DEAD, C_LIVE, C_COUNT };
+
+// component c of a 3-vector of either precision
+template <class T>
+__device__ __forceinline__ T comp3(V3<T> v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ bool row_is_body(uint8_t k) { return k == ROW_BODY || k == ROW_BODY_DRIVEN; }
+
+// largest i in [0, n) with off[i] <= item (off[0] = 0 <= item < off[n])
+__device__ __forceinline__ int list_find(const int* off, int n, int item) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int env_row_ctas(const Dev& d, int e) { return (d.env_row_off[e + 1] - d.env_row_off[e]) >> 7; }
+__device__ __forceinline__ int env_active_pairs(const Dev& d, int e) { return min(ENVI(d, e, I_NACT), d.env_pair_cap[e]); }
+
+// Rebuild the work list from the envs' I_PCG flags (one CTA, blockDim a
+// multiple of 32): list order is env order; row items of an env, then its
+// pair groups.
+__device__ void build_list(const Dev& d) {
+  __shared__ int wsum[3][32];
+  __shared__ int carry[3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+  __syncthreads();
+  for (int base = 0; base < d.n_envs; base += blockDim.x) {
+    const int e = base + threadIdx.x;
+    const bool on = e < d.n_envs && ENVI(d, e, I_PCG) != 0;
+    int v[3];
+    v[0] = on ? 1 : 0;
+    v[1] = on ? env_row_ctas(d, e) : 0;
+    v[2] = on ? v[1] + (env_active_pairs(d, e) + 7) / 8 : 0;
+    int inc[3];
+    for (int k = 0; k < 3; ++k) {
+      inc[k] = v[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc[k], o);
+        if (lane >= o) inc[k] += t;
+      }
+      if (lane == 31) wsum[k][wid] = inc[k];
+    }
+    __syncthreads();
+    if (wid == 0)
+      for (int k = 0; k < 3; ++k) {
+        const int w = lane < nw ? wsum[k][lane] : 0;
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, wi, o);
+          if (lane >= o) wi += t;
+        }
+        wsum[k][lane] = wi - w;  // exclusive warp offsets
+      }
+    __syncthreads();
+    int ex[3];
+    for (int k = 0; k < 3; ++k) ex[k] = carry[k] + wsum[k][wid] + inc[k] - v[k];
+    if (on) {
+      d.pcg_list[ex[0]] = e;
+      d.pcg_row_off[ex[0]] = ex[1];
+      d.pcg_item_off[ex[0]] = ex[2];
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1)
+      for (int k = 0; k < 3; ++k) carry[k] = ex[k] + v[k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d.pcg_row_off[carry[0]] = carry[1];
+    d.pcg_item_off[carry[0]] = carry[2];
+    d.pcg_ctl[C_LEN] = carry[0];
+    d.pcg_ctl[C_LIVE] = carry[0];
+    d.pcg_ctl[C_DEAD] = 0;
+  }
+  __syncthreads();
+}
+
+// ---- block-Jacobi preconditioner application
+// z = P^{-1} r for row r.  Body rows read the 4 sub-rows of their body (all
+// of them sit in the same warp) and apply the body's 12x12 inverse in FP64.
+__device__ __forceinline__ D3 apply_pc_body(const Dev& d, int r) {
+  const int b = d.row_body[r];
+  const int br = d.body_row[b];
+  const int kk = r - br;
+  const double* Pi = d.body_pc + 144 * (long long)b;
+  double o[3] = {0, 0, 0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
+  return D3{o[0], o[1], o[2]};
+}
+
+// FP64 mode: gel rows apply the 6 stored entries of the symmetric 3x3 inverse
+__device__ __forceinline__ D3 apply_pc64(const Dev& d, int r, uint8_t kr, D3 x) {
+  if (row_is_body(kr)) return apply_pc_body(d, r);
+  if (kr == ROW_PAD) return D3{0, 0, 0};
+  const double* P = reinterpret_cast<const double*>(d.pc) + 6 * (long long)r;
+  const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
+  return D3{a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z};
+}
+
+// mixed mode: FP32 inverse applied to the FP32-rounded residual of the row
+__device__ __forceinline__ float4 apply_pc32(const Dev& d, int r, uint8_t kr, float3 x) {
+  if (row_is_body(kr)) {
+    const D3 z = apply_pc_body(d, r);
+    return make_float4(d2f_bits(z.x), d2f_bits(z.y), d2f_bits(z.z), 0.0f);
+  }
+  if (kr == ROW_PAD) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float* P = reinterpret_cast<const float*>(d.pc) + 6 * (long long)r;
+  const float a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
+  return make_float4(a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z, 0.0f);
+}
+
+__device__ __forceinline__ float3 round_row(D3 v) { return make_float3(d2f_bits(v.x), d2f_bits(v.y), d2f_bits(v.z)); }
+__device__ __forceinline__ D3 widen_row(float4 v) { return D3{f2d_bits(v.x), f2d_bits(v.y), f2d_bits(v.z)}; }
+
+// d_k of one row from z_k and d_{k-1}: the same fused operations wherever a
+// row's direction is formed (its own row, a gathered column, a pair point)
+__device__ __forceinline__ float dk32(float z, float b, float dold) { return __fmaf_rn(b, dold, z); }
+__device__ __forceinline__ double dk64(double z, double b, double dold) { return __fma_rn(b, dold, z); }
+
+template <class HT> struct Dk;
+template <> struct Dk<float> {
+  static __device__ __forceinline__ V3<float> row(const Dev& d, int c, float b, int ob) {
+    const V3<float> z = PV<float>::gather_z(d, c), o = PV<float>::gather_dir(d, c, ob);
+    return V3<float>{dk32(z.x, b, o.x), dk32(z.y, b, o.y), dk32(z.z, b, o.z)};
+  }
+};
+template <> struct Dk<double> {
+  static __device__ __forceinline__ V3<double> row(const Dev& d, int c, double b, int ob) {
+    const V3<double> z = PV<double>::gather_z(d, c), o = PV<double>::gather_dir(d, c, ob);
+    return V3<double>{dk64(z.x, b, o.x), dk64(z.y, b, o.y), dk64(z.z, b, o.z)};
+  }
+};
+
+// ---- mat-vec item: 128 rows of SELL-32, U slots in flight per lane
+template <class HT, int U>
+__device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT beta, int ob, int nb) {
+  const int r = cta * 128 + threadIdx.x;
+  const int ch = r >> 5, lane = r & 31;
+  const int slots = d.chunk_slots[ch];
+  const long long base = d.chunk_ptr[ch];
+  const HT* __restrict__ val = reinterpret_cast<const HT*>(d.sell_val) + base * 9 + lane;
+  const int* __restrict__ colp = d.sell_col + base + lane;
+  HT ax = 0, ay = 0, az = 0;
+  int sl = 0;
+  for (; sl + U <= slots; sl += U) {
+    int c[U];
+    HT A[U][9];
+#pragma unroll
+    for (int u = 0; u < U; ++u) c[u] = colp[(sl + u) * 32];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) A[u][k] = val[(long long)(sl + u) * 288 + k * 32];
+    V3<HT> w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = Dk<HT>::row(d, c[u], beta, ob);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ax += A[u][0] * w[u].x + A[u][1] * w[u].y + A[u][2] * w[u].z;
+      ay += A[u][3] * w[u].x + A[u][4] * w[u].y + A[u][5] * w[u].z;
+      az += A[u][6] * w[u].x + A[u][7] * w[u].y + A[u][8] * w[u].z;
+    }
+  }
+  for (; sl < slots; ++sl) {
+    const int c = colp[sl * 32];
+    const HT* A = val + (long long)sl * 288;
+    const V3<HT> w = Dk<HT>::row(d, c, beta, ob);
+    ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
+    ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
+    az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
+  }
+  const V3<HT> own = Dk<HT>::row(d, r, beta, ob);
+  double out[1];
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    PV<float>::dbuf(d, nb)[r] = make_float4(own.x, own.y, own.z, 0.0f);
+    d.q4[r] = make_float4(ax, ay, az, 0.0f);
+    last = env_reduce<1, float>(d, e, 1, cta, own.x * ax + own.y * ay + own.z * az, nullptr, out);
+  } else {
+    st3(PV<double>::dbuf(d, nb), r, D3{own.x, own.y, own.z});
+    st3(d.q, r, D3{ax, ay, az});
+    last = env_reduce<1>(d, e, 1, cta, own.x * ax + own.y * ay + own.z * az, nullptr, out);
+  }
+  if (last) ENVS(d, e, S_DQ) = out[0];
+}
+
+// index of (p, q), p <= q, in the packed upper triangle of a 12x12 matrix
+__device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) / 2 + (q - p); }
+
+// ---- mat-vec item: contact terms of 8 active pairs of env e (group g)
+// q_c += H_k d_k per pair (pinned gel rows are eliminated: read as zero,
+// never written); sum_k d_k^T H_k d_k -> S_DQC.  H_k is stored as its
+// packed upper triangle, interleaved by warp of slots.  16 lanes per pair:
+// lane j < 12 owns coordinate j = 3 m + c (point m, component c); it forms
+// that component of the pair's direction, the group shares the 12 values by
+// shuffles, lane j computes row j of H_k d and scatters it: gel points
+// directly, body points as J^T (H_k d) on the body's 4 sub-rows (merged with
+// the warp's other pair when both touch the same single body).
+template <class HT>
+__device__ __forceinline__ void matvec_pairs(const Dev& d, int e, int g, HT beta, int ob) {
+  __shared__ double sdq[4];
+  const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
+  const int m = j / 3, c = j - 3 * m;
+  const int local = 8 * g + (threadIdx.x >> 4);
+  const bool live = local < env_active_pairs(d, e);
+  const int i = d.env_pair_off[e] + local;       // slot of this half-warp's pair
+  const int4 v = live ? d.act_v[i] : make_int4(0, 0, 0, 0);
+  const int cv = m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
+  int b_pt = -1, row = 0;
+  double xb[3] = {0, 0, 0};
+  HT dj = 0;
+  if (live && j < 12) {
+    row = d.cv_row[cv];
+    b_pt = d.cv_body[cv];
+    if (b_pt < 0) {
+      dj = (d.row_kind[row] == ROW_PINNED) ? (HT)0 : comp3(Dk<HT>::row(d, row, beta, ob), c);
+    } else {
+      const D3 x3 = ld3(d.cv_xbar, cv);
+      xb[0] = x3.x; xb[1] = x3.y; xb[2] = x3.z;
+      const HT d0 = comp3(Dk<HT>::row(d, row, beta, ob), c), d1 = comp3(Dk<HT>::row(d, row + 1, beta, ob), c),
+               d2 = comp3(Dk<HT>::row(d, row + 2, beta, ob), c), d3 = comp3(Dk<HT>::row(d, row + 3, beta, ob), c);
+      dj = (HT)((double)d0 + xb[0] * (double)d1 + xb[1] * (double)d2 + xb[2] * (double)d3);
+    }
+  }
+  HT oj = 0;
+  const HT* H = reinterpret_cast<const HT*>(d.pair_H) + (long long)(i >> 5) * 78 * 32 + (i & 31);
+  for (int q = 0; q < 12; ++q) {
+    const HT dq = __shfl_sync(0xffffffffu, dj, (lane & 16) + q);
+    if (live && j < 12) {
+      const int lo = min(j, q), hi = max(j, q);
+      oj += H[ut12(lo, hi) * 32] * dq;
+    }
+  }
+  // d_k^T H_k d_k of the CTA's pairs (all of env e): one atomic per CTA
+  double part = (live && j < 12) ? (double)(dj * oj) : 0.0;
+  part = warp_sum(part);
+  if (lane == 0) sdq[threadIdx.x >> 5] = part;
+  const double o = (double)oj;
+  if (live && j < 12 && b_pt < 0 && d.row_kind[row] != ROW_PINNED) atomicAdd(d.qc + 3 * row + c, o);
+  int bm[4];
+  for (int mm = 0; mm < 4; ++mm) bm[mm] = __shfl_sync(0xffffffffu, b_pt, (lane & 16) + 3 * mm);
+  int body = -2;
+  for (int mm = 0; mm < 4; ++mm)
+    if (bm[mm] >= 0) body = (body == -2 || body == bm[mm]) ? bm[mm] : -1;
+  if (!live) body = -2;
+  const int s4 = j / 3;
+  double jb = 0.0;
+  for (int mm = 0; mm < 4; ++mm) {
+    const int src = (lane & 16) + 3 * mm;
+    const double om = __shfl_sync(0xffffffffu, o, src + c);
+    const double x0 = __shfl_sync(0xffffffffu, xb[0], src);
+    const double x1 = __shfl_sync(0xffffffffu, xb[1], src);
+    const double x2 = __shfl_sync(0xffffffffu, xb[2], src);
+    const double xs = s4 == 0 ? 1.0 : (s4 == 1 ? x0 : (s4 == 2 ? x1 : x2));
+    if (body >= 0 && bm[mm] == body) jb += xs * om;
+  }
+  const int other = __shfl_xor_sync(0xffffffffu, body, 16);
+  const double jb_other = __shfl_xor_sync(0xffffffffu, jb, 16);
+  if (body >= 0 && j < 12) {
+    if (other == body) {
+      if (half == 0) atomicAdd(d.qc + 3 * d.body_row[body] + j, jb + jb_other);
+    } else {
+      atomicAdd(d.qc + 3 * d.body_row[body] + j, jb);
+    }
+  }
+  if (body == -1 && j < 12 && b_pt >= 0) {
+    const int br = d.body_row[b_pt];
+    atomicAdd(d.qc + 3 * br + c, o);
+    for (int s = 0; s < 3; ++s) atomicAdd(d.qc + 3 * (br + 1 + s) + c, xb[s] * o);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(&ENVS(d, e, S_DQC), sdq[0] + sdq[1] + sdq[2] + sdq[3]);
+  __syncthreads();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// PCG start: p = 0, r = -g, z = P^-1 r, d_{-1} = 0, beta = 0; r.z, r.r
+template <class HT>
+__global__ void k_pcg_init(Dev d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_ACTIVE)) return;
+  const uint8_t kr = d.row_kind[r];
+  const D3 rv = (kr == ROW_PINNED || kr == ROW_PAD) ? D3{0, 0, 0} : -1.0 * ld3(d.g, r);
+  st3(d.r, r, rv);
+  st3(d.p, r, D3{0, 0, 0});
+  __syncwarp();
+  const double rr = dot(rv, rv);
+  double out[2];
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    const float3 rf = round_row(rv);
+    const float4 z = apply_pc32(d, r, kr, rf);
+    d.z4[r] = z;
+    d.d4[r] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
+  } else {
+    const D3 z = apply_pc64(d, r, kr, rv);
+    PV<double>::set_z(d, r, z);
+    PV<double>::set_dir(d, r, 0, D3{0, 0, 0});
+    last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
+  }
+  if (last) {
+    ENVS(d, e, S_PBETA) = 0.0;
+    ENVS(d, e, S_RZ) = out[0];
+    ENVS(d, e, S_RR0) = out[1];
+    ENVS(d, e, S_RR) = out[1];
+    ENVS(d, e, S_DQC) = 0.0;
+    ENVI(d, e, I_PCGIT) = 0;
+    ENVI(d, e, I_PCG) = out[1] > 0.0 ? 1 : 0;
+  }
+}
+
+// work list of the envs whose I_PCG flag is set; iteration counter 0; sets
+// the solve loop's condition when launched inside a graph
+__global__ void k_pcg_begin(Dev d, cudaGraphConditionalHandle h, int use_cond) {
+  if (threadIdx.x == 0) {
+    d.pcg_ctl[C_ARRIVED] = 0;
+    d.pcg_ctl[C_ITER] = 0;
+  }
+  build_list(d);
+  if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, d.pcg_ctl[C_LIVE] > 0 ? 1u : 0u);
+}
+
+template <class HT, int U>
+__global__ void __launch_bounds__(128) k_pcg_matvec(Dev d) {
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_items = d.pcg_item_off[n_list];
+  const int nb = pcg_new_buf(d), ob = nb ^ 1;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int li = list_find(d.pcg_item_off, n_list, item);
+    const int e = d.pcg_list[li];
+    if (!ENVI(d, e, I_PCG)) continue;                // stopped; still listed
+    const int local = item - d.pcg_item_off[li];
+    const int n_cta = env_row_ctas(d, e);
+    const HT beta = (HT)ENVS(d, e, S_PBETA);
+    if (local < n_cta) matvec_rows<HT, U>(d, e, (d.env_row_off[e] >> 7) + local, beta, ob, nb);
+    else matvec_pairs<HT>(d, e, local - n_cta, beta, ob);
+  }
+}
+
+template <class HT>
+__global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalHandle h, int use_cond) {
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_items = d.pcg_row_off[n_list];
+  const int nb = pcg_new_buf(d);
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int li = list_find(d.pcg_row_off, n_list, item);
+    const int e = d.pcg_list[li];
+    if (!ENVI(d, e, I_PCG)) continue;
+    const int cta = (d.env_row_off[e] >> 7) + item - d.pcg_row_off[li];
+    const int r = cta * 128 + threadIdx.x;
+    const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
+    const double al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;
+    const uint8_t kr = d.row_kind[r];
+    // contact part of q on the rows this iteration's contact terms write
+    D3 qcv{0, 0, 0};
+    const bool touched = d.row_touch[r] == touch_tag(d, e);
+    if (touched) {
+      qcv = ld3(d.qc, r);
+      st3(d.qc, r, D3{0, 0, 0});
+    }
+    double out[2];
+    bool last;
+    if constexpr (sizeof(HT) == 4) {
+      const float4 dd = PV<float>::dbuf(d, nb)[r], qq = d.q4[r];
+      st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
+      const D3 rv = ld3(d.r, r) - al * (widen_row(qq) + qcv);
+      st3(d.r, r, rv);
+      __syncwarp();
+      const double rr = dot(rv, rv);
+      const float3 rf = round_row(rv);
+      const float4 z = apply_pc32(d, r, kr, rf);
+      d.z4[r] = z;
+      last = env_reduce<2, float>(d, e, 0, cta, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
+    } else {
+      st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r, nb));
+      const D3 rv = ld3(d.r, r) - al * (PV<double>::q(d, r) + qcv);
+      st3(d.r, r, rv);
+      __syncwarp();
+      const double rr = dot(rv, rv);
+      const D3 z = apply_pc64(d, r, kr, rv);
+      PV<double>::set_z(d, r, z);
+      last = env_reduce<2>(d, e, 0, cta, dot(rv, z), &rr, out);
+    }
+    if (last) {
+      const double rz_old = ENVS(d, e, S_RZ);
+      ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
+      ENVS(d, e, S_RZ) = out[0];
+      ENVS(d, e, S_RR) = out[1];
+      ENVS(d, e, S_DQC) = 0.0;
+      const int it = ++ENVI(d, e, I_PCGIT);
+      ENVI(d, e, I_PCGTOT) += 1;
+      const double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
+      if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) {
+        ENVI(d, e, I_PCG) = 0;
+        atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
+        atomicSub(d.pcg_ctl + C_LIVE, 1u);
+      }
+    }
+  }
+  // the grid's last CTA: next iteration, list upkeep, loop condition
+  __shared__ bool s_last;
+  __shared__ bool s_rebuild;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(d.pcg_ctl + C_ARRIVED, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    d.pcg_ctl[C_ARRIVED] = 0;
+    d.pcg_ctl[C_ITER] += 1;
+    const unsigned len = d.pcg_ctl[C_LEN];
+    const unsigned dead = d.pcg_ctl[C_DEAD];
+    const unsigned items = len ? (unsigned)d.pcg_item_off[len] : 0u;
+    s_rebuild = dead > 0 && 4u * dead >= items;
+  }
+  __syncthreads();
+  if (s_rebuild) build_list(d);
+  if (threadIdx.x == 0 && use_cond) {
+    const bool more = d.pcg_ctl[C_LIVE] > 0 && d.pcg_ctl[C_ITER] <= (unsigned)d.pcg_max + 1u;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
+// diagnostics: the direction v (FP64 rows staged in Dev::z) as z with
+// beta = 0 and d_{-1} = 0, so that one mat-vec item computes H v
+template <class HT>
+__global__ void k_debug_dir_from_rows(Dev d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  const D3 v = ld3(d.z, r);
+  PV<HT>::set_z(d, r, v);
+  PV<HT>::set_dir(d, r, 0, D3{0, 0, 0});
+  if (r == d.env_row_off[e]) {
+    ENVS(d, e, S_PBETA) = 0.0;
+    ENVS(d, e, S_DQC) = 0.0;
+  }
+}
+// q = A v + contact part back to FP64 rows in Dev::q; qc cleared
+template <class HT>
+__global__ void k_debug_q_to_rows(Dev d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = d.cta_env[r >> 7];
+  if (!ENVI(d, e, I_PCG)) return;
+  D3 q = PV<HT>::q(d, r);
+  if (d.row_touch[r] == touch_tag(d, e)) {
+    q = q + ld3(d.qc, r);
+    st3(d.qc, r, D3{0, 0, 0});
+  }
+  st3(d.q, r, q);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+int launch_pcg_init(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_pcg_init<float><<<d.n_rows / 128, 128, 0, s>>>(d);
+  else k_pcg_init<double><<<d.n_rows / 128, 128, 0, s>>>(d);
+  return 1;
+}
+int launch_pcg_begin(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  k_pcg_begin<<<1, 1024, 0, s>>>(d, h, use_cond);
+  return 1;
+}
+int launch_pcg_matvec(const Dev& d, cudaStream_t s) {
+  const int u = d.spmv_unroll ? d.spmv_unroll : (d.prec ? 4 : 2);
+  const int g = d.pcg_grid;
+  if (d.prec) {
+    if (u == 2) k_pcg_matvec<float, 2><<<g, 128, 0, s>>>(d);
+    else if (u == 8) k_pcg_matvec<float, 8><<<g, 128, 0, s>>>(d);
+    else k_pcg_matvec<float, 4><<<g, 128, 0, s>>>(d);
+  } else {
+    if (u == 4) k_pcg_matvec<double, 4><<<g, 128, 0, s>>>(d);
+    else if (u == 8) k_pcg_matvec<double, 8><<<g, 128, 0, s>>>(d);
+    else k_pcg_matvec<double, 2><<<g, 128, 0, s>>>(d);
+  }
+  return 1;
+}
+int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
+  if (d.prec) k_pcg_update<float><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond);
+  else k_pcg_update<double><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond);
+  return 1;
+}
+int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_debug_dir_from_rows<float><<<d.n_rows / 128, 128, 0, s>>>(d);
+  else k_debug_dir_from_rows<double><<<d.n_rows / 128, 128, 0, s>>>(d);
+  return 1;
+}
+int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_debug_q_to_rows<float><<<d.n_rows / 128, 128, 0, s>>>(d);
+  else k_debug_q_to_rows<double><<<d.n_rows / 128, 128, 0, s>>>(d);
+  return 1;
+}
+
+// resident CTAs per SM of the persistent PCG kernels (the smaller of the two)
+int pcg_ctas_per_sm(int prec, int unroll) {
+  int a = 0, b = 0;
+  const int u = unroll ? unroll : (prec ? 4 : 2);
+  if (prec) {
+    if (u == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<float, 2>, 128, 0);
+    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<float, 8>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<float, 4>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_update<float>, 128, 0);
+  } else {
+    if (u == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<double, 4>, 128, 0);
+    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<double, 8>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<double, 2>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_update<double>, 128, 0);
+  }
+  const int m = a < b ? a : b;
+  return m > 0 ? m : 1;
+}
+
+}  // namespace ipc

@@ -22,45 +22,6 @@ __device__ __forceinline__ bool is_gel(uint8_t k) { return k <= ROW_ATTACHED; }
 __device__ __forceinline__ bool is_body(uint8_t k) { return k == ROW_BODY || k == ROW_BODY_DRIVEN; }
 __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED || k == ROW_BODY_DRIVEN; }
 
-// Deterministic per-env reduction of CTA partials: every CTA of the env
-// writes `n` partials; the last CTA to arrive sums them in CTA order.
-// cta: the row CTA (row / 128), which is not blockIdx.x when the launch runs
-// a list of CTAs.  Returns true in thread 0 of the last CTA, with the sums
-// in out[0..n).
-// T0: type in which the first value (v0) is summed within the CTA (FP32 for
-// the FP32 products r.z and d.q of mixed mode); the other n - 1 values are
-// FP64, and the CTA partials are summed in FP64.
-// The row kernels that call it run 128-thread CTAs; FP64 values are summed
-// with block_sum128.
-template <int n, class T0 = double>
-__device__ bool env_reduce(const Dev& d, int e, int which, int cta, T0 v0, const double* rest /* n - 1 */,
-                           double* out) {
-  __shared__ double sh[128];
-  __shared__ float shf[32];
-  __shared__ bool last;
-  double part[n];
-  if constexpr (sizeof(T0) == 4) part[0] = (double)block_sum(v0, shf);
-  else part[0] = block_sum128(v0, sh);
-  for (int j = 1; j < n; ++j) part[j] = block_sum128(rest[j - 1], sh);
-  if (threadIdx.x == 0) {
-    for (int j = 0; j < n; ++j) d.cta_part[4 * cta + j] = part[j];
-    __threadfence();
-    unsigned int t = atomicAdd(&d.env_cnt[2 * e + which], 1u);
-    int ncta = (d.env_row_off[e + 1] - d.env_row_off[e]) >> 7;
-    last = (t == (unsigned)(ncta - 1));
-  }
-  __syncthreads();
-  if (!last) return false;
-  int c0 = d.env_row_off[e] >> 7, c1 = d.env_row_off[e + 1] >> 7;
-  for (int j = 0; j < n; ++j) {
-    double s = 0;
-    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) s += __ldcg(d.cta_part + 4 * c + j);
-    out[j] = block_sum(s, sh);
-  }
-  if (threadIdx.x == 0) d.env_cnt[2 * e + which] = 0;
-  return threadIdx.x == 0;
-}
-
 // ---------------------------------------------------------------------------
 // prediction: xn = x, xt = x + h v (body rows: y, ydot), multipliers zero
 // ---------------------------------------------------------------------------
@@ -350,224 +311,6 @@ __global__ void k_precond_body(Dev d) {
   for (int i = 0; i < 144; ++i) d.body_pc[144 * b + i] = Mi[i];
 }
 
-// z = P^{-1} r for row r.  Body rows read the 4 sub-rows of their body (all
-// of them sit in the same warp) and apply the body's 12x12 inverse in FP64.
-__device__ __forceinline__ D3 apply_pc_body(const Dev& d, int r) {
-  int b = d.row_body[r];
-  int br = d.body_row[b];
-  int kk = r - br;
-  const double* Pi = d.body_pc + 144 * (long long)b;
-  double o[3] = {0, 0, 0};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
-  return D3{o[0], o[1], o[2]};
-}
-
-// FP64 mode: gel rows apply the 6 stored entries of the symmetric 3x3 inverse
-__device__ __forceinline__ D3 apply_pc64(const Dev& d, int r, uint8_t kr, D3 x) {
-  if (is_body(kr)) return apply_pc_body(d, r);
-  if (kr == ROW_PAD) return D3{0, 0, 0};
-  const double* P = reinterpret_cast<const double*>(d.pc) + 6 * (long long)r;
-  const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
-  return D3{a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z};
-}
-
-// mixed mode: FP32 inverse applied to the FP32-rounded residual rf of the row
-__device__ __forceinline__ float4 apply_pc32(const Dev& d, int r, uint8_t kr, float3 x) {
-  if (is_body(kr)) {
-    const D3 z = apply_pc_body(d, r);
-    return make_float4(d2f_bits(z.x), d2f_bits(z.y), d2f_bits(z.z), 0.0f);
-  }
-  if (kr == ROW_PAD) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  const float* P = reinterpret_cast<const float*>(d.pc) + 6 * (long long)r;
-  const float a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
-  return make_float4(a * x.x + b * x.y + c * x.z, b * x.x + e * x.y + f * x.z, c * x.x + f * x.y + g * x.z, 0.0f);
-}
-
-__device__ __forceinline__ float3 round_row(D3 v) { return make_float3(d2f_bits(v.x), d2f_bits(v.y), d2f_bits(v.z)); }
-__device__ __forceinline__ D3 widen_row(float4 v) { return D3{f2d_bits(v.x), f2d_bits(v.y), f2d_bits(v.z)}; }
-
-// Mixed mode keeps FP64 for r, p and r.r only.  B300 issues FP64
-// instructions (conversions included) at a small fraction of its FP32 rate,
-// so the FP32 rows z, d, q are widened and r rounded on the integer pipe
-// (fpconv.cuh), and r.z and d.q are FP32 products summed in FP32 within a
-// CTA, in FP64 across CTAs.
-
-// PCG start: p = 0, r = -g, z = P^-1 r, d = z, beta = 0; rz, rr0
-template <class HT>
-__global__ void k_pcg_init(Dev d) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
-  uint8_t kr = d.row_kind[r];
-  D3 rv = (kr == ROW_PINNED || kr == ROW_PAD) ? D3{0, 0, 0} : -1.0 * ld3(d.g, r);
-  st3(d.r, r, rv);
-  st3(d.p, r, D3{0, 0, 0});
-  __syncwarp();
-  const double rr = dot(rv, rv);
-  double out[2];
-  bool last;
-  if constexpr (sizeof(HT) == 4) {
-    const float3 rf = round_row(rv);
-    const float4 z = apply_pc32(d, r, kr, rf);
-    d.z4[r] = z;
-    d.d4[r] = z;
-    last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
-  } else {
-    const D3 z = apply_pc64(d, r, kr, rv);
-    PV<double>::set_z(d, r, z);
-    PV<double>::set_dir(d, r, z);
-    last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
-  }
-  if (last) {
-    ENVS(d, e, S_PBETA) = 0.0;
-    ENVS(d, e, S_RZ) = out[0];
-    ENVS(d, e, S_RR0) = out[1];
-    ENVS(d, e, S_RR) = out[1];
-    ENVI(d, e, I_PCGIT) = 0;
-    ENVI(d, e, I_PCG) = out[1] > 0.0 ? 1 : 0;
-  }
-}
-
-// q = A d + qc (SELL-32, one row per thread, U slots in flight per lane),
-// qc cleared; d.q reduced per env -> alpha.
-// HT: matrix precision; the products are accumulated in HT slot by slot in
-// storage order.  FP64 mode: the contact part qc is added and d.q formed in
-// FP64; mixed: qc is rounded into the FP32 row q and d.q is an FP32 product.
-template <class HT, int U>
-__global__ void __launch_bounds__(128) k_spmv(Dev d, const int* __restrict__ cta_list) {
-  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_PCG)) return;
-  int ch = r >> 5, lane = r & 31;
-  int slots = d.chunk_slots[ch];
-  long long base = d.chunk_ptr[ch];
-  const HT* __restrict__ val = reinterpret_cast<const HT*>(d.sell_val) + base * 9 + lane;
-  const int* __restrict__ colp = d.sell_col + base + lane;
-  HT ax = 0, ay = 0, az = 0;
-  int sl = 0;
-  for (; sl + U <= slots; sl += U) {
-    int c[U];
-    HT A[U][9];
-#pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = colp[(sl + u) * 32];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int k = 0; k < 9; ++k) A[u][k] = val[(long long)(sl + u) * 288 + k * 32];
-    V3<HT> w[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = PV<HT>::gather(d, c[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      ax += A[u][0] * w[u].x + A[u][1] * w[u].y + A[u][2] * w[u].z;
-      ay += A[u][3] * w[u].x + A[u][4] * w[u].y + A[u][5] * w[u].z;
-      az += A[u][6] * w[u].x + A[u][7] * w[u].y + A[u][8] * w[u].z;
-    }
-  }
-  for (; sl < slots; ++sl) {
-    int c = colp[sl * 32];
-    const HT* A = val + (long long)sl * 288;
-    V3<HT> w = PV<HT>::gather(d, c);
-    ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
-    ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
-    az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
-  }
-  const D3 qc = ld3(d.qc, r);
-  st3(d.qc, r, D3{0, 0, 0});
-  double out[1];
-  bool last;
-  if constexpr (sizeof(HT) == 4) {
-    const float3 c3 = round_row(qc);
-    const float4 q = make_float4(ax + c3.x, ay + c3.y, az + c3.z, 0.0f);
-    d.q4[r] = q;
-    const float4 w = d.d4[r];
-    last = env_reduce<1, float>(d, e, 1, r >> 7, w.x * q.x + w.y * q.y + w.z * q.z, nullptr, out);
-  } else {
-    const D3 acc = qc + D3{(double)ax, (double)ay, (double)az};
-    PV<double>::set_q(d, r, acc);
-    last = env_reduce<1>(d, e, 1, r >> 7, dot(PV<double>::dir(d, r), acc), nullptr, out);
-  }
-  if (last) {
-    ENVS(d, e, S_DQ) = out[0];
-    ENVS(d, e, S_PALPHA) = (out[0] > 0.0) ? ENVS(d, e, S_RZ) / out[0] : 0.0;
-  }
-}
-
-// p += alpha d, r -= alpha q, z = P^-1 r; rz, rr reduced -> beta, stop test
-template <class HT>
-__global__ void k_pcg_update(Dev d, const int* __restrict__ cta_list) {
-  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_PCG)) return;
-  uint8_t kr = d.row_kind[r];
-  double al = ENVS(d, e, S_PALPHA);
-  double out[2];
-  bool last;
-  if constexpr (sizeof(HT) == 4) {
-    const float4 dd = d.d4[r], qq = d.q4[r];
-    st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
-    const D3 rv = ld3(d.r, r) - al * widen_row(qq);
-    st3(d.r, r, rv);
-    __syncwarp();
-    const double rr = dot(rv, rv);
-    const float3 rf = round_row(rv);
-    const float4 z = apply_pc32(d, r, kr, rf);
-    d.z4[r] = z;
-    last = env_reduce<2, float>(d, e, 0, r >> 7, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
-  } else {
-    st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r));
-    const D3 rv = ld3(d.r, r) - al * PV<double>::q(d, r);
-    st3(d.r, r, rv);
-    __syncwarp();
-    const double rr = dot(rv, rv);
-    const D3 z = apply_pc64(d, r, kr, rv);
-    PV<double>::set_z(d, r, z);
-    last = env_reduce<2>(d, e, 0, r >> 7, dot(rv, z), &rr, out);
-  }
-  if (last) {
-    double rz_old = ENVS(d, e, S_RZ);
-    ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
-    ENVS(d, e, S_RZ) = out[0];
-    ENVS(d, e, S_RR) = out[1];
-    int it = ++ENVI(d, e, I_PCGIT);
-    ENVI(d, e, I_PCGTOT) += 1;
-    double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
-    if (out[1] <= tol2 || it >= d.pcg_max || !(ENVS(d, e, S_DQ) > 0.0)) ENVI(d, e, I_PCG) = 0;
-  }
-}
-
-// d = z + beta d (in HT)
-template <class HT>
-__global__ void k_pcg_dir(Dev d, const int* __restrict__ cta_list) {
-  int r = (cta_list ? cta_list[blockIdx.x] : (int)blockIdx.x) * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_PCG)) return;
-  if constexpr (sizeof(HT) == 4) {
-    const float be = d2f_bits(ENVS(d, e, S_PBETA));
-    const float4 z = d.z4[r], dd = d.d4[r];
-    d.d4[r] = make_float4(z.x + be * dd.x, z.y + be * dd.y, z.z + be * dd.z, 0.0f);
-  } else {
-    PV<double>::set_dir(d, r, PV<double>::z(d, r) + ENVS(d, e, S_PBETA) * PV<double>::dir(d, r));
-  }
-}
-
-// diagnostics: the direction from FP64 rows held in d.z; q back to FP64 rows
-template <class HT>
-__global__ void k_debug_dir_from_rows(Dev d) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_PCG)) return;
-  PV<HT>::set_dir(d, r, ld3(d.z, r));
-}
-template <class HT>
-__global__ void k_debug_q_to_rows(Dev d) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_PCG)) return;
-  st3(d.q, r, PV<HT>::q(d, r));
-}
-
 // ---------------------------------------------------------------------------
 // Newton bookkeeping
 // ---------------------------------------------------------------------------
@@ -762,7 +505,7 @@ __global__ void k_clear_accept(Dev d) {
   if (e < d.n_envs) ENVI(d, e, I_ACCEPT) = 0;
 }
 
-// velocities (P:516 / App. A.2): v = (x - x^n) / h; overflowed envs restored
+// velocities (App. A.2, backward Euler): v = (x - x^n) / h; overflowed envs restored
 __global__ void k_finalize_rows(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
@@ -811,6 +554,8 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVS(d, e, S_PNORM) = 0.0;
     ENVS(d, e, S_CRES) = 0.0;
     ENVI(d, e, I_NEWTON) += 1;
+    ENVI(d, e, I_GEN) += 1;
+    ENVI(d, e, I_NACT) = 0;
   } else if (what == 2) {
     ENVI(d, e, I_NPAIRS) = 0;
   } else if (what == 3) {
@@ -892,47 +637,6 @@ int launch_precond(const Dev& d, cudaStream_t s) {
   if (!d.n_bodies) return 1;
   k_precond_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
   return 2;
-}
-int launch_pcg_init(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_pcg_init<float><<<ROWGRID>>>(d);
-  else k_pcg_init<double><<<ROWGRID>>>(d);
-  return 1;
-}
-// n_cta < 0: every row CTA; else the first n_cta entries of Dev::cta_list
-#define LISTGRID (n_cta < 0 ? d.n_rows / 128 : n_cta), 128, 0, s
-#define LISTARG (n_cta < 0 ? nullptr : d.cta_list)
-int launch_spmv(const Dev& d, cudaStream_t s, int n_cta) {
-  const int u = d.spmv_unroll ? d.spmv_unroll : (d.prec ? 4 : 2);
-  if (d.prec) {
-    if (u == 2) k_spmv<float, 2><<<LISTGRID>>>(d, LISTARG);
-    else if (u == 8) k_spmv<float, 8><<<LISTGRID>>>(d, LISTARG);
-    else k_spmv<float, 4><<<LISTGRID>>>(d, LISTARG);
-  } else {
-    if (u == 4) k_spmv<double, 4><<<LISTGRID>>>(d, LISTARG);
-    else if (u == 8) k_spmv<double, 8><<<LISTGRID>>>(d, LISTARG);
-    else k_spmv<double, 2><<<LISTGRID>>>(d, LISTARG);
-  }
-  return 1;
-}
-int launch_pcg_update(const Dev& d, cudaStream_t s, int n_cta) {
-  if (d.prec) k_pcg_update<float><<<LISTGRID>>>(d, LISTARG);
-  else k_pcg_update<double><<<LISTGRID>>>(d, LISTARG);
-  return 1;
-}
-int launch_pcg_dir(const Dev& d, cudaStream_t s, int n_cta) {
-  if (d.prec) k_pcg_dir<float><<<LISTGRID>>>(d, LISTARG);
-  else k_pcg_dir<double><<<LISTGRID>>>(d, LISTARG);
-  return 1;
-}
-int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_debug_dir_from_rows<float><<<ROWGRID>>>(d);
-  else k_debug_dir_from_rows<double><<<ROWGRID>>>(d);
-  return 1;
-}
-int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_debug_q_to_rows<float><<<ROWGRID>>>(d);
-  else k_debug_q_to_rows<double><<<ROWGRID>>>(d);
-  return 1;
 }
 int launch_newton_check(const Dev& d, cudaStream_t s) {
   k_newton_rows<<<ROWGRID>>>(d);

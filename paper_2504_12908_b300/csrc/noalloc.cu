@@ -63,11 +63,23 @@ extern "C" ipc_status ipc_read_gel_surface_all_noalloc(ipc_ctx* ctx, double* out
                " rows; use ipc_read_gel_surface_all";
     return IPC_EINVAL;
   }
+  // the staging address belongs to the device that is current when it is
+  // looked up; it must be the context's device (where x and the stream live)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess) {
     ctx->err = std::string("ipc_read_gel_surface_all_noalloc: cudaGetDevice: ") + cudaGetErrorString(e);
     return IPC_ECUDA;
+  }
+  if (dev != ctx->device) {
+    ctx->err = "ipc_read_gel_surface_all_noalloc: the current device (" + std::to_string(dev) +
+               ") is not the context's device (" + std::to_string(ctx->device) + "); make it current first";
+    return IPC_EINVAL;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    ctx->err = "ipc_read_gel_surface_all_noalloc: device ordinal " + std::to_string(dev) +
+               " is beyond the " + std::to_string(kMaxDevices) + " devices this entry point supports";
+    return IPC_EINVAL;
   }
   double* stage = nullptr;
   e = stage_ptr(dev, &stage);

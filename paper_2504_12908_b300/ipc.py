@@ -47,8 +47,8 @@ class ipc_sensor(C.Structure):
 
 
 class ipc_tuning(C.Structure):
-    _fields_ = [("spmv_unroll", C.c_int), ("pair_ctas_per_sm", C.c_int), ("spmv_us", C.c_float * 3),
-                ("pair_us", C.c_float * 4)]
+    _fields_ = [("spmv_unroll", C.c_int), ("pcg_ctas_per_sm", C.c_int), ("spmv_us", C.c_float * 3),
+                ("grid_ctas_per_sm", C.c_int * 3), ("grid_us", C.c_float * 3)]
 
 
 class ipc_step_stats(C.Structure):
@@ -89,6 +89,7 @@ def lib():
             "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "ipc_env_stats": (i32, [vp, i32, _ip]),
             "ipc_set_graph_mode": (i32, [vp, i32]),
             "ipc_autotune": (i32, [vp, i32, C.POINTER(ipc_tuning)]),
             "ipc_gel_vertex_rows": (i32, [vp, i32, i32, _ip, _ip]),
@@ -122,7 +123,7 @@ def lib():
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
-            "ipc_read_gel_surface_all_noalloc", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
+            "ipc_read_gel_surface_all_noalloc", "ipc_env_stats", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
@@ -324,6 +325,14 @@ class Envs:
         self._check(lib().ipc_step(self._ctx, _ptr(ids, _ip), n, _ptr(status, _ip), C.byref(stats)), "ipc_step")
         return status, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
 
+    ENV_STATS = ("status", "newton", "al", "pcg", "ls_trials", "ccd_limited", "accd_max", "pairs", "accd_iters")
+
+    def env_stats(self, env: int) -> dict:
+        """Counters of the last step that included `env` (ipc_env_stats)."""
+        out = np.zeros(len(self.ENV_STATS), dtype=np.int32)
+        self._check(lib().ipc_env_stats(self._ctx, env, _ptr(out, _ip)), "ipc_env_stats")
+        return dict(zip(self.ENV_STATS, (int(v) for v in out)))
+
     def read_gel_surface(self, env: int) -> np.ndarray:
         n = self.sizes[env][2]
         out = np.zeros((n, 3))
@@ -331,10 +340,20 @@ class Envs:
         self._check(lib().ipc_read_gel_surface(self._ctx, env, _ptr(out, _dp), n, C.byref(w)), "ipc_read_gel_surface")
         return out
 
+    @staticmethod
+    def _check_out_rows(out: np.ndarray, what: str):
+        """A caller's output array must be C-contiguous float64 [rows][3]: the
+        library writes 3 doubles per row up to out.shape[0] rows."""
+        if not isinstance(out, np.ndarray) or out.dtype != np.float64 or out.ndim != 2 or out.shape[1] != 3 \
+                or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{what}: out must be a C-contiguous float64 array of shape (rows, 3), got "
+                             f"{getattr(out, 'dtype', type(out))} {getattr(out, 'shape', '')}")
+
     def read_gel_surface_all(self, out: Optional[np.ndarray] = None) -> np.ndarray:
         tot = sum(s[2] for s in self.sizes)
         if out is None:
             out = np.zeros((tot, 3))
+        self._check_out_rows(out, "read_gel_surface_all")
         w = C.c_size_t()
         self._check(lib().ipc_read_gel_surface_all(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
                     "ipc_read_gel_surface_all")
@@ -347,6 +366,7 @@ class Envs:
         tot = sum(s[2] for s in self.sizes)
         if out is None:
             out = np.zeros((tot, 3))
+        self._check_out_rows(out, "read_gel_surface_all_noalloc")
         w = C.c_size_t()
         self._check(lib().ipc_read_gel_surface_all_noalloc(self._ctx, _ptr(out, _dp), out.shape[0], C.byref(w)),
                     "ipc_read_gel_surface_all_noalloc")
@@ -434,13 +454,14 @@ class Envs:
         return pos, flow
 
     def autotune(self, reps: int = 10) -> dict:
-        """Pick the SpMV unroll and the contact mat-vec grid by timing them
-        on this batch's current system (call between steps)."""
+        """Pick the PCG mat-vec's slots in flight per lane and the persistent
+        PCG grid by timing them on this batch's current system (call between
+        steps)."""
         t = ipc_tuning()
         self._check(lib().ipc_autotune(self._ctx, int(reps), C.byref(t)), "ipc_autotune")
-        return {"spmv_unroll": t.spmv_unroll, "pair_ctas_per_sm": t.pair_ctas_per_sm,
+        return {"spmv_unroll": t.spmv_unroll, "pcg_ctas_per_sm": t.pcg_ctas_per_sm,
                 "spmv_us": {u: round(float(t.spmv_us[k]), 2) for k, u in enumerate((2, 4, 8))},
-                "pair_us": {c: round(float(t.pair_us[k]), 2) for k, c in enumerate((2, 4, 8, 16))}}
+                "grid_us": {int(t.grid_ctas_per_sm[k]): round(float(t.grid_us[k]), 2) for k in range(3)}}
 
     def set_graph_mode(self, on: bool = True):
         """Replay the PCG inner loop as a captured CUDA graph (needs a

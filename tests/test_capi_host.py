@@ -91,3 +91,14 @@ def test_rejects_out_of_range_index(L):
     bad.gel_tets[3, 2] = sc.n_verts + 5
     with pytest.raises(ipc.IpcError):
         ipc.workspace_bytes([bad], scenes.SolverParams())
+
+
+def test_read_back_rejects_output_arrays_of_the_wrong_layout():
+    # the library writes 3 doubles per row up to out.shape[0] rows: anything
+    # but a C-contiguous float64 (rows, 3) array is refused before the call
+    ok = np.zeros((5, 3))
+    ipc.Envs._check_out_rows(ok, "t")
+    for bad in (np.zeros((5, 3), np.float32), np.zeros(15), np.zeros((5, 4)), np.zeros((3, 5)).T,
+                np.zeros((10, 3))[::2]):
+        with pytest.raises(ValueError):
+            ipc.Envs._check_out_rows(bad, "t")

@@ -610,8 +610,8 @@ def test_graph_mode_matches_plain_launches(precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotune_picks_valid_shapes_and_keeps_results(precision):
-    """ipc_autotune times the SpMV unrolls and contact mat-vec grids on the
-    ctx's own system between steps; later steps match a ctx that was not
+    """ipc_autotune times the PCG mat-vec's unrolls and persistent grids on
+    the ctx's own system between steps; later steps match a ctx that was not
     tuned (to rounding: atomics order)."""
     scs = [scenes.config2(e) for e in range(3)]
     prm = scenes.SolverParams().parity() if precision == 0 else scenes.SolverParams()
@@ -630,8 +630,8 @@ def test_autotune_picks_valid_shapes_and_keeps_results(precision):
         assert np.all(sa == 0) and np.all(sb == 0)
         if step == 0:
             tun = a.autotune(reps=3)
-            assert tun["spmv_unroll"] in (2, 4, 8) and tun["pair_ctas_per_sm"] in (2, 4, 8, 16)
-            assert all(v > 0 for v in tun["spmv_us"].values())
+            assert tun["spmv_unroll"] in (2, 4, 8) and tun["pcg_ctas_per_sm"] in tun["grid_us"]
+            assert all(v > 0 for v in tun["spmv_us"].values()) and all(v > 0 for v in tun["grid_us"].values())
         for e in range(3):
             xa, xb = a.get_state(e)[0], b.get_state(e)[0]
             diag = np.linalg.norm(xa.max(0) - xa.min(0))

@@ -55,3 +55,35 @@ def test_noalloc_read_back_matches_workspace_read_back():
     part = genv.read_gel_surface_all_noalloc(np.zeros((7, 3)))
     assert np.array_equal(part, ref[:7])
     genv.close()
+
+
+def test_noalloc_capacity_zero_reports_count_and_writes_nothing():
+    import ctypes as C
+    scs = [scenes.config0(), scenes.config0()]
+    genv = ipc.Envs([s.scene for s in scs], scenes.SolverParams())
+    n_all = sum(s_[2] for s_ in genv.sizes)
+    out = np.full((4, 3), np.nan)
+    w = C.c_size_t(12345)
+    st = ipc.lib().ipc_read_gel_surface_all_noalloc(genv._ctx, out.ctypes.data_as(C.POINTER(C.c_double)), 0,
+                                                     C.byref(w))
+    assert st == ipc.IPC_OK
+    assert w.value == n_all
+    assert np.all(np.isnan(out))
+    genv.close()
+
+
+def test_noalloc_rejects_more_rows_than_its_fixed_array():
+    # 14 unpinned two-layer 100 x 100 pads: every vertex is on the coated
+    # surface, 14 x 20000 = 280000 rows > 262144
+    sc = scenes.free_fall_scene(nx=100, ny=100, nz=2, with_body=False).scene
+    genv = ipc.Envs([sc] * 14, scenes.SolverParams())
+    n_all = sum(s_[2] for s_ in genv.sizes)
+    assert n_all == 280000
+    with pytest.raises(ipc.IpcError) as ei:
+        genv.read_gel_surface_all_noalloc()
+    assert ei.value.status == ipc.IPC_EINVAL
+    assert "262144" in str(ei.value) and "exceed" in str(ei.value)
+    # the workspace read-back has no such limit
+    ref = genv.read_gel_surface_all()
+    assert ref.shape == (n_all, 3) and np.all(np.isfinite(ref))
+    genv.close()
