@@ -97,6 +97,12 @@ typedef struct {
   double friction_mu;     /* lagged IPC friction coefficient mu (App. A.3,
                              D_k = mu lambda_k f0(|u_k|)); 0 = frictionless  */
   double friction_eps_v;  /* static / dynamic threshold eps_v, m/s (1e-3)   */
+  int newton_abs_after;   /* eigenvalue filter of the projected element,
+                             pair and body Hessians: Newton iterations 1..n
+                             of a step set negative eigenvalues to zero,
+                             later ones replace them by their absolute
+                             values (default 1000000: always zero; 0:
+                             always absolute values)                        */
 } ipc_params;
 
 /* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
@@ -142,6 +148,10 @@ typedef struct {
   long long accd_iters;       /* ACCD advancement iterations, all pairs        */
   int accd_iters_max;         /* most ACCD iterations taken by one pair        */
   double ms_total;      /* wall time of the call (host clock), ms            */
+  long long pair_evals;       /* static candidate pairs evaluated (barrier terms),
+                                 summed over Newton iterations and envs      */
+  long long swept_pairs;      /* swept candidate pairs of the line searches
+                                 (ACCD and line-search energies), summed     */
 } ipc_step_stats;
 
 void ipc_default_params(ipc_params* prm);
@@ -164,20 +174,27 @@ ipc_status ipc_destroy(ipc_ctx* ctx);
 /* Last error message of this ctx (empty string if none). */
 const char* ipc_last_error(const ipc_ctx* ctx);
 
-/* Run each PCG solve (the block-Jacobi PCG of every Newton iteration,
- * named as the method's main cost in the paper's Limitations) as one CUDA
- * graph: a work-list kernel, then a WHILE node over one iteration (the
- * mat-vec, the friction mat-vec when friction is on, the update) whose
- * condition the update kernel sets on the device, so the solve runs
- * without host round trips.  Captured on the ctx stream at the first solve
- * and replayed after that.  Results are the same as with plain launches,
- * which poll an on-device count of iterating envs every 16 iterations.
- * on = 0 (default) launches kernel by kernel.  The ctx stream must support
- * capture (a created stream, not the legacy default stream); otherwise
- * ipc_step returns IPC_ECUDA with the reason in ipc_last_error.  While
- * per-kernel profiling is on, plain launches are used so that every kernel
- * is timed. */
-ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on);
+/* CUDA-graph execution (a property of this library; results are the same
+ * as with plain launches):
+ *   mode 0 (default): kernel by kernel; the host polls the device's loop
+ *     state (PCG every 16 iterations, Newton and line search every
+ *     iteration).
+ *   mode 1: each PCG solve (the block-Jacobi PCG of every Newton iteration,
+ *     named as the method's main cost in the paper's Limitations) is one
+ *     graph: a work-list kernel, then a WHILE node over one iteration whose
+ *     condition the update kernel sets on the device.
+ *   mode 2: the whole step is one graph: nested WHILE / IF nodes for the
+ *     Newton loop, the PCG solve, the line-search gate and the line-search
+ *     trials, all conditions set on the device and every loop bounded by
+ *     its cap (newton_max, pcg_max, ls_max); ipc_step then needs no host
+ *     round trip (see ipc_step).
+ * Graphs are captured on the ctx stream at their first use and replayed
+ * after that; ipc_autotune and a mode change drop them.  The ctx stream must
+ * support capture (a created stream, not the legacy default stream);
+ * otherwise ipc_step returns IPC_ECUDA with the reason in ipc_last_error.
+ * While per-kernel profiling is on, plain launches are used so that every
+ * kernel is timed.  IPC_EINVAL for another mode. */
+ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int mode);
 
 /* Launch shapes chosen by ipc_autotune and the timings behind the choice. */
 typedef struct {
@@ -210,8 +227,10 @@ ipc_status ipc_body_com(const ipc_ctx* ctx, int env, int body, double com[3]);
 /* State of one env.  x, v: [n_verts][3]; y, ydot: [n_bodies][12].  Any
  * pointer may be NULL to leave that part unchanged.  set_state synchronises
  * the stream and rejects non-finite values (IPC_EINVAL), inverted tets
- * (IPC_EINVERTED) and touching or interpenetrating surfaces
- * (IPC_EINTERSECT, min distance <= 0), leaving the previous state in place.
+ * (IPC_EINVERTED) and touching or interpenetrating surfaces (IPC_EINTERSECT:
+ * a candidate pair at distance <= 0, or an edge of one contact object
+ * passing through a triangle of another), leaving the previous state in
+ * place (Sec. 1: the simulator keeps every state intersection-free).
  * A state read with get_state and set again (in this or another ctx built
  * from the same scene) continues as the original would (checkpoint /
  * resume). */
@@ -219,6 +238,17 @@ ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v
                          const double* y, const double* ydot);
 ipc_status ipc_get_state(ipc_ctx* ctx, int env, double* x, double* v,
                          double* y, double* ydot);
+
+/* Replace env `env` by a new scene of the same topology (equal mesh sizes
+ * and connectivity, pinned / attached / driven sets and body vertex counts;
+ * material, rest geometry, body shapes and masses may differ) and set it to
+ * that scene's rest state with zero velocities (as ipc_create_envs does).
+ * This lets a caller reuse an env slot of a resident context for a new
+ * request (continuous batching) without creating a context.  Copies only
+ * the env's own value tables; synchronises the ctx stream.  IPC_EINVAL
+ * (message in ipc_last_error) when the topology differs or the scene is
+ * invalid.  Not in the paper: a property of this library. */
+ipc_status ipc_reset_env(ipc_ctx* ctx, int env, const ipc_scene_desc* scene);
 
 /* Kinematic targets s^y of the driven bodies of one env for the next step,
  * [n_bodies][12] (rows of free bodies are ignored).  Gel vertices attached
@@ -235,11 +265,22 @@ ipc_status ipc_set_targets_all(ipc_ctx* ctx, const double* y_targets);
  * copy on the ctx stream; no host synchronisation). */
 ipc_status ipc_set_targets_all_device(ipc_ctx* ctx, const double* dev_y_targets);
 
-/* Advance the listed envs by one time step (env_ids NULL = all envs).
- * per_env_status (may be NULL) receives n statuses.  Synchronises the
- * stream before returning. */
+/* Advance the listed envs by one time step (env_ids NULL = all envs; the
+ * argmin of Eq. unified_ipc_variational by projected Newton, App. A.2).
+ * per_env_status (may be NULL) receives n statuses, stats the counters.
+ * With either of them non-NULL the call synchronises the stream and fills
+ * them.  With both NULL in graph mode 2 (ipc_set_graph_mode) the call only
+ * enqueues the step's graph on the ctx stream and returns: the step runs
+ * on the device without host round trips, and ipc_step_results reads its
+ * results later.  Other modes synchronise inside the Newton loop. */
 ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n,
                     int32_t* per_env_status, ipc_step_stats* stats);
+
+/* Results of the last ipc_step (the statuses of its envs, in its order,
+ * and its counters): synchronises the ctx stream.  Either pointer may be
+ * NULL.  A second call after the results were read returns zeroed stats
+ * and leaves per_env_status untouched. */
+ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stats* stats);
 
 /* Per-env counters of the last ipc_step that included `env` (host only; the
  * values were read back at the end of that step).  out[IPC_ENV_STATS]:
@@ -247,9 +288,10 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n,
  *   iterations (all Newton iterations), 4 line-search energy trials,
  *   5 line searches that started below alpha = 1 (CCD-limited), 6 most ACCD
  *   iterations one pair took, 7 candidate pairs in the last list,
- *   8 ACCD iterations over all pairs.
+ *   8 ACCD iterations over all pairs, 9 static candidate pairs evaluated
+ *   (all Newton iterations), 10 swept candidate pairs (all line searches).
  * Diagnostics of this library (the paper reports no iteration counts). */
-#define IPC_ENV_STATS 9
+#define IPC_ENV_STATS 11
 ipc_status ipc_env_stats(const ipc_ctx* ctx, int env, int32_t* out);
 
 /* Coated-surface vertex positions of one env's gel (Sec. 4.1: the surface
@@ -386,16 +428,18 @@ ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks,
 
 /* Neo-Hookean tet (App. A.1): x [n][4][3], Dm_inv [n][3][3] (row-major),
  * vol [n]; outputs (NULL to skip) energy [n] = vol Psi (+inf if J <= 0),
- * grad [n][12], hess [n][12][12] = vol B^T Pi(dP/dF) B, PSD-projected when
- * project != 0 (Pi = eigen-clamp of d2Psi/dF2), the exact Hessian when 0. */
+ * grad [n][12], hess [n][12][12] = vol B^T Pi(dP/dF) B: project = 1: Pi
+ * sets the negative eigenvalues of d2Psi/dF2 to zero, project = 2: Pi
+ * replaces them by their absolute values, project = 0: the exact Hessian. */
 ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol,
                      double mu, double lam, double* energy, double* grad, double* hess,
                      int project, void* stream);
 
 /* Weighted barrier of pairs (App. A.3): X [n][4][3], is_ee [n] (0/1),
  * weight [n] (multiplies c(x) b(d)), eps_x [n] (mollifier threshold, EE
- * only); energy [n], grad [n][12], hess [n][12][12] (PSD-projected when
- * project != 0, the exact Hessian when 0). */
+ * only); energy [n], grad [n][12], hess [n][12][12] (project = 1: negative
+ * eigenvalues set to zero, 2: replaced by their absolute values, 0: the
+ * exact Hessian). */
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight,
                          const double* eps_x, double dhat, double* energy, double* grad,
                          double* hess, int project, void* stream);

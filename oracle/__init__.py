@@ -16,8 +16,10 @@ What it computes (Taccel, arXiv 2504.12908):
   a stiff orthogonality term (Sec. 3.3, Eq. unified_ipc),
 * the kinematic constraints ``S x = s`` of Sec. 3.4 (Eq. unified_ipc_AL),
   handled with an augmented Lagrangian,
-* minimised by projected Newton: per-element Hessians clamped to PSD with
-  ``numpy.linalg.eigh``, a sparse direct solve instead of PCG, brute-force
+* minimised by projected Newton: per-element Hessians made PSD with
+  ``numpy.linalg.eigh`` (negative eigenvalues clamped to zero; optionally
+  replaced by their absolute values once a step's Newton iterations reach
+  ``newton_abs_after``), a sparse direct solve instead of PCG, brute-force
   all-pairs contact candidates, additive CCD and backtracking line search.
 
 Readings of the paper where it is silent or garbled are listed in the design

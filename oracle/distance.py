@@ -242,7 +242,9 @@ def pair_barrier(X12, is_ee, weight, eps_x, dhat, order=2, project=True):
 
     X12 (n, 4, 3); weight (n,) = dt^2 kappa A_k; eps_x (n,) mollifier
     thresholds (ignored for PT).  Returns E (n,), grad (n, 12), hess (n,12,12)
-    with the Hessian clamped to PSD when `project`.
+    with the Hessian filtered to PSD per `project` (False: raw; True /
+    "clamp": negative eigenvalues set to zero; "abs": replaced by their
+    absolute values).
     """
     n = X12.shape[0]
     kind, idx = pair_kinds(X12, is_ee)
@@ -288,9 +290,8 @@ def pair_barrier(X12, is_ee, weight, eps_x, dhat, order=2, project=True):
         Hk = (c[:, None, None] * hb + np.einsum("ni,nj->nij", gb, gc) + np.einsum("ni,nj->nij", gc, gb)
               + b0[:, None, None] * hc)
         Hk = w[:, None, None] * Hk
-        if project:
-            from .energy import psd_clamp
-            Hk = psd_clamp(Hk)
+        from .energy import psd_filter
+        Hk = psd_filter(Hk, project)
         H[a] = Hk
     return E, G, H
 

@@ -10,8 +10,11 @@ First Piola-Kirchhoff stress and its derivative (textbook):
     dP_ij/dF_kl = mu d_ik d_jl + (mu - lam ln J) G_il G_kj + lam G_ij G_kl,
     G = F^{-T}.
 The projected element Hessian is V_e B^T Pi(dP/dF) B where B = dF/dx (9x12)
-and Pi clamps negative eigenvalues of the symmetric 9x9 dP/dF to zero
-(numpy.linalg.eigh).
+and Pi filters the negative eigenvalues of the symmetric 9x9 dP/dF
+(numpy.linalg.eigh): set to zero ("clamp"), or replaced by their absolute
+values ("abs"); both give a PSD matrix.  The paper does not say how its
+Hessians are made PSD: the step clamps by default (oracle/step.py,
+newton_filter).
 
 Affine body (Sec. 3.3, Eq. unified_ipc): inertia 1/2 (y - ytilde)^T M^y
 (y - ytilde), gravity -m g.p, and the stiffness term on A read as the
@@ -84,6 +87,22 @@ def psd_clamp(H: np.ndarray) -> np.ndarray:
     return np.einsum("...ik,...k,...jk->...ij", V, np.maximum(w, 0.0), V)
 
 
+def psd_abs(H: np.ndarray) -> np.ndarray:
+    """Symmetric PSD projection V |L| V^T (batched)."""
+    Hs = 0.5 * (H + np.swapaxes(H, -1, -2))
+    w, V = np.linalg.eigh(Hs)
+    return np.einsum("...ik,...k,...jk->...ij", V, np.abs(w), V)
+
+
+def psd_filter(H: np.ndarray, project) -> np.ndarray:
+    """project: False / None = raw; True or "clamp" = psd_clamp; "abs" = psd_abs."""
+    if not project:
+        return H
+    if project == "abs":
+        return psd_abs(H)
+    return psd_clamp(H)
+
+
 def tet_energy(x4, Dm_inv, vol, mu, lam):
     """Per-tet V_e Psi(F) (T,), +inf where inverted."""
     return vol * psi(deformation_gradient(x4, Dm_inv), mu, lam)
@@ -98,11 +117,10 @@ def tet_grad(x4, Dm_inv, vol, mu, lam):
 
 
 def tet_hess(x4, Dm_inv, vol, mu, lam, project=True):
-    """(T, 12, 12) element Hessian, dP/dF clamped to PSD when `project`."""
+    """(T, 12, 12) element Hessian, dP/dF filtered to PSD per `project`
+    (False: raw; True / "clamp"; "abs")."""
     F = deformation_gradient(x4, Dm_inv)
-    A = dPdF(F, mu, lam)
-    if project:
-        A = psd_clamp(A)
+    A = psd_filter(dPdF(F, mu, lam), project)
     B = dF_dx(Dm_inv)
     return vol[:, None, None] * np.einsum("tkm,tkl,tln->tmn", B, A, B)
 

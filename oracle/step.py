@@ -24,6 +24,9 @@ Readings (the paper is silent or garbled on these):
     does not increase and no tet is inverted (cap ls_max halvings).
   * Newton stops when |p|_inf / h < tol, p measured as full-space
     vertex displacements (gel p and J_j p_y on body vertices).
+  * the Hessians are made PSD by clamping negative eigenvalues to zero
+    (optionally, from Newton iteration newton_abs_after on, by replacing
+    them with their absolute values: newton_filter).
   * the linear solve is a sparse direct solve here (the GPU uses PCG).
 """
 from __future__ import annotations
@@ -196,7 +199,9 @@ class OracleEnv:
         return E
 
     def grad_hess(self, x, y, ctx, pairs, project=True):
-        """Full gradient (ndof,) and Hessian (sparse ndof x ndof)."""
+        """Full gradient (ndof,) and Hessian (sparse ndof x ndof); project:
+        the eigenvalue filter of the element, body and pair Hessians (False:
+        raw, True / "clamp", "abs")."""
         prm, h = self.prm, self.prm.dt
         N = self.N
         m = self.gel.mass
@@ -226,7 +231,7 @@ class OracleEnv:
             gb[3:] += h * h * ks * br.vol * en.orth_grad(y[b, 3:])
             Hb = br.My.copy()
             Ho = h * h * ks * br.vol * en.orth_hess(y[b, 3:])
-            Hb[3:, 3:] += en.psd_clamp(Ho) if project else Ho
+            Hb[3:, 3:] += en.psd_filter(Ho, project)
             if b in self.driven_bodies:
                 r = y[b] - ctx["s_y"][b]
                 gb += ka * br.My @ r - br.My @ ctx["lam_y"][b]
@@ -343,6 +348,17 @@ class OracleEnv:
         pt, ee = candidates(self.sd, Xc, self.prm.dhat, self.excluded)
         return pt, ee
 
+    def newton_filter(self, it: int) -> str:
+        """Eigenvalue filter of Newton iteration `it` (0-based) of a step.
+        The paper does not say how its Hessians are made PSD.  Default
+        reading: clamp negative eigenvalues to zero.  Option: from iteration
+        newton_abs_after on, replace them by their absolute values instead
+        (an iterate near a saddle of the energy moves away from it faster;
+        measured on the press workload it did not make the slow steps
+        converge sooner once the linear solves are inexact, so it is off by
+        default)."""
+        return "abs" if it >= getattr(self.prm, "newton_abs_after", 1000000) else "clamp"
+
     def step(self, x_n, v_n, y_n, ydot_n, s_y=None, x_start=None, y_start=None):
         """Advance one time step.  s_y: (nb, 12) body targets (driven rows).
         Newton starts from (x_n, y_n) as in the paper's step; the tests may
@@ -361,7 +377,7 @@ class OracleEnv:
             st.newton_iters = it + 1
             pt, ee = self.static_pairs(x, y)
             pairs = self.pair_arrays(pt, ee)
-            g, H = self.grad_hess(x, y, ctx, pairs)
+            g, H = self.grad_hess(x, y, ctx, pairs, project=self.newton_filter(it))
             f = self.free
             p = np.zeros(self.ndof)
             rhs = -g[f]

@@ -66,16 +66,25 @@ void KL(ipc_ctx* ctx, int kind, F&& f, cudaStream_t st = nullptr) {
 }
 
 // the first n side streams start after everything issued so far on the
-// ctx stream ...
-void fork_side(ipc_ctx* ctx, int n = 2) {
-  cudaEventRecord(ctx->ev_fork, ctx->stream);
-  for (int i = 0; i < n; ++i) cudaStreamWaitEvent(ctx->side[i], ctx->ev_fork, 0);
+// main stream s (the ctx stream, or the stream capturing a graph body) ...
+int side_set(const ipc_ctx* ctx, cudaStream_t s) {
+  for (int i = 0; i < 3; ++i)
+    if (s == ctx->cap[i]) return 1 + i;
+  return 0;
 }
-// ... and the ctx stream continues only after them
-void join_side(ipc_ctx* ctx, int n = 2) {
+// side stream i of main stream s
+cudaStream_t side_of(const ipc_ctx* ctx, cudaStream_t s, int i) { return ctx->side[side_set(ctx, s)][i]; }
+void fork_side(ipc_ctx* ctx, cudaStream_t s, int n = 2) {
+  const int k = side_set(ctx, s);
+  cudaEventRecord(ctx->ev_fork[k], s);
+  for (int i = 0; i < n; ++i) cudaStreamWaitEvent(ctx->side[k][i], ctx->ev_fork[k], 0);
+}
+// ... and s continues only after them
+void join_side(ipc_ctx* ctx, cudaStream_t s, int n = 2) {
+  const int k = side_set(ctx, s);
   for (int i = 0; i < n; ++i) {
-    cudaEventRecord(ctx->ev_join[i], ctx->side[i]);
-    cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0);
+    cudaEventRecord(ctx->ev_join[k][i], ctx->side[k][i]);
+    cudaStreamWaitEvent(s, ctx->ev_join[k][i], 0);
   }
 }
 
@@ -146,6 +155,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.ls_max = prm.ls_max;
   d.accd_max = prm.accd_max;
   d.al_max = prm.al_max;
+  d.abs_after = prm.newton_abs_after;
   d.prec = prm.precision ? 1 : 0;
 
   ex.env_pair_off_i.assign(pk.env_pair_off.begin(), pk.env_pair_off.end());
@@ -216,6 +226,15 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.obj_size = carve_copy(c, pk.obj_size, up);
   d.obj_exclude = carve_copy(c, pk.obj_exclude, up);
   d.coated_row = carve_copy(c, pk.coated_row, up);
+  for (int k = 0; k < 3; ++k) {
+    d.bv_perm[k] = carve_copy(c, pk.bv_perm[k], up);
+    d.bv_cl_obj[k] = carve_copy(c, pk.bv_cl_obj[k], up);
+    d.bv_sc_obj[k] = carve_copy(c, pk.bv_sc_obj[k], up);
+    d.obj_cl_begin[k] = carve_copy(c, pk.obj_cl_begin[k], up);
+    d.obj_sc_begin[k] = carve_copy(c, pk.obj_sc_begin[k], up);
+    d.bv_n_cl[k] = (int)pk.bv_cl_obj[k].size();
+    d.bv_n_sc[k] = (int)pk.bv_sc_obj[k].size();
+  }
   // dynamic
   size_t R3 = 3 * (size_t)pk.n_rows;
   d.x = c.take<double>(R3);
@@ -239,6 +258,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_item_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_ctl = c.take<unsigned int>(8);
+  d.step_ctl = c.take<unsigned int>(8);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
   d.pc = c.take<double>(6 * (size_t)pk.n_rows);
@@ -260,6 +280,10 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.cv_box = c.take<double>(6 * (size_t)pk.n_cv);
   d.tri_box = c.take<double>(6 * (size_t)pk.n_tri);
   d.edge_box = c.take<double>(6 * (size_t)pk.n_edge);
+  for (int k = 0; k < 3; ++k) {
+    d.bv_cl_box[k] = c.take<double>(6 * (size_t)d.bv_n_cl[k]);
+    d.bv_sc_box[k] = c.take<double>(6 * (size_t)d.bv_n_sc[k]);
+  }
   {
     // worklist capacity: every query primitive against every smaller object
     long long cap = 0;
@@ -351,32 +375,65 @@ ipc_status last_cuda(ipc_ctx* ctx) {
   return IPC_OK;
 }
 
-// ---- the assembled Newton system at the current iterate of active envs
-// lag_friction: the state is x^n (first Newton iteration of a step): record
-// the lagged friction data from this iteration's static pairs
-ipc_status assemble_system(ipc_ctx* ctx, bool lag_friction) {
+// ---- the assembled Newton system at the current iterate of active envs,
+// on stream s.  The lagged friction records are taken only in the first
+// Newton iteration of a step (decided on the device).
+ipc_status assemble_system(ipc_ctx* ctx, cudaStream_t s) {
   const Dev& d = ctx->dev;
-  cudaStream_t s = ctx->stream;
-  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_ACTIVE, false, s); });
-  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_ACTIVE, false, s); });
-  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
-  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); });
-  KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_ACTIVE, false, s); }, s);
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_ACTIVE, false, s); }, s);
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); }, s);
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); }, s);
+  KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); }, s);
   // barrier terms (side stream 0) and ABD terms (side stream 1) are few,
   // latency-bound threads; they are issued first, at high priority, and run
   // beside the per-tet kernel, which fills the rest of the GPU
-  fork_side(ctx);
-  cudaStream_t s0 = ctx->side[0], s1 = ctx->side[1];
-  if (lag_friction) KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s0); }, s0);
+  fork_side(ctx, s);
+  cudaStream_t s0 = side_of(ctx, s, 0), s1 = side_of(ctx, s, 1);
+  KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s0); }, s0);
   KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s0); }, s0);
   KL(ctx, KC_BARRIER, [&] { return launch_fric_assemble(d, s0); }, s0);
   KL(ctx, KC_BODY, [&] { return launch_body(d, s1); }, s1);
-  KL(ctx, KC_TET, [&] { return launch_tet(d, s); });
-  join_side(ctx);
-  KL(ctx, KC_ASSEMBLE, [&] { return launch_assemble(d, s); });
-  KL(ctx, KC_GRAD, [&] { return launch_grad(d, s); });
-  KL(ctx, KC_PRECOND, [&] { return launch_precond(d, s); });
+  KL(ctx, KC_TET, [&] { return launch_tet(d, s); }, s);
+  join_side(ctx, s);
+  KL(ctx, KC_ASSEMBLE, [&] { return launch_assemble(d, s); }, s);
+  KL(ctx, KC_GRAD, [&] { return launch_grad(d, s); }, s);
+  KL(ctx, KC_PRECOND, [&] { return launch_precond(d, s); }, s);
   return last_cuda(ctx);
+}
+
+// Newton decision after the solve: |p|_inf, converged / AL update / line search
+void newton_decide(ipc_ctx* ctx, cudaStream_t s) {
+  const Dev& d = ctx->dev;
+  KL(ctx, KC_NEWTON, [&] { return launch_newton_check(d, s); }, s);
+  KL(ctx, KC_NEWTON, [&] { return launch_newton_decide(d, s); }, s);
+  KL(ctx, KC_NEWTON, [&] { return launch_al_update(d, s); }, s);
+}
+
+// CCD-filtered backtracking line search, set-up: swept candidates, ACCD
+// (side stream) beside the energy at alpha = 0, which needs only the swept
+// pair list; the step length starts from ACCD's bound after the join
+void line_search_prep(ipc_ctx* ctx, cudaStream_t s) {
+  const Dev& d = ctx->dev;
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, s); }, s);
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, s); }, s);
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); }, s);
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, s); }, s);
+  KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); }, s);
+  fork_side(ctx, s, 1);
+  cudaStream_t s0 = side_of(ctx, s, 0);
+  KL(ctx, KC_ACCD, [&] { return launch_accd(d, s0); }, s0);
+  KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 0, 0, s); }, s);
+  join_side(ctx, s, 1);
+  KL(ctx, KC_LS, [&] { return launch_ls_init(d, s); }, s);
+}
+
+// one line-search trial: energy at alpha, accept or halve, apply
+void line_search_trial(ipc_ctx* ctx, cudaStream_t s) {
+  const Dev& d = ctx->dev;
+  KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 1, 1, s); }, s);
+  KL(ctx, KC_LS, [&] { return launch_ls_decide(d, s); }, s);
+  KL(ctx, KC_LS, [&] { return launch_ls_apply(d, s); }, s);
 }
 
 constexpr int kPcgPoll = 16;  // host-driven path: PCG iterations between reads of the live-env count
@@ -484,7 +541,7 @@ ipc_status run_pcg(ipc_ctx* ctx) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
-  const bool graph = ctx->graph_on && !ctx->prof_on;
+  const bool graph = ctx->graph_mode == 1 && !ctx->prof_on;
   if (graph) {
     if (!ctx->pcg_exec) {
       ipc_status st = capture_pcg(ctx);
@@ -506,6 +563,119 @@ ipc_status run_pcg(ipc_ctx* ctx) {
     if (ctx->h_ctl[4] == 0) break;  // no env still iterating
   }
   return last_cuda(ctx);
+}
+
+// ---- the whole step as one CUDA graph (ipc_set_graph_mode(ctx, 2))
+//
+//   predict / targets
+//   WHILE (an env is in Newton and fewer than newton_max iterations ran)
+//     assembly; PCG: work list, WHILE (an env iterates) { mat-vec, update }
+//     Newton decision
+//     IF (an env needs a line search)
+//       swept candidates, ACCD, energy at 0
+//       WHILE (an env is in the line search) { energy at alpha, decide, apply }
+//   finalize
+//
+// Every condition is set on the device (k_flag_cond, the PCG update's last
+// CTA), so a step needs no host round trip; every loop is bounded by its
+// iteration cap on the device.  Capture streams: cap[0] fills the Newton
+// body, cap[1] the PCG and line-search bodies, cap[2] the trial loop.
+ipc_status capture_step(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = std::string("step graph capture: ") + cudaGetErrorString(e) +
+               " (the stream cannot be captured, e.g. the legacy default stream)";
+    return IPC_ECUDA;
+  }
+  const long long l0 = ctx->launches;
+  ipc_ctx::StepLaunches& L = ctx->step_launches;
+  L = ipc_ctx::StepLaunches{};
+  cudaGraph_t root = nullptr;
+  cudaGraphConditionalHandle hN = 0, hP = 0, hA = 0, hL = 0;
+  e = capturing_graph(s, &root);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hN, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hP, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hA, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hL, root, 0, 0);
+  const unsigned nmax = (unsigned)ctx->prm.newton_max, lsmax = (unsigned)ctx->prm.ls_max + 1u;
+  cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
+  auto body = [&](cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType t,
+                  auto&& fill) {
+    if (e != cudaSuccess) return;
+    cudaGraph_t g = nullptr;
+    e = add_conditional(cs, h, t, &g);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return;
+    fill();
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(bs, &g2);
+    if (e == cudaSuccess) e = e2;
+  };
+  if (e == cudaSuccess) {
+    long long m = ctx->launches;
+    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); }, s);
+    KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); }, s);
+    KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); }, s);
+    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, s, I_ACTIVE, 2, -1, -1, -1, 0, hN, 1); }, s);
+    L.pre = ctx->launches - m;
+  }
+  body(s, c0, hN, cudaGraphCondTypeWhile, [&] {
+    long long m = ctx->launches;
+    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, c0); }, c0);
+    if (assemble_system(ctx, c0) != IPC_OK) e = cudaErrorUnknown;
+    KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, c0); }, c0);
+    KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, c0, hP, 1); }, c0);
+    long long mn = ctx->launches;
+    body(c0, c1, hP, cudaGraphCondTypeWhile, [&] { L.pcg_iter = pcg_iteration(ctx, c1, hP, 1); });
+    mn = ctx->launches - mn;
+    newton_decide(ctx, c0);
+    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_LS, 3, -1, -1, 1, 0, hA, 1); }, c0);
+    long long ml = ctx->launches;
+    body(c0, c1, hA, cudaGraphCondTypeIf, [&] {
+      long long mp = ctx->launches;
+      line_search_prep(ctx, c1);
+      KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c1, I_LS, 3, 6, -1, -1, 0xffffffffu, hL, 1); }, c1);
+      L.ls_prep = ctx->launches - mp;
+      long long mt = ctx->launches;
+      body(c1, c2, hL, cudaGraphCondTypeWhile, [&] {
+        line_search_trial(ctx, c2);
+        KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c2, I_LS, 3, 1, 5, -1, lsmax, hL, 1); }, c2);
+      });
+      L.ls_trial = ctx->launches - mt;
+    });
+    ml = ctx->launches - ml;
+    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_ACTIVE, 2, 0, -1, -1, nmax, hN, 1); }, c0);
+    L.newton = ctx->launches - m - mn - ml;
+  });
+  if (e == cudaSuccess) {
+    long long m = ctx->launches;
+    KL(ctx, KC_MISC, [&] { return launch_finalize(d, s); }, s);
+    L.post = ctx->launches - m;
+  }
+  cudaGraph_t gg = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &gg);
+  if (e == cudaSuccess) e = e2;
+  ctx->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->step_exec, gg, 0);
+  if (gg) cudaGraphDestroy(gg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->step_exec = nullptr;
+    ctx->err = std::string("step graph capture: ") + cudaGetErrorString(e);
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+// drop captured graphs (launch shapes or modes changed)
+void drop_graphs(ipc_ctx* ctx) {
+  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  ctx->pcg_exec = nullptr;
+  ctx->step_exec = nullptr;
 }
 
 // user-order DoF vector <-> row space of one env
@@ -583,7 +753,7 @@ void ipc_default_params(ipc_params* p) {
   p->kappa = 1e6;
   p->newton_tol = 1e-4;
   p->pcg_rel_tol = 1e-4;
-  p->newton_max = 100;
+  p->newton_max = 300;
   p->pcg_max = 1000;
   p->ls_max = 30;
   p->accd_max = 10000;
@@ -595,6 +765,7 @@ void ipc_default_params(ipc_params* p) {
   p->max_pairs_per_env = 0;
   p->friction_mu = 0.0;
   p->friction_eps_v = 1e-3;
+  p->newton_abs_after = 1000000;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
@@ -615,6 +786,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
                            size_t ws_bytes, void* cuda_stream, ipc_ctx** out) {
   if (!prm || !out || !dev_workspace) return IPC_EINVAL;
   if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
+      prm->newton_abs_after < 0 ||
       prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
     return IPC_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
@@ -651,15 +823,18 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaMallocHost(&ctx->h_int, NUM_INTS * sizeof(int) * (size_t)pk.n_envs));
   CK(cudaMallocHost(&ctx->h_dbl, NUM_SCALARS * sizeof(double) * (size_t)pk.n_envs));
   CK(cudaMallocHost(&ctx->h_ctl, 8 * sizeof(unsigned int)));
+  CK(cudaMallocHost(&ctx->h_step_ctl, 8 * sizeof(unsigned int)));
   for (const auto& ev : pk.env) ctx->max_bodies = std::max(ctx->max_bodies, ev.n_bodies);
   int prio_least = 0, prio_greatest = 0;
   CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
   for (int i = 0; i < 2; ++i) {
-    CK(cudaStreamCreateWithPriority(&ctx->side[i], cudaStreamNonBlocking, prio_greatest));
-    CK(cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming));
+    for (int k = 0; k < 4; ++k) {
+      CK(cudaStreamCreateWithPriority(&ctx->side[k][i], cudaStreamNonBlocking, prio_greatest));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join[k][i], cudaEventDisableTiming));
+    }
   }
-  CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-  for (int i = 0; i < 2; ++i) CK(cudaStreamCreateWithFlags(&ctx->cap[i], cudaStreamNonBlocking));
+  for (int k = 0; k < 4; ++k) CK(cudaEventCreateWithFlags(&ctx->ev_fork[k], cudaEventDisableTiming));
+  for (int i = 0; i < 3; ++i) CK(cudaStreamCreateWithFlags(&ctx->cap[i], cudaStreamNonBlocking));
   // persistent PCG grid: every resident CTA of the two PCG kernels
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
@@ -672,25 +847,30 @@ ipc_status ipc_destroy(ipc_ctx* ctx) {
   if (ctx->h_int) cudaFreeHost(ctx->h_int);
   if (ctx->h_dbl) cudaFreeHost(ctx->h_dbl);
   if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
-  for (int i = 0; i < 2; ++i)
+  if (ctx->h_step_ctl) cudaFreeHost(ctx->h_step_ctl);
+  for (int i = 0; i < 3; ++i)
     if (ctx->cap[i]) cudaStreamDestroy(ctx->cap[i]);
-  if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
+  drop_graphs(ctx);
   for (auto& pe : ctx->pending) { cudaEventDestroy(pe.a); cudaEventDestroy(pe.b); }
   for (auto e : ctx->ev_free) cudaEventDestroy(e);
   for (int i = 0; i < 2; ++i) {
-    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
-    if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+    for (int k = 0; k < 4; ++k) {
+      if (ctx->side[k][i]) cudaStreamDestroy(ctx->side[k][i]);
+      if (ctx->ev_join[k][i]) cudaEventDestroy(ctx->ev_join[k][i]);
+    }
   }
-  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  for (int k = 0; k < 4; ++k)
+    if (ctx->ev_fork[k]) cudaEventDestroy(ctx->ev_fork[k]);
   delete ctx;
   return IPC_OK;
 }
 
 const char* ipc_last_error(const ipc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int on) {
-  if (!ctx) return IPC_EINVAL;
-  ctx->graph_on = on != 0;
+ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int mode) {
+  if (!ctx || mode < 0 || mode > 2) return IPC_EINVAL;
+  if (mode != ctx->graph_mode) drop_graphs(ctx);
+  ctx->graph_mode = mode;
   return IPC_OK;
 }
 
@@ -738,11 +918,8 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
   CK(cudaStreamSynchronize(s));
-  // the captured PCG graph holds the old launch shapes
-  if (ctx->pcg_exec) {
-    cudaGraphExecDestroy(ctx->pcg_exec);
-    ctx->pcg_exec = nullptr;
-  }
+  // the captured graphs hold the old launch shapes
+  drop_graphs(ctx);
   t.spmv_unroll = best_u;
   t.pcg_ctas_per_sm = best_c;
   for (int k = 0; k < 3; ++k) t.grid_ctas_per_sm[k] = cand[k];
@@ -830,19 +1007,80 @@ ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v
   KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(ctx->dev, I_SEL, false, ctx->stream); });
   KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 2, ctx->stream); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(ctx->dev, I_SEL, false, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_cross_check(ctx->dev, I_SEL, ctx->stream); });
   KL(ctx, KC_MISC, [&] { return launch_min_dist(ctx->dev, I_SEL, ctx->stream); });
   if ((st = last_cuda(ctx)) != IPC_OK) return st;
   if ((st = sync_flags(ctx)) != IPC_OK) return st;
   ipc_status verdict = IPC_OK;
-  if (ctx->h_int[env * NUM_INTS + I_FLAG]) verdict = IPC_EINVERTED;
-  else if (!(ctx->h_dbl[env * NUM_SCALARS + S_MIND] > 0.0)) verdict = IPC_EINTERSECT;
+  const int flag = ctx->h_int[env * NUM_INTS + I_FLAG];
+  if (flag == 1) verdict = IPC_EINVERTED;
+  else if (flag == 2 || !(ctx->h_dbl[env * NUM_SCALARS + S_MIND] > 0.0)) verdict = IPC_EINTERSECT;
   if (verdict != IPC_OK) {
     upload_rows(ctx, env, ctx->dev.x, old_x);
     upload_rows(ctx, env, ctx->dev.v, old_v);
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->err = verdict == IPC_EINVERTED ? "set_state: inverted tetrahedron" : "set_state: surfaces touch";
+    ctx->err = verdict == IPC_EINVERTED ? "set_state: inverted tetrahedron"
+               : flag == 2             ? "set_state: surfaces cross (an edge passes through a triangle)"
+                                       : "set_state: surfaces touch";
   }
   return verdict;
+}
+
+ipc_status ipc_reset_env(ipc_ctx* ctx, int env, const ipc_scene_desc* scene) {
+  if (check_env(ctx, env) != IPC_OK || !scene) return IPC_EINVAL;
+  std::shared_ptr<EnvLocal> L;
+  std::string err;
+  if (!build_env_local(*scene, env, ctx->prm, L, err)) {
+    ctx->err = "ipc_reset_env: " + err;
+    return IPC_EINVAL;
+  }
+  Pack& pk = ctx->pk;
+  if (!same_topology(*pk.locals[env], *L)) {
+    ctx->err = "ipc_reset_env: the scene's topology (mesh sizes, connectivity, pinned / attached / driven sets, "
+               "bodies) differs from the env's";
+    return IPC_EINVAL;
+  }
+  // the previous step may still read the tables
+  CK(cudaStreamSynchronize(ctx->stream));
+  patch_env_values(pk, env, *L);
+  const EnvInfo& ev = pk.env[env];
+  Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  auto up = [&](const void* dst, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  const size_t r0 = ev.row_begin, R = ev.n_rows, t0 = ev.tet_begin, T = ev.n_tets, c0 = ev.cv_begin,
+               NC = ev.n_cv, b0 = ev.body_begin, NB = ev.n_bodies, e0 = ev.edge_begin, NE = ev.n_edge,
+               tr0 = ev.tri_begin, NT = ev.n_tri;
+  CK(up(d.env_mu + env, &pk.env_mu[env], sizeof(double)));
+  CK(up(d.env_lam + env, &pk.env_lam[env], sizeof(double)));
+  CK(up(d.row_mass + r0, &pk.row_mass[r0], R * sizeof(double)));
+  CK(up(d.row_xbar + 3 * r0, &pk.row_xbar[3 * r0], 3 * R * sizeof(double)));
+  CK(up(d.Dm_inv + 9 * t0, &pk.Dm_inv[9 * t0], 9 * T * sizeof(double)));
+  CK(up(d.tet_vol + t0, &pk.tet_vol[t0], T * sizeof(double)));
+  if (NB) {
+    CK(up(d.body_mass + b0, &pk.body_mass[b0], NB * sizeof(double)));
+    CK(up(d.body_vol + b0, &pk.body_vol[b0], NB * sizeof(double)));
+    CK(up(d.body_kappa + b0, &pk.body_kappa[b0], NB * sizeof(double)));
+    CK(up(d.body_driven + b0, &pk.body_driven[b0], NB * sizeof(uint8_t)));
+    CK(up(d.body_S + 9 * b0, &pk.body_S[9 * b0], 9 * NB * sizeof(double)));
+  }
+  CK(up(d.cv_xbar + 3 * c0, &pk.cv_xbar[3 * c0], 3 * NC * sizeof(double)));
+  CK(up(d.cv_area + c0, &pk.cv_area[c0], NC * sizeof(double)));
+  CK(up(d.cv_fixed + c0, &pk.cv_fixed[c0], NC * sizeof(uint8_t)));
+  CK(up(d.edge_area + e0, &pk.edge_area[e0], NE * sizeof(double)));
+  CK(up(d.edge_len2 + e0, &pk.edge_len2[e0], NE * sizeof(double)));
+  CK(up(d.bv_perm[0] + c0, &pk.bv_perm[0][c0], NC * sizeof(int)));
+  CK(up(d.bv_perm[1] + tr0, &pk.bv_perm[1][tr0], NT * sizeof(int)));
+  CK(up(d.bv_perm[2] + e0, &pk.bv_perm[2][e0], NE * sizeof(int)));
+  // rest state: x = targets = rest placement, velocities and multipliers zero
+  CK(up(d.x + 3 * r0, &pk.rest_x[3 * r0], 3 * R * sizeof(double)));
+  CK(up(d.s_tgt + 3 * r0, &pk.rest_x[3 * r0], 3 * R * sizeof(double)));
+  CK(cudaMemsetAsync(d.v + 3 * r0, 0, 3 * R * sizeof(double), s));
+  CK(cudaMemsetAsync(d.lam + 3 * r0, 0, 3 * R * sizeof(double), s));
+  CK(cudaMemsetAsync(d.env_i + env * NUM_INTS + I_STATUS, 0, sizeof(int), s));
+  CK(cudaStreamSynchronize(s));
+  return IPC_OK;
 }
 
 ipc_status ipc_set_targets(ipc_ctx* ctx, int env, const double* y_target) {
@@ -874,7 +1112,7 @@ ipc_status ipc_set_targets_all_device(ipc_ctx* ctx, const double* dev_y_targets)
 
 ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_env_status, ipc_step_stats* stats) {
   if (!ctx) return IPC_EINVAL;
-  auto t0 = std::chrono::steady_clock::now();
+  ctx->step_t0 = std::chrono::steady_clock::now();
   std::vector<int> sel;
   if (!env_ids) {
     for (int e = 0; e < ctx->pk.n_envs; ++e) sel.push_back(e);
@@ -884,56 +1122,75 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
       sel.push_back(env_ids[i]);
     }
   }
+  ctx->last_sel = sel;
   if (sel.empty()) {  // nothing to step
+    ctx->step_pending = false;
     if (stats) *stats = ipc_step_stats{};
     return IPC_OK;
   }
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
   ipc_status st;
-  if ((st = select_envs(ctx, sel)) != IPC_OK) return st;
+  if (!env_ids) KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 4, s); });  // every env
+  else if ((st = select_envs(ctx, sel)) != IPC_OK) return st;
+  if (ctx->graph_mode == 2 && !ctx->prof_on) {
+    // the whole step as one graph: no host round trip until the results
+    if (!ctx->step_exec && (st = capture_step(ctx)) != IPC_OK) return st;
+    CK(cudaGraphLaunch(ctx->step_exec, s));
+    ctx->step_graph_pending = true;
+    ctx->step_pending = true;
+    if ((st = last_cuda(ctx)) != IPC_OK) return st;
+    if (!per_env_status && !stats) return IPC_OK;
+    return ipc_step_results(ctx, per_env_status, stats);
+  }
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); });
   KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); });
   KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); });
+  const unsigned nmax = (unsigned)ctx->prm.newton_max;
   for (int it = 0; it < ctx->prm.newton_max; ++it) {
     KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
-    if ((st = assemble_system(ctx, it == 0)) != IPC_OK) return st;
+    if ((st = assemble_system(ctx, s)) != IPC_OK) return st;
     if ((st = run_pcg(ctx)) != IPC_OK) return st;
-    KL(ctx, KC_NEWTON, [&] { return launch_newton_check(d, s); });
-    KL(ctx, KC_NEWTON, [&] { return launch_newton_decide(d, s); });
-    KL(ctx, KC_NEWTON, [&] { return launch_al_update(d, s); });
+    newton_decide(ctx, s);
     if ((st = sync_flags(ctx)) != IPC_OK) return st;
-    int n_ls = count_flag(ctx, I_LS);
-    if (n_ls == 0) {
-      if (count_flag(ctx, I_ACTIVE) == 0) break;
-      continue;
+    if (count_flag(ctx, I_LS) > 0) {
+      line_search_prep(ctx, s);
+      for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
+        line_search_trial(ctx, s);
+        if ((st = sync_flags(ctx)) != IPC_OK) return st;
+        if (count_flag(ctx, I_LS) == 0) break;
+      }
     }
-    // CCD-filtered backtracking line search on envs that need it
-    KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, s); });
-    KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, s); });
-    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); });
-    KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, s); });
-    KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); });
-    // ACCD (side stream) beside the energy at alpha = 0, which needs only
-    // the swept pair list; the step length starts from ACCD's bound after
-    // the join
-    fork_side(ctx, 1);
-    KL(ctx, KC_ACCD, [&] { return launch_accd(d, ctx->side[0]); }, ctx->side[0]);
-    KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 0, 0, s); });
-    join_side(ctx, 1);
-    KL(ctx, KC_LS, [&] { return launch_ls_init(d, s); });
-    for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
-      KL(ctx, KC_ENERGY, [&] { return launch_energy(d, 1, 1, s); });
-      KL(ctx, KC_LS, [&] { return launch_ls_decide(d, s); });
-      KL(ctx, KC_LS, [&] { return launch_ls_apply(d, s); });
-      if ((st = sync_flags(ctx)) != IPC_OK) return st;
-      if (count_flag(ctx, I_LS) == 0) break;
-    }
+    // Newton iteration counter on the device (the friction lag reads it)
+    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, s, I_ACTIVE, 2, 0, -1, -1, nmax, 0, 0); });
     if (count_flag(ctx, I_ACTIVE) == 0) break;
   }
   KL(ctx, KC_MISC, [&] { return launch_finalize(d, s); });
   if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  ctx->step_pending = true;
+  return ipc_step_results(ctx, per_env_status, stats);
+}
+
+ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stats* stats) {
+  if (!ctx) return IPC_EINVAL;
+  if (!ctx->step_pending) {
+    if (stats) *stats = ipc_step_stats{};
+    return IPC_OK;
+  }
+  ipc_status st;
+  if (ctx->step_graph_pending)
+    CK(cudaMemcpyAsync(ctx->h_step_ctl, ctx->dev.step_ctl, 8 * sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
   if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  if (ctx->step_graph_pending) {
+    const ipc_ctx::StepLaunches& L = ctx->step_launches;
+    const unsigned* c = ctx->h_step_ctl;
+    ctx->launches += L.pre + (long long)c[0] * L.newton + (long long)c[4] * L.pcg_iter +
+                     (long long)c[6] * L.ls_prep + (long long)c[5] * L.ls_trial + L.post;
+    ctx->step_graph_pending = false;
+  }
+  ctx->step_pending = false;
+  const std::vector<int>& sel = ctx->last_sel;
   ipc_step_stats S{};
   for (size_t i = 0; i < sel.size(); ++i) {
     const int* ei = ctx->h_int + sel[i] * NUM_INTS;
@@ -949,8 +1206,10 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     S.accd_iters += ei[I_ACCDIT];
     S.accd_iters_max = std::max(S.accd_iters_max, ei[I_ACCDMAX]);
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
+    S.pair_evals += ei[I_PAIRTOT];
+    S.swept_pairs += ei[I_SWEPTTOT];
   }
-  S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->step_t0).count();
   if (stats) *stats = S;
   return IPC_OK;
 }
@@ -958,7 +1217,8 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
 ipc_status ipc_env_stats(const ipc_ctx* ctx, int env, int32_t* out) {
   if (check_env(ctx, env) != IPC_OK || !out) return IPC_EINVAL;
   const int* ei = ctx->h_int + env * NUM_INTS;
-  const int k[IPC_ENV_STATS] = {I_STATUS, I_NEWTON, I_AL, I_PCGTOT, I_LSTOT, I_CCDCUT, I_ACCDMAX, I_NPAIRS, I_ACCDIT};
+  const int k[IPC_ENV_STATS] = {I_STATUS, I_NEWTON, I_AL,      I_PCGTOT,  I_LSTOT,   I_CCDCUT,
+                                I_ACCDMAX, I_NPAIRS, I_ACCDIT, I_PAIRTOT, I_SWEPTTOT};
   for (int i = 0; i < IPC_ENV_STATS; ++i) out[i] = ei[k[i]];
   return IPC_OK;
 }
@@ -996,7 +1256,7 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
   const Dev& d = ctx->dev;
   ipc_status st;
   if ((st = begin_single(ctx, env)) != IPC_OK) return st;
-  if ((st = assemble_system(ctx, true)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx, ctx->stream)) != IPC_OK) return st;
   std::vector<double> rows;
   if (grad) {
     if ((st = download_rows(ctx, env, d.g, rows)) != IPC_OK) return st;
@@ -1036,7 +1296,7 @@ ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters
   if (check_env(ctx, env) != IPC_OK || !p) return IPC_EINVAL;
   ipc_status st;
   if ((st = begin_single(ctx, env)) != IPC_OK) return st;
-  if ((st = assemble_system(ctx, true)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx, ctx->stream)) != IPC_OK) return st;
   if ((st = run_pcg(ctx)) != IPC_OK) return st;
   if ((st = sync_flags(ctx)) != IPC_OK) return st;
   if (pcg_iters) *pcg_iters = ctx->h_int[env * NUM_INTS + I_PCGIT];
@@ -1176,14 +1436,14 @@ ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks,
 // ---------------------------------------------------------------- element kernels
 ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double* vol, double mu, double lam,
                      double* energy, double* grad, double* hess, int project, void* stream) {
-  if (n < 0 || (n > 0 && (!x || !Dm_inv || !vol))) return IPC_EINVAL;
+  if (n < 0 || (n > 0 && (!x || !Dm_inv || !vol)) || project < 0 || project > 2) return IPC_EINVAL;
   launch_k_tet(n, x, Dm_inv, vol, mu, lam, energy, grad, hess, project, reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;
 }
 
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight, const double* eps_x,
                          double dhat, double* energy, double* grad, double* hess, int project, void* stream) {
-  if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0)) return IPC_EINVAL;
+  if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0) || project < 0 || project > 2) return IPC_EINVAL;
   launch_k_barrier(n, X, is_ee, weight, eps_x, dhat, energy, grad, hess, project,
                    reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;

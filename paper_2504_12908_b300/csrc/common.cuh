@@ -157,9 +157,10 @@ IPC_HD void jacobi_eigen(T* A, T* V, int max_sweeps = 12) {
 }
 
 // In-place PSD projection of a symmetric n x n matrix (row-major): negative
-// eigenvalues clamped to zero.  Uses `work` of 2 n^2 elements.
+// eigenvalues clamped to zero, or replaced by their absolute values when
+// `absval` is set.  Uses `work` of 2 n^2 elements.
 template <int n, class T>
-IPC_HD void psd_project(T* H, T* work) {
+IPC_HD void psd_project(T* H, T* work, bool absval = false) {
   T* A = work;
   T* V = work + n * n;
   for (int i = 0; i < n * n; ++i) A[i] = H[i];
@@ -172,6 +173,7 @@ IPC_HD void psd_project(T* H, T* work) {
       T s = 0;
       for (int k = 0; k < n; ++k) {
         T l = A[k * n + k];
+        if (absval) l = fabs(l);
         if (l > T(0)) s += V[i * n + k] * l * V[j * n + k];
       }
       H[i * n + j] = s;

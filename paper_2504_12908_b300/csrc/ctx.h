@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,8 @@ enum EnvInt {
   I_NFRIC,        // lagged friction records of this step
   I_NACT,         // active contact pairs (d < dhat) of this Newton iteration
   I_GEN,          // Newton iterations ever run (tags the rows contact terms touch)
+  I_PAIRTOT,      // static candidate pairs evaluated this step (all Newton iterations)
+  I_SWEPTTOT,     // swept candidate pairs of this step's line searches
   NUM_INTS
 };
 
@@ -65,6 +68,8 @@ struct Dev {
   // parameters
   double h, grav[3], dhat, kappa, newton_tol, pcg_tol, accd_s, al_kappa, ee_moll;
   int newton_max, pcg_max, ls_max, accd_max, al_max;
+  int abs_after;                // Newton iterations per step that clamp negative eigenvalues;
+                                // later iterations use their absolute values
   int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
   // launch shapes (ipc_autotune): SpMV slots in flight per lane (2, 4, 8;
   // 0 = default by precision)
@@ -98,6 +103,12 @@ struct Dev {
       *obj_edge_begin, *obj_edge_end, *obj_size;
   const unsigned long long* obj_exclude;
   const int* coated_row;
+  // broad-phase hierarchy per primitive kind (0 points, 1 triangles, 2
+  // edges): Morton-ordered primitives of each object in clusters of 32 and
+  // superclusters of 32 clusters, boxes refitted at every candidate search
+  const int *bv_perm[3], *bv_cl_obj[3], *bv_sc_obj[3], *obj_cl_begin[3], *obj_sc_begin[3];
+  int bv_n_cl[3], bv_n_sc[3];
+  double *bv_cl_box[3], *bv_sc_box[3];
   // state and work (row space: 3 doubles per row)
   double *x, *v, *xn, *xt, *s_tgt, *lam;
   double *p, *g, *r, *z, *d, *q, *qc;
@@ -117,6 +128,10 @@ struct Dev {
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] the list is stale
   int pcg_grid;                 // CTAs of the persistent PCG kernels
+  unsigned int* step_ctl;       // per step (device-side loops): [0] Newton iterations done,
+                                // [1] trials of the current line search, [2] envs still in
+                                // Newton, [3] envs in a line search, [4] PCG iterations,
+                                // [5] line-search trials, [6] line searches
   void* pc;                     // 6 per row: symmetric inverse of the diagonal block
                                 // (double, or float in mixed mode)
   double* pc_acc;               // 9 per row
@@ -184,16 +199,29 @@ struct ipc_ctx {
   // per-body ABD terms beside the per-tet elastic kernel; ACCD beside the
   // line search's first energy).  Forked from and joined back into `stream`
   // with events, so the caller still sees one stream.
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t ev_fork = nullptr;
-  cudaEvent_t ev_join[2] = {nullptr, nullptr};
-  // CUDA graph of the whole PCG solve, a WHILE node over one iteration
-  // (ipc_set_graph_mode); streams used to capture conditional bodies
-  bool graph_on = false;
+  // Set 0 serves the ctx stream; sets 1..3 serve the capture streams
+  // cap[0..2] (a stream pulled into one graph capture cannot join another
+  // while that capture is open).
+  cudaStream_t side[4][2] = {};
+  cudaEvent_t ev_fork[4] = {};
+  cudaEvent_t ev_join[4][2] = {};
+  // CUDA graphs (ipc_set_graph_mode): 1 = each PCG solve is one graph (a
+  // WHILE node over one iteration), 2 = the whole step is one graph
+  int graph_mode = 0;
   cudaGraphExec_t pcg_exec = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
   int pcg_iter_launches = 0;      // kernel launches per PCG iteration
   bool pcg_graph_pending = false; // a graph solve ran; its iteration count is not yet read
-  cudaStream_t cap[2] = {nullptr, nullptr};
+  struct StepLaunches {           // launches per section of the step graph, counted at capture
+    long long pre = 0, newton = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0, post = 0;
+  } step_launches;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams of conditional bodies
+  unsigned int* h_step_ctl = nullptr;  // pinned read-back of Dev::step_ctl (8)
+  // the last ipc_step: its envs, start time, and whether its results (and,
+  // for a graph step, its launch count) are still to be read
+  std::vector<int> last_sel;
+  std::chrono::steady_clock::time_point step_t0;
+  bool step_pending = false, step_graph_pending = false;
   int n_sm = 148;
   // profiling
   bool prof_on = false;

@@ -21,6 +21,8 @@ int launch_fric_spmv(const Dev& d, cudaStream_t s);
 int launch_fric_energy(const Dev& d, int use_alpha, cudaStream_t s);
 int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s);
 int launch_min_dist(const Dev& d, int flag, cudaStream_t s);
+// crossing surfaces of I_SEL-style flagged envs -> I_FLAG = 2 (needs cvx and primitive boxes)
+int launch_cross_check(const Dev& d, int flag, cudaStream_t s);
 int launch_pnorm_body(const Dev& d, cudaStream_t s);
 
 // ---- solver (kernels_solver.cu)
@@ -55,6 +57,9 @@ int launch_ls_apply(const Dev& d, cudaStream_t s);
 int launch_finalize(const Dev& d, cudaStream_t s);
 int launch_env_reset(const Dev& d, int what, cudaStream_t s);
 int launch_check_overflow(const Dev& d, cudaStream_t s);
+// loop control of the device-side step (k_flag_cond in kernels_solver.cu)
+int launch_flag_cond(const Dev& d, cudaStream_t s, int flag, int cnt, int inc, int acc, int rst, unsigned cap,
+                     cudaGraphConditionalHandle h, int use_cond);
 int launch_check_inverted(const Dev& d, cudaStream_t s);
 int launch_scatter_targets(const Dev& d, cudaStream_t s);
 int launch_gather_coated(const Dev& d, cudaStream_t s);

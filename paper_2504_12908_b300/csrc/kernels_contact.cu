@@ -168,8 +168,87 @@ __global__ void k_worklist(Dev d, int flag) {
     }
 }
 
+// Broad-phase hierarchy refit.  Per object and primitive kind the
+// primitives are kept in Morton order of their rest centroids; a cluster is
+// 32 consecutive primitives of that order and a supercluster 32 consecutive
+// clusters.  Their boxes are the unions of the current primitive boxes (the
+// order is fixed at creation: the meshes deform but keep their topology, so
+// clusters stay compact).  A union contains each of its boxes, so a box that
+// meets the query meets every enclosing cluster and supercluster: pruning
+// by them never drops a candidate.
+__device__ __forceinline__ void prim_range(const Dev& d, int k, int o, int& b, int& e) {
+  if (k == 0) { b = d.obj_cv_begin[o]; e = d.obj_cv_end[o]; }
+  else if (k == 1) { b = d.obj_tri_begin[o]; e = d.obj_tri_end[o]; }
+  else { b = d.obj_edge_begin[o]; e = d.obj_edge_end[o]; }
+}
+__device__ __forceinline__ const double* prim_boxes(const Dev& d, int k) {
+  return k == 0 ? d.cv_box : (k == 1 ? d.tri_box : d.edge_box);
+}
+
+__global__ void k_bv_refit_cl(Dev d, int flag) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = 0;
+  while (k < 3 && c >= d.bv_n_cl[k]) c -= d.bv_n_cl[k++];
+  if (k == 3) return;
+  const int o = d.bv_cl_obj[k][c];
+  if (!ENVI(d, d.obj_env[o], flag)) return;
+  int pb, pe;
+  prim_range(d, k, o, pb, pe);
+  const int p0 = pb + 32 * (c - d.obj_cl_begin[k][o]), p1 = min(p0 + 32, pe);
+  const double* pbox = prim_boxes(d, k);
+  double bx[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int p = p0; p < p1; ++p) {
+    const double* q = pbox + 6 * (long long)d.bv_perm[k][p];
+    for (int j = 0; j < 3; ++j) { bx[j] = fmin(bx[j], q[j]); bx[3 + j] = fmax(bx[3 + j], q[3 + j]); }
+  }
+  double* out = d.bv_cl_box[k] + 6 * (long long)c;
+  for (int j = 0; j < 6; ++j) out[j] = bx[j];
+}
+
+__global__ void k_bv_refit_sc(Dev d, int flag) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = 0;
+  while (k < 3 && c >= d.bv_n_sc[k]) c -= d.bv_n_sc[k++];
+  if (k == 3) return;
+  const int o = d.bv_sc_obj[k][c];
+  if (!ENVI(d, d.obj_env[o], flag)) return;
+  int pb, pe;
+  prim_range(d, k, o, pb, pe);
+  const int ncl = (pe - pb + 31) / 32;
+  const int j0 = 32 * (c - d.obj_sc_begin[k][o]), j1 = min(j0 + 32, ncl);
+  const double* cb = d.bv_cl_box[k] + 6 * (long long)d.obj_cl_begin[k][o];
+  double bx[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int j = j0; j < j1; ++j)
+    for (int q = 0; q < 3; ++q) { bx[q] = fmin(bx[q], cb[6 * j + q]); bx[3 + q] = fmax(bx[3 + q], cb[6 * j + 3 + q]); }
+  double* out = d.bv_sc_box[k] + 6 * (long long)c;
+  for (int j = 0; j < 6; ++j) out[j] = bx[j];
+}
+
+// Calls leaf(p) for every primitive p of kind k in object o whose
+// supercluster and cluster boxes meet the query box qb (widened by dh); the
+// leaf applies the exact box test itself.
+template <class Leaf>
+__device__ __forceinline__ void bv_query(const Dev& d, int k, int o, const double* qb, double dh, Leaf&& leaf) {
+  int pb, pe;
+  prim_range(d, k, o, pb, pe);
+  const int ncl = (pe - pb + 31) / 32, nsc = (ncl + 31) / 32;
+  const double* sb = d.bv_sc_box[k] + 6 * (long long)d.obj_sc_begin[k][o];
+  const double* cb = d.bv_cl_box[k] + 6 * (long long)d.obj_cl_begin[k][o];
+  const int* perm = d.bv_perm[k];
+  for (int s = 0; s < nsc; ++s) {
+    if (!overlap6(qb, sb + 6 * s, dh)) continue;
+    const int j1 = min(32 * s + 32, ncl);
+    for (int j = 32 * s; j < j1; ++j) {
+      if (!overlap6(qb, cb + 6 * j, dh)) continue;
+      const int p1 = min(pb + 32 * j + 32, pe);
+      for (int p = pb + 32 * j; p < p1; ++p) leaf(perm[p]);
+    }
+  }
+}
+
 // Broad phase, stage 2: every item tests its query box against the boxes of
-// the other object's primitives of the complementary kind.  Within one
+// the other object's primitives of the complementary kind, found through
+// that object's cluster hierarchy (bv_query).  Within one
 // (self-contacting) object: a point never pairs with a triangle it is a
 // vertex of, and an edge pairs only with edges of higher index that share
 // no vertex with it.
@@ -184,38 +263,39 @@ __global__ void k_pairs(Dev d) {
       const double* qb = d.cv_box + 6 * (long long)i;
       bool qfix = d.cv_fixed[i];
       const bool self = d.cv_obj[i] == B;
-      for (int t = d.obj_tri_begin[B]; t < d.obj_tri_end[B]; ++t) {
-        if (!overlap6(qb, d.tri_box + 6 * (long long)t, dh)) continue;
+      bv_query(d, 1, B, qb, dh, [&](int t) {
+        if (!overlap6(qb, d.tri_box + 6 * (long long)t, dh)) return;
         int t0 = d.tri[3 * t], t1 = d.tri[3 * t + 1], t2 = d.tri[3 * t + 2];
-        if (self && (i == t0 || i == t1 || i == t2)) continue;
-        if (qfix && d.cv_fixed[t0] && d.cv_fixed[t1] && d.cv_fixed[t2]) continue;
+        if (self && (i == t0 || i == t1 || i == t2)) return;
+        if (qfix && d.cv_fixed[t0] && d.cv_fixed[t1] && d.cv_fixed[t2]) return;
         emit_pair(d, e, make_int4(i, t0, t1, t2), 0, wscale * 0.5 * d.cv_area[i], 0.0);
-      }
+      });
     } else if (qk == 1) {
       const double* qb = d.tri_box + 6 * (long long)i;
       int q0 = d.tri[3 * i], q1 = d.tri[3 * i + 1], q2 = d.tri[3 * i + 2];
       bool qfix = d.cv_fixed[q0] && d.cv_fixed[q1] && d.cv_fixed[q2];
-      for (int c = d.obj_cv_begin[B]; c < d.obj_cv_end[B]; ++c) {
-        if (!overlap6(qb, d.cv_box + 6 * (long long)c, dh)) continue;
-        if (qfix && d.cv_fixed[c]) continue;
+      bv_query(d, 0, B, qb, dh, [&](int c) {
+        if (!overlap6(qb, d.cv_box + 6 * (long long)c, dh)) return;
+        if (qfix && d.cv_fixed[c]) return;
         emit_pair(d, e, make_int4(c, q0, q1, q2), 0, wscale * 0.5 * d.cv_area[c], 0.0);
-      }
+      });
     } else {
       const double* qb = d.edge_box + 6 * (long long)i;
       int q0 = d.edge[2 * i], q1 = d.edge[2 * i + 1];
       bool qfix = d.cv_fixed[q0] && d.cv_fixed[q1];
       int A = d.edge_obj[i];
       const bool self = A == B;
-      for (int f = self ? i + 1 : d.obj_edge_begin[B]; f < d.obj_edge_end[B]; ++f) {
-        if (!overlap6(qb, d.edge_box + 6 * (long long)f, dh)) continue;
+      bv_query(d, 2, B, qb, dh, [&](int f) {
+        if (self && f <= i) return;  // each unordered edge pair once
+        if (!overlap6(qb, d.edge_box + 6 * (long long)f, dh)) return;
         int b0 = d.edge[2 * f], b1 = d.edge[2 * f + 1];
-        if (self && (b0 == q0 || b0 == q1 || b1 == q0 || b1 == q1)) continue;
-        if (qfix && d.cv_fixed[b0] && d.cv_fixed[b1]) continue;
+        if (self && (b0 == q0 || b0 == q1 || b1 == q0 || b1 == q1)) return;
+        if (qfix && d.cv_fixed[b0] && d.cv_fixed[b1]) return;
         double w = wscale * 0.25 * (d.edge_area[i] + d.edge_area[f]);
         double eps = d.ee_moll * d.edge_len2[i] * d.edge_len2[f];
         int4 v = (A <= B) ? make_int4(q0, q1, b0, b1) : make_int4(b0, b1, q0, q1);
         emit_pair(d, e, v, 1, w, eps);
-      }
+      });
     }
   }
 }
@@ -328,7 +408,7 @@ __global__ void k_barrier(Dev d, int flag) {
     cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
     D3 X[4];
     for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
-    act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H);
+    act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H, newton_filter(d, e));
     d.pair_act[k] = act ? 1 : 0;
   }
   // the active pairs of an env fill its slots env_pair_off[e] + [0, I_NACT)
@@ -578,10 +658,14 @@ __device__ __forceinline__ void fr_u(const Dev& d, int j, const D3* X, double& u
   u1 = dot(t2, s);
 }
 
-__global__ void k_fric_reset(Dev d) { *d.fr_count = 0; }
+// records are taken at x^n: only in the first Newton iteration of a step
+__global__ void k_fric_reset(Dev d) {
+  if (d.step_ctl[0] == 0u) *d.fr_count = 0;
+}
 
 // Newton iteration 0 (x = x^n): one record per static pair within dhat.
 __global__ void k_fric_setup(Dev d) {
+  if (d.step_ctl[0] != 0u) return;
   FOR_PAIRS(d, f) {
   int e;
   int k = pair_at(d, f, e);
@@ -771,6 +855,48 @@ __global__ void k_min_dist(Dev d, int flag) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// crossing surfaces (set_state): an edge of one contact object passing
+// through a triangle of another (or, in a self-contacting pad, through a
+// triangle of its own that shares no vertex with it) sets I_FLAG = 2.
+// One thread per edge; boxes first (through the other object's triangle
+// hierarchy, refitted by the candidate search), then the exact-sign test: segment PQ
+// meets triangle ABC iff P and Q are not strictly on one side of ABC's plane
+// and the line PQ passes on the same side of the three triangle edges.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double orient3(D3 a, D3 b, D3 c, D3 d) { return dot(cross(b - a, c - a), d - a); }
+
+__device__ bool segment_meets_triangle(D3 p, D3 q, D3 a, D3 b, D3 c) {
+  const double sp = orient3(a, b, c, p), sq = orient3(a, b, c, q);
+  if ((sp > 0.0 && sq > 0.0) || (sp < 0.0 && sq < 0.0)) return false;
+  if (sp == 0.0 && sq == 0.0) return false;  // coplanar: left to the distance check
+  const double s0 = orient3(p, q, a, b), s1 = orient3(p, q, b, c), s2 = orient3(p, q, c, a);
+  return (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) || (s0 <= 0.0 && s1 <= 0.0 && s2 <= 0.0);
+}
+
+__global__ void k_cross_check(Dev d, int flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_edge) return;
+  const int e = find_env(d.env_edge_off, d.n_envs, i);
+  if (!ENVI(d, e, flag)) return;
+  const int A = d.edge_obj[i];
+  const int q0 = d.edge[2 * i], q1 = d.edge[2 * i + 1];
+  const D3 P = ld3(d.cvx, q0), Q = ld3(d.cvx, q1);
+  double bx[6] = {fmin(P.x, Q.x), fmin(P.y, Q.y), fmin(P.z, Q.z), fmax(P.x, Q.x), fmax(P.y, Q.y), fmax(P.z, Q.z)};
+  const unsigned long long ex = d.obj_exclude[A];
+  bool hit = false;
+  for (int B = d.env_obj_off[e]; B < d.env_obj_off[e + 1] && !hit; ++B) {
+    if ((ex >> d.obj_local[B]) & 1ull) continue;   // excluded object pair (or a pad without self-contact)
+    bv_query(d, 1, B, bx, 0.0, [&](int t) {
+      if (hit || !overlap6(bx, d.tri_box + 6 * (long long)t, 0.0)) return;
+      const int t0 = d.tri[3 * t], t1 = d.tri[3 * t + 1], t2 = d.tri[3 * t + 2];
+      if (B == A && (t0 == q0 || t0 == q1 || t1 == q0 || t1 == q1 || t2 == q0 || t2 == q1)) return;
+      hit = segment_meets_triangle(P, Q, ld3(d.cvx, t0), ld3(d.cvx, t1), ld3(d.cvx, t2));
+    });
+  }
+  if (hit && ENVI(d, e, I_FLAG) == 0) ENVI(d, e, I_FLAG) = 2;  // an inverted tet (1) takes precedence
+}
+
 // |J_j p_b|_inf over body vertices into S_PNORM; |J_j (y_b - s_b)|_inf of
 // driven bodies into S_CRES
 __global__ void k_pnorm_body(Dev d) {
@@ -813,6 +939,11 @@ int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s) {
   if (d.n_cv) { k_worklist<0><<<nblk(d.n_cv, 128), 128, 0, s>>>(d, flag); ++n; }
   if (d.n_tri) { k_worklist<1><<<nblk(d.n_tri, 128), 128, 0, s>>>(d, flag); ++n; }
   if (d.n_edge) { k_worklist<2><<<nblk(d.n_edge, 128), 128, 0, s>>>(d, flag); ++n; }
+  {
+    const int ncl = d.bv_n_cl[0] + d.bv_n_cl[1] + d.bv_n_cl[2], nsc = d.bv_n_sc[0] + d.bv_n_sc[1] + d.bv_n_sc[2];
+    if (ncl) { k_bv_refit_cl<<<nblk(ncl, 128), 128, 0, s>>>(d, flag); ++n; }
+    if (nsc) { k_bv_refit_sc<<<nblk(nsc, 128), 128, 0, s>>>(d, flag); ++n; }
+  }
   k_pairs<<<148 * 8, 128, 0, s>>>(d);
   k_bp_check<<<nblk(d.n_envs, 128), 128, 0, s>>>(d, flag);
   k_pair_scan<<<1, 1024, 0, s>>>(d);
@@ -858,6 +989,11 @@ int launch_pair_energy(const Dev& d, int use_alpha, cudaStream_t s) {
   k_pair_energy<<<PAIR_GRID>>>(d, use_alpha);
   return 1;
 }
+int launch_cross_check(const Dev& d, int flag, cudaStream_t s) {
+  if (!d.n_edge) return 0;
+  k_cross_check<<<nblk(d.n_edge, 128), 128, 0, s>>>(d, flag);
+  return 1;
+}
 int launch_min_dist(const Dev& d, int flag, cudaStream_t s) {
   if (!d.n_pairs_cap) return 0;
   k_min_dist<<<PAIR_GRID>>>(d, flag);
@@ -880,7 +1016,7 @@ __global__ void k_elem_barrier(int n, const double* X, const int* is_ee, const d
   for (int i = 0; i < 4; ++i) P[i] = ld3(X + 12 * (long long)k, i);
   double e = 0, gl[12];
   double* Hk = H ? H + 144 * (long long)k : nullptr;
-  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, project != 0);
+  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, project);
   if (E) E[k] = e;
   if (g)
     for (int i = 0; i < 12; ++i) g[12 * (long long)k + i] = act ? gl[i] : 0.0;

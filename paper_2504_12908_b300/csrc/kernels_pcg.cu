@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
   if (threadIdx.x == 0) {
     d.pcg_ctl[C_ARRIVED] = 0;
     d.pcg_ctl[C_ITER] += 1;
+    d.step_ctl[4] += 1u;
     const unsigned len = d.pcg_ctl[C_LEN];
     const unsigned dead = d.pcg_ctl[C_DEAD];
     const unsigned items = len ? (unsigned)d.pcg_item_off[len] : 0u;

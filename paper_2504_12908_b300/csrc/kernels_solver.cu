@@ -81,13 +81,15 @@ __global__ void __launch_bounds__(64) k_tet(Dev d) {
     for (int k = 0; k < 12; ++k) G[k] = g[k];
     HT Fh[9], Dh[9];
     for (int k = 0; k < 9; ++k) { Fh[k] = (HT)F[k]; Dh[k] = (HT)Dmi[k]; }
+    const int filt = newton_filter(d, e);
     if (kStage) {
       nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
-                            [&](int a, int b, int i, int j, HT v) { mine[(a * 4 + b) * 9 + i * 3 + j] = (float)v; });
+                            [&](int a, int b, int i, int j, HT v) { mine[(a * 4 + b) * 9 + i * 3 + j] = (float)v; },
+                            filt);
     } else {
       HT* H = reinterpret_cast<HT*>(d.tetH) + 144 * (long long)t;
       nh_hessian_blocks<HT>(Fh, Dh, (HT)vol, (HT)mu, (HT)lam,
-                            [&](int a, int b, int i, int j, HT v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; });
+                            [&](int a, int b, int i, int j, HT v) { H[(a * 4 + b) * 9 + i * 3 + j] = v; }, filt);
     }
   }
   if (kStage) {
@@ -162,7 +164,7 @@ __global__ void k_body(Dev d) {
         }
   // a positive definite Hessian is its own projection (the common case near
   // rigid states); the eigen-decomposition only runs otherwise
-  if (!is_pos_def<9, double>(Ho, work)) psd_project<9, double>(Ho, work);
+  if (!is_pos_def<9, double>(Ho, work)) psd_project<9, double>(Ho, work, newton_filter(d, e) == FILT_ABS);
   double* H = d.body_H + 144 * (long long)b;
   for (int i = 0; i < 144; ++i) H[i] = 0.0;
   for (int c = 0; c < 3; ++c) H[c * 12 + c] = m;
@@ -342,6 +344,7 @@ __global__ void k_newton_decide(Dev d) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.n_envs || !ENVI(d, e, I_ACTIVE)) return;
   ENVI(d, e, I_LS) = 0;
+  ENVI(d, e, I_PAIRTOT) += min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);  // this iteration's static list
   double res = ENVS(d, e, S_PNORM) / d.h;
   if (res <= d.newton_tol) {
     if (!has_driven[e] || ENVS(d, e, S_CRES) / d.h <= d.newton_tol) {
@@ -378,6 +381,7 @@ __global__ void k_ls_init(Dev d) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= d.n_envs || !ENVI(d, e, I_LS)) return;
   ENVS(d, e, S_ALPHA) = fmin(1.0, ENVS(d, e, S_ACCD));
+  ENVI(d, e, I_SWEPTTOT) += min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);
   if (ENVS(d, e, S_ACCD) < 1.0) ENVI(d, e, I_CCDCUT) += 1;
 }
 
@@ -530,9 +534,10 @@ __global__ void k_finalize_envs(Dev d) {
 }
 
 // what: 0 = new step (counters, status), 1 = Newton-iteration scalars,
-// 2 = pair list (count, overflow), 3 = min distance
+// 2 = pair list (count, overflow), 3 = min distance, 4 = select every env
 __global__ void k_env_reset(Dev d, int what) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (what == 0 && e < 8) d.step_ctl[e] = 0u;  // new step: loop counters
   if (e >= d.n_envs) return;
   if (what == 0) {
     if (!ENVI(d, e, I_SEL)) return;
@@ -548,6 +553,8 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_ACCDIT) = 0;
     ENVI(d, e, I_ACCDMAX) = 0;
     ENVI(d, e, I_NFRIC) = 0;
+    ENVI(d, e, I_PAIRTOT) = 0;
+    ENVI(d, e, I_SWEPTTOT) = 0;
     ENVS(d, e, S_ASUM) = 0.0;
   } else if (what == 1) {
     if (!ENVI(d, e, I_ACTIVE)) return;
@@ -561,7 +568,33 @@ __global__ void k_env_reset(Dev d, int what) {
   } else if (what == 3) {
     ENVS(d, e, S_MIND) = INFINITY;
     ENVI(d, e, I_FLAG) = 0;
+  } else if (what == 4) {
+    ENVI(d, e, I_SEL) = 1;
   }
+}
+
+// Loop control of the device-side step (one CTA): counts the envs whose
+// `flag` is set into step_ctl[cnt]; with inc >= 0 also advances the loop
+// counter step_ctl[inc] (and step_ctl[acc] when acc >= 0), with rst >= 0
+// zeroes step_ctl[rst].  The condition is 1 while some env has the flag and
+// (with inc >= 0) the counter is below `cap`; inside a graph it is set on the
+// conditional handle h.
+__global__ void k_flag_cond(Dev d, int flag, int cnt, int inc, int acc, int rst, unsigned cap,
+                            cudaGraphConditionalHandle h, int use_cond) {
+  __shared__ int sh[32];
+  int c = 0;
+  for (int e = threadIdx.x; e < d.n_envs; e += blockDim.x) c += ENVI(d, e, flag) != 0;
+  c = block_sum(c, sh);
+  if (threadIdx.x != 0) return;
+  d.step_ctl[cnt] = (unsigned)c;
+  if (rst >= 0) d.step_ctl[rst] = 0u;
+  bool more = c > 0;
+  if (inc >= 0) {
+    const unsigned k = ++d.step_ctl[inc];
+    if (acc >= 0) d.step_ctl[acc] += 1u;
+    more = more && k < cap;
+  }
+  if (use_cond) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // pair-list overflow ends the env's step (state restored at finalize)
@@ -668,6 +701,11 @@ int launch_finalize(const Dev& d, cudaStream_t s) {
 }
 int launch_env_reset(const Dev& d, int what, cudaStream_t s) { k_env_reset<<<ENVGRID>>>(d, what); return 1; }
 int launch_check_overflow(const Dev& d, cudaStream_t s) { k_check_overflow<<<ENVGRID>>>(d); return 1; }
+int launch_flag_cond(const Dev& d, cudaStream_t s, int flag, int cnt, int inc, int acc, int rst, unsigned cap,
+                     cudaGraphConditionalHandle h, int use_cond) {
+  k_flag_cond<<<1, 256, 0, s>>>(d, flag, cnt, inc, acc, rst, cap, h, use_cond);
+  return 1;
+}
 int launch_scatter_targets(const Dev& d, cudaStream_t s) {
   long long n = (long long)d.n_envs * d.max_bodies * 12;
   if (n == 0) return 0;
@@ -708,7 +746,7 @@ __global__ void k_elem_tet(int n, const double* x, const double* Dmi_all, const 
     } else {
       nh_hessian_blocks<double>(
           F, Dmi, vol[t], mu, lam, [&](int a, int b, int i, int j, double v) { Ht[(3 * a + i) * 12 + 3 * b + j] = v; },
-          project != 0);
+          project);
     }
   }
 }

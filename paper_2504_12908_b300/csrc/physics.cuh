@@ -13,6 +13,9 @@
 #pragma once
 
 #include "common.cuh"
+#ifdef __CUDACC__
+#include "ctx.h"
+#endif
 
 namespace ipc {
 
@@ -129,17 +132,32 @@ IPC_HD void svd3(const T* F, T* U, T* s, T* V) {
   }
 }
 
+// Eigenvalue filter of a projected Hessian: FILT_NONE keeps the raw
+// Hessian, FILT_CLAMP sets negative eigenvalues to zero, FILT_ABS replaces
+// them by their absolute values (both give a PSD matrix).
+enum { FILT_NONE = 0, FILT_CLAMP = 1, FILT_ABS = 2 };
+
+#ifdef __CUDACC__
+// Filter of env e's current Newton iteration: clamping for the first
+// Dev::abs_after iterations of a step, absolute values after that (by
+// default abs_after exceeds any Newton cap: clamping throughout).
+__device__ __forceinline__ int newton_filter(const Dev& d, int e) {
+  return d.env_i[e * NUM_INTS + I_NEWTON] > d.abs_after ? FILT_ABS : FILT_CLAMP;
+}
+#endif
+
 // Projected 9x9 d2Psi/dF2 (index 3i+j <-> F_ij), upper triangle packed into
-// Pi[45] row by row.
+// Pi[45] row by row; filt: FILT_NONE / FILT_CLAMP / FILT_ABS.
 template <class T>
-IPC_HD void nh_projected_dPdF(const T* F, T mu, T lam, T* Pi, bool project = true) {
+IPC_HD void nh_projected_dPdF(const T* F, T mu, T lam, T* Pi, int filt = FILT_CLAMP) {
   T U[9], V[9], s[3];
   svd3(F, U, s, V);
   T lnJ = log(s[0] * s[1] * s[2]);
   T c = mu - lam * lnJ;
   for (int k = 0; k < 45; ++k) Pi[k] = 0;
   auto add_mode = [&](T lmb, const T* Q) {
-    if (project && !(lmb > T(0))) return;
+    if (filt == FILT_ABS) lmb = fabs(lmb);
+    if (filt != FILT_NONE && !(lmb > T(0))) return;
     int idx = 0;
     for (int a = 0; a < 9; ++a)
       for (int b = a; b < 9; ++b) Pi[idx++] += lmb * Q[a] * Q[b];
@@ -185,9 +203,9 @@ IPC_HD int sym9(int a, int b) {  // packed index of (a, b), a, b in [0, 9)
 // Projected element Hessian, all 16 3x3 blocks: H[(a*4+b)*9 + i*3 + j]
 // = vol * sum_{n,n'} D_a[n] Pi[(i,n),(j,n')] D_b[n'].
 template <class T, class Out>
-IPC_HD void nh_hessian_blocks(const T* F, const T* Dmi, T vol, T mu, T lam, Out&& out, bool project = true) {
+IPC_HD void nh_hessian_blocks(const T* F, const T* Dmi, T vol, T mu, T lam, Out&& out, int filt = FILT_CLAMP) {
   T Pi[45];
-  nh_projected_dPdF(F, mu, lam, Pi, project);
+  nh_projected_dPdF(F, mu, lam, Pi, filt);
   T D[4][3];
   for (int n = 0; n < 3; ++n) {
     D[1][n] = Dmi[n];
@@ -481,7 +499,7 @@ static __host__ __device__ __noinline__ void gs_push(double (*Q)[12], int& nq, d
   ++nq;
 }
 
-static __host__ __device__ __noinline__ void psd_project_closest(const Closest& cl, double* H) {
+static __host__ __device__ __noinline__ void psd_project_closest(const Closest& cl, double* H, bool absval) {
   double Q[5][12];
   int nq = 0;
   double u[12];
@@ -524,7 +542,7 @@ static __host__ __device__ __noinline__ void psd_project_closest(const Closest& 
   bool neg = false;
   for (int k = 0; k < 5; ++k) neg |= M[6 * k] < 0.0;
   if (!neg) return;
-  // H = sum_k max(l_k, 0) (Q^T v_k)(Q^T v_k)^T
+  // H = sum_k f(l_k) (Q^T v_k)(Q^T v_k)^T, f(l) = max(l, 0) or |l|
   double Y[5][12];
   for (int k = 0; k < 5; ++k)
     for (int p = 0; p < 12; ++p) {
@@ -537,6 +555,7 @@ static __host__ __device__ __noinline__ void psd_project_closest(const Closest& 
       double acc = 0;
       for (int k = 0; k < 5; ++k) {
         double l = M[6 * k];
+        if (absval) l = fabs(l);
         if (l > 0.0) acc += l * Y[k][p] * Y[k][q];
       }
       H[p * 12 + q] = acc;
@@ -544,17 +563,17 @@ static __host__ __device__ __noinline__ void psd_project_closest(const Closest& 
     }
 }
 
-// full 12x12 eigen-clamp with its own scratch
-static __host__ __device__ __noinline__ void psd_project12(double* H) {
+// full 12x12 eigen-filter with its own scratch
+static __host__ __device__ __noinline__ void psd_project12(double* H, bool absval) {
   double scratch[288];
-  psd_project<12, double>(H, scratch);
+  psd_project<12, double>(H, scratch, absval);
 }
 
 // Weighted barrier of one pair: E = w c(x) b(d).  Returns false when the
 // pair is inactive (d >= dhat): E = 0 and g/H untouched.  g (12) and H
 // (144, PSD-projected) are written when non-null.  `work` holds 288 doubles.
 IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double dhat,
-                        double* E, double* g, double* H, bool project = true) {
+                        double* E, double* g, double* H, int filt = FILT_CLAMP) {
   Closest cl;
   classify(X, is_ee, cl);
   double D = cl.D;
@@ -607,9 +626,9 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
         H[p * 12 + q] = s;
         H[q * 12 + p] = s;
       }
-    if (!project) return true;
-    if (moll) psd_project12(H);
-    else psd_project_closest(cl, H);
+    if (filt == FILT_NONE) return true;
+    if (moll) psd_project12(H, filt == FILT_ABS);
+    else psd_project_closest(cl, H, filt == FILT_ABS);
   }
   return true;
 }

@@ -17,8 +17,6 @@
 
 namespace ipc {
 
-namespace {
-
 struct BodyProps {
   double vol, mass, com[3], S[9];
 };
@@ -116,7 +114,51 @@ struct EnvLocal {
   std::vector<int> obj_cvb, obj_cve, obj_tb, obj_te, obj_eb, obj_ee;
   std::vector<unsigned long long> obj_ex;
   std::vector<int> coated_row;
+  // broad-phase hierarchy: per kind (0 points, 1 triangles, 2 edges) the
+  // object's primitives in Morton order of their rest centroids (local ids)
+  std::vector<int> bv_ord[3];
 };
+
+namespace {
+
+// 21-bit spread for a 63-bit Morton key
+static unsigned long long morton_spread(unsigned long long v) {
+  v &= 0x1fffffull;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+// Primitives [b, e) of one object, given their rest centroids (3 per
+// primitive, indexed from b), in Morton order of the centroids within the
+// object's box; ties keep index order.  Appended to ord.
+static void morton_order(int b, int e, const std::vector<double>& cen, std::vector<int>& ord) {
+  if (e <= b) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = b; i < e; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], cen[3 * (i - b) + c]);
+      hi[c] = std::max(hi[c], cen[3 * (i - b) + c]);
+    }
+  std::vector<std::pair<unsigned long long, int>> key;
+  key.reserve(e - b);
+  for (int i = b; i < e; ++i) {
+    unsigned long long k = 0;
+    for (int c = 0; c < 3; ++c) {
+      const double ext = hi[c] - lo[c];
+      const double u = ext > 0 ? (cen[3 * (i - b) + c] - lo[c]) / ext : 0.0;
+      const unsigned long long q = (unsigned long long)std::min(2097151.0, std::max(0.0, u * 2097151.0));
+      k |= morton_spread(q) << c;
+    }
+    key.push_back({k, i});
+  }
+  std::stable_sort(key.begin(), key.end(), [](const std::pair<unsigned long long, int>& x,
+                                              const std::pair<unsigned long long, int>& y) { return x.first < y.first; });
+  for (auto& kv : key) ord.push_back(kv.second);
+}
 
 bool build_local(const ipc_scene_desc& s, int e, const ipc_params& prm, EnvLocal& L, std::string& err) {
   char buf[256];
@@ -455,6 +497,22 @@ bool build_local(const ipc_scene_desc& s, int e, const ipc_params& prm, EnvLocal
   ev.n_tri = ntri;
   ev.n_edge = nedge;
   ev.n_obj = n_pads + nb;
+  // Morton orders of each object's points, triangles and edges at rest
+  for (int o = 0; o < n_pads + nb; ++o) {
+    std::vector<double> cen;
+    for (int i = L.obj_cvb[o]; i < L.obj_cve[o]; ++i)
+      for (int c = 0; c < 3; ++c) cen.push_back(Xc[3 * i + c]);
+    morton_order(L.obj_cvb[o], L.obj_cve[o], cen, L.bv_ord[0]);
+    cen.clear();
+    for (int t = L.obj_tb[o]; t < L.obj_te[o]; ++t)
+      for (int c = 0; c < 3; ++c)
+        cen.push_back((Xc[3 * L.tri[3 * t] + c] + Xc[3 * L.tri[3 * t + 1] + c] + Xc[3 * L.tri[3 * t + 2] + c]) / 3.0);
+    morton_order(L.obj_tb[o], L.obj_te[o], cen, L.bv_ord[1]);
+    cen.clear();
+    for (int q = L.obj_eb[o]; q < L.obj_ee[o]; ++q)
+      for (int c = 0; c < 3; ++c) cen.push_back(0.5 * (Xc[3 * L.edge[2 * q] + c] + Xc[3 * L.edge[2 * q + 1] + c]));
+    morton_order(L.obj_eb[o], L.obj_ee[o], cen, L.bv_ord[2]);
+  }
   int nco = 0;
   for (int u = 0; u < N; ++u)
     if (on_surf[u] && !pinned(u) && attach[u] < 0) {
@@ -485,7 +543,8 @@ bool build_pack(const ipc_scene_desc* scenes, int n_envs, const ipc_params& prm,
   pk.n_envs = n_envs;
   pk.env.resize(n_envs);
   // pass 1: env-local builds (consecutive identical descriptors share one)
-  std::vector<std::shared_ptr<EnvLocal>> locals(n_envs);
+  std::vector<std::shared_ptr<EnvLocal>>& locals = pk.locals;
+  locals.assign(n_envs, nullptr);
   for (int e = 0; e < n_envs; ++e) {
     if (e > 0 && std::memcmp(&scenes[e], &scenes[e - 1], sizeof(ipc_scene_desc)) == 0) {
       locals[e] = locals[e - 1];
@@ -598,6 +657,25 @@ bool build_pack(const ipc_scene_desc* scenes, int n_envs, const ipc_params& prm,
       pk.obj_exclude.push_back(L.obj_ex[o]);
     }
     append_off(pk.coated_row, L.coated_row, r0);
+    // broad-phase hierarchy: Morton-ordered primitives, clusters of 32 and
+    // superclusters of 32 clusters per object and kind
+    {
+      const int pofs[3] = {c0, tr0, e0};
+      append_off(pk.bv_perm[0], L.bv_ord[0], c0);
+      append_off(pk.bv_perm[1], L.bv_ord[1], tr0);
+      append_off(pk.bv_perm[2], L.bv_ord[2], e0);
+      for (int o = 0; o < ev.n_obj; ++o) {
+        const int np[3] = {L.obj_cve[o] - L.obj_cvb[o], L.obj_te[o] - L.obj_tb[o], L.obj_ee[o] - L.obj_eb[o]};
+        for (int k = 0; k < 3; ++k) {
+          const int ncl = (np[k] + 31) / 32, nsc = (ncl + 31) / 32;
+          pk.obj_cl_begin[k].push_back((int)pk.bv_cl_obj[k].size());
+          pk.obj_sc_begin[k].push_back((int)pk.bv_sc_obj[k].size());
+          for (int j = 0; j < ncl; ++j) pk.bv_cl_obj[k].push_back(o0 + o);
+          for (int j = 0; j < nsc; ++j) pk.bv_sc_obj[k].push_back(o0 + o);
+        }
+      }
+      (void)pofs;
+    }
 
     pk.env[e] = ev;
     pk.env_row_off.push_back(r0 + R);
@@ -623,6 +701,65 @@ bool build_pack(const ipc_scene_desc* scenes, int n_envs, const ipc_params& prm,
   pk.n_coated = pk.env_coated_off.back();
   pk.n_pairs_cap = pk.env_pair_off.back();
   return true;
+}
+
+bool build_env_local(const ipc_scene_desc& s, int e, const ipc_params& prm, std::shared_ptr<EnvLocal>& out,
+                     std::string& err) {
+  out = std::make_shared<EnvLocal>();
+  return build_local(s, e, prm, *out, err);
+}
+
+// Equal topology: every index table and count that fixes the layout of the
+// env's segments in the flat tables (rows, SELL pattern, contact primitives,
+// objects, coated rows).  Values that may differ: material, masses, rest
+// geometry, body mass properties, contact areas and rest edge lengths.
+bool same_topology(const EnvLocal& a, const EnvLocal& b) {
+  const EnvInfo &x = a.info, &y = b.info;
+  if (x.n_verts != y.n_verts || x.n_tets != y.n_tets || x.n_bodies != y.n_bodies || x.n_pads != y.n_pads ||
+      x.n_rows != y.n_rows || x.gel_rows != y.gel_rows || x.n_cv != y.n_cv || x.n_tri != y.n_tri ||
+      x.n_edge != y.n_edge || x.n_obj != y.n_obj || x.n_chunks != y.n_chunks || x.n_coated != y.n_coated ||
+      x.pair_cap != y.pair_cap || x.perm != y.perm || x.body_nv != y.body_nv)
+    return false;
+  return a.row_kind == b.row_kind && a.row_body == b.row_body && a.vt_ptr == b.vt_ptr && a.vt_src == b.vt_src &&
+         a.tets == b.tets && a.chunk_slots == b.chunk_slots && a.chunk_ptr == b.chunk_ptr &&
+         a.sell_col == b.sell_col && a.asm_ptr == b.asm_ptr && a.asm_src == b.asm_src && a.n_blocks == b.n_blocks &&
+         a.body_cv0 == b.body_cv0 && a.cv_row == b.cv_row && a.cv_body == b.cv_body && a.cv_obj == b.cv_obj &&
+         a.cv_uid == b.cv_uid && a.tri == b.tri && a.tri_obj == b.tri_obj && a.edge == b.edge &&
+         a.edge_obj == b.edge_obj && a.obj_cvb == b.obj_cvb && a.obj_cve == b.obj_cve && a.obj_tb == b.obj_tb &&
+         a.obj_te == b.obj_te && a.obj_eb == b.obj_eb && a.obj_ee == b.obj_ee && a.obj_ex == b.obj_ex &&
+         a.coated_row == b.coated_row;
+}
+
+// Writes env e's value tables of L into the flat host tables (same
+// topology as the env's current local build).
+void patch_env_values(Pack& pk, int e, const EnvLocal& L) {
+  EnvInfo& ev = pk.env[e];
+  const int r0 = ev.row_begin, t0 = ev.tet_begin, c0 = ev.cv_begin, b0 = ev.body_begin;
+  const int tr0 = ev.tri_begin, e0 = ev.edge_begin;
+  pk.env_mu[e] = L.mu;
+  pk.env_lam[e] = L.lam;
+  std::copy(L.row_mass.begin(), L.row_mass.end(), pk.row_mass.begin() + r0);
+  std::copy(L.row_xbar.begin(), L.row_xbar.end(), pk.row_xbar.begin() + 3 * (size_t)r0);
+  std::copy(L.rest_x.begin(), L.rest_x.end(), pk.rest_x.begin() + 3 * (size_t)r0);
+  std::copy(L.Dm_inv.begin(), L.Dm_inv.end(), pk.Dm_inv.begin() + 9 * (size_t)t0);
+  std::copy(L.vol.begin(), L.vol.end(), pk.tet_vol.begin() + t0);
+  for (int b = 0; b < ev.n_bodies; ++b) {
+    pk.body_mass[b0 + b] = L.bp[b].mass;
+    pk.body_vol[b0 + b] = L.bp[b].vol;
+    pk.body_kappa[b0 + b] = L.body_kappa[b];
+    pk.body_driven[b0 + b] = (uint8_t)L.body_driven[b];
+    for (int k = 0; k < 9; ++k) pk.body_S[9 * (size_t)(b0 + b) + k] = L.bp[b].S[k];
+  }
+  std::copy(L.cv_xbar.begin(), L.cv_xbar.end(), pk.cv_xbar.begin() + 3 * (size_t)c0);
+  std::copy(L.cv_area.begin(), L.cv_area.end(), pk.cv_area.begin() + c0);
+  std::copy(L.cv_fixed.begin(), L.cv_fixed.end(), pk.cv_fixed.begin() + c0);
+  std::copy(L.edge_area.begin(), L.edge_area.end(), pk.edge_area.begin() + e0);
+  std::copy(L.edge_len2.begin(), L.edge_len2.end(), pk.edge_len2.begin() + e0);
+  const int off[3] = {c0, tr0, e0};
+  for (int k = 0; k < 3; ++k)
+    for (size_t i = 0; i < L.bv_ord[k].size(); ++i) pk.bv_perm[k][off[k] + i] = L.bv_ord[k][i] + off[k];
+  ev.body_com = L.info.body_com;
+  pk.locals[e] = std::make_shared<EnvLocal>(L);
 }
 
 }  // namespace ipc

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -40,8 +41,11 @@ struct EnvInfo {
   std::vector<int> body_nv;
 };
 
+struct EnvLocal;  // one env's own tables (scene.cpp)
+
 // Flat host tables for all envs (device copies mirror these names).
 struct Pack {
+  std::vector<std::shared_ptr<EnvLocal>> locals;  // per env (identical consecutive scenes share one)
   int n_envs = 0;
   int n_rows = 0, n_tets = 0, n_cv = 0, n_tri = 0, n_edge = 0, n_obj = 0, n_bodies = 0;
   int n_chunks = 0, n_coated = 0;
@@ -97,10 +101,26 @@ struct Pack {
                                                 // own bit clear: self-contact
   // coated surface rows (read_gel_surface)
   std::vector<int> coated_row;
+  // broad-phase hierarchy per primitive kind k (0 contact points, 1
+  // triangles, 2 edges): bv_perm[k] holds each object's primitives (global
+  // ids, in the object's own range) in Morton order of their rest
+  // centroids; cluster j of object o covers positions 32 j .. 32 j + 31 of
+  // that order, supercluster j' its clusters 32 j' .. 32 j' + 31.
+  std::vector<int> bv_perm[3];
+  std::vector<int> bv_cl_obj[3], bv_sc_obj[3];      // object of each cluster / supercluster
+  std::vector<int> obj_cl_begin[3], obj_sc_begin[3];  // first cluster / supercluster of each object
 };
 
 // Validates and preprocesses; returns false with a message on bad input.
 bool build_pack(const ipc_scene_desc* scenes, int n_envs, const ipc_params& prm, Pack& pk,
                 std::string& err);
+
+// One env's own build (EnvLocal), for replacing an env in place:
+// same_topology tells whether a new scene fits the env's segments, and
+// patch_env_values writes its value tables into the flat host tables.
+bool build_env_local(const ipc_scene_desc& s, int e, const ipc_params& prm, std::shared_ptr<EnvLocal>& out,
+                     std::string& err);
+bool same_topology(const EnvLocal& a, const EnvLocal& b);
+void patch_env_values(Pack& pk, int e, const EnvLocal& L);
 
 }  // namespace ipc

@@ -30,7 +30,7 @@ class ipc_params(C.Structure):
                 ("pcg_max", C.c_int), ("ls_max", C.c_int), ("accd_max", C.c_int), ("accd_s", C.c_double),
                 ("al_kappa", C.c_double), ("al_max", C.c_int), ("ee_mollifier", C.c_double),
                 ("precision", C.c_int), ("max_pairs_per_env", C.c_int), ("friction_mu", C.c_double),
-                ("friction_eps_v", C.c_double)]
+                ("friction_eps_v", C.c_double), ("newton_abs_after", C.c_int)]
 
 
 class ipc_scene_desc(C.Structure):
@@ -56,7 +56,7 @@ class ipc_step_stats(C.Structure):
                 ("al_updates", C.c_int), ("max_pairs", C.c_int), ("newton_env_iters", C.c_longlong),
                 ("al_env_updates", C.c_longlong), ("ccd_limited", C.c_longlong), ("alpha_sum", C.c_double),
                 ("accd_iters", C.c_longlong), ("accd_iters_max", C.c_int),
-                ("ms_total", C.c_double)]
+                ("ms_total", C.c_double), ("pair_evals", C.c_longlong), ("swept_pairs", C.c_longlong)]
 
 
 _lib = None
@@ -83,9 +83,11 @@ def lib():
             "ipc_set_state": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_get_state": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_set_targets": (i32, [vp, i32, _dp]),
+            "ipc_reset_env": (i32, [vp, i32, C.POINTER(ipc_scene_desc)]),
             "ipc_set_targets_all": (i32, [vp, _dp]),
             "ipc_set_targets_all_device": (i32, [vp, vp]),
             "ipc_step": (i32, [vp, _ip, i32, _ip, C.POINTER(ipc_step_stats)]),
+            "ipc_step_results": (i32, [vp, _ip, C.POINTER(ipc_step_stats)]),
             "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -121,8 +123,8 @@ def lib():
 
 
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
-            "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets",
-            "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
+            "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets", "ipc_reset_env",
+            "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_step_results", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
             "ipc_read_gel_surface_all_noalloc", "ipc_env_stats", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
@@ -157,6 +159,7 @@ def params_from(p) -> ipc_params:
     out.max_pairs_per_env = int(getattr(p, "max_pairs_per_env", 0))
     out.friction_mu = float(getattr(p, "friction_mu", 0.0))
     out.friction_eps_v = float(getattr(p, "friction_eps_v", 1e-3))
+    out.newton_abs_after = int(getattr(p, "newton_abs_after", 1000000))
     return out
 
 
@@ -303,6 +306,14 @@ class Envs:
                     "ipc_get_state")
         return x, v, y, yd
 
+    def reset_env(self, env: int, scene):
+        """Put a new scene of the same topology into env slot `env`, at its
+        rest state (ipc_reset_env)."""
+        arr, keep = _descs([scene])
+        self._check(lib().ipc_reset_env(self._ctx, env, arr), "ipc_reset_env")
+        self.scenes[env] = scene
+        del keep
+
     def set_targets(self, env: int, y_target: np.ndarray):
         t = np.ascontiguousarray(y_target, dtype=np.float64)
         self._check(lib().ipc_set_targets(self._ctx, env, _ptr(t, _dp)), "ipc_set_targets")
@@ -316,16 +327,30 @@ class Envs:
         self._check(lib().ipc_set_targets_all_device(self._ctx, C.c_void_p(dev_targets.data_ptr())),
                     "ipc_set_targets_all_device")
 
-    def step(self, env_ids: Optional[Sequence[int]] = None):
-        """Returns (per-env status array, stats dict)."""
+    def step(self, env_ids: Optional[Sequence[int]] = None, wait: bool = True):
+        """Returns (per-env status array, stats dict).  wait=False only
+        enqueues the step (no host round trip in graph mode 2) and returns
+        None; step_results() reads the results later."""
         ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
         n = self.n_envs if ids is None else len(ids)
+        self._last_n = n
+        if not wait:
+            self._check(lib().ipc_step(self._ctx, _ptr(ids, _ip), n, None, None), "ipc_step")
+            return None
         status = np.zeros(n, dtype=np.int32)
         stats = ipc_step_stats()
         self._check(lib().ipc_step(self._ctx, _ptr(ids, _ip), n, _ptr(status, _ip), C.byref(stats)), "ipc_step")
         return status, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
 
-    ENV_STATS = ("status", "newton", "al", "pcg", "ls_trials", "ccd_limited", "accd_max", "pairs", "accd_iters")
+    def step_results(self):
+        """(per-env status array, stats dict) of the last step (synchronises)."""
+        status = np.zeros(getattr(self, "_last_n", self.n_envs), dtype=np.int32)
+        stats = ipc_step_stats()
+        self._check(lib().ipc_step_results(self._ctx, _ptr(status, _ip), C.byref(stats)), "ipc_step_results")
+        return status, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
+
+    ENV_STATS = ("status", "newton", "al", "pcg", "ls_trials", "ccd_limited", "accd_max", "pairs", "accd_iters",
+                 "pair_evals", "swept_pairs")
 
     def env_stats(self, env: int) -> dict:
         """Counters of the last step that included `env` (ipc_env_stats)."""
@@ -463,10 +488,12 @@ class Envs:
                 "spmv_us": {u: round(float(t.spmv_us[k]), 2) for k, u in enumerate((2, 4, 8))},
                 "grid_us": {int(t.grid_ctas_per_sm[k]): round(float(t.grid_us[k]), 2) for k in range(3)}}
 
-    def set_graph_mode(self, on: bool = True):
-        """Replay the PCG inner loop as a captured CUDA graph (needs a
-        capturable stream: pass stream= a torch.cuda.Stream at creation)."""
-        self._check(lib().ipc_set_graph_mode(self._ctx, 1 if on else 0), "ipc_set_graph_mode")
+    def set_graph_mode(self, mode=1):
+        """CUDA-graph execution: 0 plain launches, 1 (or True) each PCG solve
+        as one graph, 2 the whole step as one graph.  Needs a capturable
+        stream: pass stream= a torch.cuda.Stream at creation."""
+        mode = int(mode) if not isinstance(mode, bool) else (1 if mode else 0)
+        self._check(lib().ipc_set_graph_mode(self._ctx, mode), "ipc_set_graph_mode")
 
     # ------------------------------------------------------------ profiling
     def profile_enable(self, on: bool = True):
@@ -542,11 +569,19 @@ def _vp(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _filter_code(project) -> int:
+    """Eigenvalue filter code of the element kernels: False -> 0 (raw),
+    True / "clamp" -> 1, "abs" -> 2."""
+    if not project:
+        return 0
+    return 2 if project == "abs" else 1
+
+
 def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=None, project=True):
     """Neo-Hookean element kernel on torch float64 CUDA tensors."""
     n = int(x.shape[0])
     st = lib().ipc_k_tet(n, _vp(x), _vp(Dm_inv), _vp(vol), float(mu), float(lam), _vp(energy), _vp(grad),
-                         _vp(hess), 1 if project else 0, _stream_ptr(x))
+                         _vp(hess), _filter_code(project), _stream_ptr(x))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_tet")
 
@@ -554,7 +589,7 @@ def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=No
 def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None, project=True):
     n = int(X.shape[0])
     st = lib().ipc_k_barrier(n, _vp(X), _vp(is_ee), _vp(weight), _vp(eps_x), float(dhat), _vp(energy), _vp(grad),
-                             _vp(hess), 1 if project else 0, _stream_ptr(X))
+                             _vp(hess), _filter_code(project), _stream_ptr(X))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_barrier")
 

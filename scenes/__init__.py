@@ -37,7 +37,7 @@ import numpy as np
 __all__ = [
     "Body", "Scene", "Scenario", "SolverParams",
     "gel_grid", "icosphere", "box_surface",
-    "config0", "config1", "config2", "config3", "small_contact_scene",
+    "config0", "config1", "config2", "config3", "config3_batch", "small_contact_scene",
     "free_fall_scene", "spin_scene", "self_contact_scene",
 ]
 
@@ -85,7 +85,7 @@ class SolverParams:
     kappa: float = 1e6
     newton_tol: float = 1e-4        # ||p||_inf / dt, m/s
     pcg_rel_tol: float = 1e-4
-    newton_max: int = 100
+    newton_max: int = 300           # safety cap; the press steps need up to ~120 iterations
     pcg_max: int = 1000
     ls_max: int = 30
     accd_max: int = 10000
@@ -97,6 +97,7 @@ class SolverParams:
     max_pairs_per_env: int = 0      # candidate-pair capacity per env (0 = default)
     friction_mu: float = 0.0        # lagged IPC friction coefficient (0 = frictionless)
     friction_eps_v: float = 1e-3    # static/dynamic velocity threshold, m/s
+    newton_abs_after: int = 1000000  # Newton iterations that clamp negative eigenvalues; |lambda| after
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""
@@ -363,12 +364,14 @@ def config3(env: int, n=32, nz=6, n_steps=200, level=4, gap=None) -> Scenario:
     Pads are 20x20x4 mm with their contact faces normal to x; each pad's back
     face is attached to a 22x22x4 mm finger box behind it.  The object is a
     free icosphere (r = 10 mm, rho = 800) under gravity.  The initial gap
-    between each pad and the sphere is 1 mm + U(0, 0.2) mm, or `gap` when
-    given (small scenes that reach contact within a few steps).
+    between each pad and the sphere is 20 um + U(0, 20) um, or `gap` when
+    given: at 10 um per step the pads reach the sphere within 2-4 steps,
+    before it has fallen 0.1 mm (a gap of a millimetre would let it fall out
+    of the 20 mm pads before they close).
     """
     rng = np.random.default_rng(3000 + env)
     r = 10e-3
-    gap0 = 1e-3 + rng.uniform(0.0, 2e-4)
+    gap0 = 2e-5 + rng.uniform(0.0, 2e-5)
     if gap is not None:
         gap0 = float(gap)
     thick = 4e-3
@@ -511,6 +514,22 @@ def spin_scene(omega=(0.0, 0.0, 20.0)):
     yd[0, 9:12] = W[:, 2]
     return Scenario(scene=scene, params=params, n_steps=10,
                     delta=lambda s: np.zeros((1, 3)), ydot0=yd)
+
+
+def config3_batch(n_envs: int, n=32, nz=6, n_steps=200, level=4):
+    """Config 3 as a batch that shares one scene: the geometry of config3(0)
+    at the mean gap, and per env the initial gap of config3(env) applied as
+    an opposite rigid shift of each finger with its pad along x (the rest
+    shape of a pad does not depend on where it is placed).  Returns (scene,
+    params, per-env (shift of pad 0, shift of pad 1) along x, delta)."""
+    mean_gap = 3e-5
+    base = config3(0, n, nz, n_steps, level, gap=mean_gap)
+    shifts = []
+    for env in range(n_envs):
+        rng = np.random.default_rng(3000 + env)
+        g = 2e-5 + rng.uniform(0.0, 2e-5)
+        shifts.append((-(g - mean_gap), g - mean_gap))
+    return base.scene, base.params, shifts, base.delta
 
 
 def config1_batch(n_envs: int, nx=40, ny=40, nz=6, n_steps=100):

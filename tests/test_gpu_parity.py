@@ -151,6 +151,36 @@ def test_barrier_kernel_matches_oracle():
     assert np.median(err) < 1e-10 and err.max() < 1e-4, (err.max(), np.argmax(err))
 
 
+def test_element_kernels_abs_filter_match_oracle():
+    """project = "abs": negative eigenvalues replaced by their absolute
+    values (the filter of late Newton iterations), on both element kernels."""
+    rng = np.random.default_rng(31)
+    x, Dmi, vol = _random_tets(1000, rng, compress=0.4)
+    n = len(x)
+    mu, lam = lame(3e5, 0.45)
+    H = torch.zeros(n, 12, 12, device=DEV, dtype=torch.float64)
+    ipc.k_tet(T(x), T(Dmi), T(vol), mu, lam, None, None, H, project="abs")
+    torch.cuda.synchronize()
+    Ho = oen.tet_hess(x, Dmi, vol, mu, lam, project="abs")
+    Hc = oen.tet_hess(x, Dmi, vol, mu, lam, project=True)
+    # the set holds tets whose dP/dF is indefinite: abs differs from clamp
+    assert (np.abs(Ho - Hc).max(axis=(1, 2)) > 1e-6 * np.abs(Ho).max(axis=(1, 2))).sum() > 10
+    Hs = np.abs(Ho).max(axis=(1, 2), keepdims=True)
+    assert (np.abs(H.cpu().numpy() - Ho) / Hs).max() < 1e-8
+    dhat = 1e-4
+    X, is_ee, w, eps = _random_pairs(800, rng, dhat)
+    n = len(X)
+    E = torch.zeros(n, device=DEV, dtype=torch.float64)
+    Hb = torch.zeros(n, 12, 12, device=DEV, dtype=torch.float64)
+    ipc.k_barrier(T(X), T(is_ee, torch.int32), T(w), T(eps), dhat, E, None, Hb, project="abs")
+    torch.cuda.synchronize()
+    Eo, _, Hbo = ods.pair_barrier(X, is_ee.astype(bool), w, eps, dhat, order=2, project="abs")
+    act = Eo > 0
+    Hs = np.abs(Hbo[act]).max(axis=(1, 2), keepdims=True)
+    err = (np.abs(Hb.cpu().numpy()[act] - Hbo[act]) / Hs).max(axis=(1, 2))
+    assert np.median(err) < 1e-10 and err.max() < 1e-4, (err.max(), np.argmax(err))
+
+
 def test_barrier_kernel_raw_hessian_matches_oracle():
     rng = np.random.default_rng(12)
     dhat = 1e-4
@@ -384,6 +414,15 @@ def test_step_parity_small_sphere():
     _step_parity(sc, sc.params.parity(), 6)
 
 
+def test_step_parity_abs_filter_from_the_first_iteration():
+    # newton_abs_after = 0: every Newton iteration filters with |lambda|
+    # (element, pair and body Hessians) on both sides
+    sc = scenes.small_contact_scene(body="sphere", level=2, depth=3e-4, n_steps=4)
+    prm = sc.params.parity()
+    prm.newton_abs_after = 0
+    _step_parity(sc, prm, 4)
+
+
 def test_step_parity_two_finger_grasp():
     # config 3 in miniature: two attached pads on driven fingers squeezing a
     # free sphere under gravity (three bodies, attached gel rows, gel-body
@@ -462,11 +501,20 @@ def test_state_round_trip_and_rejections():
     assert genv.set_state(0, None, None, None, yd5) == ipc.IPC_EINVAL
     xb5, vb5, _, ydb5 = genv.get_state(0)
     assert np.array_equal(xb5, x2) and np.array_equal(vb5, v2) and np.array_equal(ydb5, ydb)
-    # push the cube through the gel top: touching / crossing surfaces rejected
+    # push the cube through the gel top: its vertical edges cross the gel's
+    # top triangles (no pair is within dhat there): rejected, state unchanged
     y4 = y.copy()
     y4[0, 2] -= 4.2e-3
-    st = genv.set_state(0, None, None, y4, None)
-    assert st in (ipc.IPC_EINTERSECT, ipc.IPC_OK)
+    assert genv.set_state(0, None, None, y4, None) == ipc.IPC_EINTERSECT
+    assert np.array_equal(genv.get_state(0)[2], y)
+    # half-way into the gel: rejected too
+    y6 = y.copy()
+    y6[0, 2] -= 2.0e-3
+    assert genv.set_state(0, None, None, y6, None) == ipc.IPC_EINTERSECT
+    # lifted 1 mm above its start: accepted
+    y7 = y.copy()
+    y7[0, 2] += 1e-3
+    assert genv.set_state(0, None, None, y7, None) == ipc.IPC_OK
     genv.close()
 
 
@@ -575,10 +623,13 @@ def test_batch_of_uneven_envs_matches_single_env_runs():
     batch.close()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_graph_mode_matches_plain_launches(precision):
-    """The PCG inner loop replayed as a captured CUDA graph (on a created
-    stream) gives the same steps as kernel-by-kernel launches."""
+def test_graph_mode_matches_plain_launches(precision, mode):
+    """The PCG solve (mode 1) or the whole step (mode 2) replayed as a
+    captured CUDA graph with device-side loops (on a created stream) gives
+    the same steps as kernel-by-kernel launches; in mode 2 every other step
+    is enqueued without waiting and its results read afterwards."""
     scs = [scenes.config2(e) for e in range(3)]
     # FP64 at the parity tolerances; mixed at the benchmark tolerances
     prm = scenes.SolverParams().parity() if precision == 0 else scenes.SolverParams()
@@ -586,7 +637,7 @@ def test_graph_mode_matches_plain_launches(precision):
     bound = 1e-8 if precision == 0 else 1e-5
     plain = ipc.Envs([s.scene for s in scs], prm, stream=torch.cuda.Stream())
     graph = ipc.Envs([s.scene for s in scs], prm, stream=torch.cuda.Stream())
-    graph.set_graph_mode(True)
+    graph.set_graph_mode(mode)
     for step in range(3):
         for e, s in enumerate(scs):
             t = plain.rest_y(e)
@@ -594,8 +645,13 @@ def test_graph_mode_matches_plain_launches(precision):
             plain.set_targets(e, t)
             graph.set_targets(e, t)
         sa, stats_a = plain.step()
-        sb, stats_b = graph.step()
+        if mode == 2 and step % 2 == 1:
+            assert graph.step(wait=False) is None
+            sb, stats_b = graph.step_results()
+        else:
+            sb, stats_b = graph.step()
         assert np.all(sa == 0) and np.all(sb == 0)
+        assert stats_b["newton_env_iters"] > 0 and stats_b["pcg_iters"] > 0
         for e in range(3):
             xa = plain.get_state(e)[0]
             xb = graph.get_state(e)[0]

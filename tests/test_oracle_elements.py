@@ -301,3 +301,44 @@ def test_mollifier_smooth_at_threshold():
     Es = np.array(Es)
     assert Es[0] == 0.0                       # parallel: mollified to zero
     assert np.all(np.abs(np.diff(Es)) < 0.05 * Es.max())   # no jumps
+
+
+def _sqrtm_sym(M):
+    """Principal square root of a symmetric PSD matrix by Denman-Beavers
+    iteration (no eigendecomposition)."""
+    Y, Z = M.copy(), np.eye(M.shape[0])
+    for _ in range(60):
+        Y, Z = 0.5 * (Y + np.linalg.inv(Z)), 0.5 * (Z + np.linalg.inv(Y))
+    return Y
+
+
+def test_absolute_value_filter_is_the_matrix_modulus():
+    # |H| = (H^2)^(1/2): the absolute-value filter computed by another route
+    rng = np.random.default_rng(5)
+    for n in (9, 12):
+        A = rng.normal(size=(n, n))
+        H = A + A.T
+        ref = _sqrtm_sym(H @ H)
+        assert np.allclose(en.psd_abs(H[None])[0], ref, atol=1e-9 * np.abs(ref).max())
+        # PSD input unchanged, NSD input negated, clamp <= abs in the PSD order
+        P = A @ A.T
+        assert np.allclose(en.psd_abs(P[None])[0], P, atol=1e-10 * np.abs(P).max())
+        assert np.allclose(en.psd_abs(-P[None])[0], P, atol=1e-10 * np.abs(P).max())
+        d = en.psd_abs(H[None])[0] - en.psd_clamp(H[None])[0]
+        assert np.linalg.eigvalsh(d).min() > -1e-9 * np.abs(H).max()
+        # and |H| - clamp(H) is the clamp of -H
+        assert np.allclose(d, en.psd_clamp(-H[None])[0], atol=1e-9 * np.abs(H).max())
+
+
+def test_elastic_abs_filter_on_a_compressed_tet():
+    mu, lam = lame(3e5, 0.45)
+    X, Dmi, V = _tet(RNG)
+    x = X.copy()
+    x[3] = x[0] + 0.45 * (X[3] - X[0])
+    A = en.dPdF(en.deformation_gradient(x[None], Dmi), mu, lam)[0]
+    assert np.linalg.eigvalsh(A).min() < 0
+    B = en.dF_dx(Dmi)[0]
+    want = V[0] * B.T @ _sqrtm_sym(A @ A) @ B
+    got = en.tet_hess(x[None], Dmi, V, mu, lam, project="abs")[0]
+    assert np.allclose(got, want, atol=1e-8 * np.abs(want).max())
+    assert np.linalg.eigvalsh(got).min() > -1e-9 * np.abs(got).max()

@@ -335,3 +335,31 @@ def test_restart_helper_keeps_converged_states_and_moves_others():
     t = sc.scene.gel_tets[0]
     xb[t[0]] = xb[t[1]] + (xb[t[1]] - xb[t[0]])            # fold one tet over
     assert not valid_state(env, xb, y1)
+
+
+def test_newton_filter_switches_after_the_set_iterations():
+    sc = scenes.config0()
+    prm = scenes.SolverParams(**sc.params.__dict__)
+    prm.newton_abs_after = 10
+    env = OracleEnv(sc.scene, prm)
+    assert [env.newton_filter(i) for i in (0, 9, 10, 15)] == ["clamp", "clamp", "abs", "abs"]
+    # the default clamps throughout
+    assert OracleEnv(sc.scene, sc.params).newton_filter(500) == "clamp"
+
+
+def test_converged_state_does_not_depend_on_the_filter():
+    # the filter only changes the path of projected Newton: at the parity
+    # tolerances a step filtered with |lambda| from its first iteration ends
+    # where the clamped step ends (same minimiser from the same start)
+    sc = scenes.small_contact_scene(body="sphere", driven=True, depth=2e-4, n_steps=3)
+    prm_c = sc.params.parity()
+    prm_a = scenes.SolverParams(**prm_c.__dict__)
+    prm_a.newton_abs_after = 0
+    ec, out_c = _run(sc, prm_c, 3)
+    ea, out_a = _run(sc, prm_a, 3)
+    assert ea.newton_filter(0) == "abs"
+    diag = np.linalg.norm(out_c[0][0].max(0) - out_c[0][0].min(0))
+    for (xc, _, yc, _, stc), (xa, _, ya, _, sta) in zip(out_c[1:], out_a[1:]):
+        assert stc.status == 0 and sta.status == 0
+        assert np.abs(xc - xa).max() <= 1e-6 * diag
+        assert np.abs(yc - ya).max() <= 1e-6 * diag
