@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed path (profiling runs); no FP64 comparison")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "serving", "uneven", "self_contact", "grasp", "single"],
+                    choices=["batch", "serving", "uneven", "self_contact", "grasp", "single", "broadphase"],
                     help="batch: the uniform 256-env batch (default); serving: the Poisson request stream; "
                          "uneven: 512 config-2 envs of different sizes in one launch; "
                          "self_contact: 1024 two-block pads pressed together (gel self-contact); "
@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--req-steps", type=int, default=200, help="serving: steps per request")
     ap.add_argument("--max-resident", type=int, default=4096)
-    ap.add_argument("--max-cohort", type=int, default=256)
-    ap.add_argument("--max-cohorts", type=int, default=8)
+    ap.add_argument("--slots-per-pool", type=int, default=256, help="serving: env slots per size-class pool")
+    ap.add_argument("--max-pools", type=int, default=32)
     ap.add_argument("--no-graphs", action="store_true", help="serving: plain launches instead of PCG graphs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
@@ -628,9 +628,10 @@ def run_ours(args):
 
 def run_serving(args):
     """The serving stream: Poisson arrivals of config-2-style requests,
-    admitted into cohorts by free device memory, mixed precision, PCG inner
-    loop as captured CUDA graphs.  Compared with the same kind of requests
-    stepped one by one in plain FP64 (a bounded sample)."""
+    loaded into the env slots of resident per-size-class pools as slots free
+    up (memory-sized pools, one stream and host thread each), mixed
+    precision, whole steps as CUDA graphs.  Compared with the same kind of
+    requests stepped one by one in plain FP64 (a bounded sample)."""
     import torch
 
     import scenes
@@ -652,8 +653,8 @@ def run_serving(args):
     prm = scenes.SolverParams()
     prm.precision = 1
     eng = GpuEngine(prm, device=f"cuda:{local}", graphs=not args.no_graphs)
-    srv = Server(eng, max_resident=args.max_resident, max_cohort=args.max_cohort,
-                 max_cohorts=args.max_cohorts, keep_state=False)
+    srv = Server(eng, max_resident=args.max_resident, slots_per_pool=args.slots_per_pool,
+                 max_pools=args.max_pools, keep_state=False)
     clocks = ClockSampler(local)
     clocks.start()
     rep = srv.run(reqs, time_limit=args.serve_seconds, hard_limit=args.serve_hard)
@@ -680,8 +681,8 @@ def run_serving(args):
            "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": "serving: Poisson %.0f req/s of config-2-style envs x %d steps, window %.0f s"
                       % (args.rate, args.req_steps, args.serve_seconds),
-                      "max_resident": args.max_resident, "max_cohort": args.max_cohort,
-                      "max_cohorts": args.max_cohorts, "graphs": not args.no_graphs},
+                      "max_resident": args.max_resident, "slots_per_pool": args.slots_per_pool,
+                      "max_pools": args.max_pools, "graphs": not args.no_graphs},
            "latency_ms": {"p50": rep.step_ms_p50, "p99": rep.step_ms_p99},
            "serving": {k: v for k, v in summ.items()},
            "fp64_one_by_one": {"value": one, "unit": "env-steps/s", "step_ms_mean": float(np.mean(one_ms)),
@@ -906,6 +907,46 @@ def run_single(args):
     print(json.dumps(line), flush=True)
 
 
+def run_broadphase(args):
+    """Candidate-search time against surface size: one gel pad of n x n x 3
+    vertices with self-contact on (every pair of its own non-adjacent
+    primitives is a candidate query), n = 10, 20, 40, 80, and the level-4
+    icosphere of the grasp against a 32 x 32 x 6 pad; static and swept
+    searches from a perturbed state, per-call time from CUDA events.  The
+    brute-force search this replaces is quadratic in the pad's primitives."""
+    import torch
+
+    import scenes
+    from paper_2504_12908_b300 import ipc
+    from paper_2504_12908_b300.build import build
+    build()
+    rows = []
+    cases = [("pad %dx%dx3, self-contact" % (n, n), scenes.self_contact_pad(n)) for n in (10, 20, 40, 80)]
+    cases.append(("pad 32x32x6 + icosphere L4 (r = 10 mm)", scenes.pad_and_sphere(32, 6, 4)))
+    for name, sc in cases:
+        g = ipc.Envs([sc], scenes.SolverParams())
+        n_cv = sc.gel_x.shape[0] + sum(b.rest_x.shape[0] for b in sc.bodies)
+        rng = np.random.default_rng(7)
+        X = np.concatenate([sc.gel_x] + [b.rest_x for b in sc.bodies])
+        X = X + rng.normal(scale=2e-6, size=X.shape)
+        Xe = X + rng.normal(scale=1e-5, size=X.shape)
+        g.debug_pairs(0, X, Xe)
+        g.profile_enable(True)
+        g.profile_reset()
+        reps = 10
+        n_pairs = 0
+        for _ in range(reps):
+            n_pairs = len(g.debug_pairs(0, X, None))
+            g.debug_pairs(0, X, Xe)
+        prof = g.profile()
+        g.close()
+        ms = prof["broad_phase"][1] / (2 * reps)
+        rows.append({"case": name, "contact_vertices": int(n_cv), "ms_per_search": round(ms, 4),
+                     "static_candidates": int(n_pairs), "us_per_vertex": round(1e3 * ms / n_cv, 4)})
+    print(json.dumps({"metric": "broad-phase ms per candidate search", "unit": "ms", "data": "synthetic",
+                      "rows": rows}), flush=True)
+
+
 def run_uneven(args):
     """512 config-2 envs of different sizes stepped together: mixed vs plain
     FP64 on the same batch (press phase steps after the warm-up)."""
@@ -945,6 +986,8 @@ def main():
         run_grasp(args)
     elif args.workload == "single":
         run_single(args)
+    elif args.workload == "broadphase":
+        run_broadphase(args)
     else:
         run_ours(args)
 

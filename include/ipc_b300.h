@@ -422,6 +422,15 @@ long long ipc_launch_count(const ipc_ctx* ctx);
 ipc_status ipc_system_sizes(const ipc_ctx* ctx, int env, long long* real_blocks, long long* stored_blocks,
                             int* rows, int* tets);
 
+/* FP64 and FP32 fused multiply-add throughput of the current device in
+ * TFLOP/s (2 flops per FMA), each timed with CUDA events over one launch of
+ * independent FMA chains on every SM, on `stream` (synchronises it).
+ * scratch: device memory of at least SM count x 8 x 256 doubles (written).
+ * The denominators of the ALU rooflines of the FP64-bound kernels; touches
+ * no clock or power setting.  A property of this library, not the paper. */
+ipc_status ipc_fma_peaks(void* scratch, size_t scratch_bytes, double* fp64_tflops, double* fp32_tflops,
+                         void* stream);
+
 /* ---- element kernels on caller device buffers (no ctx) ----------------- */
 /* All pointers are device pointers; n elements; the call is asynchronous on
  * stream.  Returns IPC_EINVAL for n < 0 or NULL required pointers. */

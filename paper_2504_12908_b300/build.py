@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libipc_b300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["scene.cpp", "kernels_contact.cu", "kernels_solver.cu", "kernels_pcg.cu", "capi.cu", "noalloc.cu",
-           "tactile.cu"]
+           "tactile.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
                      "-Xptxas", "-O3", "--expt-relaxed-constexpr"]

@@ -29,12 +29,13 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 // ---- per-kernel-class launch counts and event timing
 enum Kc {
   KC_PREDICT, KC_CVPOS, KC_OBJBOX, KC_BROAD, KC_BARRIER, KC_TET, KC_BODY, KC_ASSEMBLE, KC_GRAD, KC_PRECOND,
-  KC_PCGINIT, KC_FRICSPMV, KC_SPMV, KC_PCGUPD, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC, KC_COUNT
+  KC_PCGINIT, KC_PAIRSPMV, KC_FRICSPMV, KC_SPMV, KC_PCGUPD, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC,
+  KC_COUNT
 };
-const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",      "obj_box",    "broad_phase", "barrier",
-                                 "tet_elastic",  "body_abd",    "assemble",   "gradient",    "precond",
-                                 "pcg_init",     "fric_matvec", "pcg_matvec", "pcg_update",
-                                 "newton_check", "accd",        "ls_energy",  "ls_update",   "misc"};
+const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",      "obj_box",     "broad_phase", "barrier",
+                                 "tet_elastic",  "body_abd",    "assemble",    "gradient",    "precond",
+                                 "pcg_init",     "pair_matvec", "fric_matvec", "pcg_matvec",  "pcg_update",
+                                 "newton_check", "accd",        "ls_energy",   "ls_update",   "misc"};
 
 cudaEvent_t take_ev(ipc_ctx* ctx) {
   if (!ctx->ev_free.empty()) {
@@ -255,7 +256,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.q4 = c.take<float4>((size_t)pk.n_rows);
   d.row_touch = c.take<uint8_t>((size_t)pk.n_rows);
   d.pcg_list = c.take<int>((size_t)pk.n_envs);
-  d.pcg_item_off = c.take<int>((size_t)pk.n_envs + 1);
+  d.pcg_pair_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_ctl = c.take<unsigned int>(8);
   d.step_ctl = c.take<unsigned int>(8);
@@ -443,7 +444,13 @@ constexpr int kPcgPoll = 16;  // host-driven path: PCG iterations between reads 
 int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
   const Dev& d = ctx->dev;
   long long l0 = ctx->launches;
+  // contact terms (side stream) beside the SELL mat-vec: both only read
+  // z_k and d_{k-1}
+  fork_side(ctx, s, 1);
+  cudaStream_t s0 = side_of(ctx, s, 0);
+  KL(ctx, KC_PAIRSPMV, [&] { return launch_pcg_pairs(d, s0); }, s0);
   KL(ctx, KC_SPMV, [&] { return launch_pcg_matvec(d, s); }, s);
+  join_side(ctx, s, 1);
   KL(ctx, KC_FRICSPMV, [&] { return launch_fric_spmv(d, s); }, s);
   KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, h, use_cond); }, s);
   return (int)(ctx->launches - l0);
@@ -838,6 +845,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   // persistent PCG grid: every resident CTA of the two PCG kernels
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
+  ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
 }
@@ -1282,6 +1290,7 @@ ipc_status ipc_debug_eval(ipc_ctx* ctx, int env, double* energy, double* grad, c
     KL(ctx, KC_MISC, [&] { return launch_debug_dir_from_rows(d, ctx->stream); });
     KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, ctx->stream, 0, 0); });
     KL(ctx, KC_SPMV, [&] { return launch_pcg_matvec(d, ctx->stream); });
+    KL(ctx, KC_PAIRSPMV, [&] { return launch_pcg_pairs(d, ctx->stream); });
     KL(ctx, KC_FRICSPMV, [&] { return launch_fric_spmv(d, ctx->stream); });
     KL(ctx, KC_MISC, [&] { return launch_debug_q_to_rows(d, ctx->stream); });
     if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;

@@ -122,12 +122,12 @@ struct Dev {
                                 // contact terms write the row's contact accumulator qc
   // device-side PCG work list (rebuilt on the device when an env stops):
   int* pcg_list;                // [n_envs] envs still in PCG
-  int* pcg_item_off;            // [n_envs + 1] prefix of their mat-vec work items
-                                // (128-row CTAs, then groups of 8 active pairs)
+  int* pcg_pair_off;            // [n_envs + 1] prefix of their groups of 8 active pairs
   int* pcg_row_off;             // [n_envs + 1] prefix of their 128-row CTAs
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] the list is stale
-  int pcg_grid;                 // CTAs of the persistent PCG kernels
+  int pcg_grid;                 // CTAs of the persistent PCG row kernels
+  int pcg_grid_pairs;           // CTAs of the persistent contact mat-vec
   unsigned int* step_ctl;       // per step (device-side loops): [0] Newton iterations done,
                                 // [1] trials of the current line search, [2] envs still in
                                 // Newton, [3] envs in a line search, [4] PCG iterations,

@@ -41,6 +41,7 @@ int launch_pcg_begin(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h,
 // one PCG iteration = mat-vec (+ friction mat-vec) + update; the update's
 // last CTA advances the iteration counter and, with use_cond, sets `h`
 int launch_pcg_matvec(const Dev& d, cudaStream_t s);
+int launch_pcg_pairs(const Dev& d, cudaStream_t s);
 int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond);
 // resident 128-thread CTAs per SM of the PCG kernels (grid = 148 x this)
 int pcg_ctas_per_sm(int prec, int unroll);

@@ -4,17 +4,20 @@
 // One PCG iteration is two persistent kernels over a device-side work list
 // of the envs still iterating:
 //   k_pcg_matvec: d_k = z_k + beta_k d_{k-1} (formed on the fly, written to
-//     the other direction buffer), q = A d_k over the SELL-32 matrix, and the
-//     contact terms H_c d_k of the env's active pairs (matrix-free, added to
-//     the accumulator qc); d_k . q summed per env (SELL part by CTA partials,
-//     contact part by atomics).
+//     the other direction buffer), q = A d_k over the SELL-32 matrix, d_k . q
+//     summed per env by CTA partials;
+//   k_pcg_pairs (beside it, on a side stream): the contact terms H_c d_k of
+//     the env's active pairs (matrix-free, added to the accumulator qc) and
+//     their part of d_k . q (atomics);
 //   k_pcg_update: alpha = r.z / d.q, p += alpha d, r -= alpha q, z = P^-1 r,
 //     r.z and r.r per env -> beta and the stop test.  The last CTA of the
 //     grid rebuilds the work list when stopped envs hold a quarter of its
 //     items, and (inside a CUDA graph) sets the loop's condition, so the
 //     whole solve runs without the host.
 // A work item is 128 consecutive rows of one env (one row per thread) or a
-// group of 8 active pairs of one env (16 lanes per pair).
+// group of 8 active pairs of one env (16 lanes per pair).  The two mat-vec
+// kernels are separate so that the row kernel keeps its small register
+// footprint (occupancy) and the few pair items overlap it.
 #include "common.cuh"
 #include "fpconv.cuh"
 #include "kernels.h"
@@ -49,8 +52,8 @@ __device__ __forceinline__ int env_row_ctas(const Dev& d, int e) { return (d.env
 __device__ __forceinline__ int env_active_pairs(const Dev& d, int e) { return min(ENVI(d, e, I_NACT), d.env_pair_cap[e]); }
 
 // Rebuild the work list from the envs' I_PCG flags (one CTA, blockDim a
-// multiple of 32): list order is env order; row items of an env, then its
-// pair groups.
+// multiple of 32): list order is env order; per listed env the prefix of
+// its 128-row items and of its groups of 8 active pairs.
 __device__ void build_list(const Dev& d) {
   __shared__ int wsum[3][32];
   __shared__ int carry[3];
@@ -63,7 +66,7 @@ __device__ void build_list(const Dev& d) {
     int v[3];
     v[0] = on ? 1 : 0;
     v[1] = on ? env_row_ctas(d, e) : 0;
-    v[2] = on ? v[1] + (env_active_pairs(d, e) + 7) / 8 : 0;
+    v[2] = on ? (env_active_pairs(d, e) + 7) / 8 : 0;
     int inc[3];
     for (int k = 0; k < 3; ++k) {
       inc[k] = v[k];
@@ -90,7 +93,7 @@ __device__ void build_list(const Dev& d) {
     if (on) {
       d.pcg_list[ex[0]] = e;
       d.pcg_row_off[ex[0]] = ex[1];
-      d.pcg_item_off[ex[0]] = ex[2];
+      d.pcg_pair_off[ex[0]] = ex[2];
     }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1)
@@ -99,7 +102,7 @@ __device__ void build_list(const Dev& d) {
   }
   if (threadIdx.x == 0) {
     d.pcg_row_off[carry[0]] = carry[1];
-    d.pcg_item_off[carry[0]] = carry[2];
+    d.pcg_pair_off[carry[0]] = carry[2];
     d.pcg_ctl[C_LEN] = carry[0];
     d.pcg_ctl[C_LIVE] = carry[0];
     d.pcg_ctl[C_DEAD] = 0;
@@ -175,15 +178,27 @@ __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT bet
   const int* __restrict__ colp = d.sell_col + base + lane;
   HT ax = 0, ay = 0, az = 0;
   int sl = 0;
+  // the column indices of the next group of U slots are loaded one group
+  // ahead, so that a group's gathers go out together with its value loads
+  // (one memory round trip per group instead of a column -> gather chain)
+  int cn[U];
+  if (U <= slots) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) cn[u] = colp[u * 32];
+  }
   for (; sl + U <= slots; sl += U) {
     int c[U];
     HT A[U][9];
 #pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = colp[(sl + u) * 32];
+    for (int u = 0; u < U; ++u) c[u] = cn[u];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int k = 0; k < 9; ++k) A[u][k] = val[(long long)(sl + u) * 288 + k * 32];
+    if (sl + 2 * U <= slots) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) cn[u] = colp[(sl + U + u) * 32];
+    }
     V3<HT> w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = Dk<HT>::row(d, c[u], beta, ob);
@@ -357,20 +372,55 @@ __global__ void k_pcg_begin(Dev d, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, d.pcg_ctl[C_LIVE] > 0 ? 1u : 0u);
 }
 
+// the item's env, local index and the env's per-iteration scalar, found by
+// thread 0 and shared with the CTA (one lookup per 128-row item)
+struct ItemInfo {
+  int e, local;
+  double s;
+};
+
 template <class HT, int U>
 __global__ void __launch_bounds__(128) k_pcg_matvec(Dev d) {
+  __shared__ ItemInfo it;
   const int n_list = (int)d.pcg_ctl[C_LEN];
-  const int n_items = d.pcg_item_off[n_list];
+  const int n_items = d.pcg_row_off[n_list];
   const int nb = pcg_new_buf(d), ob = nb ^ 1;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int li = list_find(d.pcg_item_off, n_list, item);
-    const int e = d.pcg_list[li];
-    if (!ENVI(d, e, I_PCG)) continue;                // stopped; still listed
-    const int local = item - d.pcg_item_off[li];
-    const int n_cta = env_row_ctas(d, e);
-    const HT beta = (HT)ENVS(d, e, S_PBETA);
-    if (local < n_cta) matvec_rows<HT, U>(d, e, (d.env_row_off[e] >> 7) + local, beta, ob, nb);
-    else matvec_pairs<HT>(d, e, local - n_cta, beta, ob);
+    __syncthreads();  // the previous item is done with `it`
+    if (threadIdx.x == 0) {
+      const int li = list_find(d.pcg_row_off, n_list, item);
+      const int e = d.pcg_list[li];
+      it.e = ENVI(d, e, I_PCG) ? e : -1;               // stopped envs stay listed until a rebuild
+      it.local = item - d.pcg_row_off[li];
+      it.s = ENVS(d, e, S_PBETA);
+    }
+    __syncthreads();
+    const int e = it.e;
+    if (e < 0) continue;
+    matvec_rows<HT, U>(d, e, (d.env_row_off[e] >> 7) + it.local, (HT)it.s, ob, nb);
+  }
+}
+
+// the contact terms of the listed envs' active pairs, beside the SELL
+// mat-vec (both form d_k on the fly from z_k and d_{k-1})
+template <class HT>
+__global__ void __launch_bounds__(128) k_pcg_pairs(Dev d) {
+  __shared__ ItemInfo it;
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_items = d.pcg_pair_off[n_list];
+  const int ob = pcg_new_buf(d) ^ 1;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int li = list_find(d.pcg_pair_off, n_list, item);
+      const int e = d.pcg_list[li];
+      it.e = ENVI(d, e, I_PCG) ? e : -1;
+      it.local = item - d.pcg_pair_off[li];
+      it.s = ENVS(d, e, S_PBETA);
+    }
+    __syncthreads();
+    if (it.e < 0) continue;
+    matvec_pairs<HT>(d, it.e, it.local, (HT)it.s, ob);
   }
 }
 
@@ -379,18 +429,32 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_items = d.pcg_row_off[n_list];
   const int nb = pcg_new_buf(d);
+  __shared__ ItemInfo it;
+  __shared__ double s_dq;
+  __shared__ uint8_t s_tag;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int li = list_find(d.pcg_row_off, n_list, item);
-    const int e = d.pcg_list[li];
-    if (!ENVI(d, e, I_PCG)) continue;
-    const int cta = (d.env_row_off[e] >> 7) + item - d.pcg_row_off[li];
+    __syncthreads();  // the previous item is done with `it`
+    if (threadIdx.x == 0) {
+      const int li = list_find(d.pcg_row_off, n_list, item);
+      const int e = d.pcg_list[li];
+      it.e = ENVI(d, e, I_PCG) ? e : -1;
+      it.local = item - d.pcg_row_off[li];
+      const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
+      s_dq = dq;
+      it.s = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;    // alpha, once per item
+      s_tag = touch_tag(d, e);
+    }
+    __syncthreads();
+    const int e = it.e;
+    if (e < 0) continue;
+    const int cta = (d.env_row_off[e] >> 7) + it.local;
     const int r = cta * 128 + threadIdx.x;
-    const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
-    const double al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;
+    const double dq = s_dq;
+    const double al = it.s;
     const uint8_t kr = d.row_kind[r];
     // contact part of q on the rows this iteration's contact terms write
     D3 qcv{0, 0, 0};
-    const bool touched = d.row_touch[r] == touch_tag(d, e);
+    const bool touched = d.row_touch[r] == s_tag;
     if (touched) {
       qcv = ld3(d.qc, r);
       st3(d.qc, r, D3{0, 0, 0});
@@ -400,7 +464,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
     if constexpr (sizeof(HT) == 4) {
       const float4 dd = PV<float>::dbuf(d, nb)[r], qq = d.q4[r];
       st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
-      const D3 rv = ld3(d.r, r) - al * (widen_row(qq) + qcv);
+      const D3 rv = ld3(d.r, r) - al * (touched ? widen_row(qq) + qcv : widen_row(qq));
       st3(d.r, r, rv);
       __syncwarp();
       const double rr = dot(rv, rv);
@@ -410,7 +474,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
       last = env_reduce<2, float>(d, e, 0, cta, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
     } else {
       st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r, nb));
-      const D3 rv = ld3(d.r, r) - al * (PV<double>::q(d, r) + qcv);
+      const D3 rv = ld3(d.r, r) - al * (touched ? PV<double>::q(d, r) + qcv : PV<double>::q(d, r));
       st3(d.r, r, rv);
       __syncwarp();
       const double rr = dot(rv, rv);
@@ -452,7 +516,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
     d.step_ctl[4] += 1u;
     const unsigned len = d.pcg_ctl[C_LEN];
     const unsigned dead = d.pcg_ctl[C_DEAD];
-    const unsigned items = len ? (unsigned)d.pcg_item_off[len] : 0u;
+    const unsigned items = len ? (unsigned)(d.pcg_row_off[len] + d.pcg_pair_off[len]) : 0u;
     s_rebuild = dead > 0 && 4u * dead >= items;
   }
   __syncthreads();
@@ -517,6 +581,11 @@ int launch_pcg_matvec(const Dev& d, cudaStream_t s) {
     else if (u == 8) k_pcg_matvec<double, 8><<<g, 128, 0, s>>>(d);
     else k_pcg_matvec<double, 2><<<g, 128, 0, s>>>(d);
   }
+  return 1;
+}
+int launch_pcg_pairs(const Dev& d, cudaStream_t s) {
+  if (d.prec) k_pcg_pairs<float><<<d.pcg_grid_pairs, 128, 0, s>>>(d);
+  else k_pcg_pairs<double><<<d.pcg_grid_pairs, 128, 0, s>>>(d);
   return 1;
 }
 int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {

@@ -121,73 +121,100 @@ __device__ __forceinline__ void body_My_mul(double m, const double* S, const dou
     }
 }
 
-__global__ void k_body(Dev d) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.n_bodies) return;
-  int e = d.body_env[b];
+// One warp per body (4 bodies per 128-thread CTA): the lanes build the
+// gradient and the 9x9 orthogonality Hessian entry by entry in shared
+// memory, lane 0 tests it for positive definiteness (and projects it when
+// it is not), the lanes write the 12x12 body Hessian.  A body's terms are a
+// few thousand FP64 operations: spread over a warp and kept in shared
+// memory they no longer set a multi-millisecond floor under the assembly of
+// the envs that are still iterating.
+__global__ void __launch_bounds__(128) k_body(Dev d) {
+  __shared__ double sy[4][12], sdy[4][12], sHo[4][81], swork[4][162];
+  __shared__ int s_pd[4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * 4 + w;
+  if (b >= d.n_bodies) return;                    // warp-uniform; no block barriers below
+  const int e = d.body_env[b];
   if (!ENVI(d, e, I_ACTIVE)) return;
-  int br = d.body_row[b];
-  double y[12], yt[12], dy[12], gb[12];
-  for (int k = 0; k < 12; ++k) {
-    y[k] = d.x[3 * br + k];
-    yt[k] = d.xt[3 * br + k];
-    dy[k] = y[k] - yt[k];
+  const int br = d.body_row[b];
+  double* y = sy[w];
+  double* dy = sdy[w];
+  double* Ho = sHo[w];
+  if (lane < 12) {
+    y[lane] = d.x[3 * br + lane];
+    dy[lane] = y[lane] - d.xt[3 * br + lane];
   }
-  double m = d.body_mass[b];
+  __syncwarp();
+  const double m = d.body_mass[b];
   const double* S = d.body_S + 9 * b;
-  body_My_mul(m, S, dy, gb);
-  double h2 = d.h * d.h;
-  for (int c = 0; c < 3; ++c) gb[c] -= h2 * m * d.grav[c];
-  double ko = h2 * d.body_kappa[b] * d.body_vol[b];
+  const double h2 = d.h * d.h;
+  const double ko = h2 * d.body_kappa[b] * d.body_vol[b];
   const double* a = y + 3;  // a_k = a[3k..3k+3)
   double C[9];
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l)
       C[3 * k + l] = a[3 * k] * a[3 * l] + a[3 * k + 1] * a[3 * l + 1] + a[3 * k + 2] * a[3 * l + 2] - (k == l ? 1.0 : 0.0);
-  for (int mm = 0; mm < 3; ++mm)
-    for (int c = 0; c < 3; ++c) {
-      double s = 0;
-      for (int l = 0; l < 3; ++l) s += C[3 * mm + l] * a[3 * l + c];
-      gb[3 + 3 * mm + c] += 4.0 * ko * s;
+  // Ho (orthogonality Hessian, 9x9), 3 entries per lane
+  for (int idx = lane; idx < 81; idx += 32) {
+    const int row = idx / 9, col = idx - 9 * row;
+    const int mm = row / 3, i = row - 3 * mm, n = col / 3, j = col - 3 * n;
+    double v = a[3 * n + i] * a[3 * mm + j] + (i == j ? C[3 * mm + n] : 0.0);
+    if (mm == n) v += a[i] * a[j] + a[3 + i] * a[3 + j] + a[6 + i] * a[6 + j];
+    Ho[idx] = 4.0 * ko * v;
+  }
+  // gradient: lane k < 12 owns entry k (inertia, gravity, orthogonality, AL)
+  double gk = 0.0;
+  if (lane < 12) {
+    if (lane < 3) {
+      gk = m * dy[lane] - h2 * m * d.grav[lane];
+    } else {
+      const int k = (lane - 3) / 3, c = (lane - 3) % 3;
+      for (int l = 0; l < 3; ++l) gk += S[3 * k + l] * dy[3 + 3 * l + c];
+      double s2 = 0;
+      for (int l = 0; l < 3; ++l) s2 += C[3 * k + l] * a[3 * l + c];
+      gk += 4.0 * ko * s2;
     }
-  double Ho[81], work[162];
-  double AAt[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) AAt[3 * i + j] = a[i] * a[j] + a[3 + i] * a[3 + j] + a[6 + i] * a[6 + j];
-  for (int mm = 0; mm < 3; ++mm)
-    for (int n = 0; n < 3; ++n)
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-          double v = a[3 * n + i] * a[3 * mm + j] + (i == j ? C[3 * mm + n] : 0.0);
-          if (mm == n) v += AAt[3 * i + j];
-          Ho[(3 * mm + i) * 9 + 3 * n + j] = 4.0 * ko * v;
-        }
-  // a positive definite Hessian is its own projection (the common case near
-  // rigid states); the eigen-decomposition only runs otherwise
-  if (!is_pos_def<9, double>(Ho, work)) psd_project<9, double>(Ho, work, newton_filter(d, e) == FILT_ABS);
-  double* H = d.body_H + 144 * (long long)b;
-  for (int i = 0; i < 144; ++i) H[i] = 0.0;
-  for (int c = 0; c < 3; ++c) H[c * 12 + c] = m;
-  for (int k = 0; k < 3; ++k)
-    for (int l = 0; l < 3; ++l)
-      for (int c = 0; c < 3; ++c) H[(3 + 3 * k + c) * 12 + 3 + 3 * l + c] = S[3 * k + l];
-  for (int i = 0; i < 9; ++i)
-    for (int j = 0; j < 9; ++j) H[(3 + i) * 12 + 3 + j] += Ho[i * 9 + j];
-  if (d.body_driven[b]) {
-    double rr[12], lm[12], t1[12], t2[12];
+  }
+  const bool driven = d.body_driven[b] != 0;
+  if (driven && lane < 12) {
+    // M^y (y - s) and M^y lambda, entry `lane`
+    auto my = [&](const double* v) {
+      if (lane < 3) return m * v[lane];
+      const int k = (lane - 3) / 3, c = (lane - 3) % 3;
+      double t = 0;
+      for (int l = 0; l < 3; ++l) t += S[3 * k + l] * v[3 + 3 * l + c];
+      return t;
+    };
+    double rr[12], lm[12];
     for (int k = 0; k < 12; ++k) {
       rr[k] = y[k] - d.s_tgt[3 * br + k];
       lm[k] = d.lam[3 * br + k];
     }
-    body_My_mul(m, S, rr, t1);
-    body_My_mul(m, S, lm, t2);
-    for (int k = 0; k < 12; ++k) gb[k] += d.al_kappa * t1[k] - t2[k];
-    for (int c = 0; c < 3; ++c) H[c * 12 + c] += d.al_kappa * m;
-    for (int k = 0; k < 3; ++k)
-      for (int l = 0; l < 3; ++l)
-        for (int c = 0; c < 3; ++c) H[(3 + 3 * k + c) * 12 + 3 + 3 * l + c] += d.al_kappa * S[3 * k + l];
+    gk += d.al_kappa * my(rr) - my(lm);
   }
-  for (int k = 0; k < 12; ++k) d.body_g[12 * b + k] = gb[k];
+  if (lane < 12) d.body_g[12 * b + lane] = gk;
+  __syncwarp();
+  // a positive definite Hessian is its own projection (the common case near
+  // rigid states); the eigen-decomposition only runs otherwise
+  if (lane == 0) {
+    const bool pd = is_pos_def<9, double>(Ho, swork[w]);
+    if (!pd) psd_project<9, double>(Ho, swork[w], newton_filter(d, e) == FILT_ABS);
+    s_pd[w] = pd;
+  }
+  __syncwarp();
+  double* H = d.body_H + 144 * (long long)b;
+  for (int idx = lane; idx < 144; idx += 32) {
+    const int row = idx / 12, col = idx - 12 * row;
+    double v = 0.0;
+    if (row < 3 && col < 3) {
+      v = row == col ? m * (1.0 + (driven ? d.al_kappa : 0.0)) : 0.0;
+    } else if (row >= 3 && col >= 3) {
+      const int k = (row - 3) / 3, c = (row - 3) % 3, l = (col - 3) / 3, c2 = (col - 3) % 3;
+      if (c == c2) v = S[3 * k + l] * (1.0 + (driven ? d.al_kappa : 0.0));
+      v += Ho[(row - 3) * 9 + (col - 3)];
+    }
+    H[idx] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -655,7 +682,7 @@ int launch_tet(const Dev& d, cudaStream_t s) {
 }
 int launch_body(const Dev& d, cudaStream_t s) {
   if (!d.n_bodies) return 0;
-  k_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
+  k_body<<<nblk(d.n_bodies, 4), 128, 0, s>>>(d);
   return 1;
 }
 int launch_assemble(const Dev& d, cudaStream_t s) {

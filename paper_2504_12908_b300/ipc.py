@@ -113,6 +113,7 @@ def lib():
             "ipc_k_tet": (i32, [i32, vp, vp, vp, dbl, dbl, vp, vp, vp, i32, vp]),
             "ipc_k_barrier": (i32, [i32, vp, vp, vp, vp, dbl, vp, vp, vp, i32, vp]),
             "ipc_k_accd": (i32, [i32, vp, vp, vp, dbl, i32, vp, vp, vp]),
+            "ipc_fma_peaks": (i32, [vp, C.c_size_t, _dp, _dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -129,7 +130,7 @@ EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
-            "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd"]
+            "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd", "ipc_fma_peaks"]
 
 
 class IpcError(RuntimeError):
@@ -600,3 +601,16 @@ def k_accd(X0, P, is_ee, s: float, max_iter: int, toi, iters=None):
                           _stream_ptr(X0))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_accd")
+
+
+def fma_peaks(device="cuda:0") -> dict:
+    """Measured FP64 / FP32 FMA throughput of the device, TFLOP/s."""
+    import torch
+    dev = torch.device(device)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    buf = torch.empty(n_sm * 8 * 256, dtype=torch.float64, device=dev)
+    f64, f32 = C.c_double(), C.c_double()
+    st = lib().ipc_fma_peaks(_vp(buf), buf.numel() * 8, C.byref(f64), C.byref(f32), _stream_ptr(buf))
+    if st != IPC_OK:
+        raise IpcError(st, "ipc_fma_peaks")
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value}

@@ -2,33 +2,34 @@
 
 A request is one environment (a scene of gel + affine bodies, a kinematic
 script and a number of steps) that arrives at some time.  The server keeps
-every admitted environment resident on the GPU until its last step and
-admits waiting requests whenever a cohort slot and device memory are free:
+resident *pools*: one library context per size class (the topology of a
+request: mesh sizes, connectivity, body vertex counts) with a fixed number
+of env slots.  Admission is per slot:
 
-* a cohort is a group of requests admitted together into one library
-  context (one `ipc_create_envs`, one workspace, one CUDA stream);
-* each cohort is stepped by its own host thread (the C-ABI calls release the
-  GIL), so cohorts admitted at different times overlap on the device;
-* admission takes the oldest waiting requests, up to the cohort size limit,
-  the resident-environment limit and what the free device memory holds
-  (`ipc_workspace_bytes` of the candidate cohort against the free memory
-  minus a reserve); a cohort that does not fit is halved until it does;
-* a finished cohort closes its context and returns its workspace, which
-  lets the next requests in.
+* arrived requests wait in a FIFO queue of their size class;
+* a pool is opened for a class when requests of that class wait and device
+  memory (``ipc_workspace_bytes`` of the pool against the free memory minus
+  a reserve) and the pool limit allow; its slot count is the largest that
+  fits, up to ``slots_per_pool``;
+* the moment a slot's request has run its last step, the next waiting
+  request of that class is loaded into the slot (``ipc_reset_env``: the new
+  scene's material, rest geometry and bodies replace the old ones in place,
+  state back to rest) and steps from the next batched step on;
+* every pool is stepped by its own host thread on its own CUDA stream (the
+  C-ABI calls release the GIL), so pools of different classes overlap on
+  the device; each batched step advances the pool's occupied slots, every
+  slot at its own script step.
 
-Every environment of a cohort is stepped by the same `ipc_step` call; an
-env whose script ended is left out of the env-id list (`ipc_step` takes a
-subset), so requests of different lengths can share a cohort.
-
-The engine behind the loop is pluggable (`Engine`): `GpuEngine` drives the
-library; the tests drive the scheduling logic with a CPU stand-in.
+The engine behind the loop is pluggable (``Engine``): ``GpuEngine`` drives
+the library; the tests drive the scheduling logic with a CPU stand-in.
 """
 from __future__ import annotations
 
 import dataclasses
 import threading
 import time
-from typing import Callable, Dict, List, Optional, Sequence
+from collections import deque
+from typing import Callable, Deque, Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -40,7 +41,7 @@ class Request:
     delta(k) -> (n_bodies, 3): translation of each driven body's rest
     placement at step k (the scripted targets; bodies keep A = I).
     Instead of scene and delta a request may carry build() -> (scene, delta),
-    called when the request is first considered for admission."""
+    called when the request first arrives."""
     rid: int
     scene: object = None
     delta: Optional[Callable[[int], np.ndarray]] = None
@@ -64,6 +65,7 @@ class RequestResult:
     finished: float
     steps: int                    # steps taken (n_steps unless the run was cut)
     status: int                   # first non-OK per-env status, else 0
+    slot: tuple = ()              # (pool index, slot index) it ran in
     final_x: Optional[np.ndarray] = None   # gel vertex positions after the last step
     final_y: Optional[np.ndarray] = None   # body DoFs after the last step
 
@@ -84,9 +86,11 @@ class ServeReport:
     completed: int                # ran all their steps with status OK
     arrived: int
     backlog: int                  # arrived, not admitted at the end
-    cohorts: int
-    max_resident: int
-    max_active_cohorts: int       # cohorts stepping at the same time (overlap)
+    pools: int                    # resident contexts opened (one per size class)
+    slots: int                    # env slots over all pools
+    slot_reuses: int              # requests loaded into a slot a previous request used
+    max_resident: int             # most requests in slots at once
+    max_active_pools: int         # pools stepping at the same time (overlap)
     results: Dict[int, RequestResult]
 
     def summary(self) -> dict:
@@ -95,13 +99,18 @@ class ServeReport:
         return d
 
 
-class Cohort:
-    """Engine-side handle of one admitted cohort."""
+class Pool:
+    """Engine-side handle of one resident context with env slots."""
 
-    def step(self, env_ids: Sequence[int], k: int) -> np.ndarray:   # per-env status
+    n_slots: int = 0
+
+    def load(self, slot: int, req: Request) -> None:
         raise NotImplementedError
 
-    def final_state(self, i: int):
+    def step(self, slots: Sequence[int], ks: Sequence[int]) -> np.ndarray:   # per-slot status
+        raise NotImplementedError
+
+    def final_state(self, slot: int):
         raise NotImplementedError
 
     def close(self) -> None:
@@ -109,18 +118,32 @@ class Cohort:
 
 
 class Engine:
-    def cohort_bytes(self, scenes: Sequence) -> int:
+    def class_key(self, scene) -> object:
+        raise NotImplementedError
+
+    def pool_bytes(self, scene, n_slots: int) -> int:
         raise NotImplementedError
 
     def free_bytes(self) -> int:
         raise NotImplementedError
 
-    def open(self, requests: Sequence[Request]) -> Cohort:
+    def open_pool(self, scene, n_slots: int, max_steps: int) -> Pool:
         raise NotImplementedError
 
 
+def topology_key(scene) -> tuple:
+    """Size class of a scene: what ipc_reset_env requires to be equal."""
+    tets = np.ascontiguousarray(scene.gel_tets)
+    bodies = tuple((b.rest_x.shape[0], b.tris.shape[0], bool(b.driven), hash(np.ascontiguousarray(b.tris).tobytes()))
+                   for b in scene.bodies)
+    return (scene.gel_x.shape[0], hash(tets.tobytes()), hash(np.asarray(scene.pinned).tobytes()),
+            hash(np.asarray(scene.attach).tobytes()), hash(np.asarray(scene.gel_obj).tobytes()),
+            None if scene.self_contact is None else tuple(bool(v) for v in scene.self_contact), bodies)
+
+
 class GpuEngine(Engine):
-    """The library on one GPU: one context and one CUDA stream per cohort."""
+    """The library on one GPU: one context and one CUDA stream per pool,
+    whole steps as CUDA graphs."""
 
     def __init__(self, params, device: str = "cuda:0", graphs: bool = True):
         import torch
@@ -131,8 +154,11 @@ class GpuEngine(Engine):
         self.device = torch.device(device)
         self.graphs = graphs
 
-    def cohort_bytes(self, scenes: Sequence) -> int:
-        return self._ipc.workspace_bytes(list(scenes), self.params)
+    def class_key(self, scene):
+        return topology_key(scene)
+
+    def pool_bytes(self, scene, n_slots):
+        return self._ipc.workspace_bytes([scene] * n_slots, self.params)
 
     def free_bytes(self) -> int:
         torch = self._torch
@@ -141,191 +167,257 @@ class GpuEngine(Engine):
         cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
         return int(free + cached)
 
-    def open(self, requests: Sequence[Request]) -> Cohort:
-        return _GpuCohort(self, requests)
+    def open_pool(self, scene, n_slots, max_steps):
+        return _GpuPool(self, scene, n_slots, max_steps)
 
 
-class _GpuCohort(Cohort):
-    def __init__(self, eng: GpuEngine, requests: Sequence[Request]):
+class _GpuPool(Pool):
+    def __init__(self, eng: GpuEngine, scene, n_slots: int, max_steps: int):
         torch, ipc = eng._torch, eng._ipc
+        self.torch, self.ipc = torch, ipc
+        self.n_slots = n_slots
         self.stream = torch.cuda.Stream(eng.device)
-        self.envs = ipc.Envs([r.scene for r in requests], eng.params, device=str(eng.device),
-                             stream=self.stream)
+        self.envs = ipc.Envs([scene] * n_slots, eng.params, device=str(eng.device), stream=self.stream)
         if eng.graphs:
-            self.envs.set_graph_mode(True)
-        for i, r in enumerate(requests):
-            if r.state is not None:
-                st = self.envs.set_state(i, *r.state)
-                if st != ipc.IPC_OK:
-                    raise ipc.IpcError(st, f"request {r.rid}: initial state rejected")
-        n, mb = len(requests), self.envs.max_bodies
-        n_steps = max(r.n_steps for r in requests)
-        # the whole script of every env, resident on the device
-        tg = np.zeros((n_steps, n, mb, 12))
-        for i, r in enumerate(requests):
-            rest = self.envs.rest_y(i)
-            nb = rest.shape[0]
-            for k in range(r.n_steps):
-                t = rest.copy()
-                dl = np.asarray(r.delta(k), dtype=np.float64).reshape(-1, 3)
-                t[:, :3] += dl[:nb]
-                tg[k, i, :nb] = t
+            self.envs.set_graph_mode(2)
+        mb = max(self.envs.max_bodies, 1)
+        # every slot's script, resident on the device: [slot][step][body][12]
         with torch.cuda.stream(self.stream):
-            self.dev_tg = torch.as_tensor(tg, device=eng.device)
+            self.dev_tg = torch.zeros((n_slots, max_steps, mb, 12), dtype=torch.float64, device=eng.device)
+        self.max_steps = max_steps
 
-    def step(self, env_ids: Sequence[int], k: int) -> np.ndarray:
-        self.envs.set_targets_all_device(self.dev_tg[k])
-        status, _ = self.envs.step(list(env_ids))
+    def load(self, slot, req):
+        torch = self.torch
+        self.envs.reset_env(slot, req.scene)
+        if req.state is not None:
+            st = self.envs.set_state(slot, *req.state)
+            if st != self.ipc.IPC_OK:
+                raise self.ipc.IpcError(st, f"request {req.rid}: initial state rejected")
+        rest = self.envs.rest_y(slot)
+        nb = rest.shape[0]
+        tg = np.zeros((self.max_steps,) + tuple(self.dev_tg.shape[2:]))
+        for k in range(min(req.n_steps, self.max_steps)):
+            t = rest.copy()
+            t[:, :3] += np.asarray(req.delta(k), dtype=np.float64).reshape(-1, 3)[:nb]
+            tg[k, :nb] = t
+        with torch.cuda.stream(self.stream):
+            self.dev_tg[slot].copy_(torch.as_tensor(tg), non_blocking=False)
+
+    def step(self, slots, ks):
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            k_all = torch.zeros(self.n_slots, dtype=torch.long, device=self.dev_tg.device)
+            k_all[torch.as_tensor(list(slots), device=self.dev_tg.device)] = torch.as_tensor(
+                list(ks), dtype=torch.long, device=self.dev_tg.device)
+            tg = self.dev_tg[torch.arange(self.n_slots, device=self.dev_tg.device), k_all].contiguous()
+        self.envs.set_targets_all_device(tg)
+        status, _ = self.envs.step(list(slots))
         return status
 
-    def final_state(self, i: int):
-        x, _, y, _ = self.envs.get_state(i)
+    def final_state(self, slot):
+        x, _, y, _ = self.envs.get_state(slot)
         return x, y
 
-    def close(self) -> None:
+    def close(self):
         self.envs.close()
         self.dev_tg = None
 
 
-class Server:
-    """Admission and stepping loop (see the module docstring)."""
+class _PoolState:
+    def __init__(self, index, key, pool, n_slots):
+        self.index, self.key, self.pool = index, key, pool
+        self.req: List[Optional[Request]] = [None] * n_slots
+        self.k = np.zeros(n_slots, int)
+        self.status = np.zeros(n_slots, np.int32)
+        self.admitted = np.zeros(n_slots)
+        self.used = np.zeros(n_slots, bool)
+        self.closed = False
 
-    def __init__(self, engine: Engine, max_resident: int = 4096, max_cohort: int = 512,
-                 max_cohorts: int = 8, mem_reserve: int = 2 << 30, keep_state: bool = True,
+
+class Server:
+    """Per-slot admission and stepping loop (see the module docstring)."""
+
+    def __init__(self, engine: Engine, max_resident: int = 4096, slots_per_pool: int = 256,
+                 max_pools: int = 32, mem_reserve: int = 2 << 30, keep_state: bool = True,
                  poll_s: float = 0.002):
         self.engine = engine
         self.max_resident = max_resident
-        self.max_cohort = max_cohort
-        self.max_cohorts = max_cohorts
+        self.slots_per_pool = slots_per_pool
+        self.max_pools = max_pools
         self.mem_reserve = mem_reserve
         self.keep_state = keep_state
         self.poll_s = poll_s
         self._lock = threading.Lock()
-        self._stop = threading.Event()
+        self._stop = threading.Event()          # stop stepping (hard limit)
+        self._closed = threading.Event()        # no further admission
+        self._queues: Dict[object, Deque[Request]] = {}
         self._resident = 0
+        self._peak_resident = 0
         self._active = 0
         self._peak_active = 0
+        self._reuses = 0
         self._step_samples: List[tuple] = []      # (ms, envs in the call)
         self._results: Dict[int, RequestResult] = {}
         self._errors: List[BaseException] = []
         self._n_steps: Dict[int, int] = {}
 
-    # ---------------------------------------------------------------- admission
-    def _admit(self, waiting: List[Request]) -> List[Request]:
-        """Largest FIFO prefix of `waiting` that fits the limits (may be empty)."""
-        with self._lock:
-            room = min(self.max_cohort, self.max_resident - self._resident)
-            slots = self.max_cohorts - self._active
-        if room <= 0 or slots <= 0 or not waiting:
-            return []
-        n = min(room, len(waiting))
-        for r in waiting[:n]:
-            r.materialize()
-        free = self.engine.free_bytes() - self.mem_reserve
-        while n > 0:
-            if self.engine.cohort_bytes([r.scene for r in waiting[:n]]) <= free:
-                return waiting[:n]
-            n //= 2
-        return []
+    # ---------------------------------------------------------------- slots
+    def _fill(self, ps: _PoolState, t0: float) -> None:
+        """Load waiting requests of the pool's class into its free slots."""
+        for s in range(len(ps.req)):
+            if ps.req[s] is not None or self._closed.is_set():
+                continue
+            with self._lock:
+                q = self._queues.get(ps.key)
+                if not q or self._resident >= self.max_resident:
+                    return
+                r = q.popleft()
+                self._resident += 1
+                self._peak_resident = max(self._peak_resident, self._resident)
+                if ps.used[s]:
+                    self._reuses += 1
+            ps.pool.load(s, r)
+            ps.req[s], ps.k[s], ps.status[s] = r, 0, 0
+            ps.admitted[s] = time.perf_counter() - t0
+            ps.used[s] = True
 
-    # ---------------------------------------------------------------- stepping
-    def _run_cohort(self, reqs: List[Request], t0: float, admitted_at: float):
+    def _finish(self, ps: _PoolState, s: int, now: float) -> None:
+        r = ps.req[s]
+        x = y = None
+        if self.keep_state:
+            x, y = ps.pool.final_state(s)
+        res = RequestResult(rid=r.rid, arrival=r.arrival, admitted=float(ps.admitted[s]), finished=now,
+                            steps=int(ps.k[s]), status=int(ps.status[s]), slot=(ps.index, s),
+                            final_x=x, final_y=y)
+        with self._lock:
+            self._results[r.rid] = res
+            self._resident -= 1
+        ps.req[s] = None
+
+    def _run_pool(self, ps: _PoolState, t0: float) -> None:
         try:
-            coh = self.engine.open(reqs)
-            status = np.zeros(len(reqs), np.int32)
-            done_at = [None] * len(reqs)
-            taken = np.zeros(len(reqs), int)
-            n_max = max(r.n_steps for r in reqs)
-            for k in range(n_max):
-                ids = [i for i, r in enumerate(reqs) if k < r.n_steps and status[i] == 0]
-                if not ids or self._stop.is_set():
-                    break
+            while True:
+                self._fill(ps, t0)
+                occ = [s for s, r in enumerate(ps.req) if r is not None]
+                if not occ:
+                    with self._lock:
+                        empty = not self._queues.get(ps.key)
+                    if self._closed.is_set() or self._stop.is_set() or (empty and self._admission_done):
+                        return
+                    time.sleep(self.poll_s)
+                    continue
+                if self._stop.is_set():
+                    now = time.perf_counter() - t0
+                    for s in occ:
+                        self._finish(ps, s, now)
+                    return
+                with self._lock:
+                    self._active += 1
+                    self._peak_active = max(self._peak_active, self._active)
                 ts = time.perf_counter()
-                st = coh.step(ids, k)
+                st = ps.pool.step(occ, [int(ps.k[s]) for s in occ])
                 ms = 1e3 * (time.perf_counter() - ts)
                 now = time.perf_counter() - t0
                 with self._lock:
-                    self._step_samples.append((ms, len(ids)))
-                for j, i in enumerate(ids):
-                    taken[i] += 1
+                    self._active -= 1
+                    self._step_samples.append((ms, len(occ)))
+                for j, s in enumerate(occ):
+                    ps.k[s] += 1
                     if st[j] != 0:
-                        status[i] = st[j]
-                    if k == reqs[i].n_steps - 1 or st[j] != 0:
-                        done_at[i] = now
-            finished = time.perf_counter() - t0
-            for i, r in enumerate(reqs):
-                x = y = None
-                if self.keep_state:
-                    x, y = coh.final_state(i)
-                res = RequestResult(rid=r.rid, arrival=r.arrival, admitted=admitted_at,
-                                    finished=done_at[i] if done_at[i] is not None else finished,
-                                    steps=int(taken[i]), status=int(status[i]), final_x=x, final_y=y)
-                with self._lock:
-                    self._results[r.rid] = res
-            coh.close()
+                        ps.status[s] = st[j]
+                    if ps.k[s] >= ps.req[s].n_steps or st[j] != 0:
+                        self._finish(ps, s, now)
         except BaseException as exc:  # surfaced by run()
             with self._lock:
                 self._errors.append(exc)
         finally:
-            with self._lock:
-                self._resident -= len(reqs)
-                self._active -= 1
+            ps.pool.close()
+            ps.closed = True
+
+    # ---------------------------------------------------------------- main loop
+    def _open_pool(self, key, scene, max_steps, n_pools) -> Optional[_PoolState]:
+        n = self.slots_per_pool
+        free = self.engine.free_bytes() - self.mem_reserve
+        while n > 0 and self.engine.pool_bytes(scene, n) > free:
+            n //= 2
+        if n == 0:
+            return None
+        return _PoolState(n_pools, key, self.engine.open_pool(scene, n, max_steps), n)
 
     def run(self, requests: Sequence[Request], time_limit: Optional[float] = None,
             realtime: bool = True, hard_limit: Optional[float] = None) -> ServeReport:
         """Serve `requests` (arrival times relative to the start).  With
         realtime=False every request counts as arrived at t = 0.  With a
         time_limit, admission stops at that time and the run ends when the
-        admitted cohorts finish; with a hard_limit, cohorts stop stepping at
-        that time too (their requests count as not completed)."""
+        loaded requests finish; with a hard_limit, stepping stops at that
+        time too (the requests in slots then count as not completed)."""
         self._stop.clear()
+        self._closed.clear()
+        self._admission_done = False
         queue = sorted(requests, key=lambda r: (r.arrival if realtime else 0.0, r.rid))
         self._n_steps = {r.rid: r.n_steps for r in queue}
+        max_steps = max([r.n_steps for r in queue] + [1])
         t0 = time.perf_counter()
+        live: Dict[object, _PoolState] = {}      # open pools by size class
+        opened: List[_PoolState] = []
         threads: List[threading.Thread] = []
         nxt = 0
-        waiting: List[Request] = []
-        cohorts = 0
-        peak = 0
         while True:
             now = time.perf_counter() - t0
-            while nxt < len(queue) and (not realtime or queue[nxt].arrival <= now):
-                waiting.append(queue[nxt])
-                nxt += 1
             stop_admitting = time_limit is not None and now >= time_limit
+            if stop_admitting:
+                self._closed.set()
+            while not stop_admitting and nxt < len(queue) and (not realtime or queue[nxt].arrival <= now):
+                r = queue[nxt].materialize()
+                with self._lock:
+                    self._queues.setdefault(self.engine.class_key(r.scene), deque()).append(r)
+                nxt += 1
+            self._admission_done = nxt == len(queue)
+            # a pool for every class with waiting requests (memory and the
+            # pool limit permitting); closed pools give their memory back
+            for key in [k for k, ps in live.items() if ps.closed]:
+                del live[key]
             if not stop_admitting:
-                batch = self._admit(waiting)
-                if batch:
-                    waiting = waiting[len(batch):]
-                    with self._lock:
-                        self._resident += len(batch)
-                        self._active += 1
-                        peak = max(peak, self._resident)
-                        self._peak_active = max(self._peak_active, self._active)
-                    cohorts += 1
-                    th = threading.Thread(target=self._run_cohort, args=(batch, t0, now), daemon=True)
+                with self._lock:
+                    want = [(k, q[0].scene) for k, q in self._queues.items() if q and k not in live]
+                for key, scene in want:
+                    if len(live) >= self.max_pools:
+                        break
+                    ps = self._open_pool(key, scene, max_steps, len(opened))
+                    if ps is None:
+                        continue
+                    live[key] = ps
+                    opened.append(ps)
+                    th = threading.Thread(target=self._run_pool, args=(ps, t0), daemon=True)
                     th.start()
                     threads.append(th)
-                    continue
             with self._lock:
-                active = self._active
                 err = list(self._errors)
+                waiting = sum(len(q) for q in self._queues.values())
             if err:
+                self._stop.set()
                 for th in threads:
                     th.join()
                 raise err[0]
-            if active == 0 and (stop_admitting or (nxt == len(queue) and not waiting)):
+            alive = any(th.is_alive() for th in threads)
+            if not alive and (stop_admitting or (nxt == len(queue) and waiting == 0)):
                 break
+            if (not alive and not live and nxt == len(queue) and waiting and not opened and time_limit is None
+                    and hard_limit is None):
+                raise RuntimeError("no pool fits in device memory")
             if hard_limit is not None and now >= hard_limit:
                 self._stop.set()
+                self._closed.set()
             time.sleep(self.poll_s)
         for th in threads:
             th.join()
         wall = time.perf_counter() - t0
-        return self._report(wall, len(queue) if not realtime else nxt, len(waiting) + (len(queue) - nxt),
-                            cohorts, peak)
+        with self._lock:
+            waiting = sum(len(q) for q in self._queues.values())
+        arrived = len(queue) if not realtime else nxt
+        return self._report(wall, arrived, waiting + (len(queue) - nxt), opened)
 
-    def _report(self, wall, arrived, backlog, cohorts, peak) -> ServeReport:
+    def _report(self, wall, arrived, backlog, pools) -> ServeReport:
         res = self._results
         env_steps = int(sum(n for _, n in self._step_samples))
         if self._step_samples:
@@ -350,8 +442,9 @@ class Server:
             queue_s_max=float(queue.max()) if len(queue) else None,
             admitted=len(res),
             completed=sum(1 for r in res.values() if r.status == 0 and r.steps == self._n_steps.get(r.rid, r.steps)),
-            arrived=arrived, backlog=backlog, cohorts=cohorts, max_resident=peak,
-            max_active_cohorts=self._peak_active, results=dict(res))
+            arrived=arrived, backlog=backlog, pools=len(pools),
+            slots=int(sum(len(p.req) for p in pools)), slot_reuses=self._reuses,
+            max_resident=self._peak_resident, max_active_pools=self._peak_active, results=dict(res))
 
 
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:

@@ -38,6 +38,7 @@ __all__ = [
     "Body", "Scene", "Scenario", "SolverParams",
     "gel_grid", "icosphere", "box_surface",
     "config0", "config1", "config2", "config3", "config3_batch", "small_contact_scene",
+    "self_contact_pad", "pad_and_sphere",
     "free_fall_scene", "spin_scene", "self_contact_scene",
 ]
 
@@ -530,6 +531,29 @@ def config3_batch(n_envs: int, n=32, nz=6, n_steps=200, level=4):
         g = 2e-5 + rng.uniform(0.0, 2e-5)
         shifts.append((-(g - mean_gap), g - mean_gap))
     return base.scene, base.params, shifts, base.delta
+
+
+def self_contact_pad(n: int, nz: int = 3) -> Scene:
+    """One free-standing n x n x nz gel pad (20 x 20 x 4 mm, bottom pinned)
+    flagged for self-contact, no bodies: a candidate-search workload."""
+    x, tets, bottom, _ = gel_grid(n, n, nz)
+    N = x.shape[0]
+    return Scene(gel_x=x, gel_tets=tets, gel_obj=np.zeros(N, np.int32), pinned=bottom.copy(),
+                 attach=-np.ones(N, np.int32), E=3e5, nu=0.45, rho=1000.0, bodies=[],
+                 name=f"self_contact_pad[{n}]", self_contact=np.array([True]))
+
+
+def pad_and_sphere(n: int, nz: int, level: int, r: float = 10e-3) -> Scene:
+    """An n x n x nz pad with a free icosphere resting 20 um above its top:
+    a candidate-search workload for a large object."""
+    x, tets, bottom, _ = gel_grid(n, n, nz)
+    N = x.shape[0]
+    sx, st = icosphere(level, r)
+    sx[:, 2] += 2e-5 - sx[:, 2].min()
+    body = Body(rest_x=sx, tris=st, rho=800.0, kappa_s=1e8, driven=False)
+    return Scene(gel_x=x, gel_tets=tets, gel_obj=np.zeros(N, np.int32), pinned=bottom.copy(),
+                 attach=-np.ones(N, np.int32), E=3e5, nu=0.45, rho=1000.0, bodies=[body],
+                 name=f"pad_and_sphere[{n},{level}]")
 
 
 def config1_batch(n_envs: int, nx=40, ny=40, nz=6, n_steps=100):

@@ -83,3 +83,16 @@ def valid_state(env: OracleEnv, x, y) -> bool:
     T = env.scene.gel_tets
     F = oen.deformation_gradient(x[T], env.gel.Dm_inv)
     return bool(np.linalg.det(F).min() > 0.0)
+
+
+def oracle_press_step(args):
+    """One oracle step of env e of the 256-env press batch from a given
+    state (run in a child process by the full-size tests)."""
+    import scenes
+    e, k, state, prm = args
+    scene, _, deltas = scenes.config1_batch(e + 1)
+    oenv = OracleEnv(scene, prm)
+    x, v, y, yd = state
+    sy = oenv.targets_from_delta(deltas[e](k))
+    xo, vo, yo, ydo, st = oenv.step(x, v, y, yd, sy)
+    return {"x": xo, "y": yo, "status": st.status, "newton": st.newton_iters}

@@ -16,7 +16,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from gpu_util import all_points, bbox_diag, from_gpu_y, oracle_restart, valid_state  # noqa: E402
+from gpu_util import all_points, bbox_diag, from_gpu_y, oracle_press_step, oracle_restart, valid_state  # noqa: E402
 from oracle import OracleEnv  # noqa: E402
 from paper_2504_12908_b300 import ipc  # noqa: E402
 from paper_2504_12908_b300.build import build  # noqa: E402
@@ -69,19 +69,54 @@ def _run(scs, prm, n_pre, samples):
     genv.close()
 
 
-def test_config1_full_batch_mixed():
+def test_config1_bench_window_mixed():
+    """The benchmark's workload in its launch configuration (256 envs, mixed
+    precision, whole steps as CUDA graphs) over the benchmark's window,
+    steps 0-24 of the press: every env converges at every step, and four
+    envs are compared with the oracle's step from the same input state at
+    the first timed step (step 5)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
     scene, params, deltas = scenes.config1_batch(256)
     prm = scenes.SolverParams(**params.__dict__)
     prm.precision = 1
+    genv = ipc.Envs([scene] * 256, prm, stream=torch.cuda.Stream())
+    genv.set_graph_mode(2)
+    com = genv.body_com(0, 0)
+    samples, k_cmp = [3, 77, 150, 222], 5
 
-    class S:
-        pass
-    scs = []
-    for e in range(256):
-        s = S()
-        s.scene, s.delta = scene, deltas[e]
-        scs.append(s)
-    _run(scs, prm, 4, samples=[0, 137])
+    def targets(k):
+        t = np.zeros((256, 1, 12))
+        for e in range(256):
+            t[e, 0, :3] = com + deltas[e](k)[0]
+            t[e, 0, 3:] = np.eye(3).T.ravel()
+        return t
+    before = after = None
+    newton_max = 0
+    for k in range(25):
+        if k == k_cmp:
+            before = {e: genv.get_state(e) for e in samples}
+        genv.set_targets_all(targets(k))
+        st, stats = genv.step()
+        assert np.all(st == 0), (k, np.nonzero(st)[0], st[st != 0])
+        newton_max = max(newton_max, stats["newton_iters"])
+        if k == k_cmp:
+            after = {e: genv.get_state(e) for e in samples}
+    assert newton_max < prm.newton_max
+    oenv = OracleEnv(scene, prm)
+    jobs = []
+    for e in samples:
+        x, v, yg, yd = before[e]
+        jobs.append((e, k_cmp, (x, v, from_gpu_y(genv, e, oenv, yg), yd), prm))
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(oracle_press_step, jobs))
+    for (e, _, (x, v, y, yd), _), r in zip(jobs, res):
+        assert r["status"] == 0
+        xg, _, ygn, _ = after[e]
+        ygn = from_gpu_y(genv, e, oenv, ygn)
+        err = np.abs(all_points(oenv, xg, ygn) - all_points(oenv, r["x"], r["y"])).max() / bbox_diag(oenv, x, y)
+        assert err <= 1e-4, (e, err)
+    genv.close()
 
 
 def test_config2_full_uneven_batch_mixed():

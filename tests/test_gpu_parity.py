@@ -779,3 +779,52 @@ def test_mixed_precision_tet_hessian_close_to_fp64():
     assert np.abs(hv32 - hv64).max() <= 1e-5 * np.abs(hv64).max()    # FP32 Hessian
     g64.close()
     g32.close()
+
+
+def _same_class(e0, start=1):
+    """A config-2 env of the same size class (grid, layers, sphere level) as
+    env e0 but with its own material, sphere radius and script."""
+    a = scenes.config2(e0)
+    for e in range(start, 400):
+        b = scenes.config2(e)
+        if (b.scene.gel_x.shape == a.scene.gel_x.shape and b.scene.gel_tets.shape == a.scene.gel_tets.shape
+                and b.scene.bodies[0].rest_x.shape == a.scene.bodies[0].rest_x.shape and b.scene.E != a.scene.E):
+            return a, b
+    raise AssertionError("no env of the same class")
+
+
+def test_reset_env_reuses_a_slot_like_a_fresh_context():
+    """ipc_reset_env puts a new request of the same size class into a used
+    env slot: its steps then match a fresh context holding only that request
+    (material, sphere radius and targets all replaced)."""
+    a, b = _same_class(0)
+    prm = scenes.SolverParams().parity()
+    other = scenes.config0()
+    slot = ipc.Envs([other.scene, a.scene], prm)
+    fresh = ipc.Envs([b.scene], prm)
+
+    def run(g, e, sc, ks):
+        for k in ks:
+            t = g.rest_y(e)
+            t[:, :3] += sc.delta(k)[:, :3]
+            g.set_targets(e, t)
+            st, _ = g.step([e])
+            assert st[0] == ipc.IPC_OK
+    run(slot, 1, a, range(3))                 # the slot's first occupant
+    slot.reset_env(1, b.scene)
+    assert np.array_equal(slot.get_state(1)[0], fresh.get_state(0)[0])
+    assert np.allclose(slot.rest_y(1), fresh.rest_y(0), rtol=0, atol=1e-15)
+    run(slot, 1, b, range(3))
+    run(fresh, 0, b, range(3))
+    xs, vs, ys, _ = slot.get_state(1)
+    xf, vf, yf, _ = fresh.get_state(0)
+    diag = np.linalg.norm(xf.max(0) - xf.min(0))
+    # contact sums use atomics: equal to rounding, not bitwise
+    assert np.abs(xs - xf).max() <= 1e-8 * diag and np.abs(ys - yf).max() <= 1e-8 * diag
+    # a scene of another size class does not fit the slot
+    c = scenes.config2(1) if scenes.config2(1).scene.gel_x.shape != a.scene.gel_x.shape else scenes.config0()
+    with pytest.raises(ipc.IpcError) as ei:
+        slot.reset_env(1, c.scene)
+    assert ei.value.status == ipc.IPC_EINVAL and "topology" in str(ei.value)
+    slot.close()
+    fresh.close()

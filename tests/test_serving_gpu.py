@@ -1,6 +1,8 @@
-"""Continuous batching on the GPU: requests admitted into overlapping
-cohorts give, for every request, the same result as that request run alone
-in its own context: whole multi-step requests at the FP64 parity tolerances
+"""Continuous batching on the GPU: requests loaded into the env slots of
+resident per-class pools (a finished request's slot takes the next request
+of its class; pools of different classes step on their own streams) give,
+for every request, the same result as that request run alone in its own
+context: whole multi-step requests at the FP64 parity tolerances
 (1e-6 of the bounding-box diagonal), and single mixed-precision steps from
 in-contact states at the mixed bar (1e-4), the per-step form in which the
 tolerances are stated.  (At the mixed benchmark tolerances whole trajectories
@@ -19,23 +21,37 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from paper_2504_12908_b300 import ipc  # noqa: E402
 from paper_2504_12908_b300.build import build  # noqa: E402
-from paper_2504_12908_b300.serving import GpuEngine, Request, Server  # noqa: E402
+from paper_2504_12908_b300.serving import GpuEngine, Request, Server, topology_key  # noqa: E402
 
 build()
 
 
 def _requests():
+    # two classes with several requests each (slots get reused) and two
+    # classes with one request; the config-2 pair shares a size class but
+    # not material, sphere radius or script
+    a, b = _same_class2()
     scs = [scenes.small_contact_scene(body="sphere", level=1, depth=2e-4, n_steps=5),
            scenes.config0(),
-           scenes.small_contact_scene(body="cube", depth=1e-4, n_steps=4),
-           scenes.config2(1),
-           scenes.small_contact_scene(body="sphere", level=2, depth=3e-4, n_steps=6),
-           scenes.config4_request(7, n_steps=6)]
-    steps = [5, 6, 4, 6, 6, 6]
-    arrival = [0.0, 0.0, 0.02, 0.04, 0.06, 0.08]
+           scenes.small_contact_scene(body="sphere", level=1, depth=1e-4, n_steps=4),
+           a,
+           scenes.small_contact_scene(body="sphere", level=1, depth=3e-4, n_steps=6),
+           b,
+           scenes.small_contact_scene(body="cube", depth=1e-4, n_steps=4)]
+    steps = [5, 6, 4, 5, 6, 4, 4]
+    arrival = [0.0, 0.0, 0.02, 0.04, 0.06, 0.08, 0.08]
     reqs = [Request(rid=i, scene=sc.scene, delta=sc.delta, n_steps=steps[i], arrival=arrival[i])
             for i, sc in enumerate(scs)]
     return reqs
+
+
+def _same_class2():
+    a = scenes.config2(0)
+    for e in range(1, 400):
+        b = scenes.config2(e)
+        if topology_key(b.scene) == topology_key(a.scene) and b.scene.E != a.scene.E:
+            return a, b
+    raise AssertionError("no env of the same class")
 
 
 def _alone(req, prm):
@@ -74,10 +90,10 @@ def test_each_request_is_the_same_alone_and_in_the_mix(graphs):
     within the FP64 bar of 1e-6 of the bbox diagonal per step."""
     prm = scenes.SolverParams().parity()
     reqs = _requests()
-    srv = Server(GpuEngine(prm, graphs=graphs), max_cohort=2, max_cohorts=3, mem_reserve=1 << 30)
+    srv = Server(GpuEngine(prm, graphs=graphs), slots_per_pool=2, mem_reserve=1 << 30)
     rep = srv.run(reqs)
     assert rep.completed == len(reqs) and rep.backlog == 0
-    assert rep.cohorts >= 3
+    assert rep.pools == 4 and rep.slot_reuses >= 1
     assert rep.env_steps == sum(r.n_steps for r in reqs)
     _compare(rep, reqs, prm, 1e-6)
 
@@ -105,7 +121,7 @@ def test_mixed_precision_steps_are_the_same_alone_and_in_the_mix():
         def delta(k, d=r.delta, k0=k0):
             return d(k0 + k)
         one.append(Request(rid=r.rid, scene=r.scene, delta=delta, n_steps=1, arrival=r.arrival, state=state))
-    srv = Server(GpuEngine(prm, graphs=True), max_cohort=2, max_cohorts=3, mem_reserve=1 << 30)
+    srv = Server(GpuEngine(prm, graphs=True), slots_per_pool=2, mem_reserve=1 << 30)
     rep = srv.run(one)
-    assert rep.completed == len(one) and rep.cohorts >= 3
+    assert rep.completed == len(one) and rep.pools == 4
     _compare(rep, one, prm, 1e-4)
