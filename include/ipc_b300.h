@@ -448,7 +448,9 @@ ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double*
  * weight [n] (multiplies c(x) b(d)), eps_x [n] (mollifier threshold, EE
  * only); energy [n], grad [n][12], hess [n][12][12] (project = 1: negative
  * eigenvalues set to zero, 2: replaced by their absolute values, 0: the
- * exact Hessian). */
+ * exact Hessian).  project | 8: the Hessian is formed and projected in FP32
+ * from the FP64 per-pair factors, as the mixed-precision step does, and
+ * written widened to FP64; energy and gradient stay FP64. */
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight,
                          const double* eps_x, double dhat, double* energy, double* grad,
                          double* hess, int project, void* stream);

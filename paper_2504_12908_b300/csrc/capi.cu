@@ -1452,7 +1452,8 @@ ipc_status ipc_k_tet(int n, const double* x, const double* Dm_inv, const double*
 
 ipc_status ipc_k_barrier(int n, const double* X, const int32_t* is_ee, const double* weight, const double* eps_x,
                          double dhat, double* energy, double* grad, double* hess, int project, void* stream) {
-  if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0) || project < 0 || project > 2) return IPC_EINVAL;
+  if (n < 0 || (n > 0 && (!X || !is_ee || !weight)) || !(dhat > 0) || project < 0 || (project & ~8) > 2)
+    return IPC_EINVAL;
   launch_k_barrier(n, X, is_ee, weight, eps_x, dhat, energy, grad, hess, project,
                    reinterpret_cast<cudaStream_t>(stream));
   return cudaGetLastError() == cudaSuccess ? IPC_OK : IPC_ECUDA;

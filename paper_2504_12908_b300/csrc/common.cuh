@@ -113,6 +113,13 @@ IPC_DEV int find_env(const int* off, int n_envs, int i) {
 }
 
 // ---------------------------------------------------------------- small dense
+// Jacobi stopping threshold on (off-diagonal / diagonal) squared norms: far
+// below FP64 rounding, and at FP32 rounding for float (sweeps beyond it
+// only rotate rounding noise).
+template <class T> struct JacobiTol;
+template <> struct JacobiTol<double> { static constexpr double v = 1e-30; };
+template <> struct JacobiTol<float> { static constexpr float v = 1e-12f; };
+
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in place:
 // on return A's diagonal holds the eigenvalues, V (row-major, columns =
 // eigenvectors).  Bounded number of sweeps.
@@ -126,7 +133,7 @@ IPC_HD void jacobi_eigen(T* A, T* V, int max_sweeps = 12) {
       diag += A[i * n + i] * A[i * n + i];
       for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
     }
-    if (off <= T(1e-30) * diag || off == T(0)) break;
+    if (off <= JacobiTol<T>::v * diag || off == T(0)) break;
     for (int p = 0; p < n - 1; ++p) {
       for (int q = p + 1; q < n; ++q) {
         T apq = A[p * n + q];

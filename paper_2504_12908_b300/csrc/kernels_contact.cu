@@ -401,14 +401,16 @@ __global__ void k_barrier(Dev d, int flag) {
   int e;
   int k = pair_at(d, f, e);
   int cvs[4] = {0, 0, 0, 0};
-  double E, g[12], H[144];
+  double E, g[12];
+  HT H[144];
   bool act = false;
   if (ENVI(d, e, flag)) {
     int4 v = d.pair_v[k];
     cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
     D3 X[4];
     for (int i = 0; i < 4; ++i) X[i] = ld3(d.cvx, cvs[i]);
-    act = pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H, newton_filter(d, e));
+    act = pair_barrier<HT>(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, g, H,
+                           newton_filter(d, e));
     d.pair_act[k] = act ? 1 : 0;
   }
   // the active pairs of an env fill its slots env_pair_off[e] + [0, I_NACT)
@@ -428,7 +430,7 @@ __global__ void k_barrier(Dev d, int flag) {
   // interleaved by warp of slots so that the mat-vec's loads coalesce
   HT* Hs = reinterpret_cast<HT*>(d.pair_H) + (long long)(slot >> 5) * 78 * 32 + (slot & 31);
   for (int p = 0, o = 0; p < 12; ++p)
-    for (int q = p; q < 12; ++q, ++o) Hs[o * 32] = (HT)H[p * 12 + q];
+    for (int q = p; q < 12; ++q, ++o) Hs[o * 32] = H[p * 12 + q];
   const uint8_t tag = touch_tag(d, e);
   for (int i = 0; i < 4; ++i) touch_cv(d, cvs[i], tag);
   for (int i = 0; i < 4; ++i) scatter_cv(d, d.qc, cvs[i], D3{g[3 * i], g[3 * i + 1], g[3 * i + 2]});
@@ -439,7 +441,7 @@ __global__ void k_barrier(Dev d, int flag) {
     int row = d.cv_row[cv];
     if (d.row_kind[row] == ROW_PINNED) continue;
     for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) atomicAdd(d.pc_acc + 9 * row + 3 * a + b, H[(3 * i + a) * 12 + 3 * i + b]);
+      for (int b = 0; b < 3; ++b) atomicAdd(d.pc_acc + 9 * row + 3 * a + b, (double)H[(3 * i + a) * 12 + 3 * i + b]);
   }
   int done_body[4] = {-1, -1, -1, -1};
   for (int i = 0; i < 4; ++i) {
@@ -450,18 +452,18 @@ __global__ void k_barrier(Dev d, int flag) {
     done_body[i] = b;
     if (seen) continue;
     // M_kl (3x3 blocks k,l in 0..3) = sum_{i,j on b} w_ik w_jl H_ij, w = [1, xbar]
-    double wv[4][4];
+    HT wv[4][4];
     bool on[4];
     for (int m = 0; m < 4; ++m) {
       on[m] = d.cv_body[cvs[m]] == b;
       D3 xb = ld3(d.cv_xbar, cvs[m]);
-      wv[m][0] = 1.0; wv[m][1] = xb.x; wv[m][2] = xb.y; wv[m][3] = xb.z;
+      wv[m][0] = HT(1); wv[m][1] = (HT)xb.x; wv[m][2] = (HT)xb.y; wv[m][3] = (HT)xb.z;
     }
     for (int kk = 0; kk < 4; ++kk)
       for (int ll = 0; ll < 4; ++ll)
         for (int a = 0; a < 3; ++a)
           for (int c = 0; c < 3; ++c) {
-            double s = 0;
+            HT s = 0;
             for (int m = 0; m < 4; ++m) {
               if (!on[m]) continue;
               for (int n = 0; n < 4; ++n) {
@@ -469,7 +471,7 @@ __global__ void k_barrier(Dev d, int flag) {
                 s += wv[m][kk] * wv[n][ll] * H[(3 * m + a) * 12 + 3 * n + c];
               }
             }
-            atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, s);
+            atomicAdd(d.body_pc_acc + 144 * b + (3 * kk + a) * 12 + 3 * ll + c, (double)s);
           }
   }
   }
@@ -835,7 +837,7 @@ __global__ void k_pair_energy(Dev d, int use_alpha) {
   double D = pair_sqdist(X, d.pair_kind[k] == 1);
   double E = 0.0;
   if (!(D > 0.0)) E = INFINITY;
-  else pair_barrier(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, nullptr, nullptr);
+  else pair_barrier<double>(X, d.pair_kind[k] == 1, d.pair_w[k], d.pair_eps[k], d.dhat, &E, nullptr, nullptr);
   d.pair_E[k] = E;
   }
 }
@@ -1016,7 +1018,17 @@ __global__ void k_elem_barrier(int n, const double* X, const int* is_ee, const d
   for (int i = 0; i < 4; ++i) P[i] = ld3(X + 12 * (long long)k, i);
   double e = 0, gl[12];
   double* Hk = H ? H + 144 * (long long)k : nullptr;
-  bool act = pair_barrier(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, project);
+  const int filt = project & 3;
+  bool act;
+  if (project & 8) {  // the mixed mode's FP32 Hessian, widened on output
+    float Hf[144];
+    act = pair_barrier<float>(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr,
+                              Hk ? Hf : nullptr, filt);
+    if (Hk && act)
+      for (int i = 0; i < 144; ++i) Hk[i] = (double)Hf[i];
+  } else {
+    act = pair_barrier<double>(P, is_ee[k] != 0, w[k], eps ? eps[k] : 0.0, dhat, &e, g ? gl : nullptr, Hk, filt);
+  }
   if (E) E[k] = e;
   if (g)
     for (int i = 0; i < 12; ++i) g[12 * (long long)k + i] = act ? gl[i] : 0.0;

@@ -122,15 +122,13 @@ __device__ __forceinline__ void body_My_mul(double m, const double* S, const dou
 }
 
 // One warp per body (4 bodies per 128-thread CTA): the lanes build the
-// gradient and the 9x9 orthogonality Hessian entry by entry in shared
-// memory, lane 0 tests it for positive definiteness (and projects it when
-// it is not), the lanes write the 12x12 body Hessian.  A body's terms are a
-// few thousand FP64 operations: spread over a warp and kept in shared
-// memory they no longer set a multi-millisecond floor under the assembly of
-// the envs that are still iterating.
+// gradient entry by entry, lane 0 takes the SVD of the body's 3x3 affine
+// part, the lanes form the orthogonality term's nine Hessian eigenpairs in
+// closed form and the filtered 9x9 block from them, and write the 12x12
+// body Hessian.  No iterative eigen-decomposition runs: on B300 a serial
+// FP64 Jacobi sweep set a ~1 ms floor under every Newton iteration.
 __global__ void __launch_bounds__(128) k_body(Dev d) {
-  __shared__ double sy[4][12], sdy[4][12], sHo[4][81], swork[4][162];
-  __shared__ int s_pd[4];
+  __shared__ double sy[4][12], sdy[4][12], sHo[4][81], swork[4][120];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x * 4 + w;
   if (b >= d.n_bodies) return;                    // warp-uniform; no block barriers below
@@ -154,14 +152,6 @@ __global__ void __launch_bounds__(128) k_body(Dev d) {
   for (int k = 0; k < 3; ++k)
     for (int l = 0; l < 3; ++l)
       C[3 * k + l] = a[3 * k] * a[3 * l] + a[3 * k + 1] * a[3 * l + 1] + a[3 * k + 2] * a[3 * l + 2] - (k == l ? 1.0 : 0.0);
-  // Ho (orthogonality Hessian, 9x9), 3 entries per lane
-  for (int idx = lane; idx < 81; idx += 32) {
-    const int row = idx / 9, col = idx - 9 * row;
-    const int mm = row / 3, i = row - 3 * mm, n = col / 3, j = col - 3 * n;
-    double v = a[3 * n + i] * a[3 * mm + j] + (i == j ? C[3 * mm + n] : 0.0);
-    if (mm == n) v += a[i] * a[j] + a[3 + i] * a[3 + j] + a[6 + i] * a[6 + j];
-    Ho[idx] = 4.0 * ko * v;
-  }
   // gradient: lane k < 12 owns entry k (inertia, gravity, orthogonality, AL)
   double gk = 0.0;
   if (lane < 12) {
@@ -196,10 +186,53 @@ __global__ void __launch_bounds__(128) k_body(Dev d) {
   __syncwarp();
   // a positive definite Hessian is its own projection (the common case near
   // rigid states); the eigen-decomposition only runs otherwise
-  if (lane == 0) {
-    const bool pd = is_pos_def<9, double>(Ho, swork[w]);
-    if (!pd) psd_project<9, double>(Ho, swork[w], newton_filter(d, e) == FILT_ABS);
-    s_pd[w] = pd;
+  // Projected orthogonality Hessian from its analytic eigensystem.  The
+  // term is ko Psi(A), Psi = |A A^T - I|_F^2 = sum_i (s_i^2 - 1)^2 over the
+  // singular values of A (rows a_k), an isotropic function of A, so with
+  // A = U diag(s) V^T the Hessian d2Psi/dA2 has the nine eigenpairs
+  //   U e_i e_i^T V^T                       12 s_i^2 - 4          (scaling)
+  //   U (e_i e_j^T -/+ e_j e_i^T) V^T / r2   4 (s_i^2 -/+ s_i s_j + s_j^2 - 1)
+  // (second derivative of Psi along each direction; the directions are
+  // orthonormal and the mixed second derivatives vanish).  The filter acts
+  // on these eigenvalues directly: no iterative eigen-decomposition.
+  double* U = swork[w];        // [9] row-major, columns u_k
+  double* V = swork[w] + 9;    // [9]
+  double* sv = swork[w] + 18;  // [3]
+  double* G = swork[w] + 24;   // [9 modes][9]
+  double* L = swork[w] + 105;  // [9] filtered eigenvalues
+  if (lane == 0) svd3<double>(a, U, sv, V);
+  __syncwarp();
+  if (lane < 9) {
+    const bool absval = newton_filter(d, e) == FILT_ABS;
+    int i, j;
+    double sg, lam;
+    if (lane < 3) {
+      i = j = lane;
+      sg = 0.0;
+      lam = 12.0 * sv[i] * sv[i] - 4.0;
+    } else {
+      const int pr = (lane - 3) >> 1;            // (0,1) (0,2) (1,2)
+      i = pr == 2 ? 1 : 0;
+      j = pr == 0 ? 1 : 2;
+      sg = (lane & 1) ? -1.0 : 1.0;              // lane 3, 5, 7: twist (-); 4, 6, 8: flip (+)
+      lam = 4.0 * (sv[i] * sv[i] + sg * sv[i] * sv[j] + sv[j] * sv[j] - 1.0);
+    }
+    const double nrm = lane < 3 ? 1.0 : 0.70710678118654752440;
+    for (int k = 0; k < 3; ++k)
+      for (int c = 0; c < 3; ++c) {
+        // (U E V^T)_kc, E = e_i e_j^T + sg e_j e_i^T (E = e_i e_i^T for scaling)
+        double g = U[3 * k + i] * V[3 * c + j];
+        if (lane >= 3) g += sg * U[3 * k + j] * V[3 * c + i];
+        G[9 * lane + 3 * k + c] = nrm * g;
+      }
+    L[lane] = absval ? fabs(lam) : fmax(lam, 0.0);
+  }
+  __syncwarp();
+  for (int idx = lane; idx < 81; idx += 32) {
+    const int row = idx / 9, col = idx - 9 * row;
+    double v = 0.0;
+    for (int m = 0; m < 9; ++m) v += L[m] * G[9 * m + row] * G[9 * m + col];
+    Ho[idx] = ko * v;
   }
   __syncwarp();
   double* H = d.body_H + 144 * (long long)b;

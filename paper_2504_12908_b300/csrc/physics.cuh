@@ -364,22 +364,31 @@ IPC_D double pair_sqdist(const D3* X, bool is_ee) {
   return cl.D;
 }
 
-// grad D (12) and hess D (12x12 row-major) from the closest-feature data.
-IPC_D void sqdist_derivs(const Closest& cl, double* gD, double* HD) {
+// grad D (12, FP64) from the closest-feature data.
+IPC_D void sqdist_grad(const Closest& cl, double* gD) {
   for (int i = 0; i < 4; ++i) {
     gD[3 * i + 0] = 2.0 * cl.w[i] * cl.r.x;
     gD[3 * i + 1] = 2.0 * cl.w[i] * cl.r.y;
     gD[3 * i + 2] = 2.0 * cl.w[i] * cl.r.z;
   }
+}
+
+// hess D (12x12 row-major) in T from the closest-feature data:
+// 2 (w w^T) (x) I3 - F Mi F^T.  The k x k system Mi (nearly singular for
+// near-parallel edges) and the factor F Mi are formed in FP64 and only the
+// final outer products in T, so T = float loses no more than its rounding
+// of well-scaled factors.
+template <class T>
+IPC_D void sqdist_hess(const Closest& cl, T* HD) {
   // f_qq = 2 (w w^T) (x) I3
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
-      double v = 2.0 * cl.w[i] * cl.w[j];
+      T v = T(2) * (T)cl.w[i] * (T)cl.w[j];
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) HD[(3 * i + a) * 12 + 3 * j + b] = (a == b) ? v : 0.0;
+        for (int b = 0; b < 3; ++b) HD[(3 * i + a) * 12 + 3 * j + b] = (a == b) ? v : T(0);
     }
   if (cl.k == 0) return;
-  // f_qtheta (12 x k) and f_thetatheta^{-1} (k x k)
+  // f_qtheta (12 x k) and f_thetatheta^{-1} (k x k), FP64
   double Fq[12][2];
   for (int i = 0; i < 4; ++i)
     for (int m = 0; m < cl.k; ++m) {
@@ -398,20 +407,32 @@ IPC_D void sqdist_derivs(const Closest& cl, double* gD, double* HD) {
     Mi[0][1] = Mi[1][0] = -m01 / det;
     Mi[1][1] = m00 / det;
   }
+  // HD -= (F Mi) F^T
+  T Ft[12][2], Gt[12][2];
   for (int p = 0; p < 12; ++p) {
-    double t0 = 0, t1 = 0;
     if (cl.k == 1) {
-      t0 = Fq[p][0] * Mi[0][0];
+      Gt[p][0] = (T)(Fq[p][0] * Mi[0][0]);
+      Gt[p][1] = T(0);
+      Ft[p][1] = T(0);
     } else {
-      t0 = Fq[p][0] * Mi[0][0] + Fq[p][1] * Mi[1][0];
-      t1 = Fq[p][0] * Mi[0][1] + Fq[p][1] * Mi[1][1];
+      Gt[p][0] = (T)(Fq[p][0] * Mi[0][0] + Fq[p][1] * Mi[1][0]);
+      Gt[p][1] = (T)(Fq[p][0] * Mi[0][1] + Fq[p][1] * Mi[1][1]);
+      Ft[p][1] = (T)Fq[p][1];
     }
+    Ft[p][0] = (T)Fq[p][0];
+  }
+  for (int p = 0; p < 12; ++p)
     for (int q = 0; q < 12; ++q) {
-      double s = t0 * Fq[q][0];
-      if (cl.k == 2) s += t1 * Fq[q][1];
+      T s = Gt[p][0] * Ft[q][0];
+      if (cl.k == 2) s += Gt[p][1] * Ft[q][1];
       HD[p * 12 + q] -= s;
     }
-  }
+}
+
+// grad D (12) and hess D (12x12 row-major), both FP64.
+IPC_D void sqdist_derivs(const Closest& cl, double* gD, double* HD) {
+  sqdist_grad(cl, gD);
+  sqdist_hess<double>(cl, HD);
 }
 
 // b(d) and derivatives w.r.t. d (App. A.3, Eq. ipc_energy), valid for 0 < d < dhat.
@@ -424,47 +445,42 @@ IPC_HD void barrier_d(double d, double dhat, double& b, double& b1, double& b2) 
 }
 
 // Skew matrix [u]x applied bookkeeping: S[a][b] such that (u x v)_a = S[a][b] v_b
-IPC_HD void skew(D3 u, double S[3][3]) {
+template <class T>
+IPC_HD void skew(V3<T> u, T S[3][3]) {
   S[0][0] = 0;    S[0][1] = -u.z; S[0][2] = u.y;
   S[1][0] = u.z;  S[1][1] = 0;    S[1][2] = -u.x;
   S[2][0] = -u.y; S[2][1] = u.x;  S[2][2] = 0;
 }
 
-// Mollifier argument x = |(a1 - a0) x (b1 - b0)|^2 with gradient / Hessian.
-IPC_D double ee_cross2(const D3* X, double* gx, double* Hx) {
-  D3 ea = X[1] - X[0], eb = X[3] - X[2];
-  D3 n = cross(ea, eb);
-  double x = norm2(n);
-  if (!gx) return x;
-  D3 ga = 2.0 * cross(eb, n);  // d x / d ea
-  D3 gb = 2.0 * cross(n, ea);  // d x / d eb
-  const double sg[4] = {-1.0, 1.0, -1.0, 1.0};
-  for (int c = 0; c < 3; ++c) {
-    gx[c] = -comp(ga, c); gx[3 + c] = comp(ga, c);
-    gx[6 + c] = -comp(gb, c); gx[9 + c] = comp(gb, c);
-  }
-  double Sa[3][3], Sb[3][3], Sn[3][3];
+// Hessian (12x12, T) of the mollifier argument x = |(a1 - a0) x (b1 - b0)|^2.
+template <class T>
+IPC_D void ee_cross2_hess(const D3* X, T* Hx) {
+  const D3 ead = X[1] - X[0], ebd = X[3] - X[2];
+  const V3<T> ea{(T)ead.x, (T)ead.y, (T)ead.z}, eb{(T)ebd.x, (T)ebd.y, (T)ebd.z};
+  const V3<T> n = cross(ea, eb);
+  const T sg[4] = {T(-1), T(1), T(-1), T(1)};
+  T Sa[3][3], Sb[3][3], Sn[3][3];
   skew(ea, Sa); skew(eb, Sb); skew(n, Sn);
-  double Haa[3][3], Hbb[3][3], Hab[3][3];
+  T Haa[3][3], Hbb[3][3], Hab[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      double sbb = 0, saa = 0, sba = 0;
+      T sbb = 0, saa = 0, sba = 0;
       for (int k = 0; k < 3; ++k) {
         sbb += Sb[i][k] * Sb[k][j];
         saa += Sa[i][k] * Sa[k][j];
         sba += Sb[i][k] * Sa[k][j];
       }
-      Haa[i][j] = -2.0 * sbb;
-      Hbb[i][j] = -2.0 * saa;
-      Hab[i][j] = 2.0 * (-Sn[i][j] + sba);
+      Haa[i][j] = T(-2) * sbb;
+      Hbb[i][j] = T(-2) * saa;
+      Hab[i][j] = T(2) * (-Sn[i][j] + sba);
     }
   for (int P = 0; P < 4; ++P)
     for (int Q = 0; Q < 4; ++Q) {
-      double s = sg[P] * sg[Q];
+      T s = sg[P] * sg[Q];
       bool pa = P < 2, qa = Q < 2;
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-          double v;
+          T v;
           if (pa && qa) v = Haa[i][j];
           else if (!pa && !qa) v = Hbb[i][j];
           else if (pa) v = Hab[i][j];
@@ -472,6 +488,23 @@ IPC_D double ee_cross2(const D3* X, double* gx, double* Hx) {
           Hx[(3 * P + i) * 12 + 3 * Q + j] = s * v;
         }
     }
+}
+
+// Mollifier argument x = |(a1 - a0) x (b1 - b0)|^2 with its gradient (gx,
+// when non-null) and Hessian (Hx, when non-null), FP64.
+IPC_D double ee_cross2(const D3* X, double* gx, double* Hx) {
+  D3 ea = X[1] - X[0], eb = X[3] - X[2];
+  D3 n = cross(ea, eb);
+  double x = norm2(n);
+  if (gx) {
+    D3 ga = 2.0 * cross(eb, n);  // d x / d ea
+    D3 gb = 2.0 * cross(n, ea);  // d x / d eb
+    for (int c = 0; c < 3; ++c) {
+      gx[c] = -comp(ga, c); gx[3 + c] = comp(ga, c);
+      gx[6 + c] = -comp(gb, c); gx[9 + c] = comp(gb, c);
+    }
+  }
+  if (Hx) ee_cross2_hess<double>(X, Hx);
   return x;
 }
 
@@ -481,82 +514,91 @@ IPC_D double ee_cross2(const D3* X, double* gx, double* Hx) {
 // gD = 2 w (x) r and hess D = 2 (w w^T (x) I3) - F Mi F^T with
 // F_m = 2 (c_m (x) r + w (x) R_m).  With Q an orthonormal basis of that span
 // (dimension <= 5), H = Q (Q^T H Q) Q^T and the clamp acts on the small matrix.
-static __host__ __device__ __noinline__ void gs_push(double (*Q)[12], int& nq, double* u) {
-  double n0 = 0;
+// Gram-Schmidt acceptance threshold on |u|^2 after / before (relative)
+template <class T> struct GsTol;
+template <> struct GsTol<double> { static constexpr double v = 1e-24; };
+template <> struct GsTol<float> { static constexpr float v = 1e-8f; };
+
+template <class T>
+static __host__ __device__ __noinline__ void gs_push(T (*Q)[12], int& nq, T* u) {
+  T n0 = 0;
   for (int p = 0; p < 12; ++p) n0 += u[p] * u[p];
-  if (!(n0 > 0.0)) return;
+  if (!(n0 > T(0))) return;
   for (int round = 0; round < 2; ++round)  // two rounds of Gram-Schmidt
     for (int j = 0; j < nq; ++j) {
-      double dd = 0;
+      T dd = 0;
       for (int p = 0; p < 12; ++p) dd += Q[j][p] * u[p];
       for (int p = 0; p < 12; ++p) u[p] -= dd * Q[j][p];
     }
-  double n1 = 0;
+  T n1 = 0;
   for (int p = 0; p < 12; ++p) n1 += u[p] * u[p];
-  if (!(n1 > 1e-24 * n0)) return;
-  double inv = 1.0 / sqrt(n1);
+  if (!(n1 > GsTol<T>::v * n0)) return;
+  T inv = T(1) / sqrt(n1);
   for (int p = 0; p < 12; ++p) Q[nq][p] = u[p] * inv;
   ++nq;
 }
 
-static __host__ __device__ __noinline__ void psd_project_closest(const Closest& cl, double* H, bool absval) {
-  double Q[5][12];
+template <class T>
+static __host__ __device__ __noinline__ void psd_project_closest(const Closest& cl, T* H, bool absval) {
+  T Q[5][12];
   int nq = 0;
-  double u[12];
+  T u[12];
   for (int c = 0; c < 3; ++c) {
     for (int i = 0; i < 4; ++i)
-      for (int a = 0; a < 3; ++a) u[3 * i + a] = (a == c) ? cl.w[i] : 0.0;
-    gs_push(Q, nq, u);
+      for (int a = 0; a < 3; ++a) u[3 * i + a] = (a == c) ? (T)cl.w[i] : T(0);
+    gs_push<T>(Q, nq, u);
   }
+  const T rx = (T)cl.r.x, ry = (T)cl.r.y, rz = (T)cl.r.z;
   for (int m = 0; m < cl.k; ++m) {
     for (int i = 0; i < 4; ++i) {
-      u[3 * i] = cl.c[i][m] * cl.r.x;
-      u[3 * i + 1] = cl.c[i][m] * cl.r.y;
-      u[3 * i + 2] = cl.c[i][m] * cl.r.z;
+      const T cm = (T)cl.c[i][m];
+      u[3 * i] = cm * rx;
+      u[3 * i + 1] = cm * ry;
+      u[3 * i + 2] = cm * rz;
     }
-    gs_push(Q, nq, u);
+    gs_push<T>(Q, nq, u);
   }
   // M = Q^T H Q (padded to 5x5)
-  double HQ[12][5];
+  T HQ[12][5];
   for (int p = 0; p < 12; ++p)
     for (int j = 0; j < 5; ++j) {
-      double acc = 0;
+      T acc = 0;
       if (j < nq)
         for (int q = 0; q < 12; ++q) acc += H[p * 12 + q] * Q[j][q];
       HQ[p][j] = acc;
     }
-  double M[25], V[25];
+  T M[25], V[25];
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j) {
-      double acc = 0;
+      T acc = 0;
       if (i < nq && j < nq)
         for (int p = 0; p < 12; ++p) acc += Q[i][p] * HQ[p][j];
       M[5 * i + j] = acc;
     }
   for (int i = 0; i < 5; ++i)
     for (int j = i + 1; j < 5; ++j) {
-      double sm = 0.5 * (M[5 * i + j] + M[5 * j + i]);
+      T sm = T(0.5) * (M[5 * i + j] + M[5 * j + i]);
       M[5 * i + j] = M[5 * j + i] = sm;
     }
-  jacobi_eigen<5, double>(M, V, 20);
+  jacobi_eigen<5, T>(M, V, 20);
   bool neg = false;
-  for (int k = 0; k < 5; ++k) neg |= M[6 * k] < 0.0;
+  for (int k = 0; k < 5; ++k) neg |= M[6 * k] < T(0);
   if (!neg) return;
   // H = sum_k f(l_k) (Q^T v_k)(Q^T v_k)^T, f(l) = max(l, 0) or |l|
-  double Y[5][12];
+  T Y[5][12];
   for (int k = 0; k < 5; ++k)
     for (int p = 0; p < 12; ++p) {
-      double acc = 0;
+      T acc = 0;
       for (int i = 0; i < nq; ++i) acc += Q[i][p] * V[5 * i + k];
       Y[k][p] = acc;
     }
   for (int p = 0; p < 12; ++p)
     for (int q = p; q < 12; ++q) {
-      double acc = 0;
+      T acc = 0;
       for (int k = 0; k < 5; ++k) {
-        double l = M[6 * k];
+        T l = M[6 * k];
         if (absval) l = fabs(l);
-        if (l > 0.0) acc += l * Y[k][p] * Y[k][q];
+        if (l > T(0)) acc += l * Y[k][p] * Y[k][q];
       }
       H[p * 12 + q] = acc;
       H[q * 12 + p] = acc;
@@ -564,16 +606,21 @@ static __host__ __device__ __noinline__ void psd_project_closest(const Closest& 
 }
 
 // full 12x12 eigen-filter with its own scratch
-static __host__ __device__ __noinline__ void psd_project12(double* H, bool absval) {
-  double scratch[288];
-  psd_project<12, double>(H, scratch, absval);
+template <class T>
+static __host__ __device__ __noinline__ void psd_project12(T* H, bool absval) {
+  T scratch[288];
+  psd_project<12, T>(H, scratch, absval);
 }
 
 // Weighted barrier of one pair: E = w c(x) b(d).  Returns false when the
-// pair is inactive (d >= dhat): E = 0 and g/H untouched.  g (12) and H
-// (144, PSD-projected) are written when non-null.  `work` holds 288 doubles.
+// pair is inactive (d >= dhat): E = 0 and g/H untouched.  g (12, FP64) and
+// H (144, PSD-projected, arithmetic type T) are written when non-null.  The
+// distance, the barrier and mollifier derivatives and the gradient are FP64
+// whatever T; with T = float the Hessian is formed and projected in FP32
+// from the FP64 per-pair factors (the mixed mode stores it in FP32).
+template <class T>
 IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double dhat,
-                        double* E, double* g, double* H, int filt = FILT_CLAMP) {
+                        double* E, double* g, T* H, int filt = FILT_CLAMP) {
   Closest cl;
   classify(X, is_ee, cl);
   double D = cl.D;
@@ -597,9 +644,9 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
   }
   *E = w * c * b;
   if (!g && !H) return true;
-  double gD[12], HD[144], gx[12], Hx[144];
-  sqdist_derivs(cl, gD, HD);
-  if (moll) ee_cross2(X, gx, Hx);
+  double gD[12], gx[12];
+  sqdist_grad(cl, gD);
+  if (moll) ee_cross2(X, gx, nullptr);
   if (g) {
     for (int p = 0; p < 12; ++p) {
       double gb = bD1 * gD[p];
@@ -607,28 +654,45 @@ IPC_D bool pair_barrier(const D3* X, bool is_ee, double w, double eps_x, double 
     }
   }
   if (H) {
+    // H = w c (bD2 gD gD^T + bD1 hess D)
+    //   + w [bD1 (gD gx^T + gx gD^T) c1 + b (c2 gx gx^T + c1 hess x)]  (mollified)
+    // with the per-pair factors folded into FP64 vectors first
+    T HD[144];
+    sqdist_hess<T>(cl, HD);
+    T u[12], v[12];
+    const double wc = w * c;
+    for (int p = 0; p < 12; ++p) {
+      u[p] = (T)gD[p];
+      v[p] = (T)(wc * bD2 * gD[p]);
+    }
+    const T khd = (T)(wc * bD1);
     for (int p = 0; p < 12; ++p)
-      for (int q = 0; q < 12; ++q) {
-        double hb = bD2 * gD[p] * gD[q] + bD1 * HD[p * 12 + q];
-        double v = c * hb;
-        if (moll) {
-          double gbp = bD1 * gD[p], gbq = bD1 * gD[q];
-          double gcp = c1 * gx[p], gcq = c1 * gx[q];
-          double hc = c2 * gx[p] * gx[q] + c1 * Hx[p * 12 + q];
-          v += gbp * gcq + gcp * gbq + b * hc;
-        }
-        H[p * 12 + q] = w * v;
+      for (int q = 0; q < 12; ++q) H[p * 12 + q] = v[p] * u[q] + khd * HD[p * 12 + q];
+    if (moll) {
+      T* Hx = HD;  // reuse
+      ee_cross2_hess<T>(X, Hx);
+      T ga[12], gc[12], gh[12], gxt[12];
+      for (int p = 0; p < 12; ++p) {
+        ga[p] = (T)(w * bD1 * gD[p]);
+        gc[p] = (T)(c1 * gx[p]);
+        gh[p] = (T)(w * b * c2 * gx[p]);
+        gxt[p] = (T)gx[p];
       }
+      const T khx = (T)(w * b * c1);
+      for (int p = 0; p < 12; ++p)
+        for (int q = 0; q < 12; ++q)
+          H[p * 12 + q] += ga[p] * gc[q] + gc[p] * ga[q] + gh[p] * gxt[q] + khx * Hx[p * 12 + q];
+    }
     // symmetrise then project: low-rank exact projection unless mollified
     for (int p = 0; p < 12; ++p)
       for (int q = p + 1; q < 12; ++q) {
-        double s = 0.5 * (H[p * 12 + q] + H[q * 12 + p]);
+        T s = T(0.5) * (H[p * 12 + q] + H[q * 12 + p]);
         H[p * 12 + q] = s;
         H[q * 12 + p] = s;
       }
     if (filt == FILT_NONE) return true;
-    if (moll) psd_project12(H, filt == FILT_ABS);
-    else psd_project_closest(cl, H, filt == FILT_ABS);
+    if (moll) psd_project12<T>(H, filt == FILT_ABS);
+    else psd_project_closest<T>(cl, H, filt == FILT_ABS);
   }
   return true;
 }

@@ -587,10 +587,13 @@ def k_tet(x, Dm_inv, vol, mu: float, lam: float, energy=None, grad=None, hess=No
         raise IpcError(st, "ipc_k_tet")
 
 
-def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None, project=True):
+def k_barrier(X, is_ee, weight, eps_x, dhat: float, energy=None, grad=None, hess=None, project=True,
+              hess_fp32=False):
+    """Pair barrier element kernel on torch CUDA tensors; hess_fp32 forms and
+    projects the Hessian in FP32 (the mixed-precision step's arithmetic)."""
     n = int(X.shape[0])
     st = lib().ipc_k_barrier(n, _vp(X), _vp(is_ee), _vp(weight), _vp(eps_x), float(dhat), _vp(energy), _vp(grad),
-                             _vp(hess), _filter_code(project), _stream_ptr(X))
+                             _vp(hess), _filter_code(project) | (8 if hess_fp32 else 0), _stream_ptr(X))
     if st != IPC_OK:
         raise IpcError(st, "ipc_k_barrier")
 

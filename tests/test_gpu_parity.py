@@ -181,6 +181,40 @@ def test_element_kernels_abs_filter_match_oracle():
     assert np.median(err) < 1e-10 and err.max() < 1e-4, (err.max(), np.argmax(err))
 
 
+@pytest.mark.parametrize("project", [False, True, "abs"])
+def test_barrier_kernel_fp32_hessian_matches_oracle(project):
+    """The mixed mode's pair Hessian: distance, barrier factors and gradient
+    in FP64, the Hessian formed and projected in FP32.  Bar, per pair and
+    relative to its largest entry: FP32 rounding (6e-8) through a few
+    hundred operations and a 5x5 / 12x12 FP32 eigen-decomposition (stopped at
+    1e-6 relative off-diagonal), i.e. 1e-5 for the median pair and 1e-3 for
+    the worst (near-parallel mollified edges, whose clamped eigenvalues sit
+    near zero)."""
+    rng = np.random.default_rng(14)
+    dhat = 1e-4
+    X, is_ee, w, eps = _random_pairs(800, rng, dhat)
+    n = len(X)
+    E = torch.zeros(n, device=DEV, dtype=torch.float64)
+    g = torch.zeros(n, 12, device=DEV, dtype=torch.float64)
+    H = torch.zeros(n, 12, 12, device=DEV, dtype=torch.float64)
+    ipc.k_barrier(T(X), T(is_ee, torch.int32), T(w), T(eps), dhat, E, g, H, project=project, hess_fp32=True)
+    torch.cuda.synchronize()
+    Eo, go, Ho = ods.pair_barrier(X, is_ee.astype(bool), w, eps, dhat, order=2, project=project)
+    act = Eo > 0
+    Eg, gg, Hg = E.cpu().numpy(), g.cpu().numpy(), H.cpu().numpy()
+    assert np.all(Hg[~act] == 0.0)
+    # energy and gradient stay FP64
+    assert np.allclose(Eg[act], Eo[act], rtol=1e-10)
+    gs = np.abs(go[act]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(gg[act] - go[act]) <= 1e-8 * gs)
+    Hs = np.abs(Ho[act]).max(axis=(1, 2), keepdims=True)
+    err = (np.abs(Hg[act] - Ho[act]) / Hs).max(axis=(1, 2))
+    assert np.median(err) < 1e-5 and err.max() < 1e-3, (np.median(err), err.max(), np.argmax(err))
+    if project:   # still PSD (to FP32 rounding of the largest eigenvalue)
+        lmin = np.linalg.eigvalsh(Hg[act]).min(axis=1)
+        assert np.all(lmin >= -1e-5 * Hs[:, 0, 0])
+
+
 def test_barrier_kernel_raw_hessian_matches_oracle():
     rng = np.random.default_rng(12)
     dhat = 1e-4

@@ -92,7 +92,9 @@ def test_each_request_is_the_same_alone_and_in_the_mix(graphs):
     reqs = _requests()
     srv = Server(GpuEngine(prm, graphs=graphs), slots_per_pool=2, mem_reserve=1 << 30)
     rep = srv.run(reqs)
-    assert rep.completed == len(reqs) and rep.backlog == 0
+    bad = {rid: (r.status, r.steps, reqs[rid].n_steps, r.slot) for rid, r in rep.results.items()
+           if r.status != 0 or r.steps != reqs[rid].n_steps}
+    assert rep.completed == len(reqs) and rep.backlog == 0, str(bad)
     assert rep.pools == 4 and rep.slot_reuses >= 1
     assert rep.env_steps == sum(r.n_steps for r in reqs)
     _compare(rep, reqs, prm, 1e-6)
