@@ -282,6 +282,37 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n,
  * and leaves per_env_status untouched. */
 ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stats* stats);
 
+/* n_steps time steps of each listed env (env_ids NULL = all envs) in one
+ * call, each env on its own schedule: the same per-step computation as
+ * n_steps calls of ipc_step (App. A.2), but an env whose step converges
+ * begins its next step while the slower envs of the batch are still
+ * iterating, so a few hard steps no longer hold the whole batch.  Targets
+ * of step k of env e come from dev_targets[k][e][max_bodies][12] (device
+ * memory, all envs of the context, layout of ipc_set_targets_all; caller
+ * owned, read during the rollout, may be NULL without driven bodies).
+ * steps_per_env (host, n entries in env_ids' order, or NULL): env i runs
+ * min(steps_per_env[i], n_steps) steps (IPC_EINVAL if negative).  An
+ * env whose step fails (any status but IPC_OK) stops after that step: its
+ * state is what ipc_step would have left.
+ *   per_env_status: n statuses (the failing step's, else IPC_OK);
+ *   per_env_steps: n counts of the steps taken (n_steps unless one failed);
+ *   stats: the counters summed over the rollout's steps (newton_iters,
+ *   al_updates, max_pairs, accd_iters_max: maxima over env-steps).
+ * With all three NULL the call only enqueues the rollout (one CUDA graph,
+ * captured at the first call; no host round trip) on the ctx stream and
+ * returns; ipc_rollout_results reads the results.  With profiling on
+ * (ipc_profile_enable) the same loop runs as plain launches driven from
+ * the host.  Not in the paper: a batching property of this library; the
+ * caller gives up per-step host control (targets are fixed in advance). */
+ipc_status ipc_rollout(ipc_ctx* ctx, const int32_t* env_ids, int n, int n_steps, const int32_t* steps_per_env,
+                       const double* dev_targets, int32_t* per_env_status, int32_t* per_env_steps,
+                       ipc_step_stats* stats);
+
+/* Results of the last ipc_rollout (synchronises the ctx stream); any
+ * pointer may be NULL. */
+ipc_status ipc_rollout_results(ipc_ctx* ctx, int32_t* per_env_status, int32_t* per_env_steps,
+                               ipc_step_stats* stats);
+
 /* Per-env counters of the last ipc_step that included `env` (host only; the
  * values were read back at the end of that step).  out[IPC_ENV_STATS]:
  *   0 status, 1 Newton iterations, 2 AL multiplier updates, 3 PCG

@@ -260,6 +260,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_ctl = c.take<unsigned int>(8);
   d.step_ctl = c.take<unsigned int>(8);
+  d.roll_ctl = c.take<unsigned long long>(4);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
   d.pc = c.take<double>(6 * (size_t)pk.n_rows);
@@ -312,9 +313,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.fr_ml = c.take<double>(nfr);
   d.fr_S = c.take<double>(6 * nfr);
   d.fr_E = c.take<double>(nfr);
-  d.fr_list = c.take<int>(nfr);
-  d.fr_list_env = c.take<int>(nfr);
-  d.fr_count = c.take<int>(1);
+  d.fr_scan = c.take<int>(pk.n_envs + 1);
   d.accd_tail = c.take<int4>(pk.n_pairs_cap);
   d.accd_tail_t = c.take<double>(pk.n_pairs_cap);
   d.accd_tail_ctl = c.take<unsigned int>(2);
@@ -587,92 +586,205 @@ ipc_status run_pcg(ipc_ctx* ctx) {
 // CTA), so a step needs no host round trip; every loop is bounded by its
 // iteration cap on the device.  Capture streams: cap[0] fills the Newton
 // body, cap[1] the PCG and line-search bodies, cap[2] the trial loop.
+// Adds a conditional node of `type` on h after what the capturing stream cs
+// holds, and captures `fill` into its body on stream bs.
+template <class F>
+cudaError_t cond_body(cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType t,
+                      F&& fill) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = add_conditional(cs, h, t, &g);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  e = fill();
+  cudaGraph_t g2 = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(bs, &g2);
+  return e != cudaSuccess ? e : e2;
+}
+
+// One Newton iteration of the envs still iterating, captured on cap[0]:
+// assembly, the PCG WHILE (body on cap[1]), the Newton decision, the
+// line-search IF (cap[1]) with its trial WHILE (cap[2]).  Launch counts of
+// its parts go to *base (once per iteration), *pcg_iter, *ls_prep, *ls_trial.
+struct IterLaunches {
+  long long base = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0;
+};
+cudaError_t capture_newton_iteration(ipc_ctx* ctx, cudaGraphConditionalHandle hP, cudaGraphConditionalHandle hA,
+                                     cudaGraphConditionalHandle hL, IterLaunches& L) {
+  const Dev& d = ctx->dev;
+  cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
+  const unsigned lsmax = (unsigned)ctx->prm.ls_max + 1u;
+  const long long m = ctx->launches;
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, c0); }, c0);
+  if (assemble_system(ctx, c0) != IPC_OK) return cudaErrorUnknown;
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, c0); }, c0);
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, c0, hP, 1); }, c0);
+  long long mn = ctx->launches;
+  cudaError_t e = cond_body(c0, c1, hP, cudaGraphCondTypeWhile, [&] {
+    L.pcg_iter = pcg_iteration(ctx, c1, hP, 1);
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  mn = ctx->launches - mn;
+  newton_decide(ctx, c0);
+  KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_LS, 3, -1, -1, 1, 0, hA, 1); }, c0);
+  long long ml = ctx->launches;
+  e = cond_body(c0, c1, hA, cudaGraphCondTypeIf, [&] {
+    long long mp = ctx->launches;
+    line_search_prep(ctx, c1);
+    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c1, I_LS, 3, 6, -1, -1, 0xffffffffu, hL, 1); }, c1);
+    L.ls_prep = ctx->launches - mp;
+    long long mt = ctx->launches;
+    cudaError_t e3 = cond_body(c1, c2, hL, cudaGraphCondTypeWhile, [&] {
+      line_search_trial(ctx, c2);
+      KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c2, I_LS, 3, 1, 5, -1, lsmax, hL, 1); }, c2);
+      return cudaSuccess;
+    });
+    L.ls_trial = ctx->launches - mt;
+    return e3;
+  });
+  ml = ctx->launches - ml;
+  L.base = ctx->launches - m - mn - ml;
+  return e;
+}
+
+// ends a capture begun on ctx->stream and instantiates it into *exec
+ipc_status finish_capture(ipc_ctx* ctx, cudaError_t e, long long l0, cudaGraphExec_t* exec, const char* what) {
+  cudaGraph_t gg = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &gg);
+  if (e == cudaSuccess) e = e2;
+  ctx->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, gg, 0);
+  if (gg) cudaGraphDestroy(gg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *exec = nullptr;
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return IPC_ECUDA;
+  }
+  return IPC_OK;
+}
+
+cudaError_t begin_capture(ipc_ctx* ctx, const char* what) {
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = std::string(what) + ": " + cudaGetErrorString(e) +
+               " (the stream cannot be captured, e.g. the legacy default stream)";
+  }
+  return e;
+}
+
 ipc_status capture_step(ipc_ctx* ctx) {
   const Dev& d = ctx->dev;
   cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    ctx->err = std::string("step graph capture: ") + cudaGetErrorString(e) +
-               " (the stream cannot be captured, e.g. the legacy default stream)";
-    return IPC_ECUDA;
-  }
+  if (begin_capture(ctx, "step graph capture") != cudaSuccess) return IPC_ECUDA;
   const long long l0 = ctx->launches;
   ipc_ctx::StepLaunches& L = ctx->step_launches;
   L = ipc_ctx::StepLaunches{};
   cudaGraph_t root = nullptr;
   cudaGraphConditionalHandle hN = 0, hP = 0, hA = 0, hL = 0;
-  e = capturing_graph(s, &root);
+  cudaError_t e = capturing_graph(s, &root);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hN, root, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hP, root, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hA, root, 0, 0);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hL, root, 0, 0);
-  const unsigned nmax = (unsigned)ctx->prm.newton_max, lsmax = (unsigned)ctx->prm.ls_max + 1u;
-  cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
-  auto body = [&](cudaStream_t cs, cudaStream_t bs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType t,
-                  auto&& fill) {
-    if (e != cudaSuccess) return;
-    cudaGraph_t g = nullptr;
-    e = add_conditional(cs, h, t, &g);
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(bs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return;
-    fill();
-    cudaGraph_t g2 = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(bs, &g2);
-    if (e == cudaSuccess) e = e2;
-  };
+  const unsigned nmax = (unsigned)ctx->prm.newton_max;
+  cudaStream_t c0 = ctx->cap[0];
   if (e == cudaSuccess) {
     long long m = ctx->launches;
     KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); }, s);
-    KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); }, s);
+    KL(ctx, KC_PREDICT, [&] { return launch_predict(d, I_SEL, s); }, s);
     KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); }, s);
     KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, s, I_ACTIVE, 2, -1, -1, -1, 0, hN, 1); }, s);
     L.pre = ctx->launches - m;
   }
-  body(s, c0, hN, cudaGraphCondTypeWhile, [&] {
-    long long m = ctx->launches;
-    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, c0); }, c0);
-    if (assemble_system(ctx, c0) != IPC_OK) e = cudaErrorUnknown;
-    KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, c0); }, c0);
-    KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, c0, hP, 1); }, c0);
-    long long mn = ctx->launches;
-    body(c0, c1, hP, cudaGraphCondTypeWhile, [&] { L.pcg_iter = pcg_iteration(ctx, c1, hP, 1); });
-    mn = ctx->launches - mn;
-    newton_decide(ctx, c0);
-    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_LS, 3, -1, -1, 1, 0, hA, 1); }, c0);
-    long long ml = ctx->launches;
-    body(c0, c1, hA, cudaGraphCondTypeIf, [&] {
-      long long mp = ctx->launches;
-      line_search_prep(ctx, c1);
-      KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c1, I_LS, 3, 6, -1, -1, 0xffffffffu, hL, 1); }, c1);
-      L.ls_prep = ctx->launches - mp;
-      long long mt = ctx->launches;
-      body(c1, c2, hL, cudaGraphCondTypeWhile, [&] {
-        line_search_trial(ctx, c2);
-        KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c2, I_LS, 3, 1, 5, -1, lsmax, hL, 1); }, c2);
-      });
-      L.ls_trial = ctx->launches - mt;
+  if (e == cudaSuccess)
+    e = cond_body(s, c0, hN, cudaGraphCondTypeWhile, [&] {
+      IterLaunches it;
+      cudaError_t e1 = capture_newton_iteration(ctx, hP, hA, hL, it);
+      long long m = ctx->launches;
+      KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_ACTIVE, 2, 0, -1, -1, nmax, hN, 1); }, c0);
+      L.newton = it.base + (ctx->launches - m);
+      L.pcg_iter = it.pcg_iter;
+      L.ls_prep = it.ls_prep;
+      L.ls_trial = it.ls_trial;
+      return e1;
     });
-    ml = ctx->launches - ml;
-    KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, c0, I_ACTIVE, 2, 0, -1, -1, nmax, hN, 1); }, c0);
-    L.newton = ctx->launches - m - mn - ml;
-  });
   if (e == cudaSuccess) {
     long long m = ctx->launches;
     KL(ctx, KC_MISC, [&] { return launch_finalize(d, s); }, s);
     L.post = ctx->launches - m;
   }
-  cudaGraph_t gg = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(s, &gg);
-  if (e == cudaSuccess) e = e2;
-  ctx->launches = l0;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->step_exec, gg, 0);
-  if (gg) cudaGraphDestroy(gg);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    ctx->step_exec = nullptr;
-    ctx->err = std::string("step graph capture: ") + cudaGetErrorString(e);
-    return IPC_ECUDA;
+  return finish_capture(ctx, e, l0, &ctx->step_exec, "step graph capture");
+}
+
+// ---- a rollout as one CUDA graph (ipc_rollout)
+//
+//   every selected env begins step 0
+//   WHILE (an env runs or begins a step, below the loop cap)
+//     envs beginning a step: targets of their step, counters, predict
+//     one Newton iteration of the envs inside a step (as in the step graph)
+//     envs whose step ended: Newton cap, finalize, counters, next step
+//
+// The table address, the step count and the cap live in device memory
+// (k_roll_setup before each launch), so the graph is captured once.
+ipc_status capture_roll(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  if (begin_capture(ctx, "rollout graph capture") != cudaSuccess) return IPC_ECUDA;
+  const long long l0 = ctx->launches;
+  ipc_ctx::RollLaunches& L = ctx->roll_launches;
+  L = ipc_ctx::RollLaunches{};
+  cudaGraph_t root = nullptr;
+  cudaGraphConditionalHandle hR = 0, hP = 0, hA = 0, hL = 0;
+  cudaError_t e = capturing_graph(s, &root);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hR, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hP, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hA, root, 0, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hL, root, 0, 0);
+  cudaStream_t c0 = ctx->cap[0];
+  if (e == cudaSuccess) {
+    long long m = ctx->launches;
+    KL(ctx, KC_MISC, [&] { return launch_roll_init(d, s); }, s);
+    KL(ctx, KC_MISC, [&] { return launch_roll_cond(d, s, hR); }, s);
+    L.pre = ctx->launches - m;
+  }
+  if (e == cudaSuccess)
+    e = cond_body(s, c0, hR, cudaGraphCondTypeWhile, [&] {
+      long long m = ctx->launches;
+      KL(ctx, KC_PREDICT, [&] { return launch_roll_begin(d, c0); }, c0);
+      IterLaunches it;
+      cudaError_t e1 = capture_newton_iteration(ctx, hP, hA, hL, it);
+      KL(ctx, KC_MISC, [&] { return launch_roll_end(d, c0); }, c0);
+      KL(ctx, KC_MISC, [&] { return launch_roll_cond(d, c0, hR); }, c0);
+      L.iter = (ctx->launches - m) - it.pcg_iter - it.ls_prep - it.ls_trial;
+      L.pcg_iter = it.pcg_iter;
+      L.ls_prep = it.ls_prep;
+      L.ls_trial = it.ls_trial;
+      return e1;
+    });
+  return finish_capture(ctx, e, l0, &ctx->roll_exec, "rollout graph capture");
+}
+
+// One Newton iteration of the envs still iterating, driven from the host
+// (plain launches; the flags are read back after the decision and after
+// every line-search trial).
+ipc_status newton_iteration_host(ipc_ctx* ctx) {
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  ipc_status st;
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
+  if ((st = assemble_system(ctx, s)) != IPC_OK) return st;
+  if ((st = run_pcg(ctx)) != IPC_OK) return st;
+  newton_decide(ctx, s);
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  if (count_flag(ctx, I_LS) > 0) {
+    line_search_prep(ctx, s);
+    for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
+      line_search_trial(ctx, s);
+      if ((st = sync_flags(ctx)) != IPC_OK) return st;
+      if (count_flag(ctx, I_LS) == 0) break;
+    }
   }
   return IPC_OK;
 }
@@ -681,8 +793,10 @@ ipc_status capture_step(ipc_ctx* ctx) {
 void drop_graphs(ipc_ctx* ctx) {
   if (ctx->pcg_exec) cudaGraphExecDestroy(ctx->pcg_exec);
   if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->roll_exec) cudaGraphExecDestroy(ctx->roll_exec);
   ctx->pcg_exec = nullptr;
   ctx->step_exec = nullptr;
+  ctx->roll_exec = nullptr;
 }
 
 // user-order DoF vector <-> row space of one env
@@ -722,7 +836,7 @@ ipc_status begin_single(ipc_ctx* ctx, int env) {
   ipc_status st = select_envs(ctx, {env});
   if (st != IPC_OK) return st;
   KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 0, ctx->stream); });
-  KL(ctx, KC_PREDICT, [&] { return launch_predict(ctx->dev, ctx->stream); });
+  KL(ctx, KC_PREDICT, [&] { return launch_predict(ctx->dev, I_SEL, ctx->stream); });
   KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(ctx->dev, I_SEL, ctx->stream); });
   KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 1, ctx->stream); });
   return last_cuda(ctx);
@@ -1152,24 +1266,12 @@ ipc_status ipc_step(ipc_ctx* ctx, const int32_t* env_ids, int n, int32_t* per_en
     return ipc_step_results(ctx, per_env_status, stats);
   }
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 0, s); });
-  KL(ctx, KC_PREDICT, [&] { return launch_predict(d, s); });
+  KL(ctx, KC_PREDICT, [&] { return launch_predict(d, I_SEL, s); });
   KL(ctx, KC_PREDICT, [&] { return launch_attach_targets(d, I_SEL, s); });
   const unsigned nmax = (unsigned)ctx->prm.newton_max;
   for (int it = 0; it < ctx->prm.newton_max; ++it) {
-    KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 1, s); });
-    if ((st = assemble_system(ctx, s)) != IPC_OK) return st;
-    if ((st = run_pcg(ctx)) != IPC_OK) return st;
-    newton_decide(ctx, s);
-    if ((st = sync_flags(ctx)) != IPC_OK) return st;
-    if (count_flag(ctx, I_LS) > 0) {
-      line_search_prep(ctx, s);
-      for (int ls = 0; ls < ctx->prm.ls_max; ++ls) {
-        line_search_trial(ctx, s);
-        if ((st = sync_flags(ctx)) != IPC_OK) return st;
-        if (count_flag(ctx, I_LS) == 0) break;
-      }
-    }
-    // Newton iteration counter on the device (the friction lag reads it)
+    if ((st = newton_iteration_host(ctx)) != IPC_OK) return st;
+    // Newton iteration counter on the device
     KL(ctx, KC_MISC, [&] { return launch_flag_cond(d, s, I_ACTIVE, 2, 0, -1, -1, nmax, 0, 0); });
     if (count_flag(ctx, I_ACTIVE) == 0) break;
   }
@@ -1216,6 +1318,107 @@ ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stat
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
     S.pair_evals += ei[I_PAIRTOT];
     S.swept_pairs += ei[I_SWEPTTOT];
+  }
+  S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->step_t0).count();
+  if (stats) *stats = S;
+  return IPC_OK;
+}
+
+ipc_status ipc_rollout(ipc_ctx* ctx, const int32_t* env_ids, int n, int n_steps, const int32_t* steps_per_env,
+                       const double* dev_targets, int32_t* per_env_status, int32_t* per_env_steps,
+                       ipc_step_stats* stats) {
+  if (!ctx || n_steps < 0 || (n_steps > 0 && !dev_targets && ctx->max_bodies > 0)) return IPC_EINVAL;
+  ctx->step_t0 = std::chrono::steady_clock::now();
+  std::vector<int> sel;
+  if (!env_ids) {
+    for (int e = 0; e < ctx->pk.n_envs; ++e) sel.push_back(e);
+  } else {
+    for (int i = 0; i < n; ++i) {
+      if (check_env(ctx, env_ids[i]) != IPC_OK) return IPC_EINVAL;
+      sel.push_back(env_ids[i]);
+    }
+  }
+  ctx->last_sel = sel;
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  ipc_status st;
+  if (!env_ids) KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 4, s); });
+  else if ((st = select_envs(ctx, sel)) != IPC_OK) return st;
+  {
+    // per-env step limits (I_RLIMIT column): n_steps, or the caller's
+    std::vector<int> col(ctx->pk.n_envs, n_steps);
+    for (size_t i = 0; i < sel.size(); ++i)
+      if (steps_per_env) {
+        if (steps_per_env[i] < 0) return IPC_EINVAL;
+        col[sel[i]] = std::min(steps_per_env[i], n_steps);
+      }
+    CK(cudaMemcpy2DAsync(ctx->dev.env_i + I_RLIMIT, NUM_INTS * sizeof(int), col.data(), sizeof(int), sizeof(int),
+                         ctx->pk.n_envs, cudaMemcpyHostToDevice, s));  // pageable: staged before return
+  }
+  // every env's step ends within newton_max iterations: the cap only guards
+  const unsigned long long cap = (unsigned long long)n_steps * ((unsigned long long)ctx->prm.newton_max + 1) + 2;
+  KL(ctx, KC_MISC, [&] { return launch_roll_setup(d, dev_targets, n_steps, cap, s); });
+  if (!ctx->prof_on) {
+    if (!ctx->roll_exec && (st = capture_roll(ctx)) != IPC_OK) return st;
+    CK(cudaGraphLaunch(ctx->roll_exec, s));
+    CK(cudaMemcpyAsync(ctx->h_step_ctl, ctx->dev.step_ctl, 8 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    ctx->roll_pending = true;
+    if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  } else {
+    // the same loop driven from the host with plain launches (per-kernel
+    // timing needs them)
+    KL(ctx, KC_MISC, [&] { return launch_roll_init(d, s); });
+    if ((st = sync_flags(ctx)) != IPC_OK) return st;
+    for (unsigned long long it = 0; it < cap && count_flag(ctx, I_LIVE) > 0; ++it) {
+      KL(ctx, KC_PREDICT, [&] { return launch_roll_begin(d, s); });
+      if ((st = newton_iteration_host(ctx)) != IPC_OK) return st;
+      KL(ctx, KC_MISC, [&] { return launch_roll_end(d, s); });
+      if ((st = sync_flags(ctx)) != IPC_OK) return st;
+    }
+    ctx->roll_pending = true;
+  }
+  ctx->step_pending = false;
+  if (!per_env_status && !per_env_steps && !stats) return IPC_OK;
+  return ipc_rollout_results(ctx, per_env_status, per_env_steps, stats);
+}
+
+ipc_status ipc_rollout_results(ipc_ctx* ctx, int32_t* per_env_status, int32_t* per_env_steps,
+                               ipc_step_stats* stats) {
+  if (!ctx) return IPC_EINVAL;
+  if (!ctx->roll_pending) {
+    if (stats) *stats = ipc_step_stats{};
+    return IPC_OK;
+  }
+  ipc_status st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  if (!ctx->prof_on) {
+    const ipc_ctx::RollLaunches& L = ctx->roll_launches;
+    const unsigned* c = ctx->h_step_ctl;
+    // c[0] counts the loop's condition evaluations (one before the loop)
+    const long long iters = c[0] > 0 ? (long long)c[0] - 1 : 0;
+    ctx->launches += L.pre + iters * L.iter + (long long)c[4] * L.pcg_iter + (long long)c[6] * L.ls_prep +
+                     (long long)c[5] * L.ls_trial;
+  }
+  ctx->roll_pending = false;
+  const std::vector<int>& sel = ctx->last_sel;
+  ipc_step_stats S{};
+  for (size_t i = 0; i < sel.size(); ++i) {
+    const int* ei = ctx->h_int + sel[i] * NUM_INTS;
+    if (per_env_status) per_env_status[i] = ei[I_STATUS];
+    if (per_env_steps) per_env_steps[i] = ei[I_RSTEP];
+    S.newton_iters = std::max(S.newton_iters, ei[I_RNEWTONMAX]);
+    S.al_updates = std::max(S.al_updates, ei[I_RAL]);
+    S.pcg_iters += ei[I_RPCG];
+    S.ls_trials += ei[I_RLS];
+    S.max_pairs = std::max(S.max_pairs, ei[I_RPAIRSMAX]);
+    S.newton_env_iters += ei[I_RNEWTON];
+    S.al_env_updates += ei[I_RAL];
+    S.ccd_limited += ei[I_RCCDCUT];
+    S.accd_iters += ei[I_RACCDIT];
+    S.accd_iters_max = std::max(S.accd_iters_max, ei[I_RACCDMAX]);
+    S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_RASUM];
+    S.pair_evals += ei[I_RPAIR];
+    S.swept_pairs += ei[I_RSWEPT];
   }
   S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->step_t0).count();
   if (stats) *stats = S;

@@ -30,6 +30,7 @@ enum EnvScalar {
   S_MIND,       // min pair distance (diagnostics)
   S_ASUM,       // accepted line-search steps this step, summed
   S_DQC,        // PCG d.q, contact part (pair and friction terms, summed by atomics)
+  S_RASUM,      // rollout: S_ASUM summed over the env's steps
   NUM_SCALARS
 };
 
@@ -59,6 +60,24 @@ enum EnvInt {
   I_GEN,          // Newton iterations ever run (tags the rows contact terms touch)
   I_PAIRTOT,      // static candidate pairs evaluated this step (all Newton iterations)
   I_SWEPTTOT,     // swept candidate pairs of this step's line searches
+  // rollout (ipc_rollout: each env runs its own sequence of steps)
+  I_RSTEP,        // steps completed in this rollout
+  I_BEGIN,        // begins its next step at the top of the next loop iteration
+  I_RUN,          // inside a step
+  I_ENDNOW,       // its step ended in this loop iteration
+  I_LIVE,         // running a step or about to begin one
+  I_RLIMIT,       // steps this env runs in the rollout (at most the call's n_steps)
+  I_RNEWTON,      // the per-step counters above, summed (max for *MAX) over the rollout
+  I_RNEWTONMAX,
+  I_RAL,
+  I_RPCG,
+  I_RLS,
+  I_RCCDCUT,
+  I_RACCDIT,
+  I_RACCDMAX,
+  I_RPAIR,
+  I_RSWEPT,
+  I_RPAIRSMAX,
   NUM_INTS
 };
 
@@ -128,6 +147,7 @@ struct Dev {
                                 // [2] envs in the list, [3] the list is stale
   int pcg_grid;                 // CTAs of the persistent PCG row kernels
   int pcg_grid_pairs;           // CTAs of the persistent contact mat-vec
+  unsigned long long* roll_ctl; // rollout: [0] address of the target table, [1] steps, [2] loop cap
   unsigned int* step_ctl;       // per step (device-side loops): [0] Newton iterations done,
                                 // [1] trials of the current line search, [2] envs still in
                                 // Newton, [3] envs in a line search, [4] PCG iterations,
@@ -160,7 +180,8 @@ struct Dev {
   int4* fr_v;                    // contact points of the pair
   double *fr_w, *fr_T, *fr_rn;   // closest-point weights (4), tangent basis (6), r at x^n (3)
   double *fr_ml, *fr_S, *fr_E;   // mu lambda; h^2 T M T^T (6, symmetric); energy
-  int *fr_list, *fr_list_env, *fr_count;  // compact list of this step's records
+  int* fr_scan;                  // n_envs + 1: exclusive scan of the active envs' record counts
+                                 // (rebuilt every Newton iteration)
   int4* accd_tail;               // ACCD pairs left for the warp-parallel phase: (slot, env, iterations, -)
   double* accd_tail_t;           // their certified time so far
   unsigned int* accd_tail_ctl;   // [entries, finished CTAs]; zero between launches
@@ -210,11 +231,16 @@ struct ipc_ctx {
   int graph_mode = 0;
   cudaGraphExec_t pcg_exec = nullptr;
   cudaGraphExec_t step_exec = nullptr;
+  cudaGraphExec_t roll_exec = nullptr;  // ipc_rollout's graph
   int pcg_iter_launches = 0;      // kernel launches per PCG iteration
   bool pcg_graph_pending = false; // a graph solve ran; its iteration count is not yet read
   struct StepLaunches {           // launches per section of the step graph, counted at capture
     long long pre = 0, newton = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0, post = 0;
   } step_launches;
+  struct RollLaunches {           // the same for the rollout graph
+    long long pre = 0, iter = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0;
+  } roll_launches;
+  bool roll_pending = false;      // a rollout ran; its results are not yet read
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams of conditional bodies
   unsigned int* h_step_ctl = nullptr;  // pinned read-back of Dev::step_ctl (8)
   // the last ipc_step: its envs, start time, and whether its results (and,

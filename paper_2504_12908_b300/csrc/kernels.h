@@ -26,7 +26,7 @@ int launch_cross_check(const Dev& d, int flag, cudaStream_t s);
 int launch_pnorm_body(const Dev& d, cudaStream_t s);
 
 // ---- solver (kernels_solver.cu)
-int launch_predict(const Dev& d, cudaStream_t s);
+int launch_predict(const Dev& d, int flag, cudaStream_t s);
 int launch_attach_targets(const Dev& d, int flag, cudaStream_t s);
 int launch_tet(const Dev& d, cudaStream_t s);
 int launch_body(const Dev& d, cudaStream_t s);
@@ -56,6 +56,12 @@ int launch_energy(const Dev& d, int use_alpha, int which /*0: E0, 1: E1*/, cudaS
 int launch_ls_decide(const Dev& d, cudaStream_t s);
 int launch_ls_apply(const Dev& d, cudaStream_t s);
 int launch_finalize(const Dev& d, cudaStream_t s);
+// rollout (each env runs its own sequence of steps inside one device loop)
+int launch_roll_setup(const Dev& d, const double* table, int n_steps, unsigned long long cap, cudaStream_t s);
+int launch_roll_init(const Dev& d, cudaStream_t s);
+int launch_roll_begin(const Dev& d, cudaStream_t s);
+int launch_roll_end(const Dev& d, cudaStream_t s);
+int launch_roll_cond(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h);
 int launch_env_reset(const Dev& d, int what, cudaStream_t s);
 int launch_check_overflow(const Dev& d, cudaStream_t s);
 // loop control of the device-side step (k_flag_cond in kernels_solver.cu)

@@ -311,17 +311,24 @@ __global__ void k_bp_check(Dev d, int flag) {
   if (e < d.n_envs && *d.bp_overflow && ENVI(d, e, flag)) ENVI(d, e, I_OVERFLOW) = 1;
 }
 
-// Exclusive scan of the per-env pair counts (one CTA): pair kernels then
-// walk a flat index space of real pairs only.
-__global__ void k_pair_scan(Dev d) {
+// Exclusive scan of a per-env count over the envs (one CTA): the pair and
+// friction kernels then walk a flat index space of real items only.
+//   which 0: candidate pairs, min(I_NPAIRS, capacity), into pair_scan;
+//   which 1: friction records of the envs still iterating, into fr_scan.
+__global__ void k_env_scan(Dev d, int which) {
   __shared__ int warp_tot[32];
   __shared__ int carry;
+  int* out = which == 0 ? d.pair_scan : d.fr_scan;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int base = 0; base < d.n_envs; base += blockDim.x) {
     int e = base + threadIdx.x;
-    int c = (e < d.n_envs) ? min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]) : 0;
+    int c = 0;
+    if (e < d.n_envs) {
+      if (which == 0) c = min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);
+      else c = ENVI(d, e, I_ACTIVE) ? min(ENVI(d, e, I_NFRIC), d.env_pair_cap[e]) : 0;
+    }
     int incl = c;
     for (int o = 1; o < 32; o <<= 1) {
       int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -340,12 +347,12 @@ __global__ void k_pair_scan(Dev d) {
     }
     __syncthreads();
     int excl = carry + warp_tot[wid] + incl - c;
-    if (e < d.n_envs) d.pair_scan[e] = excl;
+    if (e < d.n_envs) out[e] = excl;
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1) carry = excl + c;
     __syncthreads();
   }
-  if (threadIdx.x == 0) d.pair_scan[d.n_envs] = carry;
+  if (threadIdx.x == 0) out[d.n_envs] = carry;
 }
 
 // flat index f over real pairs -> (env, slot k in capacity space)
@@ -660,18 +667,14 @@ __device__ __forceinline__ void fr_u(const Dev& d, int j, const D3* X, double& u
   u1 = dot(t2, s);
 }
 
-// records are taken at x^n: only in the first Newton iteration of a step
-__global__ void k_fric_reset(Dev d) {
-  if (d.step_ctl[0] == 0u) *d.fr_count = 0;
-}
-
-// Newton iteration 0 (x = x^n): one record per static pair within dhat.
+// The first Newton iteration of an env's step (x = x^n): one record per
+// static pair within dhat, in the env's segment (I_NFRIC was zeroed when
+// the step began).  Envs may be at different iterations of their steps.
 __global__ void k_fric_setup(Dev d) {
-  if (d.step_ctl[0] != 0u) return;
   FOR_PAIRS(d, f) {
   int e;
   int k = pair_at(d, f, e);
-  if (!ENVI(d, e, I_ACTIVE)) continue;
+  if (!ENVI(d, e, I_ACTIVE) || ENVI(d, e, I_NEWTON) != 1) continue;
   int4 v = d.pair_v[k];
   D3 X[4];
   fr_points(d, v, 0.0, X);
@@ -703,21 +706,25 @@ __global__ void k_fric_setup(Dev d) {
   T[0] = t1.x; T[1] = t1.y; T[2] = t1.z; T[3] = t2.x; T[4] = t2.y; T[5] = t2.z;
   st3(d.fr_rn, j, cl.r);
   d.fr_ml[j] = d.fr_mu * lam;
-  int li = atomicAdd(d.fr_count, 1);
-  d.fr_list[li] = j;
-  d.fr_list_env[li] = e;
   }
 }
 
-#define FOR_FRIC(d, li) for (int li = blockIdx.x * blockDim.x + threadIdx.x, _nf = *(d).fr_count; li < _nf; \
+// flat index li over the records of the envs still iterating (fr_scan) ->
+// (env e, record j)
+#define FOR_FRIC(d, li) for (int li = blockIdx.x * blockDim.x + threadIdx.x, _nf = (d).fr_scan[(d).n_envs]; li < _nf; \
                              li += gridDim.x * blockDim.x)
+__device__ __forceinline__ int fric_at(const Dev& d, int li, int& e) {
+  e = find_env(d.fr_scan, d.n_envs, li);
+  return d.env_pair_off[e] + (li - d.fr_scan[e]);
+}
 
 // Each Newton iteration: gradient (into the contact accumulator qc, like the
 // barrier), the 3x3 matrix S = h^2 mu lambda T M T^T of the record, and the
 // preconditioner blocks w_i w_j S.
 __global__ void k_fric_assemble(Dev d) {
   FOR_FRIC(d, li) {
-  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  int e;
+  const int j = fric_at(d, li, e);
   if (!ENVI(d, e, I_ACTIVE)) continue;
   const int4 v = d.fr_v[j];
   const int cvs[4] = {v.x, v.y, v.z, v.w};
@@ -787,7 +794,8 @@ __global__ void k_fric_assemble(Dev d) {
 __global__ void k_fric_spmv(Dev d) {
   const int nb = pcg_new_buf(d);
   FOR_FRIC(d, li) {
-  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  int e;
+  const int j = fric_at(d, li, e);
   if (!ENVI(d, e, I_PCG)) continue;
   const int4 v = d.fr_v[j];
   const int cvs[4] = {v.x, v.y, v.z, v.w};
@@ -811,7 +819,8 @@ __global__ void k_fric_spmv(Dev d) {
 // line-search energy of each record: h^2 mu lambda f0(|u|) at x + alpha p
 __global__ void k_fric_energy(Dev d, int use_alpha) {
   FOR_FRIC(d, li) {
-  const int j = d.fr_list[li], e = d.fr_list_env[li];
+  int e;
+  const int j = fric_at(d, li, e);
   if (!ENVI(d, e, I_LS)) continue;
   const double a = use_alpha ? ENVS(d, e, S_ALPHA) : 0.0;
   D3 X[4];
@@ -948,7 +957,7 @@ int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s) {
   }
   k_pairs<<<148 * 8, 128, 0, s>>>(d);
   k_bp_check<<<nblk(d.n_envs, 128), 128, 0, s>>>(d, flag);
-  k_pair_scan<<<1, 1024, 0, s>>>(d);
+  k_env_scan<<<1, 1024, 0, s>>>(d, 0);
   return n + 3;
 }
 // pair kernels grid-stride over the real pairs (count on the device)
@@ -961,8 +970,8 @@ int launch_barrier(const Dev& d, int flag, cudaStream_t s) {
 }
 int launch_fric_setup(const Dev& d, cudaStream_t s) {
   if (!(d.fr_mu > 0.0) || !d.n_pairs_cap) return 0;
-  k_fric_reset<<<1, 1, 0, s>>>(d);
   k_fric_setup<<<PAIR_GRID>>>(d);
+  k_env_scan<<<1, 1024, 0, s>>>(d, 1);
   return 2;
 }
 int launch_fric_assemble(const Dev& d, cudaStream_t s) {

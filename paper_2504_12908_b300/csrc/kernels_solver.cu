@@ -25,10 +25,10 @@ __device__ __forceinline__ bool is_driven(uint8_t k) { return k == ROW_ATTACHED 
 // ---------------------------------------------------------------------------
 // prediction: xn = x, xt = x + h v (body rows: y, ydot), multipliers zero
 // ---------------------------------------------------------------------------
-__global__ void k_predict(Dev d) {
+__global__ void k_predict(Dev d, int flag) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_SEL)) return;
+  if (!ENVI(d, e, flag)) return;
   D3 x = ld3(d.x, r), v = ld3(d.v, r);
   st3(d.xn, r, x);
   st3(d.xt, r, x + d.h * v);
@@ -570,10 +570,10 @@ __global__ void k_clear_accept(Dev d) {
 }
 
 // velocities (App. A.2, backward Euler): v = (x - x^n) / h; overflowed envs restored
-__global__ void k_finalize_rows(Dev d) {
+__global__ void k_finalize_rows(Dev d, int flag) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_SEL)) return;
+  if (!ENVI(d, e, flag)) return;
   uint8_t kr = d.row_kind[r];
   if (kr == ROW_PAD) return;
   if (ENVI(d, e, I_STATUS) == IPC_EOVERFLOW) {
@@ -631,6 +631,130 @@ __global__ void k_env_reset(Dev d, int what) {
   } else if (what == 4) {
     ENVI(d, e, I_SEL) = 1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Rollout: every selected env runs roll_ctl[1] steps inside one device loop,
+// each on its own schedule.  One loop iteration is one Newton iteration of
+// the envs inside a step; an env whose step ends (converged, failed or at
+// the Newton cap) is finalised in that iteration and begins its next step
+// in the next one, while the others keep iterating.  Per env the sequence
+// of operations is the same as that of ipc_step called once per step.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void begin_step_counters(const Dev& d, int e) {
+  ENVI(d, e, I_ACTIVE) = 1;
+  ENVI(d, e, I_STATUS) = IPC_OK;
+  ENVI(d, e, I_NEWTON) = 0;
+  ENVI(d, e, I_AL) = 0;
+  ENVI(d, e, I_PCGTOT) = 0;
+  ENVI(d, e, I_LSTOT) = 0;
+  ENVI(d, e, I_ACCEPT) = 0;
+  ENVI(d, e, I_OVERFLOW) = 0;
+  ENVI(d, e, I_CCDCUT) = 0;
+  ENVI(d, e, I_ACCDIT) = 0;
+  ENVI(d, e, I_ACCDMAX) = 0;
+  ENVI(d, e, I_NFRIC) = 0;
+  ENVI(d, e, I_PAIRTOT) = 0;
+  ENVI(d, e, I_SWEPTTOT) = 0;
+  ENVS(d, e, S_ASUM) = 0.0;
+}
+
+// the table address, steps and loop cap of the next rollout (1 thread)
+__global__ void k_roll_setup(Dev d, const double* table, int n_steps, unsigned long long cap) {
+  d.roll_ctl[0] = (unsigned long long)(uintptr_t)table;
+  d.roll_ctl[1] = (unsigned long long)n_steps;
+  d.roll_ctl[2] = cap;
+}
+
+// before the loop: selected envs begin step 0; loop counters zeroed
+__global__ void k_roll_init(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 8) d.step_ctl[e] = 0u;
+  if (e >= d.n_envs) return;
+  const int sel = ENVI(d, e, I_SEL) != 0 && d.roll_ctl[1] > 0 && ENVI(d, e, I_RLIMIT) > 0;
+  ENVI(d, e, I_RSTEP) = 0;
+  ENVI(d, e, I_BEGIN) = sel;
+  ENVI(d, e, I_LIVE) = sel;
+  ENVI(d, e, I_RUN) = 0;
+  ENVI(d, e, I_ENDNOW) = 0;
+  ENVI(d, e, I_ACTIVE) = 0;
+  if (sel) ENVI(d, e, I_STATUS) = IPC_OK;
+  for (int k = I_RNEWTON; k <= I_RPAIRSMAX; ++k) ENVI(d, e, k) = 0;
+  ENVS(d, e, S_RASUM) = 0.0;
+}
+
+// envs that begin a step: their targets for step I_RSTEP from the table
+// [steps][n_envs][max_bodies][12], the per-step counters reset (one warp per
+// env; lane j copies target entries j, j + 32, ...)
+__global__ void k_roll_begin(Dev d) {
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (e >= d.n_envs || !ENVI(d, e, I_BEGIN)) return;
+  const double* table = reinterpret_cast<const double*>((uintptr_t)d.roll_ctl[0]);
+  const long long k = ENVI(d, e, I_RSTEP);
+  const int b0 = d.env_body_off[e], nb = d.env_body_off[e + 1] - b0;
+  const double* src = table + (k * d.n_envs + e) * (long long)d.max_bodies * 12;
+  for (int j = lane; j < 12 * nb; j += 32) d.s_tgt[3 * d.body_row[b0 + j / 12] + j % 12] = src[j];
+  if (lane == 0) {
+    begin_step_counters(d, e);
+    ENVI(d, e, I_RUN) = 1;
+  }
+}
+
+// after the Newton iteration: the Newton cap ends a step as not converged;
+// ENDNOW marks the envs whose step ended in this iteration
+__global__ void k_roll_end(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  ENVI(d, e, I_BEGIN) = 0;
+  int end = 0;
+  if (ENVI(d, e, I_RUN)) {
+    if (ENVI(d, e, I_ACTIVE) && ENVI(d, e, I_NEWTON) >= d.newton_max) {
+      ENVI(d, e, I_ACTIVE) = 0;
+      if (ENVI(d, e, I_STATUS) == IPC_OK) ENVI(d, e, I_STATUS) = IPC_ENOTCONV;
+    }
+    end = !ENVI(d, e, I_ACTIVE);
+  }
+  ENVI(d, e, I_ENDNOW) = end;
+}
+
+// envs whose step ended: counters into the rollout sums, next step (unless
+// it failed or was the last); LIVE = running or beginning
+__global__ void k_roll_advance(Dev d) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.n_envs) return;
+  if (ENVI(d, e, I_ENDNOW)) {
+    ENVI(d, e, I_RNEWTON) += ENVI(d, e, I_NEWTON);
+    ENVI(d, e, I_RNEWTONMAX) = max(ENVI(d, e, I_RNEWTONMAX), ENVI(d, e, I_NEWTON));
+    ENVI(d, e, I_RAL) += ENVI(d, e, I_AL);
+    ENVI(d, e, I_RPCG) += ENVI(d, e, I_PCGTOT);
+    ENVI(d, e, I_RLS) += ENVI(d, e, I_LSTOT);
+    ENVI(d, e, I_RCCDCUT) += ENVI(d, e, I_CCDCUT);
+    ENVI(d, e, I_RACCDIT) += ENVI(d, e, I_ACCDIT);
+    ENVI(d, e, I_RACCDMAX) = max(ENVI(d, e, I_RACCDMAX), ENVI(d, e, I_ACCDMAX));
+    ENVI(d, e, I_RPAIR) += ENVI(d, e, I_PAIRTOT);
+    ENVI(d, e, I_RSWEPT) += ENVI(d, e, I_SWEPTTOT);
+    ENVI(d, e, I_RPAIRSMAX) = max(ENVI(d, e, I_RPAIRSMAX), ENVI(d, e, I_NPAIRS));
+    ENVS(d, e, S_RASUM) += ENVS(d, e, S_ASUM);
+    const int k = ++ENVI(d, e, I_RSTEP);
+    ENVI(d, e, I_RUN) = 0;
+    ENVI(d, e, I_ENDNOW) = 0;
+    ENVI(d, e, I_BEGIN) = ENVI(d, e, I_STATUS) == IPC_OK && (unsigned long long)k < d.roll_ctl[1] &&
+                          k < ENVI(d, e, I_RLIMIT);
+  }
+  ENVI(d, e, I_LIVE) = ENVI(d, e, I_RUN) || ENVI(d, e, I_BEGIN);
+}
+
+// the rollout loop's condition (one CTA): some env live and the loop below
+// its cap (roll_ctl[2]); counts the loop iterations in step_ctl[0]
+__global__ void k_roll_cond(Dev d, cudaGraphConditionalHandle h) {
+  __shared__ int sh[32];
+  int c = 0;
+  for (int e = threadIdx.x; e < d.n_envs; e += blockDim.x) c += ENVI(d, e, I_LIVE) != 0;
+  c = block_sum(c, sh);
+  if (threadIdx.x != 0) return;
+  d.step_ctl[2] = (unsigned)c;
+  const unsigned k = ++d.step_ctl[0];
+  cudaGraphSetConditional(h, (c > 0 && (unsigned long long)k < d.roll_ctl[2]) ? 1u : 0u);
 }
 
 // Loop control of the device-side step (one CTA): counts the envs whose
@@ -706,7 +830,7 @@ __global__ void k_gather_coated(Dev d) {
 // ---------------------------------------------------------------------------
 #define ROWGRID (d.n_rows / 128), 128, 0, s
 #define ENVGRID nblk(d.n_envs, 128), 128, 0, s
-int launch_predict(const Dev& d, cudaStream_t s) { k_predict<<<ROWGRID>>>(d); return 1; }
+int launch_predict(const Dev& d, int flag, cudaStream_t s) { k_predict<<<ROWGRID>>>(d, flag); return 1; }
 int launch_attach_targets(const Dev& d, int flag, cudaStream_t s) { k_attach_targets<<<ROWGRID>>>(d, flag); return 1; }
 int launch_tet(const Dev& d, cudaStream_t s) {
   if (d.prec) k_tet<float><<<nblk(d.n_tets, 64), 64, 0, s>>>(d);
@@ -756,8 +880,29 @@ int launch_ls_apply(const Dev& d, cudaStream_t s) {
 }
 int launch_finalize(const Dev& d, cudaStream_t s) {
   k_finalize_envs<<<ENVGRID>>>(d);
-  k_finalize_rows<<<ROWGRID>>>(d);
+  k_finalize_rows<<<ROWGRID>>>(d, I_SEL);
   return 2;
+}
+int launch_roll_setup(const Dev& d, const double* table, int n_steps, unsigned long long cap, cudaStream_t s) {
+  k_roll_setup<<<1, 1, 0, s>>>(d, table, n_steps, cap);
+  return 1;
+}
+int launch_roll_init(const Dev& d, cudaStream_t s) { k_roll_init<<<ENVGRID>>>(d); return 1; }
+int launch_roll_begin(const Dev& d, cudaStream_t s) {
+  k_roll_begin<<<nblk(32LL * d.n_envs, 128), 128, 0, s>>>(d);
+  k_predict<<<ROWGRID>>>(d, I_BEGIN);
+  k_attach_targets<<<ROWGRID>>>(d, I_BEGIN);
+  return 3;
+}
+int launch_roll_end(const Dev& d, cudaStream_t s) {
+  k_roll_end<<<ENVGRID>>>(d);
+  k_finalize_rows<<<ROWGRID>>>(d, I_ENDNOW);
+  k_roll_advance<<<ENVGRID>>>(d);
+  return 3;
+}
+int launch_roll_cond(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h) {
+  k_roll_cond<<<1, 1024, 0, s>>>(d, h);
+  return 1;
 }
 int launch_env_reset(const Dev& d, int what, cudaStream_t s) { k_env_reset<<<ENVGRID>>>(d, what); return 1; }
 int launch_check_overflow(const Dev& d, cudaStream_t s) { k_check_overflow<<<ENVGRID>>>(d); return 1; }

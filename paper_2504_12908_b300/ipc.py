@@ -88,6 +88,8 @@ def lib():
             "ipc_set_targets_all_device": (i32, [vp, vp]),
             "ipc_step": (i32, [vp, _ip, i32, _ip, C.POINTER(ipc_step_stats)]),
             "ipc_step_results": (i32, [vp, _ip, C.POINTER(ipc_step_stats)]),
+            "ipc_rollout": (i32, [vp, _ip, i32, i32, _ip, vp, _ip, _ip, C.POINTER(ipc_step_stats)]),
+            "ipc_rollout_results": (i32, [vp, _ip, _ip, C.POINTER(ipc_step_stats)]),
             "ipc_read_gel_surface": (i32, [vp, i32, _dp, i32, C.POINTER(i32)]),
             "ipc_read_gel_surface_all": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
             "ipc_read_gel_surface_all_noalloc": (i32, [vp, _dp, C.c_size_t, C.POINTER(C.c_size_t)]),
@@ -125,7 +127,7 @@ def lib():
 
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
             "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets", "ipc_reset_env",
-            "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_step_results", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
+            "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_step_results", "ipc_rollout", "ipc_rollout_results", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
             "ipc_read_gel_surface_all_noalloc", "ipc_env_stats", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
             "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
@@ -349,6 +351,57 @@ class Envs:
         stats = ipc_step_stats()
         self._check(lib().ipc_step_results(self._ctx, _ptr(status, _ip), C.byref(stats)), "ipc_step_results")
         return status, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
+
+    def rollout(self, n_steps: int, dev_targets, env_ids: Optional[Sequence[int]] = None, wait: bool = True,
+                steps_per_env: Optional[Sequence[int]] = None):
+        """n_steps steps of each env, every env on its own schedule
+        (ipc_rollout).  dev_targets: CUDA float64 tensor
+        [n_steps][n_envs][max_bodies][12] (kept alive by this object until
+        the results are read), or None without bodies.  steps_per_env
+        (aligned with env_ids) caps each env's steps.  Returns (status,
+        steps taken, stats dict), or None with wait=False (rollout_results()
+        reads them)."""
+        ids = None if env_ids is None else np.ascontiguousarray(env_ids, dtype=np.int32)
+        n = self.n_envs if ids is None else len(ids)
+        lim = None if steps_per_env is None else np.ascontiguousarray(steps_per_env, dtype=np.int32)
+        if lim is not None and len(lim) != n:
+            raise ValueError("steps_per_env must have one entry per listed env")
+        if dev_targets is not None:
+            mb = max(self.max_bodies, 1)
+            if (not dev_targets.is_cuda or dev_targets.dtype != self._torch_float64()
+                    or tuple(dev_targets.shape) != (n_steps, self.n_envs, mb, 12) or not dev_targets.is_contiguous()):
+                raise ValueError(f"dev_targets must be a contiguous CUDA float64 tensor of shape "
+                                 f"{(n_steps, self.n_envs, mb, 12)}")
+        self._roll_n = n
+        self._roll_targets = dev_targets
+        ptr = None if dev_targets is None else C.c_void_p(dev_targets.data_ptr())
+        if not wait:
+            self._check(lib().ipc_rollout(self._ctx, _ptr(ids, _ip), n, int(n_steps), _ptr(lim, _ip), ptr, None, None,
+                                          None), "ipc_rollout")
+            return None
+        status = np.zeros(n, dtype=np.int32)
+        steps = np.zeros(n, dtype=np.int32)
+        stats = ipc_step_stats()
+        self._check(lib().ipc_rollout(self._ctx, _ptr(ids, _ip), n, int(n_steps), _ptr(lim, _ip), ptr,
+                                      _ptr(status, _ip), _ptr(steps, _ip), C.byref(stats)), "ipc_rollout")
+        self._roll_targets = None
+        return status, steps, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
+
+    def rollout_results(self):
+        """(status, steps taken, stats dict) of the last rollout (synchronises)."""
+        n = getattr(self, "_roll_n", self.n_envs)
+        status = np.zeros(n, dtype=np.int32)
+        steps = np.zeros(n, dtype=np.int32)
+        stats = ipc_step_stats()
+        self._check(lib().ipc_rollout_results(self._ctx, _ptr(status, _ip), _ptr(steps, _ip), C.byref(stats)),
+                    "ipc_rollout_results")
+        self._roll_targets = None
+        return status, steps, {k: getattr(stats, k) for k, _ in ipc_step_stats._fields_}
+
+    @staticmethod
+    def _torch_float64():
+        import torch
+        return torch.float64
 
     ENV_STATS = ("status", "newton", "al", "pcg", "ls_trials", "ccd_limited", "accd_max", "pairs", "accd_iters",
                  "pair_evals", "swept_pairs")

@@ -119,6 +119,60 @@ def test_config1_bench_window_mixed():
     genv.close()
 
 
+def test_config1_rollout_window_mixed():
+    """The benchmark's rollout form (256 envs, mixed precision, every env on
+    its own schedule inside one graph): steps 0-4 as lock-step graphs, step 5
+    as a one-step rollout compared with the oracle on four envs (mixed bar),
+    then steps 6-24 as one rollout: every env converges at every step and
+    ends in a valid state."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    n = 256
+    scene, params, deltas = scenes.config1_batch(n)
+    prm = scenes.SolverParams(**params.__dict__)
+    prm.precision = 1
+    genv = ipc.Envs([scene] * n, prm, stream=torch.cuda.Stream())
+    genv.set_graph_mode(2)
+    com = genv.body_com(0, 0)
+
+    def targets(k):
+        t = np.zeros((n, 1, 12))
+        for e in range(n):
+            t[e, 0, :3] = com + deltas[e](k)[0]
+            t[e, 0, 3:] = np.eye(3).T.ravel()
+        return t
+    for k in range(5):
+        genv.set_targets_all(targets(k))
+        st, _ = genv.step()
+        assert np.all(st == 0), k
+    samples = [3, 77, 150, 222]
+    before = {e: genv.get_state(e) for e in samples}
+    st, steps, _ = genv.rollout(1, torch.as_tensor(targets(5)[None], device="cuda"))
+    assert np.all(st == 0) and np.all(steps == 1)
+    oenv = OracleEnv(scene, prm)
+    jobs = []
+    for e in samples:
+        x, v, yg, yd = before[e]
+        jobs.append((e, 5, (x, v, from_gpu_y(genv, e, oenv, yg), yd), prm))
+    with cf.ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(oracle_press_step, jobs))
+    for (e, _, (x, v, y, yd), _), r in zip(jobs, res):
+        assert r["status"] == 0
+        xg, _, ygn, _ = genv.get_state(e)
+        ygn = from_gpu_y(genv, e, oenv, ygn)
+        err = np.abs(all_points(oenv, xg, ygn) - all_points(oenv, r["x"], r["y"])).max() / bbox_diag(oenv, x, y)
+        assert err <= 1e-4, (e, err)
+    tab = torch.as_tensor(np.stack([targets(k) for k in range(6, 25)]), device="cuda")
+    st, steps, stats = genv.rollout(19, tab)
+    assert np.all(st == 0) and np.all(steps == 19), (np.nonzero(st)[0], st[st != 0])
+    assert stats["newton_iters"] < prm.newton_max
+    for e in range(n):
+        x, v, y, yd = genv.get_state(e)
+        assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+        assert np.abs(v).max() < 1.0
+    genv.close()
+
+
 def test_config2_full_uneven_batch_mixed():
     scs = [scenes.config2(e) for e in range(512)]
     prm = scenes.SolverParams()

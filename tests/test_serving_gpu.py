@@ -38,7 +38,9 @@ def _requests():
            scenes.small_contact_scene(body="sphere", level=1, depth=3e-4, n_steps=6),
            b,
            scenes.small_contact_scene(body="cube", depth=1e-4, n_steps=4)]
-    steps = [5, 6, 4, 5, 6, 4, 4]
+    # (request 4's sixth step ends IPC_ENOTCONV at the parity tolerances in
+    # the oracle too: its line search stalls at 57 Newton iterations)
+    steps = [5, 6, 4, 5, 5, 4, 4]
     arrival = [0.0, 0.0, 0.02, 0.04, 0.06, 0.08, 0.08]
     reqs = [Request(rid=i, scene=sc.scene, delta=sc.delta, n_steps=steps[i], arrival=arrival[i])
             for i, sc in enumerate(scs)]
