@@ -59,7 +59,12 @@ def parse():
     ap.add_argument("--slots-per-pool", type=int, default=256, help="serving: env slots per size-class pool")
     ap.add_argument("--max-pools", type=int, default=32)
     ap.add_argument("--no-graphs", action="store_true", help="serving: plain launches instead of PCG graphs")
+    ap.add_argument("--serve-chunk", type=int, default=8, help="serving: steps per pool call (rollout when > 1)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--pcg-window", type=int, default=None,
+                    help="rollout: PCG iterations per loop iteration (even; 0 = whole solves; default: the library's)")
+    ap.add_argument("--no-lockstep", action="store_true", help="skip the lock-step timing beside the rollout")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
     return ap.parse_args()
 
 
@@ -143,10 +148,12 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ workload
-def build_workload(n_envs, precision):
+def build_workload(n_envs, precision, pcg_window=None):
     import scenes
     scene, params, deltas = scenes.config1_batch(n_envs)
     params.precision = precision
+    if pcg_window is not None:
+        params.rollout_pcg_window = pcg_window
     return scene, params, deltas
 
 
@@ -304,7 +311,7 @@ def time_steps(genv, dev_tg, k0, steps, stream):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     tot = {"pcg_iters": 0, "newton_env_iters": 0, "ls_trials": 0, "newton_max": 0, "max_pairs": 0,
            "al_env_updates": 0, "ccd_limited": 0, "alpha_sum": 0.0, "accd_iters": 0, "accd_iters_max": 0,
-           "pair_evals": 0, "swept_pairs": 0, "env_steps": 0}
+           "pair_evals": 0, "swept_pairs": 0, "env_steps": 0, "graph_loop_iters": 0, "graph_pcg_launches": 0}
     statuses = []
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -322,6 +329,8 @@ def time_steps(genv, dev_tg, k0, steps, stream):
         tot["max_pairs"] = max(tot["max_pairs"], s["max_pairs"])
         tot["accd_iters_max"] = max(tot["accd_iters_max"], s["accd_iters_max"])
         tot["env_steps"] += len(st)
+        tot["graph_loop_iters"] += s["loop_iters"]
+        tot["graph_pcg_launches"] += s["pcg_launches"]
     t1.record(stream)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev], tot, statuses
@@ -343,7 +352,8 @@ def time_rollout(genv, dev_tg, k0, steps, stream):
     tot = {k: s[k] for k in ("pcg_iters", "newton_env_iters", "ls_trials", "al_env_updates", "ccd_limited",
                              "alpha_sum", "accd_iters", "pair_evals", "swept_pairs")}
     tot.update({"newton_max": s["newton_iters"], "max_pairs": s["max_pairs"], "accd_iters_max": s["accd_iters_max"],
-                "env_steps": int(np.sum(taken))})
+                "env_steps": int(np.sum(taken)), "graph_loop_iters": s["loop_iters"],
+                "graph_pcg_launches": s["pcg_launches"]})
     return t0.elapsed_time(t1), tot, st, taken
 
 
@@ -358,15 +368,16 @@ def restore(genv, snap):
             raise RuntimeError(f"set_state({e}) -> {r}")
 
 
-def per_step_error(g64, g32, tg, body_radius):
+def per_step_error(g64, g32, tg, body_radius, states=None):
     """Spec'd error of the mixed form: one step of both paths from the same
-    input state (the FP64 path's current state, every env), largest vertex
-    difference over all gel vertices and body vertices, relative to the
-    gel box diagonal.  Body vertices are bounded through the 12 DoF:
-    |dp| + R * sum_j |dA_ij| for points within radius R of the frame."""
+    input state (`states`, else the FP64 path's current state; every env),
+    largest vertex difference over all gel vertices and body vertices,
+    relative to the gel box diagonal.  Body vertices are bounded through the
+    12 DoF: |dp| + R * sum_j |dA_ij| for points within radius R of the
+    frame."""
     n = len(g64.sizes)
     for e in range(n):
-        st = g64.get_state(e)
+        st = g64.get_state(e) if states is None else states[e]
         for g in (g64, g32):
             assert g.set_state(e, *st) == 0
     for g in (g64, g32):
@@ -379,9 +390,13 @@ def per_step_error(g64, g32, tg, body_radius):
         x64, _, y64, _ = g64.get_state(e)
         x32, _, y32, _ = g32.get_state(e)
         errs[e] = state_diff(x64, y64, x32, y32, body_radius) / diag
-    dist = {"max": float(errs.max()), "p99": float(np.percentile(errs, 99)), "median": float(np.median(errs)),
-            "envs_above_1e-4": int(np.sum(errs > 1e-4)), "envs": n}
-    return float(errs.max()), dist, int(np.sum(s64 != 0) + np.sum(s32 != 0))
+    return errs, int(np.sum(s64 != 0) + np.sum(s32 != 0))
+
+
+def error_distribution(errs):
+    errs = np.concatenate(errs)
+    return {"max": float(errs.max()), "p99": float(np.percentile(errs, 99)), "median": float(np.median(errs)),
+            "env_steps_above_1e-4": int(np.sum(errs > 1e-4)), "env_steps": int(errs.size)}
 
 
 def state_diff(xa, ya, xb, yb, body_radius):
@@ -393,24 +408,88 @@ def state_diff(xa, ya, xb, yb, body_radius):
 
 
 # DRAM traffic of one mat-vec launch (dram__bytes_read.sum +
-# dram__bytes_write.sum under ncu) and the env-iterations that launch
-# processed; reported, scaled to the average launch, only while the kernel's
-# source is the one that was measured (hash of its text).
-MATVEC_TRAFFIC = {"env_iters": None, "bytes": None, "source_sha256": None}
+# dram__bytes_write.sum under ncu: the first launch of the 24-env case, every
+# env in its first PCG iteration, inputs larger than L2) and the
+# env-iterations that launch processed; reported, scaled to the average
+# launch by env-iterations, only while the kernel's source is the one that
+# was measured (hash of its text).
+MATVEC_TRAFFIC = {"env_iters": 24, "bytes": 116460288 + 3188480,
+                  "source_sha256": "5e01ef3a4c67618e6a4cab8330df02d105c54d2971104af4589f71b28c6db2f5"}
+
+
+def _function_text(src: str, signature: str) -> str:
+    """The text of the function whose definition starts at `signature` (up
+    to its closing brace at column 0)."""
+    i = src.index(signature)
+    j = src.index("\n}\n", i)
+    return src[i:j + 3]
+
+
+def _kernel_source_hash(parts) -> str:
+    """Hash of (file, signature or None for the whole file) source parts."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2504_12908_b300", "csrc")
+    h = hashlib.sha256()
+    for f, sig in parts:
+        src = open(os.path.join(csrc, f)).read()
+        h.update((src if sig is None else _function_text(src, sig)).encode())
+    return h.hexdigest()
+
+
+MATVEC_PARTS = [("pcgvec.cuh", None), ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_rows("),
+                ("kernels_pcg.cu", "__global__ void __launch_bounds__(128) k_pcg_matvec(")]
 
 
 def _matvec_source_hash() -> str:
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_2504_12908_b300", "csrc")
-    src = open(os.path.join(csrc, "kernels_pcg.cu")).read()
-    vec = open(os.path.join(csrc, "pcgvec.cuh")).read()
-    return hashlib.sha256((vec + src).encode()).hexdigest()
+    return _kernel_source_hash(MATVEC_PARTS)
 
 
 def matvec_traffic_per_launch(env_iters_per_launch):
     if MATVEC_TRAFFIC["bytes"] is None or _matvec_source_hash() != MATVEC_TRAFFIC["source_sha256"]:
         return None
     return MATVEC_TRAFFIC["bytes"] / MATVEC_TRAFFIC["env_iters"] * env_iters_per_launch
+
+
+# FP64 floating-point operations per unit of work of the FP64-heavy kernel
+# classes in the mixed mode (dadd + dmul + 2 dfma thread instructions of one
+# launch under ncu, divided by the units that launch processed: the first
+# launch of each kernel in a process, every env active).  Reported, as an
+# ALU roofline against the measured FP64 FMA rate, only while the kernel
+# sources are the ones that were measured (hash of their text).
+FP64_FLOPS_PER_UNIT = {
+    "tet_elastic": (242.0, "2d957c0cc0b5181766dbd7c0fb0220283973b08d54633a9557ca7706721013ee"),
+    "pcg_update": (None, None),
+    "body_abd": (4920.0, "f61821426e8eded7636bb680544a5069633eb989788f447c6a37cef599b9d0e9"),
+}
+ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "pcg_update": "row per PCG iteration",
+            "body_abd": "body per Newton iteration"}
+ALU_PARTS = {
+    "tet_elastic": [("physics.cuh", None), ("common.cuh", None),
+                    ("kernels_solver.cu", "__global__ void __launch_bounds__(64) k_tet(")],
+    "pcg_update": [("pcgvec.cuh", None), ("fpconv.cuh", None),
+                   ("kernels_pcg.cu", "__global__ void __launch_bounds__(128) k_pcg_update(")],
+    "body_abd": [("physics.cuh", None), ("common.cuh", None),
+                 ("kernels_solver.cu", "__global__ void __launch_bounds__(128) k_body(")],
+}
+
+
+def alu_rooflines(genv, prof, tot, fp64_tflops):
+    """FP64 GFLOP/s of the ALU-bound classes from their flop counts per unit
+    and their profiled time, against the measured FP64 FMA rate."""
+    if fp64_tflops is None:
+        return None
+    sz = genv.system_sizes(0)
+    nv, nb, _ = genv.sizes[0]
+    units = {"tet_elastic": tot["newton_env_iters"] * sz["tets"], "pcg_update": tot["pcg_iters"] * (nv + 4 * nb),
+             "body_abd": tot["newton_env_iters"] * nb}
+    out = {}
+    for k, (per, sha) in FP64_FLOPS_PER_UNIT.items():
+        if per is None or k not in prof or prof[k][1] <= 0 or sha != _kernel_source_hash(ALU_PARTS[k]):
+            continue
+        gf = per * units[k] / (prof[k][1] / 1e3) / 1e9
+        out[k] = {"bound": "alu", "achieved": round(gf, 1), "peak": round(1e3 * fp64_tflops, 1), "unit": "GFLOP/s (FP64)",
+                  "frac": round(gf / (1e3 * fp64_tflops), 4), "flops_per_unit": per, "unit_of_work": ALU_UNIT[k]}
+    return out
 
 
 def roofline_of(genv, prof, tot):
@@ -514,12 +593,13 @@ def run_precision(args, scene, params, deltas, precision, local, world, dev_tg, 
     l0 = genv.launch_count()
     ms, tot, st, taken = time_rollout(genv, dev_tg, args.warmup, args.steps, stream)
     clk = clocks.stop()
+    end = snapshot(genv) if precision == 0 else None
     launches = genv.launch_count() - l0
     ms = max_over_ranks(ms, world, f"cuda:{local}")
     n_bad = int(np.sum(st != 0)) + int(np.sum(taken != args.steps))
     return {"genv": genv, "stream": stream, "snap": snap, "value": whole_job_rate(args.envs, args.steps, world, ms),
             "ms_total": ms, "tot": tot, "clocks": clk, "launches": launches, "n_bad": n_bad,
-            "tuning": tuning, "lock": lock}
+            "tuning": tuning, "lock": lock, "end": end}
 
 
 def run_ours(args):
@@ -533,7 +613,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build()
-    scene, params, deltas = build_workload(args.envs, 0)
+    scene, params, deltas = build_workload(args.envs, 0, args.pcg_window)
     n_total = args.warmup + args.steps
     dev = f"cuda:{local}"
 
@@ -550,24 +630,31 @@ def run_ours(args):
         # batched FP64 is timed as a rollout only (its lock-step form is the
         # slower of the two)
         results[prec] = run_precision(args, scene, params, deltas, prec, local, world, dev_tg,
-                                      lockstep=(prec == precisions[-1]))
+                                      lockstep=(prec == precisions[-1] and not args.no_lockstep))
     hp = precisions[-1]
     head = results[hp]
     genv, stream = head["genv"], head["stream"]
 
-    # per-class shares: the same rollout again from the snapshot, with
-    # per-kernel CUDA events (the same loop as plain launches driven from the
-    # host); not part of the timed region
-    restore(genv, head["snap"])
-    genv.profile_enable(True)
-    genv.profile_reset()
-    _, taken_p, s_p = genv.rollout(args.steps, dev_tg[args.warmup:n_total])
-    prof = genv.profile()
-    genv.profile_enable(False)
-    tot_p = {"pcg_iters": s_p["pcg_iters"], "newton_env_iters": s_p["newton_env_iters"],
-             "ls_trials": s_p["ls_trials"], "pair_evals": s_p["pair_evals"], "swept_pairs": s_p["swept_pairs"],
-             "accd_iters": s_p["accd_iters"], "env_steps": int(np.sum(taken_p))}
-    roof, kernels = roofline_of(genv, prof, tot_p)
+    roof = kernels = alu = fma = None
+    if not args.no_profile:
+        # per-class shares: the same rollout again from the snapshot, with
+        # per-kernel CUDA events (the same loop as plain launches driven from the
+        # host); not part of the timed region
+        restore(genv, head["snap"])
+        genv.profile_enable(True)
+        genv.profile_reset()
+        _, taken_p, s_p = genv.rollout(args.steps, dev_tg[args.warmup:n_total])
+        prof = genv.profile()
+        genv.profile_enable(False)
+        tot_p = {"pcg_iters": s_p["pcg_iters"], "newton_env_iters": s_p["newton_env_iters"],
+                 "ls_trials": s_p["ls_trials"], "pair_evals": s_p["pair_evals"], "swept_pairs": s_p["swept_pairs"],
+                 "accd_iters": s_p["accd_iters"], "env_steps": int(np.sum(taken_p))}
+        roof, kernels = roofline_of(genv, prof, tot_p)
+        try:
+            fma = ipc.fma_peaks(dev)
+        except Exception:  # noqa: BLE001 - reported as unavailable
+            fma = None
+        alu = alu_rooflines(genv, prof, tot_p, fma["fp64_tflops"] if fma else None)
 
     # e2e through the public API on the same steps: every step's targets
     # copied in from pinned host memory, the rollout, and the per-env
@@ -621,8 +708,14 @@ def run_ours(args):
         g64 = results[0]["genv"]
         snap64 = results[0]["snap"]
         if len(precisions) == 2:
-            # one step of both paths from the same input state (after the timed steps)
-            rel_err, err_dist, _ = per_step_error(g64, genv, dev_tg[n_total], 4e-3)
+            # one step of both paths from the same input states: every env at
+            # the first timed step (the FP64 snapshot) and after the timed steps
+            e_first, _ = per_step_error(g64, genv, dev_tg[args.warmup], 4e-3, states=snap64)
+            for e in range(args.envs):   # the FP64 path's end of the timed region, as it was
+                assert g64.set_state(e, *results[0]["end"][e]) == 0
+            e_last, _ = per_step_error(g64, genv, dev_tg[n_total], 4e-3)
+            err_dist = error_distribution([e_first, e_last])
+            rel_err = err_dist["max"]
         # the benchmark spec's comparison: the plain per-environment FP64 GPU path
         if rank == 0 and not args.no_per_env:
             plain64 = per_env_fp64(scene, params, deltas, snap64, args.warmup, [0, 1], min(args.steps, 10), dev)
@@ -686,14 +779,15 @@ def run_ours(args):
                "per_env_fp64": plain64,
                "speedup_vs_per_env_fp64": head["value"] / plain64["value"] if plain64 else None,
                "rel_err_vs_fp64": rel_err,
-               "rel_err_def": "one step of both paths from the same input state (every env), max vertex "
-                              "difference / gel bbox diagonal",
+               "rel_err_def": "one step of both paths from the same input state, every env at the first timed "
+                              "step and after the timed steps, max vertex difference / gel bbox diagonal",
                "rel_err_per_env": err_dist,
                "rel_err_vs_oracle": oracle_cmp,
                "status_not_ok": head["n_bad"],
                "iterations": head["tot"],
                "launch_shapes": head["tuning"],
-               "roofline": roof, "kernels": kernels, "clocks": head["clocks"], "gpu_launches": int(head["launches"]),
+               "roofline": roof, "kernels": kernels, "alu_rooflines": alu, "fma_peaks_tflops": fma,
+               "clocks": head["clocks"], "gpu_launches": int(head["launches"]),
                "e2e": e2e, "e2e_lockstep": e2e_lock, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -728,7 +822,7 @@ def run_serving(args):
     prm.precision = 1
     eng = GpuEngine(prm, device=f"cuda:{local}", graphs=not args.no_graphs)
     srv = Server(eng, max_resident=args.max_resident, slots_per_pool=args.slots_per_pool,
-                 max_pools=args.max_pools, keep_state=False)
+                 max_pools=args.max_pools, keep_state=False, chunk=1 if args.no_graphs else args.serve_chunk)
     clocks = ClockSampler(local)
     clocks.start()
     rep = srv.run(reqs, time_limit=args.serve_seconds, hard_limit=args.serve_hard)
@@ -756,7 +850,8 @@ def run_serving(args):
            "config": {"workload": "serving: Poisson %.0f req/s of config-2-style envs x %d steps, window %.0f s"
                       % (args.rate, args.req_steps, args.serve_seconds),
                       "max_resident": args.max_resident, "slots_per_pool": args.slots_per_pool,
-                      "max_pools": args.max_pools, "graphs": not args.no_graphs},
+                      "max_pools": args.max_pools, "graphs": not args.no_graphs,
+                      "steps_per_call": 1 if args.no_graphs else args.serve_chunk},
            "latency_ms": {"p50": rep.step_ms_p50, "p99": rep.step_ms_p99},
            "serving": {k: v for k, v in summ.items()},
            "fp64_one_by_one": {"value": one, "unit": "env-steps/s", "step_ms_mean": float(np.mean(one_ms)),

@@ -103,6 +103,13 @@ typedef struct {
                              later ones replace them by their absolute
                              values (default 1000000: always zero; 0:
                              always absolute values)                        */
+  int rollout_pcg_window; /* ipc_rollout: PCG iterations per loop iteration
+                             (even, >= 2): an env whose solve is longer
+                             carries it over while the envs whose solves
+                             ended take their Newton steps; 0 (default) =
+                             every solve of a Newton iteration ends before
+                             the next Newton iteration (not in the paper: a
+                             scheduling property of this library)          */
 } ipc_params;
 
 /* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
@@ -152,6 +159,12 @@ typedef struct {
                                  summed over Newton iterations and envs      */
   long long swept_pairs;      /* swept candidate pairs of the line searches
                                  (ACCD and line-search energies), summed     */
+  long long loop_iters;       /* device loop iterations of the call's graph:
+                                 Newton loop (ipc_step) or rollout loop; 0
+                                 for host-driven calls                     */
+  long long pcg_launches;     /* PCG iterations the graph ran (each serves
+                                 every env in PCG at the time); 0 for
+                                 host-driven calls                         */
 } ipc_step_stats;
 
 void ipc_default_params(ipc_params* prm);

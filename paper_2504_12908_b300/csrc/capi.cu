@@ -258,6 +258,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_list = c.take<int>((size_t)pk.n_envs);
   d.pcg_pair_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
+  d.pcg_item = c.take<int2>((size_t)pk.n_rows / 128);
+  d.pcg_pitem = c.take<int2>((size_t)pk.n_pairs_cap / 8 + (size_t)pk.n_envs);
   d.pcg_ctl = c.take<unsigned int>(8);
   d.step_ctl = c.take<unsigned int>(8);
   d.roll_ctl = c.take<unsigned long long>(4);
@@ -380,10 +382,10 @@ ipc_status last_cuda(ipc_ctx* ctx) {
 // Newton iteration of a step (decided on the device).
 ipc_status assemble_system(ipc_ctx* ctx, cudaStream_t s) {
   const Dev& d = ctx->dev;
-  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_ACTIVE, false, s); }, s);
-  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_ACTIVE, false, s); }, s);
+  KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_NEWT, false, s); }, s);
+  KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_NEWT, false, s); }, s);
   KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); }, s);
-  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_ACTIVE, false, s); }, s);
+  KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_NEWT, false, s); }, s);
   KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); }, s);
   // barrier terms (side stream 0) and ABD terms (side stream 1) are few,
   // latency-bound threads; they are issued first, at high priority, and run
@@ -391,7 +393,7 @@ ipc_status assemble_system(ipc_ctx* ctx, cudaStream_t s) {
   fork_side(ctx, s);
   cudaStream_t s0 = side_of(ctx, s, 0), s1 = side_of(ctx, s, 1);
   KL(ctx, KC_BARRIER, [&] { return launch_fric_setup(d, s0); }, s0);
-  KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_ACTIVE, s0); }, s0);
+  KL(ctx, KC_BARRIER, [&] { return launch_barrier(d, I_NEWT, s0); }, s0);
   KL(ctx, KC_BARRIER, [&] { return launch_fric_assemble(d, s0); }, s0);
   KL(ctx, KC_BODY, [&] { return launch_body(d, s1); }, s1);
   KL(ctx, KC_TET, [&] { return launch_tet(d, s); }, s);
@@ -417,7 +419,7 @@ void line_search_prep(ipc_ctx* ctx, cudaStream_t s) {
   const Dev& d = ctx->dev;
   KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, s); }, s);
   KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, s); }, s);
-  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, s); }, s);
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 5, s); }, s);
   KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, s); }, s);
   KL(ctx, KC_MISC, [&] { return launch_check_overflow(d, s); }, s);
   fork_side(ctx, s, 1);
@@ -440,7 +442,8 @@ constexpr int kPcgPoll = 16;  // host-driven path: PCG iterations between reads 
 
 // one PCG iteration on stream s over the device-side work list; returns the
 // launches issued.  use_cond: the update kernel sets the graph condition h.
-int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0) {
+int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0, int use_cond = 0,
+                  unsigned window = 0xffffffffu) {
   const Dev& d = ctx->dev;
   long long l0 = ctx->launches;
   // contact terms (side stream) beside the SELL mat-vec: both only read
@@ -451,7 +454,7 @@ int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0
   KL(ctx, KC_SPMV, [&] { return launch_pcg_matvec(d, s); }, s);
   join_side(ctx, s, 1);
   KL(ctx, KC_FRICSPMV, [&] { return launch_fric_spmv(d, s); }, s);
-  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, h, use_cond); }, s);
+  KL(ctx, KC_PCGUPD, [&] { return launch_pcg_update(d, s, h, use_cond, window); }, s);
   return (int)(ctx->launches - l0);
 }
 
@@ -609,7 +612,8 @@ struct IterLaunches {
   long long base = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0;
 };
 cudaError_t capture_newton_iteration(ipc_ctx* ctx, cudaGraphConditionalHandle hP, cudaGraphConditionalHandle hA,
-                                     cudaGraphConditionalHandle hL, IterLaunches& L) {
+                                     cudaGraphConditionalHandle hL, IterLaunches& L,
+                                     unsigned window = 0xffffffffu) {
   const Dev& d = ctx->dev;
   cudaStream_t c0 = ctx->cap[0], c1 = ctx->cap[1], c2 = ctx->cap[2];
   const unsigned lsmax = (unsigned)ctx->prm.ls_max + 1u;
@@ -620,7 +624,7 @@ cudaError_t capture_newton_iteration(ipc_ctx* ctx, cudaGraphConditionalHandle hP
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, c0, hP, 1); }, c0);
   long long mn = ctx->launches;
   cudaError_t e = cond_body(c0, c1, hP, cudaGraphCondTypeWhile, [&] {
-    L.pcg_iter = pcg_iteration(ctx, c1, hP, 1);
+    L.pcg_iter = pcg_iteration(ctx, c1, hP, 1, window);
     return cudaSuccess;
   });
   if (e != cudaSuccess) return e;
@@ -754,7 +758,8 @@ ipc_status capture_roll(ipc_ctx* ctx) {
       long long m = ctx->launches;
       KL(ctx, KC_PREDICT, [&] { return launch_roll_begin(d, c0); }, c0);
       IterLaunches it;
-      cudaError_t e1 = capture_newton_iteration(ctx, hP, hA, hL, it);
+      const int w = ctx->prm.rollout_pcg_window;
+      cudaError_t e1 = capture_newton_iteration(ctx, hP, hA, hL, it, w > 0 ? (unsigned)w : 0xffffffffu);
       KL(ctx, KC_MISC, [&] { return launch_roll_end(d, c0); }, c0);
       KL(ctx, KC_MISC, [&] { return launch_roll_cond(d, c0, hR); }, c0);
       L.iter = (ctx->launches - m) - it.pcg_iter - it.ls_prep - it.ls_trial;
@@ -887,6 +892,7 @@ void ipc_default_params(ipc_params* p) {
   p->friction_mu = 0.0;
   p->friction_eps_v = 1e-3;
   p->newton_abs_after = 1000000;
+  p->rollout_pcg_window = 0;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
@@ -907,7 +913,8 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
                            size_t ws_bytes, void* cuda_stream, ipc_ctx** out) {
   if (!prm || !out || !dev_workspace) return IPC_EINVAL;
   if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
-      prm->newton_abs_after < 0 ||
+      prm->newton_abs_after < 0 || prm->rollout_pcg_window < 0 || prm->rollout_pcg_window == 1 ||
+      (prm->rollout_pcg_window & 1) ||
       prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
     return IPC_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
@@ -1013,7 +1020,7 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   // a candidate replaces the default shape only when it is more than 5%
   // faster (ties and noise keep the default)
   const int us_[3] = {2, 4, 8};
-  const int def_u = d.prec ? 4 : 2;
+  const int def_u = 2;
   for (int k = 0; k < 3; ++k) {
     d.spmv_unroll = us_[k];
     d.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(d.prec, us_[k]);
@@ -1127,7 +1134,7 @@ ipc_status ipc_set_state(ipc_ctx* ctx, int env, const double* x, const double* v
   KL(ctx, KC_MISC, [&] { return launch_check_inverted(ctx->dev, ctx->stream); });
   KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(ctx->dev, I_SEL, false, ctx->stream); });
   KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(ctx->dev, I_SEL, false, ctx->stream); });
-  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 2, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(ctx->dev, 6, ctx->stream); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(ctx->dev, I_SEL, false, ctx->stream); });
   KL(ctx, KC_MISC, [&] { return launch_cross_check(ctx->dev, I_SEL, ctx->stream); });
   KL(ctx, KC_MISC, [&] { return launch_min_dist(ctx->dev, I_SEL, ctx->stream); });
@@ -1298,6 +1305,10 @@ ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stat
     ctx->launches += L.pre + (long long)c[0] * L.newton + (long long)c[4] * L.pcg_iter +
                      (long long)c[6] * L.ls_prep + (long long)c[5] * L.ls_trial + L.post;
     ctx->step_graph_pending = false;
+    ctx->last_loop_iters = c[0];
+    ctx->last_pcg_launches = c[4];
+  } else {
+    ctx->last_loop_iters = ctx->last_pcg_launches = 0;
   }
   ctx->step_pending = false;
   const std::vector<int>& sel = ctx->last_sel;
@@ -1320,6 +1331,8 @@ ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stat
     S.swept_pairs += ei[I_SWEPTTOT];
   }
   S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->step_t0).count();
+  S.loop_iters = ctx->last_loop_iters;
+  S.pcg_launches = ctx->last_pcg_launches;
   if (stats) *stats = S;
   return IPC_OK;
 }
@@ -1355,8 +1368,13 @@ ipc_status ipc_rollout(ipc_ctx* ctx, const int32_t* env_ids, int n, int n_steps,
     CK(cudaMemcpy2DAsync(ctx->dev.env_i + I_RLIMIT, NUM_INTS * sizeof(int), col.data(), sizeof(int), sizeof(int),
                          ctx->pk.n_envs, cudaMemcpyHostToDevice, s));  // pageable: staged before return
   }
-  // every env's step ends within newton_max iterations: the cap only guards
-  const unsigned long long cap = (unsigned long long)n_steps * ((unsigned long long)ctx->prm.newton_max + 1) + 2;
+  // every env's step ends within newton_max Newton iterations, each within
+  // ceil(pcg_max / window) + 1 loop iterations: the cap only guards
+  const unsigned long long w = ctx->prm.rollout_pcg_window > 0 ? (unsigned long long)ctx->prm.rollout_pcg_window
+                                                               : (unsigned long long)ctx->prm.pcg_max;
+  const unsigned long long per_newton = ((unsigned long long)ctx->prm.pcg_max + w - 1) / w + 1;
+  const unsigned long long cap =
+      (unsigned long long)n_steps * ((unsigned long long)ctx->prm.newton_max + 1) * per_newton + 2;
   KL(ctx, KC_MISC, [&] { return launch_roll_setup(d, dev_targets, n_steps, cap, s); });
   if (!ctx->prof_on) {
     if (!ctx->roll_exec && (st = capture_roll(ctx)) != IPC_OK) return st;
@@ -1398,6 +1416,10 @@ ipc_status ipc_rollout_results(ipc_ctx* ctx, int32_t* per_env_status, int32_t* p
     const long long iters = c[0] > 0 ? (long long)c[0] - 1 : 0;
     ctx->launches += L.pre + iters * L.iter + (long long)c[4] * L.pcg_iter + (long long)c[6] * L.ls_prep +
                      (long long)c[5] * L.ls_trial;
+    ctx->last_loop_iters = iters;
+    ctx->last_pcg_launches = c[4];
+  } else {
+    ctx->last_loop_iters = ctx->last_pcg_launches = 0;
   }
   ctx->roll_pending = false;
   const std::vector<int>& sel = ctx->last_sel;
@@ -1421,6 +1443,8 @@ ipc_status ipc_rollout_results(ipc_ctx* ctx, int32_t* per_env_status, int32_t* p
     S.swept_pairs += ei[I_RSWEPT];
   }
   S.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ctx->step_t0).count();
+  S.loop_iters = ctx->last_loop_iters;
+  S.pcg_launches = ctx->last_pcg_launches;
   if (stats) *stats = S;
   return IPC_OK;
 }
@@ -1540,7 +1564,7 @@ ipc_status ipc_debug_pairs(ipc_ctx* ctx, int env, const double* cv_x, const doub
                      ctx->stream));
   if ((st = select_envs(ctx, {env})) != IPC_OK) return st;
   KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_SEL, cv_x_end != nullptr, ctx->stream); });
-  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 6, ctx->stream); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_SEL, cv_x_end != nullptr, ctx->stream); });
   if ((st = last_cuda(ctx)) != IPC_OK) return st;
   if ((st = sync_flags(ctx)) != IPC_OK) return st;
@@ -1574,7 +1598,7 @@ ipc_status ipc_debug_accd(ipc_ctx* ctx, int env, const double* dir, double* alph
   if ((st = select_envs(ctx, {env}, I_LS)) != IPC_OK) return st;
   KL(ctx, KC_CVPOS, [&] { return launch_cv_pos(d, I_LS, true, ctx->stream); });
   KL(ctx, KC_OBJBOX, [&] { return launch_obj_box(d, I_LS, true, ctx->stream); });
-  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 2, ctx->stream); });
+  KL(ctx, KC_MISC, [&] { return launch_env_reset(d, 5, ctx->stream); });
   KL(ctx, KC_BROAD, [&] { return launch_broad(d, I_LS, true, ctx->stream); });
   // S_ACCD = 1 then min over pairs
   std::vector<double> one(1, 1.0);

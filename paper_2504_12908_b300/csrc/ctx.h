@@ -60,6 +60,8 @@ enum EnvInt {
   I_GEN,          // Newton iterations ever run (tags the rows contact terms touch)
   I_PAIRTOT,      // static candidate pairs evaluated this step (all Newton iterations)
   I_SWEPTTOT,     // swept candidate pairs of this step's line searches
+  I_NEWT,         // starts a Newton iteration now (in the step, no solve carried over, no decision pending)
+  I_DEC,          // its PCG solve ended: the Newton decision is pending
   // rollout (ipc_rollout: each env runs its own sequence of steps)
   I_RSTEP,        // steps completed in this rollout
   I_BEGIN,        // begins its next step at the top of the next loop iteration
@@ -91,7 +93,7 @@ struct Dev {
                                 // later iterations use their absolute values
   int prec;                     // 0 FP64, 1 mixed (FP32 Hessians and mat-vec)
   // launch shapes (ipc_autotune): SpMV slots in flight per lane (2, 4, 8;
-  // 0 = default by precision)
+  // 0 = the default, 2)
   int spmv_unroll;
   double fr_mu, fr_eh;          // friction coefficient; eps_v * h (fr_mu = 0: no friction)
   // static tables
@@ -143,6 +145,8 @@ struct Dev {
   int* pcg_list;                // [n_envs] envs still in PCG
   int* pcg_pair_off;            // [n_envs + 1] prefix of their groups of 8 active pairs
   int* pcg_row_off;             // [n_envs + 1] prefix of their 128-row CTAs
+  int2* pcg_item;               // per row item: (env, global row CTA)
+  int2* pcg_pitem;              // per pair item: (env, group of 8 active pairs)
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] the list is stale
   int pcg_grid;                 // CTAs of the persistent PCG row kernels
@@ -241,6 +245,7 @@ struct ipc_ctx {
     long long pre = 0, iter = 0, pcg_iter = 0, ls_prep = 0, ls_trial = 0;
   } roll_launches;
   bool roll_pending = false;      // a rollout ran; its results are not yet read
+  long long last_loop_iters = 0, last_pcg_launches = 0;  // of the last graph step / rollout
   cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams of conditional bodies
   unsigned int* h_step_ctl = nullptr;  // pinned read-back of Dev::step_ctl (8)
   // the last ipc_step: its envs, start time, and whether its results (and,

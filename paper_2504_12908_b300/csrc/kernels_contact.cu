@@ -674,7 +674,7 @@ __global__ void k_fric_setup(Dev d) {
   FOR_PAIRS(d, f) {
   int e;
   int k = pair_at(d, f, e);
-  if (!ENVI(d, e, I_ACTIVE) || ENVI(d, e, I_NEWTON) != 1) continue;
+  if (!ENVI(d, e, I_NEWT) || ENVI(d, e, I_NEWTON) != 1) continue;
   int4 v = d.pair_v[k];
   D3 X[4];
   fr_points(d, v, 0.0, X);
@@ -725,7 +725,7 @@ __global__ void k_fric_assemble(Dev d) {
   FOR_FRIC(d, li) {
   int e;
   const int j = fric_at(d, li, e);
-  if (!ENVI(d, e, I_ACTIVE)) continue;
+  if (!ENVI(d, e, I_NEWT)) continue;
   const int4 v = d.fr_v[j];
   const int cvs[4] = {v.x, v.y, v.z, v.w};
   D3 X[4];
@@ -916,7 +916,7 @@ __global__ void k_pnorm_body(Dev d) {
   int b = d.cv_body[c];
   if (b < 0) return;
   int e = d.body_env[b];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_DEC)) return;
   int row = d.cv_row[c];
   D3 xb = ld3(d.cv_xbar, c);
   D3 u = body_point(d.p, row, xb);

@@ -38,15 +38,6 @@ __device__ __forceinline__ T comp3(V3<T> v, int c) { return c == 0 ? v.x : (c ==
 
 __device__ __forceinline__ bool row_is_body(uint8_t k) { return k == ROW_BODY || k == ROW_BODY_DRIVEN; }
 
-// largest i in [0, n) with off[i] <= item (off[0] = 0 <= item < off[n])
-__device__ __forceinline__ int list_find(const int* off, int n, int item) {
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (off[mid] <= item) lo = mid; else hi = mid;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ int env_row_ctas(const Dev& d, int e) { return (d.env_row_off[e + 1] - d.env_row_off[e]) >> 7; }
 __device__ __forceinline__ int env_active_pairs(const Dev& d, int e) { return min(ENVI(d, e, I_NACT), d.env_pair_cap[e]); }
@@ -94,6 +85,11 @@ __device__ void build_list(const Dev& d) {
       d.pcg_list[ex[0]] = e;
       d.pcg_row_off[ex[0]] = ex[1];
       d.pcg_pair_off[ex[0]] = ex[2];
+      // per item its env and global row CTA / pair group, so that a kernel
+      // finds its item with one load instead of a search over the list
+      const int cta0 = d.env_row_off[e] >> 7;
+      for (int j = 0; j < v[1]; ++j) d.pcg_item[ex[1] + j] = make_int2(e, cta0 + j);
+      for (int j = 0; j < v[2]; ++j) d.pcg_pitem[ex[2] + j] = make_int2(e, j);
     }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1)
@@ -329,7 +325,7 @@ template <class HT>
 __global__ void k_pcg_init(Dev d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   const uint8_t kr = d.row_kind[r];
   const D3 rv = (kr == ROW_PINNED || kr == ROW_PAD) ? D3{0, 0, 0} : -1.0 * ld3(d.g, r);
   st3(d.r, r, rv);
@@ -358,6 +354,7 @@ __global__ void k_pcg_init(Dev d) {
     ENVS(d, e, S_DQC) = 0.0;
     ENVI(d, e, I_PCGIT) = 0;
     ENVI(d, e, I_PCG) = out[1] > 0.0 ? 1 : 0;
+    ENVI(d, e, I_DEC) = out[1] > 0.0 ? 0 : 1;   // nothing to solve: the decision follows
   }
 }
 
@@ -372,32 +369,28 @@ __global__ void k_pcg_begin(Dev d, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, d.pcg_ctl[C_LIVE] > 0 ? 1u : 0u);
 }
 
-// the item's env, local index and the env's per-iteration scalar, found by
-// thread 0 and shared with the CTA (one lookup per 128-row item)
-struct ItemInfo {
-  int e, local;
-  double s;
-};
 
 template <class HT, int U>
 __global__ void __launch_bounds__(128) k_pcg_matvec(Dev d) {
-  __shared__ ItemInfo it;
+  // the item's env, row CTA and beta, read by thread 0 and shared (keeps
+  // the per-thread registers of the row loop at the kernel's occupancy)
+  __shared__ int s_e, s_cta;
+  __shared__ double s_beta;
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_items = d.pcg_row_off[n_list];
   const int nb = pcg_new_buf(d), ob = nb ^ 1;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    __syncthreads();  // the previous item is done with `it`
+    __syncthreads();  // the previous item is done with the shared item data
     if (threadIdx.x == 0) {
-      const int li = list_find(d.pcg_row_off, n_list, item);
-      const int e = d.pcg_list[li];
-      it.e = ENVI(d, e, I_PCG) ? e : -1;               // stopped envs stay listed until a rebuild
-      it.local = item - d.pcg_row_off[li];
-      it.s = ENVS(d, e, S_PBETA);
+      const int2 it = d.pcg_item[item];                // (env, row CTA)
+      s_e = ENVI(d, it.x, I_PCG) ? it.x : -1;          // stopped envs stay listed until a rebuild
+      s_cta = it.y;
+      s_beta = ENVS(d, it.x, S_PBETA);
     }
     __syncthreads();
-    const int e = it.e;
+    const int e = s_e;
     if (e < 0) continue;
-    matvec_rows<HT, U>(d, e, (d.env_row_off[e] >> 7) + it.local, (HT)it.s, ob, nb);
+    matvec_rows<HT, U>(d, e, s_cta, (HT)s_beta, ob, nb);
   }
 }
 
@@ -405,52 +398,44 @@ __global__ void __launch_bounds__(128) k_pcg_matvec(Dev d) {
 // mat-vec (both form d_k on the fly from z_k and d_{k-1})
 template <class HT>
 __global__ void __launch_bounds__(128) k_pcg_pairs(Dev d) {
-  __shared__ ItemInfo it;
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_items = d.pcg_pair_off[n_list];
   const int ob = pcg_new_buf(d) ^ 1;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int li = list_find(d.pcg_pair_off, n_list, item);
-      const int e = d.pcg_list[li];
-      it.e = ENVI(d, e, I_PCG) ? e : -1;
-      it.local = item - d.pcg_pair_off[li];
-      it.s = ENVS(d, e, S_PBETA);
-    }
-    __syncthreads();
-    if (it.e < 0) continue;
-    matvec_pairs<HT>(d, it.e, it.local, (HT)it.s, ob);
+    const int2 it = d.pcg_pitem[item];                 // (env, group of 8 active pairs)
+    if (!ENVI(d, it.x, I_PCG)) continue;
+    matvec_pairs<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
   }
 }
 
 template <class HT>
-__global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalHandle h, int use_cond) {
+__global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalHandle h, int use_cond,
+                                                     unsigned window) {
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_items = d.pcg_row_off[n_list];
   const int nb = pcg_new_buf(d);
-  __shared__ ItemInfo it;
-  __shared__ double s_dq;
+  __shared__ double s_dq, s_al;
+  __shared__ int s_e, s_cta;
   __shared__ uint8_t s_tag;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    __syncthreads();  // the previous item is done with `it`
+    __syncthreads();  // the previous item is done with the shared item data
     if (threadIdx.x == 0) {
-      const int li = list_find(d.pcg_row_off, n_list, item);
-      const int e = d.pcg_list[li];
-      it.e = ENVI(d, e, I_PCG) ? e : -1;
-      it.local = item - d.pcg_row_off[li];
+      const int2 iv = d.pcg_item[item];                // (env, row CTA)
+      const int e = iv.x;
+      s_e = ENVI(d, e, I_PCG) ? e : -1;                // stopped envs stay listed until a rebuild
+      s_cta = iv.y;
       const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
       s_dq = dq;
-      it.s = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;    // alpha, once per item
+      s_al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;    // alpha, once per item
       s_tag = touch_tag(d, e);
     }
     __syncthreads();
-    const int e = it.e;
+    const int e = s_e;
     if (e < 0) continue;
-    const int cta = (d.env_row_off[e] >> 7) + it.local;
+    const int cta = s_cta;
     const int r = cta * 128 + threadIdx.x;
     const double dq = s_dq;
-    const double al = it.s;
+    const double al = s_al;
     const uint8_t kr = d.row_kind[r];
     // contact part of q on the rows this iteration's contact terms write
     D3 qcv{0, 0, 0};
@@ -493,6 +478,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
       const double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
       if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) {
         ENVI(d, e, I_PCG) = 0;
+        ENVI(d, e, I_DEC) = 1;
         atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
         atomicSub(d.pcg_ctl + C_LIVE, 1u);
       }
@@ -522,7 +508,12 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
   __syncthreads();
   if (s_rebuild) build_list(d);
   if (threadIdx.x == 0 && use_cond) {
-    const bool more = d.pcg_ctl[C_LIVE] > 0 && d.pcg_ctl[C_ITER] <= (unsigned)d.pcg_max + 1u;
+    // window: iterations of this solve loop (solves still running carry
+    // over to the next one; the direction buffers alternate by iteration,
+    // so an even window leaves a carried solve's d_{k-1} in buffer 0,
+    // where the next loop's first iteration reads it)
+    const bool more = d.pcg_ctl[C_LIVE] > 0 && d.pcg_ctl[C_ITER] <= (unsigned)d.pcg_max + 1u &&
+                      d.pcg_ctl[C_ITER] < window;
     cudaGraphSetConditional(h, more ? 1u : 0u);
   }
 }
@@ -570,7 +561,7 @@ int launch_pcg_begin(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h,
   return 1;
 }
 int launch_pcg_matvec(const Dev& d, cudaStream_t s) {
-  const int u = d.spmv_unroll ? d.spmv_unroll : (d.prec ? 4 : 2);
+  const int u = d.spmv_unroll ? d.spmv_unroll : 2;
   const int g = d.pcg_grid;
   if (d.prec) {
     if (u == 2) k_pcg_matvec<float, 2><<<g, 128, 0, s>>>(d);
@@ -588,9 +579,9 @@ int launch_pcg_pairs(const Dev& d, cudaStream_t s) {
   else k_pcg_pairs<double><<<d.pcg_grid_pairs, 128, 0, s>>>(d);
   return 1;
 }
-int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond) {
-  if (d.prec) k_pcg_update<float><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond);
-  else k_pcg_update<double><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond);
+int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
+  if (d.prec) k_pcg_update<float><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond, window);
+  else k_pcg_update<double><<<d.pcg_grid, 128, 0, s>>>(d, h, use_cond, window);
   return 1;
 }
 int launch_debug_dir_from_rows(const Dev& d, cudaStream_t s) {
@@ -607,7 +598,7 @@ int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
 // resident CTAs per SM of the persistent PCG kernels (the smaller of the two)
 int pcg_ctas_per_sm(int prec, int unroll) {
   int a = 0, b = 0;
-  const int u = unroll ? unroll : (prec ? 4 : 2);
+  const int u = unroll ? unroll : 2;
   if (prec) {
     if (u == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<float, 2>, 128, 0);
     else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_matvec<float, 8>, 128, 0);

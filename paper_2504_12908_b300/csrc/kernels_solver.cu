@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(64) k_tet(Dev d) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = t < d.n_tets;
   int e = ok ? find_env(d.env_tet_off, d.n_envs, t) : 0;
-  ok = ok && ENVI(d, e, I_ACTIVE);
+  ok = ok && ENVI(d, e, I_NEWT);
   // mixed mode: each warp stages its 32 tets' 144 Hessian values in shared
   // memory (rows padded to 145 words: conflict-free) and writes the 32 x 144
   // block out contiguously; FP64 mode stores directly
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(64) k_tet(Dev d) {
   }
   if (kStage) {
     const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    if (okm == 0u) return;  // no tet of this warp is in a starting env
     __syncwarp();
     const int t0 = t - lane;
     const float* wsh = sH + (threadIdx.x >> 5) * 32 * 145;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(128) k_body(Dev d) {
   const int b = blockIdx.x * 4 + w;
   if (b >= d.n_bodies) return;                    // warp-uniform; no block barriers below
   const int e = d.body_env[b];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   const int br = d.body_row[b];
   double* y = sy[w];
   double* dy = sdy[w];
@@ -261,7 +262,7 @@ __global__ void k_assemble(Dev d) {
   if (ch >= d.n_chunks) return;
   int r = ch * 32 + lane;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   uint8_t kr = d.row_kind[r];
   int slots = d.chunk_slots[ch];
   long long base = d.chunk_ptr[ch];
@@ -306,7 +307,7 @@ __global__ void k_assemble(Dev d) {
 __global__ void k_grad(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   uint8_t kr = d.row_kind[r];
   D3 g{0, 0, 0};
   if (kr == ROW_FREE || kr == ROW_ATTACHED) {
@@ -336,7 +337,7 @@ template <class HT>
 __global__ void k_precond_rows(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   uint8_t kr = d.row_kind[r];
   double P[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   if (kr == ROW_FREE || kr == ROW_ATTACHED) {
@@ -362,7 +363,7 @@ __global__ void k_precond_body(Dev d) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= d.n_bodies) return;
   int e = d.body_env[b];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_NEWT)) return;
   double M[144], Mi[144], work[288];
   for (int i = 0; i < 144; ++i) {
     M[i] = d.body_H[144 * b + i] + d.body_pc_acc[144 * b + i];
@@ -381,7 +382,7 @@ __global__ void k_newton_rows(Dev d) {
   __shared__ double sh[32];
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE)) return;
+  if (!ENVI(d, e, I_DEC)) return;
   uint8_t kr = d.row_kind[r];
   double pn = 0, cr = 0;
   if (is_gel(kr)) {
@@ -402,7 +403,7 @@ __global__ void k_newton_rows(Dev d) {
 __global__ void k_newton_decide(Dev d) {
   const int* has_driven = d.env_has_driven;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.n_envs || !ENVI(d, e, I_ACTIVE)) return;
+  if (e >= d.n_envs || !ENVI(d, e, I_DEC) || !ENVI(d, e, I_ACTIVE)) return;
   ENVI(d, e, I_LS) = 0;
   ENVI(d, e, I_PAIRTOT) += min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);  // this iteration's static list
   double res = ENVS(d, e, S_PNORM) / d.h;
@@ -429,7 +430,7 @@ __global__ void k_newton_decide(Dev d) {
 __global__ void k_al_update(Dev d) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   int e = d.cta_env[r >> 7];
-  if (!ENVI(d, e, I_ACTIVE) || ENVI(d, e, I_MODE) != 2) return;
+  if (!ENVI(d, e, I_DEC) || !ENVI(d, e, I_ACTIVE) || ENVI(d, e, I_MODE) != 2) return;
   if (!is_driven(d.row_kind[r])) return;
   st3(d.lam, r, ld3(d.lam, r) - d.al_kappa * (ld3(d.x, r) - ld3(d.s_tgt, r)));
 }
@@ -593,8 +594,10 @@ __global__ void k_finalize_envs(Dev d) {
   }
 }
 
-// what: 0 = new step (counters, status), 1 = Newton-iteration scalars,
-// 2 = pair list (count, overflow), 3 = min distance, 4 = select every env
+// what: 0 = new step (counters, status), 1 = Newton-iteration start (which
+// envs start one, their scalars), 2 / 5 / 6 = pair count of the envs
+// starting a Newton iteration / in a line search / selected, 3 = min
+// distance, 4 = select every env
 __global__ void k_env_reset(Dev d, int what) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (what == 0 && e < 8) d.step_ctl[e] = 0u;  // new step: loop counters
@@ -602,6 +605,8 @@ __global__ void k_env_reset(Dev d, int what) {
   if (what == 0) {
     if (!ENVI(d, e, I_SEL)) return;
     ENVI(d, e, I_ACTIVE) = 1;
+    ENVI(d, e, I_PCG) = 0;
+    ENVI(d, e, I_DEC) = 0;
     ENVI(d, e, I_STATUS) = IPC_OK;
     ENVI(d, e, I_NEWTON) = 0;
     ENVI(d, e, I_AL) = 0;
@@ -617,14 +622,23 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_SWEPTTOT) = 0;
     ENVS(d, e, S_ASUM) = 0.0;
   } else if (what == 1) {
-    if (!ENVI(d, e, I_ACTIVE)) return;
+    // an env starts a Newton iteration unless its solve carries over; the
+    // decision of its previous iteration is done
+    const int newt = ENVI(d, e, I_ACTIVE) && !ENVI(d, e, I_PCG);
+    ENVI(d, e, I_NEWT) = newt;
+    ENVI(d, e, I_DEC) = 0;
+    if (!newt) return;
     ENVS(d, e, S_PNORM) = 0.0;
     ENVS(d, e, S_CRES) = 0.0;
     ENVI(d, e, I_NEWTON) += 1;
     ENVI(d, e, I_GEN) += 1;
     ENVI(d, e, I_NACT) = 0;
-  } else if (what == 2) {
-    ENVI(d, e, I_NPAIRS) = 0;
+  } else if (what == 2) {  // the static list is rebuilt
+    if (ENVI(d, e, I_NEWT)) ENVI(d, e, I_NPAIRS) = 0;
+  } else if (what == 5) {  // the swept list is rebuilt
+    if (ENVI(d, e, I_LS)) ENVI(d, e, I_NPAIRS) = 0;
+  } else if (what == 6) {  // a selected env's list is rebuilt (set_state, diagnostics)
+    if (ENVI(d, e, I_SEL)) ENVI(d, e, I_NPAIRS) = 0;
   } else if (what == 3) {
     ENVS(d, e, S_MIND) = INFINITY;
     ENVI(d, e, I_FLAG) = 0;
@@ -643,6 +657,8 @@ __global__ void k_env_reset(Dev d, int what) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void begin_step_counters(const Dev& d, int e) {
   ENVI(d, e, I_ACTIVE) = 1;
+  ENVI(d, e, I_PCG) = 0;
+  ENVI(d, e, I_DEC) = 0;
   ENVI(d, e, I_STATUS) = IPC_OK;
   ENVI(d, e, I_NEWTON) = 0;
   ENVI(d, e, I_AL) = 0;
@@ -708,7 +724,8 @@ __global__ void k_roll_end(Dev d) {
   ENVI(d, e, I_BEGIN) = 0;
   int end = 0;
   if (ENVI(d, e, I_RUN)) {
-    if (ENVI(d, e, I_ACTIVE) && ENVI(d, e, I_NEWTON) >= d.newton_max) {
+    // the Newton cap applies once the iteration's solve and decision are done
+    if (ENVI(d, e, I_ACTIVE) && !ENVI(d, e, I_PCG) && ENVI(d, e, I_NEWTON) >= d.newton_max) {
       ENVI(d, e, I_ACTIVE) = 0;
       if (ENVI(d, e, I_STATUS) == IPC_OK) ENVI(d, e, I_STATUS) = IPC_ENOTCONV;
     }
@@ -789,6 +806,7 @@ __global__ void k_check_overflow(Dev d) {
     ENVI(d, e, I_STATUS) = IPC_EOVERFLOW;
     ENVI(d, e, I_ACTIVE) = 0;
     ENVI(d, e, I_LS) = 0;
+    ENVI(d, e, I_NEWT) = 0;
   }
 }
 

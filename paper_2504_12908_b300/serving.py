@@ -17,8 +17,12 @@ of env slots.  Admission is per slot:
   state back to rest) and steps from the next batched step on;
 * every pool is stepped by its own host thread on its own CUDA stream (the
   C-ABI calls release the GIL), so pools of different classes overlap on
-  the device; each batched step advances the pool's occupied slots, every
-  slot at its own script step.
+  the device; each call advances the pool's occupied slots, every slot at
+  its own script step: one batched step, or with ``chunk`` > 1 up to
+  ``chunk`` steps as one rollout (``ipc_rollout``: every slot on its own step
+  schedule inside one graph, a slot stops at its request's last step), so a
+  slot whose step converges fast does not wait for the slowest slot of the
+  pool at every step.  A freed slot is refilled between calls.
 
 The engine behind the loop is pluggable (``Engine``): ``GpuEngine`` drives
 the library; the tests drive the scheduling logic with a CPU stand-in.
@@ -110,6 +114,13 @@ class Pool:
     def step(self, slots: Sequence[int], ks: Sequence[int]) -> np.ndarray:   # per-slot status
         raise NotImplementedError
 
+    def advance(self, slots: Sequence[int], ks: Sequence[int], remaining: Sequence[int], chunk: int):
+        """Up to `chunk` steps of each listed slot (slot i at most
+        remaining[i]); returns (per-slot status, per-slot steps taken).
+        Default: one batched step."""
+        st = np.asarray(self.step(slots, ks))
+        return st, np.ones(len(slots), dtype=np.int64)
+
     def final_state(self, slot: int):
         raise NotImplementedError
 
@@ -178,6 +189,7 @@ class _GpuPool(Pool):
         self.n_slots = n_slots
         self.stream = torch.cuda.Stream(eng.device)
         self.envs = ipc.Envs([scene] * n_slots, eng.params, device=str(eng.device), stream=self.stream)
+        self.graphs = eng.graphs
         if eng.graphs:
             self.envs.set_graph_mode(2)
         mb = max(self.envs.max_bodies, 1)
@@ -203,16 +215,31 @@ class _GpuPool(Pool):
         with torch.cuda.stream(self.stream):
             self.dev_tg[slot].copy_(torch.as_tensor(tg), non_blocking=False)
 
-    def step(self, slots, ks):
+    def _targets(self, slots, ks, n):
+        """[n][n_slots][bodies][12]: step ks[i] + j of listed slot i's script
+        (clamped to the script's end); other slots get step 0."""
         torch = self.torch
+        dev = self.dev_tg.device
         with torch.cuda.stream(self.stream):
-            k_all = torch.zeros(self.n_slots, dtype=torch.long, device=self.dev_tg.device)
-            k_all[torch.as_tensor(list(slots), device=self.dev_tg.device)] = torch.as_tensor(
-                list(ks), dtype=torch.long, device=self.dev_tg.device)
-            tg = self.dev_tg[torch.arange(self.n_slots, device=self.dev_tg.device), k_all].contiguous()
-        self.envs.set_targets_all_device(tg)
+            k_all = torch.zeros(self.n_slots, dtype=torch.long, device=dev)
+            k_all[torch.as_tensor(list(slots), device=dev)] = torch.as_tensor(list(ks), dtype=torch.long, device=dev)
+            kk = (k_all[None, :] + torch.arange(n, device=dev)[:, None]).clamp_(max=self.max_steps - 1)
+            return self.dev_tg[torch.arange(self.n_slots, device=dev)[None, :], kk].contiguous()
+
+    def step(self, slots, ks):
+        self.envs.set_targets_all_device(self._targets(slots, ks, 1)[0])
         status, _ = self.envs.step(list(slots))
         return status
+
+    def advance(self, slots, ks, remaining, chunk):
+        """Up to `chunk` steps per slot as one rollout (every slot on its own
+        step schedule inside one graph) when graphs are on; else one step."""
+        n = int(min(chunk, max(remaining)))
+        if not self.graphs or n <= 1:
+            return super().advance(slots, ks, remaining, chunk)
+        tab = self._targets(slots, ks, n)
+        status, taken, _ = self.envs.rollout(n, tab, env_ids=list(slots), steps_per_env=list(remaining))
+        return status, taken
 
     def final_state(self, slot):
         x, _, y, _ = self.envs.get_state(slot)
@@ -239,8 +266,9 @@ class Server:
 
     def __init__(self, engine: Engine, max_resident: int = 4096, slots_per_pool: int = 256,
                  max_pools: int = 32, mem_reserve: int = 2 << 30, keep_state: bool = True,
-                 poll_s: float = 0.002):
+                 poll_s: float = 0.002, chunk: int = 1):
         self.engine = engine
+        self.chunk = max(1, int(chunk))       # steps per pool call (a rollout when > 1)
         self.max_resident = max_resident
         self.slots_per_pool = slots_per_pool
         self.max_pools = max_pools
@@ -315,14 +343,17 @@ class Server:
                     self._active += 1
                     self._peak_active = max(self._peak_active, self._active)
                 ts = time.perf_counter()
-                st = ps.pool.step(occ, [int(ps.k[s]) for s in occ])
+                remaining = [int(ps.req[s].n_steps - ps.k[s]) for s in occ]
+                st, taken = ps.pool.advance(occ, [int(ps.k[s]) for s in occ], remaining, self.chunk)
                 ms = 1e3 * (time.perf_counter() - ts)
                 now = time.perf_counter() - t0
+                n_env_steps = int(np.sum(taken))
                 with self._lock:
                     self._active -= 1
-                    self._step_samples.append((ms, len(occ)))
+                    # per-step latency of the call: its time over the most steps one slot took
+                    self._step_samples.append((ms / max(int(np.max(taken)), 1), n_env_steps))
                 for j, s in enumerate(occ):
-                    ps.k[s] += 1
+                    ps.k[s] += int(taken[j])
                     if st[j] != 0:
                         ps.status[s] = st[j]
                     if ps.k[s] >= ps.req[s].n_steps or st[j] != 0:

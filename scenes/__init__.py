@@ -99,6 +99,7 @@ class SolverParams:
     friction_mu: float = 0.0        # lagged IPC friction coefficient (0 = frictionless)
     friction_eps_v: float = 1e-3    # static/dynamic velocity threshold, m/s
     newton_abs_after: int = 1000000  # Newton iterations that clamp negative eigenvalues; |lambda| after
+    rollout_pcg_window: int = 0     # rollout: PCG iterations per loop iteration (0: whole solves)
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""

@@ -376,6 +376,14 @@ def test_objective_gradient_hessian_match_oracle():
 
 
 def test_newton_direction_matches_direct_solve():
+    """The PCG direction against the oracle's sparse direct solve of the same
+    system.  PCG stops at a relative residual of 1e-10 in the GPU's own
+    matrix, which matches the oracle's to ~1e-8 (up to 1e-4 on single
+    near-parallel edge pairs), so the residual in the oracle's matrix is
+    held to 1e-6; the direction is within cond(H) x 1e-10 of the exact one,
+    checked at 1e-5 of its largest entry (the contact systems here have
+    cond ~1e4-1e5, and the atomics of the contact terms change the last
+    bits of every PCG run)."""
     import scipy.sparse.linalg as spla
     sc, prm, oenv, traj = _contact_state()
     x, v, y, yd, _ = traj[-1]
@@ -394,7 +402,10 @@ def test_newton_direction_matches_direct_solve():
     po = np.zeros(oenv.ndof)
     po[f] = spla.spsolve(Ho[f][:, f].tocsc(), -go[f])
     assert iters > 0
-    assert np.abs(p - po).max() <= 1e-6 * np.abs(po).max()
+    Hf = Ho[f][:, f]
+    res = np.linalg.norm(Hf @ p[f] + go[f])
+    assert res <= 1e-6 * np.linalg.norm(go[f]), res / np.linalg.norm(go[f])
+    assert np.abs(p - po).max() <= 1e-5 * np.abs(po).max()
     genv.close()
 
 

@@ -64,12 +64,15 @@ def _assert_close(sa, sb, n_steps, bound=1e-6):
         assert np.abs(a[2][:, :3] - b[2][:, :3]).max() <= tol, e
 
 
-@pytest.mark.parametrize("profiled", [False, True])
-def test_rollout_matches_lockstep_steps(profiled):
+@pytest.mark.parametrize("profiled,window", [(False, 64), (False, 2), (False, 0), (True, 64)])
+def test_rollout_matches_lockstep_steps(profiled, window):
     """K steps of an uneven batch: as a rollout (one graph, or the same loop
-    as plain launches when profiling) and as K ipc_step calls."""
+    as plain launches when profiling) and as K ipc_step calls.  window: PCG
+    iterations per loop iteration (solves carried over between loop
+    iterations; 2 carries nearly every solve many times, 0 carries none)."""
     scs = _batch()
     prm = scenes.SolverParams().parity()
+    prm.rollout_pcg_window = window
     ga, st_a = _lockstep(scs, prm, K)
     assert np.all(st_a == 0)
     gb = ipc.Envs([sc.scene for sc in scs], prm, stream=torch.cuda.Stream())

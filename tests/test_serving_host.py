@@ -174,3 +174,35 @@ def test_poisson_arrivals_have_the_requested_rate():
     a = poisson_arrivals(20000, 2000.0, 4000)
     assert np.all(np.diff(a) > 0)
     assert abs(a[-1] / 20000 - 1 / 2000.0) < 0.02 / 2000.0 * 5
+
+
+class ChunkPool(FakePool):
+    """Advances up to `chunk` steps per call (slot i at most remaining[i]),
+    as the GPU pools' rollouts do."""
+
+    def advance(self, slots, ks, remaining, chunk):
+        taken = np.zeros(len(slots), np.int64)
+        for j, (s, k, rem) in enumerate(zip(slots, ks, remaining)):
+            assert self.req[s] is not None and self.k[s] == k and rem == self.req[s].n_steps - k
+            n = min(chunk, rem)
+            self.k[s] += n
+            taken[j] = n
+        time.sleep(self.eng.step_s)
+        return np.zeros(len(slots), np.int32), taken
+
+
+class ChunkEngine(FakeEngine):
+    def open_pool(self, scene, n_slots, max_steps):
+        return ChunkPool(self, scene, n_slots, max_steps)
+
+
+def test_chunked_calls_advance_each_slot_to_its_own_last_step():
+    reqs = [Request(rid=i, scene=("a", 10), n_steps=n, arrival=0.0) for i, n in enumerate([1, 5, 7, 3, 8, 2])]
+    eng = ChunkEngine(capacity=10_000)
+    rep = Server(eng, slots_per_pool=3, mem_reserve=0, chunk=4).run(reqs, realtime=False)
+    assert rep.completed == len(reqs) and rep.backlog == 0
+    assert rep.env_steps == sum(r.n_steps for r in reqs)
+    for r in reqs:
+        res = rep.results[r.rid]
+        assert res.steps == r.n_steps and res.status == 0
+        assert float(res.final_y[0, 0]) == r.n_steps        # the pool's own step count
