@@ -413,8 +413,8 @@ def state_diff(xa, ya, xb, yb, body_radius):
 # env-iterations that launch processed; reported, scaled to the average
 # launch by env-iterations, only while the kernel's source is the one that
 # was measured (hash of its text).
-MATVEC_TRAFFIC = {"env_iters": 24, "bytes": 116460288 + 3188480,
-                  "source_sha256": "5e01ef3a4c67618e6a4cab8330df02d105c54d2971104af4589f71b28c6db2f5"}
+MATVEC_TRAFFIC = {"env_iters": 24, "bytes": 116761088 + 3068928,
+                  "source_sha256": "5f59b1227f7cbbc216fdb82d0a701a6a93f14b4a029e90a259c69ebb902a31b2"}
 
 
 def _function_text(src: str, signature: str) -> str:
@@ -458,7 +458,7 @@ def matvec_traffic_per_launch(env_iters_per_launch):
 # sources are the ones that were measured (hash of their text).
 FP64_FLOPS_PER_UNIT = {
     "tet_elastic": (242.0, "2d957c0cc0b5181766dbd7c0fb0220283973b08d54633a9557ca7706721013ee"),
-    "pcg_update": (None, None),
+    "pcg_update": (22.63, "819bc207b9977cdc5fbf506d6a194abc4752c89fae72755d5fdb98d858eafb52"),
     "body_abd": (4920.0, "f61821426e8eded7636bb680544a5069633eb989788f447c6a37cef599b9d0e9"),
 }
 ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "pcg_update": "row per PCG iteration",
@@ -895,6 +895,10 @@ def _mixed_vs_fp64(args, scs):
             g.step()
         if prec == 1 and not args.no_autotune:
             g.autotune()
+        dev_tab = torch.as_tensor(np.stack(tg[args.warmup:args.warmup + args.steps]), dtype=torch.float64,
+                                  device=f"cuda:{local}")
+        g.rollout(0, dev_tab[:0])              # captures the rollout graph; no step
+        snap = snapshot(g)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         bad, newton_max, pcg = 0, 0, 0
@@ -907,10 +911,16 @@ def _mixed_vs_fp64(args, scs):
             pcg += stt["pcg_iters"]
         ev1.record(g.stream)
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        out[prec] = {"value": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps, "status_not_ok": bad,
-                     "newton_max": newton_max, "pcg_iters": pcg,
-                     "execution": "whole step as one CUDA graph"}
+        ms_lock = ev0.elapsed_time(ev1)
+        restore(g, snap)
+        ms_roll, tot_r, st_r, taken_r = time_rollout(g, dev_tab, 0, args.steps, g.stream)
+        out[prec] = {"value": n * args.steps / (ms_roll / 1e3), "ms_per_step": ms_roll / args.steps,
+                     "status_not_ok": int(np.sum(st_r != 0) + np.sum(taken_r != args.steps)),
+                     "newton_max": tot_r["newton_max"], "pcg_iters": tot_r["pcg_iters"],
+                     "execution": "the timed steps as one rollout (every env on its own step schedule)",
+                     "lockstep": {"value": n * args.steps / (ms_lock / 1e3), "ms_per_step": ms_lock / args.steps,
+                                  "status_not_ok": bad, "newton_max": newton_max, "pcg_iters": pcg,
+                                  "execution": "K batched steps, whole step as one CUDA graph each"}}
         g.close()
         torch.cuda.empty_cache()
     return out
@@ -974,12 +984,20 @@ def run_grasp(args):
             g.step()
         if not args.no_autotune:
             g.autotune()
-        snap = snapshot(g) if prec == 1 else None
+        g.rollout(0, dev_tg[:0])                 # captures the rollout graph; no step
+        snap = snapshot(g)
         ms, step_ms, tot, statuses = time_steps(g, dev_tg, args.warmup, args.steps, stream)
-        out[prec] = {"value": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-                     "status_not_ok": int(sum(int(np.sum(s_ != 0)) for s_ in statuses)),
-                     "newton_max": tot["newton_max"], "pcg_iters": tot["pcg_iters"]}
+        restore(g, snap)
+        ms_r, tot_r, st_r, taken_r = time_rollout(g, dev_tg, args.warmup, args.steps, stream)
+        out[prec] = {"value": n * args.steps / (ms_r / 1e3), "ms_per_step": ms_r / args.steps,
+                     "status_not_ok": int(np.sum(st_r != 0) + np.sum(taken_r != args.steps)),
+                     "newton_max": tot_r["newton_max"], "pcg_iters": tot_r["pcg_iters"],
+                     "execution": "the timed steps as one rollout (every env on its own step schedule)",
+                     "lockstep": {"value": n * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                                  "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                                                 "p99": float(np.percentile(step_ms, 99))},
+                                  "status_not_ok": int(sum(int(np.sum(s_ != 0)) for s_ in statuses)),
+                                  "newton_max": tot["newton_max"], "pcg_iters": tot["pcg_iters"]}}
         if prec == 0:
             keep["x64"] = [g.get_state(e) for e in range(n)]
             g.close()
@@ -1027,7 +1045,8 @@ def run_grasp(args):
             "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"two-finger grasp: {n} envs x (2 gel pads 32x32x6 on driven ABD fingers + "
                                    f"free ABD icosphere L4, r = 10 mm)", "timed_steps": f"{args.warmup}-{n_total - 1}",
-                       "execution": "whole step as one CUDA graph", "cache": "inputs larger than L2"},
+                       "execution": "the timed steps as one rollout (one CUDA graph, every env on its own step "
+                                    "schedule); lock-step whole-step graphs beside it", "cache": "inputs larger than L2"},
             "fp64": out[0], "mixed": out[1], "speedup_vs_fp64": out[1]["value"] / out[0]["value"],
             "rel_err_vs_fp64": {"max": float(np.max(errs)), "median": float(np.median(errs)), "envs": len(sample),
                                 "def": "one step from the FP64 end state, mixed vs FP64, max vertex difference / "

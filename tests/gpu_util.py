@@ -73,6 +73,34 @@ def oracle_restart(env: OracleEnv, x_n, v_n, y_n, yd_n, s_y, x, y):
     return xo, yo, st
 
 
+def other_minimiser(env: OracleEnv, x_n, v_n, y_n, yd_n, s_y, xg, yg, xo, yo, bar=1e-4):
+    """Reading C-21: is the GPU's end state (xg, yg), farther than the bar
+    from the oracle's (xo, yo), another converged point of the same step
+    rather than a stall?  Three tests, all on the oracle:
+    - the oracle's Newton + AL solve restarted at it, at the parity
+      tolerance (1e-7 m/s: a stall on a flat direction keeps moving there),
+      stays within the bar and converges;
+    - it is free of contact and inversion;
+    - its objective (the incremental potential with the step's targets, AL
+      multipliers zero, each point's own contact pairs) is not above the
+      oracle end point's by more than 1e-3 of the oracle step's decrease.
+    Returns (accepted, details)."""
+    prm = type(env.prm)(**env.prm.__dict__)
+    prm.newton_tol = 1e-7
+    tight = OracleEnv(env.scene, prm)
+    xr, yr, st = oracle_restart(tight, x_n, v_n, y_n, yd_n, s_y, xg, yg)
+    diag = bbox_diag(env, x_n, y_n)
+    moved = float(np.abs(all_points(env, xr, yr) - all_points(env, xg, yg)).max() / diag)
+    ctx = env.make_ctx(x_n, v_n, y_n, yd_n, s_y)
+
+    def energy(x, y):
+        return float(env.energy(x, y, ctx, env.pair_arrays(*env.static_pairs(x, y))))
+    e_n, e_g, e_o = energy(x_n, y_n), energy(xg, yg), energy(xo, yo)
+    de = (e_g - e_o) / max(e_n - e_o, 1e-300)
+    ok = st.status == 0 and moved <= bar and valid_state(env, xg, yg) and de <= 1e-3
+    return ok, {"moved": moved, "status": int(st.status), "dE_rel": de, "E_gpu": e_g, "E_oracle": e_o}
+
+
 def valid_state(env: OracleEnv, x, y) -> bool:
     """No touching pair and no inverted tet."""
     from oracle import distance as ods

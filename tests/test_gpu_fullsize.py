@@ -16,7 +16,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from gpu_util import all_points, bbox_diag, from_gpu_y, oracle_press_step, oracle_restart, valid_state  # noqa: E402
+from gpu_util import all_points, bbox_diag, from_gpu_y, oracle_press_step, other_minimiser  # noqa: E402
 from oracle import OracleEnv  # noqa: E402
 from paper_2504_12908_b300 import ipc  # noqa: E402
 from paper_2504_12908_b300.build import build  # noqa: E402
@@ -54,13 +54,10 @@ def _run(scs, prm, n_pre, samples):
         ygn = from_gpu_y(genv, e, oenv, ygn)
         err = np.abs(all_points(oenv, xg, ygn) - all_points(oenv, xo, yo)).max() / bbox_diag(oenv, x, y)
         if err > 1e-4:
-            # another minimiser of the same step (the objective is non-convex): the oracle restarted
-            # at the GPU's end state must stay there
-            xr, yr, sr = oracle_restart(oenv, x, v, y, yd, sy, xg, ygn)
-            assert sr.status == 0
-            moved = np.abs(all_points(oenv, xr, yr) - all_points(oenv, xg, ygn)).max() / bbox_diag(oenv, x, y)
-            assert moved <= 1e-4, (e, err, moved)
-            assert valid_state(oenv, xg, ygn)
+            # another converged point of the same step (the objective is
+            # non-convex; reading C-21), not a stall
+            ok, why = other_minimiser(oenv, x, v, y, yd, sy, xg, ygn, xo, yo)
+            assert ok, (e, err, why)
     # properties of every env: finite, speeds within what the scripts allow
     for e in range(len(scs)):
         x, v, y, yd = genv.get_state(e)

@@ -18,7 +18,7 @@ from oracle.broadphase import candidates, canonical
 from oracle.ccd import accd_batch, exact_toi
 from oracle.rest import lame
 
-from gpu_util import (all_points, bbox_diag, from_gpu_y, gpu_targets, oracle_restart, oracle_states, to_gpu_y,
+from gpu_util import (all_points, bbox_diag, from_gpu_y, gpu_targets, oracle_states, other_minimiser, to_gpu_y,
                       valid_state)
 
 torch = pytest.importorskip("torch")
@@ -790,14 +790,11 @@ def test_mixed_precision_step_within_1e4_of_oracle(which):
             # The step's objective is non-convex and can have several
             # minimisers (the faceted sphere squeezed between frictionless
             # pads is one such case): a different end point is accepted when
-            # the oracle's own Newton + AL solve, restarted there, stays
-            # there, and it is free of contact and inversion.  At most one
-            # such step per trajectory.
-            xr, yr, str_ = oracle_restart(same, x, v, y, yd, sy, xg, yg)
-            assert str_.status == 0, s_
-            moved = np.abs(all_points(oenv, xr, yr) - all_points(oenv, xg, yg)).max() / bbox_diag(oenv, x, y)
-            assert moved <= 1e-4, (s_, err, moved)
-            assert valid_state(same, xg, yg), s_
+            # it is another converged point of the step (reading C-21:
+            # restart at the parity tolerance, validity, objective value).
+            # At most one such step per trajectory.
+            ok, why = other_minimiser(same, x, v, y, yd, sy, xg, yg, xo, yo)
+            assert ok, (s_, err, why)
             other += 1
             continue
         worst = max(worst, err)
