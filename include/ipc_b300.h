@@ -216,21 +216,39 @@ typedef struct {
   float spmv_us[3];       /* mean mat-vec time per launch for 2, 4, 8 slots, us        */
   int grid_ctas_per_sm[3];/* grid candidates: half, all and twice the resident CTAs   */
   float grid_us[3];       /* mean mat-vec time per launch for those grids, us          */
+  int assemble_block;     /* threads per CTA of the gather assembly: 64, 128 or 256    */
+  float assemble_us[3];   /* mean assembly time per launch for 64, 128, 256, us        */
+  int pairs_ctas_per_sm;  /* broad phase: CTAs per SM of the candidate-pair search     */
+  float pairs_us[3];      /* mean broad-phase time per search for 4, 8, 16 CTAs / SM   */
 } ipc_tuning;
 
-/* Choose the PCG mat-vec's SELL slots in flight per lane and the persistent
- * PCG grid by timing `reps` launches of each candidate on this ctx's current
- * system (call it after at least one ipc_step, between steps), with every
- * env counted as iterating.  A candidate replaces the default shape only
- * when it is more than 5% faster.  It touches only PCG scratch (q, the new
- * direction buffer, the d.q sums) and clears the contact accumulator
- * afterwards, so later steps give the same results as before apart from the
- * launch shapes.  Any captured PCG graph is dropped and re-captured at the
- * next solve.  Not in the paper: a property of this library.  `out` may be
- * NULL. */
+/* Choose launch shapes by timing `reps` launches of each candidate on this
+ * ctx's current state (call it after at least one ipc_step, between steps),
+ * with every env counted as working: the PCG mat-vec's SELL slots in flight
+ * per lane and the persistent PCG grid, the gather assembly's CTA size, and
+ * the candidate-pair search's grid.  A candidate replaces the default shape
+ * only when it is more than 5% faster.  It touches only scratch that the
+ * next Newton iteration rebuilds (PCG scratch, the SELL values from the
+ * stored element blocks, the candidate pair lists) and clears the contact
+ * accumulator afterwards, so later steps give the same results as before
+ * apart from the launch shapes.  Captured graphs are dropped and
+ * re-captured at their next use.  Not in the paper: a property of this
+ * library.  `out` may be NULL. */
 ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out);
 
 int ipc_num_envs(const ipc_ctx* ctx);
+
+/* Bounds-checked builds (libipc_b300_checks.so, compiled with -DIPC_CHECKS):
+ * the kernels test the indices they gather through (SELL columns, tet
+ * vertices, pair and active-pair vertices and slots, PCG work items,
+ * assembly sources) and, on a violation, skip the access and record the
+ * first violation's code (1 SELL column, 2 tet vertex, 3 pair vertex, 4 PCG
+ * item, 5 active-pair slot or vertex, 6 assembly source) and index.
+ * *checks_built = 1 in such a build (0 otherwise, where *code stays 0);
+ * *code = 0 when nothing was recorded since the context was created.
+ * Synchronises the ctx stream.  Any pointer may be NULL.  A debugging aid of
+ * this library (no counterpart in the paper). */
+ipc_status ipc_check_report(ipc_ctx* ctx, int* checks_built, int* code, long long* index);
 ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies,
                          int* n_surface_out);
 

@@ -151,6 +151,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.fr_eh = prm.friction_eps_v * prm.dt;
   d.spmv_unroll = 0;
   d.pcg_grid = 148;
+  d.asm_block = 128;
+  d.pairs_grid = 148 * 8;
   d.newton_max = prm.newton_max;
   d.pcg_max = prm.pcg_max;
   d.ls_max = prm.ls_max;
@@ -263,6 +265,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_ctl = c.take<unsigned int>(8);
   d.step_ctl = c.take<unsigned int>(8);
   d.roll_ctl = c.take<unsigned long long>(4);
+  d.check_word = c.take<unsigned long long>(2);
   d.q = c.take<double>(R3);
   d.qc = c.take<double>(R3);
   d.pc = c.take<double>(6 * (size_t)pk.n_rows);
@@ -967,6 +970,8 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
+  CK(cudaMemsetAsync(ctx->dev.check_word, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  ctx->dev.pairs_grid = ctx->n_sm * 8;
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
 }
@@ -1046,6 +1051,40 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   d.pcg_grid = ctx->n_sm * best_c;
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
+  // gather assembly: 64, 128 or 256 threads per CTA, every env counted as
+  // starting a Newton iteration (rewrites the SELL values from the stored
+  // element blocks)
+  if ((st = select_envs(ctx, all, I_NEWT)) != IPC_OK) return st;
+  const int asm_cand[3] = {64, 128, 256};
+  for (int k = 0; k < 3; ++k) {
+    d.asm_block = asm_cand[k];
+    if ((st = time_launches(ctx, reps, [&] { launch_assemble(d, s); }, &t.assemble_us[k])) != IPC_OK) return st;
+  }
+  int best_a = 128;
+  best = t.assemble_us[1];
+  for (int k = 0; k < 3; ++k)
+    if (t.assemble_us[k] < best && t.assemble_us[k] < 0.95f * t.assemble_us[1]) { best = t.assemble_us[k]; best_a = asm_cand[k]; }
+  d.asm_block = best_a;
+  if ((st = select_envs(ctx, {}, I_NEWT)) != IPC_OK) return st;
+  // candidate-pair search: 4, 8 or 16 CTAs per SM over every env's current
+  // positions (the lists are rebuilt at the next Newton iteration)
+  if ((st = select_envs(ctx, all)) != IPC_OK) return st;
+  const int pc_cand[3] = {4, 8, 16};
+  for (int k = 0; k < 3; ++k) {
+    d.pairs_grid = ctx->n_sm * pc_cand[k];
+    if ((st = time_launches(ctx, reps, [&] {
+           launch_env_reset(d, 6, s);
+           launch_broad(d, I_SEL, false, s);
+         }, &t.pairs_us[k])) != IPC_OK)
+      return st;
+  }
+  int best_p = 8;
+  best = t.pairs_us[1];
+  for (int k = 0; k < 3; ++k)
+    if (t.pairs_us[k] < best && t.pairs_us[k] < 0.95f * t.pairs_us[1]) { best = t.pairs_us[k]; best_p = pc_cand[k]; }
+  d.pairs_grid = ctx->n_sm * best_p;
+  t.assemble_block = best_a;
+  t.pairs_ctas_per_sm = best_p;
   CK(cudaStreamSynchronize(s));
   // the captured graphs hold the old launch shapes
   drop_graphs(ctx);
@@ -1057,6 +1096,21 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
 }
 
 int ipc_num_envs(const ipc_ctx* ctx) { return ctx ? ctx->pk.n_envs : 0; }
+
+ipc_status ipc_check_report(ipc_ctx* ctx, int* checks_built, int* code, long long* index) {
+  if (!ctx) return IPC_EINVAL;
+#ifdef IPC_CHECKS
+  if (checks_built) *checks_built = 1;
+#else
+  if (checks_built) *checks_built = 0;
+#endif
+  unsigned long long w[2] = {0, 0};
+  CK(cudaMemcpyAsync(w, ctx->dev.check_word, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (code) *code = (int)w[0];
+  if (index) *index = (long long)w[1];
+  return IPC_OK;
+}
 
 ipc_status ipc_env_sizes(const ipc_ctx* ctx, int env, int* n_verts, int* n_bodies, int* n_surface_out) {
   if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;

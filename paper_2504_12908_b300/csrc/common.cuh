@@ -42,6 +42,31 @@ IPC_DEV void atomic_add3(double* p, int i, D3 v) {
 }
 IPC_D double comp(D3 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
 
+// ---------------------------------------------------------------- debug checks
+// Bounds-checked builds (-DIPC_CHECKS): IPC_CHECK(word, cond, code, index)
+// is false when cond fails, after recording (code, index) as the first
+// violation in word[0..1] (atomic, first one wins); the caller then skips
+// the access.  Release builds compile it to `true`.
+IPC_DEV bool check_record(unsigned long long* word, bool cond, unsigned code, long long index) {
+  if (cond) return true;
+  if (atomicCAS(word, 0ull, (unsigned long long)code) == 0ull) word[1] = (unsigned long long)index;
+  return false;
+}
+#ifdef IPC_CHECKS
+#define IPC_CHECK(word, cond, code, index) ::ipc::check_record((word), (cond), (code), (long long)(index))
+#else
+#define IPC_CHECK(word, cond, code, index) true
+#endif
+// codes of IPC_CHECK
+enum CheckCode : unsigned {
+  CHK_SELL_COL = 1,   // a SELL column outside the row space
+  CHK_TET_VERT = 2,   // a tet vertex outside the row space
+  CHK_PAIR_VERT = 3,  // a pair's contact vertex outside the contact vertices
+  CHK_PCG_ITEM = 4,   // a PCG work item outside the envs / row CTAs
+  CHK_ACT_SLOT = 5,   // an active-pair slot or vertex outside its range
+  CHK_ASM_SRC = 6,    // an assembly source outside the element blocks
+};
+
 // ---------------------------------------------------------------- atomics
 // min / max of non-negative doubles through their (monotone) bit patterns
 IPC_DEV void atomic_max_nonneg(double* addr, double v) {

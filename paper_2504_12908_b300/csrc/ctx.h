@@ -150,8 +150,11 @@ struct Dev {
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] the list is stale
   int pcg_grid;                 // CTAs of the persistent PCG row kernels
+  int asm_block;                // threads per CTA of the gather assembly (ipc_autotune)
+  int pairs_grid;               // CTAs of the candidate-pair search (ipc_autotune)
   int pcg_grid_pairs;           // CTAs of the persistent contact mat-vec
   unsigned long long* roll_ctl; // rollout: [0] address of the target table, [1] steps, [2] loop cap
+  unsigned long long* check_word;  // bounds-checked builds: [0] first violation's code, [1] its index
   unsigned int* step_ctl;       // per step (device-side loops): [0] Newton iterations done,
                                 // [1] trials of the current line search, [2] envs still in
                                 // Newton, [3] envs in a line search, [4] PCG iterations,

@@ -411,7 +411,10 @@ __global__ void k_barrier(Dev d, int flag) {
   double E, g[12];
   HT H[144];
   bool act = false;
-  if (ENVI(d, e, flag)) {
+  if (ENVI(d, e, flag) &&
+      IPC_CHECK(d.check_word, (unsigned)d.pair_v[k].x < (unsigned)d.n_cv && (unsigned)d.pair_v[k].y < (unsigned)d.n_cv &&
+                (unsigned)d.pair_v[k].z < (unsigned)d.n_cv && (unsigned)d.pair_v[k].w < (unsigned)d.n_cv,
+                CHK_PAIR_VERT, k)) {
     int4 v = d.pair_v[k];
     cvs[0] = v.x; cvs[1] = v.y; cvs[2] = v.z; cvs[3] = v.w;
     D3 X[4];
@@ -955,7 +958,7 @@ int launch_broad(const Dev& d, int flag, bool swept, cudaStream_t s) {
     if (ncl) { k_bv_refit_cl<<<nblk(ncl, 128), 128, 0, s>>>(d, flag); ++n; }
     if (nsc) { k_bv_refit_sc<<<nblk(nsc, 128), 128, 0, s>>>(d, flag); ++n; }
   }
-  k_pairs<<<148 * 8, 128, 0, s>>>(d);
+  k_pairs<<<d.pairs_grid > 0 ? d.pairs_grid : 148 * 8, 128, 0, s>>>(d);
   k_bp_check<<<nblk(d.n_envs, 128), 128, 0, s>>>(d, flag);
   k_env_scan<<<1, 1024, 0, s>>>(d, 0);
   return n + 3;

@@ -186,7 +186,10 @@ __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT bet
     int c[U];
     HT A[U][9];
 #pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = cn[u];
+    for (int u = 0; u < U; ++u) {
+      c[u] = cn[u];
+      if (!IPC_CHECK(d.check_word, (unsigned)c[u] < (unsigned)d.n_rows, CHK_SELL_COL, c[u])) c[u] = r;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -206,7 +209,8 @@ __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT bet
     }
   }
   for (; sl < slots; ++sl) {
-    const int c = colp[sl * 32];
+    int c = colp[sl * 32];
+    if (!IPC_CHECK(d.check_word, (unsigned)c < (unsigned)d.n_rows, CHK_SELL_COL, c)) c = r;
     const HT* A = val + (long long)sl * 288;
     const V3<HT> w = Dk<HT>::row(d, c, beta, ob);
     ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
@@ -246,9 +250,15 @@ __device__ __forceinline__ void matvec_pairs(const Dev& d, int e, int g, HT beta
   const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
   const int m = j / 3, c = j - 3 * m;
   const int local = 8 * g + (threadIdx.x >> 4);
-  const bool live = local < env_active_pairs(d, e);
   const int i = d.env_pair_off[e] + local;       // slot of this half-warp's pair
-  const int4 v = live ? d.act_v[i] : make_int4(0, 0, 0, 0);
+  bool live = local < env_active_pairs(d, e) &&
+              IPC_CHECK(d.check_word, (long long)i < d.n_pairs_cap, CHK_ACT_SLOT, i);
+  int4 v = live ? d.act_v[i] : make_int4(0, 0, 0, 0);
+  if (live && !IPC_CHECK(d.check_word, (unsigned)v.x < (unsigned)d.n_cv && (unsigned)v.y < (unsigned)d.n_cv &&
+                         (unsigned)v.z < (unsigned)d.n_cv && (unsigned)v.w < (unsigned)d.n_cv, CHK_ACT_SLOT, i)) {
+    live = false;
+    v = make_int4(0, 0, 0, 0);
+  }
   const int cv = m == 0 ? v.x : (m == 1 ? v.y : (m == 2 ? v.z : v.w));
   int b_pt = -1, row = 0;
   double xb[3] = {0, 0, 0};
@@ -383,7 +393,9 @@ __global__ void __launch_bounds__(128) k_pcg_matvec(Dev d) {
     __syncthreads();  // the previous item is done with the shared item data
     if (threadIdx.x == 0) {
       const int2 it = d.pcg_item[item];                // (env, row CTA)
-      s_e = ENVI(d, it.x, I_PCG) ? it.x : -1;          // stopped envs stay listed until a rebuild
+      const bool in = IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs &&
+                                (unsigned)it.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
+      s_e = in && ENVI(d, it.x, I_PCG) ? it.x : -1;    // stopped envs stay listed until a rebuild
       s_cta = it.y;
       s_beta = ENVS(d, it.x, S_PBETA);
     }
@@ -403,6 +415,7 @@ __global__ void __launch_bounds__(128) k_pcg_pairs(Dev d) {
   const int ob = pcg_new_buf(d) ^ 1;
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int2 it = d.pcg_pitem[item];                 // (env, group of 8 active pairs)
+    if (!IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs, CHK_PCG_ITEM, item)) continue;
     if (!ENVI(d, it.x, I_PCG)) continue;
     matvec_pairs<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
   }
@@ -420,9 +433,12 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     __syncthreads();  // the previous item is done with the shared item data
     if (threadIdx.x == 0) {
-      const int2 iv = d.pcg_item[item];                // (env, row CTA)
+      int2 iv = d.pcg_item[item];                      // (env, row CTA)
+      const bool in = IPC_CHECK(d.check_word, (unsigned)iv.x < (unsigned)d.n_envs &&
+                                (unsigned)iv.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
+      if (!in) iv = make_int2(0, 0);
       const int e = iv.x;
-      s_e = ENVI(d, e, I_PCG) ? e : -1;                // stopped envs stay listed until a rebuild
+      s_e = in && ENVI(d, e, I_PCG) ? e : -1;          // stopped envs stay listed until a rebuild
       s_cta = iv.y;
       const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
       s_dq = dq;

@@ -68,6 +68,10 @@ __global__ void __launch_bounds__(64) k_tet(Dev d) {
   float* mine = sH + (kStage ? ((threadIdx.x >> 5) * 32 + lane) * 145 : 0);
   if (ok) {
     const int* q = d.tets + 4 * (long long)t;
+    for (int a = 0; a < 4; ++a) ok = ok && IPC_CHECK(d.check_word, (unsigned)q[a] < (unsigned)d.n_rows, CHK_TET_VERT, t);
+  }
+  if (ok) {
+    const int* q = d.tets + 4 * (long long)t;
     D3 X[4];
     for (int a = 0; a < 4; ++a) X[a] = ld3(d.x, q[a]);
     double Dmi[9];
@@ -280,6 +284,7 @@ __global__ void k_assemble(Dev d) {
       } else if (live) {
         const HT* tH = reinterpret_cast<const HT*>(d.tetH);
         for (int k = d.asm_ptr[blk]; k < d.asm_ptr[blk + 1]; ++k) {
+          if (!IPC_CHECK(d.check_word, (unsigned)d.asm_src[k] < 16u * (unsigned)d.n_tets, CHK_ASM_SRC, k)) continue;
           const HT* src = tH + 9 * (long long)d.asm_src[k];
           for (int c = 0; c < 9; ++c) v[c] += src[c];
         }
@@ -861,8 +866,9 @@ int launch_body(const Dev& d, cudaStream_t s) {
   return 1;
 }
 int launch_assemble(const Dev& d, cudaStream_t s) {
-  if (d.prec) k_assemble<float><<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d);
-  else k_assemble<double><<<nblk(32LL * d.n_chunks, 128), 128, 0, s>>>(d);
+  const int b = d.asm_block > 0 ? d.asm_block : 128;
+  if (d.prec) k_assemble<float><<<nblk(32LL * d.n_chunks, b), b, 0, s>>>(d);
+  else k_assemble<double><<<nblk(32LL * d.n_chunks, b), b, 0, s>>>(d);
   return 1;
 }
 int launch_grad(const Dev& d, cudaStream_t s) { k_grad<<<ROWGRID>>>(d); return 1; }

@@ -14,7 +14,9 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libipc_b300.so")
+# IPC_B300_CHECKS=1 loads the bounds-checked build (see ipc_check_report)
+LIB_PATH = os.path.join(_HERE, "libipc_b300_checks.so" if os.environ.get("IPC_B300_CHECKS") == "1"
+                        else "libipc_b300.so")
 
 IPC_OK, IPC_EINVAL, IPC_ENOMEM, IPC_ENOTCONV, IPC_EINTERSECT, IPC_EINVERTED, IPC_EOVERFLOW, IPC_ECUDA = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ENOTCONV", "EINTERSECT", "EINVERTED", "EOVERFLOW", "ECUDA"]
@@ -49,7 +51,9 @@ class ipc_sensor(C.Structure):
 
 class ipc_tuning(C.Structure):
     _fields_ = [("spmv_unroll", C.c_int), ("pcg_ctas_per_sm", C.c_int), ("spmv_us", C.c_float * 3),
-                ("grid_ctas_per_sm", C.c_int * 3), ("grid_us", C.c_float * 3)]
+                ("grid_ctas_per_sm", C.c_int * 3), ("grid_us", C.c_float * 3),
+                ("assemble_block", C.c_int), ("assemble_us", C.c_float * 3),
+                ("pairs_ctas_per_sm", C.c_int), ("pairs_us", C.c_float * 3)]
 
 
 class ipc_step_stats(C.Structure):
@@ -80,6 +84,7 @@ def lib():
             "ipc_destroy": (i32, [vp]),
             "ipc_last_error": (C.c_char_p, [vp]),
             "ipc_num_envs": (i32, [vp]),
+            "ipc_check_report": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_longlong)]),
             "ipc_env_sizes": (i32, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
             "ipc_body_com": (i32, [vp, i32, i32, _dp]),
             "ipc_set_state": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
@@ -128,7 +133,7 @@ def lib():
 
 
 EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc_destroy", "ipc_last_error",
-            "ipc_num_envs", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets", "ipc_reset_env",
+            "ipc_num_envs", "ipc_check_report", "ipc_env_sizes", "ipc_body_com", "ipc_set_state", "ipc_get_state", "ipc_set_targets", "ipc_reset_env",
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_step_results", "ipc_rollout", "ipc_rollout_results", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
             "ipc_read_gel_surface_all_noalloc", "ipc_env_stats", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
@@ -543,7 +548,11 @@ class Envs:
         self._check(lib().ipc_autotune(self._ctx, int(reps), C.byref(t)), "ipc_autotune")
         return {"spmv_unroll": t.spmv_unroll, "pcg_ctas_per_sm": t.pcg_ctas_per_sm,
                 "spmv_us": {u: round(float(t.spmv_us[k]), 2) for k, u in enumerate((2, 4, 8))},
-                "grid_us": {int(t.grid_ctas_per_sm[k]): round(float(t.grid_us[k]), 2) for k in range(3)}}
+                "grid_us": {int(t.grid_ctas_per_sm[k]): round(float(t.grid_us[k]), 2) for k in range(3)},
+                "assemble_block": t.assemble_block,
+                "assemble_us": {b: round(float(t.assemble_us[k]), 2) for k, b in enumerate((64, 128, 256))},
+                "pairs_ctas_per_sm": t.pairs_ctas_per_sm,
+                "pairs_us": {c: round(float(t.pairs_us[k]), 2) for k, c in enumerate((4, 8, 16))}}
 
     def set_graph_mode(self, mode=1):
         """CUDA-graph execution: 0 plain launches, 1 (or True) each PCG solve
@@ -568,6 +577,13 @@ class Envs:
                         "ipc_profile_get")
             out[name.value.decode()] = (int(n.value), float(ms.value))
         return out
+
+    def check_report(self) -> dict:
+        """First bounds violation recorded by a checked build (ipc_check_report)."""
+        built, code, idx = C.c_int(), C.c_int(), C.c_longlong()
+        self._check(lib().ipc_check_report(self._ctx, C.byref(built), C.byref(code), C.byref(idx)),
+                    "ipc_check_report")
+        return {"checks_built": bool(built.value), "code": int(code.value), "index": int(idx.value)}
 
     def launch_count(self) -> int:
         return int(lib().ipc_launch_count(self._ctx))

@@ -711,9 +711,10 @@ def test_graph_mode_matches_plain_launches(precision, mode):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotune_picks_valid_shapes_and_keeps_results(precision):
-    """ipc_autotune times the PCG mat-vec's unrolls and persistent grids on
-    the ctx's own system between steps; later steps match a ctx that was not
-    tuned (to rounding: atomics order)."""
+    """ipc_autotune times the PCG mat-vec's unrolls and persistent grids, the
+    assembly's CTA size and the pair search's grid on the ctx's own state
+    between steps; later steps match a ctx that was not tuned (to rounding:
+    atomics order)."""
     scs = [scenes.config2(e) for e in range(3)]
     prm = scenes.SolverParams().parity() if precision == 0 else scenes.SolverParams()
     prm.precision = precision
@@ -733,6 +734,8 @@ def test_autotune_picks_valid_shapes_and_keeps_results(precision):
             tun = a.autotune(reps=3)
             assert tun["spmv_unroll"] in (2, 4, 8) and tun["pcg_ctas_per_sm"] in tun["grid_us"]
             assert all(v > 0 for v in tun["spmv_us"].values()) and all(v > 0 for v in tun["grid_us"].values())
+            assert tun["assemble_block"] in tun["assemble_us"] and tun["pairs_ctas_per_sm"] in tun["pairs_us"]
+            assert all(v > 0 for v in tun["assemble_us"].values()) and all(v > 0 for v in tun["pairs_us"].values())
         for e in range(3):
             xa, xb = a.get_state(e)[0], b.get_state(e)[0]
             diag = np.linalg.norm(xa.max(0) - xa.min(0))
