@@ -413,8 +413,8 @@ def state_diff(xa, ya, xb, yb, body_radius):
 # env-iterations that launch processed; reported, scaled to the average
 # launch by env-iterations, only while the kernel's source is the one that
 # was measured (hash of its text).
-MATVEC_TRAFFIC = {"env_iters": 24, "bytes": 116761088 + 3068928,
-                  "source_sha256": "5f59b1227f7cbbc216fdb82d0a701a6a93f14b4a029e90a259c69ebb902a31b2"}
+MATVEC_TRAFFIC = {"env_iters": 24, "bytes": 116996352 + 3195136,
+                  "source_sha256": "6c0cc14516947417a70839a2ad4f2b3dd6f6613b6cc979217d68974595a0b7c9"}
 
 
 def _function_text(src: str, signature: str) -> str:
@@ -457,9 +457,9 @@ def matvec_traffic_per_launch(env_iters_per_launch):
 # ALU roofline against the measured FP64 FMA rate, only while the kernel
 # sources are the ones that were measured (hash of their text).
 FP64_FLOPS_PER_UNIT = {
-    "tet_elastic": (242.0, "2d957c0cc0b5181766dbd7c0fb0220283973b08d54633a9557ca7706721013ee"),
-    "pcg_update": (22.63, "819bc207b9977cdc5fbf506d6a194abc4752c89fae72755d5fdb98d858eafb52"),
-    "body_abd": (4920.0, "f61821426e8eded7636bb680544a5069633eb989788f447c6a37cef599b9d0e9"),
+    "tet_elastic": (242.0, "0657c712ffa87872172c39c9433c5f8809afe6af23538ae1311894e1c2e972ad"),
+    "pcg_update": (22.63, "c5a50b0e2e2d219cb1553dafacbb75773f5f150648eb29ab05ae975374101f11"),
+    "body_abd": (4920.0, "176a85a7dc5c0d3c979f3de3ea30e78cb61eee8f864c11b05d2bc3a3ad460833"),
 }
 ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "pcg_update": "row per PCG iteration",
             "body_abd": "body per Newton iteration"}
