@@ -364,19 +364,76 @@ __global__ void k_precond_rows(Dev d) {
   for (int c = 0; c < 9; ++c) d.pc_acc[9 * r + c] = 0.0;
 }
 
-__global__ void k_precond_body(Dev d) {
-  int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.n_bodies) return;
-  int e = d.body_env[b];
+// Body blocks of the preconditioner: the inverse of each body's 12x12
+// diagonal block (its Hessian plus the contact terms on it), one warp per
+// body, 4 bodies per 128-thread CTA.  Gauss-Jordan with partial pivoting on
+// [M | I] in shared memory: for each column the lanes find the pivot (the
+// first row with the largest magnitude, as a serial scan would), swap and
+// scale the pivot row and eliminate the other rows, each lane owning entries
+// of the 12 x 24 array; every entry sees the same operations in the same
+// order as in the one-thread elimination.  A singular block gets the
+// identity.
+__global__ void __launch_bounds__(128) k_precond_body(Dev d) {
+  __shared__ double sM[4][12][25];   // rows padded to 25 words
+  __shared__ int s_bad[4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int b = blockIdx.x * 4 + w;
+  if (b >= d.n_bodies) return;                    // warp-uniform; no block barriers below
+  const int e = d.body_env[b];
   if (!ENVI(d, e, I_NEWT)) return;
-  double M[144], Mi[144], work[288];
-  for (int i = 0; i < 144; ++i) {
-    M[i] = d.body_H[144 * b + i] + d.body_pc_acc[144 * b + i];
+  double (*M)[25] = sM[w];
+  for (int i = lane; i < 144; i += 32) {
+    const int r = i / 12, c = i - 12 * r;
+    M[r][c] = d.body_H[144 * b + i] + d.body_pc_acc[144 * b + i];
+    M[r][12 + c] = (r == c) ? 1.0 : 0.0;
     d.body_pc_acc[144 * b + i] = 0.0;
   }
-  if (!invert_small<12, double>(M, Mi, work))
-    for (int i = 0; i < 144; ++i) Mi[i] = (i % 13 == 0) ? 1.0 : 0.0;
-  for (int i = 0; i < 144; ++i) d.body_pc[144 * b + i] = Mi[i];
+  if (lane == 0) s_bad[w] = 0;
+  __syncwarp();
+  for (int c = 0; c < 12; ++c) {
+    // pivot: largest |M[r][c]| for r >= c, the first one on ties
+    double best = lane >= c && lane < 12 ? fabs(M[lane][c]) : -1.0;
+    int piv = lane;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int op = __shfl_down_sync(0xffffffffu, piv, o);
+      if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+    }
+    best = __shfl_sync(0xffffffffu, best, 0);
+    piv = __shfl_sync(0xffffffffu, piv, 0);
+    if (!(best > 0.0)) {                           // singular (or NaN): identity below
+      if (lane == 0) s_bad[w] = 1;
+      break;
+    }
+    if (piv != c && lane < 24) {
+      const double t = M[c][lane];
+      M[c][lane] = M[piv][lane];
+      M[piv][lane] = t;
+    }
+    __syncwarp();
+    const double inv = 1.0 / M[c][c];
+    __syncwarp();
+    if (lane < 24) M[c][lane] *= inv;
+    __syncwarp();
+    // factors of the other rows, read before any row changes
+    double f[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) f[r] = M[r][c];
+    __syncwarp();
+    if (lane < 24) {
+      const double pc = M[c][lane];
+#pragma unroll
+      for (int r = 0; r < 12; ++r)
+        if (r != c && f[r] != 0.0) M[r][lane] -= f[r] * pc;
+    }
+    __syncwarp();
+  }
+  __syncwarp();
+  const bool bad = s_bad[w] != 0;
+  for (int i = lane; i < 144; i += 32) {
+    const int r = i / 12, c = i - 12 * r;
+    d.body_pc[144 * b + i] = bad ? ((r == c) ? 1.0 : 0.0) : M[r][12 + c];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -876,7 +933,7 @@ int launch_precond(const Dev& d, cudaStream_t s) {
   if (d.prec) k_precond_rows<float><<<ROWGRID>>>(d);
   else k_precond_rows<double><<<ROWGRID>>>(d);
   if (!d.n_bodies) return 1;
-  k_precond_body<<<nblk(d.n_bodies, 32), 32, 0, s>>>(d);
+  k_precond_body<<<nblk(d.n_bodies, 4), 128, 0, s>>>(d);
   return 2;
 }
 int launch_newton_check(const Dev& d, cudaStream_t s) {
