@@ -213,7 +213,8 @@ ipc_status ipc_set_graph_mode(ipc_ctx* ctx, int mode);
 typedef struct {
   int spmv_unroll;        /* SELL slots in flight per lane in the PCG mat-vec: 2, 4 or 8 */
   int pcg_ctas_per_sm;    /* persistent PCG grid: CTAs per SM (x SM count)            */
-  float spmv_us[3];       /* mean mat-vec time per launch for 2, 4, 8 slots, us        */
+  float spmv_us[3];       /* mat-vec time per launch for 2, 4, 8 slots, us (mean of a
+                             launch over every env and one over every 4th env)     */
   int grid_ctas_per_sm[3];/* grid candidates: half, all and twice the resident CTAs   */
   float grid_us[3];       /* mean mat-vec time per launch for those grids, us          */
   int assemble_block;     /* threads per CTA of the gather assembly: 64, 128 or 256    */
@@ -223,10 +224,11 @@ typedef struct {
 } ipc_tuning;
 
 /* Choose launch shapes by timing `reps` launches of each candidate on this
- * ctx's current state (call it after at least one ipc_step, between steps),
- * with every env counted as working: the PCG mat-vec's SELL slots in flight
- * per lane and the persistent PCG grid, the gather assembly's CTA size, and
- * the candidate-pair search's grid.  A candidate replaces the default shape
+ * ctx's current state (call it after at least one ipc_step, between steps):
+ * the PCG mat-vec's SELL slots in flight per lane and the persistent PCG
+ * grid (each on a batch of every env and one of every 4th env: the mean),
+ * the gather assembly's CTA size and the candidate-pair search's grid
+ * (every env).  A candidate replaces the default shape
  * only when it is more than 5% faster.  It touches only scratch that the
  * next Newton iteration rebuilds (PCG scratch, the SELL values from the
  * stored element blocks, the candidate pair lists) and clears the contact
