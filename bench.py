@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--pcg-window", type=int, default=None,
                     help="rollout: PCG iterations per loop iteration (even; 0 = whole solves; default: the library's)")
+    ap.add_argument("--pcg-fused", type=int, default=None, choices=(0, 1),
+                    help="1: one fused kernel per PCG iteration, 0: three kernels (default: the library's)")
     ap.add_argument("--no-lockstep", action="store_true", help="skip the lock-step timing beside the rollout")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
     return ap.parse_args()
@@ -148,12 +150,14 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ workload
-def build_workload(n_envs, precision, pcg_window=None):
+def build_workload(n_envs, precision, pcg_window=None, pcg_fused=None):
     import scenes
     scene, params, deltas = scenes.config1_batch(n_envs)
     params.precision = precision
     if pcg_window is not None:
         params.rollout_pcg_window = pcg_window
+    if pcg_fused is not None:
+        params.pcg_fused = pcg_fused
     return scene, params, deltas
 
 
@@ -280,11 +284,18 @@ def kernel_bytes(genv, tot):
     hs = 4 if getattr(genv.params, "precision", 0) else 8   # Hessian / matrix value bytes
     vb = 12 if hs == 4 else 24                               # a PCG row of z, d or q
     pcg, newt = tot["pcg_iters"], tot["newton_env_iters"]
-    ls_evals = tot["ls_trials"] + max(newt - tot["env_steps"], 0)   # trials + the energy at alpha = 0
+    n_ls = max(newt - tot["env_steps"], 0)                   # line searches: iterations that did not stop
+    ls_evals = tot["ls_trials"] + n_ls                       # trials + the energy at alpha = 0
+    # contact vertices, at least: the coated gel surface and the body vertices
+    n_cv = ns + sum(len(b.rest_x) for b in genv.scenes[0].bodies)
     out = {
         # matrix values + columns, z and d_{k-1} read, d_k and q written per row
         "pcg_matvec": pcg * (blocks * (9 * hs + 4) + rows * 4 * vb),
+        # per active pair and PCG iteration: its packed 78-entry Hessian, the 4 points' z and d_{k-1}
+        # rows gathered, 12 FP64 contact entries scattered
+        "pair_matvec": tot.get("act_pair_iters", 0) * (78 * hs + 4 * 2 * vb + 12 * 8),
         # p and r read + written (FP64), d_k and q read, the 6-entry inverse block, z written
+        # (the fused iteration kernel, pcg_iter, does the work of the three PCG classes)
         "pcg_update": pcg * rows * (4 * 24 + 2 * vb + 6 * hs + vb),
         # indices, positions, Dm^-1, volume read; FP64 gradient and the Hessian written
         "tet_elastic": newt * T * (16 + 96 + 72 + 8 + 96 + 144 * hs),
@@ -300,7 +311,23 @@ def kernel_bytes(genv, tot):
         "gradient": newt * (T * 4 * 24 + rows * 4 * 24),
         # per body and Newton iteration: state, target, 12x12 Hessian and gradient
         "body_abd": newt * nb * (4 * 96 + 144 * 8 + 96),
+        # per Newton iteration: each row's diagonal block read and its 6-entry inverse written; each
+        # body's 12x12 block read and its inverse written (FP64)
+        "precond": newt * (rows * 15 * hs + nb * 2 * 144 * 8),
+        # per search: the contact vertices' positions read (x for the static search of a Newton
+        # iteration, x and p for the swept search of a line search), each candidate pair written
+        # (4 ids, kind, weight, mollifier threshold)
+        "broad_phase": (newt + n_ls) * n_cv * 24 + n_ls * n_cv * 24 + (tot["pair_evals"] + tot["swept_pairs"]) * 36,
     }
+    # per Newton iteration: g read, r, p, z and d_{-1} written, the 6-entry inverse read
+    out["pcg_init"] = newt * rows * (24 + 48 + 2 * vb + 6 * hs)
+    # per Newton iteration: p read per row (x and the target on attached rows, left out)
+    out["newton_check"] = newt * rows * 24
+    # per step: x and v read, the predicted position written
+    out["predict"] = tot["env_steps"] * rows * 72
+    # per search: each contact vertex's row (gel) or body state and rest point read, its position written
+    out["cv_pos"] = (newt + n_ls) * n_cv * 48
+    out["pcg_iter"] = out["pcg_matvec"] + out["pair_matvec"] + out["pcg_update"]
     return out
 
 
@@ -311,7 +338,8 @@ def time_steps(genv, dev_tg, k0, steps, stream):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     tot = {"pcg_iters": 0, "newton_env_iters": 0, "ls_trials": 0, "newton_max": 0, "max_pairs": 0,
            "al_env_updates": 0, "ccd_limited": 0, "alpha_sum": 0.0, "accd_iters": 0, "accd_iters_max": 0,
-           "pair_evals": 0, "swept_pairs": 0, "env_steps": 0, "graph_loop_iters": 0, "graph_pcg_launches": 0}
+           "pair_evals": 0, "swept_pairs": 0, "act_pair_iters": 0, "env_steps": 0, "graph_loop_iters": 0,
+           "graph_pcg_launches": 0}
     statuses = []
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -323,7 +351,7 @@ def time_steps(genv, dev_tg, k0, steps, stream):
         ev[i][1].record(stream)
         statuses.append(st)
         for key in ("pcg_iters", "newton_env_iters", "ls_trials", "al_env_updates", "ccd_limited", "alpha_sum",
-                    "accd_iters", "pair_evals", "swept_pairs"):
+                    "accd_iters", "pair_evals", "swept_pairs", "act_pair_iters"):
             tot[key] += s[key]
         tot["newton_max"] = max(tot["newton_max"], s["newton_iters"])
         tot["max_pairs"] = max(tot["max_pairs"], s["max_pairs"])
@@ -350,7 +378,7 @@ def time_rollout(genv, dev_tg, k0, steps, stream):
     st, taken, s = genv.rollout_results()
     torch.cuda.synchronize()
     tot = {k: s[k] for k in ("pcg_iters", "newton_env_iters", "ls_trials", "al_env_updates", "ccd_limited",
-                             "alpha_sum", "accd_iters", "pair_evals", "swept_pairs")}
+                             "alpha_sum", "accd_iters", "pair_evals", "swept_pairs", "act_pair_iters")}
     tot.update({"newton_max": s["newton_iters"], "max_pairs": s["max_pairs"], "accd_iters_max": s["accd_iters_max"],
                 "env_steps": int(np.sum(taken)), "graph_loop_iters": s["loop_iters"],
                 "graph_pcg_launches": s["pcg_launches"]})
@@ -450,6 +478,24 @@ def matvec_traffic_per_launch(env_iters_per_launch):
     return MATVEC_TRAFFIC["bytes"] / MATVEC_TRAFFIC["env_iters"] * env_iters_per_launch
 
 
+# The same for the fused PCG iteration kernel (k_pcg_iter: contact terms,
+# SELL mat-vec and update in one launch): DRAM bytes of its first launch
+# in the 24-env case (every env in its first PCG iteration), scaled by
+# env-iterations.
+PCG_ITER_TRAFFIC = {"env_iters": 24, "bytes": None, "source_sha256": None}
+PCG_ITER_PARTS = [("pcgvec.cuh", None), ("fpconv.cuh", None),
+                  ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_rows("),
+                  ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_pairs("),
+                  ("kernels_pcg.cu", "__device__ __forceinline__ void update_rows("),
+                  ("kernels_pcg.cu", "k_pcg_iter(Dev d")]
+
+
+def pcg_iter_traffic_per_launch(env_iters_per_launch):
+    if PCG_ITER_TRAFFIC["bytes"] is None or _kernel_source_hash(PCG_ITER_PARTS) != PCG_ITER_TRAFFIC["source_sha256"]:
+        return None
+    return PCG_ITER_TRAFFIC["bytes"] / PCG_ITER_TRAFFIC["env_iters"] * env_iters_per_launch
+
+
 # FP64 floating-point operations per unit of work of the FP64-heavy kernel
 # classes in the mixed mode (dadd + dmul + 2 dfma thread instructions of one
 # launch under ncu, divided by the units that launch processed: the first
@@ -511,7 +557,11 @@ def roofline_of(genv, prof, tot):
     rk = dom if dom in kb else "pcg_matvec"
     n, ms = prof[rk]
     achieved = kb[rk] / (ms / 1e3) / 1e9
-    traffic = matvec_traffic_per_launch(tot["pcg_iters"] / max(n, 1)) if rk == "pcg_matvec" else None
+    traffic = None
+    if rk == "pcg_matvec":
+        traffic = matvec_traffic_per_launch(tot["pcg_iters"] / max(n, 1))
+    elif rk == "pcg_iter":
+        traffic = pcg_iter_traffic_per_launch(tot["pcg_iters"] / max(n, 1))
     roof = {"kernel": rk, "dominant_kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
             "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_kind,
             "bytes_per_launch": kb[rk] / max(n, 1), "env_iters_per_launch": tot["pcg_iters"] / max(n, 1),
@@ -613,7 +663,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build()
-    scene, params, deltas = build_workload(args.envs, 0, args.pcg_window)
+    scene, params, deltas = build_workload(args.envs, 0, args.pcg_window, args.pcg_fused)
     n_total = args.warmup + args.steps
     dev = f"cuda:{local}"
 
@@ -648,7 +698,8 @@ def run_ours(args):
         genv.profile_enable(False)
         tot_p = {"pcg_iters": s_p["pcg_iters"], "newton_env_iters": s_p["newton_env_iters"],
                  "ls_trials": s_p["ls_trials"], "pair_evals": s_p["pair_evals"], "swept_pairs": s_p["swept_pairs"],
-                 "accd_iters": s_p["accd_iters"], "env_steps": int(np.sum(taken_p))}
+                 "accd_iters": s_p["accd_iters"], "act_pair_iters": s_p["act_pair_iters"],
+                 "env_steps": int(np.sum(taken_p))}
         roof, kernels = roofline_of(genv, prof, tot_p)
         try:
             fma = ipc.fma_peaks(dev)

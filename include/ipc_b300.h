@@ -110,6 +110,12 @@ typedef struct {
                              every solve of a Newton iteration ends before
                              the next Newton iteration (not in the paper: a
                              scheduling property of this library)          */
+  int pcg_fused;          /* 1 (default): a PCG iteration is one persistent
+                             kernel (contact terms, SELL mat-vec and update;
+                             an env's update starts when its own products
+                             are in); 0: three kernels (the mat-vecs, then
+                             the update).  Runs with friction use the three
+                             kernels.  The same arithmetic either way.     */
 } ipc_params;
 
 /* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
@@ -165,6 +171,9 @@ typedef struct {
   long long pcg_launches;     /* PCG iterations the graph ran (each serves
                                  every env in PCG at the time); 0 for
                                  host-driven calls                         */
+  long long act_pair_iters;   /* active contact pairs x PCG iterations,
+                                 summed over the solves and envs (the work
+                                 of the contact mat-vec)                   */
 } ipc_step_stats;
 
 void ipc_default_params(ipc_params* prm);

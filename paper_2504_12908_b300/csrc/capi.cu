@@ -30,12 +30,13 @@ size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 enum Kc {
   KC_PREDICT, KC_CVPOS, KC_OBJBOX, KC_BROAD, KC_BARRIER, KC_TET, KC_BODY, KC_ASSEMBLE, KC_GRAD, KC_PRECOND,
   KC_PCGINIT, KC_PAIRSPMV, KC_FRICSPMV, KC_SPMV, KC_PCGUPD, KC_NEWTON, KC_ACCD, KC_ENERGY, KC_LS, KC_MISC,
-  KC_COUNT
+  KC_PCGITER, KC_COUNT
 };
 const char* KC_NAME[KC_COUNT] = {"predict",      "cv_pos",      "obj_box",     "broad_phase", "barrier",
                                  "tet_elastic",  "body_abd",    "assemble",    "gradient",    "precond",
                                  "pcg_init",     "pair_matvec", "fric_matvec", "pcg_matvec",  "pcg_update",
-                                 "newton_check", "accd",        "ls_energy",   "ls_update",   "misc"};
+                                 "newton_check", "accd",        "ls_energy",   "ls_update",   "misc",
+                                 "pcg_iter"};
 
 cudaEvent_t take_ev(ipc_ctx* ctx) {
   if (!ctx->ev_free.empty()) {
@@ -150,7 +151,9 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.fr_mu = prm.friction_mu;
   d.fr_eh = prm.friction_eps_v * prm.dt;
   d.spmv_unroll = 0;
+  d.pcg_fused = prm.pcg_fused;
   d.pcg_grid = 148;
+  d.pcg_grid_fused = 148;
   d.asm_block = 128;
   d.pairs_grid = 148 * 8;
   d.newton_max = prm.newton_max;
@@ -449,6 +452,11 @@ int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0
                   unsigned window = 0xffffffffu) {
   const Dev& d = ctx->dev;
   long long l0 = ctx->launches;
+  if (d.pcg_fused && !(d.fr_mu > 0.0)) {
+    // the whole iteration as one persistent kernel
+    KL(ctx, KC_PCGITER, [&] { return launch_pcg_iter(d, s, h, use_cond, window); }, s);
+    return (int)(ctx->launches - l0);
+  }
   // contact terms (side stream) beside the SELL mat-vec: both only read
   // z_k and d_{k-1}
   fork_side(ctx, s, 1);
@@ -896,6 +904,7 @@ void ipc_default_params(ipc_params* p) {
   p->friction_eps_v = 1e-3;
   p->newton_abs_after = 1000000;
   p->rollout_pcg_window = 0;
+  p->pcg_fused = 1;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
@@ -917,7 +926,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   if (!prm || !out || !dev_workspace) return IPC_EINVAL;
   if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
       prm->newton_abs_after < 0 || prm->rollout_pcg_window < 0 || prm->rollout_pcg_window == 1 ||
-      (prm->rollout_pcg_window & 1) ||
+      (prm->rollout_pcg_window & 1) || prm->pcg_fused < 0 || prm->pcg_fused > 1 ||
       prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
     return IPC_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
@@ -969,6 +978,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   // persistent PCG grid: every resident CTA of the two PCG kernels
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
+  ctx->dev.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
   CK(cudaMemsetAsync(ctx->dev.check_word, 0, 2 * sizeof(unsigned long long), ctx->stream));
   ctx->dev.pairs_grid = ctx->n_sm * 8;
@@ -1064,6 +1074,7 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   for (int k = 0; k < 3; ++k)
     if (t.grid_us[k] < best && t.grid_us[k] < 0.95f * t.grid_us[1]) { best = t.grid_us[k]; best_c = cand[k]; }
   d.pcg_grid = ctx->n_sm * best_c;
+  d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll);
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
   // gather assembly: 64, 128 or 256 threads per CTA, every env counted as
@@ -1396,6 +1407,7 @@ ipc_status ipc_step_results(ipc_ctx* ctx, int32_t* per_env_status, ipc_step_stat
     S.accd_iters += ei[I_ACCDIT];
     S.accd_iters_max = std::max(S.accd_iters_max, ei[I_ACCDMAX]);
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_ASUM];
+    S.act_pair_iters += (long long)ctx->h_dbl[sel[i] * NUM_SCALARS + S_APCG];
     S.pair_evals += ei[I_PAIRTOT];
     S.swept_pairs += ei[I_SWEPTTOT];
   }
@@ -1508,6 +1520,7 @@ ipc_status ipc_rollout_results(ipc_ctx* ctx, int32_t* per_env_status, int32_t* p
     S.accd_iters += ei[I_RACCDIT];
     S.accd_iters_max = std::max(S.accd_iters_max, ei[I_RACCDMAX]);
     S.alpha_sum += ctx->h_dbl[sel[i] * NUM_SCALARS + S_RASUM];
+    S.act_pair_iters += (long long)ctx->h_dbl[sel[i] * NUM_SCALARS + S_RAPCG];
     S.pair_evals += ei[I_RPAIR];
     S.swept_pairs += ei[I_RSWEPT];
   }

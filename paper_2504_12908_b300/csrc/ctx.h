@@ -31,6 +31,8 @@ enum EnvScalar {
   S_ASUM,       // accepted line-search steps this step, summed
   S_DQC,        // PCG d.q, contact part (pair and friction terms, summed by atomics)
   S_RASUM,      // rollout: S_ASUM summed over the env's steps
+  S_APCG,       // active contact pairs x PCG iterations, summed over this step's solves
+  S_RAPCG,      // rollout: S_APCG summed over the env's steps
   NUM_SCALARS
 };
 
@@ -62,6 +64,7 @@ enum EnvInt {
   I_SWEPTTOT,     // swept candidate pairs of this step's line searches
   I_NEWT,         // starts a Newton iteration now (in the step, no solve carried over, no decision pending)
   I_DEC,          // its PCG solve ended: the Newton decision is pending
+  I_PHASE,        // fused PCG iteration: the env's pair and mat-vec items finished
   // rollout (ipc_rollout: each env runs its own sequence of steps)
   I_RSTEP,        // steps completed in this rollout
   I_BEGIN,        // begins its next step at the top of the next loop iteration
@@ -148,8 +151,11 @@ struct Dev {
   int2* pcg_item;               // per row item: (env, global row CTA)
   int2* pcg_pitem;              // per pair item: (env, group of 8 active pairs)
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
-                                // [2] envs in the list, [3] the list is stale
+                                // [2] envs in the list, [3] items of stopped envs, [4] envs
+                                // solving, [5] next item of the fused kernel, [6] a wait gave up
   int pcg_grid;                 // CTAs of the persistent PCG row kernels
+  int pcg_fused;                // 1: a PCG iteration is one kernel (k_pcg_iter) when friction is off
+  int pcg_grid_fused;           // CTAs of k_pcg_iter (its resident CTAs)
   int asm_block;                // threads per CTA of the gather assembly (ipc_autotune)
   int pairs_grid;               // CTAs of the candidate-pair search (ipc_autotune)
   int pcg_grid_pairs;           // CTAs of the persistent contact mat-vec

@@ -30,7 +30,7 @@ namespace ipc {
 
 namespace {
 
-enum PcgCtl { C_ARRIVED = 0, C_ITER, C_LEN, C_DEAD, C_LIVE, C_COUNT };
+enum PcgCtl { C_ARRIVED = 0, C_ITER, C_LEN, C_DEAD, C_LIVE, C_NEXT, C_ABORT, C_COUNT };
 
 // component c of a 3-vector of either precision
 template <class T>
@@ -374,6 +374,8 @@ __global__ void k_pcg_begin(Dev d, cudaGraphConditionalHandle h, int use_cond) {
   if (threadIdx.x == 0) {
     d.pcg_ctl[C_ARRIVED] = 0;
     d.pcg_ctl[C_ITER] = 0;
+    d.pcg_ctl[C_NEXT] = 0;
+    d.pcg_ctl[C_ABORT] = 0;
   }
   build_list(d);
   if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, d.pcg_ctl[C_LIVE] > 0 ? 1u : 0u);
@@ -421,86 +423,87 @@ __global__ void __launch_bounds__(128) k_pcg_pairs(Dev d) {
   }
 }
 
+// ---- update item: 128 rows of env e.  alpha = r.z / (d.q + its contact
+// part), p += alpha d_k, r -= alpha q, z = P^-1 r, r.z and r.r of the env
+// (its last CTA: beta, the stop test).  q, d_k, the contact accumulator
+// and the env's d.q are read through L2: in the fused iteration kernel
+// they were written by other CTAs of the same launch.
 template <class HT>
-__global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalHandle h, int use_cond,
-                                                     unsigned window) {
-  const int n_list = (int)d.pcg_ctl[C_LEN];
-  const int n_items = d.pcg_row_off[n_list];
-  const int nb = pcg_new_buf(d);
-  __shared__ double s_dq, s_al;
-  __shared__ int s_e, s_cta;
-  __shared__ uint8_t s_tag;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    __syncthreads();  // the previous item is done with the shared item data
-    if (threadIdx.x == 0) {
-      int2 iv = d.pcg_item[item];                      // (env, row CTA)
-      const bool in = IPC_CHECK(d.check_word, (unsigned)iv.x < (unsigned)d.n_envs &&
-                                (unsigned)iv.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
-      if (!in) iv = make_int2(0, 0);
-      const int e = iv.x;
-      s_e = in && ENVI(d, e, I_PCG) ? e : -1;          // stopped envs stay listed until a rebuild
-      s_cta = iv.y;
-      const double dq = ENVS(d, e, S_DQ) + ENVS(d, e, S_DQC);
-      s_dq = dq;
-      s_al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;    // alpha, once per item
-      s_tag = touch_tag(d, e);
-    }
-    __syncthreads();
-    const int e = s_e;
-    if (e < 0) continue;
-    const int cta = s_cta;
-    const int r = cta * 128 + threadIdx.x;
-    const double dq = s_dq;
-    const double al = s_al;
-    const uint8_t kr = d.row_kind[r];
-    // contact part of q on the rows this iteration's contact terms write
-    D3 qcv{0, 0, 0};
-    const bool touched = d.row_touch[r] == s_tag;
-    if (touched) {
-      qcv = ld3(d.qc, r);
-      st3(d.qc, r, D3{0, 0, 0});
-    }
-    double out[2];
-    bool last;
-    if constexpr (sizeof(HT) == 4) {
-      const float4 dd = PV<float>::dbuf(d, nb)[r], qq = d.q4[r];
-      st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
-      const D3 rv = ld3(d.r, r) - al * (touched ? widen_row(qq) + qcv : widen_row(qq));
-      st3(d.r, r, rv);
-      __syncwarp();
-      const double rr = dot(rv, rv);
-      const float3 rf = round_row(rv);
-      const float4 z = apply_pc32(d, r, kr, rf);
-      d.z4[r] = z;
-      last = env_reduce<2, float>(d, e, 0, cta, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
-    } else {
-      st3(d.p, r, ld3(d.p, r) + al * PV<double>::dir(d, r, nb));
-      const D3 rv = ld3(d.r, r) - al * (touched ? PV<double>::q(d, r) + qcv : PV<double>::q(d, r));
-      st3(d.r, r, rv);
-      __syncwarp();
-      const double rr = dot(rv, rv);
-      const D3 z = apply_pc64(d, r, kr, rv);
-      PV<double>::set_z(d, r, z);
-      last = env_reduce<2>(d, e, 0, cta, dot(rv, z), &rr, out);
-    }
-    if (last) {
-      const double rz_old = ENVS(d, e, S_RZ);
-      ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
-      ENVS(d, e, S_RZ) = out[0];
-      ENVS(d, e, S_RR) = out[1];
-      ENVS(d, e, S_DQC) = 0.0;
-      const int it = ++ENVI(d, e, I_PCGIT);
-      ENVI(d, e, I_PCGTOT) += 1;
-      const double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
-      if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) {
-        ENVI(d, e, I_PCG) = 0;
-        ENVI(d, e, I_DEC) = 1;
-        atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
-        atomicSub(d.pcg_ctl + C_LIVE, 1u);
-      }
+__device__ __forceinline__ void update_rows(const Dev& d, int e, int cta, double dq, double al, uint8_t tag,
+                                            int nb) {
+  const int r = cta * 128 + threadIdx.x;
+  const uint8_t kr = d.row_kind[r];
+  // contact part of q on the rows this iteration's contact terms write
+  D3 qcv{0, 0, 0};
+  const bool touched = d.row_touch[r] == tag;
+  if (touched) {
+    qcv = D3{__ldcg(d.qc + 3 * r), __ldcg(d.qc + 3 * r + 1), __ldcg(d.qc + 3 * r + 2)};
+    st3(d.qc, r, D3{0, 0, 0});
+  }
+  double out[2];
+  bool last;
+  if constexpr (sizeof(HT) == 4) {
+    const float4 dd = __ldcg(PV<float>::dbuf(d, nb) + r), qq = __ldcg(d.q4 + r);
+    st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
+    const D3 rv = ld3(d.r, r) - al * (touched ? widen_row(qq) + qcv : widen_row(qq));
+    st3(d.r, r, rv);
+    __syncwarp();
+    const double rr = dot(rv, rv);
+    const float3 rf = round_row(rv);
+    const float4 z = apply_pc32(d, r, kr, rf);
+    d.z4[r] = z;
+    last = env_reduce<2, float>(d, e, 0, cta, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
+  } else {
+    const double* db = PV<double>::dbuf(d, nb) + 3 * r;
+    const double* qv = d.q + 3 * r;
+    const D3 dd{__ldcg(db), __ldcg(db + 1), __ldcg(db + 2)}, qq{__ldcg(qv), __ldcg(qv + 1), __ldcg(qv + 2)};
+    st3(d.p, r, ld3(d.p, r) + al * dd);
+    const D3 rv = ld3(d.r, r) - al * (touched ? qq + qcv : qq);
+    st3(d.r, r, rv);
+    __syncwarp();
+    const double rr = dot(rv, rv);
+    const D3 z = apply_pc64(d, r, kr, rv);
+    PV<double>::set_z(d, r, z);
+    last = env_reduce<2>(d, e, 0, cta, dot(rv, z), &rr, out);
+  }
+  if (last) {
+    const double rz_old = ENVS(d, e, S_RZ);
+    ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
+    ENVS(d, e, S_RZ) = out[0];
+    ENVS(d, e, S_RR) = out[1];
+    ENVS(d, e, S_DQC) = 0.0;
+    ENVI(d, e, I_PHASE) = 0;
+    const int it = ++ENVI(d, e, I_PCGIT);
+    ENVI(d, e, I_PCGTOT) += 1;
+    const double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
+    if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) {
+      ENVI(d, e, I_PCG) = 0;
+      ENVI(d, e, I_DEC) = 1;
+      atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
+      atomicSub(d.pcg_ctl + C_LIVE, 1u);
     }
   }
-  // the grid's last CTA: next iteration, list upkeep, loop condition
+}
+
+// thread 0: the update item's env (-1: skip), row CTA, d.q, alpha and row tag
+__device__ __forceinline__ void update_item_info(const Dev& d, int item, int* s_e, int* s_cta, double* s_dq,
+                                                 double* s_al, uint8_t* s_tag) {
+  int2 iv = d.pcg_item[item];                        // (env, row CTA)
+  const bool in = IPC_CHECK(d.check_word, (unsigned)iv.x < (unsigned)d.n_envs &&
+                            (unsigned)iv.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
+  if (!in) iv = make_int2(0, 0);
+  const int e = iv.x;
+  *s_e = in && ENVI(d, e, I_PCG) ? e : -1;           // stopped envs stay listed until a rebuild
+  *s_cta = iv.y;
+  const double dq = __ldcg(&ENVS(d, e, S_DQ)) + __ldcg(&ENVS(d, e, S_DQC));
+  *s_dq = dq;
+  *s_al = dq > 0.0 ? ENVS(d, e, S_RZ) / dq : 0.0;    // alpha, once per item
+  *s_tag = touch_tag(d, e);
+}
+
+// the grid's last CTA after an iteration: next iteration, list upkeep,
+// loop condition.  Every CTA of the grid calls it once, after its items.
+__device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
   __shared__ bool s_last;
   __shared__ bool s_rebuild;
   __syncthreads();
@@ -514,6 +517,7 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
   __threadfence();
   if (threadIdx.x == 0) {
     d.pcg_ctl[C_ARRIVED] = 0;
+    d.pcg_ctl[C_NEXT] = 0;
     d.pcg_ctl[C_ITER] += 1;
     d.step_ctl[4] += 1u;
     const unsigned len = d.pcg_ctl[C_LEN];
@@ -522,7 +526,31 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
     s_rebuild = dead > 0 && 4u * dead >= items;
   }
   __syncthreads();
-  if (s_rebuild) build_list(d);
+  if (d.pcg_ctl[C_ABORT]) {
+    // a wait of the fused kernel gave up (never expected): the envs still
+    // solving end their step with IPC_ECUDA, their reductions reset
+    const int n_list = (int)d.pcg_ctl[C_LEN];
+    for (int i = threadIdx.x; i < n_list; i += blockDim.x) {
+      const int e = d.pcg_list[i];
+      if (!ENVI(d, e, I_PCG)) continue;
+      ENVI(d, e, I_PCG) = 0;
+      ENVI(d, e, I_ACTIVE) = 0;
+      ENVI(d, e, I_STATUS) = IPC_ECUDA;
+      ENVI(d, e, I_PHASE) = 0;
+      d.env_cnt[2 * e] = 0;
+      d.env_cnt[2 * e + 1] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      d.pcg_ctl[C_ABORT] = 0;
+      d.pcg_ctl[C_LIVE] = 0;
+      d.pcg_ctl[C_DEAD] = 0;
+      d.pcg_ctl[C_LEN] = 0;
+    }
+    __syncthreads();
+  } else if (s_rebuild) {
+    build_list(d);
+  }
   if (threadIdx.x == 0 && use_cond) {
     // window: iterations of this solve loop (solves still running carry
     // over to the next one; the direction buffers alternate by iteration,
@@ -532,6 +560,125 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
                       d.pcg_ctl[C_ITER] < window;
     cudaGraphSetConditional(h, more ? 1u : 0u);
   }
+}
+
+template <class HT>
+__global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalHandle h, int use_cond,
+                                                     unsigned window) {
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_items = d.pcg_row_off[n_list];
+  const int nb = pcg_new_buf(d);
+  __shared__ double s_dq, s_al;
+  __shared__ int s_e, s_cta;
+  __shared__ uint8_t s_tag;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __syncthreads();  // the previous item is done with the shared item data
+    if (threadIdx.x == 0) update_item_info(d, item, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
+    __syncthreads();
+    if (s_e < 0) continue;
+    update_rows<HT>(d, s_e, s_cta, s_dq, s_al, s_tag, nb);
+  }
+  pcg_iteration_end(d, h, use_cond, window);
+}
+
+// ---- the fused PCG iteration: contact terms, SELL mat-vec and update of
+// every listed env in one persistent launch.  CTAs take items in order
+// from a device counter (C_NEXT): the pair groups, then the mat-vec row
+// items, then the update row items, each env after env.  An update item
+// of env e waits until every pair and mat-vec item of e has finished
+// (I_PHASE counts them, each after a fence): those items were taken before
+// it by CTAs that are running and wait on nothing, so the wait ends, and
+// envs pipeline (early envs update while later ones multiply).  The wait
+// is bounded all the same: after kWaitCycles (about a second) the CTA
+// raises C_ABORT, the other waits give up at once, and the envs still
+// solving end with IPC_ECUDA.
+constexpr long long kWaitCycles = 2000000000ll;
+
+__device__ __forceinline__ void phase_signal(const Dev& d, int e) {
+  __threadfence();   // every thread: its stores and atomics of the item before the count
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(&ENVI(d, e, I_PHASE), 1);
+}
+
+// thread 0: waits until env e's pair and mat-vec items are done; false on abort
+__device__ __forceinline__ bool phase_wait(const Dev& d, int e) {
+  const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+  volatile int* ph = &ENVI(d, e, I_PHASE);
+  volatile unsigned* ab = d.pcg_ctl + C_ABORT;
+  if (*ph >= need) {
+    __threadfence();
+    return true;
+  }
+  const long long t0 = clock64();
+  while (*ph < need) {
+    if (*ab) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(d.pcg_ctl + C_ABORT, 1u);
+      return false;
+    }
+    __nanosleep(200);
+  }
+  __threadfence();
+  return true;
+}
+
+template <class HT, int U>
+__global__ void __launch_bounds__(128, 12) k_pcg_iter(Dev d, cudaGraphConditionalHandle h, int use_cond,
+                                                   unsigned window) {
+  __shared__ int s_item, s_e, s_cta;
+  __shared__ double s_beta, s_dq, s_al;
+  __shared__ uint8_t s_tag;
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_rows = d.pcg_row_off[n_list];
+  const int n_pairs = d.pcg_pair_off[n_list];
+  const int n_total = n_pairs + 2 * n_rows;
+  const int nb = pcg_new_buf(d), ob = nb ^ 1;
+  for (;;) {
+    __syncthreads();  // the previous item is done with the shared item data
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(d.pcg_ctl + C_NEXT, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_total) break;
+    if (item < n_pairs) {
+      const int2 it = d.pcg_pitem[item];               // (env, group of 8 active pairs)
+      if (!IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs, CHK_PCG_ITEM, item)) continue;
+      if (!ENVI(d, it.x, I_PCG)) continue;
+      matvec_pairs<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
+      phase_signal(d, it.x);
+    } else if (item < n_pairs + n_rows) {
+      if (threadIdx.x == 0) {
+        const int2 it = d.pcg_item[item - n_pairs];    // (env, row CTA)
+        const bool in = IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs &&
+                                  (unsigned)it.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
+        s_e = in && ENVI(d, it.x, I_PCG) ? it.x : -1;
+        s_cta = it.y;
+        s_beta = ENVS(d, it.x, S_PBETA);
+      }
+      __syncthreads();
+      const int e = s_e;
+      if (e < 0) continue;
+      matvec_rows<HT, U>(d, e, s_cta, (HT)s_beta, ob, nb);
+      phase_signal(d, e);
+    } else {
+      if (threadIdx.x == 0) {
+        update_item_info(d, item - n_pairs - n_rows, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
+        if (s_e >= 0) {
+          if (phase_wait(d, s_e)) {
+            // d.q and alpha again, now that the env's terms are all in
+            const double dq = __ldcg(&ENVS(d, s_e, S_DQ)) + __ldcg(&ENVS(d, s_e, S_DQC));
+            s_dq = dq;
+            s_al = dq > 0.0 ? ENVS(d, s_e, S_RZ) / dq : 0.0;
+          } else {
+            s_e = -1;
+          }
+        }
+      }
+      __syncthreads();
+      if (s_e < 0) continue;
+      update_rows<HT>(d, s_e, s_cta, s_dq, s_al, s_tag, nb);
+    }
+  }
+  pcg_iteration_end(d, h, use_cond, window);
 }
 
 // diagnostics: the direction v (FP64 rows staged in Dev::z) as z with
@@ -612,6 +759,37 @@ int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
 }
 
 // resident CTAs per SM of the persistent PCG kernels (the smaller of the two)
+int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
+  const int u = d.spmv_unroll ? d.spmv_unroll : 2;
+  const int g = d.pcg_grid_fused;
+  if (d.prec) {
+    if (u == 2) k_pcg_iter<float, 2><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else if (u == 8) k_pcg_iter<float, 8><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else k_pcg_iter<float, 4><<<g, 128, 0, s>>>(d, h, use_cond, window);
+  } else {
+    if (u == 4) k_pcg_iter<double, 4><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else if (u == 8) k_pcg_iter<double, 8><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else k_pcg_iter<double, 2><<<g, 128, 0, s>>>(d, h, use_cond, window);
+  }
+  return 1;
+}
+
+// resident CTAs per SM of the fused iteration kernel
+int pcg_iter_ctas_per_sm(int prec, int unroll) {
+  int a = 0;
+  const int u = unroll ? unroll : 2;
+  if (prec) {
+    if (u == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 2>, 128, 0);
+    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 8>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 4>, 128, 0);
+  } else {
+    if (u == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 4>, 128, 0);
+    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 8>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 2>, 128, 0);
+  }
+  return a > 0 ? a : 1;
+}
+
 int pcg_ctas_per_sm(int prec, int unroll) {
   int a = 0, b = 0;
   const int u = unroll ? unroll : 2;

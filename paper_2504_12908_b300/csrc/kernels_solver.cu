@@ -468,6 +468,8 @@ __global__ void k_newton_decide(Dev d) {
   if (e >= d.n_envs || !ENVI(d, e, I_DEC) || !ENVI(d, e, I_ACTIVE)) return;
   ENVI(d, e, I_LS) = 0;
   ENVI(d, e, I_PAIRTOT) += min(ENVI(d, e, I_NPAIRS), d.env_pair_cap[e]);  // this iteration's static list
+  // the solve's contact mat-vec work: its active pairs are fixed over the solve
+  ENVS(d, e, S_APCG) += (double)ENVI(d, e, I_PCGIT) * min(ENVI(d, e, I_NACT), d.env_pair_cap[e]);
   double res = ENVS(d, e, S_PNORM) / d.h;
   if (res <= d.newton_tol) {
     if (!has_driven[e] || ENVS(d, e, S_CRES) / d.h <= d.newton_tol) {
@@ -683,6 +685,7 @@ __global__ void k_env_reset(Dev d, int what) {
     ENVI(d, e, I_PAIRTOT) = 0;
     ENVI(d, e, I_SWEPTTOT) = 0;
     ENVS(d, e, S_ASUM) = 0.0;
+    ENVS(d, e, S_APCG) = 0.0;
   } else if (what == 1) {
     // an env starts a Newton iteration unless its solve carries over; the
     // decision of its previous iteration is done
@@ -735,6 +738,7 @@ __device__ __forceinline__ void begin_step_counters(const Dev& d, int e) {
   ENVI(d, e, I_PAIRTOT) = 0;
   ENVI(d, e, I_SWEPTTOT) = 0;
   ENVS(d, e, S_ASUM) = 0.0;
+  ENVS(d, e, S_APCG) = 0.0;
 }
 
 // the table address, steps and loop cap of the next rollout (1 thread)
@@ -759,6 +763,7 @@ __global__ void k_roll_init(Dev d) {
   if (sel) ENVI(d, e, I_STATUS) = IPC_OK;
   for (int k = I_RNEWTON; k <= I_RPAIRSMAX; ++k) ENVI(d, e, k) = 0;
   ENVS(d, e, S_RASUM) = 0.0;
+  ENVS(d, e, S_RAPCG) = 0.0;
 }
 
 // envs that begin a step: their targets for step I_RSTEP from the table
@@ -814,6 +819,7 @@ __global__ void k_roll_advance(Dev d) {
     ENVI(d, e, I_RSWEPT) += ENVI(d, e, I_SWEPTTOT);
     ENVI(d, e, I_RPAIRSMAX) = max(ENVI(d, e, I_RPAIRSMAX), ENVI(d, e, I_NPAIRS));
     ENVS(d, e, S_RASUM) += ENVS(d, e, S_ASUM);
+    ENVS(d, e, S_RAPCG) += ENVS(d, e, S_APCG);
     const int k = ++ENVI(d, e, I_RSTEP);
     ENVI(d, e, I_RUN) = 0;
     ENVI(d, e, I_ENDNOW) = 0;

@@ -33,7 +33,7 @@ class ipc_params(C.Structure):
                 ("al_kappa", C.c_double), ("al_max", C.c_int), ("ee_mollifier", C.c_double),
                 ("precision", C.c_int), ("max_pairs_per_env", C.c_int), ("friction_mu", C.c_double),
                 ("friction_eps_v", C.c_double), ("newton_abs_after", C.c_int),
-                ("rollout_pcg_window", C.c_int)]
+                ("rollout_pcg_window", C.c_int), ("pcg_fused", C.c_int)]
 
 
 class ipc_scene_desc(C.Structure):
@@ -62,7 +62,8 @@ class ipc_step_stats(C.Structure):
                 ("al_env_updates", C.c_longlong), ("ccd_limited", C.c_longlong), ("alpha_sum", C.c_double),
                 ("accd_iters", C.c_longlong), ("accd_iters_max", C.c_int),
                 ("ms_total", C.c_double), ("pair_evals", C.c_longlong), ("swept_pairs", C.c_longlong),
-                ("loop_iters", C.c_longlong), ("pcg_launches", C.c_longlong)]
+                ("loop_iters", C.c_longlong), ("pcg_launches", C.c_longlong),
+                ("act_pair_iters", C.c_longlong)]
 
 
 _lib = None
@@ -171,6 +172,7 @@ def params_from(p) -> ipc_params:
     out.friction_eps_v = float(getattr(p, "friction_eps_v", 1e-3))
     out.newton_abs_after = int(getattr(p, "newton_abs_after", 1000000))
     out.rollout_pcg_window = int(getattr(p, "rollout_pcg_window", 0))
+    out.pcg_fused = int(getattr(p, "pcg_fused", 1))
     return out
 
 

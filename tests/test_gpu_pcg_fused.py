@@ -1,0 +1,125 @@
+"""The fused PCG iteration kernel (ipc_params.pcg_fused = 1, the default):
+contact terms, SELL mat-vec and update of every env in one persistent
+launch, an env's update waiting for its own products.  It computes what the
+three-kernel iteration (pcg_fused = 0) computes (Sec. 3.3's block-Jacobi
+PCG, one iteration after another), so the tests hold the two to each other:
+the same statuses, the same PCG work within a few iterations, and end
+states within the multi-step bar of their precision (1e-6 of the bbox
+diagonal per step in FP64 at the parity tolerances; the contact sums use
+atomics, so the two orders differ in the last bits every iteration).  The
+fused path against the oracle is covered by every other GPU test, which
+runs the default."""
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_12908_b300 import ipc  # noqa: E402
+from paper_2504_12908_b300.build import build  # noqa: E402
+
+build()
+
+K = 4
+
+
+def _batch():
+    # uneven envs pressing into contact within the K steps: several row
+    # items and pair groups per env, envs leaving PCG at different iterations
+    return [scenes.config2(e, n_steps=12) for e in (0, 1, 2, 5)]
+
+
+def _table(g, scs, k0, n):
+    mb = max(g.max_bodies, 1)
+    t = np.zeros((n, len(scs), mb, 12))
+    for k in range(n):
+        for e, sc in enumerate(scs):
+            y = g.rest_y(e)
+            y[:, :3] += np.asarray(sc.delta(k0 + k)).reshape(-1, 3)[: y.shape[0]]
+            t[k, e, : y.shape[0]] = y
+    return t
+
+
+def _run(prm, fused, rollout, stream=True):
+    scs = _batch()
+    p = type(prm)(**prm.__dict__)
+    p.pcg_fused = fused
+    g = ipc.Envs([sc.scene for sc in scs], p, stream=torch.cuda.Stream() if stream else None)
+    tab = _table(g, scs, 0, K)
+    pcg = 0
+    if rollout:
+        st, steps, s = g.rollout(K, torch.as_tensor(tab, device="cuda"))
+        assert np.all(steps == K)
+        pcg = s["pcg_iters"]
+    else:
+        st = np.zeros(len(scs), np.int32)
+        for k in range(K):
+            g.set_targets_all(tab[k])
+            s_k, s = g.step()
+            st = np.where(st == 0, s_k, st)
+            pcg += s["pcg_iters"]
+    out = [g.get_state(e) for e in range(len(scs))]
+    g.close()
+    return np.asarray(st), out, pcg
+
+
+def _close(sa, sb, bound):
+    worst = 0.0
+    for a, b in zip(sa, sb):
+        diag = float(np.linalg.norm(a[0].max(0) - a[0].min(0)))
+        worst = max(worst, np.abs(a[0] - b[0]).max() / diag, np.abs(a[2][:, :3] - b[2][:, :3]).max() / diag)
+    assert worst <= bound * K, worst
+
+
+@pytest.mark.parametrize("rollout,stream", [(False, True), (True, True), (False, False)])
+def test_fused_matches_three_kernels_fp64(rollout, stream):
+    """FP64 at the parity tolerances: lock-step graphs, the rollout graph,
+    and host-driven steps (no stream: plain launches)."""
+    prm = scenes.SolverParams().parity()
+    st_a, xa, pa = _run(prm, 1, rollout, stream)
+    st_b, xb, pb = _run(prm, 0, rollout, stream)
+    assert np.all(st_a == 0) and np.all(st_b == 0)
+    assert abs(pa - pb) <= 0.02 * pb, (pa, pb)
+    _close(xa, xb, 1e-6)
+
+
+def test_fused_matches_three_kernels_mixed():
+    """Mixed precision (FP32 matrix and mat-vec) at the default tolerances,
+    as a rollout.  Here two runs of the same path already differ: the
+    contact sums' atomic order moves the FP32 products, the slowly
+    converging envs of this batch stop at other points within the Newton
+    tolerance (measured: the PCG totals of one step in repeated runs of
+    either path spread by up to 40%, the gel's end points by up to 1e-5 m
+    within the 4 steps).  So this holds the fused path to the other at that
+    spread (statuses, PCG work within a factor 2, end points within 1e-3
+    of the diagonal per step); the mixed parity tests against the oracle
+    run the fused path by default."""
+    prm = scenes.SolverParams()
+    prm.precision = 1
+    st_a, xa, pa = _run(prm, 1, True)
+    st_b, xb, pb = _run(prm, 0, True)
+    assert np.all(st_a == 0) and np.all(st_b == 0)
+    assert 0.5 * pb <= pa <= 2.0 * pb, (pa, pb)
+    _close(xa, xb, 1e-3)
+
+
+def test_fused_profile_class():
+    """The profiled (host-driven) loop launches the fused kernel once per
+    PCG iteration and none of the three separate ones."""
+    scs = _batch()
+    prm = scenes.SolverParams().parity()
+    g = ipc.Envs([sc.scene for sc in scs], prm, stream=torch.cuda.Stream())
+    g.profile_enable(True)
+    g.profile_reset()
+    g.set_targets_all(_table(g, scs, 0, 1)[0])
+    st, s = g.step()
+    prof = g.profile()
+    g.close()
+    assert np.all(st == 0)
+    assert prof["pcg_iter"][0] > 0
+    assert prof["pcg_matvec"][0] == 0 and prof["pcg_update"][0] == 0 and prof["pair_matvec"][0] == 0
