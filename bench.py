@@ -63,8 +63,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--pcg-window", type=int, default=None,
                     help="rollout: PCG iterations per loop iteration (even; 0 = whole solves; default: the library's)")
-    ap.add_argument("--pcg-fused", type=int, default=None, choices=(0, 1),
-                    help="1: one fused kernel per PCG iteration, 0: three kernels (default: the library's)")
+    ap.add_argument("--pcg-fused", type=int, default=None, choices=(0, 1, 2),
+                    help="1 / 2: one fused kernel per PCG iteration (update items in ready / env order), "
+                         "0: three kernels (default: the library's)")
     ap.add_argument("--no-lockstep", action="store_true", help="skip the lock-step timing beside the rollout")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
     return ap.parse_args()

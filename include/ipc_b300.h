@@ -112,10 +112,13 @@ typedef struct {
                              scheduling property of this library)          */
   int pcg_fused;          /* 1 (default): a PCG iteration is one persistent
                              kernel (contact terms, SELL mat-vec and update;
-                             an env's update starts when its own products
-                             are in); 0: three kernels (the mat-vecs, then
-                             the update).  Runs with friction use the three
-                             kernels.  The same arithmetic either way.     */
+                             an env's update items start when its own
+                             products are in, in the order the envs become
+                             ready); 2: the same kernel taking the update
+                             items in env order (each waits for its env);
+                             0: three kernels (the mat-vecs, then the
+                             update).  Runs with friction use the three
+                             kernels.  The same arithmetic in every form.  */
 } ipc_params;
 
 /* One environment: a tetrahedral gel mesh (one or more pads) and affine bodies. */
@@ -230,13 +233,19 @@ typedef struct {
   float assemble_us[3];   /* mean assembly time per launch for 64, 128, 256, us        */
   int pairs_ctas_per_sm;  /* broad phase: CTAs per SM of the candidate-pair search     */
   float pairs_us[3];      /* mean broad-phase time per search for 4, 8, 16 CTAs / SM   */
+  int pcg_iter_bound;     /* fused PCG iteration kernel: register bound on (1) or off  */
+  float pcg_iter_us[2];   /* mean time per fused iteration with the bound on, off, us
+                             (0 when the fused kernel is not in use: pcg_fused = 0
+                             or friction on)                                        */
 } ipc_tuning;
 
 /* Choose launch shapes by timing `reps` launches of each candidate on this
  * ctx's current state (call it after at least one ipc_step, between steps):
  * the PCG mat-vec's SELL slots in flight per lane and the persistent PCG
  * grid (each on a batch of every env and one of every 4th env: the mean),
- * the gather assembly's CTA size and the candidate-pair search's grid
+ * the fused PCG iteration kernel's register bound (PCG iterations from a
+ * fresh start on the last system, every env and every 4th env), the
+ * gather assembly's CTA size and the candidate-pair search's grid
  * (every env).  A candidate replaces the default shape
  * only when it is more than 5% faster.  It touches only scratch that the
  * next Newton iteration rebuilds (PCG scratch, the SELL values from the

@@ -154,6 +154,7 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_fused = prm.pcg_fused;
   d.pcg_grid = 148;
   d.pcg_grid_fused = 148;
+  d.pcg_iter_bound = 1;
   d.asm_block = 128;
   d.pairs_grid = 148 * 8;
   d.newton_max = prm.newton_max;
@@ -265,7 +266,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_item = c.take<int2>((size_t)pk.n_rows / 128);
   d.pcg_pitem = c.take<int2>((size_t)pk.n_pairs_cap / 8 + (size_t)pk.n_envs);
-  d.pcg_ctl = c.take<unsigned int>(8);
+  d.pcg_ctl = c.take<unsigned int>(16);
+  d.pcg_ritem = c.take<int>((size_t)pk.n_rows / 128);
   d.step_ctl = c.take<unsigned int>(8);
   d.roll_ctl = c.take<unsigned long long>(4);
   d.check_word = c.take<unsigned long long>(2);
@@ -926,7 +928,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   if (!prm || !out || !dev_workspace) return IPC_EINVAL;
   if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
       prm->newton_abs_after < 0 || prm->rollout_pcg_window < 0 || prm->rollout_pcg_window == 1 ||
-      (prm->rollout_pcg_window & 1) || prm->pcg_fused < 0 || prm->pcg_fused > 1 ||
+      (prm->rollout_pcg_window & 1) || prm->pcg_fused < 0 || prm->pcg_fused > 2 ||
       prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
     return IPC_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
@@ -978,9 +980,11 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   // persistent PCG grid: every resident CTA of the two PCG kernels
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
-  ctx->dev.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
+  ctx->dev.pcg_grid_fused =
+      ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll, ctx->dev.pcg_iter_bound);
   ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
   CK(cudaMemsetAsync(ctx->dev.check_word, 0, 2 * sizeof(unsigned long long), ctx->stream));
+  CK(cudaMemsetAsync(ctx->dev.pcg_ritem, 0xff, sizeof(int) * (size_t)(ctx->pk.n_rows / 128), ctx->stream));
   ctx->dev.pairs_grid = ctx->n_sm * 8;
   CK(cudaStreamSynchronize(ctx->stream));
   return IPC_OK;
@@ -1074,9 +1078,44 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   for (int k = 0; k < 3; ++k)
     if (t.grid_us[k] < best && t.grid_us[k] < 0.95f * t.grid_us[1]) { best = t.grid_us[k]; best_c = cand[k]; }
   d.pcg_grid = ctx->n_sm * best_c;
-  d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll);
   CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
   if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
+  // the fused iteration kernel, register bound on (default) or off: PCG
+  // iterations from a fresh start (p = 0, r = -g, z = P^-1 r: the PCG
+  // scratch of the last Newton iteration's system), on every env and on
+  // every fourth env, the mean time per iteration; converging envs leave
+  // as in a real solve.  The flags the solve sets (I_PCG, I_DEC) are
+  // cleared afterwards; the next step's start resets the counters.
+  auto time_fused = [&](float* us) -> ipc_status {
+    float a = 0.f, q = 0.f;
+    ipc_status r;
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((r = select_envs(ctx, {}, I_PCG)) != IPC_OK) return r;
+      if ((r = select_envs(ctx, pass ? quarter : all, I_NEWT)) != IPC_OK) return r;
+      launch_pcg_init(d, s);
+      launch_pcg_begin(d, s, 0, 0);
+      if ((r = time_launches(ctx, reps, [&] { launch_pcg_iter(d, s, 0, 0, 0xffffffffu); }, pass ? &q : &a)) !=
+          IPC_OK)
+        return r;
+    }
+    *us = 0.5f * (a + q);
+    return IPC_OK;
+  };
+  int best_b = 1;
+  if (d.pcg_fused && !(d.fr_mu > 0.0)) {
+    for (int b = 1; b >= 0; --b) {
+      d.pcg_iter_bound = b;
+      d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, b);
+      if ((st = time_fused(&t.pcg_iter_us[1 - b])) != IPC_OK) return st;
+    }
+    if (t.pcg_iter_us[1] < 0.95f * t.pcg_iter_us[0]) best_b = 0;
+    CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
+    if ((st = select_envs(ctx, {}, I_NEWT)) != IPC_OK) return st;
+    if ((st = select_envs(ctx, {}, I_PCG)) != IPC_OK) return st;
+    if ((st = select_envs(ctx, {}, I_DEC)) != IPC_OK) return st;
+  }
+  d.pcg_iter_bound = best_b;
+  d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, best_b);
   // gather assembly: 64, 128 or 256 threads per CTA, every env counted as
   // starting a Newton iteration (rewrites the SELL values from the stored
   // element blocks)
@@ -1117,6 +1156,7 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   t.spmv_unroll = best_u;
   t.pcg_ctas_per_sm = best_c;
   for (int k = 0; k < 3; ++k) t.grid_ctas_per_sm[k] = cand[k];
+  t.pcg_iter_bound = best_b;
   if (out) *out = t;
   return IPC_OK;
 }

@@ -30,7 +30,14 @@ namespace ipc {
 
 namespace {
 
-enum PcgCtl { C_ARRIVED = 0, C_ITER, C_LEN, C_DEAD, C_LIVE, C_NEXT, C_ABORT, C_COUNT };
+// C_NEXT: next pair / mat-vec item of the fused kernel; C_ABORT: a wait
+// gave up; C_RALLOC / C_RTAKE: slots of the ready update items allocated /
+// taken; C_LIVEROWS: row items of the envs solving at the launch's start;
+// C_STOPROWS: row items of the envs that stopped during the launch
+enum PcgCtl {
+  C_ARRIVED = 0, C_ITER, C_LEN, C_DEAD, C_LIVE, C_NEXT, C_ABORT, C_RALLOC, C_RTAKE, C_LIVEROWS, C_STOPROWS,
+  C_COUNT
+};
 
 // component c of a 3-vector of either precision
 template <class T>
@@ -88,6 +95,7 @@ __device__ void build_list(const Dev& d) {
       // per item its env and global row CTA / pair group, so that a kernel
       // finds its item with one load instead of a search over the list
       const int cta0 = d.env_row_off[e] >> 7;
+      ENVI(d, e, I_LISTROW) = ex[1];
       for (int j = 0; j < v[1]; ++j) d.pcg_item[ex[1] + j] = make_int2(e, cta0 + j);
       for (int j = 0; j < v[2]; ++j) d.pcg_pitem[ex[2] + j] = make_int2(e, j);
     }
@@ -102,6 +110,8 @@ __device__ void build_list(const Dev& d) {
     d.pcg_ctl[C_LEN] = carry[0];
     d.pcg_ctl[C_LIVE] = carry[0];
     d.pcg_ctl[C_DEAD] = 0;
+    d.pcg_ctl[C_LIVEROWS] = carry[1];
+    d.pcg_ctl[C_STOPROWS] = 0;
   }
   __syncthreads();
 }
@@ -376,6 +386,8 @@ __global__ void k_pcg_begin(Dev d, cudaGraphConditionalHandle h, int use_cond) {
     d.pcg_ctl[C_ITER] = 0;
     d.pcg_ctl[C_NEXT] = 0;
     d.pcg_ctl[C_ABORT] = 0;
+    d.pcg_ctl[C_RALLOC] = 0;
+    d.pcg_ctl[C_RTAKE] = 0;
   }
   build_list(d);
   if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(h, d.pcg_ctl[C_LIVE] > 0 ? 1u : 0u);
@@ -480,6 +492,7 @@ __device__ __forceinline__ void update_rows(const Dev& d, int e, int cta, double
       ENVI(d, e, I_PCG) = 0;
       ENVI(d, e, I_DEC) = 1;
       atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
+      atomicAdd(d.pcg_ctl + C_STOPROWS, (unsigned)env_row_ctas(d, e));
       atomicSub(d.pcg_ctl + C_LIVE, 1u);
     }
   }
@@ -518,6 +531,10 @@ __device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, in
   if (threadIdx.x == 0) {
     d.pcg_ctl[C_ARRIVED] = 0;
     d.pcg_ctl[C_NEXT] = 0;
+    d.pcg_ctl[C_RALLOC] = 0;
+    d.pcg_ctl[C_RTAKE] = 0;
+    d.pcg_ctl[C_LIVEROWS] -= d.pcg_ctl[C_STOPROWS];
+    d.pcg_ctl[C_STOPROWS] = 0;
     d.pcg_ctl[C_ITER] += 1;
     d.step_ctl[4] += 1u;
     const unsigned len = d.pcg_ctl[C_LEN];
@@ -528,8 +545,10 @@ __device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, in
   __syncthreads();
   if (d.pcg_ctl[C_ABORT]) {
     // a wait of the fused kernel gave up (never expected): the envs still
-    // solving end their step with IPC_ECUDA, their reductions reset
+    // solving end their step with IPC_ECUDA, their reductions and the
+    // ready slots reset
     const int n_list = (int)d.pcg_ctl[C_LEN];
+    for (int i = threadIdx.x; i < (d.n_rows >> 7); i += blockDim.x) d.pcg_ritem[i] = -1;
     for (int i = threadIdx.x; i < n_list; i += blockDim.x) {
       const int e = d.pcg_list[i];
       if (!ENVI(d, e, I_PCG)) continue;
@@ -546,6 +565,7 @@ __device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, in
       d.pcg_ctl[C_LIVE] = 0;
       d.pcg_ctl[C_DEAD] = 0;
       d.pcg_ctl[C_LEN] = 0;
+      d.pcg_ctl[C_LIVEROWS] = 0;
     }
     __syncthreads();
   } else if (s_rebuild) {
@@ -582,70 +602,146 @@ __global__ void __launch_bounds__(128) k_pcg_update(Dev d, cudaGraphConditionalH
 }
 
 // ---- the fused PCG iteration: contact terms, SELL mat-vec and update of
-// every listed env in one persistent launch.  CTAs take items in order
-// from a device counter (C_NEXT): the pair groups, then the mat-vec row
-// items, then the update row items, each env after env.  An update item
-// of env e waits until every pair and mat-vec item of e has finished
-// (I_PHASE counts them, each after a fence): those items were taken before
-// it by CTAs that are running and wait on nothing, so the wait ends, and
-// envs pipeline (early envs update while later ones multiply).  The wait
-// is bounded all the same: after kWaitCycles (about a second) the CTA
-// raises C_ABORT, the other waits give up at once, and the envs still
-// solving end with IPC_ECUDA.
+// every listed env in one persistent launch.  CTAs first take the pair
+// groups and then the mat-vec row items in order from a device counter
+// (C_NEXT).  Each of these items ends with a fence and an increment of its
+// env's I_PHASE; the CTA that completes the count publishes the env's
+// update row items into the ready slots (pcg_ritem, allocated by C_RALLOC).
+// CTAs that find the pair and mat-vec items all taken take ready slots in
+// order (C_RTAKE) up to the row items of the envs solving (C_LIVEROWS), so
+// an update item starts when its own env is ready, in the order the envs
+// become ready (no item waits behind another env's).  A CTA waits only for
+// its slot to be written: when it waits, every pair and mat-vec item has
+// been taken by a running CTA that waits on nothing, so every solving env
+// publishes and every slot below C_LIVEROWS is written.  The wait is
+// bounded all the same: after kWaitCycles (about a second) the CTA raises
+// C_ABORT, the other waits give up at once, and the grid's last CTA ends
+// the envs still solving with IPC_ECUDA.
 constexpr long long kWaitCycles = 2000000000ll;
 
-__device__ __forceinline__ void phase_signal(const Dev& d, int e) {
+// end of a pair or mat-vec item of env e (every thread calls it); rq: the
+// ready-slot order (the env's last product publishes its update items)
+__device__ __forceinline__ void phase_signal(const Dev& d, int e, bool rq) {
+  __shared__ int s_pub;
   __threadfence();   // every thread: its stores and atomics of the item before the count
   __syncthreads();
-  if (threadIdx.x == 0) atomicAdd(&ENVI(d, e, I_PHASE), 1);
+  if (threadIdx.x == 0) {
+    const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+    const int old = atomicAdd(&ENVI(d, e, I_PHASE), 1);
+    s_pub = rq && old == need - 1 ? (int)atomicAdd(d.pcg_ctl + C_RALLOC, (unsigned)env_row_ctas(d, e)) : -1;
+  }
+  __syncthreads();
+  const int base = s_pub;
+  if (base >= 0) {
+    // the env's last product: its update row items become ready
+    const int n = env_row_ctas(d, e), first = ENVI(d, e, I_LISTROW);
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      if (IPC_CHECK(d.check_word, (unsigned)(base + j) < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, base + j))
+        atomicExch(d.pcg_ritem + base + j, first + j);
+  }
 }
 
-// thread 0: waits until env e's pair and mat-vec items are done; false on abort
+// thread 0, env order: waits until env e's pair and mat-vec items are
+// done (they were taken before this update item by running CTAs that wait
+// on nothing); false on abort
 __device__ __forceinline__ bool phase_wait(const Dev& d, int e) {
   const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
   volatile int* ph = &ENVI(d, e, I_PHASE);
   volatile unsigned* ab = d.pcg_ctl + C_ABORT;
-  if (*ph >= need) {
-    __threadfence();
-    return true;
-  }
-  const long long t0 = clock64();
-  while (*ph < need) {
-    if (*ab) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      atomicExch(d.pcg_ctl + C_ABORT, 1u);
-      return false;
+  if (*ph < need) {
+    const long long t0 = clock64();
+    while (*ph < need) {
+      if (*ab) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(d.pcg_ctl + C_ABORT, 1u);
+        return false;
+      }
+      __nanosleep(100);
     }
-    __nanosleep(200);
   }
   __threadfence();
   return true;
 }
 
-template <class HT, int U>
-__global__ void __launch_bounds__(128, 12) k_pcg_iter(Dev d, cudaGraphConditionalHandle h, int use_cond,
-                                                   unsigned window) {
+// thread 0, ready-slot order: the next ready update item (its index in the
+// row item table), -1 when none is left or on abort
+__device__ __forceinline__ int take_ready(const Dev& d, unsigned n_upd) {
+  const unsigned t = atomicAdd(d.pcg_ctl + C_RTAKE, 1u);
+  if (t >= n_upd) return -1;
+  volatile int* slot = d.pcg_ritem + t;
+  volatile unsigned* ab = d.pcg_ctl + C_ABORT;
+  int v = *slot;
+  if (v < 0) {
+    const long long t0 = clock64();
+    while ((v = *slot) < 0) {
+      if (*ab) return -1;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(d.pcg_ctl + C_ABORT, 1u);
+        return -1;
+      }
+      __nanosleep(100);
+    }
+  }
+  *slot = -1;  // the slot is free for the next launch
+  __threadfence();
+  return v;
+}
+
+// B = 1 bounds the registers so that the mat-vec items keep the separate
+// mat-vec kernel's occupancy (12 CTAs per SM in FP32, 6 in FP64; the pair
+// path spills a few words), B = 0 gives the pair path its registers (9
+// CTAs per SM in FP32, 5 in FP64); ipc_autotune picks one.
+template <class HT, int U, int B>
+__global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 : 5))
+    k_pcg_iter(Dev d, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
   __shared__ int s_item, s_e, s_cta;
   __shared__ double s_beta, s_dq, s_al;
   __shared__ uint8_t s_tag;
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_rows = d.pcg_row_off[n_list];
   const int n_pairs = d.pcg_pair_off[n_list];
-  const int n_total = n_pairs + 2 * n_rows;
+  const int n_a = n_pairs + n_rows;
+  const unsigned n_upd = d.pcg_ctl[C_LIVEROWS];
+  const bool rq = d.pcg_fused == 1;    // 1: ready-slot order, 2: env order
   const int nb = pcg_new_buf(d), ob = nb ^ 1;
+  bool products_left = true;
   for (;;) {
     __syncthreads();  // the previous item is done with the shared item data
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(d.pcg_ctl + C_NEXT, 1u);
+    if (threadIdx.x == 0) {
+      int it = n_a;
+      if (products_left || !rq) it = (int)atomicAdd(d.pcg_ctl + C_NEXT, 1u);
+      if (rq) {
+        if (it >= n_a) {
+          const int v = take_ready(d, n_upd);
+          it = v < 0 ? -1 : n_a + v;
+        }
+      } else if (it >= n_a + n_rows) {
+        it = -1;
+      } else if (it >= n_a) {
+        // env order: the update item waits for its own env's products
+        update_item_info(d, it - n_a, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
+        if (s_e >= 0) {
+          if (phase_wait(d, s_e)) {
+            const double dq = __ldcg(&ENVS(d, s_e, S_DQ)) + __ldcg(&ENVS(d, s_e, S_DQC));
+            s_dq = dq;
+            s_al = dq > 0.0 ? ENVS(d, s_e, S_RZ) / dq : 0.0;
+          } else {
+            s_e = -1;
+          }
+        }
+      }
+      s_item = it;
+    }
     __syncthreads();
     const int item = s_item;
-    if (item >= n_total) break;
+    if (item < 0) break;
     if (item < n_pairs) {
       const int2 it = d.pcg_pitem[item];               // (env, group of 8 active pairs)
       if (!IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs, CHK_PCG_ITEM, item)) continue;
       if (!ENVI(d, it.x, I_PCG)) continue;
       matvec_pairs<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
-      phase_signal(d, it.x);
-    } else if (item < n_pairs + n_rows) {
+      phase_signal(d, it.x, rq);
+    } else if (item < n_a) {
       if (threadIdx.x == 0) {
         const int2 it = d.pcg_item[item - n_pairs];    // (env, row CTA)
         const bool in = IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs &&
@@ -658,22 +754,15 @@ __global__ void __launch_bounds__(128, 12) k_pcg_iter(Dev d, cudaGraphConditiona
       const int e = s_e;
       if (e < 0) continue;
       matvec_rows<HT, U>(d, e, s_cta, (HT)s_beta, ob, nb);
-      phase_signal(d, e);
+      phase_signal(d, e, rq);
     } else {
-      if (threadIdx.x == 0) {
-        update_item_info(d, item - n_pairs - n_rows, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
-        if (s_e >= 0) {
-          if (phase_wait(d, s_e)) {
-            // d.q and alpha again, now that the env's terms are all in
-            const double dq = __ldcg(&ENVS(d, s_e, S_DQ)) + __ldcg(&ENVS(d, s_e, S_DQC));
-            s_dq = dq;
-            s_al = dq > 0.0 ? ENVS(d, s_e, S_RZ) / dq : 0.0;
-          } else {
-            s_e = -1;
-          }
-        }
+      products_left = false;
+      // an update item whose env's products are all in (ready slot; in env
+      // order thread 0 has waited above)
+      if (rq) {
+        if (threadIdx.x == 0) update_item_info(d, item - n_a, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
+        __syncthreads();
       }
-      __syncthreads();
       if (s_e < 0) continue;
       update_rows<HT>(d, s_e, s_cta, s_dq, s_al, s_tag, nb);
     }
@@ -759,34 +848,44 @@ int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
 }
 
 // resident CTAs per SM of the persistent PCG kernels (the smaller of the two)
+// the fused kernel's variant: slots in flight 2 or 4 (an 8-slot choice of
+// the mat-vec runs the fused kernel with 4), register bound on or off
+template <class HT>
+static void* pcg_iter_fn(int unroll, int bound) {
+  const bool u4 = unroll == 4 || unroll == 8;
+  if (bound) return u4 ? (void*)k_pcg_iter<HT, 4, 1> : (void*)k_pcg_iter<HT, 2, 1>;
+  return u4 ? (void*)k_pcg_iter<HT, 4, 0> : (void*)k_pcg_iter<HT, 2, 0>;
+}
+
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
-  const int u = d.spmv_unroll ? d.spmv_unroll : 2;
+  const bool u4 = d.spmv_unroll == 4 || d.spmv_unroll == 8;
   const int g = d.pcg_grid_fused;
+  const int b = d.pcg_iter_bound;
   if (d.prec) {
-    if (u == 2) k_pcg_iter<float, 2><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    else if (u == 8) k_pcg_iter<float, 8><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    else k_pcg_iter<float, 4><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    if (b) {
+      if (u4) k_pcg_iter<float, 4, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
+      else k_pcg_iter<float, 2, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    } else {
+      if (u4) k_pcg_iter<float, 4, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
+      else k_pcg_iter<float, 2, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    }
   } else {
-    if (u == 4) k_pcg_iter<double, 4><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    else if (u == 8) k_pcg_iter<double, 8><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    else k_pcg_iter<double, 2><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    if (b) {
+      if (u4) k_pcg_iter<double, 4, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
+      else k_pcg_iter<double, 2, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    } else {
+      if (u4) k_pcg_iter<double, 4, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
+      else k_pcg_iter<double, 2, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    }
   }
   return 1;
 }
 
 // resident CTAs per SM of the fused iteration kernel
-int pcg_iter_ctas_per_sm(int prec, int unroll) {
+int pcg_iter_ctas_per_sm(int prec, int unroll, int bound) {
   int a = 0;
-  const int u = unroll ? unroll : 2;
-  if (prec) {
-    if (u == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 2>, 128, 0);
-    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 8>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<float, 4>, 128, 0);
-  } else {
-    if (u == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 4>, 128, 0);
-    else if (u == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 8>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pcg_iter<double, 2>, 128, 0);
-  }
+  const void* f = prec ? pcg_iter_fn<float>(unroll, bound) : pcg_iter_fn<double>(unroll, bound);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, 128, 0);
   return a > 0 ? a : 1;
 }
 

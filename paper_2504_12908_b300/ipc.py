@@ -53,7 +53,8 @@ class ipc_tuning(C.Structure):
     _fields_ = [("spmv_unroll", C.c_int), ("pcg_ctas_per_sm", C.c_int), ("spmv_us", C.c_float * 3),
                 ("grid_ctas_per_sm", C.c_int * 3), ("grid_us", C.c_float * 3),
                 ("assemble_block", C.c_int), ("assemble_us", C.c_float * 3),
-                ("pairs_ctas_per_sm", C.c_int), ("pairs_us", C.c_float * 3)]
+                ("pairs_ctas_per_sm", C.c_int), ("pairs_us", C.c_float * 3),
+                ("pcg_iter_bound", C.c_int), ("pcg_iter_us", C.c_float * 2)]
 
 
 class ipc_step_stats(C.Structure):
@@ -554,7 +555,9 @@ class Envs:
                 "assemble_block": t.assemble_block,
                 "assemble_us": {b: round(float(t.assemble_us[k]), 2) for k, b in enumerate((64, 128, 256))},
                 "pairs_ctas_per_sm": t.pairs_ctas_per_sm,
-                "pairs_us": {c: round(float(t.pairs_us[k]), 2) for k, c in enumerate((4, 8, 16))}}
+                "pairs_us": {c: round(float(t.pairs_us[k]), 2) for k, c in enumerate((4, 8, 16))},
+                "pcg_iter_bound": t.pcg_iter_bound,
+                "pcg_iter_us": {b: round(float(t.pcg_iter_us[k]), 2) for k, b in enumerate((1, 0))}}
 
     def set_graph_mode(self, mode=1):
         """CUDA-graph execution: 0 plain launches, 1 (or True) each PCG solve

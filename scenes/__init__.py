@@ -100,7 +100,7 @@ class SolverParams:
     friction_eps_v: float = 1e-3    # static/dynamic velocity threshold, m/s
     newton_abs_after: int = 1000000  # Newton iterations that clamp negative eigenvalues; |lambda| after
     rollout_pcg_window: int = 0     # rollout: PCG iterations per loop iteration (0: whole solves)
-    pcg_fused: int = 1              # 1: one persistent kernel per PCG iteration; 0: three kernels
+    pcg_fused: int = 1              # 1 / 2: one persistent kernel per PCG iteration (ready / env order); 0: three
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""

@@ -1,4 +1,4 @@
-"""The fused PCG iteration kernel (ipc_params.pcg_fused = 1, the default):
+"""The fused PCG iteration kernel (ipc_params.pcg_fused = 1, the default, or 2):
 contact terms, SELL mat-vec and update of every env in one persistent
 launch, an env's update waiting for its own products.  It computes what the
 three-kernel iteration (pcg_fused = 0) computes (Sec. 3.3's block-Jacobi
@@ -76,12 +76,14 @@ def _close(sa, sb, bound):
     assert worst <= bound * K, worst
 
 
-@pytest.mark.parametrize("rollout,stream", [(False, True), (True, True), (False, False)])
-def test_fused_matches_three_kernels_fp64(rollout, stream):
+@pytest.mark.parametrize("fused,rollout,stream", [(1, False, True), (1, True, True), (1, False, False),
+                                                  (2, False, True), (2, True, True)])
+def test_fused_matches_three_kernels_fp64(fused, rollout, stream):
     """FP64 at the parity tolerances: lock-step graphs, the rollout graph,
-    and host-driven steps (no stream: plain launches)."""
+    and host-driven steps (no stream: plain launches); update items in
+    ready order (1) and in env order (2)."""
     prm = scenes.SolverParams().parity()
-    st_a, xa, pa = _run(prm, 1, rollout, stream)
+    st_a, xa, pa = _run(prm, fused, rollout, stream)
     st_b, xb, pb = _run(prm, 0, rollout, stream)
     assert np.all(st_a == 0) and np.all(st_b == 0)
     assert abs(pa - pb) <= 0.02 * pb, (pa, pb)
