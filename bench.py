@@ -483,7 +483,7 @@ def matvec_traffic_per_launch(env_iters_per_launch):
 # SELL mat-vec and update in one launch): DRAM bytes of its first launch
 # in the 24-env case (every env in its first PCG iteration), scaled by
 # env-iterations.
-PCG_ITER_TRAFFIC = {"env_iters": 24, "bytes": None, "source_sha256": None}
+PCG_ITER_TRAFFIC = {"env_iters": 24, "bytes": 136305664 + 17448192, "source_sha256": "58b0a9853d87c63cc1bcabf17f571b610e6f0b0c8670ecc9dc16ff5114fac6b5"}
 PCG_ITER_PARTS = [("pcgvec.cuh", None), ("fpconv.cuh", None),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_rows("),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_pairs("),
@@ -505,18 +505,17 @@ def pcg_iter_traffic_per_launch(env_iters_per_launch):
 # sources are the ones that were measured (hash of their text).
 FP64_FLOPS_PER_UNIT = {
     "tet_elastic": (242.0, "0657c712ffa87872172c39c9433c5f8809afe6af23538ae1311894e1c2e972ad"),
-    "pcg_update": (22.63, "c5a50b0e2e2d219cb1553dafacbb75773f5f150648eb29ab05ae975374101f11"),
     "body_abd": (4920.0, "176a85a7dc5c0d3c979f3de3ea30e78cb61eee8f864c11b05d2bc3a3ad460833"),
+    "pcg_iter": (23.25, "58b0a9853d87c63cc1bcabf17f571b610e6f0b0c8670ecc9dc16ff5114fac6b5"),
 }
-ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "pcg_update": "row per PCG iteration",
-            "body_abd": "body per Newton iteration"}
+ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "body_abd": "body per Newton iteration",
+            "pcg_iter": "row per PCG iteration"}
 ALU_PARTS = {
     "tet_elastic": [("physics.cuh", None), ("common.cuh", None),
                     ("kernels_solver.cu", "__global__ void __launch_bounds__(64) k_tet(")],
-    "pcg_update": [("pcgvec.cuh", None), ("fpconv.cuh", None),
-                   ("kernels_pcg.cu", "__global__ void __launch_bounds__(128) k_pcg_update(")],
     "body_abd": [("physics.cuh", None), ("common.cuh", None),
                  ("kernels_solver.cu", "__global__ void __launch_bounds__(128) k_body(")],
+    "pcg_iter": PCG_ITER_PARTS,
 }
 
 
@@ -527,8 +526,8 @@ def alu_rooflines(genv, prof, tot, fp64_tflops):
         return None
     sz = genv.system_sizes(0)
     nv, nb, _ = genv.sizes[0]
-    units = {"tet_elastic": tot["newton_env_iters"] * sz["tets"], "pcg_update": tot["pcg_iters"] * (nv + 4 * nb),
-             "body_abd": tot["newton_env_iters"] * nb}
+    units = {"tet_elastic": tot["newton_env_iters"] * sz["tets"], "body_abd": tot["newton_env_iters"] * nb,
+             "pcg_iter": tot["pcg_iters"] * (nv + 4 * nb)}
     out = {}
     for k, (per, sha) in FP64_FLOPS_PER_UNIT.items():
         if per is None or k not in prof or prof[k][1] <= 0 or sha != _kernel_source_hash(ALU_PARTS[k]):
