@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--pcg-fused", type=int, default=None, choices=(0, 1, 2),
                     help="1 / 2: one fused kernel per PCG iteration (update items in ready / env order), "
                          "0: three kernels (default: the library's)")
+    ap.add_argument("--pcg-iters-per-launch", type=int, default=None,
+                    help="fused PCG kernel: iterations per launch (default: the library's)")
     ap.add_argument("--no-lockstep", action="store_true", help="skip the lock-step timing beside the rollout")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel profiling pass")
     return ap.parse_args()
@@ -151,7 +153,7 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ workload
-def build_workload(n_envs, precision, pcg_window=None, pcg_fused=None):
+def build_workload(n_envs, precision, pcg_window=None, pcg_fused=None, pcg_ipl=None):
     import scenes
     scene, params, deltas = scenes.config1_batch(n_envs)
     params.precision = precision
@@ -159,6 +161,8 @@ def build_workload(n_envs, precision, pcg_window=None, pcg_fused=None):
         params.rollout_pcg_window = pcg_window
     if pcg_fused is not None:
         params.pcg_fused = pcg_fused
+    if pcg_ipl is not None:
+        params.pcg_iters_per_launch = pcg_ipl
     return scene, params, deltas
 
 
@@ -663,7 +667,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build()
-    scene, params, deltas = build_workload(args.envs, 0, args.pcg_window, args.pcg_fused)
+    scene, params, deltas = build_workload(args.envs, 0, args.pcg_window, args.pcg_fused, args.pcg_iters_per_launch)
     n_total = args.warmup + args.steps
     dev = f"cuda:{local}"
 

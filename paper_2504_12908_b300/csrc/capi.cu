@@ -155,6 +155,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_grid = 148;
   d.pcg_grid_fused = 148;
   d.pcg_iter_bound = 1;
+  d.pcg_multi = prm.pcg_iters_per_launch;
+  d.pcg_grid_multi = 148;
   d.asm_block = 128;
   d.pairs_grid = 148 * 8;
   d.newton_max = prm.newton_max;
@@ -363,7 +365,9 @@ ipc_status sync_flags(ipc_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   if (ctx->pcg_graph_pending) {
     // the graph ran the WHILE body h_ctl[1] times
-    ctx->launches += (long long)ctx->h_ctl[1] * ctx->pcg_iter_launches;
+    // the graph ran the WHILE body once per launch of iterations
+    ctx->launches += (long long)(ctx->h_ctl[1] / (unsigned)pcg_iters_per_launch(ctx->dev, 0xffffffffu)) *
+                     ctx->pcg_iter_launches;
     ctx->pcg_graph_pending = false;
   }
   prof_flush(ctx);
@@ -579,7 +583,7 @@ ipc_status run_pcg(ipc_ctx* ctx) {
   KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, s, 0, 0); });
   // every env stops by itself after at most pcg_max iterations
   for (int it = 0; it < ctx->prm.pcg_max + 1; it += kPcgPoll) {
-    for (int i = 0; i < kPcgPoll; ++i) pcg_iteration(ctx, s);
+    for (int i = 0; i < kPcgPoll; i += pcg_iters_per_launch(ctx->dev, 0xffffffffu)) pcg_iteration(ctx, s);
     ipc_status st = read_pcg_ctl(ctx);
     if (st != IPC_OK) return st;
     if (ctx->h_ctl[4] == 0) break;  // no env still iterating
@@ -907,6 +911,7 @@ void ipc_default_params(ipc_params* p) {
   p->newton_abs_after = 1000000;
   p->rollout_pcg_window = 0;
   p->pcg_fused = 1;
+  p->pcg_iters_per_launch = 1;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {
@@ -929,6 +934,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   if (prm->dt <= 0 || prm->dhat <= 0 || prm->kappa <= 0 || prm->newton_max < 1 || prm->pcg_max < 1 ||
       prm->newton_abs_after < 0 || prm->rollout_pcg_window < 0 || prm->rollout_pcg_window == 1 ||
       (prm->rollout_pcg_window & 1) || prm->pcg_fused < 0 || prm->pcg_fused > 2 ||
+      prm->pcg_iters_per_launch < 1 || prm->pcg_iters_per_launch > 16 ||
       prm->ls_max < 1 || prm->accd_max < 1 || !(prm->accd_s > 0 && prm->accd_s < 1))
     return IPC_EINVAL;
   if (reinterpret_cast<uintptr_t>(dev_workspace) % 256 != 0) return IPC_EINVAL;
@@ -982,6 +988,7 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   ctx->dev.pcg_grid_fused =
       ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll, ctx->dev.pcg_iter_bound);
+  ctx->dev.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
   CK(cudaMemsetAsync(ctx->dev.check_word, 0, 2 * sizeof(unsigned long long), ctx->stream));
   CK(cudaMemsetAsync(ctx->dev.pcg_ritem, 0xff, sizeof(int) * (size_t)(ctx->pk.n_rows / 128), ctx->stream));
@@ -1116,6 +1123,7 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   }
   d.pcg_iter_bound = best_b;
   d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, best_b);
+  d.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(d.prec, d.spmv_unroll);
   // gather assembly: 64, 128 or 256 threads per CTA, every env counted as
   // starting a Newton iteration (rewrites the SELL values from the stored
   // element blocks)

@@ -66,6 +66,7 @@ enum EnvInt {
   I_DEC,          // its PCG solve ended: the Newton decision is pending
   I_PHASE,        // fused PCG iteration: the env's pair and mat-vec items finished
   I_LISTROW,      // index of the env's first row item in the PCG work list
+  I_UPDK,         // multi-iteration PCG kernel: the env's iterations completed in the launch
   // rollout (ipc_rollout: each env runs its own sequence of steps)
   I_RSTEP,        // steps completed in this rollout
   I_BEGIN,        // begins its next step at the top of the next loop iteration
@@ -153,7 +154,7 @@ struct Dev {
   int2* pcg_pitem;              // per pair item: (env, group of 8 active pairs)
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] items of stopped envs, [4] envs
-                                // solving, [5..10] the fused kernel's counters (PcgCtl)
+                                // solving, [5..10] the fused kernels' counters (PcgCtl)
   int* pcg_ritem;               // fused kernel: update items in the order their envs became
                                 // ready (-1: slot not written)
   int pcg_grid;                 // CTAs of the persistent PCG row kernels
@@ -161,6 +162,8 @@ struct Dev {
                                 // ready order / env order) when friction is off; 0: three kernels
   int pcg_grid_fused;           // CTAs of k_pcg_iter (its resident CTAs)
   int pcg_iter_bound;           // k_pcg_iter's register bound: 1 on (default), 0 off (ipc_autotune)
+  int pcg_multi;                // PCG iterations per launch of the fused kernel (> 1: k_pcg_multi)
+  int pcg_grid_multi;           // CTAs of k_pcg_multi (its resident CTAs)
   int asm_block;                // threads per CTA of the gather assembly (ipc_autotune)
   int pairs_grid;               // CTAs of the candidate-pair search (ipc_autotune)
   int pcg_grid_pairs;           // CTAs of the persistent contact mat-vec

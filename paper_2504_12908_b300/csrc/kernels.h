@@ -44,6 +44,8 @@ int launch_pcg_matvec(const Dev& d, cudaStream_t s);
 int launch_pcg_pairs(const Dev& d, cudaStream_t s);
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window);
 int pcg_iter_ctas_per_sm(int prec, int unroll, int bound);
+int pcg_multi_ctas_per_sm(int prec, int unroll);
+int pcg_iters_per_launch(const Dev& d, unsigned window);
 int launch_pcg_update(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                       unsigned window = 0xffffffffu);
 // resident 128-thread CTAs per SM of the PCG kernels (grid = 148 x this)

@@ -96,6 +96,7 @@ __device__ void build_list(const Dev& d) {
       // finds its item with one load instead of a search over the list
       const int cta0 = d.env_row_off[e] >> 7;
       ENVI(d, e, I_LISTROW) = ex[1];
+      ENVI(d, e, I_UPDK) = 0;
       for (int j = 0; j < v[1]; ++j) d.pcg_item[ex[1] + j] = make_int2(e, cta0 + j);
       for (int j = 0; j < v[2]; ++j) d.pcg_pitem[ex[2] + j] = make_int2(e, j);
     }
@@ -119,6 +120,7 @@ __device__ void build_list(const Dev& d) {
 // ---- block-Jacobi preconditioner application
 // z = P^{-1} r for row r.  Body rows read the 4 sub-rows of their body (all
 // of them sit in the same warp) and apply the body's 12x12 inverse in FP64.
+template <bool CG = false>
 __device__ __forceinline__ D3 apply_pc_body(const Dev& d, int r) {
   const int b = d.row_body[r];
   const int br = d.body_row[b];
@@ -126,13 +128,14 @@ __device__ __forceinline__ D3 apply_pc_body(const Dev& d, int r) {
   const double* Pi = d.body_pc + 144 * (long long)b;
   double o[3] = {0, 0, 0};
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * d.r[3 * br + j];
+    for (int j = 0; j < 12; ++j) o[i] += Pi[(3 * kk + i) * 12 + j] * (CG ? __ldcg(d.r + 3 * br + j) : d.r[3 * br + j]);
   return D3{o[0], o[1], o[2]};
 }
 
 // FP64 mode: gel rows apply the 6 stored entries of the symmetric 3x3 inverse
+template <bool CG = false>
 __device__ __forceinline__ D3 apply_pc64(const Dev& d, int r, uint8_t kr, D3 x) {
-  if (row_is_body(kr)) return apply_pc_body(d, r);
+  if (row_is_body(kr)) return apply_pc_body<CG>(d, r);
   if (kr == ROW_PAD) return D3{0, 0, 0};
   const double* P = reinterpret_cast<const double*>(d.pc) + 6 * (long long)r;
   const double a = P[0], b = P[1], c = P[2], e = P[3], f = P[4], g = P[5];
@@ -140,9 +143,10 @@ __device__ __forceinline__ D3 apply_pc64(const Dev& d, int r, uint8_t kr, D3 x) 
 }
 
 // mixed mode: FP32 inverse applied to the FP32-rounded residual of the row
+template <bool CG = false>
 __device__ __forceinline__ float4 apply_pc32(const Dev& d, int r, uint8_t kr, float3 x) {
   if (row_is_body(kr)) {
-    const D3 z = apply_pc_body(d, r);
+    const D3 z = apply_pc_body<CG>(d, r);
     return make_float4(d2f_bits(z.x), d2f_bits(z.y), d2f_bits(z.z), 0.0f);
   }
   if (kr == ROW_PAD) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -159,22 +163,26 @@ __device__ __forceinline__ D3 widen_row(float4 v) { return D3{f2d_bits(v.x), f2d
 __device__ __forceinline__ float dk32(float z, float b, float dold) { return __fmaf_rn(b, dold, z); }
 __device__ __forceinline__ double dk64(double z, double b, double dold) { return __fma_rn(b, dold, z); }
 
+// CG: z and d_{k-1} read through L2 (the multi-iteration kernel, where
+// other CTAs of the same launch wrote them)
 template <class HT> struct Dk;
 template <> struct Dk<float> {
+  template <bool CG = false>
   static __device__ __forceinline__ V3<float> row(const Dev& d, int c, float b, int ob) {
-    const V3<float> z = PV<float>::gather_z(d, c), o = PV<float>::gather_dir(d, c, ob);
+    const V3<float> z = PV<float>::gather_z<CG>(d, c), o = PV<float>::gather_dir<CG>(d, c, ob);
     return V3<float>{dk32(z.x, b, o.x), dk32(z.y, b, o.y), dk32(z.z, b, o.z)};
   }
 };
 template <> struct Dk<double> {
+  template <bool CG = false>
   static __device__ __forceinline__ V3<double> row(const Dev& d, int c, double b, int ob) {
-    const V3<double> z = PV<double>::gather_z(d, c), o = PV<double>::gather_dir(d, c, ob);
+    const V3<double> z = PV<double>::gather_z<CG>(d, c), o = PV<double>::gather_dir<CG>(d, c, ob);
     return V3<double>{dk64(z.x, b, o.x), dk64(z.y, b, o.y), dk64(z.z, b, o.z)};
   }
 };
 
 // ---- mat-vec item: 128 rows of SELL-32, U slots in flight per lane
-template <class HT, int U>
+template <class HT, int U, bool CG = false>
 __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT beta, int ob, int nb) {
   const int r = cta * 128 + threadIdx.x;
   const int ch = r >> 5, lane = r & 31;
@@ -210,7 +218,7 @@ __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT bet
     }
     V3<HT> w[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = Dk<HT>::row(d, c[u], beta, ob);
+    for (int u = 0; u < U; ++u) w[u] = Dk<HT>::template row<CG>(d, c[u], beta, ob);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ax += A[u][0] * w[u].x + A[u][1] * w[u].y + A[u][2] * w[u].z;
@@ -222,12 +230,12 @@ __device__ __forceinline__ void matvec_rows(const Dev& d, int e, int cta, HT bet
     int c = colp[sl * 32];
     if (!IPC_CHECK(d.check_word, (unsigned)c < (unsigned)d.n_rows, CHK_SELL_COL, c)) c = r;
     const HT* A = val + (long long)sl * 288;
-    const V3<HT> w = Dk<HT>::row(d, c, beta, ob);
+    const V3<HT> w = Dk<HT>::template row<CG>(d, c, beta, ob);
     ax += A[0] * w.x + A[32] * w.y + A[64] * w.z;
     ay += A[96] * w.x + A[128] * w.y + A[160] * w.z;
     az += A[192] * w.x + A[224] * w.y + A[256] * w.z;
   }
-  const V3<HT> own = Dk<HT>::row(d, r, beta, ob);
+  const V3<HT> own = Dk<HT>::template row<CG>(d, r, beta, ob);
   double out[1];
   bool last;
   if constexpr (sizeof(HT) == 4) {
@@ -254,7 +262,7 @@ __device__ __forceinline__ int ut12(int p, int q) { return p * 12 - p * (p - 1) 
 // shuffles, lane j computes row j of H_k d and scatters it: gel points
 // directly, body points as J^T (H_k d) on the body's 4 sub-rows (merged with
 // the warp's other pair when both touch the same single body).
-template <class HT>
+template <class HT, bool CG = false>
 __device__ __forceinline__ void matvec_pairs(const Dev& d, int e, int g, HT beta, int ob) {
   __shared__ double sdq[4];
   const int lane = threadIdx.x & 31, j = lane & 15, half = lane >> 4;
@@ -277,12 +285,14 @@ __device__ __forceinline__ void matvec_pairs(const Dev& d, int e, int g, HT beta
     row = d.cv_row[cv];
     b_pt = d.cv_body[cv];
     if (b_pt < 0) {
-      dj = (d.row_kind[row] == ROW_PINNED) ? (HT)0 : comp3(Dk<HT>::row(d, row, beta, ob), c);
+      dj = (d.row_kind[row] == ROW_PINNED) ? (HT)0 : comp3(Dk<HT>::template row<CG>(d, row, beta, ob), c);
     } else {
       const D3 x3 = ld3(d.cv_xbar, cv);
       xb[0] = x3.x; xb[1] = x3.y; xb[2] = x3.z;
-      const HT d0 = comp3(Dk<HT>::row(d, row, beta, ob), c), d1 = comp3(Dk<HT>::row(d, row + 1, beta, ob), c),
-               d2 = comp3(Dk<HT>::row(d, row + 2, beta, ob), c), d3 = comp3(Dk<HT>::row(d, row + 3, beta, ob), c);
+      const HT d0 = comp3(Dk<HT>::template row<CG>(d, row, beta, ob), c),
+               d1 = comp3(Dk<HT>::template row<CG>(d, row + 1, beta, ob), c),
+               d2 = comp3(Dk<HT>::template row<CG>(d, row + 2, beta, ob), c),
+               d3 = comp3(Dk<HT>::template row<CG>(d, row + 3, beta, ob), c);
       dj = (HT)((double)d0 + xb[0] * (double)d1 + xb[1] * (double)d2 + xb[2] * (double)d3);
     }
   }
@@ -440,7 +450,11 @@ __global__ void __launch_bounds__(128) k_pcg_pairs(Dev d) {
 // (its last CTA: beta, the stop test).  q, d_k, the contact accumulator
 // and the env's d.q are read through L2: in the fused iteration kernel
 // they were written by other CTAs of the same launch.
-template <class HT>
+// MULTI: the multi-iteration kernel, where the previous iteration's p, r, z
+// and the env's scalars were written by other CTAs of the same launch (read
+// through L2; the env's last CTA then counts the iteration in I_UPDK, which
+// the env's next products wait for).
+template <class HT, bool MULTI = false>
 __device__ __forceinline__ void update_rows(const Dev& d, int e, int cta, double dq, double al, uint8_t tag,
                                             int nb) {
   const int r = cta * 128 + threadIdx.x;
@@ -456,37 +470,37 @@ __device__ __forceinline__ void update_rows(const Dev& d, int e, int cta, double
   bool last;
   if constexpr (sizeof(HT) == 4) {
     const float4 dd = __ldcg(PV<float>::dbuf(d, nb) + r), qq = __ldcg(d.q4 + r);
-    st3(d.p, r, ld3(d.p, r) + al * widen_row(dd));
-    const D3 rv = ld3(d.r, r) - al * (touched ? widen_row(qq) + qcv : widen_row(qq));
+    st3(d.p, r, (MULTI ? ld3cg(d.p, r) : ld3(d.p, r)) + al * widen_row(dd));
+    const D3 rv = (MULTI ? ld3cg(d.r, r) : ld3(d.r, r)) - al * (touched ? widen_row(qq) + qcv : widen_row(qq));
     st3(d.r, r, rv);
     __syncwarp();
     const double rr = dot(rv, rv);
     const float3 rf = round_row(rv);
-    const float4 z = apply_pc32(d, r, kr, rf);
+    const float4 z = apply_pc32<MULTI>(d, r, kr, rf);
     d.z4[r] = z;
     last = env_reduce<2, float>(d, e, 0, cta, rf.x * z.x + rf.y * z.y + rf.z * z.z, &rr, out);
   } else {
     const double* db = PV<double>::dbuf(d, nb) + 3 * r;
     const double* qv = d.q + 3 * r;
     const D3 dd{__ldcg(db), __ldcg(db + 1), __ldcg(db + 2)}, qq{__ldcg(qv), __ldcg(qv + 1), __ldcg(qv + 2)};
-    st3(d.p, r, ld3(d.p, r) + al * dd);
-    const D3 rv = ld3(d.r, r) - al * (touched ? qq + qcv : qq);
+    st3(d.p, r, (MULTI ? ld3cg(d.p, r) : ld3(d.p, r)) + al * dd);
+    const D3 rv = (MULTI ? ld3cg(d.r, r) : ld3(d.r, r)) - al * (touched ? qq + qcv : qq);
     st3(d.r, r, rv);
     __syncwarp();
     const double rr = dot(rv, rv);
-    const D3 z = apply_pc64(d, r, kr, rv);
+    const D3 z = apply_pc64<MULTI>(d, r, kr, rv);
     PV<double>::set_z(d, r, z);
     last = env_reduce<2>(d, e, 0, cta, dot(rv, z), &rr, out);
   }
   if (last) {
-    const double rz_old = ENVS(d, e, S_RZ);
+    const double rz_old = __ldcg(&ENVS(d, e, S_RZ));
     ENVS(d, e, S_PBETA) = rz_old > 0.0 ? out[0] / rz_old : 0.0;
     ENVS(d, e, S_RZ) = out[0];
     ENVS(d, e, S_RR) = out[1];
     ENVS(d, e, S_DQC) = 0.0;
-    ENVI(d, e, I_PHASE) = 0;
-    const int it = ++ENVI(d, e, I_PCGIT);
-    ENVI(d, e, I_PCGTOT) += 1;
+    if constexpr (!MULTI) ENVI(d, e, I_PHASE) = 0;   // the multi kernel counts across its iterations
+    const int it = atomicAdd(&ENVI(d, e, I_PCGIT), 1) + 1;
+    atomicAdd(&ENVI(d, e, I_PCGTOT), 1);
     const double tol2 = d.pcg_tol * d.pcg_tol * ENVS(d, e, S_RR0);
     if (out[1] <= tol2 || it >= d.pcg_max || !(dq > 0.0)) {
       ENVI(d, e, I_PCG) = 0;
@@ -494,6 +508,10 @@ __device__ __forceinline__ void update_rows(const Dev& d, int e, int cta, double
       atomicAdd(d.pcg_ctl + C_DEAD, (unsigned)(env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8));
       atomicAdd(d.pcg_ctl + C_STOPROWS, (unsigned)env_row_ctas(d, e));
       atomicSub(d.pcg_ctl + C_LIVE, 1u);
+    }
+    if constexpr (MULTI) {
+      __threadfence();
+      atomicAdd(&ENVI(d, e, I_UPDK), 1);
     }
   }
 }
@@ -516,7 +534,10 @@ __device__ __forceinline__ void update_item_info(const Dev& d, int item, int* s_
 
 // the grid's last CTA after an iteration: next iteration, list upkeep,
 // loop condition.  Every CTA of the grid calls it once, after its items.
-__device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
+// iters: PCG iterations the launch ran; multi: the multi-iteration kernel
+// (its per-env iteration and product counts are reset for the next launch)
+__device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, int use_cond, unsigned window,
+                                  unsigned iters = 1u, bool multi = false) {
   __shared__ bool s_last;
   __shared__ bool s_rebuild;
   __syncthreads();
@@ -535,14 +556,23 @@ __device__ void pcg_iteration_end(const Dev& d, cudaGraphConditionalHandle h, in
     d.pcg_ctl[C_RTAKE] = 0;
     d.pcg_ctl[C_LIVEROWS] -= d.pcg_ctl[C_STOPROWS];
     d.pcg_ctl[C_STOPROWS] = 0;
-    d.pcg_ctl[C_ITER] += 1;
-    d.step_ctl[4] += 1u;
+    d.pcg_ctl[C_ITER] += iters;
+    d.step_ctl[4] += 1u;   // PCG launches
     const unsigned len = d.pcg_ctl[C_LEN];
     const unsigned dead = d.pcg_ctl[C_DEAD];
     const unsigned items = len ? (unsigned)(d.pcg_row_off[len] + d.pcg_pair_off[len]) : 0u;
     s_rebuild = dead > 0 && 4u * dead >= items;
   }
   __syncthreads();
+  if (multi) {
+    const int n_list = (int)d.pcg_ctl[C_LEN];
+    for (int i = threadIdx.x; i < n_list; i += blockDim.x) {
+      const int e = d.pcg_list[i];
+      ENVI(d, e, I_PHASE) = 0;
+      ENVI(d, e, I_UPDK) = 0;
+    }
+    __syncthreads();
+  }
   if (d.pcg_ctl[C_ABORT]) {
     // a wait of the fused kernel gave up (never expected): the envs still
     // solving end their step with IPC_ECUDA, their reductions and the
@@ -770,6 +800,108 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 :
   pcg_iteration_end(d, h, use_cond, window);
 }
 
+// ---- several PCG iterations in one launch (ipc_params.pcg_iters_per_launch
+// = W > 1, no rollout window): the per-env dataflow of k_pcg_iter carried
+// across iterations, so that envs do not line up on iteration boundaries.
+// Items are W rounds of [pair groups, mat-vec row items, update row items],
+// each env after env, taken in order from C_NEXT.  Env e's products of
+// iteration k wait until its update of iteration k - 1 is done (I_UPDK >= k,
+// counted by the env's last update CTA after a fence); its update items of
+// iteration k wait until its products of rounds 0..k are in (I_PHASE >=
+// (k + 1) x its pair groups and row items; I_PHASE counts across the
+// launch).  Every wait is on items with smaller indices, taken by running
+// CTAs, so every wait ends; an env that stops ends the waits of its later
+// items (they see I_PCG = 0 and skip).  Within the launch z, the direction
+// buffers, p, r and the env's scalars are written by other CTAs and read
+// again, so these reads go through L2 (the CG / MULTI forms of the shared
+// device functions).  Waits are bounded as in k_pcg_iter.
+__device__ __forceinline__ bool multi_wait(const Dev& d, int e, int which, int need) {
+  volatile int* pcg = &ENVI(d, e, I_PCG);
+  volatile int* cnt = &ENVI(d, e, which);
+  volatile unsigned* ab = d.pcg_ctl + C_ABORT;
+  if (!*pcg) return false;
+  if (*cnt < need) {
+    const long long t0 = clock64();
+    while (*cnt < need) {
+      if (!*pcg || *ab) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        atomicExch(d.pcg_ctl + C_ABORT, 1u);
+        return false;
+      }
+      __nanosleep(100);
+    }
+  }
+  __threadfence();
+  return *pcg != 0;   // an env that stopped in the iteration waited for skips
+}
+
+template <class HT, int U>
+__global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
+    k_pcg_multi(Dev d, cudaGraphConditionalHandle h, int use_cond, unsigned window, int W) {
+  __shared__ int s_kind, s_e, s_cta, s_nb;
+  __shared__ double s_beta, s_dq, s_al;
+  __shared__ uint8_t s_tag;
+  const int n_list = (int)d.pcg_ctl[C_LEN];
+  const int n_rows = d.pcg_row_off[n_list];
+  const int n_pairs = d.pcg_pair_off[n_list];
+  const int per = n_pairs + 2 * n_rows;
+  const unsigned n_total = (unsigned)W * (unsigned)per;
+  const unsigned it0 = d.pcg_ctl[C_ITER];
+  for (;;) {
+    __syncthreads();  // the previous item is done with the shared item data
+    if (threadIdx.x == 0) {
+      const unsigned it = atomicAdd(d.pcg_ctl + C_NEXT, 1u);
+      int kind = -1;
+      if (it < n_total) {
+        const int k = (int)(it / (unsigned)per), j = (int)(it % (unsigned)per);
+        s_nb = (int)((it0 + (unsigned)k + 1u) & 1u);
+        int2 iv;
+        if (j < n_pairs) {
+          iv = d.pcg_pitem[j];                         // (env, group of 8 active pairs)
+          kind = 0;
+        } else {
+          iv = d.pcg_item[j < n_pairs + n_rows ? j - n_pairs : j - n_pairs - n_rows];   // (env, row CTA)
+          kind = j < n_pairs + n_rows ? 1 : 2;
+        }
+        if (!IPC_CHECK(d.check_word, (unsigned)iv.x < (unsigned)d.n_envs, CHK_PCG_ITEM, (long long)it)) {
+          kind = 3;
+        } else {
+          const int e = iv.x;
+          s_e = e;
+          s_cta = iv.y;
+          const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+          if (!multi_wait(d, e, kind < 2 ? I_UPDK : I_PHASE, kind < 2 ? k : (k + 1) * need)) {
+            kind = 3;                                  // the env stopped (or a wait gave up)
+          } else if (kind < 2) {
+            s_beta = __ldcg(&ENVS(d, e, S_PBETA));
+          } else {
+            const double dq = __ldcg(&ENVS(d, e, S_DQ)) + __ldcg(&ENVS(d, e, S_DQC));
+            s_dq = dq;
+            s_al = dq > 0.0 ? __ldcg(&ENVS(d, e, S_RZ)) / dq : 0.0;
+            s_tag = touch_tag(d, e);
+          }
+        }
+      }
+      s_kind = kind;
+    }
+    __syncthreads();
+    const int kind = s_kind;
+    if (kind < 0) break;
+    if (kind == 3) continue;
+    const int e = s_e, nb = s_nb, ob = nb ^ 1;
+    if (kind == 0) {
+      matvec_pairs<HT, true>(d, e, s_cta, (HT)s_beta, ob);
+      phase_signal(d, e, false);
+    } else if (kind == 1) {
+      matvec_rows<HT, U, true>(d, e, s_cta, (HT)s_beta, ob, nb);
+      phase_signal(d, e, false);
+    } else {
+      update_rows<HT, true>(d, e, s_cta, s_dq, s_al, s_tag, nb);
+    }
+  }
+  pcg_iteration_end(d, h, use_cond, window, (unsigned)W, true);
+}
+
 // diagnostics: the direction v (FP64 rows staged in Dev::z) as z with
 // beta = 0 and d_{-1} = 0, so that one mat-vec item computes H v
 template <class HT>
@@ -859,6 +991,17 @@ static void* pcg_iter_fn(int unroll, int bound) {
 
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
   const bool u4 = d.spmv_unroll == 4 || d.spmv_unroll == 8;
+  if (pcg_iters_per_launch(d, window) > 1) {
+    const int g = d.pcg_grid_multi, w = d.pcg_multi;
+    if (d.prec) {
+      if (u4) k_pcg_multi<float, 4><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+      else k_pcg_multi<float, 2><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+    } else {
+      if (u4) k_pcg_multi<double, 4><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+      else k_pcg_multi<double, 2><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+    }
+    return 1;
+  }
   const int g = d.pcg_grid_fused;
   const int b = d.pcg_iter_bound;
   if (d.prec) {
@@ -879,6 +1022,22 @@ int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, 
     }
   }
   return 1;
+}
+
+// PCG iterations one launch of the fused kernel runs: pcg_multi, or 1
+// inside a rollout window (which counts single iterations)
+int pcg_iters_per_launch(const Dev& d, unsigned window) {
+  return (d.pcg_fused && !(d.fr_mu > 0.0) && d.pcg_multi > 1 && window == 0xffffffffu) ? d.pcg_multi : 1;
+}
+
+// resident CTAs per SM of the multi-iteration kernel
+int pcg_multi_ctas_per_sm(int prec, int unroll) {
+  int a = 0;
+  const bool u4 = unroll == 4 || unroll == 8;
+  const void* f = prec ? (u4 ? (const void*)k_pcg_multi<float, 4> : (const void*)k_pcg_multi<float, 2>)
+                       : (u4 ? (const void*)k_pcg_multi<double, 4> : (const void*)k_pcg_multi<double, 2>);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, 128, 0);
+  return a > 0 ? a : 1;
 }
 
 // resident CTAs per SM of the fused iteration kernel

@@ -17,6 +17,11 @@ namespace ipc {
 
 template <class HT> struct PV;
 
+// a row of three doubles through L2 only
+__device__ __forceinline__ D3 ld3cg(const double* p, int i) {
+  return D3{__ldcg(p + 3 * i), __ldcg(p + 3 * i + 1), __ldcg(p + 3 * i + 2)};
+}
+
 template <> struct PV<double> {
   static __device__ __forceinline__ double* dbuf(const Dev& d, int b) { return b ? d.db : d.d; }
   static __device__ __forceinline__ D3 z(const Dev& d, int r) { return ld3(d.z, r); }
@@ -26,8 +31,17 @@ template <> struct PV<double> {
   static __device__ __forceinline__ D3 q(const Dev& d, int r) { return ld3(d.q, r); }
   static __device__ __forceinline__ void set_q(const Dev& d, int r, D3 v) { st3(d.q, r, v); }
   // z and the previous direction of column c as the mat-vec gathers them
-  static __device__ __forceinline__ V3<double> gather_z(const Dev& d, int c) { return ld3(d.z, c); }
-  static __device__ __forceinline__ V3<double> gather_dir(const Dev& d, int c, int b) { return ld3(dbuf(d, b), c); }
+  // (CG: through L2 only, for rows that other CTAs of the same launch wrote)
+  template <bool CG = false>
+  static __device__ __forceinline__ V3<double> gather_z(const Dev& d, int c) {
+    if constexpr (CG) return ld3cg(d.z, c);
+    return ld3(d.z, c);
+  }
+  template <bool CG = false>
+  static __device__ __forceinline__ V3<double> gather_dir(const Dev& d, int c, int b) {
+    if constexpr (CG) return ld3cg(dbuf(d, b), c);
+    return ld3(dbuf(d, b), c);
+  }
 };
 
 template <> struct PV<float> {
@@ -42,12 +56,14 @@ template <> struct PV<float> {
   static __device__ __forceinline__ void set_dir(const Dev& d, int r, int b, D3 v) { dbuf(d, b)[r] = to4(v); }
   static __device__ __forceinline__ D3 q(const Dev& d, int r) { return f4(d.q4[r]); }
   static __device__ __forceinline__ void set_q(const Dev& d, int r, D3 v) { d.q4[r] = to4(v); }
+  template <bool CG = false>
   static __device__ __forceinline__ V3<float> gather_z(const Dev& d, int c) {
-    const float4 v = __ldg(d.z4 + c);
+    const float4 v = CG ? __ldcg(d.z4 + c) : __ldg(d.z4 + c);
     return V3<float>{v.x, v.y, v.z};
   }
+  template <bool CG = false>
   static __device__ __forceinline__ V3<float> gather_dir(const Dev& d, int c, int b) {
-    const float4 v = __ldg(dbuf(d, b) + c);
+    const float4 v = CG ? __ldcg(dbuf(d, b) + c) : __ldg(dbuf(d, b) + c);
     return V3<float>{v.x, v.y, v.z};
   }
 };

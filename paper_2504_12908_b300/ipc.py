@@ -33,7 +33,7 @@ class ipc_params(C.Structure):
                 ("al_kappa", C.c_double), ("al_max", C.c_int), ("ee_mollifier", C.c_double),
                 ("precision", C.c_int), ("max_pairs_per_env", C.c_int), ("friction_mu", C.c_double),
                 ("friction_eps_v", C.c_double), ("newton_abs_after", C.c_int),
-                ("rollout_pcg_window", C.c_int), ("pcg_fused", C.c_int)]
+                ("rollout_pcg_window", C.c_int), ("pcg_fused", C.c_int), ("pcg_iters_per_launch", C.c_int)]
 
 
 class ipc_scene_desc(C.Structure):
@@ -174,6 +174,7 @@ def params_from(p) -> ipc_params:
     out.newton_abs_after = int(getattr(p, "newton_abs_after", 1000000))
     out.rollout_pcg_window = int(getattr(p, "rollout_pcg_window", 0))
     out.pcg_fused = int(getattr(p, "pcg_fused", 1))
+    out.pcg_iters_per_launch = int(getattr(p, "pcg_iters_per_launch", 1))
     return out
 
 

@@ -45,10 +45,11 @@ def _table(g, scs, k0, n):
     return t
 
 
-def _run(prm, fused, rollout, stream=True):
+def _run(prm, fused, rollout, stream=True, ipl=1):
     scs = _batch()
     p = type(prm)(**prm.__dict__)
     p.pcg_fused = fused
+    p.pcg_iters_per_launch = ipl
     g = ipc.Envs([sc.scene for sc in scs], p, stream=torch.cuda.Stream() if stream else None)
     tab = _table(g, scs, 0, K)
     pcg = 0
@@ -76,14 +77,17 @@ def _close(sa, sb, bound):
     assert worst <= bound * K, worst
 
 
-@pytest.mark.parametrize("fused,rollout,stream", [(1, False, True), (1, True, True), (1, False, False),
-                                                  (2, False, True), (2, True, True)])
-def test_fused_matches_three_kernels_fp64(fused, rollout, stream):
+@pytest.mark.parametrize("fused,rollout,stream,ipl", [(1, False, True, 1), (1, True, True, 1), (1, False, False, 1),
+                                                      (2, False, True, 1), (2, True, True, 1),
+                                                      (1, False, True, 4), (1, True, True, 4), (1, False, False, 3),
+                                                      (1, True, True, 16)])
+def test_fused_matches_three_kernels_fp64(fused, rollout, stream, ipl):
     """FP64 at the parity tolerances: lock-step graphs, the rollout graph,
     and host-driven steps (no stream: plain launches); update items in
-    ready order (1) and in env order (2)."""
+    ready order (1) and in env order (2); ipl > 1: that many iterations
+    per launch (k_pcg_multi, the per-env dataflow across iterations)."""
     prm = scenes.SolverParams().parity()
-    st_a, xa, pa = _run(prm, fused, rollout, stream)
+    st_a, xa, pa = _run(prm, fused, rollout, stream, ipl)
     st_b, xb, pb = _run(prm, 0, rollout, stream)
     assert np.all(st_a == 0) and np.all(st_b == 0)
     assert abs(pa - pb) <= 0.02 * pb, (pa, pb)
@@ -103,11 +107,24 @@ def test_fused_matches_three_kernels_mixed():
     run the fused path by default."""
     prm = scenes.SolverParams()
     prm.precision = 1
-    st_a, xa, pa = _run(prm, 1, True)
+    st_a, xa, pa = _run(prm, 1, True, ipl=4)
     st_b, xb, pb = _run(prm, 0, True)
     assert np.all(st_a == 0) and np.all(st_b == 0)
     assert 0.5 * pb <= pa <= 2.0 * pb, (pa, pb)
     _close(xa, xb, 1e-3)
+
+
+def test_multi_iteration_rollout_window_runs_single_iterations():
+    """Inside a rollout window (which counts single iterations) the fused
+    kernel runs one iteration per launch whatever pcg_iters_per_launch
+    says: the same end states as the three kernels with that window."""
+    prm = scenes.SolverParams().parity()
+    prm.rollout_pcg_window = 2
+    st_a, xa, pa = _run(prm, 1, True, ipl=4)
+    st_b, xb, pb = _run(prm, 0, True)
+    assert np.all(st_a == 0) and np.all(st_b == 0)
+    assert abs(pa - pb) <= 0.02 * pb, (pa, pb)
+    _close(xa, xb, 1e-6)
 
 
 def test_fused_profile_class():
