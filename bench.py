@@ -483,16 +483,17 @@ def matvec_traffic_per_launch(env_iters_per_launch):
     return MATVEC_TRAFFIC["bytes"] / MATVEC_TRAFFIC["env_iters"] * env_iters_per_launch
 
 
-# The same for the fused PCG iteration kernel (k_pcg_iter: contact terms,
-# SELL mat-vec and update in one launch): DRAM bytes of its first launch
-# in the 24-env case (every env in its first PCG iteration), scaled by
-# env-iterations.
-PCG_ITER_TRAFFIC = {"env_iters": 24, "bytes": 136305664 + 17448192, "source_sha256": "58b0a9853d87c63cc1bcabf17f571b610e6f0b0c8670ecc9dc16ff5114fac6b5"}
+# The same for the fused PCG kernel as the bench runs it (k_pcg_multi: 8
+# iterations of contact terms, SELL mat-vec and update per launch): DRAM
+# bytes of its third launch in the 24-env case (mid-solve, ~180 of its 192
+# env-iterations run: counted from its FP64 instructions at 23.25 per row
+# and iteration), scaled by env-iterations.
+PCG_ITER_TRAFFIC = {"env_iters": 179.73, "bytes": 1059331584, "source_sha256": "7f0f1b78b02086a5b365e3f8ca9700a9e90906c88e847fab1202935471ae9e67"}
 PCG_ITER_PARTS = [("pcgvec.cuh", None), ("fpconv.cuh", None),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_rows("),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_pairs("),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void update_rows("),
-                  ("kernels_pcg.cu", "k_pcg_iter(Dev d")]
+                  ("kernels_pcg.cu", "k_pcg_multi(Dev d")]
 
 
 def pcg_iter_traffic_per_launch(env_iters_per_launch):
@@ -510,7 +511,7 @@ def pcg_iter_traffic_per_launch(env_iters_per_launch):
 FP64_FLOPS_PER_UNIT = {
     "tet_elastic": (242.0, "0657c712ffa87872172c39c9433c5f8809afe6af23538ae1311894e1c2e972ad"),
     "body_abd": (4920.0, "176a85a7dc5c0d3c979f3de3ea30e78cb61eee8f864c11b05d2bc3a3ad460833"),
-    "pcg_iter": (23.25, "58b0a9853d87c63cc1bcabf17f571b610e6f0b0c8670ecc9dc16ff5114fac6b5"),
+    "pcg_iter": (23.25, "7f0f1b78b02086a5b365e3f8ca9700a9e90906c88e847fab1202935471ae9e67"),
 }
 ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "body_abd": "body per Newton iteration",
             "pcg_iter": "row per PCG iteration"}

@@ -120,7 +120,7 @@ typedef struct {
                              update).  Runs with friction use the three
                              kernels.  The same arithmetic in every form.  */
   int pcg_iters_per_launch; /* fused kernel: PCG iterations per launch, 1
-                             (default) to 16.  Above 1 an env's next
+                             to 16 (default 8).  Above 1 an env's next
                              products wait only for its own update, so
                              envs do not line up on iteration boundaries
                              (not inside a rollout window, which counts

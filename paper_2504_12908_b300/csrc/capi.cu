@@ -911,7 +911,7 @@ void ipc_default_params(ipc_params* p) {
   p->newton_abs_after = 1000000;
   p->rollout_pcg_window = 0;
   p->pcg_fused = 1;
-  p->pcg_iters_per_launch = 1;
+  p->pcg_iters_per_launch = 8;
 }
 
 ipc_status ipc_workspace_bytes(const ipc_scene_desc* scenes, int n_envs, const ipc_params* prm, size_t* bytes) {

@@ -174,7 +174,7 @@ def params_from(p) -> ipc_params:
     out.newton_abs_after = int(getattr(p, "newton_abs_after", 1000000))
     out.rollout_pcg_window = int(getattr(p, "rollout_pcg_window", 0))
     out.pcg_fused = int(getattr(p, "pcg_fused", 1))
-    out.pcg_iters_per_launch = int(getattr(p, "pcg_iters_per_launch", 1))
+    out.pcg_iters_per_launch = int(getattr(p, "pcg_iters_per_launch", 8))
     return out
 
 

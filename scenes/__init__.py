@@ -101,7 +101,7 @@ class SolverParams:
     newton_abs_after: int = 1000000  # Newton iterations that clamp negative eigenvalues; |lambda| after
     rollout_pcg_window: int = 0     # rollout: PCG iterations per loop iteration (0: whole solves)
     pcg_fused: int = 1              # 1 / 2: one persistent kernel per PCG iteration (ready / env order); 0: three
-    pcg_iters_per_launch: int = 1   # fused kernel: PCG iterations per launch (> 1: no line-up per iteration)
+    pcg_iters_per_launch: int = 8   # fused kernel: PCG iterations per launch (> 1: no line-up per iteration)
 
     def parity(self) -> "SolverParams":
         """Tighter tolerances used when two implementations are compared."""
