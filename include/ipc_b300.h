@@ -177,9 +177,11 @@ typedef struct {
   long long loop_iters;       /* device loop iterations of the call's graph:
                                  Newton loop (ipc_step) or rollout loop; 0
                                  for host-driven calls                     */
-  long long pcg_launches;     /* PCG iterations the graph ran (each serves
-                                 every env in PCG at the time); 0 for
-                                 host-driven calls                         */
+  long long pcg_launches;     /* PCG kernel launches the graph ran (each
+                                 runs pcg_iters_per_launch iterations of
+                                 every env in PCG at the time, one inside
+                                 a rollout window); 0 for host-driven
+                                 calls                                     */
   long long act_pair_iters;   /* active contact pairs x PCG iterations,
                                  summed over the solves and envs (the work
                                  of the contact mat-vec)                   */
