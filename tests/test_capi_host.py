@@ -44,6 +44,29 @@ def test_default_params(L):
     p = ipc.ipc_params()
     L.ipc_default_params(C.byref(p))
     assert p.dt == 1e-3 and p.dhat == 1e-4 and p.kappa == 1e6 and p.gravity[2] == -9.81
+    # PCG scheduling defaults: whole solves in a rollout, the fused kernel,
+    # 8 iterations per launch (the binding's SolverParams mirrors them)
+    assert p.rollout_pcg_window == 0 and p.pcg_fused == 1 and p.pcg_iters_per_launch == 8
+    sp = scenes.SolverParams()
+    assert (sp.rollout_pcg_window, sp.pcg_fused, sp.pcg_iters_per_launch) == (0, 1, 8)
+
+
+@pytest.mark.parametrize("field,value", [("pcg_fused", 3), ("pcg_fused", -1), ("pcg_iters_per_launch", 0),
+                                         ("pcg_iters_per_launch", 17), ("rollout_pcg_window", 3),
+                                         ("rollout_pcg_window", 1), ("newton_max", 0)])
+def test_create_rejects_bad_scheduling_params(L, field, value):
+    """ipc_create_envs checks its parameters before it touches the device:
+    out-of-range scheduling parameters give IPC_EINVAL (a placeholder
+    workspace address suffices, nothing is written)."""
+    sc = scenes.config0()
+    prm = ipc.params_from(sc.params)
+    setattr(prm, field, value)
+    arr, keep = ipc._descs([sc.scene])
+    ctx = C.c_void_p()
+    fake = C.c_void_p(1 << 20)   # 256-byte aligned, never dereferenced on this path
+    st = L.ipc_create_envs(arr, 1, C.byref(prm), fake, C.c_size_t(1 << 20), None, C.byref(ctx))
+    assert st == ipc.IPC_EINVAL
+    assert not ctx.value
 
 
 def test_workspace_bytes_scales_with_envs(L):
