@@ -241,7 +241,9 @@ typedef struct {
   float assemble_us[3];   /* mean assembly time per launch for 64, 128, 256, us        */
   int pairs_ctas_per_sm;  /* broad phase: CTAs per SM of the candidate-pair search     */
   float pairs_us[3];      /* mean broad-phase time per search for 4, 8, 16 CTAs / SM   */
-  int pcg_iter_bound;     /* fused PCG iteration kernel: register bound on (1) or off  */
+  int pcg_iter_bound;     /* single-iteration fused PCG kernel (one iteration per
+                             launch: inside rollout windows): register bound on (1)
+                             or off                                                  */
   float pcg_iter_us[2];   /* mean time per fused iteration with the bound on, off, us
                              (0 when the fused kernel is not in use: pcg_fused = 0
                              or friction on)                                        */

@@ -1110,11 +1110,19 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
   };
   int best_b = 1;
   if (d.pcg_fused && !(d.fr_mu > 0.0)) {
+    // the bound applies to the single-iteration kernel (k_pcg_iter: one
+    // iteration per launch, inside rollout windows), so that is what is timed
+    const int multi = d.pcg_multi;
+    d.pcg_multi = 1;
     for (int b = 1; b >= 0; --b) {
       d.pcg_iter_bound = b;
       d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, b);
-      if ((st = time_fused(&t.pcg_iter_us[1 - b])) != IPC_OK) return st;
+      if ((st = time_fused(&t.pcg_iter_us[1 - b])) != IPC_OK) {
+        d.pcg_multi = multi;
+        return st;
+      }
     }
+    d.pcg_multi = multi;
     if (t.pcg_iter_us[1] < 0.95f * t.pcg_iter_us[0]) best_b = 0;
     CK(cudaMemsetAsync(d.qc, 0, 3 * sizeof(double) * (size_t)d.n_rows, s));
     if ((st = select_envs(ctx, {}, I_NEWT)) != IPC_OK) return st;
