@@ -488,7 +488,7 @@ def matvec_traffic_per_launch(env_iters_per_launch):
 # bytes of its third launch in the 24-env case (mid-solve, ~180 of its 192
 # env-iterations run: counted from its FP64 instructions at 23.25 per row
 # and iteration), scaled by env-iterations.
-PCG_ITER_TRAFFIC = {"env_iters": 179.73, "bytes": 1059331584, "source_sha256": "7f0f1b78b02086a5b365e3f8ca9700a9e90906c88e847fab1202935471ae9e67"}
+PCG_ITER_TRAFFIC = {"env_iters": 179.73, "bytes": 922980096 + 133039616, "source_sha256": "32b2347407bcfb0359651f38d18ec402c9e53d4005e7196b8e55ac856ae6c319"}
 PCG_ITER_PARTS = [("pcgvec.cuh", None), ("fpconv.cuh", None),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_rows("),
                   ("kernels_pcg.cu", "__device__ __forceinline__ void matvec_pairs("),
@@ -511,7 +511,7 @@ def pcg_iter_traffic_per_launch(env_iters_per_launch):
 FP64_FLOPS_PER_UNIT = {
     "tet_elastic": (242.0, "0657c712ffa87872172c39c9433c5f8809afe6af23538ae1311894e1c2e972ad"),
     "body_abd": (4920.0, "176a85a7dc5c0d3c979f3de3ea30e78cb61eee8f864c11b05d2bc3a3ad460833"),
-    "pcg_iter": (23.25, "7f0f1b78b02086a5b365e3f8ca9700a9e90906c88e847fab1202935471ae9e67"),
+    "pcg_iter": (23.25, "32b2347407bcfb0359651f38d18ec402c9e53d4005e7196b8e55ac856ae6c319"),
 }
 ALU_UNIT = {"tet_elastic": "tet per Newton iteration", "body_abd": "body per Newton iteration",
             "pcg_iter": "row per PCG iteration"}

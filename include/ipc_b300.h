@@ -117,8 +117,9 @@ typedef struct {
                              ready); 2: the same kernel taking the update
                              items in env order (each waits for its env);
                              0: three kernels (the mat-vecs, then the
-                             update).  Runs with friction use the three
-                             kernels.  The same arithmetic in every form.  */
+                             update).  With friction the fused kernels take
+                             the friction records among an env's products.
+                             The same arithmetic in every form.            */
   int pcg_iters_per_launch; /* fused kernel: PCG iterations per launch, 1
                              to 16 (default 8).  Above 1 an env's next
                              products wait only for its own update, so

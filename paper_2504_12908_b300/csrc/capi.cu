@@ -268,6 +268,8 @@ void carve(const Pack& pk, const ipc_params& prm, Carver& c, Dev& d, Extra& ex,
   d.pcg_row_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_item = c.take<int2>((size_t)pk.n_rows / 128);
   d.pcg_pitem = c.take<int2>((size_t)pk.n_pairs_cap / 8 + (size_t)pk.n_envs);
+  d.pcg_fitem = c.take<int2>((size_t)pk.n_pairs_cap / 128 + (size_t)pk.n_envs);
+  d.pcg_fric_off = c.take<int>((size_t)pk.n_envs + 1);
   d.pcg_ctl = c.take<unsigned int>(16);
   d.pcg_ritem = c.take<int>((size_t)pk.n_rows / 128);
   d.step_ctl = c.take<unsigned int>(8);
@@ -458,8 +460,8 @@ int pcg_iteration(ipc_ctx* ctx, cudaStream_t s, cudaGraphConditionalHandle h = 0
                   unsigned window = 0xffffffffu) {
   const Dev& d = ctx->dev;
   long long l0 = ctx->launches;
-  if (d.pcg_fused && !(d.fr_mu > 0.0)) {
-    // the whole iteration as one persistent kernel
+  if (d.pcg_fused) {
+    // the whole iteration (with friction terms) as one persistent kernel
     KL(ctx, KC_PCGITER, [&] { return launch_pcg_iter(d, s, h, use_cond, window); }, s);
     return (int)(ctx->launches - l0);
   }
@@ -987,8 +989,8 @@ ipc_status ipc_create_envs(const ipc_scene_desc* scenes, int n_envs, const ipc_p
   CK(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device));
   ctx->dev.pcg_grid = ctx->n_sm * pcg_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
   ctx->dev.pcg_grid_fused =
-      ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll, ctx->dev.pcg_iter_bound);
-  ctx->dev.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll);
+      ctx->n_sm * pcg_iter_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll, ctx->dev.pcg_iter_bound, ctx->dev.fr_mu > 0.0);
+  ctx->dev.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(ctx->dev.prec, ctx->dev.spmv_unroll, ctx->dev.fr_mu > 0.0);
   ctx->dev.pcg_grid_pairs = ctx->n_sm * 4;
   CK(cudaMemsetAsync(ctx->dev.check_word, 0, 2 * sizeof(unsigned long long), ctx->stream));
   CK(cudaMemsetAsync(ctx->dev.pcg_ritem, 0xff, sizeof(int) * (size_t)(ctx->pk.n_rows / 128), ctx->stream));
@@ -1109,14 +1111,14 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
     return IPC_OK;
   };
   int best_b = 1;
-  if (d.pcg_fused && !(d.fr_mu > 0.0)) {
+  if (d.pcg_fused) {
     // the bound applies to the single-iteration kernel (k_pcg_iter: one
     // iteration per launch, inside rollout windows), so that is what is timed
     const int multi = d.pcg_multi;
     d.pcg_multi = 1;
     for (int b = 1; b >= 0; --b) {
       d.pcg_iter_bound = b;
-      d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, b);
+      d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, b, d.fr_mu > 0.0);
       if ((st = time_fused(&t.pcg_iter_us[1 - b])) != IPC_OK) {
         d.pcg_multi = multi;
         return st;
@@ -1130,8 +1132,8 @@ ipc_status ipc_autotune(ipc_ctx* ctx, int reps, ipc_tuning* out) {
     if ((st = select_envs(ctx, {}, I_DEC)) != IPC_OK) return st;
   }
   d.pcg_iter_bound = best_b;
-  d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, best_b);
-  d.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(d.prec, d.spmv_unroll);
+  d.pcg_grid_fused = ctx->n_sm * pcg_iter_ctas_per_sm(d.prec, d.spmv_unroll, best_b, d.fr_mu > 0.0);
+  d.pcg_grid_multi = ctx->n_sm * pcg_multi_ctas_per_sm(d.prec, d.spmv_unroll, d.fr_mu > 0.0);
   // gather assembly: 64, 128 or 256 threads per CTA, every env counted as
   // starting a Newton iteration (rewrites the SELL values from the stored
   // element blocks)

@@ -152,6 +152,8 @@ struct Dev {
   int* pcg_row_off;             // [n_envs + 1] prefix of their 128-row CTAs
   int2* pcg_item;               // per row item: (env, global row CTA)
   int2* pcg_pitem;              // per pair item: (env, group of 8 active pairs)
+  int2* pcg_fitem;              // per friction item: (env, group of 128 friction records)
+  int* pcg_fric_off;            // [n_envs + 1] prefix of the listed envs' friction items
   unsigned int* pcg_ctl;        // [0] CTAs arrived in the update kernel, [1] PCG iteration,
                                 // [2] envs in the list, [3] items of stopped envs, [4] envs
                                 // solving, [5..10] the fused kernels' counters (PcgCtl)

@@ -48,25 +48,38 @@ __device__ __forceinline__ bool row_is_body(uint8_t k) { return k == ROW_BODY ||
 
 __device__ __forceinline__ int env_row_ctas(const Dev& d, int e) { return (d.env_row_off[e + 1] - d.env_row_off[e]) >> 7; }
 __device__ __forceinline__ int env_active_pairs(const Dev& d, int e) { return min(ENVI(d, e, I_NACT), d.env_pair_cap[e]); }
+// friction records of env e in PCG (records of this step; none without friction)
+__device__ __forceinline__ int env_fric(const Dev& d, int e) {
+  return d.fr_mu > 0.0 ? min(ENVI(d, e, I_NFRIC), d.env_pair_cap[e]) : 0;
+}
+// the fused kernels' product items of env e per iteration: row items, groups
+// of 8 active pairs and (FR: the kernel variant for runs with friction)
+// groups of 128 friction records
+template <bool FR>
+__device__ __forceinline__ int env_products(const Dev& d, int e) {
+  if constexpr (FR) return env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8 + (env_fric(d, e) + 127) / 128;
+  return env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+}
 
 // Rebuild the work list from the envs' I_PCG flags (one CTA, blockDim a
 // multiple of 32): list order is env order; per listed env the prefix of
 // its 128-row items and of its groups of 8 active pairs.
 __device__ void build_list(const Dev& d) {
-  __shared__ int wsum[3][32];
-  __shared__ int carry[3];
+  __shared__ int wsum[4][32];
+  __shared__ int carry[4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x < 3) carry[threadIdx.x] = 0;
+  if (threadIdx.x < 4) carry[threadIdx.x] = 0;
   __syncthreads();
   for (int base = 0; base < d.n_envs; base += blockDim.x) {
     const int e = base + threadIdx.x;
     const bool on = e < d.n_envs && ENVI(d, e, I_PCG) != 0;
-    int v[3];
+    int v[4];
     v[0] = on ? 1 : 0;
     v[1] = on ? env_row_ctas(d, e) : 0;
     v[2] = on ? (env_active_pairs(d, e) + 7) / 8 : 0;
-    int inc[3];
-    for (int k = 0; k < 3; ++k) {
+    v[3] = on ? (env_fric(d, e) + 127) / 128 : 0;
+    int inc[4];
+    for (int k = 0; k < 4; ++k) {
       inc[k] = v[k];
       for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, inc[k], o);
@@ -76,7 +89,7 @@ __device__ void build_list(const Dev& d) {
     }
     __syncthreads();
     if (wid == 0)
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < 4; ++k) {
         const int w = lane < nw ? wsum[k][lane] : 0;
         int wi = w;
         for (int o = 1; o < 32; o <<= 1) {
@@ -86,12 +99,13 @@ __device__ void build_list(const Dev& d) {
         wsum[k][lane] = wi - w;  // exclusive warp offsets
       }
     __syncthreads();
-    int ex[3];
-    for (int k = 0; k < 3; ++k) ex[k] = carry[k] + wsum[k][wid] + inc[k] - v[k];
+    int ex[4];
+    for (int k = 0; k < 4; ++k) ex[k] = carry[k] + wsum[k][wid] + inc[k] - v[k];
     if (on) {
       d.pcg_list[ex[0]] = e;
       d.pcg_row_off[ex[0]] = ex[1];
       d.pcg_pair_off[ex[0]] = ex[2];
+      d.pcg_fric_off[ex[0]] = ex[3];
       // per item its env and global row CTA / pair group, so that a kernel
       // finds its item with one load instead of a search over the list
       const int cta0 = d.env_row_off[e] >> 7;
@@ -99,15 +113,17 @@ __device__ void build_list(const Dev& d) {
       ENVI(d, e, I_UPDK) = 0;
       for (int j = 0; j < v[1]; ++j) d.pcg_item[ex[1] + j] = make_int2(e, cta0 + j);
       for (int j = 0; j < v[2]; ++j) d.pcg_pitem[ex[2] + j] = make_int2(e, j);
+      for (int j = 0; j < v[3]; ++j) d.pcg_fitem[ex[3] + j] = make_int2(e, j);
     }
     __syncthreads();
     if (threadIdx.x == blockDim.x - 1)
-      for (int k = 0; k < 3; ++k) carry[k] = ex[k] + v[k];
+      for (int k = 0; k < 4; ++k) carry[k] = ex[k] + v[k];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     d.pcg_row_off[carry[0]] = carry[1];
     d.pcg_pair_off[carry[0]] = carry[2];
+    d.pcg_fric_off[carry[0]] = carry[3];
     d.pcg_ctl[C_LEN] = carry[0];
     d.pcg_ctl[C_LIVE] = carry[0];
     d.pcg_ctl[C_DEAD] = 0;
@@ -344,6 +360,63 @@ __device__ __forceinline__ void matvec_pairs(const Dev& d, int e, int g, HT beta
   }
   __syncthreads();
   if (threadIdx.x == 0) atomicAdd(&ENVS(d, e, S_DQC), sdq[0] + sdq[1] + sdq[2] + sdq[3]);
+  __syncthreads();
+}
+
+template <class HT>
+__device__ __forceinline__ D3 widen3(V3<HT> v) { return D3{(double)v.x, (double)v.y, (double)v.z}; }
+
+// ---- mat-vec item of the fused kernels: the lagged friction terms of 128
+// records of env e (group g), one thread per record (Sec. 3.2, App. A.3):
+// u = sum_i w_i d_k(point i), q_c += w_i S u per point, d_k.q part u.S.u.
+// d_k of the points is formed on the fly from z_k and d_{k-1} (the same
+// fused operation the mat-vec writes, so the same values the separate
+// friction kernel reads from the new direction buffer).
+template <class HT, bool CG = false>
+__device__ __forceinline__ void matvec_fric(const Dev& d, int e, int g, HT beta, int ob) {
+  __shared__ double sdq[32];
+  const int local = 128 * g + threadIdx.x;
+  double part = 0.0;
+  if (local < env_fric(d, e)) {
+    const int j = d.env_pair_off[e] + local;
+    const int4 v = d.fr_v[j];
+    const int cvs[4] = {v.x, v.y, v.z, v.w};
+    const double* w = d.fr_w + 4 * (long long)j;
+    D3 a{0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+      const int cv = cvs[i], row = d.cv_row[cv];
+      D3 u;
+      if (d.cv_body[cv] < 0) {
+        u = (d.row_kind[row] == ROW_PINNED) ? D3{0, 0, 0} : widen3(Dk<HT>::template row<CG>(d, row, beta, ob));
+      } else {
+        const D3 xb = ld3(d.cv_xbar, cv);
+        u = widen3(Dk<HT>::template row<CG>(d, row, beta, ob)) +
+            xb.x * widen3(Dk<HT>::template row<CG>(d, row + 1, beta, ob)) +
+            xb.y * widen3(Dk<HT>::template row<CG>(d, row + 2, beta, ob)) +
+            xb.z * widen3(Dk<HT>::template row<CG>(d, row + 3, beta, ob));
+      }
+      a = a + w[i] * u;
+    }
+    const double* S = d.fr_S + 6 * (long long)j;
+    const D3 t{S[0] * a.x + S[1] * a.y + S[2] * a.z, S[1] * a.x + S[3] * a.y + S[4] * a.z,
+               S[2] * a.x + S[4] * a.y + S[5] * a.z};
+    for (int i = 0; i < 4; ++i) {
+      const int cv = cvs[i], row = d.cv_row[cv];
+      const D3 gv = w[i] * t;
+      if (d.cv_body[cv] < 0) {
+        if (d.row_kind[row] != ROW_PINNED) atomic_add3(d.qc, row, gv);
+      } else {
+        const D3 xb = ld3(d.cv_xbar, cv);
+        atomic_add3(d.qc, row, gv);
+        atomic_add3(d.qc, row + 1, xb.x * gv);
+        atomic_add3(d.qc, row + 2, xb.y * gv);
+        atomic_add3(d.qc, row + 3, xb.z * gv);
+      }
+    }
+    part = dot(a, t);
+  }
+  part = block_sum(part, sdq);
+  if (threadIdx.x == 0) atomicAdd(&ENVS(d, e, S_DQC), part);
   __syncthreads();
 }
 
@@ -651,12 +724,13 @@ constexpr long long kWaitCycles = 2000000000ll;
 
 // end of a pair or mat-vec item of env e (every thread calls it); rq: the
 // ready-slot order (the env's last product publishes its update items)
+template <bool FR>
 __device__ __forceinline__ void phase_signal(const Dev& d, int e, bool rq) {
   __shared__ int s_pub;
   __threadfence();   // every thread: its stores and atomics of the item before the count
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+    const int need = env_products<FR>(d, e);
     const int old = atomicAdd(&ENVI(d, e, I_PHASE), 1);
     s_pub = rq && old == need - 1 ? (int)atomicAdd(d.pcg_ctl + C_RALLOC, (unsigned)env_row_ctas(d, e)) : -1;
   }
@@ -674,8 +748,9 @@ __device__ __forceinline__ void phase_signal(const Dev& d, int e, bool rq) {
 // thread 0, env order: waits until env e's pair and mat-vec items are
 // done (they were taken before this update item by running CTAs that wait
 // on nothing); false on abort
+template <bool FR>
 __device__ __forceinline__ bool phase_wait(const Dev& d, int e) {
-  const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
+  const int need = env_products<FR>(d, e);
   volatile int* ph = &ENVI(d, e, I_PHASE);
   volatile unsigned* ab = d.pcg_ctl + C_ABORT;
   if (*ph < need) {
@@ -720,8 +795,10 @@ __device__ __forceinline__ int take_ready(const Dev& d, unsigned n_upd) {
 // B = 1 bounds the registers so that the mat-vec items keep the separate
 // mat-vec kernel's occupancy (12 CTAs per SM in FP32, 6 in FP64; the pair
 // path spills a few words), B = 0 gives the pair path its registers (9
-// CTAs per SM in FP32, 5 in FP64); ipc_autotune picks one.
-template <class HT, int U, int B>
+// CTAs per SM in FP32, 5 in FP64); ipc_autotune picks one.  FR: the
+// variant for runs with friction (friction record groups among the
+// products).
+template <class HT, int U, int B, bool FR>
 __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 : 5))
     k_pcg_iter(Dev d, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
   __shared__ int s_item, s_e, s_cta;
@@ -730,7 +807,9 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 :
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_rows = d.pcg_row_off[n_list];
   const int n_pairs = d.pcg_pair_off[n_list];
-  const int n_a = n_pairs + n_rows;
+  const int n_fric = FR ? d.pcg_fric_off[n_list] : 0;
+  const int n_pf = n_pairs + n_fric;                 // pair groups, then friction groups, then rows
+  const int n_a = n_pf + n_rows;
   const unsigned n_upd = d.pcg_ctl[C_LIVEROWS];
   const bool rq = d.pcg_fused == 1;    // 1: ready-slot order, 2: env order
   const int nb = pcg_new_buf(d), ob = nb ^ 1;
@@ -751,7 +830,7 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 :
         // env order: the update item waits for its own env's products
         update_item_info(d, it - n_a, &s_e, &s_cta, &s_dq, &s_al, &s_tag);
         if (s_e >= 0) {
-          if (phase_wait(d, s_e)) {
+          if (phase_wait<FR>(d, s_e)) {
             const double dq = __ldcg(&ENVS(d, s_e, S_DQ)) + __ldcg(&ENVS(d, s_e, S_DQC));
             s_dq = dq;
             s_al = dq > 0.0 ? ENVS(d, s_e, S_RZ) / dq : 0.0;
@@ -770,10 +849,18 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 :
       if (!IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs, CHK_PCG_ITEM, item)) continue;
       if (!ENVI(d, it.x, I_PCG)) continue;
       matvec_pairs<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
-      phase_signal(d, it.x, rq);
+      phase_signal<FR>(d, it.x, rq);
+    } else if (item < n_pf) {
+      if constexpr (FR) {
+        const int2 it = d.pcg_fitem[item - n_pairs];   // (env, group of 128 friction records)
+        if (!IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs, CHK_PCG_ITEM, item)) continue;
+        if (!ENVI(d, it.x, I_PCG)) continue;
+        matvec_fric<HT>(d, it.x, it.y, (HT)ENVS(d, it.x, S_PBETA), ob);
+        phase_signal<FR>(d, it.x, rq);
+      }
     } else if (item < n_a) {
       if (threadIdx.x == 0) {
-        const int2 it = d.pcg_item[item - n_pairs];    // (env, row CTA)
+        const int2 it = d.pcg_item[item - n_pf];       // (env, row CTA)
         const bool in = IPC_CHECK(d.check_word, (unsigned)it.x < (unsigned)d.n_envs &&
                                   (unsigned)it.y < (unsigned)(d.n_rows >> 7), CHK_PCG_ITEM, item);
         s_e = in && ENVI(d, it.x, I_PCG) ? it.x : -1;
@@ -784,7 +871,7 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? (B ? 12 : 9) : (B ? 6 :
       const int e = s_e;
       if (e < 0) continue;
       matvec_rows<HT, U>(d, e, s_cta, (HT)s_beta, ob, nb);
-      phase_signal(d, e, rq);
+      phase_signal<FR>(d, e, rq);
     } else {
       products_left = false;
       // an update item whose env's products are all in (ready slot; in env
@@ -835,7 +922,7 @@ __device__ __forceinline__ bool multi_wait(const Dev& d, int e, int which, int n
   return *pcg != 0;   // an env that stopped in the iteration waited for skips
 }
 
-template <class HT, int U>
+template <class HT, int U, bool FR>
 __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
     k_pcg_multi(Dev d, cudaGraphConditionalHandle h, int use_cond, unsigned window, int W) {
   __shared__ int s_kind, s_e, s_cta, s_nb;
@@ -844,9 +931,12 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
   const int n_list = (int)d.pcg_ctl[C_LEN];
   const int n_rows = d.pcg_row_off[n_list];
   const int n_pairs = d.pcg_pair_off[n_list];
-  const int per = n_pairs + 2 * n_rows;
+  const int n_fric = FR ? d.pcg_fric_off[n_list] : 0;
+  const int n_pf = n_pairs + n_fric;
+  const int per = n_pf + 2 * n_rows;                 // a round: pairs, friction, rows, updates
   const unsigned n_total = (unsigned)W * (unsigned)per;
   const unsigned it0 = d.pcg_ctl[C_ITER];
+  enum { K_PAIRS = 0, K_FRIC, K_ROWS, K_UPDATE, K_SKIP };
   for (;;) {
     __syncthreads();  // the previous item is done with the shared item data
     if (threadIdx.x == 0) {
@@ -858,21 +948,24 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
         int2 iv;
         if (j < n_pairs) {
           iv = d.pcg_pitem[j];                         // (env, group of 8 active pairs)
-          kind = 0;
+          kind = K_PAIRS;
+        } else if (j < n_pf) {
+          iv = d.pcg_fitem[j - n_pairs];               // (env, group of 128 friction records)
+          kind = K_FRIC;
         } else {
-          iv = d.pcg_item[j < n_pairs + n_rows ? j - n_pairs : j - n_pairs - n_rows];   // (env, row CTA)
-          kind = j < n_pairs + n_rows ? 1 : 2;
+          iv = d.pcg_item[j < n_pf + n_rows ? j - n_pf : j - n_pf - n_rows];   // (env, row CTA)
+          kind = j < n_pf + n_rows ? K_ROWS : K_UPDATE;
         }
         if (!IPC_CHECK(d.check_word, (unsigned)iv.x < (unsigned)d.n_envs, CHK_PCG_ITEM, (long long)it)) {
-          kind = 3;
+          kind = K_SKIP;
         } else {
           const int e = iv.x;
           s_e = e;
           s_cta = iv.y;
-          const int need = env_row_ctas(d, e) + (env_active_pairs(d, e) + 7) / 8;
-          if (!multi_wait(d, e, kind < 2 ? I_UPDK : I_PHASE, kind < 2 ? k : (k + 1) * need)) {
-            kind = 3;                                  // the env stopped (or a wait gave up)
-          } else if (kind < 2) {
+          const bool product = kind != K_UPDATE;
+          if (!multi_wait(d, e, product ? I_UPDK : I_PHASE, product ? k : (k + 1) * env_products<FR>(d, e))) {
+            kind = K_SKIP;                             // the env stopped (or a wait gave up)
+          } else if (product) {
             s_beta = __ldcg(&ENVS(d, e, S_PBETA));
           } else {
             const double dq = __ldcg(&ENVS(d, e, S_DQ)) + __ldcg(&ENVS(d, e, S_DQC));
@@ -887,14 +980,19 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
     __syncthreads();
     const int kind = s_kind;
     if (kind < 0) break;
-    if (kind == 3) continue;
+    if (kind == K_SKIP) continue;
     const int e = s_e, nb = s_nb, ob = nb ^ 1;
-    if (kind == 0) {
+    if (kind == K_PAIRS) {
       matvec_pairs<HT, true>(d, e, s_cta, (HT)s_beta, ob);
-      phase_signal(d, e, false);
-    } else if (kind == 1) {
+      phase_signal<FR>(d, e, false);
+    } else if (kind == K_FRIC) {
+      if constexpr (FR) {
+        matvec_fric<HT, true>(d, e, s_cta, (HT)s_beta, ob);
+        phase_signal<FR>(d, e, false);
+      }
+    } else if (kind == K_ROWS) {
       matvec_rows<HT, U, true>(d, e, s_cta, (HT)s_beta, ob, nb);
-      phase_signal(d, e, false);
+      phase_signal<FR>(d, e, false);
     } else {
       update_rows<HT, true>(d, e, s_cta, s_dq, s_al, s_tag, nb);
     }
@@ -980,46 +1078,48 @@ int launch_debug_q_to_rows(const Dev& d, cudaStream_t s) {
 }
 
 // resident CTAs per SM of the persistent PCG kernels (the smaller of the two)
-// the fused kernel's variant: slots in flight 2 or 4 (an 8-slot choice of
-// the mat-vec runs the fused kernel with 4), register bound on or off
-template <class HT>
-static void* pcg_iter_fn(int unroll, int bound) {
-  const bool u4 = unroll == 4 || unroll == 8;
-  if (bound) return u4 ? (void*)k_pcg_iter<HT, 4, 1> : (void*)k_pcg_iter<HT, 2, 1>;
-  return u4 ? (void*)k_pcg_iter<HT, 4, 0> : (void*)k_pcg_iter<HT, 2, 0>;
+// the fused kernels' variants: slots in flight 2 or 4 (an 8-slot choice of
+// the mat-vec runs the fused kernels with 4), register bound on or off
+// (single-iteration kernel), friction items or none (runs with friction)
+template <class HT, bool FR>
+static const void* pcg_iter_fn_t(bool u4, int bound) {
+  if (bound) return u4 ? (const void*)k_pcg_iter<HT, 4, 1, FR> : (const void*)k_pcg_iter<HT, 2, 1, FR>;
+  return u4 ? (const void*)k_pcg_iter<HT, 4, 0, FR> : (const void*)k_pcg_iter<HT, 2, 0, FR>;
+}
+template <class HT, bool FR>
+static const void* pcg_multi_fn_t(bool u4) {
+  return u4 ? (const void*)k_pcg_multi<HT, 4, FR> : (const void*)k_pcg_multi<HT, 2, FR>;
+}
+static bool unroll4(int unroll) { return unroll == 4 || unroll == 8; }
+
+template <class HT, bool FR>
+static void launch_iter_t(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                          unsigned window) {
+  const bool u4 = unroll4(d.spmv_unroll);
+  if (pcg_iters_per_launch(d, window) > 1) {
+    const int g = d.pcg_grid_multi, w = d.pcg_multi;
+    if (u4) k_pcg_multi<HT, 4, FR><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+    else k_pcg_multi<HT, 2, FR><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
+    return;
+  }
+  const int g = d.pcg_grid_fused;
+  if (d.pcg_iter_bound) {
+    if (u4) k_pcg_iter<HT, 4, 1, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else k_pcg_iter<HT, 2, 1, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
+  } else {
+    if (u4) k_pcg_iter<HT, 4, 0, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
+    else k_pcg_iter<HT, 2, 0, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
+  }
 }
 
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {
-  const bool u4 = d.spmv_unroll == 4 || d.spmv_unroll == 8;
-  if (pcg_iters_per_launch(d, window) > 1) {
-    const int g = d.pcg_grid_multi, w = d.pcg_multi;
-    if (d.prec) {
-      if (u4) k_pcg_multi<float, 4><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
-      else k_pcg_multi<float, 2><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
-    } else {
-      if (u4) k_pcg_multi<double, 4><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
-      else k_pcg_multi<double, 2><<<g, 128, 0, s>>>(d, h, use_cond, window, w);
-    }
-    return 1;
-  }
-  const int g = d.pcg_grid_fused;
-  const int b = d.pcg_iter_bound;
+  const bool fr = d.fr_mu > 0.0;
   if (d.prec) {
-    if (b) {
-      if (u4) k_pcg_iter<float, 4, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
-      else k_pcg_iter<float, 2, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    } else {
-      if (u4) k_pcg_iter<float, 4, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
-      else k_pcg_iter<float, 2, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    }
+    if (fr) launch_iter_t<float, true>(d, s, h, use_cond, window);
+    else launch_iter_t<float, false>(d, s, h, use_cond, window);
   } else {
-    if (b) {
-      if (u4) k_pcg_iter<double, 4, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
-      else k_pcg_iter<double, 2, 1><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    } else {
-      if (u4) k_pcg_iter<double, 4, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
-      else k_pcg_iter<double, 2, 0><<<g, 128, 0, s>>>(d, h, use_cond, window);
-    }
+    if (fr) launch_iter_t<double, true>(d, s, h, use_cond, window);
+    else launch_iter_t<double, false>(d, s, h, use_cond, window);
   }
   return 1;
 }
@@ -1027,23 +1127,25 @@ int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, 
 // PCG iterations one launch of the fused kernel runs: pcg_multi, or 1
 // inside a rollout window (which counts single iterations)
 int pcg_iters_per_launch(const Dev& d, unsigned window) {
-  return (d.pcg_fused && !(d.fr_mu > 0.0) && d.pcg_multi > 1 && window == 0xffffffffu) ? d.pcg_multi : 1;
+  return (d.pcg_fused && d.pcg_multi > 1 && window == 0xffffffffu) ? d.pcg_multi : 1;
 }
 
-// resident CTAs per SM of the multi-iteration kernel
-int pcg_multi_ctas_per_sm(int prec, int unroll) {
+// resident CTAs per SM of the multi-iteration kernel (fr: the friction variant)
+int pcg_multi_ctas_per_sm(int prec, int unroll, bool fr) {
   int a = 0;
-  const bool u4 = unroll == 4 || unroll == 8;
-  const void* f = prec ? (u4 ? (const void*)k_pcg_multi<float, 4> : (const void*)k_pcg_multi<float, 2>)
-                       : (u4 ? (const void*)k_pcg_multi<double, 4> : (const void*)k_pcg_multi<double, 2>);
+  const bool u4 = unroll4(unroll);
+  const void* f = prec ? (fr ? pcg_multi_fn_t<float, true>(u4) : pcg_multi_fn_t<float, false>(u4))
+                       : (fr ? pcg_multi_fn_t<double, true>(u4) : pcg_multi_fn_t<double, false>(u4));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, 128, 0);
   return a > 0 ? a : 1;
 }
 
-// resident CTAs per SM of the fused iteration kernel
-int pcg_iter_ctas_per_sm(int prec, int unroll, int bound) {
+// resident CTAs per SM of the single-iteration fused kernel
+int pcg_iter_ctas_per_sm(int prec, int unroll, int bound, bool fr) {
   int a = 0;
-  const void* f = prec ? pcg_iter_fn<float>(unroll, bound) : pcg_iter_fn<double>(unroll, bound);
+  const bool u4 = unroll4(unroll);
+  const void* f = prec ? (fr ? pcg_iter_fn_t<float, true>(u4, bound) : pcg_iter_fn_t<float, false>(u4, bound))
+                       : (fr ? pcg_iter_fn_t<double, true>(u4, bound) : pcg_iter_fn_t<double, false>(u4, bound));
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, f, 128, 0);
   return a > 0 ? a : 1;
 }

@@ -127,6 +127,52 @@ def test_multi_iteration_rollout_window_runs_single_iterations():
     _close(xa, xb, 1e-6)
 
 
+def test_fused_with_friction_matches_three_kernels():
+    """Lagged friction (App. A.3) on: the fused kernels take the friction
+    record groups among an env's products (d_k of the record points formed
+    on the fly, as the pair terms do) and hold to the three-kernel form,
+    where the friction kernel reads d_k after the mat-vec; a driven cube
+    pressed into the gel and dragged along it, FP64 parity tolerances, as
+    lock-step graphs and as a rollout with 8 iterations per launch."""
+    base = scenes.small_contact_scene(body="cube", gap=2e-5, depth=1e-4, n_steps=3)
+    press = base.delta
+
+    def delta(k):
+        dl = press(k).copy()
+        dl[0, 0] = 3e-5 * max(0, k - 2)
+        return dl
+    n = 6
+    for rollout in (False, True):
+        out = []
+        for fused in (1, 0):
+            prm = base.params.parity()
+            prm.friction_mu = 0.5
+            prm.pcg_fused = fused
+            g = ipc.Envs([base.scene], prm, stream=torch.cuda.Stream())
+            mb = max(g.max_bodies, 1)
+            tab = np.zeros((n, 1, mb, 12))
+            for k in range(n):
+                y = g.rest_y(0)
+                y[:, :3] += np.asarray(delta(k)).reshape(-1, 3)[: y.shape[0]]
+                tab[k, 0, : y.shape[0]] = y
+            if rollout:
+                st, steps, _ = g.rollout(n, torch.as_tensor(tab, device="cuda"))
+                assert np.all(steps == n)
+            else:
+                st = np.zeros(1, np.int32)
+                for k in range(n):
+                    g.set_targets_all(tab[k])
+                    s_k, _ = g.step()
+                    st = np.where(st == 0, s_k, st)
+            assert np.all(np.asarray(st) == 0)
+            out.append(g.get_state(0))
+            g.close()
+        a, b = out
+        diag = float(np.linalg.norm(a[0].max(0) - a[0].min(0)))
+        assert np.abs(a[0] - b[0]).max() <= 1e-6 * n * diag
+        assert np.abs(a[2][:, :3] - b[2][:, :3]).max() <= 1e-6 * n * diag
+
+
 def test_fused_profile_class():
     """The profiled (host-driven) loop launches the fused kernel once per
     PCG iteration and none of the three separate ones."""
