@@ -115,7 +115,9 @@ typedef struct {
                              an env's update items start when its own
                              products are in, in the order the envs become
                              ready); 2: the same kernel taking the update
-                             items in env order (each waits for its env);
+                             items in env order (each waits for its env;
+                             with more than one iteration per launch both
+                             run the multi-iteration kernel, env order);
                              0: three kernels (the mat-vecs, then the
                              update).  With friction the fused kernels take
                              the friction records among an env's products.
