@@ -1,23 +1,26 @@
 // Block-Jacobi preconditioned conjugate gradients on H p = -g (K6), the
 // step the paper names as its main cost (Limitations).
 //
-// One PCG iteration is two persistent kernels over a device-side work list
-// of the envs still iterating:
-//   k_pcg_matvec: d_k = z_k + beta_k d_{k-1} (formed on the fly, written to
-//     the other direction buffer), q = A d_k over the SELL-32 matrix, d_k . q
+// Every form works over a device-side work list of the envs still
+// iterating, in items: 128 consecutive rows of one env (one row per
+// thread), a group of 8 active pairs (16 lanes per pair) or of 128 friction
+// records (one per thread).  The per-item work is shared:
+//   matvec_rows: d_k = z_k + beta_k d_{k-1} (formed on the fly, written to
+//     the other direction buffer), q = A d_k over the SELL-32 matrix, d_k.q
 //     summed per env by CTA partials;
-//   k_pcg_pairs (beside it, on a side stream): the contact terms H_c d_k of
-//     the env's active pairs (matrix-free, added to the accumulator qc) and
-//     their part of d_k . q (atomics);
-//   k_pcg_update: alpha = r.z / d.q, p += alpha d, r -= alpha q, z = P^-1 r,
-//     r.z and r.r per env -> beta and the stop test.  The last CTA of the
-//     grid rebuilds the work list when stopped envs hold a quarter of its
-//     items, and (inside a CUDA graph) sets the loop's condition, so the
-//     whole solve runs without the host.
-// A work item is 128 consecutive rows of one env (one row per thread) or a
-// group of 8 active pairs of one env (16 lanes per pair).  The two mat-vec
-// kernels are separate so that the row kernel keeps its small register
-// footprint (occupancy) and the few pair items overlap it.
+//   matvec_pairs / matvec_fric: the contact and friction terms of d_k
+//     (matrix-free, added to the accumulator qc) and their part of d_k.q;
+//   update_rows: alpha = r.z / d.q, p += alpha d, r -= alpha q, z = P^-1 r,
+//     r.z and r.r per env -> beta and the stop test.
+// Three forms run them:
+//   k_pcg_multi (the default): W iterations per persistent launch, each
+//     env's items waiting only for its own earlier ones;
+//   k_pcg_iter: one iteration per launch (inside rollout windows);
+//   k_pcg_matvec + k_pcg_pairs (beside it) + k_fric_spmv, then
+//     k_pcg_update (ipc_params.pcg_fused = 0).
+// The grid's last CTA of each launch rebuilds the work list when stopped
+// envs hold a quarter of its items and (inside a CUDA graph) sets the
+// loop's condition, so the whole solve runs without the host.
 #include "common.cuh"
 #include "fpconv.cuh"
 #include "kernels.h"
