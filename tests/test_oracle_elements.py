@@ -104,6 +104,44 @@ def test_elastic_zero_at_rest_and_rigid_motion():
         assert np.abs(en.tet_grad(x[None], Dmi, V, mu, lam)).max() < 1e-12 * mu * 1e-6
 
 
+def test_elastic_frame_indifferent_at_deformed_states():
+    """A rotation R and a translation of a deformed tet leave the energy
+    unchanged and rotate its gradient (g_i -> R g_i) and its projected
+    Hessian (H -> Q H Q^T, Q = diag(R, R, R, R)): the energy depends on F
+    only through F^T F, as a neo-Hookean energy must (a term in F itself,
+    or a transposed F, fails this away from the rest state)."""
+    mu, lam = lame(3e5, 0.45)
+    for _ in range(5):
+        X, Dmi, V = _tet(RNG)
+        x = X + RNG.normal(scale=1.5e-4, size=X.shape)   # ~15% strains, det F > 0
+        R = _rand_rot(RNG)
+        xr = x @ R.T + RNG.normal(size=3)
+        E0 = en.tet_energy(x[None], Dmi, V, mu, lam)[0]
+        E1 = en.tet_energy(xr[None], Dmi, V, mu, lam)[0]
+        assert E0 > 0 and E1 == pytest.approx(E0, rel=1e-9)
+        g0 = en.tet_grad(x[None], Dmi, V, mu, lam)[0].reshape(4, 3)
+        g1 = en.tet_grad(xr[None], Dmi, V, mu, lam)[0].reshape(4, 3)
+        assert np.allclose(g1, g0 @ R.T, rtol=1e-8, atol=1e-10 * np.abs(g0).max())
+        Q = np.kron(np.eye(4), R)
+        for project in (False, True):
+            H0 = en.tet_hess(x[None], Dmi, V, mu, lam, project=project)[0]
+            H1 = en.tet_hess(xr[None], Dmi, V, mu, lam, project=project)[0]
+            assert np.allclose(H1, Q @ H0 @ Q.T, rtol=1e-7, atol=1e-9 * np.abs(H0).max())
+
+
+def test_orthogonality_invariant_under_rotations_of_either_side():
+    """|A A^T - I|_F^2 is unchanged by A -> R A and by A -> A R for
+    rotations R (the columns of A, the body's affine axes, rotate
+    together), at non-orthogonal A."""
+    for _ in range(5):
+        A = _rand_rot(RNG) + RNG.normal(scale=0.1, size=(3, 3))
+        R = _rand_rot(RNG)
+        e0 = en.orth_energy(A.T.ravel())
+        assert e0 > 0
+        assert en.orth_energy((R @ A).T.ravel()) == pytest.approx(e0, rel=1e-10)
+        assert en.orth_energy((A @ R).T.ravel()) == pytest.approx(e0, rel=1e-10)
+
+
 def test_elastic_gradient_and_hessian_fd():
     mu, lam = lame(3e5, 0.45)
     X, Dmi, V = _tet(RNG)
