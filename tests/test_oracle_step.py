@@ -89,6 +89,38 @@ def test_config0_invariants_and_monotone_energy():
     assert out[-1][4].min_dist < sc.params.dhat
 
 
+def test_step_is_translation_invariant():
+    """Moving the whole scene (gel, body, and with them the pinned vertices
+    and the driven body's targets) by a constant vector moves every step's
+    result by that vector: no absolute position enters the step (a body
+    mapped through x = A X instead of p + A (X - X_c), or a contact test on
+    absolute coordinates, would fail).  Three contact steps of a driven
+    sphere at the parity tolerances."""
+    import copy
+    sc = scenes.small_contact_scene(body="sphere", driven=True, depth=2e-4, n_steps=3)
+    c = np.array([0.0125, -0.0375, 0.00625])           # exact in binary: no rounding of the shift
+    moved = copy.deepcopy(sc.scene)
+    moved.gel_x = moved.gel_x + c
+    for b in moved.bodies:
+        b.rest_x = b.rest_x + c
+    prm = sc.params.parity()
+    ea, eb = OracleEnv(sc.scene, prm), OracleEnv(moved, prm)
+    sa, sb = ea.rest_state(), eb.rest_state()
+    diag = float(np.linalg.norm(sc.scene.gel_x.max(0) - sc.scene.gel_x.min(0)))
+    touched = False
+    for s in range(3):
+        sa = ea.step(*sa, ea.targets_from_delta(sc.delta(s)))
+        sb = eb.step(*sb, eb.targets_from_delta(sc.delta(s)))
+        assert sa[4].status == 0 and sb[4].status == 0
+        assert np.abs((sb[0] - c) - sa[0]).max() <= 1e-9 * diag
+        assert np.abs((sb[2][:, :3] - c) - sa[2][:, :3]).max() <= 1e-9 * diag
+        assert np.abs(sb[2][:, 3:] - sa[2][:, 3:]).max() <= 1e-9
+        assert np.abs(sb[1] - sa[1]).max() <= 1e-9 * diag / prm.dt
+        touched |= sa[4].min_dist < prm.dhat
+        sa, sb = sa[:4], sb[:4]
+    assert touched
+
+
 def test_converged_step_is_stationary():
     sc = scenes.small_contact_scene(body="sphere", driven=True, depth=2e-4, n_steps=3)
     prm = sc.params.parity()
