@@ -1034,7 +1034,6 @@ __global__ void k_debug_q_to_rows(Dev d) {
 
 // ---------------------------------------------------------------------------
 // launchers
-static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
 int launch_pcg_init(const Dev& d, cudaStream_t s) {
   if (d.prec) k_pcg_init<float><<<d.n_rows / 128, 128, 0, s>>>(d);
