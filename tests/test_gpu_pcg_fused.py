@@ -133,7 +133,8 @@ def test_fused_with_friction_matches_three_kernels():
     on the fly, as the pair terms do) and hold to the three-kernel form,
     where the friction kernel reads d_k after the mat-vec; a driven cube
     pressed into the gel and dragged along it, FP64 parity tolerances, as
-    lock-step graphs and as a rollout with 8 iterations per launch."""
+    lock-step graphs, as a rollout with 8 iterations per launch, and as a
+    rollout with a PCG window of 2 (one iteration per launch)."""
     base = scenes.small_contact_scene(body="cube", gap=2e-5, depth=1e-4, n_steps=3)
     press = base.delta
 
@@ -142,12 +143,13 @@ def test_fused_with_friction_matches_three_kernels():
         dl[0, 0] = 3e-5 * max(0, k - 2)
         return dl
     n = 6
-    for rollout in (False, True):
+    for rollout, window in ((False, 0), (True, 0), (True, 2)):
         out = []
         for fused in (1, 0):
             prm = base.params.parity()
             prm.friction_mu = 0.5
             prm.pcg_fused = fused
+            prm.rollout_pcg_window = window
             g = ipc.Envs([base.scene], prm, stream=torch.cuda.Stream())
             mb = max(g.max_bodies, 1)
             tab = np.zeros((n, 1, mb, 12))
