@@ -217,8 +217,9 @@ const char* ipc_last_error(const ipc_ctx* ctx);
  *     iteration).
  *   mode 1: each PCG solve (the block-Jacobi PCG of every Newton iteration,
  *     named as the method's main cost in the paper's Limitations) is one
- *     graph: a work-list kernel, then a WHILE node over one iteration whose
- *     condition the update kernel sets on the device.
+ *     graph: a work-list kernel, then a WHILE node over one launch of the
+ *     PCG kernel (pcg_iters_per_launch iterations) whose condition its
+ *     last CTA sets on the device.
  *   mode 2: the whole step is one graph: nested WHILE / IF nodes for the
  *     Newton loop, the PCG solve, the line-search gate and the line-search
  *     trials, all conditions set on the device and every loop bounded by
