@@ -772,7 +772,7 @@ def run_ours(args):
             e_last, _ = per_step_error(g64, genv, dev_tg[n_total], 4e-3)
             err_dist = error_distribution([e_first, e_last])
             rel_err = err_dist["max"]
-        # the benchmark spec's comparison: the plain per-environment FP64 GPU path
+        # the metric's comparison: the plain per-environment FP64 GPU path
         if rank == 0 and not args.no_per_env:
             plain64 = per_env_fp64(scene, params, deltas, snap64, args.warmup, [0, 1], min(args.steps, 10), dev)
         # the FP64 oracle on the host cores: one step of `cores` envs from the
