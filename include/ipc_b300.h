@@ -498,6 +498,18 @@ ipc_status ipc_debug_pairs(ipc_ctx* ctx, int env, const double* cv_x, const doub
 /* First Newton direction of one env from its current state (PCG solve). */
 ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters);
 
+/* Failure path of the multi-iteration PCG kernel's bounded waits: assembles
+ * env's system from its current state, starts its PCG solve, sets its
+ * count of completed update rounds to -1 (so its first products wait for a
+ * round that nothing completes) and runs one launch of the kernel.  The
+ * waits give up after about a second; the kernel ends the env's step with
+ * IPC_ECUDA (*env_status) and resets its counters, and the context stays
+ * usable (set_state, then step, as after any failed step).  *ms: the
+ * launch's device time.  Synchronises.  IPC_EINVAL when the context does
+ * not run the multi-iteration kernel (pcg_fused 0 or pcg_iters_per_launch
+ * 1).  A test aid of this library (no counterpart in the paper). */
+ipc_status ipc_debug_pcg_wait_out(ipc_ctx* ctx, int env, int* env_status, float* ms);
+
 /* Largest CCD-safe step along dir (ACCD over the swept candidates). */
 ipc_status ipc_debug_accd(ipc_ctx* ctx, int env, const double* dir, double* alpha);
 

@@ -1682,6 +1682,39 @@ ipc_status ipc_debug_newton_dir(ipc_ctx* ctx, int env, double* p, int* pcg_iters
   return IPC_OK;
 }
 
+ipc_status ipc_debug_pcg_wait_out(ipc_ctx* ctx, int env, int* env_status, float* ms) {
+  if (check_env(ctx, env) != IPC_OK) return IPC_EINVAL;
+  const Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  if (pcg_iters_per_launch(d, 0xffffffffu) <= 1) {
+    ctx->err = "pcg_wait_out: needs the multi-iteration PCG kernel (pcg_fused > 0, pcg_iters_per_launch > 1)";
+    return IPC_EINVAL;
+  }
+  ipc_status st;
+  if ((st = begin_single(ctx, env)) != IPC_OK) return st;
+  if ((st = assemble_system(ctx, s)) != IPC_OK) return st;
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_init(d, s); });
+  KL(ctx, KC_PCGINIT, [&] { return launch_pcg_begin(d, s, 0, 0); });
+  // the env's first products wait for an update round that never completes
+  KL(ctx, KC_MISC, [&] { return launch_debug_set_updk(d, env, -1, s); });
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, s));
+  pcg_iteration(ctx, s);
+  CK(cudaEventRecord(b, s));
+  CK(cudaEventSynchronize(b));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if ((st = last_cuda(ctx)) != IPC_OK) return st;
+  if ((st = sync_flags(ctx)) != IPC_OK) return st;
+  if (env_status) *env_status = ctx->h_int[env * NUM_INTS + I_STATUS];
+  if (ms) *ms = t;
+  return IPC_OK;
+}
+
 ipc_status ipc_debug_pairs(ipc_ctx* ctx, int env, const double* cv_x, const double* cv_x_end, int32_t* out,
                            int capacity, int* n_pairs) {
   if (check_env(ctx, env) != IPC_OK || !cv_x) return IPC_EINVAL;

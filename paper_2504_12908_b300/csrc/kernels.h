@@ -43,6 +43,7 @@ int launch_pcg_begin(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h,
 int launch_pcg_matvec(const Dev& d, cudaStream_t s);
 int launch_pcg_pairs(const Dev& d, cudaStream_t s);
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window);
+int launch_debug_set_updk(const Dev& d, int env, int v, cudaStream_t s);
 int pcg_iter_ctas_per_sm(int prec, int unroll, int bound, bool fr);
 int pcg_multi_ctas_per_sm(int prec, int unroll, bool fr);
 int pcg_iters_per_launch(const Dev& d, unsigned window);

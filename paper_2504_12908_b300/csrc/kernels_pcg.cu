@@ -1003,6 +1003,13 @@ __global__ void __launch_bounds__(128, sizeof(HT) == 4 ? 12 : 6)
   pcg_iteration_end(d, h, use_cond, window, (unsigned)W, true);
 }
 
+// diagnostics: env e's count of completed update rounds set to v (-1: its
+// first products wait for a round that nothing completes, so the bounded
+// waits of the multi-iteration kernel run out)
+__global__ void k_debug_set_updk(Dev d, int e, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ENVI(d, e, I_UPDK) = v;
+}
+
 // diagnostics: the direction v (FP64 rows staged in Dev::z) as z with
 // beta = 0 and d_{-1} = 0, so that one mat-vec item computes H v
 template <class HT>
@@ -1112,6 +1119,11 @@ static void launch_iter_t(const Dev& d, cudaStream_t s, cudaGraphConditionalHand
     if (u4) k_pcg_iter<HT, 4, 0, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
     else k_pcg_iter<HT, 2, 0, FR><<<g, 128, 0, s>>>(d, h, use_cond, window);
   }
+}
+
+int launch_debug_set_updk(const Dev& d, int env, int v, cudaStream_t s) {
+  k_debug_set_updk<<<1, 32, 0, s>>>(d, env, v);
+  return 1;
 }
 
 int launch_pcg_iter(const Dev& d, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond, unsigned window) {

@@ -112,6 +112,7 @@ def lib():
             "ipc_debug_eval": (i32, [vp, i32, _dp, _dp, _dp, _dp]),
             "ipc_debug_pairs": (i32, [vp, i32, _dp, _dp, _ip, i32, C.POINTER(i32)]),
             "ipc_debug_newton_dir": (i32, [vp, i32, _dp, C.POINTER(i32)]),
+            "ipc_debug_pcg_wait_out": (i32, [vp, i32, C.POINTER(i32), C.POINTER(C.c_float)]),
             "ipc_debug_accd": (i32, [vp, i32, _dp, _dp]),
             "ipc_profile_enable": (i32, [vp, i32]),
             "ipc_profile_reset": (i32, [vp]),
@@ -139,7 +140,7 @@ EXPORTED = ["ipc_default_params", "ipc_workspace_bytes", "ipc_create_envs", "ipc
             "ipc_set_targets_all", "ipc_set_targets_all_device", "ipc_step", "ipc_step_results", "ipc_rollout", "ipc_rollout_results", "ipc_read_gel_surface", "ipc_read_gel_surface_all",
             "ipc_read_gel_surface_all_noalloc", "ipc_env_stats", "ipc_set_graph_mode", "ipc_gel_vertex_rows", "ipc_sensor_triangles",
             "ipc_tactile_maps_device", "ipc_markers_device", "ipc_autotune",
-            "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_accd",
+            "ipc_debug_eval", "ipc_debug_pairs", "ipc_debug_newton_dir", "ipc_debug_pcg_wait_out", "ipc_debug_accd",
             "ipc_profile_enable", "ipc_profile_reset", "ipc_profile_count", "ipc_profile_get", "ipc_launch_count",
             "ipc_system_sizes", "ipc_k_tet", "ipc_k_barrier", "ipc_k_accd", "ipc_fma_peaks"]
 
@@ -630,6 +631,13 @@ class Envs:
         it = C.c_int()
         self._check(lib().ipc_debug_newton_dir(self._ctx, env, _ptr(p, _dp), C.byref(it)), "ipc_debug_newton_dir")
         return p, it.value
+
+    def debug_pcg_wait_out(self, env: int):
+        """Make the multi-iteration PCG kernel's bounded waits run out for
+        env (ipc_debug_pcg_wait_out): (the env's status, the launch's ms)."""
+        st, ms = C.c_int(), C.c_float()
+        self._check(lib().ipc_debug_pcg_wait_out(self._ctx, env, C.byref(st), C.byref(ms)), "ipc_debug_pcg_wait_out")
+        return st.value, float(ms.value)
 
     def debug_accd(self, env: int, direction: np.ndarray) -> float:
         a = np.zeros(1)

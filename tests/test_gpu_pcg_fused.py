@@ -175,6 +175,42 @@ def test_fused_with_friction_matches_three_kernels():
         assert np.abs(a[2][:, :3] - b[2][:, :3]).max() <= 1e-6 * n * diag
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a GPU fault: one env's products are made to
+    wait for an update round that nothing completes (ipc_debug_pcg_wait_out).
+    The waits give up after about a second, the kernel ends that env's step
+    with IPC_ECUDA, and the context goes on: the same env steps normally
+    from a set state afterwards, and its result equals a fresh context's."""
+    scs = _batch()[:2]
+    prm = scenes.SolverParams().parity()
+    g = ipc.Envs([sc.scene for sc in scs], prm, stream=torch.cuda.Stream())
+    tab = _table(g, scs, 0, 2)
+    g.set_targets_all(tab[0])
+    st, _ = g.step()
+    assert np.all(st == 0)
+    state = [g.get_state(e) for e in range(2)]
+    status, ms = g.debug_pcg_wait_out(0)
+    assert status == ipc.IPC_ECUDA
+    assert 200.0 < ms < 10000.0, ms                  # the ~1 s limit, not a hang
+    # the context is usable: restore the state and take the next step
+    for e in range(2):
+        assert g.set_state(e, *state[e]) == ipc.IPC_OK
+    g.set_targets_all(tab[1])
+    st, _ = g.step()
+    assert np.all(st == 0)
+    after = [g.get_state(e) for e in range(2)]
+    g.close()
+    h = ipc.Envs([sc.scene for sc in scs], prm, stream=torch.cuda.Stream())
+    for e in range(2):
+        assert h.set_state(e, *state[e]) == ipc.IPC_OK
+    h.set_targets_all(tab[1])
+    st, _ = h.step()
+    assert np.all(st == 0)
+    ref = [h.get_state(e) for e in range(2)]
+    h.close()
+    _close(after, ref, 1e-6 / K)
+
+
 def test_fused_profile_class():
     """The profiled (host-driven) loop launches the fused kernel once per
     PCG iteration and none of the three separate ones."""
